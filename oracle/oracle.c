@@ -1,0 +1,789 @@
+/*
+ * CPU oracle -- TEST INFRASTRUCTURE ONLY (see oracle.h).  Plain float64 C,
+ * compiled with -ffp-contract=off so that every + - * / sqrt is a single
+ * correctly rounded IEEE operation.  Parity: pinned by tests/test_oracle_*.py
+ * (closed forms, exact enumeration and detailed balance on lattice worlds,
+ * prior-only chains, brute-force differences, numpy's Philox).
+ *
+ * Model (§Generative Model of Seismic Signals, with the attenuating,
+ * finite-reach extension that §Partitioning the World names as the case where
+ * a spatial partition is natural):
+ *   event e = (x, y, t, m) in [0,W)^2 x [0,T) x [2, inf)
+ *   prior: Poisson process with intensity beta(e) = Lambda/(W^2 T) exp(-(m-2));
+ *          log-density  -Lambda + sum_i log beta(e_i)
+ *   arrival at station j: a = t + d/v  (d = distance, deterministic arrival)
+ *   the event reaches station j iff d < R_max
+ *   variance added at sample k (time k/f): (A g(k/f - a))^2 for
+ *          k in [ceil(a f), ceil(a f) + n_w), A = exp(alpha m - beta_att d),
+ *          g(u) = exp(-u / tau)
+ *   s_jk ~ N(0, V_jk), V_jk = noise_var + sum of the variances above
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* Planted mistakes for the pin tests (tests/test_oracle_mutants.py build the
+ * oracle with -DORC_MUTANT=n and check that some pin fails):
+ *   1: birth ratio uses 1/(n+2) for the reverse death;  2: death drops log q_b;
+ *   3: an arrival adds its standard deviation instead of its variance;
+ *   4: a move ignores the prior ratio.  0 (the default) is the oracle itself. */
+#ifndef ORC_MUTANT
+#define ORC_MUTANT 0
+#endif
+
+typedef struct { double x, y, t, m; uint64_t id; } ev_t;
+
+struct orc_world {
+    orc_params p;
+    int32_t n_st;
+    double* st;          /* [n_st][2], owned copy */
+    const void* sig;     /* [n_st][pitch], caller-owned */
+    int32_t f32;
+    int64_t n_samp, pitch;
+};
+
+struct orc_set { ev_t* e; int64_t n, cap; };
+
+/* ------------------------------------------------------------------------
+ * Philox4x64-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11).  Round: two 64x64->128 products of the counter's
+ * even words with fixed multipliers, the high halves xored with the odd words
+ * and the key, the key bumped by the Weyl constants between rounds.
+ * ---------------------------------------------------------------------- */
+static const uint64_t PHILOX_M0 = 0xD2E7470EE14C6C93ULL;
+static const uint64_t PHILOX_M1 = 0xCA5A826395121157ULL;
+static const uint64_t PHILOX_W0 = 0x9E3779B97F4A7C15ULL;
+static const uint64_t PHILOX_W1 = 0xBB67AE8584CAA73BULL;
+
+void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        unsigned __int128 p0 = (unsigned __int128)PHILOX_M0 * x0;
+        unsigned __int128 p1 = (unsigned __int128)PHILOX_M1 * x2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        x0 = hi1 ^ x1 ^ k0;
+        x1 = lo1;
+        x2 = hi0 ^ x3 ^ k1;
+        x3 = lo0;
+        k0 += PHILOX_W0;
+        k1 += PHILOX_W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* uniform in [0,1) from the top 53 bits */
+static double u01(uint64_t w) { return (double)(w >> 11) * (1.0 / 9007199254740992.0); }
+/* uniform in (0,1] */
+static double u01o(uint64_t w) { return (double)((w >> 11) + 1) * (1.0 / 9007199254740992.0); }
+/* uniform integer in [0, n) from the low 32 bits */
+static int64_t pick(uint64_t w, int64_t n) { return (int64_t)(((w & 0xffffffffULL) * (uint64_t)n) >> 32); }
+
+/* eight 64-bit words of one MH step: counter (c0, c1, c2, 0|1), key (seed, stream) */
+static void step_words(const orc_world* w, uint64_t stream, uint64_t c0, uint64_t c1, uint64_t c2,
+                       uint64_t out[8]) {
+    uint64_t key[2] = { w->p.seed, stream };
+    uint64_t ctr[4] = { c0, c1, c2, 0 };
+    orc_philox4x64(ctr, key, out);
+    ctr[3] = 1;
+    orc_philox4x64(ctr, key, out + 4);
+}
+
+/* ------------------------------------------------------------------------
+ * world and event sets
+ * ---------------------------------------------------------------------- */
+orc_world* orc_world_new(const orc_params* p, const double* stations, int32_t n_st,
+                         const void* signals, int32_t signals_f32, int64_t n_samp, int64_t pitch) {
+    orc_world* w = (orc_world*)calloc(1, sizeof(orc_world));
+    w->p = *p;
+    w->n_st = n_st;
+    w->st = (double*)malloc(sizeof(double) * 2 * (size_t)(n_st > 0 ? n_st : 1));
+    if (n_st > 0) memcpy(w->st, stations, sizeof(double) * 2 * (size_t)n_st);
+    w->sig = signals;
+    w->f32 = signals_f32;
+    w->n_samp = n_samp;
+    w->pitch = pitch;
+    return w;
+}
+
+void orc_world_free(orc_world* w) {
+    if (!w) return;
+    free(w->st);
+    free(w);
+}
+
+static double sig_at(const orc_world* w, int32_t j, int64_t k) {
+    if (w->f32) return (double)((const float*)w->sig)[(int64_t)j * w->pitch + k];
+    return ((const double*)w->sig)[(int64_t)j * w->pitch + k];
+}
+
+orc_set* orc_set_new(const double* ev, const uint64_t* ids, int64_t n) {
+    orc_set* s = (orc_set*)calloc(1, sizeof(orc_set));
+    s->cap = n > 16 ? n : 16;
+    s->e = (ev_t*)malloc(sizeof(ev_t) * (size_t)s->cap);
+    s->n = n;
+    for (int64_t i = 0; i < n; ++i) {
+        s->e[i].x = ev[4 * i]; s->e[i].y = ev[4 * i + 1];
+        s->e[i].t = ev[4 * i + 2]; s->e[i].m = ev[4 * i + 3];
+        s->e[i].id = ids ? ids[i] : (uint64_t)i;
+    }
+    return s;
+}
+int64_t orc_set_size(const orc_set* s) { return s->n; }
+void orc_set_get(const orc_set* s, double* ev, uint64_t* ids) {
+    for (int64_t i = 0; i < s->n; ++i) {
+        ev[4 * i] = s->e[i].x; ev[4 * i + 1] = s->e[i].y;
+        ev[4 * i + 2] = s->e[i].t; ev[4 * i + 3] = s->e[i].m;
+        if (ids) ids[i] = s->e[i].id;
+    }
+}
+void orc_set_free(orc_set* s) {
+    if (!s) return;
+    free(s->e);
+    free(s);
+}
+
+static void to_ev(const double* a, ev_t* e) { e->x = a[0]; e->y = a[1]; e->t = a[2]; e->m = a[3]; e->id = 0; }
+
+/* ------------------------------------------------------------------------
+ * likelihood pieces (§Generative Model: the observed signal is a zero-mean
+ * diagonal Gaussian whose per-sample variance is the noise variance plus the
+ * variances of the arriving event signals)
+ * ---------------------------------------------------------------------- */
+typedef struct { int reach; int64_t k0; double a, amp; } arr_t;
+
+/* arrival of event e at station j: a = t + d/v (mean of the arrival-time
+ * distribution of §Event Detections; the jitter is zero here) */
+static arr_t arrival_of(const orc_world* w, const ev_t* e, int32_t j) {
+    arr_t r;
+    double dx = e->x - w->st[2 * j];
+    double dy = e->y - w->st[2 * j + 1];
+    double d = sqrt(dx * dx + dy * dy);
+    r.reach = d < w->p.R_max;
+    r.a = e->t + d / w->p.v;
+    r.k0 = (int64_t)ceil(r.a * w->p.f_hz);
+    r.amp = exp(w->p.alpha * e->m - w->p.beta_att * d);
+    return r;
+}
+
+/* variance this arrival adds at sample k */
+static double arr_var(const orc_world* w, const arr_t* r, int64_t k) {
+    if (!r->reach || k < r->k0 || k >= r->k0 + w->p.n_w) return 0.0;
+    double u = (double)k / w->p.f_hz - r->a;
+    double sd = r->amp * exp(-u / w->p.tau);
+    return ORC_MUTANT == 3 ? sd : sd * sd;
+}
+
+static double log_normal0(double s, double V) {
+    return -0.5 * log(2.0 * M_PI * V) - s * s / (2.0 * V);
+}
+
+void orc_variance(const orc_world* w, const double* ev, int64_t n, int32_t j,
+                  int64_t k0, int64_t k1, double* out) {
+    arr_t* ar = (arr_t*)malloc(sizeof(arr_t) * (size_t)(n > 0 ? n : 1));
+    int64_t na = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        ev_t e; to_ev(ev + 4 * i, &e);
+        arr_t a = arrival_of(w, &e, j);
+        if (a.reach) ar[na++] = a;
+    }
+    for (int64_t k = k0; k < k1; ++k) {
+        double V = w->p.noise_var;
+        for (int64_t i = 0; i < na; ++i) V += arr_var(w, &ar[i], k);
+        out[k - k0] = V;
+    }
+    free(ar);
+}
+
+double orc_log_likelihood(const orc_world* w, const double* ev, int64_t n) {
+    double total = 0.0;
+    double* V = (double*)malloc(sizeof(double) * (size_t)(w->n_samp > 0 ? w->n_samp : 1));
+    for (int32_t j = 0; j < w->n_st; ++j) {
+        orc_variance(w, ev, n, j, 0, w->n_samp, V);
+        for (int64_t k = 0; k < w->n_samp; ++k) total += log_normal0(sig_at(w, j, k), V[k]);
+    }
+    free(V);
+    return total;
+}
+
+/* ------------------------------------------------------------------------
+ * prior (§Generative Model, "Event prior"): Poisson count, uniform location
+ * and time; magnitude 2 + Exp(1).  Written as a Poisson-process density:
+ * -Lambda + sum log beta(e).  Lattice mode restricts coordinates to a grid
+ * and beta to point masses (used only by the enumeration tests).
+ * ---------------------------------------------------------------------- */
+static int lat_index(double v, double v0, double dv, int32_t n) {
+    double f = (v - v0) / dv;
+    double r = rint(f);
+    if (fabs(f - r) > 1e-9 || r < 0 || r >= n) return -1;
+    return (int)r;
+}
+
+static double lat_log_wm(const orc_params* p, int im) {
+    double z = 0.0;
+    for (int i = 0; i < p->lat_nm; ++i) z += exp(-(p->lat_m0 + i * p->lat_dm - 2.0));
+    return -(p->lat_m0 + im * p->lat_dm - 2.0) - log(z);
+}
+
+static double log_beta(const orc_world* w, const ev_t* e) {
+    const orc_params* p = &w->p;
+    if (p->lattice) {
+        int ix = lat_index(e->x, p->lat_x0, p->lat_dx, p->lat_nx);
+        int iy = lat_index(e->y, p->lat_y0, p->lat_dy, p->lat_ny);
+        int it = lat_index(e->t, p->lat_t0, p->lat_dt, p->lat_nt);
+        int im = lat_index(e->m, p->lat_m0, p->lat_dm, p->lat_nm);
+        if (ix < 0 || iy < 0 || it < 0 || im < 0) return -INFINITY;
+        return log(p->Lambda) - log((double)p->lat_nx * p->lat_ny) - log((double)p->lat_nt)
+               + lat_log_wm(p, im);
+    }
+    if (!(e->x >= 0.0 && e->x < p->W && e->y >= 0.0 && e->y < p->W &&
+          e->t >= 0.0 && e->t < p->T && e->m >= 2.0))
+        return -INFINITY;
+    return log(p->Lambda) - log(p->W * p->W * p->T) - (e->m - 2.0);
+}
+
+double orc_log_prior(const orc_world* w, const double* ev, int64_t n) {
+    double lp = -w->p.Lambda;
+    for (int64_t i = 0; i < n; ++i) {
+        ev_t e; to_ev(ev + 4 * i, &e);
+        lp += log_beta(w, &e);
+    }
+    return lp;
+}
+
+/* ------------------------------------------------------------------------
+ * log-likelihood change of one proposal: the event own[old_idx] (if any) is
+ * replaced by cand (if any); context = own + oth.  Plain definition: for every
+ * station and sample whose variance changes, the difference of the two
+ * Gaussian log-densities, each variance summed from scratch.
+ * ---------------------------------------------------------------------- */
+static double delta_ll2(const orc_world* w, const ev_t* own, int64_t n_own, const ev_t* oth,
+                        int64_t n_oth, int64_t old_idx, const ev_t* cand) {
+    double total = 0.0;
+    int64_t cap = n_own + n_oth;
+    arr_t* ar = (arr_t*)malloc(sizeof(arr_t) * (size_t)(cap > 0 ? cap : 1));
+    for (int32_t j = 0; j < w->n_st; ++j) {
+        arr_t ao = { 0, 0, 0.0, 0.0 }, an = { 0, 0, 0.0, 0.0 };
+        if (old_idx >= 0) ao = arrival_of(w, &own[old_idx], j);
+        if (cand) an = arrival_of(w, cand, j);
+        if (!ao.reach && !an.reach) continue;
+        int64_t lo = INT64_MAX, hi = INT64_MIN;
+        if (ao.reach) { if (ao.k0 < lo) lo = ao.k0; if (ao.k0 + w->p.n_w > hi) hi = ao.k0 + w->p.n_w; }
+        if (an.reach) { if (an.k0 < lo) lo = an.k0; if (an.k0 + w->p.n_w > hi) hi = an.k0 + w->p.n_w; }
+        if (lo < 0) lo = 0;
+        if (hi > w->n_samp) hi = w->n_samp;
+        if (lo >= hi) continue;
+        int64_t na = 0;
+        for (int64_t i = 0; i < n_own; ++i) {
+            if (i == old_idx) continue;
+            arr_t a = arrival_of(w, &own[i], j);
+            if (a.reach) ar[na++] = a;
+        }
+        for (int64_t i = 0; i < n_oth; ++i) {
+            arr_t a = arrival_of(w, &oth[i], j);
+            if (a.reach) ar[na++] = a;
+        }
+        for (int64_t k = lo; k < hi; ++k) {
+            double base = w->p.noise_var;
+            for (int64_t i = 0; i < na; ++i) base += arr_var(w, &ar[i], k);
+            double V_old = base + arr_var(w, &ao, k);
+            double V_new = base + arr_var(w, &an, k);
+            double s = sig_at(w, j, k);
+            total += log_normal0(s, V_new) - log_normal0(s, V_old);
+        }
+    }
+    free(ar);
+    return total;
+}
+
+double orc_delta_loglik(const orc_world* w, const double* ev, int64_t n,
+                        int64_t old_idx, const double* cand) {
+    ev_t* own = (ev_t*)malloc(sizeof(ev_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) to_ev(ev + 4 * i, &own[i]);
+    ev_t c;
+    if (cand) to_ev(cand, &c);
+    double d = delta_ll2(w, own, n, NULL, 0, old_idx, cand ? &c : NULL);
+    free(own);
+    return d;
+}
+
+/* ------------------------------------------------------------------------
+ * spatial partition (§Partitioning the World, in two spatial dimensions):
+ * square cells of side L whose boundaries are shifted by (sx, sy);
+ * cell index ix = floor((x - sx)/L) + 1.  Cells whose indices differ by a
+ * multiple of the period p = ceil(2 R_max / L) + 1 in both axes share a colour;
+ * their nearest points are >= (p-1) L >= 2 R_max apart, so no station lies
+ * within R_max of both: same-colour regions have disjoint Markov blankets.
+ * ---------------------------------------------------------------------- */
+int32_t orc_period(const orc_world* w) { return (int32_t)ceil(2.0 * w->p.R_max / w->p.L) + 1; }
+
+void orc_grid_dims(const orc_world* w, int32_t* ncx, int32_t* ncy) {
+    int32_t n = (int32_t)floor(w->p.W / w->p.L) + 2;
+    *ncx = n;
+    *ncy = n;
+}
+
+int32_t orc_cell_of(const orc_world* w, double sx, double sy, double x, double y) {
+    int32_t ncx, ncy;
+    orc_grid_dims(w, &ncx, &ncy);
+    int32_t ix = (int32_t)floor((x - sx) / w->p.L) + 1;
+    int32_t iy = (int32_t)floor((y - sy) / w->p.L) + 1;
+    if (ix < 0 || ix >= ncx || iy < 0 || iy >= ncy) return -1;
+    return iy * ncx + ix;
+}
+
+void orc_cell_rect(const orc_world* w, double sx, double sy, int32_t cell, double* r4) {
+    int32_t ncx, ncy;
+    orc_grid_dims(w, &ncx, &ncy);
+    int32_t ix = cell % ncx, iy = cell / ncx;
+    double x0 = sx + (double)(ix - 1) * w->p.L, x1 = sx + (double)ix * w->p.L;
+    double y0 = sy + (double)(iy - 1) * w->p.L, y1 = sy + (double)iy * w->p.L;
+    if (x0 < 0.0) x0 = 0.0;
+    if (y0 < 0.0) y0 = 0.0;
+    if (x1 > w->p.W) x1 = w->p.W;
+    if (y1 > w->p.W) y1 = w->p.W;
+    r4[0] = x0; r4[1] = x1; r4[2] = y0; r4[3] = y1;
+}
+
+int32_t orc_colour_of(const orc_world* w, int32_t cell) {
+    int32_t ncx, ncy, p = orc_period(w);
+    orc_grid_dims(w, &ncx, &ncy);
+    int32_t ix = cell % ncx, iy = cell / ncx;
+    return (ix % p) + p * (iy % p);
+}
+
+/* §Chromatic MH with Dynamic Coloring: a uniform offset in [0, L) per axis,
+ * drawn from Philox stream 1 at counter (sweep, 0, 0, 0) */
+void orc_shift(const orc_world* w, int64_t sweep, double* sx, double* sy) {
+    uint64_t key[2] = { w->p.seed, 1 };
+    uint64_t ctr[4] = { (uint64_t)sweep, 0, 0, 0 };
+    uint64_t out[4];
+    orc_philox4x64(ctr, key, out);
+    *sx = u01(out[0]) * w->p.L;
+    *sy = u01(out[1]) * w->p.L;
+}
+
+static int cell_live(const double* r) { return r[1] > r[0] && r[3] > r[2]; }
+
+void orc_blankets(const orc_world* w, double sx, double sy, uint8_t* member) {
+    int32_t ncx, ncy;
+    orc_grid_dims(w, &ncx, &ncy);
+    for (int32_t c = 0; c < ncx * ncy; ++c) {
+        double r[4];
+        orc_cell_rect(w, sx, sy, c, r);
+        for (int32_t j = 0; j < w->n_st; ++j) {
+            uint8_t in = 0;
+            if (cell_live(r)) {
+                double xs = w->st[2 * j], ys = w->st[2 * j + 1];
+                double dx = 0.0, dy = 0.0;
+                if (xs < r[0]) dx = r[0] - xs; else if (xs > r[1]) dx = xs - r[1];
+                if (ys < r[2]) dy = r[2] - ys; else if (ys > r[3]) dy = ys - r[3];
+                in = sqrt(dx * dx + dy * dy) < w->p.R_max;
+            }
+            member[(int64_t)c * w->n_st + j] = in;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * proposals (§Generative Model, the MH moves: birth from a uniform
+ * distribution, death of an existing event, Gaussian location move), restricted
+ * to one region as in Algorithm "Chromatic MH with Static Coloring".
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t cell;          /* -1: whole domain (serial sampler) */
+    double r[4];           /* x0, x1, y0, y1 of the region within the domain */
+    double sx, sy;
+} region_t;
+
+static int in_region(const orc_world* w, const region_t* g, const ev_t* e) {
+    const orc_params* p = &w->p;
+    if (!(e->x >= 0.0 && e->x < p->W && e->y >= 0.0 && e->y < p->W)) return 0;
+    if (g->cell < 0) return 1;
+    return orc_cell_of(w, g->sx, g->sy, e->x, e->y) == g->cell;
+}
+
+static int in_time_mag(const orc_world* w, const ev_t* e) {
+    if (w->p.lattice) {
+        const orc_params* p = &w->p;
+        return lat_index(e->t, p->lat_t0, p->lat_dt, p->lat_nt) >= 0 &&
+               lat_index(e->m, p->lat_m0, p->lat_dm, p->lat_nm) >= 0 &&
+               lat_index(e->x, p->lat_x0, p->lat_dx, p->lat_nx) >= 0 &&
+               lat_index(e->y, p->lat_y0, p->lat_dy, p->lat_ny) >= 0;
+    }
+    return e->t >= 0.0 && e->t < w->p.T && e->m >= 2.0;
+}
+
+/* xy lattice points of a region, in row-major order */
+static int64_t lat_points(const orc_world* w, const region_t* g, int64_t want, double* xy) {
+    const orc_params* p = &w->p;
+    int64_t c = 0;
+    for (int iy = 0; iy < p->lat_ny; ++iy)
+        for (int ix = 0; ix < p->lat_nx; ++ix) {
+            ev_t e = { p->lat_x0 + ix * p->lat_dx, p->lat_y0 + iy * p->lat_dy, 0.0, 2.0, 0 };
+            if (!in_region(w, g, &e)) continue;
+            if (c == want && xy) { xy[0] = e.x; xy[1] = e.y; }
+            ++c;
+        }
+    return c;
+}
+
+/* log of the birth proposal density (mass in lattice mode) at e */
+static double log_qb(const orc_world* w, const region_t* g, const ev_t* e) {
+    const orc_params* p = &w->p;
+    if (p->lattice) {
+        double nr = (double)lat_points(w, g, -1, NULL);
+        return -log(nr) - log((double)p->lat_nt) - log((double)p->lat_nm);
+    }
+    double area = (g->r[1] - g->r[0]) * (g->r[3] - g->r[2]);
+    return -log(area) - log(p->T) - (e->m - 2.0);
+}
+
+/* Gaussian magnitude of a Box-Muller pair, rounded to a multiple of 2^-20 so
+ * that platform differences in log/cos/sin below that grain cannot change a
+ * coordinate; the sign comes from an independent bit, so the offset is
+ * exactly symmetric. */
+static double qgauss(double z) { return rint(fabs(z) * 1048576.0) * (1.0 / 1048576.0); }
+
+typedef struct { int32_t type, valid; int64_t idx; ev_t cand; } prop_t;
+
+static prop_t decode(const orc_world* w, const region_t* g, const uint64_t* wd,
+                     const ev_t* own, int64_t n_own, int64_t n_total) {
+    const orc_params* p = &w->p;
+    prop_t q;
+    memset(&q, 0, sizeof(q));
+    double u = u01(wd[0]);
+    q.type = u < p->p_birth ? 0 : (u < p->p_birth + p->p_death ? 1 : 2);
+    q.idx = -1;
+    if (q.type == 0) {
+        if (p->lattice) {
+            if (n_total >= p->lat_nmax) return q;
+            int64_t nr = lat_points(w, g, -1, NULL);
+            if (nr == 0) return q;
+            double xy[2];
+            lat_points(w, g, pick(wd[2], nr), xy);
+            q.cand.x = xy[0]; q.cand.y = xy[1];
+            q.cand.t = p->lat_t0 + (double)pick(wd[3], p->lat_nt) * p->lat_dt;
+            q.cand.m = p->lat_m0 + (double)pick(wd[4], p->lat_nm) * p->lat_dm;
+        } else {
+            q.cand.x = g->r[0] + u01(wd[2]) * (g->r[1] - g->r[0]);
+            q.cand.y = g->r[2] + u01(wd[3]) * (g->r[3] - g->r[2]);
+            q.cand.t = u01(wd[4]) * p->T;
+            q.cand.m = 2.0 - log(u01o(wd[5]));
+        }
+        q.valid = in_region(w, g, &q.cand) && in_time_mag(w, &q.cand);
+        return q;
+    }
+    if (n_own == 0) return q;
+    q.idx = pick(wd[1], n_own);
+    if (q.type == 1) { q.valid = 1; return q; }
+    q.cand = own[q.idx];
+    if (p->lattice) {
+        int64_t dir = pick(wd[2], 8);
+        double step = (dir & 1) ? -1.0 : 1.0;
+        switch (dir >> 1) {
+            case 0: q.cand.x += step * p->lat_dx; break;
+            case 1: q.cand.y += step * p->lat_dy; break;
+            case 2: q.cand.t += step * p->lat_dt; break;
+            default: q.cand.m += step * p->lat_dm; break;
+        }
+    } else {
+        double r1 = sqrt(-2.0 * log(u01o(wd[2]))), th1 = 2.0 * M_PI * u01(wd[3]);
+        double r2 = sqrt(-2.0 * log(u01o(wd[4]))), th2 = 2.0 * M_PI * u01(wd[5]);
+        double z[4] = { qgauss(r1 * cos(th1)), qgauss(r1 * sin(th1)),
+                        qgauss(r2 * cos(th2)), qgauss(r2 * sin(th2)) };
+        for (int i = 0; i < 4; ++i)
+            if ((wd[1] >> (32 + i)) & 1) z[i] = -z[i];
+        q.cand.x += p->sig_xy * z[0];
+        q.cand.y += p->sig_xy * z[1];
+        q.cand.t += p->sig_t * z[2];
+        q.cand.m += p->sig_m * z[3];
+    }
+    q.valid = in_region(w, g, &q.cand) && in_time_mag(w, &q.cand);
+    return q;
+}
+
+/* log acceptance ratio (MH, §Background / Algorithm "Serial Metropolis
+ * Hastings"): log pi(x') - log pi(x) + log q(x | x') - log q(x' | x), with
+ * pi the Poisson-process posterior and the proposal restricted to the region.
+ *   birth:  dll + log beta(c) - log q_b(c) + log p_d - log(n+1) - log p_b
+ *   death:  dll - log beta(e) + log q_b(e) + log p_b - log p_d + log n
+ *   move:   dll + log beta(c) - log beta(e)        (symmetric offset)
+ */
+static double log_alpha_of(const orc_world* w, const region_t* g, const prop_t* q,
+                           const ev_t* own, int64_t n_own, const ev_t* oth, int64_t n_oth,
+                           double* dll_out, double* dlp_out) {
+    const orc_params* p = &w->p;
+    double dll, dlp, la;
+    if (q->type == 0) {
+        dll = delta_ll2(w, own, n_own, oth, n_oth, -1, &q->cand);
+        dlp = log_beta(w, &q->cand);
+        la = dll + dlp - log_qb(w, g, &q->cand) + log(p->p_death)
+             - log((double)(n_own + (ORC_MUTANT == 1 ? 2 : 1))) - log(p->p_birth);
+    } else if (q->type == 1) {
+        const ev_t* e = &own[q->idx];
+        dll = delta_ll2(w, own, n_own, oth, n_oth, q->idx, NULL);
+        dlp = -log_beta(w, e);
+        la = dll + dlp + (ORC_MUTANT == 2 ? 0.0 : log_qb(w, g, e)) + log(p->p_birth) - log(p->p_death)
+             + log((double)n_own);
+    } else {
+        dll = delta_ll2(w, own, n_own, oth, n_oth, q->idx, &q->cand);
+        dlp = log_beta(w, &q->cand) - log_beta(w, &own[q->idx]);
+        la = dll + (ORC_MUTANT == 4 ? 0.0 : dlp);
+    }
+    *dll_out = dll;
+    *dlp_out = dlp;
+    return la;
+}
+
+/* ------------------------------------------------------------------------
+ * region runner: k MH steps on the region's own events with the others fixed
+ * ---------------------------------------------------------------------- */
+typedef struct { ev_t* e; int64_t n, cap; } vec_t;
+
+static void vec_push(vec_t* v, const ev_t* e) {
+    if (v->n == v->cap) {
+        v->cap = v->cap ? 2 * v->cap : 16;
+        v->e = (ev_t*)realloc(v->e, sizeof(ev_t) * (size_t)v->cap);
+    }
+    v->e[v->n++] = *e;
+}
+
+static void apply(vec_t* own, const prop_t* q, uint64_t new_id) {
+    if (q->type == 0) {
+        ev_t e = q->cand;
+        e.id = new_id;
+        vec_push(own, &e);
+    } else if (q->type == 1) {
+        for (int64_t i = q->idx; i + 1 < own->n; ++i) own->e[i] = own->e[i + 1];
+        own->n--;
+    } else {
+        uint64_t id = own->e[q->idx].id;
+        own->e[q->idx] = q->cand;
+        own->e[q->idx].id = id;
+    }
+}
+
+/* one MH step; stream/c0/c1/c2 select the Philox counter */
+static void mh_step(const orc_world* w, const region_t* g, vec_t* own, const ev_t* oth, int64_t n_oth,
+                    int64_t n_total_other, uint64_t stream, uint64_t c0, uint64_t c1, uint64_t c2,
+                    uint64_t new_id, orc_trace* tr, double* dlogp) {
+    uint64_t wd[8];
+    step_words(w, stream, c0, c1, c2, wd);
+    prop_t q = decode(w, g, wd, own->e, own->n, own->n + n_total_other);
+    double dll = 0.0, dlp = 0.0, la = -INFINITY;
+    int acc = 0;
+    if (tr) {
+        tr->type = q.type;
+        tr->n_before = (int32_t)own->n;
+        tr->evaluated = q.valid;
+    }
+    if (q.valid) {
+        la = log_alpha_of(w, g, &q, own->e, own->n, oth, n_oth, &dll, &dlp);
+        acc = log(u01o(wd[6])) < la;
+    }
+    if (tr) {
+        tr->accepted = acc;
+        tr->dll = dll;
+        tr->log_alpha = la;
+    }
+    if (acc && w->p.commit) {
+        apply(own, &q, new_id);
+        *dlogp += dll + dlp;
+    }
+}
+
+double orc_log_alpha(const orc_world* w, double sx, double sy, int32_t cell,
+                     const double* ev, int64_t n, int32_t type, int64_t idx,
+                     const double* cand, int32_t* valid) {
+    region_t g;
+    g.cell = cell; g.sx = sx; g.sy = sy;
+    if (cell < 0) { g.r[0] = 0.0; g.r[1] = w->p.W; g.r[2] = 0.0; g.r[3] = w->p.W; }
+    else orc_cell_rect(w, sx, sy, cell, g.r);
+    vec_t own = { 0, 0, 0 }, oth = { 0, 0, 0 };
+    for (int64_t i = 0; i < n; ++i) {
+        ev_t e; to_ev(ev + 4 * i, &e);
+        e.id = (uint64_t)i;
+        if (cell < 0 || orc_cell_of(w, sx, sy, e.x, e.y) == cell) vec_push(&own, &e);
+        else vec_push(&oth, &e);
+    }
+    prop_t q;
+    memset(&q, 0, sizeof(q));
+    q.type = type;
+    q.idx = idx;
+    if (cand) to_ev(cand, &q.cand);
+    q.valid = 1;
+    if (type != 0 && (idx < 0 || idx >= own.n)) q.valid = 0;
+    if (type == 0 && w->p.lattice && n >= w->p.lat_nmax) q.valid = 0;
+    if (type != 1 && q.valid) q.valid = in_region(w, &g, &q.cand) && in_time_mag(w, &q.cand);
+    double la = -INFINITY, dll, dlp;
+    if (q.valid) la = log_alpha_of(w, &g, &q, own.e, own.n, oth.e, oth.n, &dll, &dlp);
+    *valid = q.valid;
+    free(own.e);
+    free(oth.e);
+    return la;
+}
+
+/* ------------------------------------------------------------------------
+ * Serial MH (Algorithm "Serial Metropolis Hastings"): the whole domain is one
+ * region; Philox stream 2, counter (step, 0, 0, 0|1).
+ * ---------------------------------------------------------------------- */
+int orc_run_serial(const orc_world* w, orc_set* s, int64_t step0, int64_t n_steps,
+                   orc_trace* trace, int64_t trace_cap, int64_t* n_trace, double* dlogp) {
+    region_t g;
+    g.cell = -1; g.sx = 0.0; g.sy = 0.0;
+    g.r[0] = 0.0; g.r[1] = w->p.W; g.r[2] = 0.0; g.r[3] = w->p.W;
+    vec_t own = { s->e, s->n, s->cap };
+    double acc_lp = 0.0;
+    int64_t nt = 0;
+    for (int64_t i = 0; i < n_steps; ++i) {
+        int64_t step = step0 + i;
+        orc_trace* tr = (trace && nt < trace_cap) ? &trace[nt] : NULL;
+        if (tr) {
+            memset(tr, 0, sizeof(*tr));
+            tr->sweep = (int32_t)(step >> 31);
+            tr->cell = -1;
+            tr->step = (int32_t)(step & 0x7fffffff);
+        }
+        uint64_t new_id = 0x8000000000000000ULL | (uint64_t)step;
+        mh_step(w, &g, &own, NULL, 0, 0, 2, (uint64_t)step, 0, 0, new_id, tr, &acc_lp);
+        ++nt;
+    }
+    s->e = own.e; s->n = own.n; s->cap = own.cap;
+    if (n_trace) *n_trace = nt;
+    if (dlogp) *dlogp = acc_lp;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Chromatic MH (Algorithm "Chromatic MH with Static Coloring"; with
+ * shift_mode = 1 the boundaries move by a fresh uniform offset before every
+ * sweep, §Chromatic MH with Dynamic Coloring).  Within a sweep the colours run
+ * in order 0..p^2-1; the regions of one colour are independent and may run on
+ * several threads.  Region r runs k steps with Philox stream 0, counter
+ * (sweep, r, step, 0|1).  Births get id (sweep+1) << 32 | r << 12 | step,
+ * which keeps every region's events sorted by id.
+ * ---------------------------------------------------------------------- */
+static int cmp_cell_id(const void* a, const void* b) {
+    const int64_t* x = (const int64_t*)a;
+    const int64_t* y = (const int64_t*)b;
+    if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;
+    if ((uint64_t)x[1] != (uint64_t)y[1]) return (uint64_t)x[1] < (uint64_t)y[1] ? -1 : 1;
+    return 0;
+}
+
+int orc_run_chromatic(const orc_world* w, orc_set* s, int64_t sweep0, int64_t n_sweeps,
+                      int32_t shift_mode, double sx_static, double sy_static,
+                      orc_trace* trace, int64_t trace_cap, int64_t* n_trace,
+                      int32_t n_threads, double* dlogp) {
+    int32_t ncx, ncy;
+    orc_grid_dims(w, &ncx, &ncy);
+    const int32_t nc = ncx * ncy, per = orc_period(w), ncol = per * per;
+    const int32_t k = w->p.k_per_phase;
+    if (2.0 * w->p.R_max > (double)(per - 1) * w->p.L) return -1;
+    if (k >= 4096 || nc >= (1 << 20)) return -2;
+    vec_t* cells = (vec_t*)calloc((size_t)nc, sizeof(vec_t));
+    int32_t* regs = (int32_t*)malloc(sizeof(int32_t) * (size_t)nc);
+    double* reg_lp = (double*)malloc(sizeof(double) * (size_t)nc);
+    double total_lp = 0.0;
+    int64_t nt = 0;
+    int rc = 0;
+    for (int64_t sw = sweep0; sw < sweep0 + n_sweeps; ++sw) {
+        double sx = sx_static, sy = sy_static;
+        if (shift_mode == 1) orc_shift(w, sw, &sx, &sy);
+        /* bin events into cells, each cell sorted by id */
+        int64_t* key = (int64_t*)malloc(sizeof(int64_t) * 3 * (size_t)(s->n > 0 ? s->n : 1));
+        for (int64_t i = 0; i < s->n; ++i) {
+            int32_t c = orc_cell_of(w, sx, sy, s->e[i].x, s->e[i].y);
+            if (c < 0) { rc = -3; free(key); goto done; }
+            key[3 * i] = c;
+            key[3 * i + 1] = (int64_t)s->e[i].id;
+            key[3 * i + 2] = i;
+        }
+        qsort(key, (size_t)s->n, sizeof(int64_t) * 3, cmp_cell_id);
+        for (int32_t c = 0; c < nc; ++c) cells[c].n = 0;
+        for (int64_t i = 0; i < s->n; ++i) vec_push(&cells[key[3 * i]], &s->e[key[3 * i + 2]]);
+        free(key);
+
+        for (int32_t col = 0; col < ncol; ++col) {
+            int32_t nr = 0;
+            for (int32_t c = 0; c < nc; ++c) {
+                double r[4];
+                orc_cell_rect(w, sx, sy, c, r);
+                if (orc_colour_of(w, c) == col && cell_live(r)) regs[nr++] = c;
+            }
+            int64_t tbase = nt;
+            int use_threads = (n_threads > 1 && !w->p.lattice) ? n_threads : 1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(use_threads)
+#endif
+            for (int32_t ri = 0; ri < nr; ++ri) {
+                int32_t c = regs[ri];
+                region_t g;
+                g.cell = c; g.sx = sx; g.sy = sy;
+                orc_cell_rect(w, sx, sy, c, g.r);
+                /* the region's Markov blanket: events of cells within per-1 */
+                vec_t oth = { 0, 0, 0 };
+                int32_t ix = c % ncx, iy = c / ncx;
+                for (int32_t jy = iy - (per - 1); jy <= iy + (per - 1); ++jy)
+                    for (int32_t jx = ix - (per - 1); jx <= ix + (per - 1); ++jx) {
+                        if (jx < 0 || jy < 0 || jx >= ncx || jy >= ncy) continue;
+                        int32_t cc = jy * ncx + jx;
+                        if (cc == c) continue;
+                        for (int64_t i = 0; i < cells[cc].n; ++i) vec_push(&oth, &cells[cc].e[i]);
+                    }
+                double lp = 0.0;
+                /* lattice cap on the total count (lattice mode runs regions in order) */
+                int64_t n_other_world = 0;
+                if (w->p.lattice)
+                    for (int32_t cc = 0; cc < nc; ++cc)
+                        if (cc != c) n_other_world += cells[cc].n;
+                for (int32_t st = 0; st < k; ++st) {
+                    int64_t ti = tbase + (int64_t)ri * k + st;
+                    orc_trace* tr = (trace && ti < trace_cap) ? &trace[ti] : NULL;
+                    if (tr) {
+                        memset(tr, 0, sizeof(*tr));
+                        tr->sweep = (int32_t)sw;
+                        tr->cell = c;
+                        tr->step = st;
+                    }
+                    uint64_t new_id = ((uint64_t)(sw + 1) << 32) | ((uint64_t)c << 12) | (uint64_t)st;
+                    mh_step(w, &g, &cells[c], oth.e, oth.n, n_other_world, 0,
+                            (uint64_t)sw, (uint64_t)c, (uint64_t)st, new_id, tr, &lp);
+                }
+                free(oth.e);
+                reg_lp[ri] = lp;
+            }
+            for (int32_t ri = 0; ri < nr; ++ri) total_lp += reg_lp[ri];
+            nt += (int64_t)nr * k;
+        }
+        /* flatten back, cell order then id */
+        int64_t n_new = 0;
+        for (int32_t c = 0; c < nc; ++c) n_new += cells[c].n;
+        if (n_new > s->cap) {
+            s->cap = n_new + 16;
+            s->e = (ev_t*)realloc(s->e, sizeof(ev_t) * (size_t)s->cap);
+        }
+        s->n = 0;
+        for (int32_t c = 0; c < nc; ++c)
+            for (int64_t i = 0; i < cells[c].n; ++i) s->e[s->n++] = cells[c].e[i];
+    }
+done:
+    for (int32_t c = 0; c < nc; ++c) free(cells[c].e);
+    free(cells);
+    free(regs);
+    free(reg_lp);
+    if (n_trace) *n_trace = nt;
+    if (dlogp) *dlogp = total_lp;
+    return rc;
+}

@@ -1,0 +1,264 @@
+"""Pins of the oracle's MH samplers.
+
+* Exact enumeration on a lattice world: the posterior over every multiset of
+  at most two events is computed from the definition (Poisson process on a
+  finite point set: independent Poisson counts, times the likelihood), and
+  the transition matrix of the serial kernel and of every region-restricted
+  kernel is assembled from the proposal probabilities and the oracle's
+  acceptance ratios.  Each kernel must leave the posterior invariant and
+  satisfy detailed balance to ~1e-12 (MH acceptance rule, §Background; the
+  region kernels of Algorithm "Chromatic MH with Static Coloring").
+* Long lattice chains (serial, static and dynamic chromatic) reproduce the
+  enumerated marginals within batch-means error.
+* Prior-only continuous chains (no stations) reproduce the prior: Poisson
+  count, uniform locations (including edge regions cut by the domain),
+  Exp(1) magnitudes.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import worldgen
+
+PB, PD = 0.25, 0.25
+PMV = 1.0 - PB - PD
+
+
+def _lattice_world(orc, shift_cells=False):
+    p = worldgen.ModelParams(W=200.0, T=60.0, Lambda=1.5, v=6.0, alpha=0.5, beta_att=0.01,
+                             tau=5.0, t_s=10.0, f_hz=1.0, R_max=50.0, L=100.0)
+    st = np.array([[50.0, 50.0], [150.0, 150.0], [60.0, 140.0]])
+    truth = np.array([[75.0, 75.0, 10.0, 3.5], [125.0, 175.0, 30.0, 2.5]])
+    w = worldgen.make_world(p, st, seed=77, events=truth)
+    lat = orc.Lattice(nx=4, ny=4, nt=2, nm=2, nmax=2, x0=25.0, dx=50.0, y0=25.0, dy=50.0,
+                      t0=10.0, dt=20.0, m0=2.5, dm=1.0)
+    return w, lat
+
+
+def _points(lat):
+    pts = []
+    for iy in range(lat.ny):
+        for ix in range(lat.nx):
+            for it in range(lat.nt):
+                for im in range(lat.nm):
+                    pts.append((lat.x0 + ix * lat.dx, lat.y0 + iy * lat.dy,
+                                lat.t0 + it * lat.dt, lat.m0 + im * lat.dm))
+    return np.array(pts)
+
+
+def _enumerate(o, lat, p):
+    pts = _points(lat)
+    states = [()]
+    for n in range(1, lat.nmax + 1):
+        states += list(itertools.combinations_with_replacement(range(len(pts)), n))
+    index = {s: i for i, s in enumerate(states)}
+    # Poisson process on the finite set: beta_p = Lambda * 1/(nx ny) * 1/nt * w_m
+    wm = np.exp(-(lat.m0 + np.arange(lat.nm) * lat.dm - 2.0))
+    wm /= wm.sum()
+    beta = np.array([p.Lambda / (lat.nx * lat.ny * lat.nt) * wm[int(round((q[3] - lat.m0) / lat.dm))]
+                     for q in pts])
+    logpi = np.empty(len(states))
+    for i, s in enumerate(states):
+        ev = pts[list(s)]
+        counts = np.bincount(np.array(s, dtype=int), minlength=len(pts)) if s else np.zeros(1)
+        logpi[i] = (-p.Lambda + np.log(beta[list(s)]).sum()
+                    - sum(math.lgamma(c + 1) for c in counts)
+                    + o.log_likelihood(ev))
+    pi = np.exp(logpi - logpi.max())
+    pi /= pi.sum()
+    return pts, states, index, pi
+
+
+def _kernel(o, lat, pts, states, index, cell, sx, sy):
+    n = len(states)
+    P = np.zeros((n, n))
+    key = {tuple(q): i for i, q in enumerate(pts)}
+
+    def in_region(x, y):
+        return cell < 0 or o.cell_of(sx, sy, x, y) == cell
+
+    xy_pts = sorted({(q[0], q[1]) for q in pts if in_region(q[0], q[1])})
+    n_r = len(xy_pts)
+    for i, s in enumerate(states):
+        ev = pts[list(s)]
+        own = [q for q in range(len(s)) if in_region(ev[q, 0], ev[q, 1])]
+        # births
+        if n_r == 0:
+            P[i, i] += PB
+        else:
+            prob = PB / (n_r * lat.nt * lat.nm)
+            for (x, y) in xy_pts:
+                for it in range(lat.nt):
+                    for im in range(lat.nm):
+                        c = np.array([x, y, lat.t0 + it * lat.dt, lat.m0 + im * lat.dm])
+                        la, ok = o.log_alpha(sx, sy, cell, ev, 0, -1, c)
+                        if not ok:
+                            P[i, i] += prob
+                            continue
+                        a = min(1.0, math.exp(min(la, 0.0)))
+                        j = index[tuple(sorted(s + (key[tuple(c)],)))]
+                        P[i, j] += prob * a
+                        P[i, i] += prob * (1 - a)
+        if not own:
+            P[i, i] += PD + PMV
+            continue
+        for qi, q in enumerate(own):
+            prob = PD / len(own)
+            la, ok = o.log_alpha(sx, sy, cell, ev, 1, qi, None)
+            assert ok
+            a = min(1.0, math.exp(min(la, 0.0)))
+            rest = list(s)
+            rest.remove(s[q])
+            j = index[tuple(sorted(rest))]
+            P[i, j] += prob * a
+            P[i, i] += prob * (1 - a)
+            for d in range(8):
+                prob = PMV / (len(own) * 8)
+                c = ev[q].copy()
+                step = -1.0 if d & 1 else 1.0
+                c[d >> 1] += step * (lat.dx, lat.dy, lat.dt, lat.dm)[d >> 1]
+                la, ok = o.log_alpha(sx, sy, cell, ev, 2, qi, c)
+                if not ok:
+                    P[i, i] += prob
+                    continue
+                a = min(1.0, math.exp(min(la, 0.0)))
+                moved = list(s)
+                moved.remove(s[q])
+                moved.append(key[tuple(c)])
+                j = index[tuple(sorted(moved))]
+                P[i, j] += prob * a
+                P[i, i] += prob * (1 - a)
+    return P
+
+
+@pytest.fixture(scope="module")
+def lattice_case(orc):
+    w, lat = _lattice_world(orc)
+    o = orc.World(w, p_birth=PB, p_death=PD, k_per_phase=10, seed=3, lattice=lat)
+    pts, states, index, pi = _enumerate(o, lat, w.params)
+    return o, lat, pts, states, index, pi
+
+
+def _check_kernel(P, pi):
+    assert np.allclose(P.sum(axis=1), 1.0, atol=1e-13)
+    assert P.min() >= -1e-15
+    flow = pi[:, None] * P
+    assert np.max(np.abs(flow - flow.T)) < 1e-13 * pi.max()
+    assert np.max(np.abs(pi @ P - pi)) < 1e-13 * pi.max()
+
+
+def test_serial_kernel_detailed_balance(lattice_case):
+    o, lat, pts, states, index, pi = lattice_case
+    P = _kernel(o, lat, pts, states, index, -1, 0.0, 0.0)
+    _check_kernel(P, pi)
+    # the kernel moves: it is not the identity
+    assert np.mean(np.diag(P)) < 0.95
+
+
+@pytest.mark.parametrize("shift", [(0.0, 0.0), (30.0, 70.0)])
+def test_region_kernels_detailed_balance(lattice_case, shift):
+    o, lat, pts, states, index, pi = lattice_case
+    sx, sy = shift
+    ncx, ncy = o.grid_dims()
+    live = [c for c in range(ncx * ncy)
+            if (lambda r: r[1] > r[0] and r[3] > r[2])(o.cell_rect(sx, sy, c))]
+    assert len(live) == (4 if shift == (0.0, 0.0) else 9)
+    for c in live:
+        _check_kernel(_kernel(o, lat, pts, states, index, c, sx, sy), pi)
+
+
+def _batch_se(x, nb=40):
+    x = np.asarray(x, dtype=np.float64)
+    m = len(x) // nb
+    b = x[: m * nb].reshape(nb, m).mean(axis=1)
+    return b.mean(), b.std(ddof=1) / math.sqrt(nb)
+
+
+@pytest.mark.parametrize("mode", ["serial", "static", "dynamic"])
+def test_lattice_chain_marginals(lattice_case, mode):
+    o, lat, pts, states, index, pi = lattice_case
+    # exact marginals: P(N = n) and the mean occupancy of every xy site
+    pN = np.zeros(lat.nmax + 1)
+    occ = np.zeros(lat.nx * lat.ny)
+    for s, q in zip(states, pi):
+        pN[len(s)] += q
+        for a in s:
+            x, y = pts[a][:2]
+            occ[int(round((y - lat.y0) / lat.dy)) * lat.nx + int(round((x - lat.x0) / lat.dx))] += q
+    ev = np.zeros((0, 4))
+    ids = None
+    n_samples = 6000
+    Ns, O = [], []
+    for it in range(n_samples):
+        if mode == "serial":
+            ev, ids, _, _ = o.run_serial(ev, 40, ids=ids, step0=it * 40)
+        else:
+            ev, ids, _, _ = o.run_chromatic(ev, 1, ids=ids, sweep0=it,
+                                            shift_mode=1 if mode == "dynamic" else 0,
+                                            sx=0.0, sy=0.0)
+        Ns.append(len(ev))
+        o_ = np.zeros(lat.nx * lat.ny)
+        for e in ev:
+            o_[int(round((e[1] - lat.y0) / lat.dy)) * lat.nx + int(round((e[0] - lat.x0) / lat.dx))] += 1
+        O.append(o_)
+    Ns = np.array(Ns)
+    O = np.array(O)
+    for n in range(lat.nmax + 1):
+        m, se = _batch_se(Ns == n)
+        assert abs(m - pN[n]) < 5 * se + 2e-3, (n, m, pN[n], se)
+    for site in range(lat.nx * lat.ny):
+        m, se = _batch_se(O[:, site])
+        assert abs(m - occ[site]) < 5 * se + 2e-3, (site, m, occ[site], se)
+
+
+@pytest.mark.parametrize("mode", ["serial", "static", "dynamic"])
+def test_prior_only_chain_recovers_prior(orc, mode):
+    p = worldgen.ModelParams(W=200.0, T=100.0, Lambda=12.0, R_max=50.0, L=100.0)
+    w = worldgen.World(params=p, stations=np.zeros((0, 2)), signals=np.zeros((0, 0)),
+                       events=np.zeros((0, 4)))
+    o = orc.World(w, k_per_phase=8, seed=11, sig_xy=20.0, sig_t=10.0, sig_m=0.5)
+    ev = np.zeros((0, 4))
+    ids = None
+    Ns, xs, ms = [], [], []
+    for it in range(3000):
+        if mode == "serial":
+            ev, ids, _, _ = o.run_serial(ev, 40, ids=ids, step0=it * 40)
+        else:
+            ev, ids, _, _ = o.run_chromatic(ev, 1, ids=ids, sweep0=it,
+                                            shift_mode=1 if mode == "dynamic" else 0,
+                                            sx=37.0, sy=61.0)
+        Ns.append(len(ev))
+        if it % 5 == 0:
+            xs.extend(ev[:, 0])
+            xs.extend(ev[:, 1])
+            ms.extend(ev[:, 3] - 2.0)
+    m, se = _batch_se(Ns)
+    assert abs(m - p.Lambda) < 5 * se, (m, se)
+    v = np.var(Ns)
+    assert abs(v / p.Lambda - 1.0) < 0.25
+    # uniform location over the domain, edge regions included
+    h, _ = np.histogram(xs, bins=10, range=(0.0, p.W))
+    frac = h / h.sum()
+    assert np.max(np.abs(frac - 0.1)) < 0.02, frac
+    # Exp(1) magnitudes above 2
+    ms = np.array(ms)
+    assert abs(ms.mean() - 1.0) < 0.06
+    assert abs(np.mean(ms > 1.0) - math.exp(-1.0)) < 0.03
+
+
+def test_threaded_chromatic_equals_sequential(orc):
+    """Same-colour regions are independent (disjoint blankets), so running
+    them on several threads gives bit-identical chains and traces."""
+    p = worldgen.ModelParams(W=500.0, T=400.0, Lambda=40.0, f_hz=2.0)
+    w = worldgen.make_world(p, worldgen.jittered_grid_stations(5, p.W, 3), seed=3)
+    o = orc.World(w, k_per_phase=16, seed=21)
+    a = o.run_chromatic(np.zeros((0, 4)), 6, trace_cap=100000, threads=1)
+    b = o.run_chromatic(np.zeros((0, 4)), 6, trace_cap=100000, threads=4)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(a[2], b[2])
+    assert a[3] == b[3]
+    # the running log-density change equals a from-scratch recomputation
+    empty = np.zeros((0, 4))
+    assert a[3] == pytest.approx(o.log_density(a[0]) - o.log_density(empty), rel=1e-9)

@@ -1,0 +1,304 @@
+"""Throughput of the dynamic-chromatic MH sweep on one GB300.
+
+One step = one sweep: the partition is shifted, every region of each colour
+runs k MH steps, colours in order.  The default workload is the float32 sweep
+at scale (4000 x 4000 km, 24 h, ~10^4 events, 1600 stations x 864000 samples,
+40 x 40 regions of 100 km, k = 32).
+
+Printed (one JSON line): MH proposals/s over the timed sweeps (value), sweeps/s,
+an end-to-end figure through the C ABI with host buffers (model creation from
+pinned host signals, the sweeps, and a read-back of the state after every
+sweep), the roofline of the colour-phase kernel measured live with CUDA
+events, and the oracle timed on the host cores.
+
+--impl reference times the CPU oracle (the only other implementation) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import worldgen  # noqa: E402
+
+K_PER_PHASE = 32
+SEED = 1000
+CHAIN_SEED = 7
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _workload(name: str):
+    if name == "scale":
+        return worldgen.config_scale(seed=SEED), "fp32 sweep at scale: 4000x4000 km, 24 h, ~1e4 events, " \
+                                                 "1600 stations x 864000 f32 samples, 40x40 regions, k=32"
+    if name == "replay":
+        return worldgen.config_replay(seed=SEED), "fp64 replay: 1000x1000 km, 1 h, ~500 events, " \
+                                                  "100 stations x 36000 f64 samples, 10x10 regions, k=32"
+    raise SystemExit("unknown workload " + name)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index: int = 0):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _cpu_baseline(world, seconds_target: float = 15.0):
+    """The oracle's chromatic sampler on a 1000 x 1000 km corner of the world
+    (same station density, event intensity and record length)."""
+    import oracle
+    oracle.build()
+    sub_side = 1000.0
+    sub = worldgen.subworld(world, 0.0, sub_side, 0.0, sub_side)
+    frac = (sub_side / world.params.W) ** 2
+    p = worldgen.ModelParams(**{**world.params.__dict__, "W": sub_side, "Lambda": world.params.Lambda * frac})
+    sub.params = p
+    threads = os.cpu_count() or 1
+    o = oracle.World(sub, k_per_phase=K_PER_PHASE, seed=CHAIN_SEED)
+    ev = sub.events
+    ids = None
+    t0 = time.perf_counter()
+    props, sweeps = 0, 0
+    while True:
+        ev, ids, tr, _ = o.run_chromatic(ev, 1, ids=ids, sweep0=sweeps, trace_cap=200000, threads=threads)
+        props += len(tr)
+        sweeps += 1
+        if time.perf_counter() - t0 > seconds_target:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": props / dt, "unit": "proposals/s", "cores": threads, "kind": "oracle",
+            "sample": "%d sweeps of the oracle's chromatic sampler (OpenMP over same-colour regions) on a "
+                      "1000x1000 km corner of the same world (100 stations x %d samples, ~%d events), "
+                      "started from the ground truth" % (sweeps, world.params.n_samples, len(sub.events)),
+            "sweeps": sweeps, "proposals": props, "seconds": dt}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    world, desc = _workload(args.workload)
+    base = _cpu_baseline(world, seconds_target=max(5.0, 3.0 * args.steps / 10.0))
+    line = {"impl": "reference", "metric": "MH proposals/sec and sweeps/sec on 1 GB300",
+            "value": base["value"], "unit": "proposals/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded worldgen)",
+            "config": {"workload": desc + " [oracle on a 1000x1000 km corner]"},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": "proposals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+
+    world_size = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world_size > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1612_00595_gb300 as cm
+
+    world, desc = _workload(args.workload)
+    p = world.params
+    f32 = world.signals.dtype == np.float32
+    dtype = cm.F32 if f32 else cm.F64
+    esz = 4 if f32 else 8
+    # each rank runs an independent chain (weak scaling: fixed work per GPU)
+    params = cm.make_params(p, k_per_phase=K_PER_PHASE, seed=CHAIN_SEED + 1000 * rank, dtype=dtype)
+    stream = torch.cuda.Stream()
+    sig_dev = torch.from_numpy(world.signals).to("cuda", non_blocking=False)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------- device-resident throughput ----------------
+    m = cm.create_model(world.events, world.stations, sig_dev, params, stream=stream)
+    m.partition_and_color(p.L, shift_mode=1)
+    m.run_sweeps(args.warmup)
+    m.sync()
+    _, _, _, st0 = m.read_state(cap=0)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        e0.record(stream)
+        m.run_sweeps(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    _, _, _, st1 = m.read_state(cap=0)
+    props = sum(st1["proposed"]) - sum(st0["proposed"])
+    launches = st1["kernel_launches"] - st0["kernel_launches"]
+    t = torch.tensor([ms], device="cuda")
+    tp = torch.tensor([float(props)], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tp, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    total_props = float(tp.item())
+    value = total_props / (ms_max / 1e3)
+    sweeps_per_s = args.steps / (ms_max / 1e3)
+
+    # ---------------- live kernel timing for the roofline ----------------
+    m.set_timing(True)
+    _, _, _, sa = m.read_state(cap=0)
+    m.run_sweeps(args.steps)
+    _, _, _, sb = m.read_state(cap=0)
+    m.set_timing(False)
+    n_launch = sb["phase_launches"] - sa["phase_launches"]
+    phase_ms = sb["phase_ms"] - sa["phase_ms"]
+    priced = sb["priced_samples"] - sa["priced_samples"]
+    rewritten = sb["rewritten_samples"] - sa["rewritten_samples"]
+    # algorithmic bytes: every priced sample reads s and V once, every
+    # re-synthesised sample writes V once
+    alg_bytes = priced * 2 * esz + rewritten * esz
+    per_launch_bytes = alg_bytes / max(n_launch, 1)
+    per_launch_s = phase_ms / 1e3 / max(n_launch, 1)
+    peaks, peak_kind = _peaks()
+    achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "kernel": "phase_kernel<float32>" if f32 else "phase_kernel<float64>",
+            "avg_launch_us": per_launch_s * 1e6, "alg_bytes_per_launch": per_launch_bytes,
+            "peak_source": peak_kind}
+    m.destroy()
+    del sig_dev
+    torch.cuda.empty_cache()
+
+    # ---------------- end to end through the C ABI, host buffers ----------------
+    pinned = torch.from_numpy(world.signals).pin_memory()
+    host_sig = pinned.numpy()
+    barrier()
+    t0 = time.perf_counter()
+    m2 = cm.create_model(world.events, world.stations, host_sig, params, stream=stream)
+    m2.partition_and_color(p.L, shift_mode=1)
+    d2h = 0
+    for _ in range(args.steps):
+        m2.run_sweeps(1)
+        ev, ids, lp, st = m2.read_state()
+        d2h += ev.nbytes + ids.nbytes + 8
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    _, _, _, st2 = m2.read_state(cap=0)
+    e2e_props = sum(st2["proposed"])
+    m2.destroy()
+    te = torch.tensor([e2e_s], device="cuda")
+    tq = torch.tensor([float(e2e_props)], device="cuda")
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tq, op=dist.ReduceOp.SUM)
+    e2e_value = float(tq.item()) / float(te.item())
+    h2d_per_step = world.signals.nbytes / args.steps
+
+    if rank == 0:
+        cpu = _cpu_baseline(world) if world_size == 1 else None
+        line = {"metric": "MH proposals/sec and sweeps/sec on 1 GB300", "value": value, "unit": "proposals/s",
+                "sweeps_per_s": sweeps_per_s, "n_gpus": world_size, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if f32 else "f64",
+                "data": "synthetic (seeded worldgen, the model's generative story)",
+                "config": {"workload": desc, "l2": "inputs larger than L2 (signals + variance %.1f GB)" % (
+                    2 * world.signals.nbytes / 1e9), "chain_start": "ground truth",
+                           "parallelism": "independent chain per GPU" if world_size > 1 else "1 GPU"},
+                "clocks": clocks.summary(), "gpu_launches": int(launches),
+                "e2e": {"value": e2e_value, "unit": "proposals/s", "h2d_bytes_per_step": h2d_per_step,
+                        "d2h_bytes_per_step": d2h / args.steps,
+                        "note": "cmh_create_model from pinned host signals (copied once, amortised over the "
+                                "steps) + per step cmh_run_sweeps(1) and cmh_read_state"},
+                "roofline": roof, "cpu_baseline": cpu}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "replay"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * chromh -- chromatic Metropolis-Hastings with dynamic spatial partitioning
+ * for the toy seismic event model, on one GB300 (sm_103a).
+ *
+ * The calls follow the paper's statement of the inference problem (Song &
+ * Moore, "Parallel Chromatic MCMC with Spatial Partitioning", §Generative
+ * Model of Seismic Signals: "recover the number of events, and their
+ * space-time positions, given noisy observed signals"):
+ *   cmh_create_model         events, stations, signals -> model
+ *   cmh_partition_and_color  region grid + boundary shift (§Partitioning the
+ *                            World; §Chromatic MH with Dynamic Coloring)
+ *   cmh_run_sweeps           n sweeps of Algorithm "Chromatic MH with Static
+ *                            Coloring" (a fresh shift per sweep when dynamic)
+ *   cmh_read_state           the current event hypothesis and log-density
+ *
+ * Model (all lengths km, times s):
+ *   event (x, y, t, m) in [0,W)^2 x [0,T) x [2, inf), Poisson prior with mean
+ *   count Lambda, uniform location and time, m - 2 ~ Exp(1);
+ *   arrival at a station at distance d: a = t + d / v; reach iff d < R_max;
+ *   at sample k (time k / f_hz, k in [ceil(a f), ceil(a f) + t_s f)) the
+ *   station's variance grows by (exp(alpha m - beta_att d) exp(-(k/f - a)/tau))^2;
+ *   each sample s ~ N(0, noise_var + sum of those variances).
+ *
+ * Conventions for every call:
+ *   - return 0 (CMH_OK) or a negative CMH_ERR_* code; nothing throws across
+ *     the ABI; cmh_strerror() names the code;
+ *   - a model is driven by one host thread at a time;
+ *   - device-side errors (a capacity exceeded inside a kernel) are latched in
+ *     the model and returned by the next call that synchronises
+ *     (cmh_read_state, cmh_sync, ...); once latched the model refuses work;
+ *   - all device work is ordered on the model's CUDA stream.
+ */
+#ifndef CHROMH_H
+#define CHROMH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CMH_OK 0
+#define CMH_ERR_ARG (-1)       /* invalid argument (null pointer, bad size, non-finite parameter) */
+#define CMH_ERR_GEOMETRY (-2)  /* R_max too large for the colour pattern of the grid */
+#define CMH_ERR_NONFINITE (-3) /* a signal sample or event coordinate is NaN/Inf */
+#define CMH_ERR_OOM (-4)       /* device allocation failed */
+#define CMH_ERR_CAPACITY (-5)  /* a fixed capacity (events, blanket, arrivals) was exceeded */
+#define CMH_ERR_TIMEOUT (-6)   /* a bounded device wait gave up */
+#define CMH_ERR_CUDA (-7)      /* a CUDA runtime call failed */
+#define CMH_ERR_STATE (-8)     /* call out of order (e.g. run before partition) or error latched */
+
+typedef struct cmh_model cmh_model;
+
+/* one event: epicentre (km), origin time (s), magnitude */
+typedef struct { double x, y, t, m; } cmh_event;
+/* one station (km) */
+typedef struct { double x, y; } cmh_station;
+
+typedef enum { CMH_F64 = 0, CMH_F32 = 1 } cmh_dtype;
+
+typedef struct {
+    /* model (see the header comment) */
+    double W, T, Lambda, v, alpha, beta_att, tau, t_s, noise_var, f_hz, R_max;
+    /* proposal mix and random-walk steps (km, s, magnitude units) */
+    double p_birth, p_death, sig_xy, sig_t, sig_m;
+    int32_t k_per_phase;   /* MH steps per region per colour phase (1..4095) */
+    int32_t commit;        /* 1: accepted proposals change the state; 0: price only */
+    uint64_t seed;         /* key of every Philox stream */
+    cmh_dtype dtype;       /* arithmetic of per-sample terms: CMH_F64 (replay) or CMH_F32 */
+    int32_t ev_capacity;   /* max events one region may hold in a phase; 0: 128 */
+    int32_t frozen_capacity; /* max arrivals from neighbouring regions per blanket
+                                station; 0: 32 */
+    int32_t block_threads; /* threads per region CTA (64..512, multiple of 32); 0: 256 */
+    int64_t max_events;    /* capacity of the whole event store; 0: 4 (n0 + Lambda) + 4096 */
+} cmh_params;
+
+/* region grid: squares of side L anchored at the origin, shifted by (sx, sy) */
+typedef struct { double L; } cmh_grid;
+
+typedef struct {
+    uint64_t proposed[3];   /* by move type: 0 birth, 1 death, 2 move */
+    uint64_t evaluated[3];  /* proposals that were priced (not rejected outright) */
+    uint64_t accepted[3];
+    int64_t sweeps;         /* sweeps run so far */
+    int64_t n_events;
+    double phase_ms;        /* summed device time of the colour-phase kernels while timing
+                               is enabled (cmh_set_timing), CUDA events on the model stream */
+    int64_t phase_launches; /* colour-phase kernels counted in phase_ms */
+    int64_t kernel_launches;/* all kernels this model launched */
+    uint64_t priced_samples;    /* station samples priced over all evaluated proposals */
+    uint64_t rewritten_samples; /* station samples whose variance was re-synthesised */
+} cmh_stats;
+
+/* one record per MH step (optional, cmh_set_trace) */
+typedef struct {
+    int32_t sweep, cell, step, type;   /* type: 0 birth, 1 death, 2 move */
+    int32_t evaluated, accepted, n_before, written;
+    double dll;        /* log-likelihood change of the proposal (0 if not evaluated) */
+    double log_alpha;  /* log acceptance ratio (-inf if not evaluated) */
+} cmh_trace;
+
+/*
+ * Build a model from an initial event hypothesis (the paper starts from the
+ * empty set: n_events = 0 is valid), the stations and their signals.
+ *   init_events  [n_events] host array (may be NULL when n_events == 0)
+ *   stations     [n_stations] host array, n_stations >= 0
+ *   signals      row-major [n_stations][row_pitch] samples of type sig_dtype;
+ *                host memory, or device memory when signals_on_device != 0
+ *                (then ordered after work already on cuda_stream)
+ *   n_samples    samples per station (>= 1), row_pitch >= n_samples (elements)
+ *   p            model parameters (copied)
+ *   cuda_stream  cudaStream_t all device work of the model is ordered on;
+ *                NULL: the model creates and owns a non-blocking stream
+ * The library copies every input (FP64 signals are rounded to FP32 when
+ * p->dtype == CMH_F32) and synthesises the predicted-variance buffer.
+ * Errors: CMH_ERR_ARG, CMH_ERR_NONFINITE (signals or events), CMH_ERR_OOM,
+ * CMH_ERR_CUDA.  *out is NULL on error.
+ */
+int cmh_create_model(const cmh_event* init_events, int64_t n_events,
+                     const cmh_station* stations, int32_t n_stations,
+                     const void* signals, int64_t n_samples, int64_t row_pitch,
+                     cmh_dtype sig_dtype, int32_t signals_on_device,
+                     const cmh_params* p, void* cuda_stream, cmh_model** out);
+
+/*
+ * Partition the event space into squares of side grid->L and colour them
+ * (§Partitioning the World): cells whose indices differ by the period
+ * P = ceil(2 R_max / L) + 1 share a colour (P^2 colours, 4 when
+ * R_max <= L/2), so same-colour regions have disjoint Markov blankets.
+ *   shift_mode 0: boundaries fixed at offset (sx, sy), 0 <= sx, sy < L
+ *                 (Algorithm "Chromatic MH with Static Coloring")
+ *   shift_mode 1: a fresh uniform offset in [0, L)^2 before every sweep, drawn
+ *                 from Philox (§Chromatic MH with Dynamic Coloring); sx, sy ignored
+ * Bins the current events into the cells.  May be called again (new grid).
+ * *n_colors_out (may be NULL) receives P^2.
+ * Errors: CMH_ERR_ARG, CMH_ERR_GEOMETRY (P^2 > 16), CMH_ERR_OOM, CMH_ERR_CAPACITY.
+ */
+int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mode,
+                            double sx, double sy, int32_t* n_colors_out);
+
+/*
+ * Enqueue n >= 0 sweeps on the model's stream and return (asynchronous).
+ * A sweep: (re)bin events into the shifted cells, then for each colour in
+ * order one launch in which every region of that colour runs k_per_phase MH
+ * steps (birth / death / move) on its own events with all others fixed.
+ * Errors: CMH_ERR_STATE (no partition yet, or an error is latched), CMH_ERR_CUDA.
+ */
+int cmh_run_sweeps(cmh_model* m, int64_t n);
+
+/*
+ * Synchronise and copy the current events out.
+ *   out [cap] host array (may be NULL when cap == 0); ids_out [cap] or NULL
+ *   *n_out receives the number of events (even when it exceeds cap)
+ *   *log_density_out (may be NULL): running log-density (prior + likelihood)
+ *   *stats_out (may be NULL)
+ * Events are ordered by region, then by id.  Returns a latched device error.
+ */
+int cmh_read_state(cmh_model* m, cmh_event* out, uint64_t* ids_out, int64_t cap,
+                   int64_t* n_out, double* log_density_out, cmh_stats* stats_out);
+
+/* Wait for the model's stream; return a latched device error if any. */
+int cmh_sync(cmh_model* m);
+
+/*
+ * Recompute the log-density from scratch on the device: the variance buffer
+ * is re-synthesised from the events, then prior + Gaussian log-likelihood are
+ * summed in float64.  Also resets the running log-density to that value.
+ */
+int cmh_log_density(cmh_model* m, double* out);
+
+/*
+ * Keep one cmh_trace record per MH step of the next sweeps, up to `capacity`
+ * records (0 disables).  Records are indexed by (sweep, cell, step).
+ */
+int cmh_set_trace(cmh_model* m, int64_t capacity);
+/* Copy the written trace records (ordered by sweep, cell, step). */
+int cmh_read_trace(cmh_model* m, cmh_trace* out, int64_t cap, int64_t* n_out);
+
+/* 1: launch sweeps without a CUDA graph and time every colour-phase kernel
+ * with CUDA events on the model stream (summed into cmh_stats.phase_ms). */
+int cmh_set_timing(cmh_model* m, int32_t enable);
+
+/* Current shift (sx, sy) of the partition. */
+int cmh_read_shift(cmh_model* m, double* sx, double* sy);
+
+/*
+ * Serialise the sampler state (parameters, grid, sweep counter, events with
+ * ids, running log-density) into buf.  With buf == NULL only *len is set.
+ * Errors: CMH_ERR_ARG (buffer too small: *len holds the size needed).
+ */
+int cmh_checkpoint(cmh_model* m, void* buf, size_t* len);
+/* Restore a checkpoint into a model built over the same stations and
+ * signals; re-synthesises the variance buffer.  Errors: CMH_ERR_ARG (corrupt
+ * or mismatched checkpoint). */
+int cmh_restore(cmh_model* m, const void* buf, size_t len);
+
+void cmh_destroy(cmh_model* m);
+const char* cmh_strerror(int code);
+
+/*
+ * Test hook: n Philox4x64-10 blocks computed by a device kernel.
+ * ctr [n][4], key [2], out [n][4] host arrays.
+ */
+int cmh_philox4x64(const uint64_t* ctr, const uint64_t* key, uint64_t* out, int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHROMH_H */

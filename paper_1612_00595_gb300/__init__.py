@@ -1,0 +1,294 @@
+"""Python binding of libchromh (include/chromh.h): argument marshalling only.
+
+Every step of the sampler runs in the CUDA library; this module converts
+numpy arrays / torch tensors into pointers and sizes and back.  Importing it
+loads ``libchromh.so`` from this directory and raises if it is missing: there
+is no fallback implementation.
+
+Names follow the C ABI: ``create_model``, ``partition_and_color``,
+``run_sweeps``, ``read_state`` (the calls of the paper's problem statement:
+events, stations and signals in; the event hypothesis out), plus trace,
+timing, checkpoint and test hooks.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libchromh.so")
+
+CMH_OK = 0
+ERRORS = {
+    -1: "CMH_ERR_ARG", -2: "CMH_ERR_GEOMETRY", -3: "CMH_ERR_NONFINITE", -4: "CMH_ERR_OOM",
+    -5: "CMH_ERR_CAPACITY", -6: "CMH_ERR_TIMEOUT", -7: "CMH_ERR_CUDA", -8: "CMH_ERR_STATE",
+}
+F64, F32 = 0, 1
+
+
+class ChromhError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__("%s failed: %s (%d, %s)" % (what, ERRORS.get(code, "?"), code, strerror(code)))
+
+
+class Params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in
+                ("W", "T", "Lambda", "v", "alpha", "beta_att", "tau", "t_s", "noise_var", "f_hz",
+                 "R_max", "p_birth", "p_death", "sig_xy", "sig_t", "sig_m")] + [
+        ("k_per_phase", C.c_int32), ("commit", C.c_int32), ("seed", C.c_uint64), ("dtype", C.c_int32),
+        ("ev_capacity", C.c_int32), ("frozen_capacity", C.c_int32), ("block_threads", C.c_int32),
+        ("max_events", C.c_int64)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("L", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("proposed", C.c_uint64 * 3), ("evaluated", C.c_uint64 * 3), ("accepted", C.c_uint64 * 3),
+                ("sweeps", C.c_int64), ("n_events", C.c_int64), ("phase_ms", C.c_double),
+                ("phase_launches", C.c_int64), ("kernel_launches", C.c_int64),
+                ("priced_samples", C.c_uint64), ("rewritten_samples", C.c_uint64)]
+
+    def as_dict(self):
+        return {"proposed": list(self.proposed), "evaluated": list(self.evaluated),
+                "accepted": list(self.accepted), "sweeps": self.sweeps, "n_events": self.n_events,
+                "phase_ms": self.phase_ms, "phase_launches": self.phase_launches,
+                "kernel_launches": self.kernel_launches, "priced_samples": self.priced_samples,
+                "rewritten_samples": self.rewritten_samples}
+
+
+TRACE_DTYPE = np.dtype([("sweep", "<i4"), ("cell", "<i4"), ("step", "<i4"), ("type", "<i4"),
+                        ("evaluated", "<i4"), ("accepted", "<i4"), ("n_before", "<i4"),
+                        ("written", "<i4"), ("dll", "<f8"), ("log_alpha", "<f8")])
+
+EXPORTS = ["cmh_create_model", "cmh_partition_and_color", "cmh_run_sweeps", "cmh_read_state", "cmh_sync",
+           "cmh_log_density", "cmh_set_trace", "cmh_read_trace", "cmh_set_timing", "cmh_read_shift",
+           "cmh_checkpoint", "cmh_restore", "cmh_destroy", "cmh_strerror", "cmh_philox4x64"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libchromh.so is not built (run __graft_entry__.build()); "
+                          "the sampler has no CPU fallback")
+    L = C.CDLL(LIB_PATH)
+    P, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    sig = {
+        "cmh_create_model": (C.c_int, [P, i64, P, i32, P, i64, i64, i32, i32, C.POINTER(Params), P,
+                                       C.POINTER(P)]),
+        "cmh_partition_and_color": (C.c_int, [P, C.POINTER(Grid), i32, C.c_double, C.c_double,
+                                              C.POINTER(i32)]),
+        "cmh_run_sweeps": (C.c_int, [P, i64]),
+        "cmh_read_state": (C.c_int, [P, P, P, i64, C.POINTER(i64), C.POINTER(C.c_double),
+                                     C.POINTER(Stats)]),
+        "cmh_sync": (C.c_int, [P]),
+        "cmh_log_density": (C.c_int, [P, C.POINTER(C.c_double)]),
+        "cmh_set_trace": (C.c_int, [P, i64]),
+        "cmh_read_trace": (C.c_int, [P, P, i64, C.POINTER(i64)]),
+        "cmh_set_timing": (C.c_int, [P, i32]),
+        "cmh_read_shift": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "cmh_checkpoint": (C.c_int, [P, P, C.POINTER(C.c_size_t)]),
+        "cmh_restore": (C.c_int, [P, P, C.c_size_t]),
+        "cmh_destroy": (None, [P]),
+        "cmh_strerror": (C.c_char_p, [C.c_int]),
+        "cmh_philox4x64": (C.c_int, [P, P, P, i64]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def strerror(code: int) -> str:
+    return lib.cmh_strerror(code).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != CMH_OK:
+        raise ChromhError(rc, what)
+
+
+def _ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def make_params(model_params, *, k_per_phase=32, seed=1, dtype=F64, p_birth=0.25, p_death=0.25,
+                sig_xy=5.0, sig_t=2.0, sig_m=0.1, commit=True, ev_capacity=0, frozen_capacity=0,
+                block_threads=0, max_events=0) -> Params:
+    """cmh_params from an object with the model fields (e.g. worldgen.ModelParams)."""
+    p = Params()
+    for n in ("W", "T", "Lambda", "v", "alpha", "beta_att", "tau", "t_s", "noise_var", "f_hz", "R_max"):
+        setattr(p, n, float(getattr(model_params, n)))
+    p.p_birth, p.p_death = p_birth, p_death
+    p.sig_xy, p.sig_t, p.sig_m = sig_xy, sig_t, sig_m
+    p.k_per_phase = k_per_phase
+    p.commit = 1 if commit else 0
+    p.seed = seed
+    p.dtype = dtype
+    p.ev_capacity = ev_capacity
+    p.frozen_capacity = frozen_capacity
+    p.block_threads = block_threads
+    p.max_events = max_events
+    return p
+
+
+class Model:
+    """A cmh_model handle (see create_model)."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep
+
+    def __del__(self):
+        self.destroy()
+
+    def destroy(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib.cmh_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    # ---- the four calls of the problem statement -------------------------
+    def partition_and_color(self, L: float, shift_mode: int = 1, sx: float = 0.0, sy: float = 0.0) -> int:
+        n = C.c_int32()
+        _check(lib.cmh_partition_and_color(self._h, C.byref(Grid(L)), shift_mode, sx, sy, C.byref(n)),
+               "cmh_partition_and_color")
+        return n.value
+
+    def run_sweeps(self, n: int):
+        _check(lib.cmh_run_sweeps(self._h, int(n)), "cmh_run_sweeps")
+
+    def read_state(self, cap: Optional[int] = None):
+        """(events [n,4] float64, ids [n] uint64, log_density, stats dict)."""
+        n = C.c_int64()
+        if cap is None:
+            _check(lib.cmh_read_state(self._h, None, None, 0, C.byref(n), None, None), "cmh_read_state")
+            cap = n.value
+        ev = np.zeros((cap, 4), dtype=np.float64)
+        ids = np.zeros(cap, dtype=np.uint64)
+        lp = C.c_double()
+        st = Stats()
+        _check(lib.cmh_read_state(self._h, _ptr(ev), _ptr(ids), cap, C.byref(n), C.byref(lp), C.byref(st)),
+               "cmh_read_state")
+        k = min(cap, n.value)
+        return ev[:k], ids[:k], lp.value, st.as_dict()
+
+    # ---- extras -------------------------------------------------------------
+    def sync(self):
+        _check(lib.cmh_sync(self._h), "cmh_sync")
+
+    def log_density(self) -> float:
+        out = C.c_double()
+        _check(lib.cmh_log_density(self._h, C.byref(out)), "cmh_log_density")
+        return out.value
+
+    def set_trace(self, capacity: int):
+        _check(lib.cmh_set_trace(self._h, int(capacity)), "cmh_set_trace")
+
+    def read_trace(self) -> np.ndarray:
+        n = C.c_int64()
+        _check(lib.cmh_read_trace(self._h, None, 0, C.byref(n)), "cmh_read_trace")
+        out = np.zeros(n.value, dtype=TRACE_DTYPE)
+        _check(lib.cmh_read_trace(self._h, _ptr(out), n.value, C.byref(n)), "cmh_read_trace")
+        return out
+
+    def set_timing(self, enable: bool):
+        _check(lib.cmh_set_timing(self._h, 1 if enable else 0), "cmh_set_timing")
+
+    def read_shift(self):
+        a, b = C.c_double(), C.c_double()
+        _check(lib.cmh_read_shift(self._h, C.byref(a), C.byref(b)), "cmh_read_shift")
+        return a.value, b.value
+
+    def checkpoint(self) -> bytes:
+        n = C.c_size_t()
+        _check(lib.cmh_checkpoint(self._h, None, C.byref(n)), "cmh_checkpoint")
+        buf = C.create_string_buffer(n.value)
+        _check(lib.cmh_checkpoint(self._h, buf, C.byref(n)), "cmh_checkpoint")
+        return buf.raw[: n.value]
+
+    def restore(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(lib.cmh_restore(self._h, buf, len(blob)), "cmh_restore")
+
+
+def create_model(events, stations, signals, params: Params, stream=None) -> Model:
+    """cmh_create_model.
+
+    events   [n, 4] float64 (x, y, t, m) or None for the empty hypothesis
+    stations [n_st, 2] float64
+    signals  [n_st, n_samples]: numpy float32/float64 (host) or a CUDA torch
+             tensor (device; its current stream orders the copy unless
+             ``stream`` is given)
+    stream   an int cudaStream_t or a torch.cuda.Stream; None lets the model
+             create its own stream
+    """
+    ev = np.zeros((0, 4)) if events is None else np.ascontiguousarray(events, dtype=np.float64).reshape(-1, 4)
+    st = np.ascontiguousarray(stations, dtype=np.float64).reshape(-1, 2)
+    on_device = 0
+    keep = [ev, st]
+    if hasattr(signals, "data_ptr") and getattr(signals, "is_cuda", False):
+        import torch
+        if signals.dtype not in (torch.float32, torch.float64) or signals.dim() != 2 or signals.stride(1) != 1:
+            raise ValueError("device signals must be a 2-D row-major float32/float64 tensor")
+        sig_ptr = C.c_void_p(signals.data_ptr())
+        n_st, n_samp = signals.shape
+        pitch = signals.stride(0)
+        sdt = F32 if signals.dtype == torch.float32 else F64
+        on_device = 1
+        if stream is None:
+            stream = torch.cuda.current_stream(signals.device)
+        keep.append(signals)
+    else:
+        sig = np.asarray(signals)
+        if sig.dtype not in (np.float32, np.float64):
+            sig = sig.astype(np.float64)
+        if sig.ndim != 2:
+            sig = sig.reshape(st.shape[0], -1)
+        sig = np.ascontiguousarray(sig)
+        n_st, n_samp = sig.shape
+        pitch = n_samp
+        sdt = F32 if sig.dtype == np.float32 else F64
+        sig_ptr = _ptr(sig) if n_st else None
+        keep.append(sig)
+    if hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    h = C.c_void_p()
+    _check(lib.cmh_create_model(_ptr(ev) if len(ev) else None, ev.shape[0], _ptr(st) if len(st) else None,
+                                st.shape[0], sig_ptr, n_samp, pitch, sdt, on_device, C.byref(params),
+                                C.c_void_p(stream) if stream else None, C.byref(h)),
+           "cmh_create_model")
+    return Model(h, keep[:0])
+
+
+def partition_and_color(model: Model, L: float, shift_mode: int = 1, sx: float = 0.0, sy: float = 0.0):
+    return model.partition_and_color(L, shift_mode, sx, sy)
+
+
+def run_sweeps(model: Model, n: int):
+    return model.run_sweeps(n)
+
+
+def read_state(model: Model, cap: Optional[int] = None):
+    return model.read_state(cap)
+
+
+def philox4x64(ctr, key) -> np.ndarray:
+    """Device Philox4x64-10 blocks for counters ctr [n, 4] and key [2]."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint64).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint64).reshape(2)
+    out = np.zeros_like(c)
+    _check(lib.cmh_philox4x64(_ptr(c), _ptr(k), _ptr(out), c.shape[0]), "cmh_philox4x64")
+    return out

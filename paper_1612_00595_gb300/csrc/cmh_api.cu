@@ -1,0 +1,827 @@
+// Host side of the chromh C ABI (include/chromh.h).
+//
+// A model owns: the signals and the predicted-variance buffer V (row-major
+// [station][pitch], pitch a multiple of 64 samples), two event stores used
+// alternately by consecutive sweeps, the partition tables, and a CUDA graph
+// of one sweep (re-bin + one phase launch per colour + bookkeeping) that
+// cmh_run_sweeps replays.  Every kernel reads the sweep number from device
+// memory, so one captured graph serves every sweep.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "chromh.h"
+#include "cmh_common.cuh"
+
+using namespace cmh;
+
+namespace {
+
+constexpr uint64_t kCkptMagic = 0x31484d4f52484343ULL;  // "CCHROMH1"
+constexpr int kCkptVersion = 1;
+
+int cuda_err(cudaError_t e) {
+    if (e == cudaSuccess) return CMH_OK;
+    if (e == cudaErrorMemoryAllocation) return CMH_ERR_OOM;
+    return CMH_ERR_CUDA;
+}
+
+#define CK(expr)                                 \
+    do {                                         \
+        cudaError_t e_ = (expr);                 \
+        if (e_ != cudaSuccess) return cuda_err(e_); \
+    } while (0)
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+}  // namespace
+
+struct cmh_model {
+    cmh_params p{};
+    Geo g{};
+    Dev d{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<void*> allocs;        // freed at destroy
+    std::vector<void*> part_allocs;   // freed when re-partitioned
+    FlatList flat{};
+    long long flat_cap = 0;
+    double* partial = nullptr;
+    int n_partial = 0;
+    bool partitioned = false;
+    double grid_L = 0.0, sx0 = 0.0, sy0 = 0.0;
+    int shift_mode = 0;
+    long long sweeps = 0;             // host mirror of the device sweep counter
+    long long launches = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int timing = 0;
+    double phase_ms = 0.0;
+    long long phase_launches = 0;
+    int latched = 0;
+    long long trace_cap = 0;
+    long long n0 = 0;
+
+    template <typename T>
+    cudaError_t alloc(T** ptr, size_t count, bool partition_scope = false) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+        if (e != cudaSuccess) return e;
+        (partition_scope ? part_allocs : allocs).push_back(q);
+        *ptr = (T*)q;
+        return cudaSuccess;
+    }
+
+    void drop_graph() {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (graph) cudaGraphDestroy(graph);
+        graph_exec = nullptr;
+        graph = nullptr;
+    }
+
+    void free_partition() {
+        drop_graph();
+        for (void* q : part_allocs) cudaFree(q);
+        part_allocs.clear();
+    }
+};
+
+namespace {
+
+// exact upper bound of how many stations lie within `radius` of any point:
+// all of them are within 2 * radius of one of them
+int max_within(const std::vector<double>& sx, const std::vector<double>& sy, double radius) {
+    const size_t n = sx.size();
+    int best = 0;
+    const double r2 = 4.0 * radius * radius;
+    for (size_t i = 0; i < n; ++i) {
+        int c = 0;
+        for (size_t j = 0; j < n; ++j) {
+            const double dx = sx[i] - sx[j], dy = sy[i] - sy[j];
+            c += dx * dx + dy * dy < r2;
+        }
+        best = std::max(best, c);
+    }
+    return best;
+}
+
+int check_status(cmh_model* m) {
+    if (m->latched) return m->latched;
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, m->d.status, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    if (st) m->latched = st;
+    return st;
+}
+
+// the store holding the current events between sweeps
+int cur_buf(const cmh_model* m) { return (int)((m->sweeps + 1) & 1); }
+
+int upload_sweep(cmh_model* m, long long s) {
+    CK(cudaMemcpyAsync(m->d.sweep, &s, sizeof(long long), cudaMemcpyHostToDevice, m->stream));
+    return CMH_OK;
+}
+
+// events of the current store -> flat list (device), count on the host
+int flatten_current(cmh_model* m, int* n_host) {
+    int dummy = 0;
+    CK(launch_flatten(m->g, m->d, cur_buf(m), m->flat, m->stream, &dummy));
+    m->launches += dummy;
+    CK(cudaMemcpyAsync(n_host, m->flat.n, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    return CMH_OK;
+}
+
+double host_log_prior(const cmh_params& p, const double* x, const double* y, const double* t,
+                      const double* mm, long long n) {
+    double lp = -p.Lambda;
+    for (long long i = 0; i < n; ++i) {
+        if (!(x[i] >= 0.0 && x[i] < p.W && y[i] >= 0.0 && y[i] < p.W && t[i] >= 0.0 && t[i] < p.T &&
+              mm[i] >= 2.0))
+            return -INFINITY;
+        lp += std::log(p.Lambda) - std::log(p.W * p.W * p.T) - (mm[i] - 2.0);
+    }
+    return lp;
+}
+
+// V from the flat list, then prior (host) + likelihood (device) in float64
+int synth_and_logdensity(cmh_model* m, int n_flat, double* out) {
+    int l = 0;
+    CK(launch_vsynth(m->g, m->d, m->flat, m->stream, &l));
+    CK(launch_loglik(m->g, m->d, m->partial, m->n_partial, m->stream));
+    l += 1;
+    m->launches += l;
+    std::vector<double> part(m->n_partial);
+    std::vector<double> hx(n_flat), hy(n_flat), ht(n_flat), hm(n_flat);
+    CK(cudaMemcpyAsync(part.data(), m->partial, sizeof(double) * m->n_partial, cudaMemcpyDeviceToHost, m->stream));
+    if (n_flat) {
+        CK(cudaMemcpyAsync(hx.data(), m->flat.x, sizeof(double) * n_flat, cudaMemcpyDeviceToHost, m->stream));
+        CK(cudaMemcpyAsync(hy.data(), m->flat.y, sizeof(double) * n_flat, cudaMemcpyDeviceToHost, m->stream));
+        CK(cudaMemcpyAsync(ht.data(), m->flat.t, sizeof(double) * n_flat, cudaMemcpyDeviceToHost, m->stream));
+        CK(cudaMemcpyAsync(hm.data(), m->flat.m, sizeof(double) * n_flat, cudaMemcpyDeviceToHost, m->stream));
+    }
+    CK(cudaStreamSynchronize(m->stream));
+    double ll = 0.0;
+    for (double v : part) ll += v;
+    *out = host_log_prior(m->p, hx.data(), hy.data(), ht.data(), hm.data(), n_flat) + ll;
+    CK(cudaMemcpyAsync(m->d.logp, out, sizeof(double), cudaMemcpyHostToDevice, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    return CMH_OK;
+}
+
+int validate_params(const cmh_params* p) {
+    if (!p) return CMH_ERR_ARG;
+    const double pos[] = {p->W, p->T, p->Lambda, p->v, p->tau, p->t_s, p->noise_var, p->f_hz, p->R_max,
+                          p->sig_xy, p->sig_t, p->sig_m};
+    for (double v : pos)
+        if (!finite_pos(v)) return CMH_ERR_ARG;
+    if (!std::isfinite(p->alpha) || !std::isfinite(p->beta_att)) return CMH_ERR_ARG;
+    if (!(p->p_birth > 0.0 && p->p_death > 0.0 && p->p_birth + p->p_death < 1.0)) return CMH_ERR_ARG;
+    if (p->k_per_phase < 1 || p->k_per_phase > kMaxK) return CMH_ERR_ARG;
+    if (p->dtype != CMH_F32 && p->dtype != CMH_F64) return CMH_ERR_ARG;
+    if (p->ev_capacity < 0 || p->frozen_capacity < 0 || p->max_events < 0) return CMH_ERR_ARG;
+    if (p->block_threads != 0 && (p->block_threads < 64 || p->block_threads > 512 || p->block_threads % 32))
+        return CMH_ERR_ARG;
+    const double nw = std::llround(p->t_s * p->f_hz);
+    if (nw < 1 || nw > 1e8) return CMH_ERR_ARG;
+    return CMH_OK;
+}
+
+int bin_flat_into_current(cmh_model* m, int n_flat) {
+    // the flat list becomes the "previous" store of a pseudo sweep s+1; its
+    // re-bin writes the store sweep s will read
+    const long long s = m->sweeps;
+    Store src = m->d.st[s & 1];
+    if (n_flat) {
+        CK(cudaMemcpyAsync(src.x, m->flat.x, sizeof(double) * n_flat, cudaMemcpyDeviceToDevice, m->stream));
+        CK(cudaMemcpyAsync(src.y, m->flat.y, sizeof(double) * n_flat, cudaMemcpyDeviceToDevice, m->stream));
+        CK(cudaMemcpyAsync(src.t, m->flat.t, sizeof(double) * n_flat, cudaMemcpyDeviceToDevice, m->stream));
+        CK(cudaMemcpyAsync(src.m, m->flat.m, sizeof(double) * n_flat, cudaMemcpyDeviceToDevice, m->stream));
+        CK(cudaMemcpyAsync(src.id, m->flat.id, sizeof(unsigned long long) * n_flat, cudaMemcpyDeviceToDevice,
+                           m->stream));
+    }
+    int rc = upload_sweep(m, s + 1);
+    if (rc) return rc;
+    int l = 0;
+    CK(launch_rebin(m->g, m->d, n_flat, m->stream, &l));
+    m->launches += l;
+    rc = upload_sweep(m, s);
+    if (rc) return rc;
+    return check_status(m);
+}
+
+int capture_graph(cmh_model* m) {
+    m->drop_graph();
+    CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+    int l = 0;
+    cudaError_t e = launch_rebin(m->g, m->d, -1, m->stream, &l);
+    for (int c = 0; c < m->g.n_colours && e == cudaSuccess; ++c) e = launch_phase(m->g, m->d, c, m->stream);
+    if (e == cudaSuccess) e = launch_sweep_end(m->g, m->d, m->stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(m->stream, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_err(e);
+    }
+    CK(e2);
+    m->graph = graph;
+    CK(cudaGraphInstantiate(&m->graph_exec, graph, 0));
+    return CMH_OK;
+}
+
+int launches_per_sweep(const cmh_model* m) { return 3 + m->g.n_colours + 1; }
+
+// grow the flat list to `cap` events, keeping its first n_keep
+int ensure_flat(cmh_model* m, long long cap, int n_keep) {
+    if (cap <= m->flat_cap) return CMH_OK;
+    FlatList nf{};
+    void* q[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    const size_t sz[6] = {sizeof(double), sizeof(double), sizeof(double), sizeof(double),
+                          sizeof(unsigned long long), sizeof(int)};
+    for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaMalloc(&q[i], sz[i] * (i == 5 ? 1 : (size_t)cap));
+    if (e != cudaSuccess) {
+        for (void* x : q) if (x) cudaFree(x);
+        return cuda_err(e);
+    }
+    nf.x = (double*)q[0]; nf.y = (double*)q[1]; nf.t = (double*)q[2]; nf.m = (double*)q[3];
+    nf.id = (unsigned long long*)q[4]; nf.n = (int*)q[5];
+    void* old[6] = {m->flat.x, m->flat.y, m->flat.t, m->flat.m, m->flat.id, m->flat.n};
+    for (int i = 0; i < 6; ++i) {
+        const size_t bytes = sz[i] * (i == 5 ? 1 : (size_t)n_keep);
+        if (bytes) CK(cudaMemcpyAsync(q[i], old[i], bytes, cudaMemcpyDeviceToDevice, m->stream));
+    }
+    CK(cudaStreamSynchronize(m->stream));
+    for (void* x : old) {
+        auto it = std::find(m->allocs.begin(), m->allocs.end(), x);
+        if (it != m->allocs.end()) m->allocs.erase(it);
+        cudaFree(x);
+    }
+    for (void* x : q) m->allocs.push_back(x);
+    m->flat = nf;
+    m->flat_cap = cap;
+    return CMH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cmh_strerror(int code) {
+    switch (code) {
+        case CMH_OK: return "ok";
+        case CMH_ERR_ARG: return "invalid argument";
+        case CMH_ERR_GEOMETRY: return "R_max too large for the colour pattern of this grid";
+        case CMH_ERR_NONFINITE: return "non-finite signal sample or event coordinate";
+        case CMH_ERR_OOM: return "device allocation failed";
+        case CMH_ERR_CAPACITY: return "a fixed capacity (events, blanket, arrivals) was exceeded";
+        case CMH_ERR_TIMEOUT: return "a bounded device wait gave up";
+        case CMH_ERR_CUDA: return "CUDA runtime error";
+        case CMH_ERR_STATE: return "call out of order or error latched";
+        default: return "unknown error";
+    }
+}
+
+int cmh_create_model(const cmh_event* init_events, int64_t n_events, const cmh_station* stations,
+                     int32_t n_stations, const void* signals, int64_t n_samples, int64_t row_pitch,
+                     cmh_dtype sig_dtype, int32_t signals_on_device, const cmh_params* p, void* cuda_stream,
+                     cmh_model** out) {
+    if (!out) return CMH_ERR_ARG;
+    *out = nullptr;
+    int rc = validate_params(p);
+    if (rc) return rc;
+    if (n_events < 0 || (n_events > 0 && !init_events) || n_stations < 0 || (n_stations > 0 && !stations) ||
+        n_samples < 1 || row_pitch < n_samples || (n_stations > 0 && !signals) ||
+        (sig_dtype != CMH_F32 && sig_dtype != CMH_F64))
+        return CMH_ERR_ARG;
+    if (n_samples > (1LL << 30)) return CMH_ERR_ARG;
+    for (int64_t i = 0; i < n_events; ++i) {
+        const cmh_event& e = init_events[i];
+        if (!std::isfinite(e.x) || !std::isfinite(e.y) || !std::isfinite(e.t) || !std::isfinite(e.m))
+            return CMH_ERR_NONFINITE;
+        if (!(e.x >= 0.0 && e.x < p->W && e.y >= 0.0 && e.y < p->W && e.t >= 0.0 && e.t < p->T && e.m >= 2.0))
+            return CMH_ERR_ARG;
+    }
+    for (int32_t j = 0; j < n_stations; ++j)
+        if (!std::isfinite(stations[j].x) || !std::isfinite(stations[j].y)) return CMH_ERR_NONFINITE;
+
+    cmh_model* m = new (std::nothrow) cmh_model();
+    if (!m) return CMH_ERR_OOM;
+    m->p = *p;
+    if (m->p.ev_capacity == 0) m->p.ev_capacity = 128;
+    if (m->p.frozen_capacity == 0) m->p.frozen_capacity = 32;
+    if (m->p.block_threads == 0) m->p.block_threads = 256;
+    if (m->p.max_events == 0) m->p.max_events = 4 * (n_events + (int64_t)std::ceil(p->Lambda)) + 4096;
+    if (m->p.max_events < n_events) { delete m; return CMH_ERR_ARG; }
+    m->n0 = n_events;
+
+    auto fail = [&](int code) {
+        cmh_destroy(m);
+        return code;
+    };
+    if (cuda_stream) {
+        m->stream = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail(cuda_err(e));
+        m->own_stream = true;
+    }
+    Geo& g = m->g;
+    g.W = p->W; g.T = p->T; g.Lambda = p->Lambda; g.v = p->v; g.alpha = p->alpha; g.beta_att = p->beta_att;
+    g.tau = p->tau; g.noise_var = p->noise_var; g.f_hz = p->f_hz; g.R_max = p->R_max;
+    g.p_birth = p->p_birth; g.p_death = p->p_death; g.sig_xy = p->sig_xy; g.sig_t = p->sig_t; g.sig_m = p->sig_m;
+    g.log_pb = std::log(p->p_birth);
+    g.log_pd = std::log(p->p_death);
+    g.log_Lambda = std::log(p->Lambda);
+    g.log_WWT = std::log(p->W * p->W * p->T);
+    g.log_T = std::log(p->T);
+    g.n_w = (int)std::llround(p->t_s * p->f_hz);
+    g.k = p->k_per_phase;
+    g.commit = p->commit ? 1 : 0;
+    g.n_st = n_stations;
+    g.n_samp = n_samples;
+    g.pitch = (n_samples + 63) / 64 * 64;
+    g.seed = p->seed;
+    g.ev_cap = m->p.ev_capacity;
+    g.frz_cap = m->p.frozen_capacity;
+    g.f32 = p->dtype == CMH_F32;
+    g.threads = m->p.block_threads;
+    g.max_events = m->p.max_events;
+    if (g.ev_cap < g.k + 1) return fail(CMH_ERR_ARG);
+
+    Dev& d = m->d;
+    const size_t esz = g.f32 ? sizeof(float) : sizeof(double);
+    std::vector<double> hx(n_stations), hy(n_stations);
+    for (int j = 0; j < n_stations; ++j) { hx[j] = stations[j].x; hy[j] = stations[j].y; }
+    double *stx = nullptr, *sty = nullptr;
+    cudaError_t e;
+    if ((e = m->alloc(&stx, n_stations)) || (e = m->alloc(&sty, n_stations))) return fail(cuda_err(e));
+    d.stx = stx;
+    d.sty = sty;
+    unsigned char *sig = nullptr, *V = nullptr;
+    if ((e = m->alloc(&sig, (size_t)n_stations * g.pitch * esz)) ||
+        (e = m->alloc(&V, (size_t)n_stations * g.pitch * esz)))
+        return fail(cuda_err(e));
+    d.sig = sig;
+    d.V = V;
+    int* nonfinite = nullptr;
+    if ((e = m->alloc(&d.status, 1)) || (e = m->alloc(&d.sweep, 1)) || (e = m->alloc(&d.shift, 2)) ||
+        (e = m->alloc(&d.logp, 1)) || (e = m->alloc(&d.stats, kStats)) || (e = m->alloc(&nonfinite, 1)))
+        return fail(cuda_err(e));
+    double* log_n = nullptr;
+    if ((e = m->alloc(&log_n, g.ev_cap + 2))) return fail(cuda_err(e));
+    d.log_n = log_n;
+    m->n_partial = 1216;
+    if ((e = m->alloc(&m->partial, m->n_partial))) return fail(cuda_err(e));
+    m->flat_cap = m->p.max_events;
+    if ((e = m->alloc(&m->flat.x, m->flat_cap)) || (e = m->alloc(&m->flat.y, m->flat_cap)) ||
+        (e = m->alloc(&m->flat.t, m->flat_cap)) || (e = m->alloc(&m->flat.m, m->flat_cap)) ||
+        (e = m->alloc(&m->flat.id, m->flat_cap)) || (e = m->alloc(&m->flat.n, 1)))
+        return fail(cuda_err(e));
+
+    std::vector<double> ln(g.ev_cap + 2);
+    ln[0] = -INFINITY;
+    for (int i = 1; i < g.ev_cap + 2; ++i) ln[i] = std::log((double)i);
+    cudaStream_t s = m->stream;
+    if ((e = cudaMemcpyAsync(log_n, ln.data(), sizeof(double) * ln.size(), cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(stx, hx.data(), sizeof(double) * n_stations, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(sty, hy.data(), sizeof(double) * n_stations, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemsetAsync(d.status, 0, sizeof(int), s)) || (e = cudaMemsetAsync(nonfinite, 0, sizeof(int), s)) ||
+        (e = cudaMemsetAsync(d.sweep, 0, sizeof(long long), s)) ||
+        (e = cudaMemsetAsync(d.stats, 0, sizeof(unsigned long long) * kStats, s)) ||
+        (e = cudaMemsetAsync(d.V, 0, (size_t)n_stations * g.pitch * esz, s)))
+        return fail(cuda_err(e));
+
+    // signals: copy (and convert) into the padded device buffer
+    if (n_stations > 0) {
+        const size_t ssz = sig_dtype == CMH_F32 ? sizeof(float) : sizeof(double);
+        const void* src = signals;
+        void* staged = nullptr;
+        if (!signals_on_device) {
+            e = cudaMalloc(&staged, (size_t)n_stations * n_samples * ssz);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(staged, n_samples * ssz, signals, row_pitch * ssz, n_samples * ssz, n_stations,
+                                      cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) {
+                if (staged) cudaFree(staged);
+                return fail(cuda_err(e));
+            }
+            src = staged;
+        }
+        e = launch_convert_signals(src, sig_dtype == CMH_F32, signals_on_device ? row_pitch : n_samples, sig,
+                                   g.f32, g.pitch, n_stations, n_samples, nonfinite, s);
+        m->launches += 1;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (staged) cudaFree(staged);
+        if (e != cudaSuccess) return fail(cuda_err(e));
+        int bad = 0;
+        if ((e = cudaMemcpy(&bad, nonfinite, sizeof(int), cudaMemcpyDeviceToHost))) return fail(cuda_err(e));
+        if (bad) return fail(CMH_ERR_NONFINITE);
+    }
+    // initial events -> flat list -> V and the log-density
+    {
+        std::vector<double> ex(n_events), ey(n_events), et(n_events), em(n_events);
+        std::vector<unsigned long long> id(n_events);
+        for (int64_t i = 0; i < n_events; ++i) {
+            ex[i] = init_events[i].x; ey[i] = init_events[i].y; et[i] = init_events[i].t; em[i] = init_events[i].m;
+            id[i] = (unsigned long long)i;
+        }
+        const int n = (int)n_events;
+        if ((e = cudaMemcpyAsync(m->flat.x, ex.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemcpyAsync(m->flat.y, ey.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemcpyAsync(m->flat.t, et.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemcpyAsync(m->flat.m, em.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemcpyAsync(m->flat.id, id.data(), sizeof(unsigned long long) * n, cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemcpyAsync(m->flat.n, &n, sizeof(int), cudaMemcpyHostToDevice, s)))
+            return fail(cuda_err(e));
+        double lp = 0.0;
+        rc = synth_and_logdensity(m, n, &lp);
+        if (rc) return fail(rc);
+    }
+    *out = m;
+    return CMH_OK;
+}
+
+int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mode, double sx, double sy,
+                            int32_t* n_colors_out) {
+    if (!m || !grid) return CMH_ERR_ARG;
+    if (m->latched) return CMH_ERR_STATE;
+    const double L = grid->L;
+    if (!finite_pos(L) || (shift_mode != 0 && shift_mode != 1)) return CMH_ERR_ARG;
+    if (shift_mode == 0 && !(sx >= 0.0 && sx < L && sy >= 0.0 && sy < L)) return CMH_ERR_ARG;
+    const int P = (int)std::ceil(2.0 * m->p.R_max / L) + 1;
+    if (P * P > kMaxColours) return CMH_ERR_GEOMETRY;
+    const double ncell_axis = std::floor(m->p.W / L) + 2;
+    if (ncell_axis * ncell_axis > (double)(1 << 20)) return CMH_ERR_ARG;
+
+    // current events -> flat list (the model's own order)
+    int n_flat = (int)m->n0;
+    if (m->partitioned) {
+        int rc = flatten_current(m, &n_flat);
+        if (rc) return rc;
+        m->n0 = n_flat;   // until binned again, the flat list is the state
+    }
+    m->free_partition();
+    m->partitioned = false;
+
+    Geo& g = m->g;
+    g.L = L;
+    g.shift_mode = shift_mode;
+    g.sx_static = shift_mode == 0 ? sx : 0.0;
+    g.sy_static = shift_mode == 0 ? sy : 0.0;
+    g.ncx = g.ncy = (int)ncell_axis;
+    g.n_cells = g.ncx * g.ncy;
+    g.period = P;
+    g.n_colours = P * P;
+    g.max_rpc = ((g.ncx + P - 1) / P) * ((g.ncy + P - 1) / P);
+    // capacities that depend on the station geometry (exact bounds)
+    std::vector<double> hx(g.n_st), hy(g.n_st);
+    if (g.n_st) {
+        CK(cudaMemcpy(hx.data(), m->d.stx, sizeof(double) * g.n_st, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(hy.data(), m->d.sty, sizeof(double) * g.n_st, cudaMemcpyDeviceToHost));
+    }
+    const double Rm = m->p.R_max * 1.0001 + 1e-3;
+    g.arr_cap = std::max(1, max_within(hx, hy, m->p.R_max));
+    g.blk_cap = std::max(1, std::min(g.n_st, max_within(hx, hy, L * std::sqrt(0.5) + Rm)));
+    g.store_cap = m->p.max_events + (long long)g.n_cells * g.k;
+    if (g.store_cap > (1LL << 31) - 1) return CMH_ERR_ARG;
+    if (n_flat > m->p.max_events) return CMH_ERR_CAPACITY;   // the new store could not hold them
+    {
+        int rc = ensure_flat(m, g.store_cap, n_flat);
+        if (rc) return rc;
+    }
+    if (phase_smem_bytes(g) > 227 * 1024) return CMH_ERR_CAPACITY;
+    CK(prepare_kernels(g));
+
+    Dev& d = m->d;
+    cudaError_t e;
+    for (int b = 0; b < 2; ++b) {
+        Store& S = d.st[b];
+        if ((e = m->alloc(&S.x, g.store_cap, true)) || (e = m->alloc(&S.y, g.store_cap, true)) ||
+            (e = m->alloc(&S.t, g.store_cap, true)) || (e = m->alloc(&S.m, g.store_cap, true)) ||
+            (e = m->alloc(&S.id, g.store_cap, true)) || (e = m->alloc(&S.start, g.n_cells, true)) ||
+            (e = m->alloc(&S.count, g.n_cells, true)) || (e = m->alloc(&S.cap, g.n_cells, true)) ||
+            (e = m->alloc(&S.total, 1, true)))
+            return cuda_err(e);
+        CK(cudaMemsetAsync(S.count, 0, sizeof(int) * g.n_cells, m->stream));
+        CK(cudaMemsetAsync(S.start, 0, sizeof(int) * g.n_cells, m->stream));
+        CK(cudaMemsetAsync(S.total, 0, sizeof(int), m->stream));
+    }
+    if ((e = m->alloc(&d.colour_count, kMaxColours, true)) ||
+        (e = m->alloc(&d.colour_cells, (size_t)g.n_colours * g.max_rpc, true)) ||
+        (e = m->alloc(&d.fill, g.n_cells, true)) || (e = m->alloc(&d.region_dlp, g.n_cells, true)))
+        return cuda_err(e);
+    CK(cudaMemsetAsync(d.region_dlp, 0, sizeof(double) * g.n_cells, m->stream));
+    CK(cudaMemsetAsync(d.colour_count, 0, sizeof(int) * kMaxColours, m->stream));
+    if (m->trace_cap > 0) CK(cudaMemsetAsync(d.trace, 0, sizeof(cmh_trace) * m->trace_cap, m->stream));
+
+    m->grid_L = L;
+    m->shift_mode = shift_mode;
+    m->sx0 = sx;
+    m->sy0 = sy;
+    int rc = bin_flat_into_current(m, n_flat);
+    if (rc) return rc;
+    m->partitioned = true;
+    if (n_colors_out) *n_colors_out = g.n_colours;
+    return CMH_OK;
+}
+
+int cmh_run_sweeps(cmh_model* m, int64_t n) {
+    if (!m || n < 0) return CMH_ERR_ARG;
+    if (!m->partitioned || m->latched) return CMH_ERR_STATE;
+    if (n == 0) return CMH_OK;
+    if (m->timing) {
+        std::vector<cudaEvent_t> ev;
+        ev.reserve((size_t)(2 * n * m->g.n_colours));
+        int rc = CMH_OK;
+        for (int64_t i = 0; i < n && rc == CMH_OK; ++i) {
+            int l = 0;
+            cudaError_t e = launch_rebin(m->g, m->d, -1, m->stream, &l);
+            for (int c = 0; c < m->g.n_colours && e == cudaSuccess; ++c) {
+                cudaEvent_t a, b;
+                cudaEventCreate(&a);
+                cudaEventCreate(&b);
+                ev.push_back(a);
+                ev.push_back(b);
+                cudaEventRecord(a, m->stream);
+                e = launch_phase(m->g, m->d, c, m->stream);
+                cudaEventRecord(b, m->stream);
+            }
+            if (e == cudaSuccess) e = launch_sweep_end(m->g, m->d, m->stream);
+            if (e != cudaSuccess) rc = cuda_err(e);
+            m->launches += launches_per_sweep(m);
+            m->sweeps += 1;
+        }
+        cudaError_t e = cudaStreamSynchronize(m->stream);
+        for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) m->phase_ms += ms;
+            m->phase_launches += 1;
+        }
+        for (cudaEvent_t x : ev) cudaEventDestroy(x);
+        if (rc) return rc;
+        return cuda_err(e);
+    }
+    if (!m->graph_exec) {
+        int rc = capture_graph(m);
+        if (rc) return rc;
+    }
+    for (int64_t i = 0; i < n; ++i) CK(cudaGraphLaunch(m->graph_exec, m->stream));
+    m->launches += n * launches_per_sweep(m);
+    m->sweeps += n;
+    return CMH_OK;
+}
+
+int cmh_sync(cmh_model* m) {
+    if (!m) return CMH_ERR_ARG;
+    CK(cudaStreamSynchronize(m->stream));
+    return check_status(m);
+}
+
+int cmh_read_state(cmh_model* m, cmh_event* out, uint64_t* ids_out, int64_t cap, int64_t* n_out,
+                   double* log_density_out, cmh_stats* stats_out) {
+    if (!m || cap < 0 || (cap > 0 && !out)) return CMH_ERR_ARG;
+    CK(cudaStreamSynchronize(m->stream));
+    int rc = check_status(m);
+    if (rc) return rc;
+    int n = (int)m->n0;
+    if (m->partitioned) {
+        rc = flatten_current(m, &n);
+        if (rc) return rc;
+    }
+    if (n_out) *n_out = n;
+    const int64_t nc = std::min<int64_t>(cap, n);
+    if (nc > 0) {
+        std::vector<double> x(nc), y(nc), t(nc), mm(nc);
+        CK(cudaMemcpy(x.data(), m->flat.x, sizeof(double) * nc, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(y.data(), m->flat.y, sizeof(double) * nc, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(t.data(), m->flat.t, sizeof(double) * nc, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(mm.data(), m->flat.m, sizeof(double) * nc, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < nc; ++i) out[i] = cmh_event{x[i], y[i], t[i], mm[i]};
+        if (ids_out) CK(cudaMemcpy(ids_out, m->flat.id, sizeof(uint64_t) * nc, cudaMemcpyDeviceToHost));
+    }
+    if (log_density_out) CK(cudaMemcpy(log_density_out, m->d.logp, sizeof(double), cudaMemcpyDeviceToHost));
+    if (stats_out) {
+        unsigned long long st[kStats];
+        CK(cudaMemcpy(st, m->d.stats, sizeof(st), cudaMemcpyDeviceToHost));
+        std::memset(stats_out, 0, sizeof(*stats_out));
+        for (int i = 0; i < 3; ++i) {
+            stats_out->proposed[i] = st[i];
+            stats_out->evaluated[i] = st[3 + i];
+            stats_out->accepted[i] = st[6 + i];
+        }
+        stats_out->sweeps = m->sweeps;
+        stats_out->n_events = n;
+        stats_out->phase_ms = m->phase_ms;
+        stats_out->phase_launches = m->phase_launches;
+        stats_out->kernel_launches = m->launches;
+        stats_out->priced_samples = st[9];
+        stats_out->rewritten_samples = st[10];
+    }
+    return CMH_OK;
+}
+
+int cmh_log_density(cmh_model* m, double* out) {
+    if (!m || !out) return CMH_ERR_ARG;
+    CK(cudaStreamSynchronize(m->stream));
+    int rc = check_status(m);
+    if (rc) return rc;
+    int n = (int)m->n0;
+    if (m->partitioned) {
+        rc = flatten_current(m, &n);
+        if (rc) return rc;
+    }
+    return synth_and_logdensity(m, n, out);
+}
+
+int cmh_set_trace(cmh_model* m, int64_t capacity) {
+    if (!m || capacity < 0) return CMH_ERR_ARG;
+    CK(cudaStreamSynchronize(m->stream));
+    m->drop_graph();
+    if (m->d.trace) {
+        cudaFree(m->d.trace);
+        auto it = std::find(m->allocs.begin(), m->allocs.end(), (void*)m->d.trace);
+        if (it != m->allocs.end()) m->allocs.erase(it);
+        m->d.trace = nullptr;
+    }
+    m->trace_cap = capacity;
+    m->d.trace_cap = capacity;
+    m->d.trace_sweep0 = m->sweeps;
+    if (capacity > 0) {
+        cudaError_t e = m->alloc(&m->d.trace, capacity);
+        if (e) return cuda_err(e);
+        CK(cudaMemsetAsync(m->d.trace, 0, sizeof(cmh_trace) * capacity, m->stream));
+    }
+    return CMH_OK;
+}
+
+int cmh_read_trace(cmh_model* m, cmh_trace* out, int64_t cap, int64_t* n_out) {
+    if (!m || cap < 0 || (cap > 0 && !out)) return CMH_ERR_ARG;
+    CK(cudaStreamSynchronize(m->stream));
+    std::vector<cmh_trace> all(m->trace_cap);
+    if (m->trace_cap) CK(cudaMemcpy(all.data(), m->d.trace, sizeof(cmh_trace) * m->trace_cap, cudaMemcpyDeviceToHost));
+    int64_t n = 0;
+    for (const cmh_trace& r : all) {
+        if (!r.written) continue;
+        if (n < cap) out[n] = r;
+        ++n;
+    }
+    if (n_out) *n_out = n;
+    return CMH_OK;
+}
+
+int cmh_set_timing(cmh_model* m, int32_t enable) {
+    if (!m) return CMH_ERR_ARG;
+    m->timing = enable ? 1 : 0;
+    return CMH_OK;
+}
+
+int cmh_read_shift(cmh_model* m, double* sx, double* sy) {
+    if (!m || !sx || !sy) return CMH_ERR_ARG;
+    if (!m->partitioned) return CMH_ERR_STATE;
+    double s[2];
+    CK(cudaMemcpyAsync(s, m->d.shift, sizeof(s), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    *sx = s[0];
+    *sy = s[1];
+    return CMH_OK;
+}
+
+namespace {
+struct CkptHeader {
+    uint64_t magic;
+    int32_t version, shift_mode;
+    cmh_params p;
+    int64_t n_st, n_samp, sweeps, n_events;
+    double L, sx, sy, logp;
+    uint64_t stats[kStats];
+    int32_t partitioned, pad;
+};
+}  // namespace
+
+int cmh_checkpoint(cmh_model* m, void* buf, size_t* len) {
+    if (!m || !len) return CMH_ERR_ARG;
+    CK(cudaStreamSynchronize(m->stream));
+    int rc = check_status(m);
+    if (rc) return rc;
+    int n = (int)m->n0;
+    if (m->partitioned) {
+        rc = flatten_current(m, &n);
+        if (rc) return rc;
+    }
+    const size_t need = sizeof(CkptHeader) + (size_t)n * (4 * sizeof(double) + sizeof(uint64_t));
+    if (!buf) { *len = need; return CMH_OK; }
+    if (*len < need) { *len = need; return CMH_ERR_ARG; }
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.magic = kCkptMagic;
+    h.version = kCkptVersion;
+    h.shift_mode = m->shift_mode;
+    h.p = m->p;
+    h.n_st = m->g.n_st;
+    h.n_samp = m->g.n_samp;
+    h.sweeps = m->sweeps;
+    h.n_events = n;
+    h.L = m->grid_L;
+    h.sx = m->sx0;
+    h.sy = m->sy0;
+    h.partitioned = m->partitioned;
+    CK(cudaMemcpy(&h.logp, m->d.logp, sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(h.stats, m->d.stats, sizeof(h.stats), cudaMemcpyDeviceToHost));
+    unsigned char* q = (unsigned char*)buf;
+    std::memcpy(q, &h, sizeof(h));
+    q += sizeof(h);
+    if (n) {
+        CK(cudaMemcpy(q, m->flat.x, sizeof(double) * n, cudaMemcpyDeviceToHost)); q += sizeof(double) * n;
+        CK(cudaMemcpy(q, m->flat.y, sizeof(double) * n, cudaMemcpyDeviceToHost)); q += sizeof(double) * n;
+        CK(cudaMemcpy(q, m->flat.t, sizeof(double) * n, cudaMemcpyDeviceToHost)); q += sizeof(double) * n;
+        CK(cudaMemcpy(q, m->flat.m, sizeof(double) * n, cudaMemcpyDeviceToHost)); q += sizeof(double) * n;
+        CK(cudaMemcpy(q, m->flat.id, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
+    }
+    *len = need;
+    return CMH_OK;
+}
+
+int cmh_restore(cmh_model* m, const void* buf, size_t len) {
+    if (!m || !buf || len < sizeof(CkptHeader)) return CMH_ERR_ARG;
+    CkptHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != kCkptMagic || h.version != kCkptVersion) return CMH_ERR_ARG;
+    if (h.n_st != m->g.n_st || h.n_samp != m->g.n_samp || h.n_events < 0 || h.n_events > m->flat_cap ||
+        h.p.dtype != m->p.dtype || h.p.seed != m->p.seed)
+        return CMH_ERR_ARG;
+    const size_t need = sizeof(CkptHeader) + (size_t)h.n_events * (4 * sizeof(double) + sizeof(uint64_t));
+    if (len < need) return CMH_ERR_ARG;
+    CK(cudaStreamSynchronize(m->stream));
+    const int n = (int)h.n_events;
+    const unsigned char* q = (const unsigned char*)buf + sizeof(h);
+    const double* x = (const double*)q;
+    const double* y = x + n;
+    const double* t = y + n;
+    const double* mm = t + n;
+    for (int i = 0; i < n; ++i)
+        if (!(x[i] >= 0.0 && x[i] < m->p.W && y[i] >= 0.0 && y[i] < m->p.W && t[i] >= 0.0 && t[i] < m->p.T &&
+              mm[i] >= 2.0))
+            return CMH_ERR_ARG;
+    CK(cudaMemcpy(m->flat.x, x, sizeof(double) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->flat.y, y, sizeof(double) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->flat.t, t, sizeof(double) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->flat.m, mm, sizeof(double) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->flat.id, mm + n, sizeof(uint64_t) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->flat.n, &n, sizeof(int), cudaMemcpyHostToDevice));
+    double lp = 0.0;
+    int rc = synth_and_logdensity(m, n, &lp);
+    if (rc) return rc;
+    CK(cudaMemcpy(m->d.logp, &h.logp, sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->d.stats, h.stats, sizeof(h.stats), cudaMemcpyHostToDevice));
+    m->latched = 0;
+    CK(cudaMemset(m->d.status, 0, sizeof(int)));
+    m->free_partition();
+    m->partitioned = false;
+    m->sweeps = h.sweeps;
+    m->n0 = n;
+    rc = upload_sweep(m, h.sweeps);
+    if (rc) return rc;
+    if (h.partitioned) {
+        cmh_grid gr{h.L};
+        // the flat list already holds the events: partition bins it
+        rc = cmh_partition_and_color(m, &gr, h.shift_mode, h.sx, h.sy, nullptr);
+        if (rc) return rc;
+    }
+    return CMH_OK;
+}
+
+void cmh_destroy(cmh_model* m) {
+    if (!m) return;
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    m->free_partition();
+    for (void* q : m->allocs) cudaFree(q);
+    m->allocs.clear();
+    if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+    delete m;
+}
+
+int cmh_philox4x64(const uint64_t* ctr, const uint64_t* key, uint64_t* out, int64_t n) {
+    if (n < 0 || (n > 0 && (!ctr || !key || !out))) return CMH_ERR_ARG;
+    if (n == 0) return CMH_OK;
+    unsigned long long *dc = nullptr, *dk = nullptr, *dout = nullptr;
+    cudaError_t e = cudaMalloc(&dc, sizeof(uint64_t) * 4 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&dk, sizeof(uint64_t) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, sizeof(uint64_t) * 4 * n);
+    if (e == cudaSuccess) e = cudaMemcpy(dc, ctr, sizeof(uint64_t) * 4 * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dk, key, sizeof(uint64_t) * 2, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_philox_test(dc, dk, dout, n, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, sizeof(uint64_t) * 4 * n, cudaMemcpyDeviceToHost);
+    cudaFree(dc);
+    cudaFree(dk);
+    cudaFree(dout);
+    return cuda_err(e);
+}
+
+}  // extern "C"

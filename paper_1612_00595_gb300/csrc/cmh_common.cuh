@@ -1,0 +1,168 @@
+// Internal definitions shared by the chromh CUDA translation units.
+//
+// Precision policy:
+//  * event coordinates, the partition and every proposal are float64 and use
+//    explicitly rounded intrinsics (__dadd_rn, __dmul_rn, __ddiv_rn,
+//    __dsqrt_rn) where a result decides an integer (a cell, a window start)
+//    or a coordinate, so no fused multiply-add changes them;
+//  * per-sample likelihood terms are float64 (replay mode) or float32 with
+//    compensated sums (throughput mode);
+//  * the log acceptance ratio and the running log-density are float64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "chromh.h"
+
+namespace cmh {
+
+constexpr int kMaxColours = 16;
+constexpr int kMaxK = 4095;
+constexpr int kStats = 11;   // proposed[3], evaluated[3], accepted[3], priced samples, rewritten samples
+
+// model, partition and launch constants; passed by value to every kernel
+struct Geo {
+    double W, T, Lambda, v, alpha, beta_att, tau, noise_var, f_hz, R_max, L;
+    double p_birth, p_death, sig_xy, sig_t, sig_m;
+    // logs computed once on the host
+    double log_pb, log_pd, log_Lambda, log_WWT, log_T;
+    int n_w, k, commit, shift_mode;
+    double sx_static, sy_static;
+    int ncx, ncy, n_cells, period, n_colours, max_rpc;
+    int n_st;
+    long long n_samp, pitch;
+    unsigned long long seed;
+    int ev_cap, blk_cap, frz_cap, arr_cap;
+    long long store_cap, max_events;
+    int f32;
+    int threads;
+};
+
+// one event store (structure of arrays) with per-cell slices
+struct Store {
+    double *x, *y, *t, *m;
+    unsigned long long* id;
+    int *start, *count, *cap;   // [n_cells]
+    int* total;                 // number of events
+};
+
+struct Dev {
+    Store st[2];                // sweep s works on st[s & 1]
+    long long* sweep;           // device sweep counter
+    double* shift;              // [2] current (sx, sy)
+    int* colour_count;          // [n_colours]
+    int* colour_cells;          // [n_colours][max_rpc]
+    int* fill;                  // [n_cells] scratch
+    double* region_dlp;         // [n_cells] log-density change of the current sweep
+    double* logp;               // running log-density
+    int* status;                // latched CMH_ERR_* (0 = fine)
+    unsigned long long* stats;  // [kStats]
+    cmh_trace* trace;
+    long long trace_cap, trace_sweep0;
+    const void* sig;            // [n_st][pitch] float or double
+    void* V;                    // [n_st][pitch] predicted variance
+    const double* stx;
+    const double* sty;
+    const double* log_n;        // [ev_cap + 2] log(n) table, computed on the host
+};
+
+// --------------------------------------------------------------------------
+// Philox4x64-10 (Salmon et al., SC'11): ten rounds of two 64x64->128-bit
+// products with the multipliers below, xor with the odd words and the key,
+// key bumped by the Weyl increments.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x64(unsigned long long c[4], unsigned long long k0,
+                                           unsigned long long k1) {
+    const unsigned long long M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const unsigned long long W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        unsigned long long hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+        unsigned long long hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+        unsigned long long n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+}
+
+// uniform doubles from the top 53 bits: [0,1) and (0,1]
+__device__ __forceinline__ double u01(unsigned long long w) {
+    return __dmul_rn((double)(w >> 11), 1.0 / 9007199254740992.0);
+}
+__device__ __forceinline__ double u01o(unsigned long long w) {
+    return __dmul_rn((double)((w >> 11) + 1ULL), 1.0 / 9007199254740992.0);
+}
+// uniform integer in [0, n) from the low 32 bits
+__device__ __forceinline__ int pick32(unsigned long long w, int n) {
+    return (int)(((w & 0xffffffffULL) * (unsigned long long)n) >> 32);
+}
+
+// cell index along one axis: floor((x - s) / L) + 1
+__device__ __forceinline__ int cell_axis(double x, double s, double L) {
+    return (int)floor(__ddiv_rn(__dsub_rn(x, s), L)) + 1;
+}
+
+__device__ __forceinline__ int cell_of(const Geo& g, double sx, double sy, double x, double y) {
+    int ix = cell_axis(x, sx, g.L), iy = cell_axis(y, sy, g.L);
+    if (ix < 0 || ix >= g.ncx || iy < 0 || iy >= g.ncy) return -1;
+    return iy * g.ncx + ix;
+}
+
+// [x0, x1) x [y0, y1) of a cell, clipped to the domain
+__device__ __forceinline__ void cell_rect(const Geo& g, double sx, double sy, int cell, double r[4]) {
+    int ix = cell % g.ncx, iy = cell / g.ncx;
+    double x0 = __dadd_rn(sx, __dmul_rn((double)(ix - 1), g.L));
+    double x1 = __dadd_rn(sx, __dmul_rn((double)ix, g.L));
+    double y0 = __dadd_rn(sy, __dmul_rn((double)(iy - 1), g.L));
+    double y1 = __dadd_rn(sy, __dmul_rn((double)iy, g.L));
+    r[0] = x0 < 0.0 ? 0.0 : x0;
+    r[1] = x1 > g.W ? g.W : x1;
+    r[2] = y0 < 0.0 ? 0.0 : y0;
+    r[3] = y1 > g.W ? g.W : y1;
+}
+
+__device__ __forceinline__ double dist_rn(double x, double y, double xs, double ys) {
+    double dx = __dsub_rn(x, xs), dy = __dsub_rn(y, ys);
+    return __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+}
+
+// the shift of one sweep: Philox stream 1 at counter (sweep, 0, 0, 0)
+__device__ __forceinline__ void sweep_shift(const Geo& g, long long sweep, double* sx, double* sy) {
+    if (g.shift_mode == 1) {
+        unsigned long long c[4] = {(unsigned long long)sweep, 0ULL, 0ULL, 0ULL};
+        philox4x64(c, g.seed, 1ULL);
+        *sx = __dmul_rn(u01(c[0]), g.L);
+        *sy = __dmul_rn(u01(c[1]), g.L);
+    } else {
+        *sx = g.sx_static;
+        *sy = g.sy_static;
+    }
+}
+
+__device__ __forceinline__ void latch(int* status, int code) { atomicCAS(status, 0, code); }
+
+// a flat event list in device memory (canonical order)
+struct FlatList {
+    double *x, *y, *t, *m;
+    unsigned long long* id;
+    int* n;
+};
+
+// host-side launchers (defined in the .cu files)
+cudaError_t launch_rebin(const Geo& g, const Dev& d, int init_n, cudaStream_t s, int* launches);
+cudaError_t launch_phase(const Geo& g, const Dev& d, int colour, cudaStream_t s);
+cudaError_t launch_sweep_end(const Geo& g, const Dev& d, cudaStream_t s);
+size_t phase_smem_bytes(const Geo& g);
+cudaError_t launch_vsynth(const Geo& g, const Dev& d, const FlatList& f, cudaStream_t s, int* launches);
+cudaError_t launch_flatten(const Geo& g, const Dev& d, int buf, const FlatList& f, cudaStream_t s, int* launches);
+cudaError_t prepare_kernels(const Geo& g);
+cudaError_t launch_loglik(const Geo& g, const Dev& d, double* partial, int n_part, cudaStream_t s);
+cudaError_t launch_convert_signals(const void* src, int src_f32, long long src_pitch, void* dst,
+                                   int dst_f32, long long dst_pitch, int n_st, long long n_samp,
+                                   int* nonfinite, cudaStream_t s);
+cudaError_t launch_philox_test(const unsigned long long* ctr, const unsigned long long* key,
+                               unsigned long long* out, long long n, cudaStream_t s);
+
+}  // namespace cmh

@@ -1,0 +1,989 @@
+// Colour-phase kernel of chromatic Metropolis-Hastings (Algorithm "Chromatic
+// MH with Static Coloring": for one colour, every region of that colour runs
+// k MH steps in parallel with all other regions fixed), plus the predicted-
+// variance synthesis and the log-density reduction.
+//
+// One CTA per region of the active colour.  Within a CTA:
+//   * warp 0 is the control warp: it decodes each step's proposal (birth,
+//     death, Gaussian move; §Generative Model of Seismic Signals, the MH
+//     moves), finds the stations the proposal reaches and makes the float64
+//     accept decision (MH rule, §Background);
+//   * all warps price the proposal: the change of the Gaussian
+//     log-likelihood over the samples whose variance changes (§Generative
+//     Model: zero-mean diagonal Gaussian with variance = noise + arriving
+//     signals' variances), reduced with warp shuffles;
+//   * on accept all warps re-synthesise the predicted variance V over the
+//     touched windows from the arrivals that cover them.
+// Same-colour regions have disjoint Markov blankets (the partition guarantees
+// it), so no two CTAs of a launch touch the same station row of V.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "cmh_common.cuh"
+
+namespace cmh {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr double LOG2E = 1.4426950408889634074;
+
+struct EvArr {          // one arrival of an own event at a blanket station
+    int slot, k0;       // blanket slot, first sample of the window
+    double af, lnA2;    // arrival time x f, 2 (alpha m - beta_att d)
+    float E0;           // log2 of the variance added at sample k0
+    int pad;
+};
+
+struct Arr {            // an arrival in a list (frozen neighbours, others of a task)
+    int k0;
+    float E0;
+    double af, lnA2;
+};
+
+struct Draw {           // state-independent part of one MH step
+    double a[4];        // birth: candidate (x, y, t, m); move: signed offsets
+    double logu;        // log of the accept uniform, (0, 1]
+    unsigned pickw;     // low word for the event pick
+    int type;           // 0 birth, 1 death, 2 move
+    int bvalid;         // birth candidate inside region, time and magnitude range
+    int pad;
+};
+
+struct Task {           // one station whose variance the proposal changes
+    int row, slot, lo, hi;
+    int has_o, has_n, k0o, k0n;
+    float E0o, E0n, rm1f;
+    int oth0;           // others list: [oth0, oth0 + noth) in the pool
+    int noth, pad0;
+    double afo, lnA2o, afn, lnA2n, rm1d;
+};
+
+// shared-memory layout of the phase kernel (host computes the size)
+struct Layout {
+    size_t ev_x, ev_y, ev_t, ev_m, ev_id, ev_narr, ev_arr, order, freel;
+    size_t b_sta, b_x, b_y, f_cnt, f_arr, draws, cand, tasks, pool, total;
+    static constexpr int kMaxTasks = 64;
+    int pool_cap;
+    __host__ __device__ Layout(const Geo& g) {
+        pool_cap = g.ev_cap + g.frz_cap;
+        size_t o = 0;
+        auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 15) & ~size_t(15); return r; };
+        ev_x = take(sizeof(double) * g.ev_cap);
+        ev_y = take(sizeof(double) * g.ev_cap);
+        ev_t = take(sizeof(double) * g.ev_cap);
+        ev_m = take(sizeof(double) * g.ev_cap);
+        ev_id = take(sizeof(unsigned long long) * g.ev_cap);
+        ev_narr = take(sizeof(int) * g.ev_cap);
+        ev_arr = take(sizeof(EvArr) * (size_t)g.ev_cap * g.arr_cap);
+        order = take(sizeof(int) * g.ev_cap);
+        freel = take(sizeof(int) * g.ev_cap);
+        b_sta = take(sizeof(int) * g.blk_cap);
+        b_x = take(sizeof(double) * g.blk_cap);
+        b_y = take(sizeof(double) * g.blk_cap);
+        f_cnt = take(sizeof(int) * g.blk_cap);
+        f_arr = take(sizeof(Arr) * (size_t)g.blk_cap * g.frz_cap);
+        draws = take(sizeof(Draw) * g.k);
+        cand = take(sizeof(EvArr) * g.arr_cap);
+        tasks = take(sizeof(Task) * kMaxTasks);
+        pool = take(sizeof(Arr) * (size_t)pool_cap);
+        total = o;
+    }
+};
+
+__device__ __forceinline__ bool arrival(const Geo& g, double x, double y, double t, double m, double xs,
+                                        double ys, int& k0, double& af, double& lnA2) {
+    const double dd = dist_rn(x, y, xs, ys);
+    if (!(dd < g.R_max)) return false;
+    const double a = __dadd_rn(t, __ddiv_rn(dd, g.v));
+    af = __dmul_rn(a, g.f_hz);
+    k0 = (int)ceil(af);
+    lnA2 = 2.0 * (g.alpha * m - g.beta_att * dd);
+    return true;
+}
+
+// log2 of the variance an arrival adds at its first sample k0
+__device__ __forceinline__ float arr_E0(const Geo& g, int k0, double af, double lnA2) {
+    const double twof_tau = 2.0 / (g.f_hz * g.tau);
+    return (float)(LOG2E * (lnA2 - ((double)k0 - af) * twof_tau));
+}
+
+// variance added at sample k by an arrival (float64 form)
+__device__ __forceinline__ double arr_c64(const Geo& g, double af, double lnA2, int k) {
+    return exp(lnA2 - ((double)k - af) * (2.0 / (g.f_hz * g.tau)));
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// float-float (hi, lo) sum of two pairs (TwoSum on the high parts)
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    const float e = (a.x - (s - bb)) + (b.x - bb);
+    const float lo = a.y + b.y + e;
+    const float hi = s + lo;
+    return make_float2(hi, lo - (hi - s));
+}
+
+// ordered append across the block: returns the position of this thread's
+// element among the flagged ones of this round; *total (shared) is advanced
+__device__ __forceinline__ int block_append(bool flag, int* s_warp, int* s_base) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned bal = __ballot_sync(FULL, flag);
+    if (lane == 0) s_warp[wid] = __popc(bal);
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int w = 0; w < nw; ++w) {
+        const int c = s_warp[w];
+        if (w < wid) before += c;
+        all += c;
+    }
+    const int pos = *s_base + before + __popc(bal & ((1u << lane) - 1));
+    __syncthreads();
+    if (threadIdx.x == 0) *s_base += all;
+    __syncthreads();
+    return pos;
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
+    if (*d.status) return;
+    const long long sweep = *d.sweep;
+    if ((int)blockIdx.x >= d.colour_count[colour]) return;
+    const int cell = d.colour_cells[colour * g.max_rpc + blockIdx.x];
+    const Store S = d.st[sweep & 1];
+    const double sx = d.shift[0], sy = d.shift[1];
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Layout Lo(g);
+    double* ex = (double*)(smem + Lo.ev_x);
+    double* ey = (double*)(smem + Lo.ev_y);
+    double* et = (double*)(smem + Lo.ev_t);
+    double* em = (double*)(smem + Lo.ev_m);
+    unsigned long long* eid = (unsigned long long*)(smem + Lo.ev_id);
+    int* enarr = (int*)(smem + Lo.ev_narr);
+    EvArr* earr = (EvArr*)(smem + Lo.ev_arr);
+    int* order = (int*)(smem + Lo.order);
+    int* freel = (int*)(smem + Lo.freel);
+    int* bsta = (int*)(smem + Lo.b_sta);
+    double* bx = (double*)(smem + Lo.b_x);
+    double* by = (double*)(smem + Lo.b_y);
+    int* fcnt = (int*)(smem + Lo.f_cnt);
+    Arr* farr = (Arr*)(smem + Lo.f_arr);
+    Draw* draws = (Draw*)(smem + Lo.draws);
+    EvArr* cand = (EvArr*)(smem + Lo.cand);
+    Task* tasks = (Task*)(smem + Lo.tasks);
+    Arr* pool = (Arr*)(smem + Lo.pool);
+
+    __shared__ double s_rect[4];
+    __shared__ double s_log_area, s_dll, s_region_dlp;
+    __shared__ double s_c[4];
+    __shared__ int s_n_own, s_n_free, s_n_blk, s_err, s_valid, s_idx, s_type, s_ncand, s_ntask, s_acc;
+    __shared__ int s_warp[32], s_base;
+    __shared__ float2 s_redf[32];
+    __shared__ double s_redd[32];
+
+    const int start = S.start[cell], n0 = S.count[cell];
+    if (tid == 0) {
+        cell_rect(g, sx, sy, cell, s_rect);
+        s_log_area = log(__dmul_rn(__dsub_rn(s_rect[1], s_rect[0]), __dsub_rn(s_rect[3], s_rect[2])));
+        s_err = (n0 + g.k > g.ev_cap) ? CMH_ERR_CAPACITY : 0;
+        s_n_own = n0;
+        s_n_free = g.ev_cap - n0;
+        s_base = 0;
+        s_region_dlp = 0.0;
+    }
+    __syncthreads();
+    if (s_err) {
+        if (tid == 0) latch(d.status, s_err);
+        return;
+    }
+    // own events (physical slots 0..n0-1, order = identity), free list
+    for (int i = tid; i < g.ev_cap; i += nthr) {
+        if (i < n0) {
+            ex[i] = S.x[start + i];
+            ey[i] = S.y[start + i];
+            et[i] = S.t[start + i];
+            em[i] = S.m[start + i];
+            eid[i] = S.id[start + i];
+            order[i] = i;
+        } else {
+            freel[g.ev_cap - 1 - i] = i;  // pop from the top gives the lowest slot first
+        }
+    }
+    // blanket: stations within R_max of the region (float32 test with a margin;
+    // a superset is harmless, every reach test below is exact float64)
+    {
+        const float r0 = (float)s_rect[0], r1 = (float)s_rect[1], r2 = (float)s_rect[2], r3 = (float)s_rect[3];
+        const float Rm = (float)g.R_max * 1.0001f + 1e-3f;
+        for (int base = 0; base < g.n_st; base += nthr) {
+            const int j = base + tid;
+            bool in = false;
+            double xs = 0.0, ys = 0.0;
+            if (j < g.n_st) {
+                xs = d.stx[j];
+                ys = d.sty[j];
+                const float fx = (float)xs, fy = (float)ys;
+                const float dx = fx < r0 ? r0 - fx : (fx > r1 ? fx - r1 : 0.f);
+                const float dy = fy < r2 ? r2 - fy : (fy > r3 ? fy - r3 : 0.f);
+                in = dx * dx + dy * dy < Rm * Rm;
+            }
+            const int pos = block_append(in, s_warp, &s_base);
+            if (in) {
+                if (pos < g.blk_cap) {
+                    bsta[pos] = j;
+                    bx[pos] = xs;
+                    by[pos] = ys;
+                } else {
+                    atomicCAS(&s_err, 0, CMH_ERR_CAPACITY);
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) s_n_blk = min(s_base, g.blk_cap);
+        __syncthreads();
+    }
+    const int n_blk = s_n_blk;
+    // arrival cache of the own events
+    for (int i = tid; i < n0; i += nthr) {
+        int na = 0;
+        for (int b = 0; b < n_blk; ++b) {
+            int k0;
+            double af, lnA2;
+            if (arrival(g, ex[i], ey[i], et[i], em[i], bx[b], by[b], k0, af, lnA2)) {
+                if (na < g.arr_cap) {
+                    EvArr& A = earr[i * g.arr_cap + na];
+                    A.slot = b; A.k0 = k0; A.af = af; A.lnA2 = lnA2; A.E0 = arr_E0(g, k0, af, lnA2);
+                }
+                ++na;
+            }
+        }
+        if (na > g.arr_cap) atomicCAS(&s_err, 0, CMH_ERR_CAPACITY);
+        enarr[i] = na;
+    }
+    // frozen arrivals: events of the neighbouring cells (other colours) that
+    // reach each blanket station, in (cell, id) order
+    for (int b = tid; b < n_blk; b += nthr) {
+        const int ix = cell % g.ncx, iy = cell / g.ncx, P1 = g.period - 1;
+        int nf = 0;
+        for (int jy = iy - P1; jy <= iy + P1; ++jy) {
+            if (jy < 0 || jy >= g.ncy) continue;
+            for (int jx = ix - P1; jx <= ix + P1; ++jx) {
+                if (jx < 0 || jx >= g.ncx) continue;
+                const int oc = jy * g.ncx + jx;
+                if (oc == cell) continue;
+                const int s0 = S.start[oc], n = S.count[oc];
+                for (int i = 0; i < n; ++i) {
+                    int k0;
+                    double af, lnA2;
+                    if (arrival(g, S.x[s0 + i], S.y[s0 + i], S.t[s0 + i], S.m[s0 + i], bx[b], by[b], k0, af, lnA2)) {
+                        if (nf < g.frz_cap) {
+                            Arr& A = farr[b * g.frz_cap + nf];
+                            A.k0 = k0; A.af = af; A.lnA2 = lnA2; A.E0 = arr_E0(g, k0, af, lnA2);
+                        }
+                        ++nf;
+                    }
+                }
+            }
+        }
+        if (nf > g.frz_cap) atomicCAS(&s_err, 0, CMH_ERR_CAPACITY);
+        fcnt[b] = min(nf, g.frz_cap);
+    }
+    // the k steps' random draws and their state-independent decoding
+    for (int st = tid; st < g.k; st += nthr) {
+        unsigned long long w[8];
+        unsigned long long c0[4] = {(unsigned long long)sweep, (unsigned long long)cell, (unsigned long long)st, 0ULL};
+        philox4x64(c0, g.seed, 0ULL);
+        unsigned long long c1[4] = {(unsigned long long)sweep, (unsigned long long)cell, (unsigned long long)st, 1ULL};
+        philox4x64(c1, g.seed, 0ULL);
+        for (int i = 0; i < 4; ++i) { w[i] = c0[i]; w[4 + i] = c1[i]; }
+        Draw D;
+        const double u = u01(w[0]);
+        D.type = u < g.p_birth ? 0 : (u < __dadd_rn(g.p_birth, g.p_death) ? 1 : 2);
+        D.pickw = (unsigned)(w[1] & 0xffffffffULL);
+        D.logu = log(u01o(w[6]));
+        D.bvalid = 0;
+        if (D.type == 0) {
+            const double x = __dadd_rn(s_rect[0], __dmul_rn(u01(w[2]), __dsub_rn(s_rect[1], s_rect[0])));
+            const double y = __dadd_rn(s_rect[2], __dmul_rn(u01(w[3]), __dsub_rn(s_rect[3], s_rect[2])));
+            const double t = __dmul_rn(u01(w[4]), g.T);
+            const double m = __dsub_rn(2.0, log(u01o(w[5])));
+            D.a[0] = x; D.a[1] = y; D.a[2] = t; D.a[3] = m;
+            D.bvalid = x >= 0.0 && x < g.W && y >= 0.0 && y < g.W && cell_of(g, sx, sy, x, y) == cell &&
+                       t >= 0.0 && t < g.T && m >= 2.0;
+        } else if (D.type == 2) {
+            const double r1 = __dsqrt_rn(__dmul_rn(-2.0, log(u01o(w[2]))));
+            const double th1 = __dmul_rn(6.283185307179586, u01(w[3]));
+            const double r2 = __dsqrt_rn(__dmul_rn(-2.0, log(u01o(w[4]))));
+            const double th2 = __dmul_rn(6.283185307179586, u01(w[5]));
+            double z[4] = {__dmul_rn(r1, cos(th1)), __dmul_rn(r1, sin(th1)), __dmul_rn(r2, cos(th2)),
+                           __dmul_rn(r2, sin(th2))};
+            const double sig[4] = {g.sig_xy, g.sig_xy, g.sig_t, g.sig_m};
+            for (int i = 0; i < 4; ++i) {
+                double q = __dmul_rn(rint(__dmul_rn(fabs(z[i]), 1048576.0)), 1.0 / 1048576.0);
+                if ((w[1] >> (32 + i)) & 1ULL) q = -q;
+                D.a[i] = __dmul_rn(sig[i], q);
+            }
+        } else {
+            D.a[0] = D.a[1] = D.a[2] = D.a[3] = 0.0;
+        }
+        draws[st] = D;
+    }
+    __syncthreads();
+    if (s_err) {
+        if (tid == 0) latch(d.status, s_err);
+        return;
+    }
+
+    const float kap = (float)(2.0 * LOG2E / (g.f_hz * g.tau));
+    const float noise_f = (float)g.noise_var;
+    unsigned long long n_prop[3] = {0, 0, 0}, n_eval[3] = {0, 0, 0}, n_acc[3] = {0, 0, 0};
+    unsigned long long n_priced = 0, n_rewritten = 0;   // sample terms (thread 0's tally)
+
+    for (int step = 0; step < g.k; ++step) {
+        // ---------------- control: decode, reach, tasks (warp 0) ----------------
+        if (wid == 0) {
+            const Draw dr = draws[step];
+            const int n_own = s_n_own;
+            int valid = 0, idx = -1, ncand = 0;
+            double cx = 0.0, cy = 0.0, ct = 0.0, cm = 0.0;
+            if (dr.type == 0) {
+                valid = dr.bvalid;
+                cx = dr.a[0]; cy = dr.a[1]; ct = dr.a[2]; cm = dr.a[3];
+            } else if (n_own > 0) {
+                idx = pick32(dr.pickw, n_own);
+                if (dr.type == 1) {
+                    valid = 1;
+                } else {
+                    const int ps = order[idx];
+                    cx = __dadd_rn(ex[ps], dr.a[0]);
+                    cy = __dadd_rn(ey[ps], dr.a[1]);
+                    ct = __dadd_rn(et[ps], dr.a[2]);
+                    cm = __dadd_rn(em[ps], dr.a[3]);
+                    valid = cx >= 0.0 && cx < g.W && cy >= 0.0 && cy < g.W &&
+                            cell_of(g, sx, sy, cx, cy) == cell && ct >= 0.0 && ct < g.T && cm >= 2.0;
+                }
+            }
+            if (valid && dr.type != 1) {
+                for (int b0 = 0; b0 < n_blk; b0 += 32) {
+                    const int b = b0 + lane;
+                    int k0 = 0;
+                    double af = 0.0, lnA2 = 0.0;
+                    const bool r = b < n_blk && arrival(g, cx, cy, ct, cm, bx[b], by[b], k0, af, lnA2);
+                    const unsigned bal = __ballot_sync(FULL, r);
+                    const int pos = ncand + __popc(bal & ((1u << lane) - 1));
+                    if (r && pos < g.arr_cap) {
+                        EvArr& A = cand[pos];
+                        A.slot = b; A.k0 = k0; A.af = af; A.lnA2 = lnA2; A.E0 = arr_E0(g, k0, af, lnA2);
+                    }
+                    ncand += __popc(bal);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                int err = ncand > g.arr_cap ? CMH_ERR_CAPACITY : 0;
+                int nt = 0, npool = 0;
+                if (valid && !err) {
+                    // merge the old event's arrivals and the candidate's, by slot
+                    const int ps = idx >= 0 ? order[idx] : -1;
+                    const EvArr* oa = ps >= 0 && dr.type != 0 ? earr + ps * g.arr_cap : nullptr;
+                    const int no = oa ? enarr[ps] : 0;
+                    const int nn = dr.type != 1 ? ncand : 0;
+                    int io = 0, in = 0;
+                    while ((io < no || in < nn) && !err) {
+                        const int so = io < no ? oa[io].slot : 1 << 30;
+                        const int sn = in < nn ? cand[in].slot : 1 << 30;
+                        if (nt >= Layout::kMaxTasks) { err = CMH_ERR_CAPACITY; break; }
+                        Task& T = tasks[nt];
+                        T.slot = so < sn ? so : sn;
+                        T.row = bsta[T.slot];
+                        T.has_o = so <= sn;
+                        T.has_n = sn <= so;
+                        long long lo = 1LL << 40, hi = -1;
+                        if (T.has_o) {
+                            const EvArr& A = oa[io++];
+                            T.k0o = A.k0; T.afo = A.af; T.lnA2o = A.lnA2; T.E0o = A.E0;
+                            lo = min(lo, (long long)A.k0);
+                            hi = max(hi, (long long)A.k0 + g.n_w);
+                        }
+                        if (T.has_n) {
+                            const EvArr& A = cand[in++];
+                            T.k0n = A.k0; T.afn = A.af; T.lnA2n = A.lnA2; T.E0n = A.E0;
+                            lo = min(lo, (long long)A.k0);
+                            hi = max(hi, (long long)A.k0 + g.n_w);
+                        }
+                        if (T.has_o && T.has_n) {
+                            // c_new / c_old is constant over the overlap of the two windows
+                            T.rm1d = expm1((T.lnA2n - T.lnA2o) + (T.afo - T.afn) * (-2.0 / (g.f_hz * g.tau)));
+                            T.rm1f = (float)T.rm1d;
+                        } else {
+                            T.rm1d = 0.0;
+                            T.rm1f = 0.f;
+                        }
+                        if (lo < 0) lo = 0;
+                        if (hi > g.n_samp) hi = g.n_samp;
+                        T.lo = (int)lo;
+                        T.hi = (int)hi;
+                        if (lo >= hi) continue;  // window entirely after the record
+                        // the other arrivals covering [lo, hi) at this station:
+                        // own events except the changed one, then frozen neighbours
+                        T.oth0 = npool;
+                        const int n_own2 = s_n_own;
+                        for (int q = 0; q < n_own2 && !err; ++q) {
+                            const int p2 = order[q];
+                            if (p2 == ps) continue;
+                            for (int a = 0; a < enarr[p2]; ++a) {
+                                const EvArr& A = earr[p2 * g.arr_cap + a];
+                                if (A.slot != T.slot) continue;
+                                if (A.k0 + g.n_w <= lo || A.k0 >= hi) continue;
+                                if (npool >= Lo.pool_cap) { err = CMH_ERR_CAPACITY; break; }
+                                Arr& B = pool[npool++];
+                                B.k0 = A.k0; B.E0 = A.E0; B.af = A.af; B.lnA2 = A.lnA2;
+                            }
+                        }
+                        for (int a = 0; a < fcnt[T.slot] && !err; ++a) {
+                            const Arr& A = farr[T.slot * g.frz_cap + a];
+                            if (A.k0 + g.n_w <= lo || A.k0 >= hi) continue;
+                            if (npool >= Lo.pool_cap) { err = CMH_ERR_CAPACITY; break; }
+                            pool[npool++] = A;
+                        }
+                        T.noth = npool - T.oth0;
+                        ++nt;
+                    }
+                }
+                s_err = err;
+                s_valid = valid;
+                s_idx = idx;
+                s_type = dr.type;
+                s_ncand = ncand;
+                s_ntask = nt;
+                s_c[0] = cx; s_c[1] = cy; s_c[2] = ct; s_c[3] = cm;
+            }
+        }
+        __syncthreads();
+        if (s_err) break;
+        const int valid = s_valid, ntask = s_ntask;
+
+        // ---------------- pricing: all threads ----------------
+        if (valid) {
+            if (F32) {
+                float acc = 0.f, comp = 0.f;
+                for (int ti = 0; ti < ntask; ++ti) {
+                    const Task& T = tasks[ti];
+                    const float* srow = (const float*)d.sig + (size_t)T.row * g.pitch;
+                    const float* vrow = (const float*)d.V + (size_t)T.row * g.pitch;
+                    for (int q = (T.lo >> 2) + tid; (q << 2) < T.hi; q += nthr) {
+                        const int k = q << 2;
+                        const float4 s4 = __ldg(reinterpret_cast<const float4*>(srow + k));
+                        const float4 v4 = *reinterpret_cast<const float4*>(vrow + k);
+                        const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+                        const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int kk = k + e;
+                            const int ro = kk - T.k0o, rn = kk - T.k0n;
+                            const bool io = T.has_o && (unsigned)ro < (unsigned)g.n_w;
+                            const bool inn = T.has_n && (unsigned)rn < (unsigned)g.n_w;
+                            float dd = 0.f;
+                            if (io) {
+                                const float co = exp2f(T.E0o - kap * (float)ro);
+                                dd = inn ? co * T.rm1f : -co;
+                            } else if (inn) {
+                                dd = exp2f(T.E0n - kap * (float)rn);
+                            }
+                            if (kk < T.hi && dd != 0.f) {
+                                const float V = vv[e], s = sv[e];
+                                const float Vp = V + dd;
+                                float term;
+                                if (Vp < 0.5f * V) {
+                                    // the changed arrival dominates V: V + d cancels, so
+                                    // rebuild V' from the arrivals that stay
+                                    float a2 = noise_f, c2 = 0.f;
+                                    for (int o = 0; o < T.noth; ++o) {
+                                        const Arr& A = pool[T.oth0 + o];
+                                        const int r = kk - A.k0;
+                                        if ((unsigned)r < (unsigned)g.n_w) kahan_add(a2, c2, exp2f(A.E0 - kap * (float)r));
+                                    }
+                                    if (inn) kahan_add(a2, c2, exp2f(T.E0n - kap * (float)rn));
+                                    const float Vr = a2 - c2;
+                                    term = logf(Vr / V) + s * s * (1.f / Vr - 1.f / V);
+                                } else {
+                                    term = log1pf(dd / V) - s * s * dd / (V * Vp);
+                                }
+                                kahan_add(acc, comp, -0.5f * term);
+                            }
+                        }
+                    }
+                }
+                float2 v = make_float2(acc, -comp);
+                for (int o = 16; o > 0; o >>= 1) {
+                    float2 w2;
+                    w2.x = __shfl_xor_sync(FULL, v.x, o);
+                    w2.y = __shfl_xor_sync(FULL, v.y, o);
+                    v = ff_add(v, w2);
+                }
+                if (lane == 0) s_redf[wid] = v;
+                __syncthreads();
+                if (tid == 0) {
+                    float2 t = s_redf[0];
+                    for (int w = 1; w < (nthr >> 5); ++w) t = ff_add(t, s_redf[w]);
+                    s_dll = (double)t.x + (double)t.y;
+                }
+            } else {
+                double acc = 0.0;
+                for (int ti = 0; ti < ntask; ++ti) {
+                    const Task& T = tasks[ti];
+                    const double* srow = (const double*)d.sig + (size_t)T.row * g.pitch;
+                    const double* vrow = (const double*)d.V + (size_t)T.row * g.pitch;
+                    for (int kk = T.lo + tid; kk < T.hi; kk += nthr) {
+                        const int ro = kk - T.k0o, rn = kk - T.k0n;
+                        const bool io = T.has_o && (unsigned)ro < (unsigned)g.n_w;
+                        const bool inn = T.has_n && (unsigned)rn < (unsigned)g.n_w;
+                        double dd = 0.0;
+                        if (io) {
+                            const double co = arr_c64(g, T.afo, T.lnA2o, kk);
+                            dd = inn ? co * T.rm1d : -co;
+                        } else if (inn) {
+                            dd = arr_c64(g, T.afn, T.lnA2n, kk);
+                        }
+                        if (dd != 0.0) {
+                            const double V = vrow[kk], s = __ldg(srow + kk);
+                            const double Vp = V + dd;
+                            if (Vp < 0.5 * V) {
+                                double a2 = g.noise_var;
+                                for (int o = 0; o < T.noth; ++o) {
+                                    const Arr& A = pool[T.oth0 + o];
+                                    const int r = kk - A.k0;
+                                    if ((unsigned)r < (unsigned)g.n_w) a2 += arr_c64(g, A.af, A.lnA2, kk);
+                                }
+                                if (inn) a2 += arr_c64(g, T.afn, T.lnA2n, kk);
+                                acc += -0.5 * (log(a2 / V) + s * s * (1.0 / a2 - 1.0 / V));
+                            } else {
+                                acc += -0.5 * (log1p(dd / V) - s * s * dd / (V * Vp));
+                            }
+                        }
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+                if (lane == 0) s_redd[wid] = acc;
+                __syncthreads();
+                if (tid == 0) {
+                    double t = 0.0;
+                    for (int w = 0; w < (nthr >> 5); ++w) t += s_redd[w];
+                    s_dll = t;
+                }
+            }
+        }
+
+        // ---------------- decision (thread 0) ----------------
+        if (tid == 0) {
+            const int type = s_type;
+            const int n_own = s_n_own;
+            const Draw& dr = draws[step];
+            ++n_prop[type];
+            double dll = 0.0, la = -INFINITY, dlp = 0.0;
+            int acc = 0;
+            if (valid) {
+                ++n_eval[type];
+                for (int ti = 0; ti < s_ntask; ++ti) n_priced += (unsigned long long)(tasks[ti].hi - tasks[ti].lo);
+                dll = s_dll;
+                const double cm = s_c[3];
+                if (type == 0) {
+                    const double lb = g.log_Lambda - g.log_WWT - (cm - 2.0);
+                    const double lq = -s_log_area - g.log_T - (cm - 2.0);
+                    dlp = lb;
+                    la = dll + dlp - lq + g.log_pd - d.log_n[n_own + 1] - g.log_pb;
+                } else if (type == 1) {
+                    const double me = em[order[s_idx]];
+                    const double lb = g.log_Lambda - g.log_WWT - (me - 2.0);
+                    const double lq = -s_log_area - g.log_T - (me - 2.0);
+                    dlp = -lb;
+                    la = dll + dlp + lq + g.log_pb - g.log_pd + d.log_n[n_own];
+                } else {
+                    const double me = em[order[s_idx]];
+                    const double lb_new = g.log_Lambda - g.log_WWT - (cm - 2.0);
+                    const double lb_old = g.log_Lambda - g.log_WWT - (me - 2.0);
+                    dlp = lb_new - lb_old;
+                    la = dll + dlp;
+                }
+                acc = dr.logu < la;
+            }
+            if (d.trace) {
+                const long long slot = ((sweep - d.trace_sweep0) * g.n_cells + cell) * (long long)g.k + step;
+                if (slot >= 0 && slot < d.trace_cap) {
+                    cmh_trace& R = d.trace[slot];
+                    R.sweep = (int)sweep; R.cell = cell; R.step = step; R.type = type;
+                    R.evaluated = valid; R.accepted = acc; R.n_before = n_own; R.written = 1;
+                    R.dll = dll; R.log_alpha = la;
+                }
+            }
+            int do_commit = acc && g.commit;
+            if (do_commit) {
+                ++n_acc[type];
+                for (int ti = 0; ti < s_ntask; ++ti) n_rewritten += (unsigned long long)(tasks[ti].hi - tasks[ti].lo);
+                s_region_dlp += dll + dlp;
+                if (type == 0) {
+                    const int ps = freel[--s_n_free];
+                    ex[ps] = s_c[0]; ey[ps] = s_c[1]; et[ps] = s_c[2]; em[ps] = s_c[3];
+                    eid[ps] = ((unsigned long long)(sweep + 1) << 32) | ((unsigned long long)cell << 12) |
+                              (unsigned long long)step;
+                    for (int a = 0; a < s_ncand; ++a) earr[ps * g.arr_cap + a] = cand[a];
+                    enarr[ps] = s_ncand;
+                    order[n_own] = ps;
+                    s_n_own = n_own + 1;
+                } else if (type == 1) {
+                    const int ps = order[s_idx];
+                    for (int q = s_idx; q + 1 < n_own; ++q) order[q] = order[q + 1];
+                    freel[s_n_free++] = ps;
+                    s_n_own = n_own - 1;
+                } else {
+                    const int ps = order[s_idx];
+                    ex[ps] = s_c[0]; ey[ps] = s_c[1]; et[ps] = s_c[2]; em[ps] = s_c[3];
+                    for (int a = 0; a < s_ncand; ++a) earr[ps * g.arr_cap + a] = cand[a];
+                    enarr[ps] = s_ncand;
+                }
+            } else if (acc) {
+                ++n_acc[type];
+            }
+            s_acc = do_commit;
+        }
+        __syncthreads();
+
+        // ---------------- commit: re-synthesise V over the touched windows ----------------
+        if (s_acc) {
+            const int type = s_type;
+            for (int ti = 0; ti < ntask; ++ti) {
+                const Task& T = tasks[ti];
+                const bool has_new = type != 1 && T.has_n;
+                if (F32) {
+                    float* vrow = (float*)d.V + (size_t)T.row * g.pitch;
+                    for (int kk = T.lo + tid; kk < T.hi; kk += nthr) {
+                        float a2 = noise_f, c2 = 0.f;
+                        for (int o = 0; o < T.noth; ++o) {
+                            const Arr& A = pool[T.oth0 + o];
+                            const int r = kk - A.k0;
+                            if ((unsigned)r < (unsigned)g.n_w) kahan_add(a2, c2, exp2f(A.E0 - kap * (float)r));
+                        }
+                        if (has_new) {
+                            const int r = kk - T.k0n;
+                            if ((unsigned)r < (unsigned)g.n_w) kahan_add(a2, c2, exp2f(T.E0n - kap * (float)r));
+                        }
+                        vrow[kk] = a2 - c2;
+                    }
+                } else {
+                    double* vrow = (double*)d.V + (size_t)T.row * g.pitch;
+                    for (int kk = T.lo + tid; kk < T.hi; kk += nthr) {
+                        double a2 = g.noise_var;
+                        for (int o = 0; o < T.noth; ++o) {
+                            const Arr& A = pool[T.oth0 + o];
+                            const int r = kk - A.k0;
+                            if ((unsigned)r < (unsigned)g.n_w) a2 += arr_c64(g, A.af, A.lnA2, kk);
+                        }
+                        if (has_new) {
+                            const int r = kk - T.k0n;
+                            if ((unsigned)r < (unsigned)g.n_w) a2 += arr_c64(g, T.afn, T.lnA2n, kk);
+                        }
+                        vrow[kk] = a2;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    if (s_err) {
+        if (tid == 0) latch(d.status, s_err);
+        return;
+    }
+    // write the region's events back in order (ids stay sorted)
+    const int n_fin = s_n_own;
+    for (int i = tid; i < n_fin; i += nthr) {
+        const int ps = order[i];
+        S.x[start + i] = ex[ps];
+        S.y[start + i] = ey[ps];
+        S.t[start + i] = et[ps];
+        S.m[start + i] = em[ps];
+        S.id[start + i] = eid[ps];
+    }
+    if (tid == 0) {
+        S.count[cell] = n_fin;
+        d.region_dlp[cell] = s_region_dlp;
+        for (int t = 0; t < 3; ++t) {
+            if (n_prop[t]) atomicAdd(&d.stats[t], n_prop[t]);
+            if (n_eval[t]) atomicAdd(&d.stats[3 + t], n_eval[t]);
+            if (n_acc[t]) atomicAdd(&d.stats[6 + t], n_acc[t]);
+        }
+        if (n_priced) atomicAdd(&d.stats[9], n_priced);
+        if (n_rewritten) atomicAdd(&d.stats[10], n_rewritten);
+    }
+}
+
+__global__ void sweep_end(Geo g, Dev d) {
+    if (*d.status) return;
+    __shared__ double s_part[32];
+    double acc = 0.0;
+    // fixed assignment and fixed tree: the sum does not depend on scheduling
+    for (int c = threadIdx.x; c < g.n_cells; c += blockDim.x) {
+        acc += d.region_dlp[c];
+        d.region_dlp[c] = 0.0;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w];
+        *d.logp += t;
+        *d.sweep += 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// predicted-variance synthesis: V_j[k] = noise + sum of the variances of the
+// arrivals covering sample k, for every station (one block per station).
+// Events come from a flat list (fx, fy, ft, fm)[0, *n) in canonical order;
+// arrivals are gathered in list order, kSynthArr per pass, and applied tile
+// by tile in that order, so the result does not depend on scheduling.
+// ---------------------------------------------------------------------------
+constexpr int kSynthThreads = 256;
+constexpr int kSynthArr = 512;
+constexpr int kSynthTile = kSynthThreads * 8;
+
+template <bool F32>
+__global__ void __launch_bounds__(kSynthThreads) vsynth_kernel(Geo g, Dev d, const double* fx, const double* fy,
+                                                               const double* ft, const double* fm, const int* n_ptr) {
+    const int j = blockIdx.x;
+    const int n = *n_ptr;
+    const double xs = d.stx[j], ys = d.sty[j];
+    __shared__ int s_k0[kSynthArr];
+    __shared__ double s_af[kSynthArr], s_ln[kSynthArr];
+    __shared__ int s_tl[kSynthArr];
+    __shared__ int s_warp[32], s_base, s_cnt, s_nt;
+    const float kap = (float)(2.0 * LOG2E / (g.f_hz * g.tau));
+    int base = 0;
+    bool first = true;
+    while (true) {
+        if (threadIdx.x == 0) s_base = 0;
+        __syncthreads();
+        while (base < n) {
+            const int idx = base + threadIdx.x;
+            int k0 = 0;
+            double af = 0.0, ln = 0.0;
+            const bool r = idx < n && arrival(g, fx[idx], fy[idx], ft[idx], fm[idx], xs, ys, k0, af, ln);
+            if (threadIdx.x == 0) s_cnt = 0;
+            __syncthreads();
+            if (r) atomicAdd(&s_cnt, 1);
+            __syncthreads();
+            if (s_base + s_cnt > kSynthArr) break;   // full: apply, then resume here
+            const int pos = block_append(r, s_warp, &s_base);
+            if (r) {
+                s_k0[pos] = k0;
+                s_af[pos] = af;
+                s_ln[pos] = ln;
+            }
+            base += blockDim.x;
+        }
+        __syncthreads();
+        const int na = s_base;
+        for (long long t0 = 0; t0 < g.n_samp; t0 += kSynthTile) {
+            const long long t1 = min((long long)g.n_samp, t0 + kSynthTile);
+            if (threadIdx.x == 0) s_nt = 0;
+            __syncthreads();
+            for (int a0 = 0; a0 < na; a0 += blockDim.x) {
+                const int a = a0 + threadIdx.x;
+                const bool hit = a < na && s_k0[a] < t1 && (long long)s_k0[a] + g.n_w > t0;
+                const int pos = block_append(hit, s_warp, &s_nt);
+                if (hit) s_tl[pos] = a;
+            }
+            const int nt = s_nt;
+            for (long long k = t0 + threadIdx.x; k < t1; k += blockDim.x) {
+                if (F32) {
+                    float* vrow = (float*)d.V + (size_t)j * g.pitch;
+                    float a2 = first ? (float)g.noise_var : vrow[k], c2 = 0.f;
+                    for (int q = 0; q < nt; ++q) {
+                        const int a = s_tl[q];
+                        const int r = (int)(k - s_k0[a]);
+                        if ((unsigned)r < (unsigned)g.n_w)
+                            kahan_add(a2, c2, exp2f(arr_E0(g, s_k0[a], s_af[a], s_ln[a]) - kap * (float)r));
+                    }
+                    vrow[k] = a2 - c2;
+                } else {
+                    double* vrow = (double*)d.V + (size_t)j * g.pitch;
+                    double a2 = first ? g.noise_var : vrow[k];
+                    for (int q = 0; q < nt; ++q) {
+                        const int a = s_tl[q];
+                        const int r = (int)(k - s_k0[a]);
+                        if ((unsigned)r < (unsigned)g.n_w) a2 += arr_c64(g, s_af[a], s_ln[a], (int)k);
+                    }
+                    vrow[k] = a2;
+                }
+            }
+            __syncthreads();
+        }
+        first = false;
+        if (base >= n) break;
+    }
+}
+
+// copy the events of store `buf` into a flat list, cells in index order
+__global__ void __launch_bounds__(1024) flatten_kernel(Geo g, Dev d, int buf, double* fx, double* fy, double* ft,
+                                                       double* fm, unsigned long long* fid, int* n_out) {
+    const Store S = d.st[buf];
+    __shared__ int s_warp[32], s_base;
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < g.n_cells; c0 += blockDim.x) {
+        const int c = c0 + threadIdx.x;
+        const int n = c < g.n_cells ? S.count[c] : 0;
+        // exclusive prefix of n across the block, then advance the base
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        int x = n;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[wid] = x;
+        __syncthreads();
+        int before = 0, all = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < wid) before += s_warp[w];
+            all += s_warp[w];
+        }
+        const int off = s_base + before + x - n;
+        if (n) {
+            const int s0 = S.start[c];
+            for (int i = 0; i < n; ++i) {
+                fx[off + i] = S.x[s0 + i];
+                fy[off + i] = S.y[s0 + i];
+                ft[off + i] = S.t[s0 + i];
+                fm[off + i] = S.m[s0 + i];
+                fid[off + i] = S.id[s0 + i];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_base += all;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_out = s_base;
+}
+
+// sum over all stations and samples of log N(s; 0, V): per-block partials
+template <bool F32>
+__global__ void loglik_kernel(Geo g, Dev d, double* partial) {
+    __shared__ double s_part[32];
+    double acc = 0.0;
+    const long long total = (long long)g.n_st * g.n_samp;
+    const double half_log_2pi = 0.91893853320467274178;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long j = i / g.n_samp, k = i - j * g.n_samp;
+        if (F32) {
+            const float s = ((const float*)d.sig)[j * g.pitch + k];
+            const float V = ((const float*)d.V)[j * g.pitch + k];
+            acc += (double)(-0.5f * logf(V) - s * s / (2.f * V)) - half_log_2pi;
+        } else {
+            const double s = ((const double*)d.sig)[j * g.pitch + k];
+            const double V = ((const double*)d.V)[j * g.pitch + k];
+            acc += -half_log_2pi - 0.5 * log(V) - s * s / (2.0 * V);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w];
+        partial[blockIdx.x] = t;
+    }
+}
+
+__global__ void convert_kernel(const void* src, int src_f32, long long src_pitch, void* dst, int dst_f32,
+                               long long dst_pitch, int n_st, long long n_samp, int* nonfinite) {
+    const long long total = (long long)n_st * dst_pitch;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long j = i / dst_pitch, k = i - j * dst_pitch;
+        double v = 0.0;
+        if (k < n_samp) {
+            v = src_f32 ? (double)((const float*)src)[j * src_pitch + k] : ((const double*)src)[j * src_pitch + k];
+            if (!isfinite(v)) atomicExch(nonfinite, 1);
+        }
+        if (dst_f32) ((float*)dst)[i] = (float)v;
+        else ((double*)dst)[i] = v;
+    }
+}
+
+__global__ void philox_test_kernel(const unsigned long long* ctr, const unsigned long long* key,
+                                   unsigned long long* out, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long c[4] = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+    philox4x64(c, key[0], key[1]);
+    for (int q = 0; q < 4; ++q) out[4 * i + q] = c[q];
+}
+
+}  // namespace
+
+size_t phase_smem_bytes(const Geo& g) { return Layout(g).total; }
+
+cudaError_t launch_phase(const Geo& g, const Dev& d, int colour, cudaStream_t s) {
+    const size_t smem = phase_smem_bytes(g);
+    if (g.f32) phase_kernel<true><<<g.max_rpc, g.threads, smem, s>>>(g, d, colour);
+    else phase_kernel<false><<<g.max_rpc, g.threads, smem, s>>>(g, d, colour);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_end(const Geo& g, const Dev& d, cudaStream_t s) {
+    sweep_end<<<1, 1024, 0, s>>>(g, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vsynth(const Geo& g, const Dev& d, const FlatList& f, cudaStream_t s, int* launches) {
+    if (g.n_st == 0) return cudaSuccess;
+    if (g.f32) vsynth_kernel<true><<<g.n_st, kSynthThreads, 0, s>>>(g, d, f.x, f.y, f.t, f.m, f.n);
+    else vsynth_kernel<false><<<g.n_st, kSynthThreads, 0, s>>>(g, d, f.x, f.y, f.t, f.m, f.n);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flatten(const Geo& g, const Dev& d, int buf, const FlatList& f, cudaStream_t s, int* launches) {
+    flatten_kernel<<<1, 1024, 0, s>>>(g, d, buf, f.x, f.y, f.t, f.m, f.id, f.n);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_kernels(const Geo& g) {
+    const size_t smem = phase_smem_bytes(g);
+    cudaError_t e = cudaFuncSetAttribute(phase_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(phase_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_loglik(const Geo& g, const Dev& d, double* partial, int n_part, cudaStream_t s) {
+    if (g.f32) loglik_kernel<true><<<n_part, 256, 0, s>>>(g, d, partial);
+    else loglik_kernel<false><<<n_part, 256, 0, s>>>(g, d, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_signals(const void* src, int src_f32, long long src_pitch, void* dst, int dst_f32,
+                                   long long dst_pitch, int n_st, long long n_samp, int* nonfinite,
+                                   cudaStream_t s) {
+    if (n_st == 0) return cudaSuccess;
+    convert_kernel<<<1216, 256, 0, s>>>(src, src_f32, src_pitch, dst, dst_f32, dst_pitch, n_st, n_samp, nonfinite);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox_test(const unsigned long long* ctr, const unsigned long long* key,
+                               unsigned long long* out, long long n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    philox_test_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(ctr, key, out, n);
+    return cudaGetLastError();
+}
+
+}  // namespace cmh

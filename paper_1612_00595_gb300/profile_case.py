@@ -1,0 +1,55 @@
+"""Run a named workload for profiling: build the model, warm up, run sweeps.
+
+    python paper_1612_00595_gb300/profile_case.py --workload scale --warmup 3 --sweeps 2
+
+Workloads: ``scale`` (4000 x 4000 km, 24 h, 1600 stations, float32),
+``corner`` (1000 x 1000 km corner of the same density and record length,
+100 stations: 0.7 GB of signals + variance, larger than L2), ``replay``
+(1000 x 1000 km, 1 h, 100 stations, float64).
+"""
+import argparse
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import worldgen  # noqa: E402
+
+
+def world_for(name: str):
+    if name == "scale":
+        return worldgen.config_scale(seed=1000)
+    if name == "corner":
+        return worldgen.config_scale(seed=1000, side_regions=10)
+    if name == "replay":
+        return worldgen.config_replay(seed=1000)
+    raise SystemExit("unknown workload " + name)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="corner")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--sweeps", type=int, default=2)
+    ap.add_argument("--k", type=int, default=32)
+    args = ap.parse_args()
+    import paper_1612_00595_gb300 as cm
+    w = world_for(args.workload)
+    dtype = cm.F32 if w.signals.dtype == np.float32 else cm.F64
+    m = cm.create_model(w.events, w.stations, w.signals, cm.make_params(w.params, k_per_phase=args.k, seed=7,
+                                                                        dtype=dtype))
+    m.partition_and_color(w.params.L, shift_mode=1)
+    m.run_sweeps(args.warmup)
+    m.sync()
+    m.run_sweeps(args.sweeps)
+    ev, ids, lp, st = m.read_state()
+    print("events %d  proposals %d  accepted %s  launches %d" % (len(ev), sum(st["proposed"]), st["accepted"],
+                                                                  st["kernel_launches"]))
+    m.destroy()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+"""CUDA path vs the CPU oracle, through the C ABI.
+
+float64 replay: every MH step's move type, validity, event pick and accept
+decision are bit-identical to the oracle's; log-likelihood changes and log
+acceptance ratios agree to 1e-9 relative (to max(|x|, 1)); the final event
+sets are identical (ids and coordinates).  The oracle never sees anything
+the GPU produced: both start from the same seeded world and seed.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import worldgen
+from gpu_helpers import assert_traces_match, lib, run_gpu, run_oracle, small_world
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cm():
+    return lib()
+
+
+def test_philox_device_matches_oracle(cm, orc):
+    rng = np.random.default_rng(3)
+    ctr = rng.integers(0, 2**63, size=(2048, 4), dtype=np.uint64)
+    ctr[:4] = [[0, 0, 0, 0], [2**64 - 1, 2**64 - 1, 2**64 - 1, 2**64 - 1], [1, 2, 3, 4], [7, 0, 0, 1]]
+    for key in ([0, 0], [11, 0], [2**64 - 1, 1], [12345, 2]):
+        dev = cm.philox4x64(ctr, key)
+        ref = np.array([orc.philox4x64(c, key) for c in ctr])
+        assert np.array_equal(dev, ref)
+
+
+@pytest.mark.parametrize("init", ["empty", "truth"])
+@pytest.mark.parametrize("shift_mode", [1, 0])
+def test_replay_small_bit_exact(cm, orc, init, shift_mode):
+    w = small_world()
+    ev0 = w.events if init == "truth" else None
+    sweeps = 6
+    m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=sweeps, events=ev0, shift_mode=shift_mode,
+                                          sx=37.0, sy=81.5)
+    o, oev, oids, otr, odlp = run_oracle(orc, w, sweeps=sweeps, events=ev0, shift_mode=shift_mode,
+                                         sx=37.0, sy=81.5)
+    assert_traces_match(tr, otr)
+    assert np.array_equal(ids, oids)
+    # x, y, t are sums of exactly rounded operations on both sides; m goes
+    # through log() at birth, which may differ by an ulp between libraries
+    assert np.array_equal(ev[:, :3], oev[:, :3])
+    assert np.allclose(ev[:, 3], oev[:, 3], rtol=1e-14, atol=0)
+    assert stats["accepted"][0] + stats["accepted"][1] + stats["accepted"][2] == int(tr["accepted"].sum())
+    assert sum(stats["proposed"]) == len(tr)
+    # running log-density: change equals the oracle's accumulated change
+    lp0 = o.log_density(w.events if init == "truth" else np.zeros((0, 4)))
+    assert logp == pytest.approx(lp0 + odlp, rel=1e-11)
+    m.destroy()
+
+
+def test_replay_shift_matches_oracle(cm, orc):
+    w = small_world(seed=8)
+    params = cm.make_params(w.params, k_per_phase=4, seed=99, dtype=cm.F64)
+    m = cm.create_model(None, w.stations, w.signals, params)
+    m.partition_and_color(w.params.L, shift_mode=1)
+    o = orc.World(w, seed=99)
+    for s in range(5):
+        m.run_sweeps(1)
+        assert m.read_shift() == o.shift(s)
+    m.destroy()
+
+
+def test_replay_config2_world(cm, orc):
+    """The 1000 x 1000 km, 100-station, 36000-sample world of the replay
+    workload: a few sweeps from the ground truth and from the empty set."""
+    w = worldgen.config_replay(seed=1000)
+    threads = min(16, os.cpu_count() or 1)
+    for init in (w.events, None):
+        m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=3, k=32, seed=7, events=init)
+        o, oev, oids, otr, odlp = run_oracle(orc, w, sweeps=3, k=32, seed=7, events=init, threads=threads)
+        assert_traces_match(tr, otr)
+        assert np.array_equal(ids, oids)
+        assert np.array_equal(ev[:, :3], oev[:, :3])
+        m.destroy()
+
+
+def test_log_density_recompute_matches_oracle(cm, orc):
+    w = small_world(seed=9)
+    params = cm.make_params(w.params, k_per_phase=8, seed=5, dtype=cm.F64)
+    m = cm.create_model(w.events, w.stations, w.signals, params)
+    o = orc.World(w)
+    want = o.log_density(w.events)
+    assert m.log_density() == pytest.approx(want, rel=1e-12)
+    _, _, lp_run, _ = m.read_state()
+    assert lp_run == pytest.approx(want, rel=1e-12)
+    # after sweeps, the running value tracks a from-scratch recomputation
+    m.partition_and_color(w.params.L, 1)
+    m.run_sweeps(10)
+    _, _, lp_run, _ = m.read_state()
+    assert m.log_density() == pytest.approx(lp_run, rel=1e-10)
+    m.destroy()
+
+
+def test_device_signals_and_empty_start(cm, orc):
+    w = small_world(seed=12)
+    a = run_gpu(cm, w, sweeps=3, on_device=True)
+    b = run_gpu(cm, w, sweeps=3, on_device=False)
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[5], b[5])
+    a[0].destroy()
+    b[0].destroy()
+
+
+def test_ragged_samples_and_single_step(cm, orc):
+    # n_samples not a multiple of 4 or 64; windows cut by the record's end
+    w = small_world(seed=13, T=1234.5, Lambda=40.0)
+    assert w.signals.shape[1] % 4 != 0
+    m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=4, k=1, events=w.events)
+    o, oev, oids, otr, odlp = run_oracle(orc, w, sweeps=4, k=1, events=w.events)
+    assert_traces_match(tr, otr)
+    assert np.array_equal(ids, oids)
+    m.destroy()
+
+
+def test_prior_only_world(cm, orc):
+    """No stations: the chain samples the prior; still bit-identical."""
+    p = worldgen.ModelParams(W=300.0, T=100.0, Lambda=15.0)
+    w = worldgen.World(params=p, stations=np.zeros((0, 2)), signals=np.zeros((0, p.n_samples)),
+                       events=np.zeros((0, 4)))
+    m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=20, k=8)
+    o, oev, oids, otr, odlp = run_oracle(orc, w, sweeps=20, k=8)
+    assert_traces_match(tr, otr)
+    assert np.array_equal(ids, oids) and 0 < len(ev) < 60
+    m.destroy()
+
+
+def test_capacity_overflow_is_reported_not_faulted(cm):
+    w = small_world(seed=14, Lambda=400.0)
+    params = cm.make_params(w.params, k_per_phase=16, seed=1, dtype=cm.F64, ev_capacity=17)
+    m = cm.create_model(w.events, w.stations, w.signals, params)
+    with pytest.raises(cm.ChromhError) as ei:
+        m.partition_and_color(w.params.L, 1)
+        m.run_sweeps(1)
+        m.read_state()
+    assert ei.value.code == -5
+    with pytest.raises(cm.ChromhError) as ei:
+        m.run_sweeps(1)
+    assert ei.value.code == -8
+    m.destroy()
+
+
+def test_checkpoint_restore_continues_the_chain(cm):
+    w = small_world(seed=15)
+    params = cm.make_params(w.params, k_per_phase=8, seed=4, dtype=cm.F64)
+    a = cm.create_model(None, w.stations, w.signals, params)
+    a.partition_and_color(w.params.L, 1)
+    a.run_sweeps(10)
+    ev_a, ids_a, lp_a, _ = a.read_state()
+    b = cm.create_model(None, w.stations, w.signals, params)
+    b.partition_and_color(w.params.L, 1)
+    b.run_sweeps(5)
+    blob = b.checkpoint()
+    c = cm.create_model(None, w.stations, w.signals, params)
+    c.restore(blob)
+    c.run_sweeps(5)
+    ev_c, ids_c, lp_c, _ = c.read_state()
+    assert np.array_equal(ids_a, ids_c)
+    assert np.array_equal(ev_a[:, :3], ev_c[:, :3])
+    assert lp_c == pytest.approx(lp_a, rel=1e-11)
+    with pytest.raises(cm.ChromhError):
+        c.restore(blob[:40])
+    for x in (a, b, c):
+        x.destroy()
+
+
+def test_fp32_dry_run_deltas(cm, orc):
+    """float32 per-sample terms vs the float64 oracle on the same proposals:
+    with commit off, every proposal is priced against the ground-truth state,
+    so the two sides price identical (state, candidate) pairs."""
+    w = small_world(seed=16, W=1000.0, T=3600.0, Lambda=500.0, n_side=10, dtype=np.float32)
+    m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=4, k=32, events=w.events, commit=False, seed=21)
+    o, oev, oids, otr, odlp = run_oracle(orc, w, sweeps=4, k=32, events=w.events, commit=False, seed=21,
+                                         threads=min(16, os.cpu_count() or 1))
+    assert len(tr) == len(otr)
+    for key in ("sweep", "cell", "step", "type", "evaluated", "n_before"):
+        assert np.array_equal(tr[key], otr[key]), key
+    ev_ = otr["evaluated"] == 1
+    err = np.abs(tr["dll"][ev_] - otr["dll"][ev_]) / np.maximum(np.abs(otr["dll"][ev_]), 1.0)
+    print("fp32 dll rel err: n=%d median %.2e p99 %.2e p99.9 %.2e max %.2e" % (
+        err.size, np.median(err), np.quantile(err, 0.99), np.quantile(err, 0.999), err.max()))
+    assert err.max() <= 1e-4
+    mism = np.count_nonzero(tr["accepted"][ev_] != otr["accepted"][ev_])
+    assert mism <= max(2, err.size // 10000)
+    m.destroy()

@@ -199,6 +199,34 @@ void cmh_destroy(cmh_model* m);
 const char* cmh_strerror(int code);
 
 /*
+ * Sum over rows r < n_rows and samples k < n_samples of the Gaussian
+ * log-density log N(signals[r][k]; 0, variance[r][k]), for callers that cannot
+ * allocate device memory: applications whose memory manager owns the whole
+ * GPU, hooks that must not trigger the device synchronisation an allocation
+ * may cause, plugins in processes that forbid allocations outside their
+ * framework.  The paper has no counterpart; it is the likelihood reduction of
+ * cmh_log_density applied to caller-owned buffers.
+ *   signals, variance  device pointers, row-major [n_rows][row_pitch] of dtype
+ *                      (caller-owned, read only)
+ *   out                host pointer; receives the sum (float64 accumulation)
+ *   cuda_stream        stream the two kernels and the 8-byte read-back are
+ *                      ordered on (NULL: legacy default stream); the call
+ *                      synchronises it before returning
+ * Allocates nothing: the partial sums live in a fixed 64 KB device array
+ * that every GPU loading the library keeps until exit.  The first call on a
+ * device looks that array's address up (cudaGetSymbolAddress), so make it
+ * before capturing a stream.  Every call reuses the same array: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.
+ * Errors: CMH_ERR_ARG (null pointer, n_samples < 1, row_pitch < n_samples,
+ * unknown dtype), CMH_ERR_CAPACITY (n_rows > 8191, the array's limit),
+ * CMH_ERR_CUDA.
+ */
+int cmh_gaussian_loglik_noalloc(const void* signals, const void* variance, int32_t n_rows,
+                                int64_t n_samples, int64_t row_pitch, cmh_dtype dtype, double* out,
+                                void* cuda_stream);
+
+/*
  * Test hook: n Philox4x64-10 blocks computed by a device kernel.
  * ctr [n][4], key [2], out [n][4] host arrays.
  */

@@ -68,7 +68,8 @@ TRACE_DTYPE = np.dtype([("sweep", "<i4"), ("cell", "<i4"), ("step", "<i4"), ("ty
 
 EXPORTS = ["cmh_create_model", "cmh_partition_and_color", "cmh_run_sweeps", "cmh_read_state", "cmh_sync",
            "cmh_log_density", "cmh_set_trace", "cmh_read_trace", "cmh_set_timing", "cmh_read_shift",
-           "cmh_checkpoint", "cmh_restore", "cmh_destroy", "cmh_strerror", "cmh_philox4x64"]
+           "cmh_checkpoint", "cmh_restore", "cmh_destroy", "cmh_strerror", "cmh_philox4x64",
+           "cmh_gaussian_loglik_noalloc"]
 
 
 def _load():
@@ -96,6 +97,7 @@ def _load():
         "cmh_destroy": (None, [P]),
         "cmh_strerror": (C.c_char_p, [C.c_int]),
         "cmh_philox4x64": (C.c_int, [P, P, P, i64]),
+        "cmh_gaussian_loglik_noalloc": (C.c_int, [P, P, i32, i64, i64, i32, C.POINTER(C.c_double), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

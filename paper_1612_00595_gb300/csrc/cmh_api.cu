@@ -352,17 +352,41 @@ int cmh_create_model(const cmh_event* init_events, int64_t n_events, const cmh_s
     g.f32 = p->dtype == CMH_F32;
     g.threads = m->p.block_threads;
     g.max_events = m->p.max_events;
+    g.fv_f = (float)(p->f_hz / p->v);
+    g.twoftau_f = (float)(2.0 / (p->f_hz * p->tau));
+    g.kap_f = (float)(2.0 * 1.4426950408889634074 / (p->f_hz * p->tau));
+    g.alpha_f = (float)p->alpha;
+    g.beta_f = (float)p->beta_att;
+    g.R_f = (float)p->R_max;
+    g.noise_f = (float)p->noise_var;
+    g.f_f = (float)p->f_hz;
+    g.tau_f = (float)p->tau;
+    g.v_f = (float)p->v;
+    g.Tf = p->T * p->f_hz;
+    g.TfK = (int)std::floor(g.Tf);
+    g.lb0 = g.log_Lambda - g.log_WWT + 2.0;
+    g.Cb0 = g.log_Lambda - g.log_WWT + g.log_T + g.log_pd - g.log_pb;
     if (g.ev_cap < g.k + 1) return fail(CMH_ERR_ARG);
 
     Dev& d = m->d;
     const size_t esz = g.f32 ? sizeof(float) : sizeof(double);
     std::vector<double> hx(n_stations), hy(n_stations);
-    for (int j = 0; j < n_stations; ++j) { hx[j] = stations[j].x; hy[j] = stations[j].y; }
+    std::vector<float> hxf(n_stations), hyf(n_stations);
+    for (int j = 0; j < n_stations; ++j) {
+        hx[j] = stations[j].x;
+        hy[j] = stations[j].y;
+        hxf[j] = (float)hx[j];
+        hyf[j] = (float)hy[j];
+    }
     double *stx = nullptr, *sty = nullptr;
     cudaError_t e;
     if ((e = m->alloc(&stx, n_stations)) || (e = m->alloc(&sty, n_stations))) return fail(cuda_err(e));
     d.stx = stx;
     d.sty = sty;
+    float *stxf = nullptr, *styf = nullptr;
+    if ((e = m->alloc(&stxf, n_stations)) || (e = m->alloc(&styf, n_stations))) return fail(cuda_err(e));
+    d.stxf = stxf;
+    d.styf = styf;
     unsigned char *sig = nullptr, *V = nullptr;
     if ((e = m->alloc(&sig, (size_t)n_stations * g.pitch * esz)) ||
         (e = m->alloc(&V, (size_t)n_stations * g.pitch * esz)))
@@ -391,6 +415,8 @@ int cmh_create_model(const cmh_event* init_events, int64_t n_events, const cmh_s
     if ((e = cudaMemcpyAsync(log_n, ln.data(), sizeof(double) * ln.size(), cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(stx, hx.data(), sizeof(double) * n_stations, cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(sty, hy.data(), sizeof(double) * n_stations, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(stxf, hxf.data(), sizeof(float) * n_stations, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(styf, hyf.data(), sizeof(float) * n_stations, cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemsetAsync(d.status, 0, sizeof(int), s)) || (e = cudaMemsetAsync(nonfinite, 0, sizeof(int), s)) ||
         (e = cudaMemsetAsync(d.sweep, 0, sizeof(long long), s)) ||
         (e = cudaMemsetAsync(d.stats, 0, sizeof(unsigned long long) * kStats, s)) ||
@@ -495,8 +521,9 @@ int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mo
         int rc = ensure_flat(m, g.store_cap, n_flat);
         if (rc) return rc;
     }
-    if (phase_smem_bytes(g) > 227 * 1024) return CMH_ERR_CAPACITY;
+    if ((g.f32 ? phase32_smem_bytes(g) : phase_smem_bytes(g)) > 227 * 1024) return CMH_ERR_CAPACITY;
     CK(prepare_kernels(g));
+    CK(prepare_phase32(g));
 
     Dev& d = m->d;
     cudaError_t e;

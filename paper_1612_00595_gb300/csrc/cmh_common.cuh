@@ -37,6 +37,15 @@ struct Geo {
     long long store_cap, max_events;
     int f32;
     int threads;
+    // float32 form of the model constants (host-computed)
+    float fv_f;        // f / v
+    float twoftau_f;   // 2 / (f tau)
+    float kap_f;       // 2 log2(e) / (f tau): per-sample decay of log2 of a variance
+    float alpha_f, beta_f, R_f, noise_f, f_f, tau_f, v_f;
+    double Tf;         // T f
+    int TfK;           // floor(T f)
+    double lb0;        // log Lambda - log(W^2 T) + 2: log beta(m) = lb0 - m
+    double Cb0;        // log Lambda - log(W^2 T) + log T + log p_d - log p_b (+ log area per region)
 };
 
 // one event store (structure of arrays) with per-cell slices
@@ -64,6 +73,8 @@ struct Dev {
     void* V;                    // [n_st][pitch] predicted variance
     const double* stx;
     const double* sty;
+    const float* stxf;          // float copies of the station coordinates
+    const float* styf;
     const double* log_n;        // [ev_cap + 2] log(n) table, computed on the host
 };
 
@@ -143,6 +154,56 @@ __device__ __forceinline__ void sweep_shift(const Geo& g, long long sweep, doubl
 
 __device__ __forceinline__ void latch(int* status, int code) { atomicCAS(status, 0, code); }
 
+// --------------------------------------------------------------------------
+// float32 form of an arrival, shared by every kernel that builds or changes
+// the float32 variance buffer, so that the variance an event adds at a station
+// is the same bit pattern wherever it is computed (a pure function of the
+// event's float64 master and the station).  Every float operation is
+// explicitly rounded (no contraction differences between translation units).
+// The reach test and the window start have margins ~10x their worst-case
+// float32 error and fall back to the exact float64 expressions inside them,
+// so both integer decisions equal the float64 definition's.
+// --------------------------------------------------------------------------
+constexpr float kMarginR = 2e-3f;   // km
+constexpr float kMarginK = 2e-3f;   // samples
+
+// per-event float32 terms: K = floor(t f), ph = t f - K, mf = m
+__device__ __forceinline__ void event_terms32(const Geo& g, double t, double m, int& K, float& ph, float& mf) {
+    const double tf = __dmul_rn(t, g.f_hz);
+    const double fk = floor(tf);
+    K = (int)fk;
+    ph = (float)__dsub_rn(tf, fk);
+    mf = (float)m;
+}
+
+// reach, first sample k0 and E0 = log2 of the variance added at k0
+__device__ __forceinline__ bool arrival32c(const Geo& g, double x, double y, double t, int K, float ph, float mf,
+                                           double xs, double ys, int& k0, float& E0) {
+    const float dx = (float)__dsub_rn(x, xs), dy = (float)__dsub_rn(y, ys);
+    const float d = __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
+    bool reach;
+    if (d < g.R_f - kMarginR) reach = true;
+    else if (d > g.R_f + kMarginR) reach = false;
+    else reach = dist_rn(x, y, xs, ys) < g.R_max;
+    if (!reach) return false;
+    const float q = __fadd_rn(ph, __fmul_rn(d, g.fv_f));   // arrival x f - K
+    if (fabsf(__fsub_rn(q, rintf(q))) < kMarginK) {
+        const double a = __dadd_rn(t, __ddiv_rn(dist_rn(x, y, xs, ys), g.v));
+        k0 = (int)ceil(__dmul_rn(a, g.f_hz));
+    } else {
+        k0 = K + (int)ceilf(q);
+    }
+    const float lnA2 = __fmul_rn(2.f, __fsub_rn(__fmul_rn(g.alpha_f, mf), __fmul_rn(g.beta_f, d)));
+    const float frac = __fsub_rn((float)(k0 - K), q);      // k0 - arrival x f, in [0, 1)
+    E0 = __fmul_rn(1.4426950408889634f, __fsub_rn(lnA2, __fmul_rn(frac, g.twoftau_f)));
+    return true;
+}
+
+// variance added r samples after the window start (0 <= r < n_w)
+__device__ __forceinline__ float arr_var32(const Geo& g, float E0, int r) {
+    return exp2f(__fsub_rn(E0, __fmul_rn(g.kap_f, (float)r)));
+}
+
 // a flat event list in device memory (canonical order)
 struct FlatList {
     double *x, *y, *t, *m;
@@ -153,6 +214,9 @@ struct FlatList {
 // host-side launchers (defined in the .cu files)
 cudaError_t launch_rebin(const Geo& g, const Dev& d, int init_n, cudaStream_t s, int* launches);
 cudaError_t launch_phase(const Geo& g, const Dev& d, int colour, cudaStream_t s);
+cudaError_t launch_phase32(const Geo& g, const Dev& d, int colour, cudaStream_t s);
+size_t phase32_smem_bytes(const Geo& g);
+cudaError_t prepare_phase32(const Geo& g);
 cudaError_t launch_sweep_end(const Geo& g, const Dev& d, cudaStream_t s);
 size_t phase_smem_bytes(const Geo& g);
 cudaError_t launch_vsynth(const Geo& g, const Dev& d, const FlatList& f, cudaStream_t s, int* launches);

@@ -1,7 +1,9 @@
-// Colour-phase kernel of chromatic Metropolis-Hastings (Algorithm "Chromatic
-// MH with Static Coloring": for one colour, every region of that colour runs
-// k MH steps in parallel with all other regions fixed), plus the predicted-
-// variance synthesis and the log-density reduction.
+// Colour-phase kernel of chromatic Metropolis-Hastings in float64 (the replay
+// form that reproduces the CPU oracle step for step; the float32 throughput
+// form is cmh_phase32.cu), plus the predicted-variance synthesis and the
+// log-density reduction.  (Algorithm "Chromatic MH with Static Coloring": for
+// one colour, every region of that colour runs k MH steps in parallel with
+// all other regions fixed.)
 //
 // One CTA per region of the active colour.  Within a CTA:
 //   * warp 0 is the control warp: it decodes each step's proposal (birth,
@@ -31,13 +33,10 @@ constexpr double LOG2E = 1.4426950408889634074;
 struct EvArr {          // one arrival of an own event at a blanket station
     int slot, k0;       // blanket slot, first sample of the window
     double af, lnA2;    // arrival time x f, 2 (alpha m - beta_att d)
-    float E0;           // log2 of the variance added at sample k0
-    int pad;
 };
 
 struct Arr {            // an arrival in a list (frozen neighbours, others of a task)
-    int k0;
-    float E0;
+    int k0, pad;
     double af, lnA2;
 };
 
@@ -53,9 +52,8 @@ struct Draw {           // state-independent part of one MH step
 struct Task {           // one station whose variance the proposal changes
     int row, slot, lo, hi;
     int has_o, has_n, k0o, k0n;
-    float E0o, E0n, rm1f;
     int oth0;           // others list: [oth0, oth0 + noth) in the pool
-    int noth, pad0;
+    int noth;
     double afo, lnA2o, afn, lnA2n, rm1d;
 };
 
@@ -102,12 +100,6 @@ __device__ __forceinline__ bool arrival(const Geo& g, double x, double y, double
     return true;
 }
 
-// log2 of the variance an arrival adds at its first sample k0
-__device__ __forceinline__ float arr_E0(const Geo& g, int k0, double af, double lnA2) {
-    const double twof_tau = 2.0 / (g.f_hz * g.tau);
-    return (float)(LOG2E * (lnA2 - ((double)k0 - af) * twof_tau));
-}
-
 // variance added at sample k by an arrival (float64 form)
 __device__ __forceinline__ double arr_c64(const Geo& g, double af, double lnA2, int k) {
     return exp(lnA2 - ((double)k - af) * (2.0 / (g.f_hz * g.tau)));
@@ -150,7 +142,6 @@ __device__ __forceinline__ int block_append(bool flag, int* s_warp, int* s_base)
     return pos;
 }
 
-template <bool F32>
 __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
     if (*d.status) return;
     const long long sweep = *d.sweep;
@@ -259,7 +250,7 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
             if (arrival(g, ex[i], ey[i], et[i], em[i], bx[b], by[b], k0, af, lnA2)) {
                 if (na < g.arr_cap) {
                     EvArr& A = earr[i * g.arr_cap + na];
-                    A.slot = b; A.k0 = k0; A.af = af; A.lnA2 = lnA2; A.E0 = arr_E0(g, k0, af, lnA2);
+                    A.slot = b; A.k0 = k0; A.af = af; A.lnA2 = lnA2;
                 }
                 ++na;
             }
@@ -285,7 +276,7 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
                     if (arrival(g, S.x[s0 + i], S.y[s0 + i], S.t[s0 + i], S.m[s0 + i], bx[b], by[b], k0, af, lnA2)) {
                         if (nf < g.frz_cap) {
                             Arr& A = farr[b * g.frz_cap + nf];
-                            A.k0 = k0; A.af = af; A.lnA2 = lnA2; A.E0 = arr_E0(g, k0, af, lnA2);
+                            A.k0 = k0; A.af = af; A.lnA2 = lnA2;
                         }
                         ++nf;
                     }
@@ -341,8 +332,6 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
         return;
     }
 
-    const float kap = (float)(2.0 * LOG2E / (g.f_hz * g.tau));
-    const float noise_f = (float)g.noise_var;
     unsigned long long n_prop[3] = {0, 0, 0}, n_eval[3] = {0, 0, 0}, n_acc[3] = {0, 0, 0};
     unsigned long long n_priced = 0, n_rewritten = 0;   // sample terms (thread 0's tally)
 
@@ -380,7 +369,7 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
                     const int pos = ncand + __popc(bal & ((1u << lane) - 1));
                     if (r && pos < g.arr_cap) {
                         EvArr& A = cand[pos];
-                        A.slot = b; A.k0 = k0; A.af = af; A.lnA2 = lnA2; A.E0 = arr_E0(g, k0, af, lnA2);
+                        A.slot = b; A.k0 = k0; A.af = af; A.lnA2 = lnA2;
                     }
                     ncand += __popc(bal);
                 }
@@ -408,23 +397,21 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
                         long long lo = 1LL << 40, hi = -1;
                         if (T.has_o) {
                             const EvArr& A = oa[io++];
-                            T.k0o = A.k0; T.afo = A.af; T.lnA2o = A.lnA2; T.E0o = A.E0;
+                            T.k0o = A.k0; T.afo = A.af; T.lnA2o = A.lnA2;
                             lo = min(lo, (long long)A.k0);
                             hi = max(hi, (long long)A.k0 + g.n_w);
                         }
                         if (T.has_n) {
                             const EvArr& A = cand[in++];
-                            T.k0n = A.k0; T.afn = A.af; T.lnA2n = A.lnA2; T.E0n = A.E0;
+                            T.k0n = A.k0; T.afn = A.af; T.lnA2n = A.lnA2;
                             lo = min(lo, (long long)A.k0);
                             hi = max(hi, (long long)A.k0 + g.n_w);
                         }
                         if (T.has_o && T.has_n) {
                             // c_new / c_old is constant over the overlap of the two windows
                             T.rm1d = expm1((T.lnA2n - T.lnA2o) + (T.afo - T.afn) * (-2.0 / (g.f_hz * g.tau)));
-                            T.rm1f = (float)T.rm1d;
                         } else {
                             T.rm1d = 0.0;
-                            T.rm1f = 0.f;
                         }
                         if (lo < 0) lo = 0;
                         if (hi > g.n_samp) hi = g.n_samp;
@@ -444,7 +431,7 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
                                 if (A.k0 + g.n_w <= lo || A.k0 >= hi) continue;
                                 if (npool >= Lo.pool_cap) { err = CMH_ERR_CAPACITY; break; }
                                 Arr& B = pool[npool++];
-                                B.k0 = A.k0; B.E0 = A.E0; B.af = A.af; B.lnA2 = A.lnA2;
+                                B.k0 = A.k0; B.af = A.af; B.lnA2 = A.lnA2;
                             }
                         }
                         for (int a = 0; a < fcnt[T.slot] && !err; ++a) {
@@ -472,70 +459,7 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
 
         // ---------------- pricing: all threads ----------------
         if (valid) {
-            if (F32) {
-                float acc = 0.f, comp = 0.f;
-                for (int ti = 0; ti < ntask; ++ti) {
-                    const Task& T = tasks[ti];
-                    const float* srow = (const float*)d.sig + (size_t)T.row * g.pitch;
-                    const float* vrow = (const float*)d.V + (size_t)T.row * g.pitch;
-                    for (int q = (T.lo >> 2) + tid; (q << 2) < T.hi; q += nthr) {
-                        const int k = q << 2;
-                        const float4 s4 = __ldg(reinterpret_cast<const float4*>(srow + k));
-                        const float4 v4 = *reinterpret_cast<const float4*>(vrow + k);
-                        const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
-                        const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int kk = k + e;
-                            const int ro = kk - T.k0o, rn = kk - T.k0n;
-                            const bool io = T.has_o && (unsigned)ro < (unsigned)g.n_w;
-                            const bool inn = T.has_n && (unsigned)rn < (unsigned)g.n_w;
-                            float dd = 0.f;
-                            if (io) {
-                                const float co = exp2f(T.E0o - kap * (float)ro);
-                                dd = inn ? co * T.rm1f : -co;
-                            } else if (inn) {
-                                dd = exp2f(T.E0n - kap * (float)rn);
-                            }
-                            if (kk < T.hi && dd != 0.f) {
-                                const float V = vv[e], s = sv[e];
-                                const float Vp = V + dd;
-                                float term;
-                                if (Vp < 0.5f * V) {
-                                    // the changed arrival dominates V: V + d cancels, so
-                                    // rebuild V' from the arrivals that stay
-                                    float a2 = noise_f, c2 = 0.f;
-                                    for (int o = 0; o < T.noth; ++o) {
-                                        const Arr& A = pool[T.oth0 + o];
-                                        const int r = kk - A.k0;
-                                        if ((unsigned)r < (unsigned)g.n_w) kahan_add(a2, c2, exp2f(A.E0 - kap * (float)r));
-                                    }
-                                    if (inn) kahan_add(a2, c2, exp2f(T.E0n - kap * (float)rn));
-                                    const float Vr = a2 - c2;
-                                    term = logf(Vr / V) + s * s * (1.f / Vr - 1.f / V);
-                                } else {
-                                    term = log1pf(dd / V) - s * s * dd / (V * Vp);
-                                }
-                                kahan_add(acc, comp, -0.5f * term);
-                            }
-                        }
-                    }
-                }
-                float2 v = make_float2(acc, -comp);
-                for (int o = 16; o > 0; o >>= 1) {
-                    float2 w2;
-                    w2.x = __shfl_xor_sync(FULL, v.x, o);
-                    w2.y = __shfl_xor_sync(FULL, v.y, o);
-                    v = ff_add(v, w2);
-                }
-                if (lane == 0) s_redf[wid] = v;
-                __syncthreads();
-                if (tid == 0) {
-                    float2 t = s_redf[0];
-                    for (int w = 1; w < (nthr >> 5); ++w) t = ff_add(t, s_redf[w]);
-                    s_dll = (double)t.x + (double)t.y;
-                }
-            } else {
+            {
                 double acc = 0.0;
                 for (int ti = 0; ti < ntask; ++ti) {
                     const Task& T = tasks[ti];
@@ -661,22 +585,7 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
             for (int ti = 0; ti < ntask; ++ti) {
                 const Task& T = tasks[ti];
                 const bool has_new = type != 1 && T.has_n;
-                if (F32) {
-                    float* vrow = (float*)d.V + (size_t)T.row * g.pitch;
-                    for (int kk = T.lo + tid; kk < T.hi; kk += nthr) {
-                        float a2 = noise_f, c2 = 0.f;
-                        for (int o = 0; o < T.noth; ++o) {
-                            const Arr& A = pool[T.oth0 + o];
-                            const int r = kk - A.k0;
-                            if ((unsigned)r < (unsigned)g.n_w) kahan_add(a2, c2, exp2f(A.E0 - kap * (float)r));
-                        }
-                        if (has_new) {
-                            const int r = kk - T.k0n;
-                            if ((unsigned)r < (unsigned)g.n_w) kahan_add(a2, c2, exp2f(T.E0n - kap * (float)r));
-                        }
-                        vrow[kk] = a2 - c2;
-                    }
-                } else {
+                {
                     double* vrow = (double*)d.V + (size_t)T.row * g.pitch;
                     for (int kk = T.lo + tid; kk < T.hi; kk += nthr) {
                         double a2 = g.noise_var;
@@ -763,9 +672,9 @@ __global__ void __launch_bounds__(kSynthThreads) vsynth_kernel(Geo g, Dev d, con
     const double xs = d.stx[j], ys = d.sty[j];
     __shared__ int s_k0[kSynthArr];
     __shared__ double s_af[kSynthArr], s_ln[kSynthArr];
+    __shared__ float s_E0[kSynthArr];
     __shared__ int s_tl[kSynthArr];
     __shared__ int s_warp[32], s_base, s_cnt, s_nt;
-    const float kap = (float)(2.0 * LOG2E / (g.f_hz * g.tau));
     int base = 0;
     bool first = true;
     while (true) {
@@ -775,7 +684,18 @@ __global__ void __launch_bounds__(kSynthThreads) vsynth_kernel(Geo g, Dev d, con
             const int idx = base + threadIdx.x;
             int k0 = 0;
             double af = 0.0, ln = 0.0;
-            const bool r = idx < n && arrival(g, fx[idx], fy[idx], ft[idx], fm[idx], xs, ys, k0, af, ln);
+            float E0 = 0.f;
+            bool r = false;
+            if (idx < n) {
+                if (F32) {
+                    int K;
+                    float ph, mf;
+                    event_terms32(g, ft[idx], fm[idx], K, ph, mf);
+                    r = arrival32c(g, fx[idx], fy[idx], ft[idx], K, ph, mf, xs, ys, k0, E0);
+                } else {
+                    r = arrival(g, fx[idx], fy[idx], ft[idx], fm[idx], xs, ys, k0, af, ln);
+                }
+            }
             if (threadIdx.x == 0) s_cnt = 0;
             __syncthreads();
             if (r) atomicAdd(&s_cnt, 1);
@@ -786,6 +706,7 @@ __global__ void __launch_bounds__(kSynthThreads) vsynth_kernel(Geo g, Dev d, con
                 s_k0[pos] = k0;
                 s_af[pos] = af;
                 s_ln[pos] = ln;
+                s_E0[pos] = E0;
             }
             base += blockDim.x;
         }
@@ -809,8 +730,7 @@ __global__ void __launch_bounds__(kSynthThreads) vsynth_kernel(Geo g, Dev d, con
                     for (int q = 0; q < nt; ++q) {
                         const int a = s_tl[q];
                         const int r = (int)(k - s_k0[a]);
-                        if ((unsigned)r < (unsigned)g.n_w)
-                            kahan_add(a2, c2, exp2f(arr_E0(g, s_k0[a], s_af[a], s_ln[a]) - kap * (float)r));
+                        if ((unsigned)r < (unsigned)g.n_w) kahan_add(a2, c2, arr_var32(g, s_E0[a], r));
                     }
                     vrow[k] = a2 - c2;
                 } else {
@@ -933,9 +853,9 @@ __global__ void philox_test_kernel(const unsigned long long* ctr, const unsigned
 size_t phase_smem_bytes(const Geo& g) { return Layout(g).total; }
 
 cudaError_t launch_phase(const Geo& g, const Dev& d, int colour, cudaStream_t s) {
+    if (g.f32) return launch_phase32(g, d, colour, s);
     const size_t smem = phase_smem_bytes(g);
-    if (g.f32) phase_kernel<true><<<g.max_rpc, g.threads, smem, s>>>(g, d, colour);
-    else phase_kernel<false><<<g.max_rpc, g.threads, smem, s>>>(g, d, colour);
+    phase_kernel<<<g.max_rpc, g.threads, smem, s>>>(g, d, colour);
     return cudaGetLastError();
 }
 
@@ -960,9 +880,7 @@ cudaError_t launch_flatten(const Geo& g, const Dev& d, int buf, const FlatList& 
 
 cudaError_t prepare_kernels(const Geo& g) {
     const size_t smem = phase_smem_bytes(g);
-    cudaError_t e = cudaFuncSetAttribute(phase_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(phase_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(phase_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 cudaError_t launch_loglik(const Geo& g, const Dev& d, double* partial, int n_part, cudaStream_t s) {

@@ -180,13 +180,35 @@ def test_fp32_dry_run_deltas(cm, orc):
     o, oev, oids, otr, odlp = run_oracle(orc, w, sweeps=4, k=32, events=w.events, commit=False, seed=21,
                                          threads=min(16, os.cpu_count() or 1))
     assert len(tr) == len(otr)
-    for key in ("sweep", "cell", "step", "type", "evaluated", "n_before"):
+    for key in ("sweep", "cell", "step", "type", "n_before"):
         assert np.array_equal(tr[key], otr[key]), key
-    ev_ = otr["evaluated"] == 1
+    # the float32 Box-Muller may round a Gaussian offset to the neighbouring
+    # 2^-20 quantum (a few micrometres), which can flip validity only for a
+    # candidate that close to a region boundary
+    assert np.count_nonzero(tr["evaluated"] != otr["evaluated"]) <= max(2, len(tr) // 10000)
+    ev_ = (otr["evaluated"] == 1) & (tr["evaluated"] == 1)
     err = np.abs(tr["dll"][ev_] - otr["dll"][ev_]) / np.maximum(np.abs(otr["dll"][ev_]), 1.0)
     print("fp32 dll rel err: n=%d median %.2e p99 %.2e p99.9 %.2e max %.2e" % (
         err.size, np.median(err), np.quantile(err, 0.99), np.quantile(err, 0.999), err.max()))
     assert err.max() <= 1e-4
     mism = np.count_nonzero(tr["accepted"][ev_] != otr["accepted"][ev_])
     assert mism <= max(2, err.size // 10000)
+    m.destroy()
+
+
+@pytest.mark.parametrize("init", ["empty", "truth"])
+def test_fp32_chain_tracks_recomputed_log_density(cm, init):
+    """float32 chain with commits: the running log-density (float64 sum of
+    accepted changes) agrees with a from-scratch recomputation of the final
+    state, so the variance re-synthesised on every accept stays consistent
+    with the events."""
+    w = small_world(seed=17, W=1000.0, T=3600.0, Lambda=500.0, n_side=10, dtype=np.float32)
+    ev0 = w.events if init == "truth" else None
+    m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=30, k=32, events=ev0, seed=5)
+    assert sum(stats["accepted"]) > 1000
+    full = m.log_density()
+    assert logp == pytest.approx(full, rel=2e-7, abs=1.0)
+    assert len(np.unique(ids)) == len(ids)
+    assert np.all((ev[:, 0] >= 0) & (ev[:, 0] < w.params.W) & (ev[:, 2] >= 0) & (ev[:, 2] < w.params.T))
+    assert np.all(ev[:, 3] >= 2.0)
     m.destroy()

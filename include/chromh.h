@@ -69,9 +69,16 @@ typedef struct {
     uint64_t seed;         /* key of every Philox stream */
     cmh_dtype dtype;       /* arithmetic of per-sample terms: CMH_F64 (replay) or CMH_F32 */
     int32_t ev_capacity;   /* max events one region may hold in a phase; 0: 128 */
-    int32_t frozen_capacity; /* max arrivals from neighbouring regions per blanket
-                                station; 0: 32 */
+    int32_t frozen_capacity; /* max arrivals listed per blanket station in a phase
+                                (neighbouring regions', plus the region's own in the
+                                float32 form); 0: 64 */
     int32_t block_threads; /* threads per region CTA (64..512, multiple of 32); 0: 256 */
+    int32_t stage_samples; /* float32 form: samples per shared-memory buffer into which the
+                              station windows of the next step are staged by bulk copies
+                              while the current step is priced; 0: no staging (windows are
+                              read from global memory); -1: one window, cut down to what
+                              keeps three CTAs resident per SM; > 0: that many (rounded
+                              down to a multiple of 4) */
     int64_t max_events;    /* capacity of the whole event store; 0: 4 (n0 + Lambda) + 4096 */
 } cmh_params;
 

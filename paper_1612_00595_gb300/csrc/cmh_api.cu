@@ -185,6 +185,7 @@ int validate_params(const cmh_params* p) {
     if (p->k_per_phase < 1 || p->k_per_phase > kMaxK) return CMH_ERR_ARG;
     if (p->dtype != CMH_F32 && p->dtype != CMH_F64) return CMH_ERR_ARG;
     if (p->ev_capacity < 0 || p->frozen_capacity < 0 || p->max_events < 0) return CMH_ERR_ARG;
+    if (p->stage_samples < -1) return CMH_ERR_ARG;
     if (p->block_threads != 0 && (p->block_threads < 64 || p->block_threads > 512 || p->block_threads % 32))
         return CMH_ERR_ARG;
     const double nw = std::llround(p->t_s * p->f_hz);
@@ -314,7 +315,7 @@ int cmh_create_model(const cmh_event* init_events, int64_t n_events, const cmh_s
     if (!m) return CMH_ERR_OOM;
     m->p = *p;
     if (m->p.ev_capacity == 0) m->p.ev_capacity = 128;
-    if (m->p.frozen_capacity == 0) m->p.frozen_capacity = 32;
+    if (m->p.frozen_capacity == 0) m->p.frozen_capacity = 64;
     if (m->p.block_threads == 0) m->p.block_threads = 256;
     if (m->p.max_events == 0) m->p.max_events = 4 * (n_events + (int64_t)std::ceil(p->Lambda)) + 4096;
     if (m->p.max_events < n_events) { delete m; return CMH_ERR_ARG; }
@@ -355,6 +356,7 @@ int cmh_create_model(const cmh_event* init_events, int64_t n_events, const cmh_s
     g.fv_f = (float)(p->f_hz / p->v);
     g.twoftau_f = (float)(2.0 / (p->f_hz * p->tau));
     g.kap_f = (float)(2.0 * 1.4426950408889634074 / (p->f_hz * p->tau));
+    for (int e = 0; e < 4; ++e) g.rho_f[e] = (float)std::exp2(-(double)g.kap_f * e);
     g.alpha_f = (float)p->alpha;
     g.beta_f = (float)p->beta_att;
     g.R_f = (float)p->R_max;
@@ -521,6 +523,8 @@ int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mo
         int rc = ensure_flat(m, g.store_cap, n_flat);
         if (rc) return rc;
     }
+    g.stage_cap = 0;
+    if (g.f32) CK(choose_stage_cap(g, m->p.stage_samples));
     if ((g.f32 ? phase32_smem_bytes(g) : phase_smem_bytes(g)) > 227 * 1024) return CMH_ERR_CAPACITY;
     CK(prepare_kernels(g));
     CK(prepare_phase32(g));

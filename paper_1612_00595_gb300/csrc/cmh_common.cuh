@@ -34,6 +34,7 @@ struct Geo {
     long long n_samp, pitch;
     unsigned long long seed;
     int ev_cap, blk_cap, frz_cap, arr_cap;
+    int stage_cap;      // floats per shared-memory staging buffer of the float32 phase (0: none)
     long long store_cap, max_events;
     int f32;
     int threads;
@@ -41,6 +42,7 @@ struct Geo {
     float fv_f;        // f / v
     float twoftau_f;   // 2 / (f tau)
     float kap_f;       // 2 log2(e) / (f tau): per-sample decay of log2 of a variance
+    float rho_f[4];    // 2^(-kap e), e = 0..3 (rho_f[0] = 1)
     float alpha_f, beta_f, R_f, noise_f, f_f, tau_f, v_f;
     double Tf;         // T f
     int TfK;           // floor(T f)
@@ -167,6 +169,15 @@ __device__ __forceinline__ void latch(int* status, int code) { atomicCAS(status,
 constexpr float kMarginR = 2e-3f;   // km
 constexpr float kMarginK = 2e-3f;   // samples
 
+// the exact float64 decisions, out of line: they run only inside the margins
+static __device__ __noinline__ bool reach_exact(double x, double y, double xs, double ys, double R) {
+    return dist_rn(x, y, xs, ys) < R;
+}
+static __device__ __noinline__ int k0_exact(double x, double y, double t, double xs, double ys, double v, double f) {
+    const double a = __dadd_rn(t, __ddiv_rn(dist_rn(x, y, xs, ys), v));
+    return (int)ceil(__dmul_rn(a, f));
+}
+
 // per-event float32 terms: K = floor(t f), ph = t f - K, mf = m
 __device__ __forceinline__ void event_terms32(const Geo& g, double t, double m, int& K, float& ph, float& mf) {
     const double tf = __dmul_rn(t, g.f_hz);
@@ -184,24 +195,53 @@ __device__ __forceinline__ bool arrival32c(const Geo& g, double x, double y, dou
     bool reach;
     if (d < g.R_f - kMarginR) reach = true;
     else if (d > g.R_f + kMarginR) reach = false;
-    else reach = dist_rn(x, y, xs, ys) < g.R_max;
+    else reach = reach_exact(x, y, xs, ys, g.R_max);
     if (!reach) return false;
     const float q = __fadd_rn(ph, __fmul_rn(d, g.fv_f));   // arrival x f - K
-    if (fabsf(__fsub_rn(q, rintf(q))) < kMarginK) {
-        const double a = __dadd_rn(t, __ddiv_rn(dist_rn(x, y, xs, ys), g.v));
-        k0 = (int)ceil(__dmul_rn(a, g.f_hz));
-    } else {
-        k0 = K + (int)ceilf(q);
-    }
+    if (fabsf(__fsub_rn(q, rintf(q))) < kMarginK) k0 = k0_exact(x, y, t, xs, ys, g.v, g.f_hz);
+    else k0 = K + (int)ceilf(q);
     const float lnA2 = __fmul_rn(2.f, __fsub_rn(__fmul_rn(g.alpha_f, mf), __fmul_rn(g.beta_f, d)));
     const float frac = __fsub_rn((float)(k0 - K), q);      // k0 - arrival x f, in [0, 1)
     E0 = __fmul_rn(1.4426950408889634f, __fsub_rn(lnA2, __fmul_rn(frac, g.twoftau_f)));
     return true;
 }
 
-// variance added r samples after the window start (0 <= r < n_w)
-__device__ __forceinline__ float arr_var32(const Geo& g, float E0, int r) {
-    return exp2f(__fsub_rn(E0, __fmul_rn(g.kap_f, (float)r)));
+// 2^x by the SFU (relative error ~2^-22); inline PTX so that every kernel
+// evaluates the same instruction
+__device__ __forceinline__ float ex2_sfu(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// float32 variance an arrival (window start k0, E0 = log2 of the variance at
+// k0) adds at sample k, for k in its window.  Samples are grouped in fours
+// (k4 = k & ~3): the SFU evaluates the group's base 2^(E0 - kap (k4 - k0))
+// and the sample multiplies it by rho[k - k4] = 2^(-kap (k - k4)), constants
+// computed once on the host.  Every kernel evaluates exactly this, so a
+// group's four values can be produced from one SFU result.
+__device__ __forceinline__ float arr_base32(const Geo& g, float E0, int k0, int k4) {
+    return ex2_sfu(__fsub_rn(E0, __fmul_rn(g.kap_f, (float)(k4 - k0))));
+}
+__device__ __forceinline__ float arr_var32(const Geo& g, float E0, int k0, int k) {
+    return __fmul_rn(arr_base32(g, E0, k0, k & ~3), g.rho_f[k & 3]);
+}
+
+// log(1 + x) for x >= -1/2: the Taylor series x - x^2/2 + ... + x^7/7 for
+// |x| < 1/16 (truncation < 3e-11 relative), else the SFU log of 1 + x
+// (1 + x is within 1.2e-7 relative when x >= -1/2)
+__device__ __forceinline__ float log1p_fast(float x) {
+    if (fabsf(x) < 0.0625f) {
+        float p = 1.f / 7.f;
+        p = fmaf(p, x, -1.f / 6.f);
+        p = fmaf(p, x, 1.f / 5.f);
+        p = fmaf(p, x, -1.f / 4.f);
+        p = fmaf(p, x, 1.f / 3.f);
+        p = fmaf(p, x, -0.5f);
+        p = fmaf(p, x, 1.f);
+        return p * x;
+    }
+    return __logf(1.f + x);
 }
 
 // a flat event list in device memory (canonical order)
@@ -217,6 +257,7 @@ cudaError_t launch_phase(const Geo& g, const Dev& d, int colour, cudaStream_t s)
 cudaError_t launch_phase32(const Geo& g, const Dev& d, int colour, cudaStream_t s);
 size_t phase32_smem_bytes(const Geo& g);
 cudaError_t prepare_phase32(const Geo& g);
+cudaError_t choose_stage_cap(Geo& g, int requested);
 cudaError_t launch_sweep_end(const Geo& g, const Dev& d, cudaStream_t s);
 size_t phase_smem_bytes(const Geo& g);
 cudaError_t launch_vsynth(const Geo& g, const Dev& d, const FlatList& f, cudaStream_t s, int* launches);

@@ -2,21 +2,38 @@
 // Static Coloring": every region of one colour runs k MH steps in parallel
 // with the other regions fixed).  One CTA per region.
 //
-// The state stays float64 (the event masters), but within a phase every
-// per-step test runs in float32 on cell-relative coordinates:
+// Precision.  The state stays float64 (the event masters), but within a
+// phase every per-step test runs in float32:
 //   * "does the event reach station j" (distance < R_max),
 //   * "which sample does its window start at" (ceil(arrival x f)),
 //   * "is the moved event still in the region / domain / time range".
 // Each float32 test has a margin about 10x its worst-case rounding error; a
 // value inside the margin is decided by the exact float64 expression of the
-// float64 master coordinates instead.  So every integer decision is the one
-// the float64 definition gives, while the float64 pipe (1/64 of the float32
-// rate on this part) is used only for the accept decision and for master
-// updates on accept.  Per-sample likelihood terms are float32 with Kahan sums
-// per thread, float-float (TwoSum) warp-shuffle reductions and a float64
-// result.
+// float64 master coordinates instead (out-of-line functions).  So every
+// integer decision is the one the float64 definition gives, while the float64
+// pipe (64-cycle dependent latency, 1/64 of the float32 rate on this part) is
+// used for little more than the accept decision.  Per-sample likelihood terms
+// are float32, summed in groups of four and compensated (Kahan) per thread,
+// reduced across threads in float-float (TwoSum) and finished in float64.
+//
+// Schedule.  Warp 0 manages: while warps 1.. price step i it prepares step
+// i+1 (decode, reach, tasks), assuming step i is rejected (the common case),
+// then decides step i; after an accepted step it prepares step i+1 again.
+// Each blanket station keeps the list of arrivals that cover it (neighbouring
+// regions' and the region's own, tagged by owner), updated on every commit,
+// so preparing a step never scans the region's events and re-synthesising V
+// reads one list.
+//
+// Staging (optional, the STAGE instantiation).  Having prepared step i+1,
+// warp 0 copies its station windows of s and V into shared memory with bulk
+// copies (cp.async.bulk, completion counted on an mbarrier; two buffers
+// alternate by step parity), and the workers price from shared memory.  After
+// an accepted step, V is re-written, fenced for the async proxy, and the next
+// step's copies are issued again.  Every mbarrier wait is bounded.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <algorithm>
 
 #include "cmh_common.cuh"
 
@@ -28,17 +45,23 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr float kDr = 2e-3f;   // km: margin of the region tests
 constexpr float kDm = 1e-5f;   // magnitude units: margin of the m >= 2 test
 constexpr int kThreads32 = 256;
-constexpr int kMaxTasks32 = 64;
+constexpr int kMaxTasks32 = 32;
+constexpr int kUnroll = 2;     // float4 groups whose loads a pricing thread issues together
+constexpr int kFrozen = -2;    // owner tag of an arrival from a neighbouring region
+constexpr int kMinBlocks32 = 3;   // resident CTAs per SM the kernel is built for
+constexpr unsigned kWaitLimit = 1u << 24;   // bounded mbarrier waits
 
-struct A32 {            // arrival of an event at a blanket slot
+struct A32 {            // arrival of an own event at a blanket slot (the event's cache)
     int slot, k0;
-    float E0;           // log2 of the variance added at sample k0
+    float E0;
     int pad;
 };
 
-struct F32a {           // an arrival in a list (frozen neighbours, others of a task)
+struct SA {             // an entry of a station's arrival list
     int k0;
-    float E0;
+    float E0;           // log2 of the variance added at sample k0
+    int own;            // physical slot of the own event, or kFrozen
+    int pad;
 };
 
 struct D32 {            // state-independent part of one MH step
@@ -53,46 +76,96 @@ struct T32 {            // one station whose variance the proposal changes
     int row, slot, lo, hi;
     int has_o, has_n, k0o, k0n;
     float E0o, E0n;
-    int oth0, noth;
+    int skip;           // owner whose arrival leaves the station (-1: none)
+    int u0;             // first float4 group of this task in the step's flat range
 };
 
-struct L32 {
-    size_t mx, my, mt, mm, id, xr, yr, ph, mf, K, narr, arr, order, freel, tabB, tabD;
-    size_t bsta, bx, by, fcnt, farr, draws, cand, tasks, pool;
-    size_t nx, ny, nt, nmm, nxr, nyr, nph, nmf, nK, total;
-    int pool_cap;
-    __host__ __device__ L32(const Geo& g) {
-        pool_cap = g.ev_cap + g.frz_cap;
-        size_t o = 0;
-        auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 15) & ~size_t(15); return r; };
-        const size_t E = g.ev_cap;
-        mx = take(8 * E); my = take(8 * E); mt = take(8 * E); mm = take(8 * E); id = take(8 * E);
-        xr = take(4 * E); yr = take(4 * E); ph = take(4 * E); mf = take(4 * E); K = take(4 * E);
-        narr = take(4 * E);
-        arr = take(sizeof(A32) * E * g.arr_cap);
-        order = take(4 * E); freel = take(4 * E);
-        tabB = take(8 * (E + 1)); tabD = take(8 * (E + 1));
-        bsta = take(4 * (size_t)g.blk_cap);
-        bx = take(8 * (size_t)g.blk_cap); by = take(8 * (size_t)g.blk_cap);
-        fcnt = take(4 * (size_t)g.blk_cap);
-        farr = take(sizeof(F32a) * (size_t)g.blk_cap * g.frz_cap);
-        draws = take(sizeof(D32) * (size_t)g.k);
-        cand = take(sizeof(A32) * (size_t)g.arr_cap);
-        tasks = take(sizeof(T32) * kMaxTasks32);
-        pool = take(sizeof(F32a) * (size_t)pool_cap);
-        // one neighbouring cell's events at a time (frozen arrivals)
-        nx = take(8 * E); ny = take(8 * E); nt = take(8 * E); nmm = take(8 * E);
-        nxr = take(4 * E); nyr = take(4 * E); nph = take(4 * E); nmf = take(4 * E); nK = take(4 * E);
-        total = o;
-    }
-};
-
-// an event in cell-relative float form plus its float64 master
-struct P32 {
-    float xr, yr, ph, mf;
-    int K;
+struct P32 {            // an event: float64 master, float32 terms, region-relative position
     double x, y, t, m;
+    float xr, yr, ph, mf;
+    int K, pad;
 };
+
+// everything a CTA keeps in shared memory: pointers into the dynamic buffer
+// and the scalars of the region and of the two step buffers
+struct Sm {
+    double *mx, *my, *mt, *mm;
+    unsigned long long* eid;
+    float *exr, *eyr;
+    int *enarr, *order, *freel;
+    A32* earr;
+    double *tabB, *tabD;
+    int* bsta;
+    double *bx, *by;
+    int* scnt;          // entries of each station's arrival list
+    SA* sarr;           // [blk_cap][scap]
+    D32* draws;
+    A32* cand;          // [2][arr_cap]
+    T32* tasks;         // [2][kMaxTasks32]
+    double *nx, *ny, *nt;
+    float *nph, *nmf;
+    int* nK;
+    int* tsoff;         // [2][kMaxTasks32] staging offset of each task's window (floats), -1: global
+    float* stage_s;     // [2][scap] staged signal windows
+    float* stage_v;     // [2][scap] staged variance windows
+    int scap;           // floats per staging buffer (0: no staging)
+    unsigned long long bar[2];   // mbarrier of each staging buffer
+    int ph[2], on[2];   // parity of its pending completion; copies in flight
+    double rect[4], X0, Y0, sx, sy, region_dlp;
+    float rl[4];        // region in relative coordinates: x lo, x hi, y lo, y hi
+    int cell, n_own, n_free, n_blk, err, acc;
+    int valid[2], idx[2], type[2], ncand[2], ntask[2], units[2], width[2];
+    P32 c[2];           // candidate of each step buffer
+    int warp_cnt[32];
+    float2 redf[32];
+    // statistics of this CTA: proposed[3], evaluated[3], accepted[3], priced
+    // samples, re-synthesised samples (thread 0)
+    unsigned long long cnt[11];
+};
+
+// carve the dynamic shared buffer; returns its size (base may be null)
+__host__ __device__ inline size_t layout32(const Geo& g, Sm* S, unsigned char* base) {
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o += (bytes + 15) & ~size_t(15);
+        return base + r;
+    };
+    const size_t E = g.ev_cap, B = g.blk_cap;
+    double *mx = (double*)take(8 * E), *my = (double*)take(8 * E), *mt = (double*)take(8 * E),
+           *mm = (double*)take(8 * E);
+    unsigned long long* eid = (unsigned long long*)take(8 * E);
+    float *exr = (float*)take(4 * E), *eyr = (float*)take(4 * E);
+    int *enarr = (int*)take(4 * E), *order = (int*)take(4 * E), *freel = (int*)take(4 * E);
+    A32* earr = (A32*)take(sizeof(A32) * E * g.arr_cap);
+    double *tabB = (double*)take(8 * (E + 1)), *tabD = (double*)take(8 * (E + 1));
+    int* bsta = (int*)take(4 * B);
+    double *bx = (double*)take(8 * B), *by = (double*)take(8 * B);
+    int* scnt = (int*)take(4 * B);
+    SA* sarr = (SA*)take(sizeof(SA) * B * g.frz_cap);
+    D32* draws = (D32*)take(sizeof(D32) * (size_t)g.k);
+    A32* cand = (A32*)take(sizeof(A32) * 2 * (size_t)g.arr_cap);
+    T32* tasks = (T32*)take(sizeof(T32) * 2 * kMaxTasks32);
+    double *nx = (double*)take(8 * E), *ny = (double*)take(8 * E), *nt = (double*)take(8 * E);
+    float *nph = (float*)take(4 * E), *nmf = (float*)take(4 * E);
+    int* nK = (int*)take(4 * E);
+    int* tsoff = (int*)take(4 * 2 * kMaxTasks32);
+    const size_t scap = (size_t)g.stage_cap;
+    float* stage_s = scap ? (float*)take(4 * 2 * scap) : nullptr;
+    float* stage_v = scap ? (float*)take(4 * 2 * scap) : nullptr;
+    if (S) {
+        S->tsoff = tsoff;
+        S->stage_s = stage_s;
+        S->stage_v = stage_v;
+        S->scap = (int)scap;
+        S->mx = mx; S->my = my; S->mt = mt; S->mm = mm; S->eid = eid; S->exr = exr; S->eyr = eyr;
+        S->enarr = enarr; S->order = order; S->freel = freel; S->earr = earr;
+        S->tabB = tabB; S->tabD = tabD; S->bsta = bsta; S->bx = bx; S->by = by;
+        S->scnt = scnt; S->sarr = sarr; S->draws = draws; S->cand = cand; S->tasks = tasks;
+        S->nx = nx; S->ny = ny; S->nt = nt; S->nph = nph; S->nmf = nmf; S->nK = nK;
+    }
+    return o;
+}
 
 __device__ __forceinline__ void kahan_add32(float& s, float& c, float x) {
     const float y = x - c;
@@ -110,24 +183,53 @@ __device__ __forceinline__ float2 ff_add32(float2 a, float2 b) {
     return make_float2(hi, lo - (hi - s));
 }
 
-// ordered append across the block (see cmh_sweep.cu)
-__device__ __forceinline__ int block_append32(bool flag, int* s_warp, int* s_base) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const unsigned bal = __ballot_sync(FULL, flag);
-    if (lane == 0) s_warp[wid] = __popc(bal);
-    __syncthreads();
-    int before = 0, all = 0;
-    for (int w = 0; w < nw; ++w) {
-        const int c = s_warp[w];
-        if (w < wid) before += c;
-        all += c;
-    }
-    const int pos = *s_base + before + __popc(bal & ((1u << lane) - 1));
-    __syncthreads();
-    if (threadIdx.x == 0) *s_base += all;
-    __syncthreads();
-    return pos;
+// 1/x by the SFU (relative error ~1 ulp)
+__device__ __forceinline__ float rcp_sfu(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
+
+// ---- bulk copies and mbarriers (inline PTX) ---------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// one arrival that also announces `bytes` of transactions to come
+__device__ __forceinline__ void mbar_arm(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// wait for the phase with this parity to complete, at most kWaitLimit tries
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (unsigned i = 0; i < kWaitLimit; ++i)
+        if (mbar_test(bar, parity)) return true;
+    return false;
+}
+
+// global -> shared bulk copy (both addresses 16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // uniform in (0, 1] from the top 32 bits, as a float (relative precision
 // 2^-24 even for small values, so its log is accurate to ~6e-8)
@@ -146,156 +248,450 @@ __device__ __forceinline__ double mag_from_u53(unsigned long long w) {
     return 2.0 + 0.69314718055994530942 * (double)(53 - e) - (double)(0.69314718f * lm);
 }
 
-// relative float form of a float64 event (region tests) and its float32 terms
-__device__ __forceinline__ void to_rel(const Geo& g, double X0, double Y0, double x, double y, double t, double m,
-                                       float& xr, float& yr, float& ph, float& mf, int& K) {
-    xr = (float)__dsub_rn(x, X0);
-    yr = (float)__dsub_rn(y, Y0);
-    event_terms32(g, t, m, K, ph, mf);
+// region-relative position and float32 terms of a float64 event
+__device__ __forceinline__ void to_rel(const Geo& g, double X0, double Y0, P32& e) {
+    e.xr = (float)__dsub_rn(e.x, X0);
+    e.yr = (float)__dsub_rn(e.y, Y0);
+    event_terms32(g, e.t, e.m, e.K, e.ph, e.mf);
 }
 
-__global__ void __launch_bounds__(kThreads32, 3) phase32_kernel(Geo g, Dev d, int colour) {
+// the exact float64 region / range test of a candidate (the oracle's)
+__device__ __noinline__ bool inside_exact(const Geo& g, double sx, double sy, int cell, double x, double y, double t,
+                                          double m) {
+    return x >= 0.0 && x < g.W && y >= 0.0 && y < g.W && cell_of(g, sx, sy, x, y) == cell && t >= 0.0 && t < g.T &&
+           m >= 2.0;
+}
+
+// ---------------------------------------------------------------------------
+// preparation of one step (all lanes of warp 0): decode the proposal against
+// the current state, find the stations the candidate reaches, and merge the
+// old and new arrivals into tasks (one per station whose variance changes)
+// in step buffer sl; with STAGE, start the bulk copies of the task windows
+// ---------------------------------------------------------------------------
+template <bool STAGE>
+__device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int step, int sl) {
+    const int lane = threadIdx.x & 31;
+    if (STAGE) {
+        // copies of an earlier preparation of this buffer may still be in
+        // flight: let them land before the buffer is reused
+        if (lane == 0 && S.on[sl]) {
+            if (!mbar_wait(&S.bar[sl], (unsigned)S.ph[sl])) S.err = CMH_ERR_TIMEOUT;
+            S.ph[sl] ^= 1;
+            S.on[sl] = 0;
+        }
+        __syncwarp();
+    }
+    const D32& dr = S.draws[step];
+    const int n_own = S.n_own, n_blk = S.n_blk;
+    A32* cd = S.cand + sl * g.arr_cap;
+    T32* tk = S.tasks + sl * kMaxTasks32;
+    int valid = 0, idx = -1, ps = -1;
+    P32 c;
+    c.x = c.y = c.t = c.m = 0.0;
+    c.xr = c.yr = c.ph = c.mf = 0.f;
+    c.K = 0;
+    c.pad = 0;
+    if (dr.type == 0) {
+        valid = dr.bvalid;
+        c.x = dr.bx; c.y = dr.by; c.t = dr.bt; c.m = dr.bm;
+        c.xr = dr.xr; c.yr = dr.yr; c.ph = dr.ph; c.mf = dr.mf; c.K = dr.bK;
+    } else if (n_own > 0) {
+        idx = pick32(dr.pickw, n_own);
+        ps = S.order[idx];
+        if (dr.type == 1) {
+            valid = 1;
+        } else {
+            // the float64 state the move proposes, its float32 terms, and the
+            // region-relative position for the region test
+            c.x = __dadd_rn(S.mx[ps], (double)dr.xr);
+            c.y = __dadd_rn(S.my[ps], (double)dr.yr);
+            c.t = __dadd_rn(S.mt[ps], (double)dr.ph);
+            c.m = __dadd_rn(S.mm[ps], (double)dr.mf);
+            event_terms32(g, c.t, c.m, c.K, c.ph, c.mf);
+            c.xr = S.exr[ps] + dr.xr;
+            c.yr = S.eyr[ps] + dr.yr;
+            const bool xin = c.xr >= S.rl[0] + kDr && c.xr < S.rl[1] - kDr;
+            const bool yin = c.yr >= S.rl[2] + kDr && c.yr < S.rl[3] - kDr;
+            const bool xout = c.xr < S.rl[0] - kDr || c.xr >= S.rl[1] + kDr;
+            const bool yout = c.yr < S.rl[2] - kDr || c.yr >= S.rl[3] + kDr;
+            const bool tin = c.K >= 1 && c.K + 2 <= g.TfK;
+            const bool min_ = c.mf >= 2.f + kDm;
+            const bool mout = c.mf < 2.f - kDm;
+            if (xout || yout || mout) {
+                valid = 0;
+            } else if (xin && yin && tin && min_) {
+                valid = 1;
+            } else {
+                valid = inside_exact(g, S.sx, S.sy, S.cell, c.x, c.y, c.t, c.m);
+                if (valid) to_rel(g, S.X0, S.Y0, c);
+            }
+        }
+    }
+    // candidate arrivals, lanes over blanket slots, compacted in slot order
+    int ncand = 0;
+    if (valid && dr.type != 1) {
+        for (int b0 = 0; b0 < n_blk; b0 += 32) {
+            const int b = b0 + lane;
+            int k0 = 0;
+            float E0 = 0.f;
+            const bool r = b < n_blk && arrival32c(g, c.x, c.y, c.t, c.K, c.ph, c.mf, S.bx[b], S.by[b], k0, E0);
+            const unsigned bal = __ballot_sync(FULL, r);
+            const int pos = ncand + __popc(bal & ((1u << lane) - 1));
+            if (r && pos < g.arr_cap) cd[pos] = A32{b, k0, E0, 0};
+            ncand += __popc(bal);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        int err = ncand > g.arr_cap ? CMH_ERR_CAPACITY : 0;
+        int ntask = 0, units = 0, width = 0;
+        if (valid && !err) {
+            // merge the old event's arrivals and the candidate's, by slot
+            const A32* oa = (ps >= 0 && dr.type != 0) ? S.earr + ps * g.arr_cap : nullptr;
+            const int no = oa ? S.enarr[ps] : 0;
+            const int nnw = dr.type != 1 ? ncand : 0;
+            int io = 0, in = 0;
+            while (io < no || in < nnw) {
+                const int so = io < no ? oa[io].slot : 1 << 30;
+                const int sn = in < nnw ? cd[in].slot : 1 << 30;
+                if (ntask >= kMaxTasks32) {
+                    err = CMH_ERR_CAPACITY;
+                    break;
+                }
+                T32 T;
+                T.slot = so < sn ? so : sn;
+                T.row = S.bsta[T.slot];
+                T.has_o = so <= sn;
+                T.has_n = sn <= so;
+                T.k0o = T.k0n = 0;
+                T.E0o = T.E0n = 0.f;
+                T.skip = dr.type == 0 ? -1 : ps;
+                int lo = 1 << 30, hi = -1;
+                if (T.has_o) {
+                    const A32 A = oa[io++];
+                    T.k0o = A.k0; T.E0o = A.E0;
+                    lo = min(lo, A.k0);
+                    hi = max(hi, A.k0 + g.n_w);
+                }
+                if (T.has_n) {
+                    const A32 A = cd[in++];
+                    T.k0n = A.k0; T.E0n = A.E0;
+                    lo = min(lo, A.k0);
+                    hi = max(hi, A.k0 + g.n_w);
+                }
+                lo = max(lo, 0);
+                hi = (long long)hi > g.n_samp ? (int)g.n_samp : hi;
+                T.lo = lo;
+                T.hi = hi;
+                if (lo < hi) {
+                    T.u0 = units;   // float4 groups [lo/4, ceil(hi/4)) continue the flat range
+                    units += ((hi + 3) >> 2) - (lo >> 2);
+                    width += hi - lo;
+                    tk[ntask++] = T;
+                }
+            }
+        }
+        if (STAGE && !err && ntask > 0) {
+            // stage the windows that fit (in task order) into this step's buffer
+            int* so = S.tsoff + sl * kMaxTasks32;
+            int used = 0;
+            unsigned bytes = 0;
+            for (int ti = 0; ti < ntask; ++ti) {
+                const int w4 = ((tk[ti].hi + 3) & ~3) - (tk[ti].lo & ~3);
+                so[ti] = -1;
+                if (used + w4 <= S.scap) {
+                    so[ti] = used;
+                    used += w4;
+                    bytes += 8u * (unsigned)w4;
+                }
+            }
+            if (bytes) {
+                mbar_arm(&S.bar[sl], bytes);
+                for (int ti = 0; ti < ntask; ++ti) {
+                    if (so[ti] < 0) continue;
+                    const int lo4 = tk[ti].lo & ~3;
+                    const unsigned nb = 4u * (unsigned)(((tk[ti].hi + 3) & ~3) - lo4);
+                    const size_t off = (size_t)tk[ti].row * g.pitch + lo4;
+                    bulk_g2s(S.stage_s + sl * S.scap + so[ti], (const float*)d.sig + off, nb, &S.bar[sl]);
+                    bulk_g2s(S.stage_v + sl * S.scap + so[ti], (const float*)d.V + off, nb, &S.bar[sl]);
+                }
+                S.on[sl] = 1;
+            }
+        }
+        if (err) S.err = err;
+        S.valid[sl] = valid && !err;
+        S.ntask[sl] = ntask;
+        S.units[sl] = units;
+        S.width[sl] = width;
+        S.idx[sl] = idx;
+        S.type[sl] = dr.type;
+        S.ncand[sl] = ncand;
+        S.c[sl] = c;
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// pricing of step buffer sl by warps 1..: the change of the Gaussian
+// log-likelihood over the float4 groups of all tasks (one flat range; each
+// thread issues the loads of kUnroll groups before computing them), one
+// float-float partial per warp in S.redf
+// ---------------------------------------------------------------------------
+template <bool STAGE>
+__device__ __forceinline__ void price_step(const Geo& g, const Dev& d, Sm& S, int sl) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const T32* tk = S.tasks + sl * kMaxTasks32;
+    const int U = S.units[sl], ntask = S.ntask[sl];
+    const int wt = threadIdx.x - 32, nwk = blockDim.x - 32;
+    const int* so = S.tsoff + sl * kMaxTasks32;
+    const float* ss = STAGE ? S.stage_s + sl * S.scap : nullptr;
+    const float* sv_ = STAGE ? S.stage_v + sl * S.scap : nullptr;
+    if (STAGE && S.on[sl] && !mbar_wait(&S.bar[sl], (unsigned)S.ph[sl])) atomicCAS(&S.err, 0, CMH_ERR_TIMEOUT);
+    float acc = 0.f, comp = 0.f;
+    for (int u0 = wt; u0 < U; u0 += nwk * kUnroll) {
+        float4 s4[kUnroll], v4[kUnroll];
+        int ti_[kUnroll], k_[kUnroll];
+#pragma unroll
+        for (int r = 0; r < kUnroll; ++r) {
+            const int u = u0 + r * nwk;
+            ti_[r] = -1;
+            k_[r] = 0;
+            if (u < U) {
+                int ti = 0;
+                while (ti + 1 < ntask && u >= tk[ti + 1].u0) ++ti;
+                const T32& T = tk[ti];
+                const int k = ((T.lo >> 2) + (u - T.u0)) << 2;
+                ti_[r] = ti;
+                k_[r] = k;
+                const int o = STAGE ? so[ti] : -1;
+                if (STAGE && o >= 0) {
+                    s4[r] = *reinterpret_cast<const float4*>(ss + o + (k - (T.lo & ~3)));
+                    v4[r] = *reinterpret_cast<const float4*>(sv_ + o + (k - (T.lo & ~3)));
+                } else {
+                    s4[r] = __ldg(reinterpret_cast<const float4*>((const float*)d.sig + (size_t)T.row * g.pitch + k));
+                    v4[r] = *reinterpret_cast<const float4*>((const float*)d.V + (size_t)T.row * g.pitch + k);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kUnroll; ++r) {
+            if (ti_[r] < 0) continue;
+            const T32& T = tk[ti_[r]];
+            const int k4 = k_[r];
+            // one SFU evaluation per arrival for the whole group (see arr_var32)
+            const float bo = T.has_o ? arr_base32(g, T.E0o, T.k0o, k4) : 0.f;
+            const float bn = T.has_n ? arr_base32(g, T.E0n, T.k0n, k4) : 0.f;
+            const float sv[4] = {s4[r].x, s4[r].y, s4[r].z, s4[r].w};
+            const float vv[4] = {v4[r].x, v4[r].y, v4[r].z, v4[r].w};
+            float gs = 0.f;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int kk = k4 + e;
+                const bool io = T.has_o && (unsigned)(kk - T.k0o) < (unsigned)g.n_w;
+                const bool inn = T.has_n && (unsigned)(kk - T.k0n) < (unsigned)g.n_w;
+                // the same per-sample values the variance synthesis adds, so the
+                // priced change is the change written to V on accept
+                const float co = io ? __fmul_rn(bo, g.rho_f[e]) : 0.f;
+                const float cn = inn ? __fmul_rn(bn, g.rho_f[e]) : 0.f;
+                const float dd = cn - co;
+                if (kk < T.hi && dd != 0.f) {
+                    const float V = vv[e], sm = sv[e];
+                    const float Vp = V + dd;
+                    float term;
+                    if (Vp < 0.5f * V) {
+                        // the changed arrival dominates V: rebuild V' from the arrivals
+                        // that stay on this station
+                        float a2 = g.noise_f, c2 = 0.f;
+                        const SA* L = S.sarr + T.slot * g.frz_cap;
+                        const int nl = S.scnt[T.slot];
+                        for (int o = 0; o < nl; ++o) {
+                            const SA A = L[o];
+                            if (A.own != T.skip && (unsigned)(kk - A.k0) < (unsigned)g.n_w)
+                                kahan_add32(a2, c2, arr_var32(g, A.E0, A.k0, kk));
+                        }
+                        if (inn) kahan_add32(a2, c2, cn);
+                        const float Vr = a2 - c2;
+                        term = __logf(__fdividef(Vr, V)) + sm * sm * (rcp_sfu(Vr) - rcp_sfu(V));
+                    } else {
+                        // log(V'/V) - s^2 d / (V V'), one reciprocal
+                        const float inv = rcp_sfu(V * Vp);
+                        term = log1p_fast(dd * Vp * inv) - sm * sm * dd * inv;
+                    }
+                    gs += -0.5f * term;
+                }
+            }
+            kahan_add32(acc, comp, gs);
+        }
+    }
+    float2 v = make_float2(acc, -comp);
+    for (int o = 16; o > 0; o >>= 1) {
+        float2 w2;
+        w2.x = __shfl_xor_sync(FULL, v.x, o);
+        w2.y = __shfl_xor_sync(FULL, v.y, o);
+        v = ff_add32(v, w2);
+    }
+    if (lane == 0) S.redf[wid] = v;
+}
+
+// remove the arrivals of own event ps from its stations' lists (stable)
+__device__ __forceinline__ void lists_remove(const Geo& g, Sm& S, int ps) {
+    for (int a = 0; a < S.enarr[ps]; ++a) {
+        const int b = S.earr[ps * g.arr_cap + a].slot;
+        SA* L = S.sarr + b * g.frz_cap;
+        const int n = S.scnt[b];
+        int w = 0;
+        for (int i = 0; i < n; ++i)
+            if (L[i].own != ps) L[w++] = L[i];
+        S.scnt[b] = w;
+    }
+}
+
+// append the arrivals A[0..na) of own event ps to their stations' lists
+__device__ __forceinline__ void lists_add(const Geo& g, Sm& S, int ps, const A32* A, int na) {
+    for (int a = 0; a < na; ++a) {
+        const int b = A[a].slot;
+        const int n = S.scnt[b];
+        if (n >= g.frz_cap) {
+            S.err = CMH_ERR_CAPACITY;
+            return;
+        }
+        S.sarr[b * g.frz_cap + n] = SA{A[a].k0, A[a].E0, ps, 0};
+        S.scnt[b] = n + 1;
+    }
+}
+
+template <bool STAGE>
+__global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const __grid_constant__ Geo g,
+                                                                           const __grid_constant__ Dev d, int colour) {
     if (*d.status) return;
     const long long sweep = *d.sweep;
     if ((int)blockIdx.x >= d.colour_count[colour]) return;
     const int cell = d.colour_cells[colour * g.max_rpc + blockIdx.x];
-    const Store S = d.st[sweep & 1];
-    const double sx = d.shift[0], sy = d.shift[1];
-    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    const Store St = d.st[sweep & 1];
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
     const int ix = cell % g.ncx, iy = cell / g.ncx;
 
     extern __shared__ __align__(16) unsigned char smem[];
-    const L32 Lo(g);
-    double* mx = (double*)(smem + Lo.mx);
-    double* my = (double*)(smem + Lo.my);
-    double* mt = (double*)(smem + Lo.mt);
-    double* mm = (double*)(smem + Lo.mm);
-    unsigned long long* eid = (unsigned long long*)(smem + Lo.id);
-    float* exr = (float*)(smem + Lo.xr);
-    float* eyr = (float*)(smem + Lo.yr);
-    float* eph = (float*)(smem + Lo.ph);
-    float* emf = (float*)(smem + Lo.mf);
-    int* eK = (int*)(smem + Lo.K);
-    int* enarr = (int*)(smem + Lo.narr);
-    A32* earr = (A32*)(smem + Lo.arr);
-    int* order = (int*)(smem + Lo.order);
-    int* freel = (int*)(smem + Lo.freel);
-    double* tabB = (double*)(smem + Lo.tabB);
-    double* tabD = (double*)(smem + Lo.tabD);
-    int* bsta = (int*)(smem + Lo.bsta);
-    double* bx = (double*)(smem + Lo.bx);
-    double* by = (double*)(smem + Lo.by);
-    int* fcnt = (int*)(smem + Lo.fcnt);
-    F32a* farr = (F32a*)(smem + Lo.farr);
-    D32* draws = (D32*)(smem + Lo.draws);
-    A32* cand = (A32*)(smem + Lo.cand);
-    T32* tasks = (T32*)(smem + Lo.tasks);
-    F32a* pool = (F32a*)(smem + Lo.pool);
-    double* nx = (double*)(smem + Lo.nx);
-    double* ny = (double*)(smem + Lo.ny);
-    double* nt = (double*)(smem + Lo.nt);
-    double* nmm = (double*)(smem + Lo.nmm);
-    float* nxr = (float*)(smem + Lo.nxr);
-    float* nyr = (float*)(smem + Lo.nyr);
-    float* nph = (float*)(smem + Lo.nph);
-    float* nmf = (float*)(smem + Lo.nmf);
-    int* nK = (int*)(smem + Lo.nK);
-
-    __shared__ double s_rect[4], s_X0, s_Y0, s_region_dlp;
-    __shared__ float s_rl[4];   // region in relative coordinates: x lo, x hi, y lo, y hi
-    __shared__ int s_n_own, s_n_free, s_n_blk, s_err, s_valid, s_idx, s_type, s_ncand, s_ntask, s_acc;
-    __shared__ int s_warp[32], s_base;
-    __shared__ float2 s_redf[32];
-    __shared__ P32 s_cand;
-
-    const int start = S.start[cell], n0 = S.count[cell];
+    __shared__ Sm S;
+    const int start = St.start[cell], n0 = St.count[cell];
     if (tid == 0) {
-        cell_rect(g, sx, sy, cell, s_rect);
-        s_X0 = __dadd_rn(sx, __dmul_rn((double)(ix - 1), g.L));
-        s_Y0 = __dadd_rn(sy, __dmul_rn((double)(iy - 1), g.L));
-        s_rl[0] = (float)(s_rect[0] - s_X0);
-        s_rl[1] = (float)(s_rect[1] - s_X0);
-        s_rl[2] = (float)(s_rect[2] - s_Y0);
-        s_rl[3] = (float)(s_rect[3] - s_Y0);
-        s_err = (n0 + g.k > g.ev_cap) ? CMH_ERR_CAPACITY : 0;
-        s_n_own = n0;
-        s_n_free = g.ev_cap - n0;
-        s_base = 0;
-        s_region_dlp = 0.0;
+        layout32(g, &S, smem);
+        S.cell = cell;
+        S.sx = d.shift[0];
+        S.sy = d.shift[1];
+        cell_rect(g, S.sx, S.sy, cell, S.rect);
+        S.X0 = __dadd_rn(S.sx, __dmul_rn((double)(ix - 1), g.L));
+        S.Y0 = __dadd_rn(S.sy, __dmul_rn((double)(iy - 1), g.L));
+        S.rl[0] = (float)(S.rect[0] - S.X0);
+        S.rl[1] = (float)(S.rect[1] - S.X0);
+        S.rl[2] = (float)(S.rect[2] - S.Y0);
+        S.rl[3] = (float)(S.rect[3] - S.Y0);
+        S.err = (n0 + g.k > g.ev_cap) ? CMH_ERR_CAPACITY : 0;
+        S.n_own = n0;
+        S.n_free = g.ev_cap - n0;
+        S.region_dlp = 0.0;
+        S.acc = 0;
+        for (int b = 0; b < 2; ++b) {
+            S.ph[b] = 0;
+            S.on[b] = 0;
+            if (STAGE) mbar_init(&S.bar[b], 1);
+        }
+        if (STAGE) fence_async_shared();   // the initialised barriers are visible to the async proxy
     }
+    if (tid < 11) S.cnt[tid] = 0;
     __syncthreads();
-    if (s_err) {
-        if (tid == 0) latch(d.status, s_err);
+    if (S.err) {
+        if (tid == 0) latch(d.status, S.err);
         return;
     }
-    const double X0 = s_X0, Y0 = s_Y0;
-    // ---- own events: masters, relative form, free list --------------------------
+    const double X0 = S.X0, Y0 = S.Y0;
+    // ---- own events: masters, relative position, free list ----------------------
     for (int i = tid; i < g.ev_cap; i += nthr) {
         if (i < n0) {
-            const double x = S.x[start + i], y = S.y[start + i], t = S.t[start + i], m = S.m[start + i];
-            mx[i] = x; my[i] = y; mt[i] = t; mm[i] = m;
-            eid[i] = S.id[start + i];
-            to_rel(g, X0, Y0, x, y, t, m, exr[i], eyr[i], eph[i], emf[i], eK[i]);
-            order[i] = i;
+            const double x = St.x[start + i], y = St.y[start + i];
+            S.mx[i] = x; S.my[i] = y; S.mt[i] = St.t[start + i]; S.mm[i] = St.m[start + i];
+            S.exr[i] = (float)__dsub_rn(x, X0);
+            S.eyr[i] = (float)__dsub_rn(y, Y0);
+            S.eid[i] = St.id[start + i];
+            S.order[i] = i;
         } else {
-            freel[g.ev_cap - 1 - i] = i;
+            S.freel[g.ev_cap - 1 - i] = i;   // pops give the lowest free slot first
         }
     }
-    // ---- acceptance constants: log(beta / q_b) = log(Lambda area / W^2) ----------
+    // ---- acceptance constants: log(beta / q_b) = log(Lambda area / W^2) --------
     {
-        const double area = (s_rect[1] - s_rect[0]) * (s_rect[3] - s_rect[2]);
+        const double area = (S.rect[1] - S.rect[0]) * (S.rect[3] - S.rect[2]);
         const double Cb = g.Cb0 + (double)logf((float)area);
         for (int n = tid; n <= g.ev_cap; n += nthr) {
-            tabB[n] = Cb - d.log_n[n + 1];
-            tabD[n] = n > 0 ? -Cb + d.log_n[n] : 0.0;
+            S.tabB[n] = Cb - d.log_n[n + 1];
+            S.tabD[n] = n > 0 ? -Cb + d.log_n[n] : 0.0;
         }
     }
-    // ---- blanket: stations within R_max of the region (float test, margin) ------
+    // ---- blanket: stations within R_max of the region (float test, margin) ----
+    // warp w scans a contiguous chunk of stations; chunks are concatenated in
+    // order, so the blanket lists stations by index
     {
-        const float r0 = (float)s_rect[0], r1 = (float)s_rect[1], r2 = (float)s_rect[2], r3 = (float)s_rect[3];
+        const float r0 = (float)S.rect[0], r1 = (float)S.rect[1], r2 = (float)S.rect[2], r3 = (float)S.rect[3];
         const float Rm = g.R_f * 1.0001f + 1e-3f;
-        for (int base = 0; base < g.n_st; base += nthr) {
-            const int j = base + tid;
-            bool in = false;
-            if (j < g.n_st) {
-                const float fx = d.stxf[j], fy = d.styf[j];
-                const float dx = fx < r0 ? r0 - fx : (fx > r1 ? fx - r1 : 0.f);
-                const float dy = fy < r2 ? r2 - fy : (fy > r3 ? fy - r3 : 0.f);
-                in = dx * dx + dy * dy < Rm * Rm;
+        const int chunk = (g.n_st + nw - 1) / nw;
+        const int j0 = wid * chunk, j1 = min(g.n_st, j0 + chunk);
+        auto in_blanket = [&](int j) {
+            const float fx = d.stxf[j], fy = d.styf[j];
+            const float dx = fx < r0 ? r0 - fx : (fx > r1 ? fx - r1 : 0.f);
+            const float dy = fy < r2 ? r2 - fy : (fy > r3 ? fy - r3 : 0.f);
+            return dx * dx + dy * dy < Rm * Rm;
+        };
+        int cnt = 0;
+        for (int j = j0 + lane; j - lane < j1; j += 32) cnt += __popc(__ballot_sync(FULL, j < j1 && in_blanket(j)));
+        if (lane == 0) S.warp_cnt[wid] = cnt;
+        __syncthreads();
+        int pos = 0, total = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < wid) pos += S.warp_cnt[w];
+            total += S.warp_cnt[w];
+        }
+        for (int j = j0 + lane; j - lane < j1; j += 32) {
+            const bool in = j < j1 && in_blanket(j);
+            const unsigned bal = __ballot_sync(FULL, in);
+            const int p = pos + __popc(bal & ((1u << lane) - 1));
+            if (in && p < g.blk_cap) {
+                S.bsta[p] = j;
+                S.bx[p] = d.stx[j];
+                S.by[p] = d.sty[j];
             }
-            const int pos = block_append32(in, s_warp, &s_base);
-            if (in) {
-                if (pos < g.blk_cap) {
-                    const double xs = d.stx[j], ys = d.sty[j];
-                    bsta[pos] = j;
-                    bx[pos] = xs;
-                    by[pos] = ys;
-                } else {
-                    atomicCAS(&s_err, 0, CMH_ERR_CAPACITY);
-                }
-            }
+            pos += __popc(bal);
+        }
+        if (tid == 0) {
+            if (total > g.blk_cap) S.err = CMH_ERR_CAPACITY;
+            S.n_blk = min(total, g.blk_cap);
         }
         __syncthreads();
-        if (tid == 0) s_n_blk = min(s_base, g.blk_cap);
-        __syncthreads();
     }
-    const int n_blk = s_n_blk;
-    // ---- arrival cache of the own events -----------------------------------------
-    for (int i = tid; i < n0; i += nthr) {
+    const int n_blk = S.n_blk;
+    // ---- arrival cache of the own events (warp per event, lanes over slots) -----
+    for (int i = wid; i < n0; i += nw) {
+        int K;
+        float ph, mf;
+        event_terms32(g, S.mt[i], S.mm[i], K, ph, mf);
         int na = 0;
-        for (int b = 0; b < n_blk; ++b) {
-            int k0;
-            float E0;
-            if (arrival32c(g, mx[i], my[i], mt[i], eK[i], eph[i], emf[i], bx[b], by[b], k0, E0)) {
-                if (na < g.arr_cap) earr[i * g.arr_cap + na] = A32{b, k0, E0, 0};
-                ++na;
-            }
+        for (int b0 = 0; b0 < n_blk; b0 += 32) {
+            const int b = b0 + lane;
+            int k0 = 0;
+            float E0 = 0.f;
+            const bool r = b < n_blk && arrival32c(g, S.mx[i], S.my[i], S.mt[i], K, ph, mf, S.bx[b], S.by[b], k0, E0);
+            const unsigned bal = __ballot_sync(FULL, r);
+            const int p = na + __popc(bal & ((1u << lane) - 1));
+            if (r && p < g.arr_cap) S.earr[i * g.arr_cap + p] = A32{b, k0, E0, 0};
+            na += __popc(bal);
         }
-        if (na > g.arr_cap) atomicCAS(&s_err, 0, CMH_ERR_CAPACITY);
-        enarr[i] = min(na, g.arr_cap);
+        if (lane == 0) {
+            if (na > g.arr_cap) atomicCAS(&S.err, 0, CMH_ERR_CAPACITY);
+            S.enarr[i] = min(na, g.arr_cap);
+        }
     }
-    // ---- frozen arrivals: neighbouring cells (other colours), in (cell, id) order -
-    for (int b = tid; b < n_blk; b += nthr) fcnt[b] = 0;
+    // ---- station lists: arrivals of the neighbouring cells (other colours) in
+    // (cell, id) order, then the region's own events in id order
+    for (int b = tid; b < n_blk; b += nthr) S.scnt[b] = 0;
     {
         const int P1 = g.period - 1;
         for (int jy = iy - P1; jy <= iy + P1; ++jy) {
@@ -303,34 +699,69 @@ __global__ void __launch_bounds__(kThreads32, 3) phase32_kernel(Geo g, Dev d, in
                 if (jx < 0 || jy < 0 || jx >= g.ncx || jy >= g.ncy) continue;
                 const int oc = jy * g.ncx + jx;
                 if (oc == cell) continue;
-                const int s0 = S.start[oc], nn = S.count[oc];
+                const int s0 = St.start[oc], nn = St.count[oc];
                 if (nn == 0) continue;
-                __syncthreads();   // previous cell's list fully consumed
+                __syncthreads();   // the previous cell's events fully consumed
                 if (nn > g.ev_cap) {
-                    if (tid == 0) s_err = CMH_ERR_CAPACITY;
+                    if (tid == 0) S.err = CMH_ERR_CAPACITY;
                     break;
                 }
                 for (int i = tid; i < nn; i += nthr) {
-                    const double x = S.x[s0 + i], y = S.y[s0 + i], t = S.t[s0 + i], m = S.m[s0 + i];
-                    nx[i] = x; ny[i] = y; nt[i] = t; nmm[i] = m;
-                    to_rel(g, X0, Y0, x, y, t, m, nxr[i], nyr[i], nph[i], nmf[i], nK[i]);
+                    const double t = St.t[s0 + i];
+                    S.nx[i] = St.x[s0 + i];
+                    S.ny[i] = St.y[s0 + i];
+                    S.nt[i] = t;
+                    event_terms32(g, t, St.m[s0 + i], S.nK[i], S.nph[i], S.nmf[i]);
                 }
                 __syncthreads();
-                for (int b = tid; b < n_blk; b += nthr) {
-                    int nf = fcnt[b];
-                    for (int i = 0; i < nn; ++i) {
-                        int k0;
-                        float E0;
-                        if (arrival32c(g, nx[i], ny[i], nt[i], nK[i], nph[i], nmf[i], bx[b], by[b], k0, E0)) {
-                            if (nf < g.frz_cap) farr[b * g.frz_cap + nf] = F32a{k0, E0};
-                            ++nf;
-                        }
+                for (int b = wid; b < n_blk; b += nw) {
+                    int nf = S.scnt[b];
+                    for (int i0 = 0; i0 < nn; i0 += 32) {
+                        const int i = i0 + lane;
+                        int k0 = 0;
+                        float E0 = 0.f;
+                        const bool r = i < nn && arrival32c(g, S.nx[i], S.ny[i], S.nt[i], S.nK[i], S.nph[i], S.nmf[i],
+                                                            S.bx[b], S.by[b], k0, E0);
+                        const unsigned bal = __ballot_sync(FULL, r);
+                        const int p = nf + __popc(bal & ((1u << lane) - 1));
+                        if (r && p < g.frz_cap) S.sarr[b * g.frz_cap + p] = SA{k0, E0, kFrozen, 0};
+                        nf += __popc(bal);
                     }
-                    if (nf > g.frz_cap) atomicCAS(&s_err, 0, CMH_ERR_CAPACITY);
-                    fcnt[b] = min(nf, g.frz_cap);
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (nf > g.frz_cap) atomicCAS(&S.err, 0, CMH_ERR_CAPACITY);
+                        S.scnt[b] = min(nf, g.frz_cap);
+                    }
+                    __syncwarp();
                 }
             }
         }
+    }
+    __syncthreads();
+    for (int b = wid; b < n_blk; b += nw) {
+        int nf = S.scnt[b];
+        for (int q0 = 0; q0 < n0; q0 += 32) {
+            const int q = q0 + lane;
+            bool hit = false;
+            SA A = {0, 0.f, q, 0};
+            if (q < n0)
+                for (int a = 0; a < S.enarr[q]; ++a)
+                    if (S.earr[q * g.arr_cap + a].slot == b) {
+                        hit = true;
+                        A.k0 = S.earr[q * g.arr_cap + a].k0;
+                        A.E0 = S.earr[q * g.arr_cap + a].E0;
+                    }
+            const unsigned bal = __ballot_sync(FULL, hit);
+            const int p = nf + __popc(bal & ((1u << lane) - 1));
+            if (hit && p < g.frz_cap) S.sarr[b * g.frz_cap + p] = A;
+            nf += __popc(bal);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            if (nf > g.frz_cap) atomicCAS(&S.err, 0, CMH_ERR_CAPACITY);
+            S.scnt[b] = min(nf, g.frz_cap);
+        }
+        __syncwarp();
     }
     // ---- the k steps' random draws (Philox stream 0, counter (sweep, cell, step, 0|1))
     const unsigned long long thr_b = (unsigned long long)ceil(g.p_birth * 9007199254740992.0);
@@ -341,23 +772,29 @@ __global__ void __launch_bounds__(kThreads32, 3) phase32_kernel(Geo g, Dev d, in
         philox4x64(c0, g.seed, 0ULL);
         philox4x64(c1, g.seed, 0ULL);
         D32 D;
-        const unsigned long long u53 = c0[0] >> 11;   // u < p  <=>  u53 < p 2^53 (p 2^53 rounded up)
+        const unsigned long long u53 = c0[0] >> 11;   // u < p  <=>  u53 < p 2^53 (rounded up)
         D.type = u53 < thr_b ? 0 : (u53 < thr_d ? 1 : 2);
         D.pickw = (unsigned)(c0[1] & 0xffffffffULL);
         D.logu = __logf(u32o(c1[2]));
         D.bvalid = 0;
         D.bK = 0;
+        D.pad = 0;
         D.bx = D.by = D.bt = D.bm = D.blb = 0.0;
         if (D.type == 0) {
-            const double x = __dadd_rn(s_rect[0], __dmul_rn(u01(c0[2]), __dsub_rn(s_rect[1], s_rect[0])));
-            const double y = __dadd_rn(s_rect[2], __dmul_rn(u01(c0[3]), __dsub_rn(s_rect[3], s_rect[2])));
-            const double t = __dmul_rn(u01(c1[0]), g.T);
-            const double m = mag_from_u53(c1[1]);
-            D.bx = x; D.by = y; D.bt = t; D.bm = m;
-            D.blb = g.lb0 - m;
-            D.bvalid = x >= 0.0 && x < g.W && y >= 0.0 && y < g.W && cell_of(g, sx, sy, x, y) == cell &&
-                       t >= 0.0 && t < g.T && m >= 2.0;
-            to_rel(g, X0, Y0, x, y, t, m, D.xr, D.yr, D.ph, D.mf, D.bK);
+            P32 e;
+            e.x = __dadd_rn(S.rect[0], __dmul_rn(u01(c0[2]), __dsub_rn(S.rect[1], S.rect[0])));
+            e.y = __dadd_rn(S.rect[2], __dmul_rn(u01(c0[3]), __dsub_rn(S.rect[3], S.rect[2])));
+            e.t = __dmul_rn(u01(c1[0]), g.T);
+            e.m = mag_from_u53(c1[1]);
+            to_rel(g, X0, Y0, e);
+            D.bx = e.x; D.by = e.y; D.bt = e.t; D.bm = e.m;
+            D.blb = g.lb0 - e.m;
+            D.xr = e.xr; D.yr = e.yr; D.ph = e.ph; D.mf = e.mf; D.bK = e.K;
+            // inside [r0, r1) x [r2, r3) by construction up to rounding at the
+            // edges: decide in float32 away from them, exactly near them
+            const bool sure = e.xr >= S.rl[0] + kDr && e.xr < S.rl[1] - kDr && e.yr >= S.rl[2] + kDr &&
+                              e.yr < S.rl[3] - kDr && e.K >= 1 && e.K + 2 <= g.TfK;
+            D.bvalid = sure || inside_exact(g, S.sx, S.sy, cell, e.x, e.y, e.t, e.m);
         } else if (D.type == 2) {
             const float u2 = (float)(c0[3] >> 40) * (1.0f / 16777216.0f);
             const float u4 = (float)(c1[1] >> 40) * (1.0f / 16777216.0f);
@@ -367,6 +804,7 @@ __global__ void __launch_bounds__(kThreads32, 3) phase32_kernel(Geo g, Dev d, in
             __sincosf(6.2831853071795865f * u4, &s2, &co2);
             float z[4] = {r1 * co1, r1 * s1, r2 * co2, r2 * s2};
             const float sg[4] = {(float)g.sig_xy, (float)g.sig_xy, (float)g.sig_t, (float)g.sig_m};
+#pragma unroll
             for (int i = 0; i < 4; ++i) {
                 float q = rintf(fabsf(z[i]) * 1048576.f) * (1.f / 1048576.f);
                 if ((c0[1] >> (32 + i)) & 1ULL) q = -q;
@@ -376,370 +814,214 @@ __global__ void __launch_bounds__(kThreads32, 3) phase32_kernel(Geo g, Dev d, in
         } else {
             D.xr = D.yr = D.ph = D.mf = 0.f;
         }
-        draws[st] = D;
+        S.draws[st] = D;
     }
     __syncthreads();
-    if (s_err) {
-        if (tid == 0) latch(d.status, s_err);
+    if (S.err) {
+        if (tid == 0) latch(d.status, S.err);
         return;
     }
 
-    unsigned long long n_prop[3] = {0, 0, 0}, n_eval[3] = {0, 0, 0}, n_acc[3] = {0, 0, 0};
-    unsigned long long n_priced = 0, n_rewritten = 0;
-
+    if (wid == 0) prepare_step<STAGE>(g, d, S, 0, 0);
+    __syncthreads();
     for (int step = 0; step < g.k; ++step) {
-        // ===================== control (warp 0) =====================
+        const int sl = step & 1;
+        if (S.err) break;
+        const int valid = S.valid[sl];
+        // ================ prepare step+1 (warp 0) || price step (warps 1..) =========
         if (wid == 0) {
-            const D32& dr = draws[step];
-            const int n_own = s_n_own;
-            int valid = 0, idx = -1, ps = -1;
-            P32 c;
-            c.xr = c.yr = c.ph = c.mf = 0.f;
-            c.K = 0;
-            c.x = c.y = c.t = c.m = 0.0;
-            if (dr.type == 0) {
-                valid = dr.bvalid;
-                c.xr = dr.xr; c.yr = dr.yr; c.ph = dr.ph; c.mf = dr.mf; c.K = dr.bK;
-                c.x = dr.bx; c.y = dr.by; c.t = dr.bt; c.m = dr.bm;
-            } else if (n_own > 0) {
-                idx = pick32(dr.pickw, n_own);
-                ps = order[idx];
-                if (dr.type == 1) {
-                    valid = 1;
-                } else {
-                    // masters of the candidate (what the state becomes on accept), their
-                    // float32 terms, and region-relative coordinates for the region test
-                    c.x = __dadd_rn(mx[ps], (double)dr.xr);
-                    c.y = __dadd_rn(my[ps], (double)dr.yr);
-                    c.t = __dadd_rn(mt[ps], (double)dr.ph);
-                    c.m = __dadd_rn(mm[ps], (double)dr.mf);
-                    event_terms32(g, c.t, c.m, c.K, c.ph, c.mf);
-                    c.xr = exr[ps] + dr.xr;
-                    c.yr = eyr[ps] + dr.yr;
-                    // region, domain, time, magnitude: float test, exact inside the margins
-                    const bool xin = c.xr >= s_rl[0] + kDr && c.xr < s_rl[1] - kDr;
-                    const bool yin = c.yr >= s_rl[2] + kDr && c.yr < s_rl[3] - kDr;
-                    const bool xout = c.xr < s_rl[0] - kDr || c.xr >= s_rl[1] + kDr;
-                    const bool yout = c.yr < s_rl[2] - kDr || c.yr >= s_rl[3] + kDr;
-                    const bool tin = c.K >= 1 && c.K + 2 <= g.TfK;
-                    const bool min_ = c.mf >= 2.f + kDm;
-                    const bool mout = c.mf < 2.f - kDm;
-                    if (xout || yout || mout) {
-                        valid = 0;
-                    } else if (xin && yin && tin && min_) {
-                        valid = 1;
-                    } else {
-                        valid = c.x >= 0.0 && c.x < g.W && c.y >= 0.0 && c.y < g.W &&
-                                cell_of(g, sx, sy, c.x, c.y) == cell && c.t >= 0.0 && c.t < g.T && c.m >= 2.0;
-                        if (valid) to_rel(g, X0, Y0, c.x, c.y, c.t, c.m, c.xr, c.yr, c.ph, c.mf, c.K);
-                    }
-                }
-            }
-            // candidate arrivals, lanes over blanket slots, compacted in slot order
-            int ncand = 0;
-            if (valid && dr.type != 1) {
-                for (int b0 = 0; b0 < n_blk; b0 += 32) {
-                    const int b = b0 + lane;
-                    int k0 = 0;
-                    float E0 = 0.f;
-                    const bool r = b < n_blk && arrival32c(g, c.x, c.y, c.t, c.K, c.ph, c.mf, bx[b], by[b], k0, E0);
-                    const unsigned bal = __ballot_sync(FULL, r);
-                    const int pos = ncand + __popc(bal & ((1u << lane) - 1));
-                    if (r && pos < g.arr_cap) cand[pos] = A32{b, k0, E0, 0};
-                    ncand += __popc(bal);
-                }
-            }
-            __syncwarp();
-            int err = ncand > g.arr_cap ? CMH_ERR_CAPACITY : 0;
-            int ntask = 0, npool = 0;
-            if (valid && !err) {
-                const A32* oa = (ps >= 0 && dr.type != 0) ? earr + ps * g.arr_cap : nullptr;
-                const int no = oa ? enarr[ps] : 0;
-                const int nnw = dr.type != 1 ? ncand : 0;
-                int io = 0, in = 0;
-                while (io < no || in < nnw) {
-                    const int so = io < no ? oa[io].slot : 1 << 30;
-                    const int sn = in < nnw ? cand[in].slot : 1 << 30;
-                    if (ntask >= kMaxTasks32) { err = CMH_ERR_CAPACITY; break; }
-                    T32 T;
-                    T.slot = so < sn ? so : sn;
-                    T.row = bsta[T.slot];
-                    T.has_o = so <= sn;
-                    T.has_n = sn <= so;
-                    T.k0o = T.k0n = 0;
-                    T.E0o = T.E0n = 0.f;
-                    int lo = 1 << 30, hi = -1;
-                    if (T.has_o) {
-                        const A32 A = oa[io++];
-                        T.k0o = A.k0; T.E0o = A.E0;
-                        lo = min(lo, A.k0);
-                        hi = max(hi, A.k0 + g.n_w);
-                    }
-                    if (T.has_n) {
-                        const A32 A = cand[in++];
-                        T.k0n = A.k0; T.E0n = A.E0;
-                        lo = min(lo, A.k0);
-                        hi = max(hi, A.k0 + g.n_w);
-                    }
-                    lo = max(lo, 0);
-                    hi = (long long)hi > g.n_samp ? (int)g.n_samp : hi;
-                    T.lo = lo;
-                    T.hi = hi;
-                    T.oth0 = npool;
-                    T.noth = 0;
-                    if (lo < hi) {
-                        if (lane == 0) tasks[ntask] = T;
-                        ++ntask;
-                    }
-                }
-                __syncwarp();
-                // others lists of every task: own events except the changed one, then
-                // frozen neighbours, each covering part of [lo, hi), in order
-                for (int ti = 0; ti < ntask && !err; ++ti) {
-                    const int slot = tasks[ti].slot, lo = tasks[ti].lo, hi = tasks[ti].hi;
-                    const int o0 = npool;
-                    for (int q0 = 0; q0 < n_own; q0 += 32) {
-                        const int q = q0 + lane;
-                        bool hit = false;
-                        F32a A = {0, 0.f};
-                        if (q < n_own) {
-                            const int p2 = order[q];
-                            if (p2 != ps) {
-                                for (int a = 0; a < enarr[p2]; ++a) {
-                                    const A32& B = earr[p2 * g.arr_cap + a];
-                                    if (B.slot == slot && B.k0 + g.n_w > lo && B.k0 < hi) {
-                                        hit = true;
-                                        A = F32a{B.k0, B.E0};
-                                    }
-                                }
-                            }
-                        }
-                        const unsigned bal = __ballot_sync(FULL, hit);
-                        const int pos = npool + __popc(bal & ((1u << lane) - 1));
-                        if (hit && pos < Lo.pool_cap) pool[pos] = A;
-                        npool += __popc(bal);
-                    }
-                    for (int a0 = 0; a0 < fcnt[slot]; a0 += 32) {
-                        const int a = a0 + lane;
-                        bool hit = false;
-                        F32a A = {0, 0.f};
-                        if (a < fcnt[slot]) {
-                            A = farr[slot * g.frz_cap + a];
-                            hit = A.k0 + g.n_w > lo && A.k0 < hi;
-                        }
-                        const unsigned bal = __ballot_sync(FULL, hit);
-                        const int pos = npool + __popc(bal & ((1u << lane) - 1));
-                        if (hit && pos < Lo.pool_cap) pool[pos] = A;
-                        npool += __popc(bal);
-                    }
-                    if (npool > Lo.pool_cap) err = CMH_ERR_CAPACITY;
-                    if (lane == 0) {
-                        tasks[ti].oth0 = o0;
-                        tasks[ti].noth = min(npool, Lo.pool_cap) - o0;
-                    }
-                }
-            }
-            if (lane == 0) {
-                s_err = err;
-                s_valid = valid;
-                s_idx = idx;
-                s_type = dr.type;
-                s_ncand = ncand;
-                s_ntask = ntask;
-                s_cand = c;
-            }
+            if (step + 1 < g.k) prepare_step<STAGE>(g, d, S, step + 1, sl ^ 1);   // assumes a rejection
+        } else if (valid) {
+            // (this buffer is refilled by bulk copies only after two more
+            // barriers: these generic reads come first)
+            price_step<STAGE>(g, d, S, sl);
         }
         __syncthreads();
-        if (s_err) break;
-        const int valid = s_valid, ntask = s_ntask;
-
-        // ===================== pricing (all threads) =====================
-        if (valid) {
-            float acc = 0.f, comp = 0.f;
-            for (int ti = 0; ti < ntask; ++ti) {
-                const T32& T = tasks[ti];
-                const float* srow = (const float*)d.sig + (size_t)T.row * g.pitch;
-                const float* vrow = (const float*)d.V + (size_t)T.row * g.pitch;
-                for (int q = (T.lo >> 2) + tid; (q << 2) < T.hi; q += nthr) {
-                    const int k = q << 2;
-                    const float4 s4 = __ldg(reinterpret_cast<const float4*>(srow + k));
-                    const float4 v4 = *reinterpret_cast<const float4*>(vrow + k);
-                    const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
-                    const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int kk = k + e;
-                        const int ro = kk - T.k0o, rn = kk - T.k0n;
-                        const bool io = T.has_o && (unsigned)ro < (unsigned)g.n_w;
-                        const bool inn = T.has_n && (unsigned)rn < (unsigned)g.n_w;
-                        // the same per-sample values the variance synthesis adds, so the
-                        // priced change is the change written to V on accept
-                        const float co = io ? arr_var32(g, T.E0o, ro) : 0.f;
-                        const float cn = inn ? arr_var32(g, T.E0n, rn) : 0.f;
-                        const float dd = cn - co;
-                        if (kk < T.hi && dd != 0.f) {
-                            const float V = vv[e], s = sv[e];
-                            const float Vp = V + dd;
-                            float term;
-                            if (Vp < 0.5f * V) {
-                                // the changed arrival dominates V: rebuild V' from the others
-                                float a2 = g.noise_f, c2 = 0.f;
-                                for (int o = 0; o < T.noth; ++o) {
-                                    const F32a A = pool[T.oth0 + o];
-                                    const int r = kk - A.k0;
-                                    if ((unsigned)r < (unsigned)g.n_w) kahan_add32(a2, c2, arr_var32(g, A.E0, r));
-                                }
-                                if (inn) kahan_add32(a2, c2, cn);
-                                const float Vr = a2 - c2;
-                                term = logf(Vr / V) + s * s * (1.f / Vr - 1.f / V);
-                            } else {
-                                term = log1pf(dd / V) - s * s * dd / (V * Vp);
-                            }
-                            kahan_add32(acc, comp, -0.5f * term);
-                        }
-                    }
-                }
-            }
-            float2 v = make_float2(acc, -comp);
+        // ================ decision (warp 0; float64 on lane 0) =====================
+        if (wid == 0) {
+            float2 t = (valid && lane > 0 && lane < nw) ? S.redf[lane] : make_float2(0.f, 0.f);
             for (int o = 16; o > 0; o >>= 1) {
                 float2 w2;
-                w2.x = __shfl_xor_sync(FULL, v.x, o);
-                w2.y = __shfl_xor_sync(FULL, v.y, o);
-                v = ff_add32(v, w2);
+                w2.x = __shfl_xor_sync(FULL, t.x, o);
+                w2.y = __shfl_xor_sync(FULL, t.y, o);
+                t = ff_add32(t, w2);
             }
-            if (lane == 0) s_redf[wid] = v;
-            __syncthreads();
-        }
-
-        // ===================== decision (thread 0, float64) =====================
-        if (tid == 0) {
-            const int type = s_type, n_own = s_n_own;
-            const D32& dr = draws[step];
-            ++n_prop[type];
-            double dll = 0.0, la = -INFINITY, dlp = 0.0;
-            int acc = 0;
-            if (valid) {
-                ++n_eval[type];
-                for (int ti = 0; ti < ntask; ++ti) n_priced += (unsigned long long)(tasks[ti].hi - tasks[ti].lo);
-                float2 t = s_redf[0];
-                for (int w = 1; w < (nthr >> 5); ++w) t = ff_add32(t, s_redf[w]);
-                dll = (double)t.x + (double)t.y;
-                if (type == 0) {
-                    la = dll + tabB[n_own];
-                    dlp = dr.blb;
-                } else if (type == 1) {
-                    la = dll + tabD[n_own];
-                    dlp = mm[order[s_idx]] - g.lb0;
-                } else {
-                    const double dm = __dsub_rn(s_cand.m, mm[order[s_idx]]);
-                    la = dll - dm;
-                    dlp = -dm;
+            if (lane == 0) {
+                const int type = S.type[sl], n_own = S.n_own, idx = S.idx[sl];
+                const D32& dr = S.draws[step];
+                if (STAGE && S.on[sl]) {   // this buffer's copies have landed (the workers waited)
+                    if (!mbar_wait(&S.bar[sl], (unsigned)S.ph[sl])) S.err = CMH_ERR_TIMEOUT;
+                    S.ph[sl] ^= 1;
+                    S.on[sl] = 0;
                 }
-                acc = (double)dr.logu < la;
-            }
-            if (d.trace) {
-                const long long slot = ((sweep - d.trace_sweep0) * g.n_cells + cell) * (long long)g.k + step;
-                if (slot >= 0 && slot < d.trace_cap) {
-                    cmh_trace& R = d.trace[slot];
-                    R.sweep = (int)sweep; R.cell = cell; R.step = step; R.type = type;
-                    R.evaluated = valid; R.accepted = acc; R.n_before = n_own; R.written = 1;
-                    R.dll = dll; R.log_alpha = la;
-                }
-            }
-            const int do_commit = acc && g.commit;
-            if (acc) ++n_acc[type];
-            if (do_commit) {
-                for (int ti = 0; ti < ntask; ++ti) n_rewritten += (unsigned long long)(tasks[ti].hi - tasks[ti].lo);
-                s_region_dlp += dll + dlp;
-                const P32 c = s_cand;
-                int ps;
-                if (type == 1) {
-                    ps = order[s_idx];
-                    for (int q = s_idx; q + 1 < n_own; ++q) order[q] = order[q + 1];
-                    freel[s_n_free++] = ps;
-                    s_n_own = n_own - 1;
-                } else {
+                ++S.cnt[type];
+                double dll = 0.0, la = -INFINITY, dlp = 0.0;
+                int acc = 0;
+                if (valid) {
+                    ++S.cnt[3 + type];
+                    S.cnt[9] += (unsigned long long)S.width[sl];
+                    dll = (double)t.x + (double)t.y;
                     if (type == 0) {
-                        ps = freel[--s_n_free];
-                        eid[ps] = ((unsigned long long)(sweep + 1) << 32) | ((unsigned long long)cell << 12) |
-                                  (unsigned long long)step;
-                        order[n_own] = ps;
-                        s_n_own = n_own + 1;
+                        la = dll + S.tabB[n_own];
+                        dlp = dr.blb;
+                    } else if (type == 1) {
+                        la = dll + S.tabD[n_own];
+                        dlp = S.mm[S.order[idx]] - g.lb0;
                     } else {
-                        ps = order[s_idx];
+                        const double dm = __dsub_rn(S.c[sl].m, S.mm[S.order[idx]]);
+                        la = dll - dm;
+                        dlp = -dm;
                     }
-                    mx[ps] = c.x; my[ps] = c.y; mt[ps] = c.t; mm[ps] = c.m;
-                    exr[ps] = c.xr; eyr[ps] = c.yr; eph[ps] = c.ph; emf[ps] = c.mf; eK[ps] = c.K;
-                    for (int a = 0; a < s_ncand; ++a) earr[ps * g.arr_cap + a] = cand[a];
-                    enarr[ps] = s_ncand;
+                    acc = (double)dr.logu < la;
                 }
+                if (d.trace) {
+                    const long long slot = ((sweep - d.trace_sweep0) * g.n_cells + cell) * (long long)g.k + step;
+                    if (slot >= 0 && slot < d.trace_cap) {
+                        cmh_trace& R = d.trace[slot];
+                        R.sweep = (int)sweep; R.cell = cell; R.step = step; R.type = type;
+                        R.evaluated = valid; R.accepted = acc; R.n_before = n_own; R.written = 1;
+                        R.dll = dll; R.log_alpha = la;
+                    }
+                }
+                const int do_commit = acc && g.commit;
+                if (acc) ++S.cnt[6 + type];
+                if (do_commit) {
+                    S.cnt[10] += (unsigned long long)S.width[sl];
+                    S.region_dlp += dll + dlp;
+                    const P32& c = S.c[sl];
+                    const A32* cd = S.cand + sl * g.arr_cap;
+                    int ps;
+                    if (type == 1) {
+                        ps = S.order[idx];
+                        lists_remove(g, S, ps);
+                        for (int q = idx; q + 1 < n_own; ++q) S.order[q] = S.order[q + 1];
+                        S.freel[S.n_free++] = ps;
+                        S.n_own = n_own - 1;
+                    } else {
+                        if (type == 0) {
+                            ps = S.freel[--S.n_free];
+                            S.eid[ps] = ((unsigned long long)(sweep + 1) << 32) | ((unsigned long long)cell << 12) |
+                                        (unsigned long long)step;
+                            S.order[n_own] = ps;
+                            S.n_own = n_own + 1;
+                        } else {
+                            ps = S.order[idx];
+                            lists_remove(g, S, ps);
+                        }
+                        S.mx[ps] = c.x; S.my[ps] = c.y; S.mt[ps] = c.t; S.mm[ps] = c.m;
+                        S.exr[ps] = c.xr; S.eyr[ps] = c.yr;
+                        for (int a = 0; a < S.ncand[sl]; ++a) S.earr[ps * g.arr_cap + a] = cd[a];
+                        S.enarr[ps] = S.ncand[sl];
+                        lists_add(g, S, ps, cd, S.ncand[sl]);
+                    }
+                }
+                S.acc = do_commit;
             }
-            s_acc = do_commit;
         }
         __syncthreads();
-
-        // ===================== commit: re-synthesise V on the touched windows ======
-        if (s_acc) {
-            const bool has_new_type = s_type != 1;
-            for (int ti = 0; ti < ntask; ++ti) {
-                const T32& T = tasks[ti];
-                const bool has_new = has_new_type && T.has_n;
+        // ================ commit: re-synthesise V on the touched windows ============
+        if (S.acc) {
+            const T32* tk = S.tasks + sl * kMaxTasks32;
+            for (int ti = 0; ti < S.ntask[sl]; ++ti) {
+                const T32& T = tk[ti];
+                const SA* L = S.sarr + T.slot * g.frz_cap;
+                const int nl = S.scnt[T.slot];
                 float* vrow = (float*)d.V + (size_t)T.row * g.pitch;
                 for (int kk = T.lo + tid; kk < T.hi; kk += nthr) {
                     float a2 = g.noise_f, c2 = 0.f;
-                    for (int o = 0; o < T.noth; ++o) {
-                        const F32a A = pool[T.oth0 + o];
-                        const int r = kk - A.k0;
-                        if ((unsigned)r < (unsigned)g.n_w) kahan_add32(a2, c2, arr_var32(g, A.E0, r));
-                    }
-                    if (has_new) {
-                        const int r = kk - T.k0n;
-                        if ((unsigned)r < (unsigned)g.n_w) kahan_add32(a2, c2, arr_var32(g, T.E0n, r));
+                    for (int o = 0; o < nl; ++o) {
+                        const SA A = L[o];
+                        if ((unsigned)(kk - A.k0) < (unsigned)g.n_w) kahan_add32(a2, c2, arr_var32(g, A.E0, A.k0, kk));
                     }
                     vrow[kk] = a2 - c2;
                 }
             }
+            if (STAGE) fence_async_global();   // the new V is visible to the next bulk copies
+            __syncthreads();
+            // the prepared next step assumed a rejection: prepare it again
+            if (wid == 0 && step + 1 < g.k) prepare_step<STAGE>(g, d, S, step + 1, sl ^ 1);
             __syncthreads();
         }
     }
     __syncthreads();
-    if (s_err) {
-        if (tid == 0) latch(d.status, s_err);
+    if (STAGE && tid == 0)
+        for (int b = 0; b < 2; ++b)
+            if (S.on[b]) {   // copies still in flight after an early exit: let them land
+                if (!mbar_wait(&S.bar[b], (unsigned)S.ph[b])) S.err = CMH_ERR_TIMEOUT;
+                S.on[b] = 0;
+            }
+    __syncthreads();
+    if (S.err) {
+        if (tid == 0) latch(d.status, S.err);
         return;
     }
-    const int n_fin = s_n_own;
+    const int n_fin = S.n_own;
     for (int i = tid; i < n_fin; i += nthr) {
-        const int ps = order[i];
-        S.x[start + i] = mx[ps];
-        S.y[start + i] = my[ps];
-        S.t[start + i] = mt[ps];
-        S.m[start + i] = mm[ps];
-        S.id[start + i] = eid[ps];
+        const int ps = S.order[i];
+        St.x[start + i] = S.mx[ps];
+        St.y[start + i] = S.my[ps];
+        St.t[start + i] = S.mt[ps];
+        St.m[start + i] = S.mm[ps];
+        St.id[start + i] = S.eid[ps];
     }
     if (tid == 0) {
-        S.count[cell] = n_fin;
-        d.region_dlp[cell] = s_region_dlp;
-        for (int t = 0; t < 3; ++t) {
-            if (n_prop[t]) atomicAdd(&d.stats[t], n_prop[t]);
-            if (n_eval[t]) atomicAdd(&d.stats[3 + t], n_eval[t]);
-            if (n_acc[t]) atomicAdd(&d.stats[6 + t], n_acc[t]);
-        }
-        if (n_priced) atomicAdd(&d.stats[9], n_priced);
-        if (n_rewritten) atomicAdd(&d.stats[10], n_rewritten);
+        St.count[cell] = n_fin;
+        d.region_dlp[cell] = S.region_dlp;
+        for (int t = 0; t < 11; ++t)
+            if (S.cnt[t]) atomicAdd(&d.stats[t], S.cnt[t]);
     }
 }
 
 }  // namespace
 
-size_t phase32_smem_bytes(const Geo& g) { return L32(g).total; }
+size_t phase32_smem_bytes(const Geo& g) { return layout32(g, nullptr, nullptr); }
+
+// staging capacity (samples per buffer): 0 for `requested` 0 (no staging);
+// `requested` rounded down to a multiple of 4 when positive; for -1, one
+// arrival window (a move's shift included), cut down to what keeps the CTAs
+// of one colour phase resident in a single wave (at most kMinBlocks32 per SM;
+// none when fewer than 64 samples fit).  Windows that do not fit are read
+// from global memory.
+cudaError_t choose_stage_cap(Geo& g, int requested) {
+    g.stage_cap = 0;
+    if (requested == 0) return cudaSuccess;
+    if (requested > 0) {
+        g.stage_cap = requested & ~3;
+        return cudaSuccess;
+    }
+    int dev = 0, per_sm = 0, reserved = 0, n_sm = 1, optin = 0;
+    cudaError_t e;
+    cudaFuncAttributes fa;
+    if ((e = cudaGetDevice(&dev)) ||
+        (e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) ||
+        (e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) ||
+        (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) ||
+        (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) ||
+        (e = cudaFuncGetAttributes(&fa, phase32_kernel<true>)))
+        return e;
+    const int resident = std::min(kMinBlocks32, std::max(1, (g.max_rpc + n_sm - 1) / std::max(1, n_sm)));
+    const long long dyn = (long long)layout32(g, nullptr, nullptr);
+    long long budget = (long long)per_sm / resident - reserved - (long long)fa.sharedSizeBytes - dyn;
+    budget = std::min(budget, (long long)optin - (long long)fa.sharedSizeBytes - dyn);
+    const long long want = (((long long)g.n_w + 3) & ~3LL) + 64;
+    long long cap = budget > 0 ? (budget / 16) & ~3LL : 0;
+    if (cap > want) cap = want;
+    g.stage_cap = cap >= 64 ? (int)cap : 0;
+    return cudaSuccess;
+}
 
 cudaError_t prepare_phase32(const Geo& g) {
-    return cudaFuncSetAttribute(phase32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)phase32_smem_bytes(g));
+    const int bytes = (int)phase32_smem_bytes(g);
+    cudaError_t e = cudaFuncSetAttribute(phase32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(phase32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 cudaError_t launch_phase32(const Geo& g, const Dev& d, int colour, cudaStream_t s) {
-    phase32_kernel<<<g.max_rpc, kThreads32, phase32_smem_bytes(g), s>>>(g, d, colour);
+    if (g.stage_cap > 0)
+        phase32_kernel<true><<<g.max_rpc, kThreads32, phase32_smem_bytes(g), s>>>(g, d, colour);
+    else
+        phase32_kernel<false><<<g.max_rpc, kThreads32, phase32_smem_bytes(g), s>>>(g, d, colour);
     return cudaGetLastError();
 }
 

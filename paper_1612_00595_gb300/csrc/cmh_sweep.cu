@@ -28,7 +28,6 @@ namespace cmh {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr double LOG2E = 1.4426950408889634074;
 
 struct EvArr {          // one arrival of an own event at a blanket station
     int slot, k0;       // blanket slot, first sample of the window
@@ -112,16 +111,6 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     s = t;
 }
 
-// float-float (hi, lo) sum of two pairs (TwoSum on the high parts)
-__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
-    const float s = a.x + b.x;
-    const float bb = s - a.x;
-    const float e = (a.x - (s - bb)) + (b.x - bb);
-    const float lo = a.y + b.y + e;
-    const float hi = s + lo;
-    return make_float2(hi, lo - (hi - s));
-}
-
 // ordered append across the block: returns the position of this thread's
 // element among the flagged ones of this round; *total (shared) is advanced
 __device__ __forceinline__ int block_append(bool flag, int* s_warp, int* s_base) {
@@ -177,7 +166,6 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
     __shared__ double s_c[4];
     __shared__ int s_n_own, s_n_free, s_n_blk, s_err, s_valid, s_idx, s_type, s_ncand, s_ntask, s_acc;
     __shared__ int s_warp[32], s_base;
-    __shared__ float2 s_redf[32];
     __shared__ double s_redd[32];
 
     const int start = S.start[cell], n0 = S.count[cell];
@@ -730,7 +718,7 @@ __global__ void __launch_bounds__(kSynthThreads) vsynth_kernel(Geo g, Dev d, con
                     for (int q = 0; q < nt; ++q) {
                         const int a = s_tl[q];
                         const int r = (int)(k - s_k0[a]);
-                        if ((unsigned)r < (unsigned)g.n_w) kahan_add(a2, c2, arr_var32(g, s_E0[a], r));
+                        if ((unsigned)r < (unsigned)g.n_w) kahan_add(a2, c2, arr_var32(g, s_E0[a], s_k0[a], (int)k));
                     }
                     vrow[k] = a2 - c2;
                 } else {

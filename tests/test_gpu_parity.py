@@ -212,3 +212,21 @@ def test_fp32_chain_tracks_recomputed_log_density(cm, init):
     assert np.all((ev[:, 0] >= 0) & (ev[:, 0] < w.params.W) & (ev[:, 2] >= 0) & (ev[:, 2] < w.params.T))
     assert np.all(ev[:, 3] >= 2.0)
     m.destroy()
+
+
+def test_fp32_staging_modes_agree(cm):
+    """Station windows staged in shared memory by bulk copies (automatic
+    size), staged only where they fit in 64 samples, or read from global
+    memory (the default): the same arithmetic on the same values, so the
+    chains agree bit for bit."""
+    w = small_world(seed=18, W=1000.0, T=3600.0, Lambda=500.0, n_side=10, dtype=np.float32)
+    runs = []
+    for stage in (-1, 64, 0):
+        m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=6, k=32, events=w.events, seed=9, stage_samples=stage)
+        runs.append((ev, ids, logp, tr, stats))
+        m.destroy()
+    assert sum(runs[0][4]["accepted"]) > 100
+    for ev, ids, logp, tr, _ in runs[1:]:
+        assert np.array_equal(ev, runs[0][0]) and np.array_equal(ids, runs[0][1])
+        assert logp == runs[0][2]
+        assert np.array_equal(tr, runs[0][3])

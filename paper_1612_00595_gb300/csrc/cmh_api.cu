@@ -499,6 +499,7 @@ int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mo
 
     Geo& g = m->g;
     g.L = L;
+    g.invL_f = (float)(1.0 / L);
     g.shift_mode = shift_mode;
     g.sx_static = shift_mode == 0 ? sx : 0.0;
     g.sy_static = shift_mode == 0 ? sy : 0.0;
@@ -528,6 +529,7 @@ int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mo
     if ((g.f32 ? phase32_smem_bytes(g) : phase_smem_bytes(g)) > 227 * 1024) return CMH_ERR_CAPACITY;
     CK(prepare_kernels(g));
     CK(prepare_phase32(g));
+    CK(prepare_rebin(g));
 
     Dev& d = m->d;
     cudaError_t e;
@@ -545,8 +547,10 @@ int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mo
     }
     if ((e = m->alloc(&d.colour_count, kMaxColours, true)) ||
         (e = m->alloc(&d.colour_cells, (size_t)g.n_colours * g.max_rpc, true)) ||
-        (e = m->alloc(&d.fill, g.n_cells, true)) || (e = m->alloc(&d.region_dlp, g.n_cells, true)))
+        (e = m->alloc(&d.fill, g.n_cells, true)) || (e = m->alloc(&d.ncell, g.store_cap, true)) ||
+        (e = m->alloc(&d.region_dlp, g.n_cells, true)))
         return cuda_err(e);
+    CK(cudaMemsetAsync(d.fill, 0, sizeof(int) * g.n_cells, m->stream));
     CK(cudaMemsetAsync(d.region_dlp, 0, sizeof(double) * g.n_cells, m->stream));
     CK(cudaMemsetAsync(d.colour_count, 0, sizeof(int) * kMaxColours, m->stream));
     if (m->trace_cap > 0) CK(cudaMemsetAsync(d.trace, 0, sizeof(cmh_trace) * m->trace_cap, m->stream));

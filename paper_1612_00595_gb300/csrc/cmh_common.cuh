@@ -39,6 +39,7 @@ struct Geo {
     int f32;
     int threads;
     // float32 form of the model constants (host-computed)
+    float invL_f;      // 1 / L
     float fv_f;        // f / v
     float twoftau_f;   // 2 / (f tau)
     float kap_f;       // 2 log2(e) / (f tau): per-sample decay of log2 of a variance
@@ -64,7 +65,8 @@ struct Dev {
     double* shift;              // [2] current (sx, sy)
     int* colour_count;          // [n_colours]
     int* colour_cells;          // [n_colours][max_rpc]
-    int* fill;                  // [n_cells] scratch
+    int* fill;                  // [n_cells] events counted into each new cell (cleared by the scan)
+    int* ncell;                 // [store_cap] new cell of the event at each position of the old store
     double* region_dlp;         // [n_cells] log-density change of the current sweep
     double* logp;               // running log-density
     int* status;                // latched CMH_ERR_* (0 = fine)
@@ -253,6 +255,7 @@ struct FlatList {
 
 // host-side launchers (defined in the .cu files)
 cudaError_t launch_rebin(const Geo& g, const Dev& d, int init_n, cudaStream_t s, int* launches);
+cudaError_t prepare_rebin(const Geo& g);
 cudaError_t launch_phase(const Geo& g, const Dev& d, int colour, cudaStream_t s);
 cudaError_t launch_phase32(const Geo& g, const Dev& d, int colour, cudaStream_t s);
 size_t phase32_smem_bytes(const Geo& g);

@@ -2,17 +2,25 @@
 // per-sweep boundary shift (§Chromatic MH with Dynamic Coloring).
 //
 // A sweep starts by re-binning every event into the cells of the shifted grid:
-//   rebin_count   one block per new cell counts the events that fall in it;
-//                 the old cells that can feed a new cell are its 3 x 3
-//                 neighbourhood, because the two grids differ by less than
-//                 one cell side along each axis;
+//   rebin_assign  one warp per old cell (or one thread per event of the
+//                 initial flat list) computes the new cell of each event and
+//                 counts it into fill[] with an atomic add;
 //   rebin_scan    one block: exclusive scan of (count + k births of slack)
-//                 over cells -> slices of the new store; colour lists of the
-//                 live cells (cells with a non-empty intersection with the
-//                 domain), each in cell-index order;
-//   rebin_gather  one block per new cell collects its events and writes them
-//                 sorted by event id, the canonical order every region uses.
+//                 over cells -> slices of the new store (fill is cleared for
+//                 the next sweep); colour lists of the live cells (cells with
+//                 a non-empty intersection with the domain), each in
+//                 cell-index order;
+//   rebin_gather  one warp per new cell collects its events from the 3 x 3
+//                 old cells around it (the two grids differ by less than one
+//                 cell side along each axis), by their new-cell index, and
+//                 writes them sorted by event id, the canonical order every
+//                 region uses.
+// Only rebin_assign evaluates the cell index of a coordinate; the exact
+// float64 form of floor((x - s) / L) runs only when a float32 estimate lies
+// within 1e-3 of an integer.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "cmh_common.cuh"
 
@@ -20,38 +28,31 @@ namespace cmh {
 
 namespace {
 
-constexpr int kRebinThreads = 128;
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kRebinThreads = 256;
+constexpr int kWarpsPerBlock = kRebinThreads / 32;
+constexpr int kAxisMax = 1024;   // cells per axis (the host keeps ncx * ncy <= 2^20)
+constexpr int kMaxPeriod = 4;    // colour period per axis (the host keeps P^2 <= kMaxColours)
 
-__device__ __forceinline__ bool cell_live(const Geo& g, double sx, double sy, int c) {
-    double r[4];
-    cell_rect(g, sx, sy, c, r);
-    return r[1] > r[0] && r[3] > r[2];
+// cell index along one axis, floor((x - s) / L) + 1 as its float64 definition
+// gives it.  The float32 quotient is within |q| 2^-22 of the float64 one;
+// away from integers by more than 1e-3 (|q| <= 1024 cells) its floor is the
+// same, otherwise the float64 division decides.
+__device__ __forceinline__ int cell_axis_fast(const Geo& g, double x, double s) {
+    const double dd = __dsub_rn(x, s);
+    const float q = (float)dd * g.invL_f;
+    const float fl = floorf(q);
+    if (q - fl > 1e-3f && fl + 1.f - q > 1e-3f) return (int)fl + 1;
+    return cell_axis(x, s, g.L);
 }
 
-// iterate the candidate old events of new cell c: the 3 x 3 old cells around
-// c, or (init_n >= 0) the flat list [0, init_n) of store `old`
-template <typename F>
-__device__ __forceinline__ void for_candidates(const Geo& g, const Store& old, int c, int init_n, F&& f) {
-    if (init_n >= 0) {
-        for (int base = 0; base < init_n; base += blockDim.x) f(base + (int)threadIdx.x, base + (int)threadIdx.x < init_n);
-        return;
-    }
-    const int ix = c % g.ncx, iy = c / g.ncx;
-    for (int jy = iy - 1; jy <= iy + 1; ++jy) {
-        if (jy < 0 || jy >= g.ncy) continue;
-        for (int jx = ix - 1; jx <= ix + 1; ++jx) {
-            if (jx < 0 || jx >= g.ncx) continue;
-            const int oc = jy * g.ncx + jx;
-            const int s0 = old.start[oc], n = old.count[oc];
-            for (int base = 0; base < n; base += blockDim.x) {
-                const int i = base + (int)threadIdx.x;
-                f(s0 + i, i < n);
-            }
-        }
-    }
+__device__ __forceinline__ int cell_of_fast(const Geo& g, double sx, double sy, double x, double y) {
+    const int ix = cell_axis_fast(g, x, sx), iy = cell_axis_fast(g, y, sy);
+    if (ix < 0 || ix >= g.ncx || iy < 0 || iy >= g.ncy) return -1;
+    return iy * g.ncx + ix;
 }
 
-__global__ void __launch_bounds__(kRebinThreads) rebin_count(Geo g, Dev d, int init_n) {
+__global__ void __launch_bounds__(kRebinThreads) rebin_assign(Geo g, Dev d, int init_n) {
     if (*d.status) return;
     const long long sweep = *d.sweep;
     double sx, sy;
@@ -61,27 +62,29 @@ __global__ void __launch_bounds__(kRebinThreads) rebin_count(Geo g, Dev d, int i
         d.shift[1] = sy;
     }
     const Store old = d.st[(sweep + 1) & 1];
-    const int c = blockIdx.x;
-    int cnt = 0;
-    if (cell_live(g, sx, sy, c)) {
-        for_candidates(g, old, c, init_n, [&](int idx, bool ok) {
-            if (ok && cell_of(g, sx, sy, old.x[idx], old.y[idx]) == c) ++cnt;
-        });
+    auto assign = [&](int pos) {
+        const int c = cell_of_fast(g, sx, sy, old.x[pos], old.y[pos]);
+        d.ncell[pos] = c;
+        if (c >= 0)
+            atomicAdd(&d.fill[c], 1);
+        else
+            latch(d.status, CMH_ERR_GEOMETRY);   // an event outside the domain
+    };
+    if (init_n >= 0) {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i < init_n) assign(i);
+        return;
     }
-    __shared__ int s_cnt;
-    if (threadIdx.x == 0) s_cnt = 0;
-    __syncthreads();
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&s_cnt, cnt);
-    __syncthreads();
-    if (threadIdx.x == 0) d.fill[c] = s_cnt;
+    const int oc = blockIdx.x * kWarpsPerBlock + (int)(threadIdx.x >> 5);
+    if (oc >= g.n_cells) return;
+    const int s0 = old.start[oc], n = old.count[oc];
+    for (int i = threadIdx.x & 31; i < n; i += 32) assign(s0 + i);
 }
 
-// live cells form a rectangle in index space; the colour lists hold them in
-// cell-index order: rank of (ix, iy) among live cells of the same colour
-__device__ __forceinline__ bool x_live(const Geo& g, double s, int ix) {
-    double a = __dadd_rn(s, __dmul_rn((double)(ix - 1), g.L));
-    double b = __dadd_rn(s, __dmul_rn((double)ix, g.L));
+// is index i along an axis (shift s) a live cell: [s + (i-1) L, s + i L) meets [0, W)
+__device__ __forceinline__ bool axis_live(const Geo& g, double s, int i) {
+    double a = __dadd_rn(s, __dmul_rn((double)(i - 1), g.L));
+    double b = __dadd_rn(s, __dmul_rn((double)i, g.L));
     if (a < 0.0) a = 0.0;
     if (b > g.W) b = g.W;
     return b > a;
@@ -92,36 +95,54 @@ __global__ void __launch_bounds__(1024) rebin_scan(Geo g, Dev d) {
     const long long sweep = *d.sweep;
     const Store nw = d.st[sweep & 1];
     const double sx = d.shift[0], sy = d.shift[1];
+    const int P = g.period;
     __shared__ long long s_carry, s_events;
     __shared__ long long s_warp[32];
-    if (threadIdx.x == 0) { s_carry = 0; s_events = 0; }
-    __syncthreads();
+    __shared__ unsigned char s_live[2][kAxisMax];
+    __shared__ int s_rank[2][kAxisMax];     // rank among the live indices of the same residue mod P
+    __shared__ int s_num[2][kMaxPeriod];    // live indices of each residue
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    if (threadIdx.x == 0) {
+        s_carry = 0;
+        s_events = 0;
+    }
+    for (int i = threadIdx.x; i < g.ncx; i += blockDim.x) s_live[0][i] = axis_live(g, sx, i);
+    for (int i = threadIdx.x; i < g.ncy; i += blockDim.x) s_live[1][i] = axis_live(g, sy, i);
+    __syncthreads();
+    if (threadIdx.x < 2 * P) {
+        const int ax = threadIdx.x / P, r = threadIdx.x % P, n = ax ? g.ncy : g.ncx;
+        int cnt = 0;
+        for (int i = r; i < n; i += P) {
+            s_rank[ax][i] = cnt;
+            cnt += s_live[ax][i];
+        }
+        s_num[ax][r] = cnt;
+    }
+    __syncthreads();
     for (int base = 0; base < g.n_cells; base += blockDim.x) {
         const int c = base + threadIdx.x;
         long long v = 0;
         int cnt = 0;
-        bool live = false;
         if (c < g.n_cells) {
             cnt = d.fill[c];
-            live = x_live(g, sx, c % g.ncx) && x_live(g, sy, c / g.ncx);
-            v = cnt + (live ? g.k : 0);
+            d.fill[c] = 0;
+            v = cnt + ((s_live[0][c % g.ncx] && s_live[1][c / g.ncx]) ? g.k : 0);
         }
         // block inclusive scan of v
         long long x = v;
         for (int o = 1; o < 32; o <<= 1) {
-            long long y = __shfl_up_sync(0xffffffffu, x, o);
+            long long y = __shfl_up_sync(FULL, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) s_warp[wid] = x;
         long long ev = cnt;
-        for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+        for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(FULL, ev, o);
         if (lane == 0) atomicAdd((unsigned long long*)&s_events, (unsigned long long)ev);
         __syncthreads();
         if (wid == 0) {
             long long w = lane < nwarp ? s_warp[lane] : 0;
             for (int o = 1; o < 32; o <<= 1) {
-                long long y = __shfl_up_sync(0xffffffffu, w, o);
+                long long y = __shfl_up_sync(FULL, w, o);
                 if (lane >= o) w += y;
             }
             if (lane < nwarp) s_warp[lane] = w;
@@ -141,87 +162,109 @@ __global__ void __launch_bounds__(1024) rebin_scan(Geo g, Dev d) {
         if (s_carry > g.store_cap || s_events > g.max_events) latch(d.status, CMH_ERR_CAPACITY);
         *nw.total = (int)s_events;
     }
-    // colour lists
-    const int P = g.period;
+    // colour lists: live cell (ix, iy) has colour (ix mod P) + P (iy mod P) and
+    // position (rank of iy) x (live columns of its residue) + (rank of ix)
     for (int c = threadIdx.x; c < g.n_cells; c += blockDim.x) {
         const int ix = c % g.ncx, iy = c / g.ncx;
-        if (!(x_live(g, sx, ix) && x_live(g, sy, iy))) continue;
-        int rx = 0, nx = 0, ry = 0;
-        for (int j = ix % P; j < g.ncx; j += P) {
-            if (!x_live(g, sx, j)) continue;
-            if (j < ix) ++rx;
-            ++nx;
-        }
-        for (int j = iy % P; j < iy; j += P)
-            if (x_live(g, sy, j)) ++ry;
+        if (!(s_live[0][ix] && s_live[1][iy])) continue;
         const int col = (ix % P) + P * (iy % P);
-        d.colour_cells[col * g.max_rpc + ry * nx + rx] = c;
+        d.colour_cells[col * g.max_rpc + s_rank[1][iy] * s_num[0][ix % P] + s_rank[0][ix]] = c;
     }
-    for (int col = threadIdx.x; col < g.n_colours; col += blockDim.x) {
-        const int cx = col % P, cy = col / P;
-        int nx = 0, ny = 0;
-        for (int j = cx; j < g.ncx; j += P) nx += x_live(g, sx, j);
-        for (int j = cy; j < g.ncy; j += P) ny += x_live(g, sy, j);
-        d.colour_count[col] = nx * ny;
-    }
+    for (int col = threadIdx.x; col < g.n_colours; col += blockDim.x)
+        d.colour_count[col] = s_num[0][col % P] * s_num[1][col / P];
 }
 
-__global__ void __launch_bounds__(kRebinThreads) rebin_gather(Geo g, Dev d, int init_n) {
+__global__ void __launch_bounds__(kRebinThreads) rebin_gather(Geo g, Dev d, int init_n, int wpb) {
     if (*d.status) return;
     const long long sweep = *d.sweep;
     const Store old = d.st[(sweep + 1) & 1];
     const Store nw = d.st[sweep & 1];
-    const double sx = d.shift[0], sy = d.shift[1];
-    const int c = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = blockIdx.x * wpb + w;
+    if (c >= g.n_cells) return;
     const int n = nw.count[c];
     if (n == 0) return;
     if (n > g.ev_cap) {
-        if (threadIdx.x == 0) latch(d.status, CMH_ERR_CAPACITY);
+        if (lane == 0) latch(d.status, CMH_ERR_CAPACITY);
         return;
     }
     extern __shared__ __align__(16) unsigned char smem[];
-    double* bx = (double*)smem;
-    double* by = bx + g.ev_cap;
-    double* bt = by + g.ev_cap;
-    double* bm = bt + g.ev_cap;
-    unsigned long long* bid = (unsigned long long*)(bm + g.ev_cap);
-    __shared__ int s_pos;
-    if (threadIdx.x == 0) s_pos = 0;
-    __syncthreads();
-    for_candidates(g, old, c, init_n, [&](int idx, bool ok) {
-        if (ok && cell_of(g, sx, sy, old.x[idx], old.y[idx]) == c) {
-            const int p = atomicAdd(&s_pos, 1);
-            if (p < g.ev_cap) {
-                bx[p] = old.x[idx];
-                by[p] = old.y[idx];
-                bt[p] = old.t[idx];
-                bm[p] = old.m[idx];
-                bid[p] = old.id[idx];
+    unsigned long long* bid = (unsigned long long*)smem + (size_t)w * g.ev_cap;
+    int* bpos = (int*)((unsigned long long*)smem + (size_t)wpb * g.ev_cap) + (size_t)w * g.ev_cap;
+    const unsigned lt = (1u << lane) - 1u;
+    int got = 0;
+    auto collect = [&](int s0, int cnt) {
+        for (int i0 = 0; i0 < cnt; i0 += 32) {
+            const int i = i0 + lane;
+            const bool hit = i < cnt && d.ncell[s0 + i] == c;
+            const unsigned bal = __ballot_sync(FULL, hit);
+            if (hit) {
+                const int p = got + __popc(bal & lt);
+                if (p < g.ev_cap) {
+                    bpos[p] = s0 + i;
+                    bid[p] = old.id[s0 + i];
+                }
+            }
+            got += __popc(bal);
+        }
+    };
+    if (init_n >= 0) {
+        collect(0, init_n);
+    } else {
+        const int ix = c % g.ncx, iy = c / g.ncx;
+        for (int jy = iy - 1; jy <= iy + 1; ++jy) {
+            if (jy < 0 || jy >= g.ncy) continue;
+            for (int jx = ix - 1; jx <= ix + 1; ++jx) {
+                if (jx < 0 || jx >= g.ncx) continue;
+                const int oc = jy * g.ncx + jx;
+                collect(old.start[oc], old.count[oc]);
             }
         }
-    });
-    __syncthreads();
+    }
+    __syncwarp();
+    if (got != n) {   // counted and collected events disagree: not expected
+        if (lane == 0) latch(d.status, CMH_ERR_GEOMETRY);
+        return;
+    }
     // rank by id (ids are unique) and write in id order
     const int s0 = nw.start[c];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = lane; i < n; i += 32) {
         const unsigned long long me = bid[i];
         int r = 0;
         for (int j = 0; j < n; ++j) r += bid[j] < me;
-        nw.x[s0 + r] = bx[i];
-        nw.y[s0 + r] = by[i];
-        nw.t[s0 + r] = bt[i];
-        nw.m[s0 + r] = bm[i];
+        const int src = bpos[i];
+        nw.x[s0 + r] = old.x[src];
+        nw.y[s0 + r] = old.y[src];
+        nw.t[s0 + r] = old.t[src];
+        nw.m[s0 + r] = old.m[src];
         nw.id[s0 + r] = me;
     }
 }
 
 }  // namespace
 
+namespace {
+
+// warps (new cells) per rebin_gather block: each holds ev_cap ids and positions
+int gather_warps(const Geo& g) { return g.ev_cap <= 512 ? kWarpsPerBlock : 1; }
+
+size_t gather_smem(const Geo& g) {
+    return (size_t)gather_warps(g) * g.ev_cap * (sizeof(unsigned long long) + sizeof(int));
+}
+
+}  // namespace
+
+cudaError_t prepare_rebin(const Geo& g) {
+    return cudaFuncSetAttribute(rebin_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gather_smem(g));
+}
+
 cudaError_t launch_rebin(const Geo& g, const Dev& d, int init_n, cudaStream_t s, int* launches) {
-    rebin_count<<<g.n_cells, kRebinThreads, 0, s>>>(g, d, init_n);
+    const int assign_blocks = init_n >= 0 ? std::max(1, (init_n + kRebinThreads - 1) / kRebinThreads)
+                                          : (g.n_cells + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    rebin_assign<<<assign_blocks, kRebinThreads, 0, s>>>(g, d, init_n);
     rebin_scan<<<1, 1024, 0, s>>>(g, d);
-    const size_t smem = (size_t)g.ev_cap * (4 * sizeof(double) + sizeof(unsigned long long));
-    rebin_gather<<<g.n_cells, kRebinThreads, smem, s>>>(g, d, init_n);
+    const int wpb = gather_warps(g);
+    rebin_gather<<<(g.n_cells + wpb - 1) / wpb, 32 * wpb, gather_smem(g), s>>>(g, d, init_n, wpb);
     if (launches) *launches += 3;
     return cudaGetLastError();
 }

@@ -826,7 +826,6 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const
     __syncthreads();
     for (int step = 0; step < g.k; ++step) {
         const int sl = step & 1;
-        if (S.err) break;
         const int valid = S.valid[sl];
         // ================ prepare step+1 (warp 0) || price step (warps 1..) =========
         if (wid == 0) {
@@ -836,7 +835,9 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const
             // barriers: these generic reads come first)
             price_step<STAGE>(g, d, S, sl);
         }
-        __syncthreads();
+        // errors are set before a barrier and read through its OR, so every
+        // thread leaves the loop at the same point
+        if (__syncthreads_or(S.err != 0)) break;
         // ================ decision (warp 0; float64 on lane 0) =====================
         if (wid == 0) {
             float2 t = (valid && lane > 0 && lane < nw) ? S.redf[lane] : make_float2(0.f, 0.f);
@@ -918,7 +919,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const
                 S.acc = do_commit;
             }
         }
-        __syncthreads();
+        if (__syncthreads_or(S.err != 0)) break;
         // ================ commit: re-synthesise V on the touched windows ============
         if (S.acc) {
             const T32* tk = S.tasks + sl * kMaxTasks32;
@@ -940,7 +941,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const
             __syncthreads();
             // the prepared next step assumed a rejection: prepare it again
             if (wid == 0 && step + 1 < g.k) prepare_step<STAGE>(g, d, S, step + 1, sl ^ 1);
-            __syncthreads();
+            if (__syncthreads_or(S.err != 0)) break;
         }
     }
     __syncthreads();

@@ -49,6 +49,7 @@ constexpr int kMaxTasks32 = 32;
 constexpr int kUnroll = 2;     // float4 groups whose loads a pricing thread issues together
 constexpr int kFrozen = -2;    // owner tag of an arrival from a neighbouring region
 constexpr int kMinBlocks32 = 3;   // resident CTAs per SM the kernel is built for
+static_assert(kThreads32 <= 256, "the decision reduces the worker warps' partials in a three-level tree");
 constexpr unsigned kWaitLimit = 1u << 24;   // bounded mbarrier waits
 
 struct A32 {            // arrival of an own event at a blanket slot (the event's cache)
@@ -115,6 +116,9 @@ struct Sm {
     float rl[4];        // region in relative coordinates: x lo, x hi, y lo, y hi
     int cell, n_own, n_free, n_blk, err, acc;
     int valid[2], idx[2], type[2], ncand[2], ntask[2], units[2], width[2];
+    double thr[2];      // accept iff the log-likelihood change exceeds this (log u minus the other terms of log alpha)
+    double dlp[2];      // log-prior change of the step
+    int nb_start[64], nb_cnt[64], nb_off[65];   // neighbouring cells of the region (prologue)
     P32 c[2];           // candidate of each step buffer
     int warp_cnt[32];
     float2 redf[32];
@@ -419,6 +423,24 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
             }
         }
         if (err) S.err = err;
+        if (valid && !err) {
+            // the state-dependent terms of log alpha, so that the decision is
+            // one comparison with the log-likelihood change
+            double thr, dlp;
+            if (dr.type == 0) {
+                thr = (double)dr.logu - S.tabB[n_own];
+                dlp = dr.blb;
+            } else if (dr.type == 1) {
+                thr = (double)dr.logu - S.tabD[n_own];
+                dlp = S.mm[ps] - g.lb0;
+            } else {
+                const double dm = __dsub_rn(c.m, S.mm[ps]);
+                thr = (double)dr.logu + dm;
+                dlp = -dm;
+            }
+            S.thr[sl] = thr;
+            S.dlp[sl] = dlp;
+        }
         S.valid[sl] = valid && !err;
         S.ntask[sl] = ntask;
         S.units[sl] = units;
@@ -693,48 +715,65 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const
     // (cell, id) order, then the region's own events in id order
     for (int b = tid; b < n_blk; b += nthr) S.scnt[b] = 0;
     {
-        const int P1 = g.period - 1;
-        for (int jy = iy - P1; jy <= iy + P1; ++jy) {
-            for (int jx = ix - P1; jx <= ix + P1; ++jx) {
-                if (jx < 0 || jy < 0 || jx >= g.ncx || jy >= g.ncy) continue;
-                const int oc = jy * g.ncx + jx;
-                if (oc == cell) continue;
-                const int s0 = St.start[oc], nn = St.count[oc];
-                if (nn == 0) continue;
-                __syncthreads();   // the previous cell's events fully consumed
-                if (nn > g.ev_cap) {
-                    if (tid == 0) S.err = CMH_ERR_CAPACITY;
-                    break;
-                }
-                for (int i = tid; i < nn; i += nthr) {
-                    const double t = St.t[s0 + i];
-                    S.nx[i] = St.x[s0 + i];
-                    S.ny[i] = St.y[s0 + i];
-                    S.nt[i] = t;
-                    event_terms32(g, t, St.m[s0 + i], S.nK[i], S.nph[i], S.nmf[i]);
-                }
-                __syncthreads();
-                for (int b = wid; b < n_blk; b += nw) {
-                    int nf = S.scnt[b];
-                    for (int i0 = 0; i0 < nn; i0 += 32) {
-                        const int i = i0 + lane;
-                        int k0 = 0;
-                        float E0 = 0.f;
-                        const bool r = i < nn && arrival32c(g, S.nx[i], S.ny[i], S.nt[i], S.nK[i], S.nph[i], S.nmf[i],
-                                                            S.bx[b], S.by[b], k0, E0);
-                        const unsigned bal = __ballot_sync(FULL, r);
-                        const int p = nf + __popc(bal & ((1u << lane) - 1));
-                        if (r && p < g.frz_cap) S.sarr[b * g.frz_cap + p] = SA{k0, E0, kFrozen, 0};
-                        nf += __popc(bal);
-                    }
-                    __syncwarp();
-                    if (lane == 0) {
-                        if (nf > g.frz_cap) atomicCAS(&S.err, 0, CMH_ERR_CAPACITY);
-                        S.scnt[b] = min(nf, g.frz_cap);
-                    }
-                    __syncwarp();
-                }
+        // the neighbouring cells' slices in one round, then their events in
+        // batches of up to ev_cap, in (cell, id) order
+        const int P1 = g.period - 1, side = 2 * P1 + 1, n_nb = side * side;
+        if (tid < n_nb) {
+            const int jx = ix - P1 + tid % side, jy = iy - P1 + tid / side;
+            int s0 = 0, nn = 0;
+            if (jx >= 0 && jy >= 0 && jx < g.ncx && jy < g.ncy && jy * g.ncx + jx != cell) {
+                s0 = St.start[jy * g.ncx + jx];
+                nn = St.count[jy * g.ncx + jx];
             }
+            S.nb_start[tid] = s0;
+            S.nb_cnt[tid] = nn;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int off = 0;
+            for (int q = 0; q < n_nb; ++q) {
+                S.nb_off[q] = off;
+                off += S.nb_cnt[q];
+            }
+            S.nb_off[n_nb] = off;
+        }
+        __syncthreads();
+        const int total = S.nb_off[n_nb];
+        for (int b0 = 0; b0 < total; b0 += g.ev_cap) {
+            const int nn = min(g.ev_cap, total - b0);
+            for (int i = tid; i < nn; i += nthr) {
+                const int gi = b0 + i;
+                int q = 0;
+                while (S.nb_off[q + 1] <= gi) ++q;
+                const int src = S.nb_start[q] + (gi - S.nb_off[q]);
+                const double t = St.t[src];
+                S.nx[i] = St.x[src];
+                S.ny[i] = St.y[src];
+                S.nt[i] = t;
+                event_terms32(g, t, St.m[src], S.nK[i], S.nph[i], S.nmf[i]);
+            }
+            __syncthreads();
+            for (int b = wid; b < n_blk; b += nw) {
+                int nf = S.scnt[b];
+                for (int i0 = 0; i0 < nn; i0 += 32) {
+                    const int i = i0 + lane;
+                    int k0 = 0;
+                    float E0 = 0.f;
+                    const bool r = i < nn && arrival32c(g, S.nx[i], S.ny[i], S.nt[i], S.nK[i], S.nph[i], S.nmf[i],
+                                                        S.bx[b], S.by[b], k0, E0);
+                    const unsigned bal = __ballot_sync(FULL, r);
+                    const int p = nf + __popc(bal & ((1u << lane) - 1));
+                    if (r && p < g.frz_cap) S.sarr[b * g.frz_cap + p] = SA{k0, E0, kFrozen, 0};
+                    nf += __popc(bal);
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    if (nf > g.frz_cap) atomicCAS(&S.err, 0, CMH_ERR_CAPACITY);
+                    S.scnt[b] = min(nf, g.frz_cap);
+                }
+                __syncwarp();
+            }
+            __syncthreads();   // this batch fully consumed
         }
     }
     __syncthreads();
@@ -840,8 +879,9 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const
         if (__syncthreads_or(S.err != 0)) break;
         // ================ decision (warp 0; float64 on lane 0) =====================
         if (wid == 0) {
+            // partials of warps 1..7 in lanes 1..7: a three-level tree
             float2 t = (valid && lane > 0 && lane < nw) ? S.redf[lane] : make_float2(0.f, 0.f);
-            for (int o = 16; o > 0; o >>= 1) {
+            for (int o = 4; o > 0; o >>= 1) {
                 float2 w2;
                 w2.x = __shfl_xor_sync(FULL, t.x, o);
                 w2.y = __shfl_xor_sync(FULL, t.y, o);
@@ -862,18 +902,9 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const
                     ++S.cnt[3 + type];
                     S.cnt[9] += (unsigned long long)S.width[sl];
                     dll = (double)t.x + (double)t.y;
-                    if (type == 0) {
-                        la = dll + S.tabB[n_own];
-                        dlp = dr.blb;
-                    } else if (type == 1) {
-                        la = dll + S.tabD[n_own];
-                        dlp = S.mm[S.order[idx]] - g.lb0;
-                    } else {
-                        const double dm = __dsub_rn(S.c[sl].m, S.mm[S.order[idx]]);
-                        la = dll - dm;
-                        dlp = -dm;
-                    }
-                    acc = (double)dr.logu < la;
+                    dlp = S.dlp[sl];
+                    acc = dll > S.thr[sl];
+                    if (d.trace) la = dll + ((double)dr.logu - S.thr[sl]);
                 }
                 if (d.trace) {
                     const long long slot = ((sweep - d.trace_sweep0) * g.n_cells + cell) * (long long)g.k + step;

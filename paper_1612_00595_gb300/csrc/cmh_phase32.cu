@@ -505,7 +505,8 @@ __device__ __forceinline__ void price_step(const Geo& g, const Dev& d, Sm& S, in
             const float bn = T.has_n ? arr_base32(g, T.E0n, T.k0n, k4) : 0.f;
             const float sv[4] = {s4[r].x, s4[r].y, s4[r].z, s4[r].w};
             const float vv[4] = {v4[r].x, v4[r].y, v4[r].z, v4[r].w};
-            float gs = 0.f;
+            float term[4], cnv[4];
+            unsigned need = 0;   // samples whose V' is rebuilt from the arrivals that stay
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int kk = k4 + e;
@@ -516,33 +517,55 @@ __device__ __forceinline__ void price_step(const Geo& g, const Dev& d, Sm& S, in
                 const float co = io ? __fmul_rn(bo, g.rho_f[e]) : 0.f;
                 const float cn = inn ? __fmul_rn(bn, g.rho_f[e]) : 0.f;
                 const float dd = cn - co;
+                cnv[e] = cn;
+                term[e] = 0.f;
                 if (kk < T.hi && dd != 0.f) {
                     const float V = vv[e], sm = sv[e];
                     const float Vp = V + dd;
-                    float term;
                     if (Vp < 0.5f * V) {
-                        // the changed arrival dominates V: rebuild V' from the arrivals
-                        // that stay on this station
-                        float a2 = g.noise_f, c2 = 0.f;
-                        const SA* L = S.sarr + T.slot * g.frz_cap;
-                        const int nl = S.scnt[T.slot];
-                        for (int o = 0; o < nl; ++o) {
-                            const SA A = L[o];
-                            if (A.own != T.skip && (unsigned)(kk - A.k0) < (unsigned)g.n_w)
-                                kahan_add32(a2, c2, arr_var32(g, A.E0, A.k0, kk));
-                        }
-                        if (inn) kahan_add32(a2, c2, cn);
-                        const float Vr = a2 - c2;
-                        term = __logf(__fdividef(Vr, V)) + sm * sm * (rcp_sfu(Vr) - rcp_sfu(V));
+                        need |= 1u << e;   // the changed arrival dominates V
                     } else {
-                        // log(V'/V) - s^2 d / (V V'), one reciprocal
-                        const float inv = rcp_sfu(V * Vp);
-                        term = log1p_fast(dd * Vp * inv) - sm * sm * dd * inv;
+                        // log(V'/V) - s^2 d / (V V'), one reciprocal (explicitly
+                        // rounded, so every build of this code gives the same bits)
+                        const float inv = rcp_sfu(__fmul_rn(V, Vp));
+                        const float x = __fmul_rn(__fmul_rn(dd, Vp), inv);
+                        const float q = __fmul_rn(__fmul_rn(sm, sm), __fmul_rn(dd, inv));
+                        term[e] = __fmul_rn(-0.5f, __fsub_rn(log1p_fast(x), q));
                     }
-                    gs += -0.5f * term;
                 }
             }
-            kahan_add32(acc, comp, gs);
+            if (need) {
+                // V' of the flagged samples from the arrivals that stay on this
+                // station (list order, compensated), one SFU evaluation per
+                // arrival for the group; the candidate's own arrival last
+                float a2[4], c2[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    a2[e] = g.noise_f;
+                    c2[e] = 0.f;
+                }
+                const SA* L = S.sarr + T.slot * g.frz_cap;
+                const int nl = S.scnt[T.slot];
+                for (int o = 0; o < nl; ++o) {
+                    const SA A = L[o];
+                    if (A.own == T.skip || (unsigned)(k4 + 3 - A.k0) >= (unsigned)(g.n_w + 3)) continue;
+                    const float base = arr_base32(g, A.E0, A.k0, k4);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (((need >> e) & 1u) && (unsigned)(k4 + e - A.k0) < (unsigned)g.n_w)
+                            kahan_add32(a2[e], c2[e], __fmul_rn(base, g.rho_f[e]));
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (!((need >> e) & 1u)) continue;
+                    if (cnv[e] != 0.f) kahan_add32(a2[e], c2[e], cnv[e]);
+                    const float V = vv[e], sm = sv[e];
+                    const float Vr = a2[e] - c2[e];
+                    const float q = __fmul_rn(__fmul_rn(sm, sm), __fsub_rn(rcp_sfu(Vr), rcp_sfu(V)));
+                    term[e] = __fmul_rn(-0.5f, __fadd_rn(__logf(__fdividef(Vr, V)), q));
+                }
+            }
+            kahan_add32(acc, comp, __fadd_rn(__fadd_rn(__fadd_rn(term[0], term[1]), term[2]), term[3]));
         }
     }
     float2 v = make_float2(acc, -comp);
@@ -959,13 +982,26 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const
                 const SA* L = S.sarr + T.slot * g.frz_cap;
                 const int nl = S.scnt[T.slot];
                 float* vrow = (float*)d.V + (size_t)T.row * g.pitch;
-                for (int kk = T.lo + tid; kk < T.hi; kk += nthr) {
-                    float a2 = g.noise_f, c2 = 0.f;
+                // groups of four samples: one SFU evaluation per arrival and group
+                for (int k4 = ((T.lo >> 2) + tid) << 2; k4 < T.hi; k4 += nthr << 2) {
+                    float a2[4], c2[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        a2[e] = g.noise_f;
+                        c2[e] = 0.f;
+                    }
                     for (int o = 0; o < nl; ++o) {
                         const SA A = L[o];
-                        if ((unsigned)(kk - A.k0) < (unsigned)g.n_w) kahan_add32(a2, c2, arr_var32(g, A.E0, A.k0, kk));
+                        if ((unsigned)(k4 + 3 - A.k0) >= (unsigned)(g.n_w + 3)) continue;
+                        const float base = arr_base32(g, A.E0, A.k0, k4);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if ((unsigned)(k4 + e - A.k0) < (unsigned)g.n_w)
+                                kahan_add32(a2[e], c2[e], __fmul_rn(base, g.rho_f[e]));
                     }
-                    vrow[kk] = a2 - c2;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (k4 + e >= T.lo && k4 + e < T.hi) vrow[k4 + e] = a2[e] - c2[e];
                 }
             }
             if (STAGE) fence_async_global();   // the new V is visible to the next bulk copies

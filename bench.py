@@ -45,6 +45,32 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+KERNEL_SOURCES = ["paper_1612_00595_gb300/csrc/cmh_phase32.cu", "paper_1612_00595_gb300/csrc/cmh_common.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "phase32_scale_dram.json")
+
+
+def _kernel_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _traffic():
+    """DRAM bytes per launch of the colour-phase kernel from the committed ncu
+    capture, or None when the kernel sources changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None, "no ncu capture committed"
+    if rec.get("kernel_sha256") != _kernel_digest():
+        return None, "kernel changed since the ncu capture"
+    return float(rec["dram_bytes_per_launch"]), rec.get("command", "")
+
+
 def _workload(name: str):
     if name == "scale":
         return worldgen.config_scale(seed=SEED), "fp32 sweep at scale: 4000x4000 km, 24 h, ~1e4 events, " \
@@ -229,9 +255,10 @@ def run_ours(args):
     per_launch_s = phase_ms / 1e3 / max(n_launch, 1)
     peaks, peak_kind = _peaks()
     achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
+    traffic, traffic_src = _traffic() if f32 else (None, "float64 path not captured")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-            "kernel": "phase_kernel<float32>" if f32 else "phase_kernel<float64>",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": traffic_src,
+            "kernel": "phase32_kernel<false> (float32 colour phase)" if f32 else "phase_kernel (float64 replay)",
             "avg_launch_us": per_launch_s * 1e6, "alg_bytes_per_launch": per_launch_bytes,
             "peak_source": peak_kind}
     m.destroy()
@@ -287,7 +314,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scale", choices=["scale", "replay"])

@@ -79,6 +79,10 @@ typedef struct {
                               read from global memory); -1: one window, cut down to what
                               keeps three CTAs resident per SM; > 0: that many (rounded
                               down to a multiple of 4) */
+    int32_t schedule;      /* float32 form: 0 = one persistent launch per sweep in which each
+                              region waits only for its neighbouring regions of lower colours
+                              (same results as colour by colour, shorter tails); 1 = one launch
+                              per colour phase.  The float64 form always runs colour by colour */
     int64_t max_events;    /* capacity of the whole event store; 0: 4 (n0 + Lambda) + 4096 */
 } cmh_params;
 

@@ -41,7 +41,7 @@ class Params(C.Structure):
                  "R_max", "p_birth", "p_death", "sig_xy", "sig_t", "sig_m")] + [
         ("k_per_phase", C.c_int32), ("commit", C.c_int32), ("seed", C.c_uint64), ("dtype", C.c_int32),
         ("ev_capacity", C.c_int32), ("frozen_capacity", C.c_int32), ("block_threads", C.c_int32),
-        ("stage_samples", C.c_int32), ("max_events", C.c_int64)]
+        ("stage_samples", C.c_int32), ("schedule", C.c_int32), ("max_events", C.c_int64)]
 
 
 class Grid(C.Structure):
@@ -124,7 +124,7 @@ def _ptr(a):
 
 def make_params(model_params, *, k_per_phase=32, seed=1, dtype=F64, p_birth=0.25, p_death=0.25,
                 sig_xy=5.0, sig_t=2.0, sig_m=0.1, commit=True, ev_capacity=0, frozen_capacity=0,
-                block_threads=0, stage_samples=0, max_events=0) -> Params:
+                block_threads=0, stage_samples=0, schedule=0, max_events=0) -> Params:
     """cmh_params from an object with the model fields (e.g. worldgen.ModelParams)."""
     p = Params()
     for n in ("W", "T", "Lambda", "v", "alpha", "beta_att", "tau", "t_s", "noise_var", "f_hz", "R_max"):
@@ -139,6 +139,7 @@ def make_params(model_params, *, k_per_phase=32, seed=1, dtype=F64, p_birth=0.25
     p.frozen_capacity = frozen_capacity
     p.block_threads = block_threads
     p.stage_samples = stage_samples
+    p.schedule = schedule
     p.max_events = max_events
     return p
 

@@ -61,6 +61,7 @@ struct cmh_model {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     int timing = 0;
+    int sweep_grid = 0;               // CTAs of the persistent sweep kernel (0: colour by colour)
     double phase_ms = 0.0;
     long long phase_launches = 0;
     int latched = 0;
@@ -185,7 +186,7 @@ int validate_params(const cmh_params* p) {
     if (p->k_per_phase < 1 || p->k_per_phase > kMaxK) return CMH_ERR_ARG;
     if (p->dtype != CMH_F32 && p->dtype != CMH_F64) return CMH_ERR_ARG;
     if (p->ev_capacity < 0 || p->frozen_capacity < 0 || p->max_events < 0) return CMH_ERR_ARG;
-    if (p->stage_samples < -1) return CMH_ERR_ARG;
+    if (p->stage_samples < -1 || (p->schedule != 0 && p->schedule != 1)) return CMH_ERR_ARG;
     if (p->block_threads != 0 && (p->block_threads < 64 || p->block_threads > 512 || p->block_threads % 32))
         return CMH_ERR_ARG;
     const double nw = std::llround(p->t_s * p->f_hz);
@@ -221,7 +222,11 @@ int capture_graph(cmh_model* m) {
     CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
     int l = 0;
     cudaError_t e = launch_rebin(m->g, m->d, -1, m->stream, &l);
-    for (int c = 0; c < m->g.n_colours && e == cudaSuccess; ++c) e = launch_phase(m->g, m->d, c, m->stream);
+    if (m->sweep_grid > 0) {
+        if (e == cudaSuccess) e = launch_sweep32(m->g, m->d, m->sweep_grid, m->stream);
+    } else {
+        for (int c = 0; c < m->g.n_colours && e == cudaSuccess; ++c) e = launch_phase(m->g, m->d, c, m->stream);
+    }
     if (e == cudaSuccess) e = launch_sweep_end(m->g, m->d, m->stream);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(m->stream, &graph);
@@ -235,7 +240,7 @@ int capture_graph(cmh_model* m) {
     return CMH_OK;
 }
 
-int launches_per_sweep(const cmh_model* m) { return 3 + m->g.n_colours + 1; }
+int launches_per_sweep(const cmh_model* m) { return 3 + (m->sweep_grid > 0 ? 1 : m->g.n_colours) + 1; }
 
 // grow the flat list to `cap` events, keeping its first n_keep
 int ensure_flat(cmh_model* m, long long cap, int n_keep) {
@@ -530,6 +535,8 @@ int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mo
     CK(prepare_kernels(g));
     CK(prepare_phase32(g));
     CK(prepare_rebin(g));
+    m->sweep_grid = 0;
+    if (g.f32 && m->p.schedule == 0) CK(sweep32_grid(g, &m->sweep_grid));
 
     Dev& d = m->d;
     cudaError_t e;
@@ -548,8 +555,12 @@ int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mo
     if ((e = m->alloc(&d.colour_count, kMaxColours, true)) ||
         (e = m->alloc(&d.colour_cells, (size_t)g.n_colours * g.max_rpc, true)) ||
         (e = m->alloc(&d.fill, g.n_cells, true)) || (e = m->alloc(&d.ncell, g.store_cap, true)) ||
+        (e = m->alloc(&d.cell_col, g.n_cells, true)) || (e = m->alloc(&d.colour_off, kMaxColours + 1, true)) ||
+        (e = m->alloc(&d.queue, 1, true)) || (e = m->alloc(&d.done, g.n_cells, true)) ||
         (e = m->alloc(&d.region_dlp, g.n_cells, true)))
         return cuda_err(e);
+    CK(cudaMemsetAsync(d.done, 0, sizeof(long long) * g.n_cells, m->stream));
+    CK(cudaMemsetAsync(d.colour_off, 0, sizeof(int) * (kMaxColours + 1), m->stream));
     CK(cudaMemsetAsync(d.fill, 0, sizeof(int) * g.n_cells, m->stream));
     CK(cudaMemsetAsync(d.region_dlp, 0, sizeof(double) * g.n_cells, m->stream));
     CK(cudaMemsetAsync(d.colour_count, 0, sizeof(int) * kMaxColours, m->stream));
@@ -577,14 +588,17 @@ int cmh_run_sweeps(cmh_model* m, int64_t n) {
         for (int64_t i = 0; i < n && rc == CMH_OK; ++i) {
             int l = 0;
             cudaError_t e = launch_rebin(m->g, m->d, -1, m->stream, &l);
-            for (int c = 0; c < m->g.n_colours && e == cudaSuccess; ++c) {
+            // one timed launch per colour phase, or one per sweep (persistent)
+            const int n_launch = m->sweep_grid > 0 ? 1 : m->g.n_colours;
+            for (int c = 0; c < n_launch && e == cudaSuccess; ++c) {
                 cudaEvent_t a, b;
                 cudaEventCreate(&a);
                 cudaEventCreate(&b);
                 ev.push_back(a);
                 ev.push_back(b);
                 cudaEventRecord(a, m->stream);
-                e = launch_phase(m->g, m->d, c, m->stream);
+                e = m->sweep_grid > 0 ? launch_sweep32(m->g, m->d, m->sweep_grid, m->stream)
+                                      : launch_phase(m->g, m->d, c, m->stream);
                 cudaEventRecord(b, m->stream);
             }
             if (e == cudaSuccess) e = launch_sweep_end(m->g, m->d, m->stream);

@@ -67,6 +67,10 @@ struct Dev {
     int* colour_cells;          // [n_colours][max_rpc]
     int* fill;                  // [n_cells] events counted into each new cell (cleared by the scan)
     int* ncell;                 // [store_cap] new cell of the event at each position of the old store
+    int* cell_col;              // [n_cells] colour of each live cell of the current sweep, -1 if not live
+    int* colour_off;            // [n_colours + 1] first queue item of each colour (persistent sweep)
+    int* queue;                 // next queue item (persistent sweep)
+    long long* done;            // [n_cells] last sweep + 1 whose phase the cell's region has finished
     double* region_dlp;         // [n_cells] log-density change of the current sweep
     double* logp;               // running log-density
     int* status;                // latched CMH_ERR_* (0 = fine)
@@ -261,6 +265,8 @@ cudaError_t launch_phase32(const Geo& g, const Dev& d, int colour, cudaStream_t 
 size_t phase32_smem_bytes(const Geo& g);
 cudaError_t prepare_phase32(const Geo& g);
 cudaError_t choose_stage_cap(Geo& g, int requested);
+cudaError_t sweep32_grid(const Geo& g, int* grid);
+cudaError_t launch_sweep32(const Geo& g, const Dev& d, int grid, cudaStream_t s);
 cudaError_t launch_sweep_end(const Geo& g, const Dev& d, cudaStream_t s);
 size_t phase_smem_bytes(const Geo& g);
 cudaError_t launch_vsynth(const Geo& g, const Dev& d, const FlatList& f, cudaStream_t s, int* launches);

@@ -166,12 +166,26 @@ __global__ void __launch_bounds__(1024) rebin_scan(Geo g, Dev d) {
     // position (rank of iy) x (live columns of its residue) + (rank of ix)
     for (int c = threadIdx.x; c < g.n_cells; c += blockDim.x) {
         const int ix = c % g.ncx, iy = c / g.ncx;
-        if (!(s_live[0][ix] && s_live[1][iy])) continue;
+        if (!(s_live[0][ix] && s_live[1][iy])) {
+            d.cell_col[c] = -1;
+            continue;
+        }
         const int col = (ix % P) + P * (iy % P);
+        d.cell_col[c] = col;
         d.colour_cells[col * g.max_rpc + s_rank[1][iy] * s_num[0][ix % P] + s_rank[0][ix]] = c;
     }
     for (int col = threadIdx.x; col < g.n_colours; col += blockDim.x)
         d.colour_count[col] = s_num[0][col % P] * s_num[1][col / P];
+    // the queue of the persistent sweep: regions in colour order
+    if (threadIdx.x == 0) {
+        int off = 0;
+        for (int col = 0; col < g.n_colours; ++col) {
+            d.colour_off[col] = off;
+            off += s_num[0][col % P] * s_num[1][col / P];
+        }
+        d.colour_off[g.n_colours] = off;
+        *d.queue = 0;
+    }
 }
 
 __global__ void __launch_bounds__(kRebinThreads) rebin_gather(Geo g, Dev d, int init_n, int wpb) {

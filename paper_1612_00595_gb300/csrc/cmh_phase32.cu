@@ -605,19 +605,28 @@ __device__ __forceinline__ void lists_add(const Geo& g, Sm& S, int ps, const A32
     }
 }
 
+// the mbarriers of the staging buffers, once per CTA (their phase bits carry
+// over from one region to the next; every region leaves no copy in flight)
 template <bool STAGE>
-__global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const __grid_constant__ Geo g,
-                                                                           const __grid_constant__ Dev d, int colour) {
-    if (*d.status) return;
-    const long long sweep = *d.sweep;
-    if ((int)blockIdx.x >= d.colour_count[colour]) return;
-    const int cell = d.colour_cells[colour * g.max_rpc + blockIdx.x];
+__device__ __forceinline__ void init_staging(Sm& S) {
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b) {
+            S.ph[b] = 0;
+            S.on[b] = 0;
+            if (STAGE) mbar_init(&S.bar[b], 1);
+        }
+        if (STAGE) fence_async_shared();   // the initialised barriers are visible to the async proxy
+    }
+}
+
+// one colour phase of one region (every thread of the CTA): load the region,
+// run its k MH steps, write it back
+template <bool STAGE>
+__device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cell, long long sweep, Sm& S,
+                                             unsigned char* smem) {
     const Store St = d.st[sweep & 1];
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
     const int ix = cell % g.ncx, iy = cell / g.ncx;
-
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ Sm S;
     const int start = St.start[cell], n0 = St.count[cell];
     if (tid == 0) {
         layout32(g, &S, smem);
@@ -636,16 +645,11 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const
         S.n_free = g.ev_cap - n0;
         S.region_dlp = 0.0;
         S.acc = 0;
-        for (int b = 0; b < 2; ++b) {
-            S.ph[b] = 0;
-            S.on[b] = 0;
-            if (STAGE) mbar_init(&S.bar[b], 1);
-        }
-        if (STAGE) fence_async_shared();   // the initialised barriers are visible to the async proxy
     }
     if (tid < 11) S.cnt[tid] = 0;
-    __syncthreads();
-    if (S.err) {
+    // only thread 0 has S.err initialised yet: the others would read what an
+    // earlier CTA left in this shared memory
+    if (__syncthreads_or(tid == 0 && S.err != 0)) {
         if (tid == 0) latch(d.status, S.err);
         return;
     }
@@ -878,8 +882,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const
         }
         S.draws[st] = D;
     }
-    __syncthreads();
-    if (S.err) {
+    if (__syncthreads_or(S.err != 0)) {
         if (tid == 0) latch(d.status, S.err);
         return;
     }
@@ -1018,8 +1021,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const
                 if (!mbar_wait(&S.bar[b], (unsigned)S.ph[b])) S.err = CMH_ERR_TIMEOUT;
                 S.on[b] = 0;
             }
-    __syncthreads();
-    if (S.err) {
+    if (__syncthreads_or(S.err != 0)) {
         if (tid == 0) latch(d.status, S.err);
         return;
     }
@@ -1037,6 +1039,98 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const
         d.region_dlp[cell] = S.region_dlp;
         for (int t = 0; t < 11; ++t)
             if (S.cnt[t]) atomicAdd(&d.stats[t], S.cnt[t]);
+    }
+}
+
+// one colour phase: a CTA per region of the colour
+template <bool STAGE>
+__global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const __grid_constant__ Geo g,
+                                                                           const __grid_constant__ Dev d, int colour) {
+    if (*d.status) return;
+    const long long sweep = *d.sweep;
+    if ((int)blockIdx.x >= d.colour_count[colour]) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Sm S;
+    init_staging<STAGE>(S);
+    region_phase<STAGE>(g, d, d.colour_cells[colour * g.max_rpc + blockIdx.x], sweep, S, smem);
+}
+
+__device__ __forceinline__ long long ld_acquire(const long long* p) {
+    long long v;
+    asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(long long* p, long long v) {
+    asm volatile("st.release.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+constexpr unsigned kDepWaitLimit = 1u << 22;   // bounded waits for neighbouring regions
+
+// All colour phases of one sweep in one persistent launch.  Regions are
+// taken from a queue in colour order (colour 0's regions first, each
+// colour's in its list order); a region waits only until its neighbouring
+// regions of lower colours have finished this sweep (the regions whose
+// blankets share stations with its own), then runs its phase.  A region of
+// a higher colour waits for it in turn, so every region sees its
+// neighbours' state exactly as in the colour-by-colour schedule, and the
+// results do not depend on the order in which CTAs take regions.  Every
+// region a CTA waits for was taken earlier by a CTA that is running, so the
+// waits end; they are bounded all the same (CMH_ERR_TIMEOUT).
+template <bool STAGE>
+__global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_kernel(const __grid_constant__ Geo g,
+                                                                           const __grid_constant__ Dev d) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Sm S;
+    __shared__ int s_cell, s_run;
+    __shared__ long long s_sweep;
+    init_staging<STAGE>(S);
+    for (;;) {
+        // thread 0 takes the next region and broadcasts it (-1: none left)
+        if (threadIdx.x == 0) {
+            const int total = d.colour_off[g.n_colours];
+            const int it = *(volatile int*)d.status ? total : atomicAdd(d.queue, 1);
+            int colour = 0, cell = -1;
+            if (it < total) {
+                while (colour + 1 < g.n_colours && it >= d.colour_off[colour + 1]) ++colour;
+                cell = d.colour_cells[colour * g.max_rpc + (it - d.colour_off[colour])];
+            }
+            s_cell = cell;
+            s_sweep = *d.sweep;
+            s_run = colour;
+        }
+        __syncthreads();
+        const int cell = s_cell;
+        if (cell < 0) break;
+        const long long sweep = s_sweep, stamp = sweep + 1;
+        if (threadIdx.x == 0) {
+            const int colour = s_run;
+            const int P1 = g.period - 1, ix = cell % g.ncx, iy = cell / g.ncx;
+            for (int jy = iy - P1; jy <= iy + P1; ++jy)
+                for (int jx = ix - P1; jx <= ix + P1; ++jx) {
+                    if (jx < 0 || jy < 0 || jx >= g.ncx || jy >= g.ncy) continue;
+                    const int nb = jy * g.ncx + jx;
+                    const int c = d.cell_col[nb];
+                    if (nb == cell || c < 0 || c >= colour) continue;
+                    unsigned n = 0;
+                    while (ld_acquire(d.done + nb) < stamp && !*(volatile int*)d.status) {
+                        if (++n >= kDepWaitLimit) {
+                            latch(d.status, CMH_ERR_TIMEOUT);
+                            break;
+                        }
+                        __nanosleep(128);
+                    }
+                }
+            if (STAGE) fence_async_global();   // the neighbours' V writes before any bulk copy of them
+            s_run = *(volatile int*)d.status == 0;
+        }
+        __syncthreads();
+        if (s_run) region_phase<STAGE>(g, d, cell, sweep, S, smem);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(d.done + cell, stamp);
+        }
     }
 }
 
@@ -1080,9 +1174,37 @@ cudaError_t choose_stage_cap(Geo& g, int requested) {
 
 cudaError_t prepare_phase32(const Geo& g) {
     const int bytes = (int)phase32_smem_bytes(g);
-    cudaError_t e = cudaFuncSetAttribute(phase32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(phase32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(phase32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) ||
+        (e = cudaFuncSetAttribute(phase32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) ||
+        (e = cudaFuncSetAttribute(sweep32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) ||
+        (e = cudaFuncSetAttribute(sweep32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
+        return e;
+    return cudaSuccess;
+}
+
+// CTAs of the persistent sweep kernel: as many as can be resident at once
+// (at most kMinBlocks32 per SM, never more than the regions of a sweep)
+cudaError_t sweep32_grid(const Geo& g, int* grid) {
+    int dev = 0, n_sm = 1, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)))
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+             &per_sm, g.stage_cap > 0 ? (const void*)sweep32_kernel<true> : (const void*)sweep32_kernel<false>,
+             kThreads32, phase32_smem_bytes(g))))
+        return e;
+    per_sm = std::max(1, std::min(per_sm, kMinBlocks32));
+    *grid = std::max(1, std::min(n_sm * per_sm, g.n_colours * g.max_rpc));
+    return cudaSuccess;
+}
+
+cudaError_t launch_sweep32(const Geo& g, const Dev& d, int grid, cudaStream_t s) {
+    if (g.stage_cap > 0)
+        sweep32_kernel<true><<<grid, kThreads32, phase32_smem_bytes(g), s>>>(g, d);
+    else
+        sweep32_kernel<false><<<grid, kThreads32, phase32_smem_bytes(g), s>>>(g, d);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_phase32(const Geo& g, const Dev& d, int colour, cudaStream_t s) {

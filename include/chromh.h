@@ -209,6 +209,31 @@ int cmh_restore(cmh_model* m, const void* buf, size_t len);
 void cmh_destroy(cmh_model* m);
 const char* cmh_strerror(int code);
 
+/* ---- batches of independent models (same library, float32 form) -----------
+ * A batch sweeps many independent models together: one sweep of every model
+ * per step, the re-binning of all models in three launches, and every
+ * region of every model in one persistent launch fed by a device work queue
+ * (colour order across models; a region waits only for its own model's
+ * neighbouring regions of lower colours), captured in one CUDA graph.  The
+ * chains are the ones cmh_run_sweeps gives each model alone.
+ *
+ * cmh_batch_create: models[0..n_models) must be distinct, partitioned, of
+ *   dtype CMH_F32, without staging (stage_samples 0) and with ev_capacity
+ *   <= 512 (CMH_ERR_ARG otherwise; CMH_ERR_STATE for an unpartitioned or
+ *   failed model).  The batch refers to the models (it does not own them)
+ *   and to their current partitions; cuda_stream may be NULL (the batch
+ *   creates its own).  Destroy the batch before its models.
+ * cmh_batch_run_sweeps: n sweeps of every model; returns after they finish.
+ *   CMH_ERR_STATE if a model failed or was re-partitioned since the batch
+ *   was made; a device-side error of a model is latched in that model and
+ *   the first one is returned.  Each model's state, statistics and sweep
+ *   count advance as if cmh_run_sweeps(model, n) had run.
+ */
+typedef struct cmh_batch cmh_batch;
+int cmh_batch_create(cmh_model* const* models, int32_t n_models, void* cuda_stream, cmh_batch** out);
+int cmh_batch_run_sweeps(cmh_batch* b, int64_t n);
+void cmh_batch_destroy(cmh_batch* b);
+
 /*
  * Sum over rows r < n_rows and samples k < n_samples of the Gaussian
  * log-density log N(signals[r][k]; 0, variance[r][k]), for callers that cannot

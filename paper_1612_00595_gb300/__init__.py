@@ -69,7 +69,7 @@ TRACE_DTYPE = np.dtype([("sweep", "<i4"), ("cell", "<i4"), ("step", "<i4"), ("ty
 EXPORTS = ["cmh_create_model", "cmh_partition_and_color", "cmh_run_sweeps", "cmh_read_state", "cmh_sync",
            "cmh_log_density", "cmh_set_trace", "cmh_read_trace", "cmh_set_timing", "cmh_read_shift",
            "cmh_checkpoint", "cmh_restore", "cmh_destroy", "cmh_strerror", "cmh_philox4x64",
-           "cmh_gaussian_loglik_noalloc"]
+           "cmh_gaussian_loglik_noalloc", "cmh_batch_create", "cmh_batch_run_sweeps", "cmh_batch_destroy"]
 
 
 def _load():
@@ -98,6 +98,9 @@ def _load():
         "cmh_strerror": (C.c_char_p, [C.c_int]),
         "cmh_philox4x64": (C.c_int, [P, P, P, i64]),
         "cmh_gaussian_loglik_noalloc": (C.c_int, [P, P, i32, i64, i64, i32, C.POINTER(C.c_double), P]),
+        "cmh_batch_create": (C.c_int, [C.POINTER(P), i32, P, C.POINTER(P)]),
+        "cmh_batch_run_sweeps": (C.c_int, [P, i64]),
+        "cmh_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -275,6 +278,37 @@ def create_model(events, stations, signals, params: Params, stream=None) -> Mode
                                 C.c_void_p(stream) if stream else None, C.byref(h)),
            "cmh_create_model")
     return Model(h, keep[:0])
+
+
+class Batch:
+    """A cmh_batch: independent float32 models swept together (see create_batch)."""
+
+    def __init__(self, handle, models):
+        self._h = handle
+        self._models = list(models)   # the batch refers to them: keep them alive
+
+    def __del__(self):
+        self.destroy()
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.cmh_batch_destroy(self._h)
+        self._h = None
+
+    def run_sweeps(self, n: int):
+        _check(lib.cmh_batch_run_sweeps(self._h, n), "cmh_batch_run_sweeps")
+
+
+def create_batch(models, stream=None) -> Batch:
+    """One persistent launch per sweep for every region of every model (each
+    partitioned, float32, no staging); destroy the batch before the models."""
+    arr = (C.c_void_p * len(models))(*[m._h.value for m in models])
+    if hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    h = C.c_void_p()
+    _check(lib.cmh_batch_create(arr, len(models), C.c_void_p(stream) if stream else None, C.byref(h)),
+           "cmh_batch_create")
+    return Batch(h, models)
 
 
 def partition_and_color(model: Model, L: float, shift_mode: int = 1, sx: float = 0.0, sy: float = 0.0):

@@ -13,6 +13,8 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "chromh.h"
@@ -41,6 +43,24 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
 }  // namespace
 
+namespace cmh {
+
+cudaError_t raise_smem_limit(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> limit;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = limit[{dev, func}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
+}  // namespace cmh
+
 struct cmh_model {
     cmh_params p{};
     Geo g{};
@@ -62,6 +82,7 @@ struct cmh_model {
     cudaGraphExec_t graph_exec = nullptr;
     int timing = 0;
     int sweep_grid = 0;               // CTAs of the persistent sweep kernel (0: colour by colour)
+    long long part_gen = 0;           // partitions made so far (a batch refuses a re-partitioned model)
     double phase_ms = 0.0;
     long long phase_launches = 0;
     int latched = 0;
@@ -573,6 +594,7 @@ int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mo
     int rc = bin_flat_into_current(m, n_flat);
     if (rc) return rc;
     m->partitioned = true;
+    m->part_gen += 1;
     if (n_colors_out) *n_colors_out = g.n_colours;
     return CMH_OK;
 }
@@ -874,3 +896,122 @@ int cmh_philox4x64(const uint64_t* ctr, const uint64_t* key, uint64_t* out, int6
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batches of independent models
+// ---------------------------------------------------------------------------
+struct cmh_batch {
+    std::vector<cmh_model*> models;
+    std::vector<long long> gens;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Geo* G = nullptr;
+    Dev* D = nullptr;
+    int* blk_off = nullptr;
+    int* item_tab = nullptr;
+    int* queue = nullptr;
+    int n = 0, n_blocks = 0, max_ev_cap = 0, n_col = 0, grid = 0;
+    size_t smem = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+
+    void release() {
+        if (stream) cudaStreamSynchronize(stream);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (void* q : {(void*)G, (void*)D, (void*)blk_off, (void*)item_tab, (void*)queue})
+            if (q) cudaFree(q);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+constexpr int kBatchLaunchesPerSweep = 6;   // assign, scan, gather, plan, phase, sweep end
+
+extern "C" int cmh_batch_create(cmh_model* const* models, int32_t n_models, void* cuda_stream, cmh_batch** out) {
+    if (!out || !models || n_models < 1) return CMH_ERR_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n_models; ++i) {
+        const cmh_model* m = models[i];
+        if (!m) return CMH_ERR_ARG;
+        for (int j = 0; j < i; ++j)
+            if (models[j] == m) return CMH_ERR_ARG;   // each model once
+        if (!m->partitioned || m->latched) return CMH_ERR_STATE;
+        if (!m->g.f32 || m->g.stage_cap != 0 || m->g.ev_cap > 512) return CMH_ERR_ARG;
+    }
+    cmh_batch* b = new cmh_batch;
+    auto fail = [&](int rc) {
+        b->release();
+        delete b;
+        return rc;
+    };
+    b->n = n_models;
+    b->models.assign(models, models + n_models);
+    b->stream = (cudaStream_t)cuda_stream;
+    if (!b->stream) {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(CMH_ERR_CUDA);
+        b->own_stream = true;
+    }
+    std::vector<Geo> hg(n_models);
+    std::vector<Dev> hd(n_models);
+    std::vector<int> off(n_models + 1, 0);
+    for (int i = 0; i < n_models; ++i) {
+        cmh_model* m = models[i];
+        if (cudaStreamSynchronize(m->stream) != cudaSuccess) return fail(CMH_ERR_CUDA);
+        hg[i] = m->g;
+        hd[i] = m->d;
+        b->gens.push_back(m->part_gen);
+        off[i + 1] = off[i] + rebin_blocks(m->g);
+        b->max_ev_cap = std::max(b->max_ev_cap, m->g.ev_cap);
+        b->n_col = std::max(b->n_col, m->g.n_colours);
+        b->smem = std::max(b->smem, phase32_smem_bytes(m->g));
+    }
+    b->n_blocks = off[n_models];
+    if (b->smem > 227 * 1024) return fail(CMH_ERR_CAPACITY);
+    if (cudaMalloc(&b->G, sizeof(Geo) * n_models) || cudaMalloc(&b->D, sizeof(Dev) * n_models) ||
+        cudaMalloc(&b->blk_off, sizeof(int) * (n_models + 1)) ||
+        cudaMalloc(&b->item_tab, sizeof(int) * ((size_t)b->n_col * n_models + 1)) ||
+        cudaMalloc(&b->queue, sizeof(int)))
+        return fail(CMH_ERR_OOM);
+    if (cudaMemcpy(b->G, hg.data(), sizeof(Geo) * n_models, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(b->D, hd.data(), sizeof(Dev) * n_models, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(b->blk_off, off.data(), sizeof(int) * (n_models + 1), cudaMemcpyHostToDevice))
+        return fail(CMH_ERR_CUDA);
+    if (prepare_rebin_batch(b->max_ev_cap) || prepare_sweep32_batch(b->smem, &b->grid)) return fail(CMH_ERR_CUDA);
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(CMH_ERR_CUDA);
+    cudaError_t e = launch_rebin_batch(b->G, b->D, b->blk_off, b->n, b->n_blocks, b->max_ev_cap, b->stream);
+    if (e == cudaSuccess)
+        e = launch_sweep32_batch(b->G, b->D, b->n, b->n_col, b->item_tab, b->queue, b->smem, b->grid, b->stream);
+    if (e == cudaSuccess) e = launch_sweep_end_batch(b->G, b->D, b->n, b->stream);
+    const cudaError_t e2 = cudaStreamEndCapture(b->stream, &b->graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) return fail(CMH_ERR_CUDA);
+    if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) return fail(CMH_ERR_CUDA);
+    *out = b;
+    return CMH_OK;
+}
+
+extern "C" int cmh_batch_run_sweeps(cmh_batch* b, int64_t n) {
+    if (!b || n < 0) return CMH_ERR_ARG;
+    for (int i = 0; i < b->n; ++i) {
+        const cmh_model* m = b->models[i];
+        if (m->latched || !m->partitioned || m->part_gen != b->gens[i]) return CMH_ERR_STATE;
+    }
+    for (int i = 0; i < b->n; ++i)   // the models' own queued work first
+        CK(cudaStreamSynchronize(b->models[i]->stream));
+    for (int64_t s = 0; s < n; ++s) CK(cudaGraphLaunch(b->exec, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    int rc = CMH_OK;
+    for (int i = 0; i < b->n; ++i) {
+        cmh_model* m = b->models[i];
+        m->sweeps += n;
+        m->launches += n * kBatchLaunchesPerSweep;
+        const int st = check_status(m);
+        if (st && rc == CMH_OK) rc = st;
+    }
+    return rc;
+}
+
+extern "C" void cmh_batch_destroy(cmh_batch* b) {
+    if (!b) return;
+    b->release();
+    delete b;
+}

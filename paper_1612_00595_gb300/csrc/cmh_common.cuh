@@ -258,7 +258,19 @@ struct FlatList {
 };
 
 // host-side launchers (defined in the .cu files)
+// raise a kernel's dynamic shared-memory limit to at least `bytes`, never
+// lowering it (the attribute is shared by every model of the process)
+cudaError_t raise_smem_limit(const void* func, size_t bytes);
 cudaError_t launch_rebin(const Geo& g, const Dev& d, int init_n, cudaStream_t s, int* launches);
+// a batch of independent instances (device arrays of their Geo and Dev)
+int rebin_blocks(const Geo& g);
+cudaError_t prepare_rebin_batch(int max_ev_cap);
+cudaError_t launch_rebin_batch(const Geo* G, const Dev* D, const int* blk_off, int n_inst, int n_blocks,
+                               int max_ev_cap, cudaStream_t s);
+cudaError_t prepare_sweep32_batch(size_t smem_bytes, int* grid);
+cudaError_t launch_sweep32_batch(const Geo* G, const Dev* D, int n_inst, int n_col, int* item_tab, int* queue,
+                                 size_t smem_bytes, int grid, cudaStream_t s);
+cudaError_t launch_sweep_end_batch(const Geo* G, const Dev* D, int n_inst, cudaStream_t s);
 cudaError_t prepare_rebin(const Geo& g);
 cudaError_t launch_phase(const Geo& g, const Dev& d, int colour, cudaStream_t s);
 cudaError_t launch_phase32(const Geo& g, const Dev& d, int colour, cudaStream_t s);

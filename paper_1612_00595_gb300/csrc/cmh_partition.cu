@@ -52,12 +52,13 @@ __device__ __forceinline__ int cell_of_fast(const Geo& g, double sx, double sy, 
     return iy * g.ncx + ix;
 }
 
-__global__ void __launch_bounds__(kRebinThreads) rebin_assign(Geo g, Dev d, int init_n) {
+// block `blk` of an instance's rebin_assign
+__device__ __forceinline__ void rebin_assign_body(const Geo& g, const Dev& d, int init_n, int blk) {
     if (*d.status) return;
     const long long sweep = *d.sweep;
     double sx, sy;
     sweep_shift(g, sweep, &sx, &sy);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blk == 0 && threadIdx.x == 0) {
         d.shift[0] = sx;
         d.shift[1] = sy;
     }
@@ -71,11 +72,11 @@ __global__ void __launch_bounds__(kRebinThreads) rebin_assign(Geo g, Dev d, int 
             latch(d.status, CMH_ERR_GEOMETRY);   // an event outside the domain
     };
     if (init_n >= 0) {
-        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        const int i = blk * blockDim.x + threadIdx.x;
         if (i < init_n) assign(i);
         return;
     }
-    const int oc = blockIdx.x * kWarpsPerBlock + (int)(threadIdx.x >> 5);
+    const int oc = blk * kWarpsPerBlock + (int)(threadIdx.x >> 5);
     if (oc >= g.n_cells) return;
     const int s0 = old.start[oc], n = old.count[oc];
     for (int i = threadIdx.x & 31; i < n; i += 32) assign(s0 + i);
@@ -90,7 +91,7 @@ __device__ __forceinline__ bool axis_live(const Geo& g, double s, int i) {
     return b > a;
 }
 
-__global__ void __launch_bounds__(1024) rebin_scan(Geo g, Dev d) {
+__device__ __forceinline__ void rebin_scan_body(const Geo& g, const Dev& d) {
     if (*d.status) return;
     const long long sweep = *d.sweep;
     const Store nw = d.st[sweep & 1];
@@ -188,13 +189,14 @@ __global__ void __launch_bounds__(1024) rebin_scan(Geo g, Dev d) {
     }
 }
 
-__global__ void __launch_bounds__(kRebinThreads) rebin_gather(Geo g, Dev d, int init_n, int wpb) {
+__device__ __forceinline__ void rebin_gather_body(const Geo& g, const Dev& d, int init_n, int wpb, int blk,
+                                                  unsigned char* smem) {
     if (*d.status) return;
     const long long sweep = *d.sweep;
     const Store old = d.st[(sweep + 1) & 1];
     const Store nw = d.st[sweep & 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int c = blockIdx.x * wpb + w;
+    const int c = blk * wpb + w;
     if (c >= g.n_cells) return;
     const int n = nw.count[c];
     if (n == 0) return;
@@ -202,7 +204,6 @@ __global__ void __launch_bounds__(kRebinThreads) rebin_gather(Geo g, Dev d, int 
         if (lane == 0) latch(d.status, CMH_ERR_CAPACITY);
         return;
     }
-    extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* bid = (unsigned long long*)smem + (size_t)w * g.ev_cap;
     int* bpos = (int*)((unsigned long long*)smem + (size_t)wpb * g.ev_cap) + (size_t)w * g.ev_cap;
     const unsigned lt = (1u << lane) - 1u;
@@ -255,6 +256,49 @@ __global__ void __launch_bounds__(kRebinThreads) rebin_gather(Geo g, Dev d, int 
     }
 }
 
+__global__ void __launch_bounds__(kRebinThreads) rebin_assign(const __grid_constant__ Geo g,
+                                                              const __grid_constant__ Dev d, int init_n) {
+    rebin_assign_body(g, d, init_n, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(1024) rebin_scan(const __grid_constant__ Geo g, const __grid_constant__ Dev d) {
+    rebin_scan_body(g, d);
+}
+
+__global__ void __launch_bounds__(kRebinThreads) rebin_gather(const __grid_constant__ Geo g,
+                                                              const __grid_constant__ Dev d, int init_n, int wpb) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    rebin_gather_body(g, d, init_n, wpb, blockIdx.x, smem);
+}
+
+// ---- a batch of independent instances: the same bodies, one instance per
+// block range (blk_off[i] .. blk_off[i+1]) or per block ----------------------
+__device__ __forceinline__ int instance_of_block(const int* blk_off, int n_inst, int b) {
+    int lo = 0, hi = n_inst - 1;   // largest i with blk_off[i] <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (blk_off[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kRebinThreads) rebin_assign_batch(const Geo* G, const Dev* D, const int* blk_off,
+                                                                    int n_inst) {
+    const int i = instance_of_block(blk_off, n_inst, blockIdx.x);
+    rebin_assign_body(G[i], D[i], -1, blockIdx.x - blk_off[i]);
+}
+
+__global__ void __launch_bounds__(1024) rebin_scan_batch(const Geo* G, const Dev* D) {
+    rebin_scan_body(G[blockIdx.x], D[blockIdx.x]);
+}
+
+__global__ void __launch_bounds__(kRebinThreads) rebin_gather_batch(const Geo* G, const Dev* D, const int* blk_off,
+                                                                    int n_inst) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int i = instance_of_block(blk_off, n_inst, blockIdx.x);
+    rebin_gather_body(G[i], D[i], -1, kWarpsPerBlock, blockIdx.x - blk_off[i], smem);
+}
+
 }  // namespace
 
 namespace {
@@ -269,7 +313,27 @@ size_t gather_smem(const Geo& g) {
 }  // namespace
 
 cudaError_t prepare_rebin(const Geo& g) {
-    return cudaFuncSetAttribute(rebin_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gather_smem(g));
+    return raise_smem_limit((const void*)rebin_gather, gather_smem(g));
+}
+
+// blocks of rebin_assign / rebin_gather for one instance in a batch
+int rebin_blocks(const Geo& g) { return (g.n_cells + kWarpsPerBlock - 1) / kWarpsPerBlock; }
+
+size_t rebin_batch_smem(int max_ev_cap) {
+    return (size_t)kWarpsPerBlock * max_ev_cap * (sizeof(unsigned long long) + sizeof(int));
+}
+
+cudaError_t prepare_rebin_batch(int max_ev_cap) {
+    return raise_smem_limit((const void*)rebin_gather_batch, rebin_batch_smem(max_ev_cap));
+}
+
+cudaError_t launch_rebin_batch(const Geo* G, const Dev* D, const int* blk_off, int n_inst, int n_blocks,
+                               int max_ev_cap, cudaStream_t s) {
+    const size_t smem = rebin_batch_smem(max_ev_cap);
+    rebin_assign_batch<<<n_blocks, kRebinThreads, 0, s>>>(G, D, blk_off, n_inst);
+    rebin_scan_batch<<<n_inst, 1024, 0, s>>>(G, D);
+    rebin_gather_batch<<<n_blocks, kRebinThreads, smem, s>>>(G, D, blk_off, n_inst);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rebin(const Geo& g, const Dev& d, int init_n, cudaStream_t s, int* launches) {

@@ -1134,9 +1134,139 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_kernel(const
     }
 }
 
+// ---- a batch of independent instances ------------------------------------
+// The queue holds every instance's regions in colour order across instances:
+// item_tab[c * n_inst + i] is the first item of (colour c, instance i) and
+// item_tab[n_col * n_inst] the number of items.  Dependencies stay inside an
+// instance (lower colours come earlier in the queue), so the argument of the
+// single-instance kernel carries over.
+__global__ void __launch_bounds__(1024) batch_plan(const Geo* G, const Dev* D, int n_inst, int n_col, int* item_tab,
+                                                   int* queue) {
+    __shared__ int s_warp[32];
+    __shared__ int s_carry;
+    const int n = n_col * n_inst, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int e = base + threadIdx.x;
+        int v = 0;
+        if (e < n) {
+            const int c = e / n_inst, i = e % n_inst;
+            if (c < G[i].n_colours && *(volatile int*)D[i].status == 0) v = D[i].colour_count[c];
+        }
+        int x = v;   // block inclusive scan
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int w = lane < nwarp ? s_warp[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, w, o);
+                if (lane >= o) w += y;
+            }
+            if (lane < nwarp) s_warp[lane] = w;
+        }
+        __syncthreads();
+        const int excl = s_carry + (wid ? s_warp[wid - 1] : 0) + x - v;
+        if (e < n) item_tab[e] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        item_tab[n] = s_carry;
+        *queue = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_batch(const Geo* G, const Dev* D, int n_inst,
+                                                                          int n_col, const int* item_tab,
+                                                                          int* queue) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Sm S;
+    __shared__ int s_inst, s_cell, s_col, s_run;
+    __shared__ long long s_sweep;
+    init_staging<false>(S);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int n = n_col * n_inst, total = item_tab[n];
+            const int it = atomicAdd(queue, 1);
+            int inst = -1, col = 0, cell = -1;
+            if (it < total) {
+                int lo = 0, hi = n - 1;   // largest entry whose first item is <= it
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (item_tab[mid] <= it) lo = mid; else hi = mid - 1;
+                }
+                col = lo / n_inst;
+                inst = lo % n_inst;
+                cell = D[inst].colour_cells[col * G[inst].max_rpc + (it - item_tab[lo])];
+                s_sweep = *D[inst].sweep;
+            }
+            s_inst = inst;
+            s_cell = cell;
+            s_col = col;
+        }
+        __syncthreads();
+        const int inst = s_inst, cell = s_cell;
+        if (inst < 0) break;
+        const Geo& g = G[inst];
+        const Dev& d = D[inst];
+        const long long sweep = s_sweep, stamp = sweep + 1;
+        if (threadIdx.x == 0) {
+            const int colour = s_col;
+            const int P1 = g.period - 1, ix = cell % g.ncx, iy = cell / g.ncx;
+            for (int jy = iy - P1; jy <= iy + P1; ++jy)
+                for (int jx = ix - P1; jx <= ix + P1; ++jx) {
+                    if (jx < 0 || jy < 0 || jx >= g.ncx || jy >= g.ncy) continue;
+                    const int nb = jy * g.ncx + jx;
+                    const int c = d.cell_col[nb];
+                    if (nb == cell || c < 0 || c >= colour) continue;
+                    unsigned k = 0;
+                    while (ld_acquire(d.done + nb) < stamp && !*(volatile int*)d.status) {
+                        if (++k >= kDepWaitLimit) {
+                            latch(d.status, CMH_ERR_TIMEOUT);
+                            break;
+                        }
+                        __nanosleep(128);
+                    }
+                }
+            s_run = *(volatile int*)d.status == 0;
+        }
+        __syncthreads();
+        if (s_run) region_phase<false>(g, d, cell, sweep, S, smem);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(d.done + cell, stamp);
+        }
+    }
+}
+
 }  // namespace
 
 size_t phase32_smem_bytes(const Geo& g) { return layout32(g, nullptr, nullptr); }
+
+cudaError_t prepare_sweep32_batch(size_t smem_bytes, int* grid) {
+    cudaError_t e = raise_smem_limit((const void*)sweep32_batch, smem_bytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0, n_sm = 1, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep32_batch, kThreads32, smem_bytes)))
+        return e;
+    *grid = std::max(1, n_sm * std::max(1, std::min(per_sm, kMinBlocks32)));
+    return cudaSuccess;
+}
+
+cudaError_t launch_sweep32_batch(const Geo* G, const Dev* D, int n_inst, int n_col, int* item_tab, int* queue,
+                                 size_t smem_bytes, int grid, cudaStream_t s) {
+    batch_plan<<<1, 1024, 0, s>>>(G, D, n_inst, n_col, item_tab, queue);
+    sweep32_batch<<<grid, kThreads32, smem_bytes, s>>>(G, D, n_inst, n_col, item_tab, queue);
+    return cudaGetLastError();
+}
 
 // staging capacity (samples per buffer): 0 for `requested` 0 (no staging);
 // `requested` rounded down to a multiple of 4 when positive; for -1, one
@@ -1175,10 +1305,10 @@ cudaError_t choose_stage_cap(Geo& g, int requested) {
 cudaError_t prepare_phase32(const Geo& g) {
     const int bytes = (int)phase32_smem_bytes(g);
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(phase32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) ||
-        (e = cudaFuncSetAttribute(phase32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) ||
-        (e = cudaFuncSetAttribute(sweep32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) ||
-        (e = cudaFuncSetAttribute(sweep32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
+    if ((e = raise_smem_limit((const void*)phase32_kernel<false>, bytes)) ||
+        (e = raise_smem_limit((const void*)phase32_kernel<true>, bytes)) ||
+        (e = raise_smem_limit((const void*)sweep32_kernel<false>, bytes)) ||
+        (e = raise_smem_limit((const void*)sweep32_kernel<true>, bytes)))
         return e;
     return cudaSuccess;
 }

@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
     }
 }
 
-__global__ void sweep_end(Geo g, Dev d) {
+__device__ __forceinline__ void sweep_end_body(const Geo& g, const Dev& d) {
     if (*d.status) return;
     __shared__ double s_part[32];
     double acc = 0.0;
@@ -640,6 +640,11 @@ __global__ void sweep_end(Geo g, Dev d) {
         *d.sweep += 1;
     }
 }
+
+__global__ void sweep_end(const __grid_constant__ Geo g, const __grid_constant__ Dev d) { sweep_end_body(g, d); }
+
+// one block per instance of a batch
+__global__ void sweep_end_batch(const Geo* G, const Dev* D) { sweep_end_body(G[blockIdx.x], D[blockIdx.x]); }
 
 // ---------------------------------------------------------------------------
 // predicted-variance synthesis: V_j[k] = noise + sum of the variances of the
@@ -847,6 +852,11 @@ cudaError_t launch_phase(const Geo& g, const Dev& d, int colour, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_sweep_end_batch(const Geo* G, const Dev* D, int n_inst, cudaStream_t s) {
+    sweep_end_batch<<<n_inst, 1024, 0, s>>>(G, D);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sweep_end(const Geo& g, const Dev& d, cudaStream_t s) {
     sweep_end<<<1, 1024, 0, s>>>(g, d);
     return cudaGetLastError();
@@ -868,7 +878,7 @@ cudaError_t launch_flatten(const Geo& g, const Dev& d, int buf, const FlatList& 
 
 cudaError_t prepare_kernels(const Geo& g) {
     const size_t smem = phase_smem_bytes(g);
-    return cudaFuncSetAttribute(phase_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return raise_smem_limit((const void*)phase_kernel, smem);
 }
 
 cudaError_t launch_loglik(const Geo& g, const Dev& d, double* partial, int n_part, cudaStream_t s) {

@@ -87,3 +87,9 @@ def test_null_handles(cm):
     assert cm.lib.cmh_read_state(None, None, None, 0, None, None, None) == -1
     assert cm.lib.cmh_philox4x64(None, None, None, -1) == -1
     cm.lib.cmh_destroy(None)
+    h = C.c_void_p()
+    assert cm.lib.cmh_batch_create(None, 0, None, C.byref(h)) == -1 and not h.value
+    arr = (C.c_void_p * 1)(None)
+    assert cm.lib.cmh_batch_create(arr, 1, None, C.byref(h)) == -1 and not h.value
+    assert cm.lib.cmh_batch_run_sweeps(None, 1) == -1
+    cm.lib.cmh_batch_destroy(None)

@@ -83,6 +83,8 @@ typedef struct {
                               region waits only for its neighbouring regions of lower colours
                               (same results as colour by colour, shorter tails); 1 = one launch
                               per colour phase.  The float64 form always runs colour by colour */
+    int32_t ctas_per_sm;   /* schedule 0: resident CTAs per SM of the persistent launch
+                              (1..3; 0: as many as fit, at most 3) */
     int64_t max_events;    /* capacity of the whole event store; 0: 4 (n0 + Lambda) + 4096 */
 } cmh_params;
 
@@ -229,6 +231,22 @@ const char* cmh_strerror(int code);
  *   the first one is returned.  Each model's state, statistics and sweep
  *   count advance as if cmh_run_sweeps(model, n) had run.
  */
+/* ---- autotuning ------------------------------------------------------------
+ * cmh_autotune times, from a checkpoint of the model, trial_sweeps sweeps of
+ * each launch configuration the float32 form offers (colour by colour or
+ * persistent; staging off or automatic; 1-3 CTAs per SM for the persistent
+ * launch), keeps the fastest in the model's parameters and restores the
+ * checkpoint, so the chain continues as if no trial had run.  Needs a
+ * partitioned CMH_F32 model (CMH_ERR_ARG / CMH_ERR_STATE otherwise). */
+typedef struct {
+    int32_t schedule, stage_samples, ctas_per_sm;   /* the choice */
+    double ms_per_sweep;                            /* its trial time */
+    int32_t n_tried;
+    int32_t tried_schedule[16], tried_stage[16], tried_ctas[16];
+    double tried_ms[16];                            /* -1: the configuration does not fit */
+} cmh_tuning;
+int cmh_autotune(cmh_model* m, int32_t trial_sweeps, cmh_tuning* out);
+
 typedef struct cmh_batch cmh_batch;
 int cmh_batch_create(cmh_model* const* models, int32_t n_models, void* cuda_stream, cmh_batch** out);
 int cmh_batch_run_sweeps(cmh_batch* b, int64_t n);

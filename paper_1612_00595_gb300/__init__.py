@@ -41,7 +41,21 @@ class Params(C.Structure):
                  "R_max", "p_birth", "p_death", "sig_xy", "sig_t", "sig_m")] + [
         ("k_per_phase", C.c_int32), ("commit", C.c_int32), ("seed", C.c_uint64), ("dtype", C.c_int32),
         ("ev_capacity", C.c_int32), ("frozen_capacity", C.c_int32), ("block_threads", C.c_int32),
-        ("stage_samples", C.c_int32), ("schedule", C.c_int32), ("max_events", C.c_int64)]
+        ("stage_samples", C.c_int32), ("schedule", C.c_int32), ("ctas_per_sm", C.c_int32),
+        ("max_events", C.c_int64)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("schedule", C.c_int32), ("stage_samples", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("ms_per_sweep", C.c_double), ("n_tried", C.c_int32), ("tried_schedule", C.c_int32 * 16),
+                ("tried_stage", C.c_int32 * 16), ("tried_ctas", C.c_int32 * 16), ("tried_ms", C.c_double * 16)]
+
+    def as_dict(self):
+        n = self.n_tried
+        return {"schedule": self.schedule, "stage_samples": self.stage_samples, "ctas_per_sm": self.ctas_per_sm,
+                "ms_per_sweep": self.ms_per_sweep,
+                "tried": [{"schedule": self.tried_schedule[i], "stage_samples": self.tried_stage[i],
+                           "ctas_per_sm": self.tried_ctas[i], "ms_per_sweep": self.tried_ms[i]} for i in range(n)]}
 
 
 class Grid(C.Structure):
@@ -69,7 +83,8 @@ TRACE_DTYPE = np.dtype([("sweep", "<i4"), ("cell", "<i4"), ("step", "<i4"), ("ty
 EXPORTS = ["cmh_create_model", "cmh_partition_and_color", "cmh_run_sweeps", "cmh_read_state", "cmh_sync",
            "cmh_log_density", "cmh_set_trace", "cmh_read_trace", "cmh_set_timing", "cmh_read_shift",
            "cmh_checkpoint", "cmh_restore", "cmh_destroy", "cmh_strerror", "cmh_philox4x64",
-           "cmh_gaussian_loglik_noalloc", "cmh_batch_create", "cmh_batch_run_sweeps", "cmh_batch_destroy"]
+           "cmh_gaussian_loglik_noalloc", "cmh_batch_create", "cmh_batch_run_sweeps", "cmh_batch_destroy",
+           "cmh_autotune"]
 
 
 def _load():
@@ -101,6 +116,7 @@ def _load():
         "cmh_batch_create": (C.c_int, [C.POINTER(P), i32, P, C.POINTER(P)]),
         "cmh_batch_run_sweeps": (C.c_int, [P, i64]),
         "cmh_batch_destroy": (None, [P]),
+        "cmh_autotune": (C.c_int, [P, i32, C.POINTER(Tuning)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -127,7 +143,7 @@ def _ptr(a):
 
 def make_params(model_params, *, k_per_phase=32, seed=1, dtype=F64, p_birth=0.25, p_death=0.25,
                 sig_xy=5.0, sig_t=2.0, sig_m=0.1, commit=True, ev_capacity=0, frozen_capacity=0,
-                block_threads=0, stage_samples=0, schedule=0, max_events=0) -> Params:
+                block_threads=0, stage_samples=0, schedule=0, ctas_per_sm=0, max_events=0) -> Params:
     """cmh_params from an object with the model fields (e.g. worldgen.ModelParams)."""
     p = Params()
     for n in ("W", "T", "Lambda", "v", "alpha", "beta_att", "tau", "t_s", "noise_var", "f_hz", "R_max"):
@@ -143,6 +159,7 @@ def make_params(model_params, *, k_per_phase=32, seed=1, dtype=F64, p_birth=0.25
     p.block_threads = block_threads
     p.stage_samples = stage_samples
     p.schedule = schedule
+    p.ctas_per_sm = ctas_per_sm
     p.max_events = max_events
     return p
 
@@ -176,6 +193,13 @@ class Model:
 
     def run_sweeps(self, n: int):
         _check(lib.cmh_run_sweeps(self._h, int(n)), "cmh_run_sweeps")
+
+    def autotune(self, trial_sweeps: int = 8) -> dict:
+        """Time each launch configuration from a checkpoint, keep the fastest,
+        restore the checkpoint (the chain is unchanged)."""
+        t = Tuning()
+        _check(lib.cmh_autotune(self._h, int(trial_sweeps), C.byref(t)), "cmh_autotune")
+        return t.as_dict()
 
     def read_state(self, cap: Optional[int] = None):
         """(events [n,4] float64, ids [n] uint64, log_density, stats dict)."""

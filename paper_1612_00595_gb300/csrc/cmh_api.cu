@@ -207,7 +207,8 @@ int validate_params(const cmh_params* p) {
     if (p->k_per_phase < 1 || p->k_per_phase > kMaxK) return CMH_ERR_ARG;
     if (p->dtype != CMH_F32 && p->dtype != CMH_F64) return CMH_ERR_ARG;
     if (p->ev_capacity < 0 || p->frozen_capacity < 0 || p->max_events < 0) return CMH_ERR_ARG;
-    if (p->stage_samples < -1 || (p->schedule != 0 && p->schedule != 1)) return CMH_ERR_ARG;
+    if (p->stage_samples < -1 || (p->schedule != 0 && p->schedule != 1) || p->ctas_per_sm < 0 || p->ctas_per_sm > 3)
+        return CMH_ERR_ARG;
     if (p->block_threads != 0 && (p->block_threads < 64 || p->block_threads > 512 || p->block_threads % 32))
         return CMH_ERR_ARG;
     const double nw = std::llround(p->t_s * p->f_hz);
@@ -557,7 +558,7 @@ int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mo
     CK(prepare_phase32(g));
     CK(prepare_rebin(g));
     m->sweep_grid = 0;
-    if (g.f32 && m->p.schedule == 0) CK(sweep32_grid(g, &m->sweep_grid));
+    if (g.f32 && m->p.schedule == 0) CK(sweep32_grid(g, m->p.ctas_per_sm, &m->sweep_grid));
 
     Dev& d = m->d;
     cudaError_t e;
@@ -896,6 +897,70 @@ int cmh_philox4x64(const uint64_t* ctr, const uint64_t* key, uint64_t* out, int6
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// autotuning of the launch configuration
+// ---------------------------------------------------------------------------
+extern "C" int cmh_autotune(cmh_model* m, int32_t trial_sweeps, cmh_tuning* out) {
+    if (!m || !out || trial_sweeps < 1) return CMH_ERR_ARG;
+    if (!m->partitioned || m->latched) return CMH_ERR_STATE;
+    if (!m->g.f32) return CMH_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    size_t len = 0;
+    int rc = cmh_checkpoint(m, nullptr, &len);
+    if (rc) return rc;
+    std::vector<unsigned char> ck(len);
+    if ((rc = cmh_checkpoint(m, ck.data(), &len))) return rc;
+    const cmh_params keep = m->p;
+    const long long launches0 = m->launches;
+    struct Cand { int schedule, stage, ctas; };
+    const Cand cands[] = {{1, 0, 0}, {1, -1, 0}, {0, 0, 3}, {0, 0, 2}, {0, 0, 1}, {0, -1, 0}};
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    double best = -1.0;
+    int best_i = -1;
+    for (const Cand& c : cands) {
+        const int i = out->n_tried++;
+        out->tried_schedule[i] = c.schedule;
+        out->tried_stage[i] = c.stage;
+        out->tried_ctas[i] = c.ctas;
+        out->tried_ms[i] = -1.0;
+        m->p = keep;
+        m->p.schedule = c.schedule;
+        m->p.stage_samples = c.stage;
+        m->p.ctas_per_sm = c.ctas;
+        if (cmh_restore(m, ck.data(), len) != CMH_OK) continue;   // does not fit: skip it
+        if (cmh_run_sweeps(m, 1) != CMH_OK) continue;             // warm-up (and graph capture)
+        cudaEventRecord(a, m->stream);
+        if (cmh_run_sweeps(m, trial_sweeps) != CMH_OK) continue;
+        cudaEventRecord(b, m->stream);
+        if (cudaEventSynchronize(b) != cudaSuccess || check_status(m) != CMH_OK) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        out->tried_ms[i] = ms / trial_sweeps;
+        if (best < 0.0 || out->tried_ms[i] < best) {
+            best = out->tried_ms[i];
+            best_i = i;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    m->p = keep;
+    if (best_i >= 0) {
+        m->p.schedule = out->tried_schedule[best_i];
+        m->p.stage_samples = out->tried_stage[best_i];
+        m->p.ctas_per_sm = out->tried_ctas[best_i];
+    }
+    m->latched = 0;
+    if ((rc = cmh_restore(m, ck.data(), len))) return rc;
+    m->launches = launches0;   // the trials are not part of the chain
+    out->schedule = m->p.schedule;
+    out->stage_samples = m->p.stage_samples;
+    out->ctas_per_sm = m->p.ctas_per_sm;
+    out->ms_per_sweep = best;
+    return best_i >= 0 ? CMH_OK : CMH_ERR_STATE;
+}
 
 // ---------------------------------------------------------------------------
 // batches of independent models

@@ -277,7 +277,7 @@ cudaError_t launch_phase32(const Geo& g, const Dev& d, int colour, cudaStream_t 
 size_t phase32_smem_bytes(const Geo& g);
 cudaError_t prepare_phase32(const Geo& g);
 cudaError_t choose_stage_cap(Geo& g, int requested);
-cudaError_t sweep32_grid(const Geo& g, int* grid);
+cudaError_t sweep32_grid(const Geo& g, int ctas_per_sm, int* grid);
 cudaError_t launch_sweep32(const Geo& g, const Dev& d, int grid, cudaStream_t s);
 cudaError_t launch_sweep_end(const Geo& g, const Dev& d, cudaStream_t s);
 size_t phase_smem_bytes(const Geo& g);

@@ -1315,7 +1315,7 @@ cudaError_t prepare_phase32(const Geo& g) {
 
 // CTAs of the persistent sweep kernel: as many as can be resident at once
 // (at most kMinBlocks32 per SM, never more than the regions of a sweep)
-cudaError_t sweep32_grid(const Geo& g, int* grid) {
+cudaError_t sweep32_grid(const Geo& g, int ctas_per_sm, int* grid) {
     int dev = 0, n_sm = 1, per_sm = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)))
@@ -1325,6 +1325,7 @@ cudaError_t sweep32_grid(const Geo& g, int* grid) {
              kThreads32, phase32_smem_bytes(g))))
         return e;
     per_sm = std::max(1, std::min(per_sm, kMinBlocks32));
+    if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
     *grid = std::max(1, std::min(n_sm * per_sm, g.n_colours * g.max_rpc));
     return cudaSuccess;
 }

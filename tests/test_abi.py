@@ -49,6 +49,8 @@ def _params(cm, **kw):
     dict(k_per_phase=5000),
     dict(block_threads=100),
     dict(stage_samples=-2),
+    dict(schedule=2),
+    dict(ctas_per_sm=4),
     dict(dtype=7),
 ])
 def test_create_model_rejects_bad_params_on_host(cm, bad):

@@ -248,3 +248,28 @@ def test_fp32_persistent_sweep_matches_colour_by_colour(cm):
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
     assert runs[0][2] == runs[1][2]
     assert np.array_equal(runs[0][3], runs[1][3])
+
+
+def test_autotune_restores_the_chain(cm):
+    """The autotuner's trial sweeps run from a checkpoint that is restored:
+    the chain afterwards is the one without tuning."""
+    w = small_world(seed=20, W=800.0, T=1800.0, Lambda=200.0, n_side=8, dtype=np.float32)
+    out = []
+    for tune in (True, False):
+        m = cm.create_model(w.events, w.stations, w.signals,
+                            cm.make_params(w.params, k_per_phase=32, seed=3, dtype=cm.F32))
+        m.partition_and_color(w.params.L, 1)
+        m.run_sweeps(3)
+        if tune:
+            t = m.autotune(2)
+            assert t["ms_per_sweep"] > 0 and len(t["tried"]) == 6
+            assert any(r["ms_per_sweep"] == t["ms_per_sweep"] for r in t["tried"])
+        m.run_sweeps(5)
+        ev, ids, lp, st = m.read_state()
+        out.append((ev, ids, lp, st["proposed"], st["sweeps"]))
+        m.destroy()
+    (ea, ia, la, pa, sa), (eb, ib, lb, pb, sb) = out
+    # restoring re-synthesises V from the events, which may change its last
+    # bits (summation order): the log-density agrees to rounding
+    assert np.array_equal(ia, ib) and np.array_equal(ea, eb) and pa == pb and sa == sb == 8
+    assert la == pytest.approx(lb, rel=1e-11)

@@ -311,18 +311,84 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """256 independent instances of uneven size swept together: one
+    persistent launch per sweep over every instance's regions."""
+    import torch
+    import paper_1612_00595_gb300 as cm
+    torch.cuda.set_device(0)
+    worlds = worldgen.config_batched(256, seed=2000)
+    models, kept, skipped = [], [], []
+    for i, w in enumerate(worlds):
+        p = w.params
+        # capacities from the instance's density: events per region and
+        # arrivals per station, mean + 6 sd + slack
+        per_region = p.Lambda * p.L * p.L / (p.W * p.W)
+        per_station = p.Lambda * math.pi * p.R_max ** 2 / (p.W * p.W)
+        ev_cap = int(min(512, max(128, per_region + 6 * math.sqrt(per_region) + K_PER_PHASE + 16)))
+        frz_cap = int(max(64, per_station + 6 * math.sqrt(per_station) + 16))
+        m = cm.create_model(w.events, w.stations, w.signals,
+                            cm.make_params(p, k_per_phase=K_PER_PHASE, seed=CHAIN_SEED + i, dtype=cm.F32,
+                                           ev_capacity=ev_cap, frozen_capacity=frz_cap))
+        try:
+            m.partition_and_color(p.L, shift_mode=1)
+        except cm.ChromhError:   # a region's structures exceed shared memory
+            skipped.append(i)
+            m.destroy()
+            continue
+        models.append(m)
+        kept.append(w)
+    stream = torch.cuda.Stream()
+    b = cm.create_batch(models, stream=stream)
+    b.run_sweeps(args.warmup)
+    b.sync()
+    p0 = sum(sum(m.read_state(cap=0)[3]["proposed"]) for m in models)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        e0.record(stream)
+        b.run_sweeps(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+    b.sync()
+    ms = e0.elapsed_time(e1)
+    p1 = sum(sum(m.read_state(cap=0)[3]["proposed"]) for m in models)
+    n_regions = sum((int(w.params.W // w.params.L) + 2) ** 2 for w in kept)
+    worlds_all, worlds = worlds, kept
+    line = {"metric": "MH proposals/sec and sweeps/sec on 1 GB300 (batched instances)", "value": (p1 - p0) / (ms / 1e3),
+            "unit": "proposals/s", "sweeps_per_s": args.steps / (ms / 1e3), "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded worldgen, the model's generative story)",
+            "config": {"workload": "256 independent instances: stations logU[16,256], Lambda logU[10,500], side "
+                                   "logU[200,2000] km, T logU[600,7200] s, f32, k=32; one sweep of every instance "
+                                   "per step",
+                       "instances": len(worlds), "instances_drawn": len(worlds_all),
+                       "skipped": "%d dense instances whose per-region structures exceed shared memory: %s"
+                                  % (len(skipped), skipped),
+                       "groups (models, CTAs)": b.groups(), "cells": n_regions,
+                       "signal_bytes": int(sum(w.signals.nbytes for w in worlds))},
+            "clocks": clocks.summary(), "gpu_launches": (4 + 2 * len(b.groups())) * args.steps}
+    print(json.dumps(line))
+    b.destroy()
+    for m in models:
+        m.destroy()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="scale", choices=["scale", "replay"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "replay", "batched"])
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -214,10 +214,13 @@ const char* cmh_strerror(int code);
 /* ---- batches of independent models (same library, float32 form) -----------
  * A batch sweeps many independent models together: one sweep of every model
  * per step, the re-binning of all models in three launches, and every
- * region of every model in one persistent launch fed by a device work queue
+ * region of every model in persistent launches fed by device work queues
  * (colour order across models; a region waits only for its own model's
- * neighbouring regions of lower colours), captured in one CUDA graph.  The
- * chains are the ones cmh_run_sweeps gives each model alone.
+ * neighbouring regions of lower colours), captured in one CUDA graph.
+ * Models are grouped by how many of their region CTAs fit on an SM (3, 2 or
+ * 1, from the shared memory a region needs); each group has its own queue
+ * and launch, and the groups run concurrently.  The chains are the ones
+ * cmh_run_sweeps gives each model alone.
  *
  * cmh_batch_create: models[0..n_models) must be distinct, partitioned, of
  *   dtype CMH_F32, without staging (stage_samples 0) and with ev_capacity
@@ -225,11 +228,15 @@ const char* cmh_strerror(int code);
  *   failed model).  The batch refers to the models (it does not own them)
  *   and to their current partitions; cuda_stream may be NULL (the batch
  *   creates its own).  Destroy the batch before its models.
- * cmh_batch_run_sweeps: n sweeps of every model; returns after they finish.
+ * cmh_batch_run_sweeps: enqueues n sweeps of every model on the batch's
+ *   stream and returns; later calls on a model's own stream wait for them.
  *   CMH_ERR_STATE if a model failed or was re-partitioned since the batch
- *   was made; a device-side error of a model is latched in that model and
- *   the first one is returned.  Each model's state, statistics and sweep
- *   count advance as if cmh_run_sweeps(model, n) had run.
+ *   was made.  Each model's state, statistics and sweep count advance as if
+ *   cmh_run_sweeps(model, n) had run.
+ * cmh_batch_sync: waits for the batch's sweeps; a device-side error of a
+ *   model is latched in that model and the first one is returned.
+ * cmh_batch_groups: the number of groups and, for the first `cap`, their
+ *   models and persistent-launch CTAs.
  */
 /* ---- autotuning ------------------------------------------------------------
  * cmh_autotune times, from a checkpoint of the model, trial_sweeps sweeps of
@@ -250,6 +257,9 @@ int cmh_autotune(cmh_model* m, int32_t trial_sweeps, cmh_tuning* out);
 typedef struct cmh_batch cmh_batch;
 int cmh_batch_create(cmh_model* const* models, int32_t n_models, void* cuda_stream, cmh_batch** out);
 int cmh_batch_run_sweeps(cmh_batch* b, int64_t n);
+int cmh_batch_sync(cmh_batch* b);
+int cmh_batch_groups(const cmh_batch* b, int32_t* n_groups, int32_t* models_per_group, int32_t* grid_per_group,
+                     int32_t cap);
 void cmh_batch_destroy(cmh_batch* b);
 
 /*

@@ -84,7 +84,7 @@ EXPORTS = ["cmh_create_model", "cmh_partition_and_color", "cmh_run_sweeps", "cmh
            "cmh_log_density", "cmh_set_trace", "cmh_read_trace", "cmh_set_timing", "cmh_read_shift",
            "cmh_checkpoint", "cmh_restore", "cmh_destroy", "cmh_strerror", "cmh_philox4x64",
            "cmh_gaussian_loglik_noalloc", "cmh_batch_create", "cmh_batch_run_sweeps", "cmh_batch_destroy",
-           "cmh_autotune"]
+           "cmh_autotune", "cmh_batch_sync", "cmh_batch_groups"]
 
 
 def _load():
@@ -117,6 +117,8 @@ def _load():
         "cmh_batch_run_sweeps": (C.c_int, [P, i64]),
         "cmh_batch_destroy": (None, [P]),
         "cmh_autotune": (C.c_int, [P, i32, C.POINTER(Tuning)]),
+        "cmh_batch_sync": (C.c_int, [P]),
+        "cmh_batch_groups": (C.c_int, [P, C.POINTER(i32), P, P, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -320,7 +322,19 @@ class Batch:
         self._h = None
 
     def run_sweeps(self, n: int):
+        """Enqueue n sweeps of every model (asynchronous; see sync)."""
         _check(lib.cmh_batch_run_sweeps(self._h, n), "cmh_batch_run_sweeps")
+
+    def sync(self):
+        _check(lib.cmh_batch_sync(self._h), "cmh_batch_sync")
+
+    def groups(self):
+        """[(models, persistent-launch CTAs)] per shared-memory group."""
+        n = C.c_int32()
+        mp = (C.c_int32 * 3)()
+        gp = (C.c_int32 * 3)()
+        _check(lib.cmh_batch_groups(self._h, C.byref(n), mp, gp, 3), "cmh_batch_groups")
+        return [(mp[i], gp[i]) for i in range(n.value)]
 
 
 def create_batch(models, stream=None) -> Batch:

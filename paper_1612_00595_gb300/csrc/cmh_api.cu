@@ -319,6 +319,7 @@ int cmh_create_model(const cmh_event* init_events, int64_t n_events, const cmh_s
                      int32_t n_stations, const void* signals, int64_t n_samples, int64_t row_pitch,
                      cmh_dtype sig_dtype, int32_t signals_on_device, const cmh_params* p, void* cuda_stream,
                      cmh_model** out) {
+    (void)cudaGetLastError();   // an earlier call's failed launch must not be reported here
     if (!out) return CMH_ERR_ARG;
     *out = nullptr;
     int rc = validate_params(p);
@@ -504,6 +505,7 @@ int cmh_create_model(const cmh_event* init_events, int64_t n_events, const cmh_s
 
 int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mode, double sx, double sy,
                             int32_t* n_colors_out) {
+    (void)cudaGetLastError();   // an earlier call's failed launch must not be reported here
     if (!m || !grid) return CMH_ERR_ARG;
     if (m->latched) return CMH_ERR_STATE;
     const double L = grid->L;
@@ -554,8 +556,10 @@ int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mo
     g.stage_cap = 0;
     if (g.f32) CK(choose_stage_cap(g, m->p.stage_samples));
     if ((g.f32 ? phase32_smem_bytes(g) : phase_smem_bytes(g)) > 227 * 1024) return CMH_ERR_CAPACITY;
-    CK(prepare_kernels(g));
-    CK(prepare_phase32(g));
+    if (g.f32)
+        CK(prepare_phase32(g));
+    else
+        CK(prepare_kernels(g));
     CK(prepare_rebin(g));
     m->sweep_grid = 0;
     if (g.f32 && m->p.schedule == 0) CK(sweep32_grid(g, m->p.ctas_per_sm, &m->sweep_grid));
@@ -820,6 +824,7 @@ int cmh_checkpoint(cmh_model* m, void* buf, size_t* len) {
 }
 
 int cmh_restore(cmh_model* m, const void* buf, size_t len) {
+    (void)cudaGetLastError();   // an earlier call's failed launch must not be reported here
     if (!m || !buf || len < sizeof(CkptHeader)) return CMH_ERR_ARG;
     CkptHeader h;
     std::memcpy(&h, buf, sizeof(h));
@@ -965,6 +970,22 @@ extern "C" int cmh_autotune(cmh_model* m, int32_t trial_sweeps, cmh_tuning* out)
 // ---------------------------------------------------------------------------
 // batches of independent models
 // ---------------------------------------------------------------------------
+// Models are grouped by how many of their region CTAs fit on an SM (the
+// shared memory one region needs): each group gets its own persistent launch
+// with its own queue and shared-memory size, and the groups run concurrently
+// (forked branches of the sweep's graph) between the common re-binning and
+// sweep-end launches.
+struct BatchGroup {
+    Geo* G = nullptr;
+    Dev* D = nullptr;
+    int* item_tab = nullptr;
+    int* queue = nullptr;
+    int n = 0, n_col = 0, grid = 0;
+    size_t smem = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
 struct cmh_batch {
     std::vector<cmh_model*> models;
     std::vector<long long> gens;
@@ -973,10 +994,9 @@ struct cmh_batch {
     Geo* G = nullptr;
     Dev* D = nullptr;
     int* blk_off = nullptr;
-    int* item_tab = nullptr;
-    int* queue = nullptr;
-    int n = 0, n_blocks = 0, max_ev_cap = 0, n_col = 0, grid = 0;
-    size_t smem = 0;
+    int n = 0, n_blocks = 0, max_ev_cap = 0;
+    std::vector<BatchGroup> groups;
+    cudaEvent_t fork = nullptr, finished = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 
@@ -984,15 +1004,23 @@ struct cmh_batch {
         if (stream) cudaStreamSynchronize(stream);
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
-        for (void* q : {(void*)G, (void*)D, (void*)blk_off, (void*)item_tab, (void*)queue})
-            if (q) cudaFree(q);
+        for (BatchGroup& q : groups) {
+            for (void* x : {(void*)q.G, (void*)q.D, (void*)q.item_tab, (void*)q.queue})
+                if (x) cudaFree(x);
+            if (q.stream) cudaStreamDestroy(q.stream);
+            if (q.done) cudaEventDestroy(q.done);
+        }
+        for (void* x : {(void*)G, (void*)D, (void*)blk_off})
+            if (x) cudaFree(x);
+        if (fork) cudaEventDestroy(fork);
+        if (finished) cudaEventDestroy(finished);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
 
-constexpr int kBatchLaunchesPerSweep = 6;   // assign, scan, gather, plan, phase, sweep end
 
 extern "C" int cmh_batch_create(cmh_model* const* models, int32_t n_models, void* cuda_stream, cmh_batch** out) {
+    (void)cudaGetLastError();   // an earlier call's failed launch must not be reported here
     if (!out || !models || n_models < 1) return CMH_ERR_ARG;
     *out = nullptr;
     for (int i = 0; i < n_models; ++i) {
@@ -1016,9 +1044,14 @@ extern "C" int cmh_batch_create(cmh_model* const* models, int32_t n_models, void
         if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(CMH_ERR_CUDA);
         b->own_stream = true;
     }
+    int dev = 0, per_sm = 0, reserved = 0;
+    if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev))
+        return fail(CMH_ERR_CUDA);
     std::vector<Geo> hg(n_models);
     std::vector<Dev> hd(n_models);
     std::vector<int> off(n_models + 1, 0);
+    std::vector<int> fit(n_models);
     for (int i = 0; i < n_models; ++i) {
         cmh_model* m = models[i];
         if (cudaStreamSynchronize(m->stream) != cudaSuccess) return fail(CMH_ERR_CUDA);
@@ -1027,25 +1060,58 @@ extern "C" int cmh_batch_create(cmh_model* const* models, int32_t n_models, void
         b->gens.push_back(m->part_gen);
         off[i + 1] = off[i] + rebin_blocks(m->g);
         b->max_ev_cap = std::max(b->max_ev_cap, m->g.ev_cap);
-        b->n_col = std::max(b->n_col, m->g.n_colours);
-        b->smem = std::max(b->smem, phase32_smem_bytes(m->g));
+        const size_t sm = phase32_smem_bytes(m->g);
+        if (sm > 227 * 1024) return fail(CMH_ERR_CAPACITY);
+        // region CTAs of this model that fit on one SM (static shared memory ~2 KB)
+        fit[i] = std::max(1, std::min(3, (int)(per_sm / (sm + 2048 + (size_t)reserved))));
     }
     b->n_blocks = off[n_models];
-    if (b->smem > 227 * 1024) return fail(CMH_ERR_CAPACITY);
     if (cudaMalloc(&b->G, sizeof(Geo) * n_models) || cudaMalloc(&b->D, sizeof(Dev) * n_models) ||
-        cudaMalloc(&b->blk_off, sizeof(int) * (n_models + 1)) ||
-        cudaMalloc(&b->item_tab, sizeof(int) * ((size_t)b->n_col * n_models + 1)) ||
-        cudaMalloc(&b->queue, sizeof(int)))
+        cudaMalloc(&b->blk_off, sizeof(int) * (n_models + 1)))
         return fail(CMH_ERR_OOM);
     if (cudaMemcpy(b->G, hg.data(), sizeof(Geo) * n_models, cudaMemcpyHostToDevice) ||
         cudaMemcpy(b->D, hd.data(), sizeof(Dev) * n_models, cudaMemcpyHostToDevice) ||
         cudaMemcpy(b->blk_off, off.data(), sizeof(int) * (n_models + 1), cudaMemcpyHostToDevice))
         return fail(CMH_ERR_CUDA);
-    if (prepare_rebin_batch(b->max_ev_cap) || prepare_sweep32_batch(b->smem, &b->grid)) return fail(CMH_ERR_CUDA);
+    if (prepare_rebin_batch(b->max_ev_cap)) return fail(CMH_ERR_CUDA);
+    for (int f = 3; f >= 1; --f) {   // groups: 3, 2, then 1 resident region per SM
+        std::vector<Geo> gg;
+        std::vector<Dev> gd;
+        BatchGroup q;
+        for (int i = 0; i < n_models; ++i)
+            if (fit[i] == f) {
+                gg.push_back(hg[i]);
+                gd.push_back(hd[i]);
+                q.n_col = std::max(q.n_col, hg[i].n_colours);
+                q.smem = std::max(q.smem, phase32_smem_bytes(hg[i]));
+            }
+        if (gg.empty()) continue;
+        q.n = (int)gg.size();
+        b->groups.push_back(q);
+        BatchGroup& r = b->groups.back();
+        if (cudaMalloc(&r.G, sizeof(Geo) * r.n) || cudaMalloc(&r.D, sizeof(Dev) * r.n) ||
+            cudaMalloc(&r.item_tab, sizeof(int) * ((size_t)r.n_col * r.n + 1)) || cudaMalloc(&r.queue, sizeof(int)))
+            return fail(CMH_ERR_OOM);
+        if (cudaMemcpy(r.G, gg.data(), sizeof(Geo) * r.n, cudaMemcpyHostToDevice) ||
+            cudaMemcpy(r.D, gd.data(), sizeof(Dev) * r.n, cudaMemcpyHostToDevice))
+            return fail(CMH_ERR_CUDA);
+        if (prepare_sweep32_batch(r.smem, &r.grid)) return fail(CMH_ERR_CUDA);
+        if (cudaStreamCreateWithFlags(&r.stream, cudaStreamNonBlocking) ||
+            cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming))
+            return fail(CMH_ERR_CUDA);
+    }
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) ||
+        cudaEventCreateWithFlags(&b->finished, cudaEventDisableTiming))
+        return fail(CMH_ERR_CUDA);
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(CMH_ERR_CUDA);
     cudaError_t e = launch_rebin_batch(b->G, b->D, b->blk_off, b->n, b->n_blocks, b->max_ev_cap, b->stream);
-    if (e == cudaSuccess)
-        e = launch_sweep32_batch(b->G, b->D, b->n, b->n_col, b->item_tab, b->queue, b->smem, b->grid, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
+    for (BatchGroup& r : b->groups) {
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(r.stream, b->fork, 0);
+        if (e == cudaSuccess) e = launch_sweep32_batch(r.G, r.D, r.n, r.n_col, r.item_tab, r.queue, r.smem, r.grid, r.stream);
+        if (e == cudaSuccess) e = cudaEventRecord(r.done, r.stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, r.done, 0);
+    }
     if (e == cudaSuccess) e = launch_sweep_end_batch(b->G, b->D, b->n, b->stream);
     const cudaError_t e2 = cudaStreamEndCapture(b->stream, &b->graph);
     if (e != cudaSuccess || e2 != cudaSuccess) return fail(CMH_ERR_CUDA);
@@ -1060,19 +1126,41 @@ extern "C" int cmh_batch_run_sweeps(cmh_batch* b, int64_t n) {
         const cmh_model* m = b->models[i];
         if (m->latched || !m->partitioned || m->part_gen != b->gens[i]) return CMH_ERR_STATE;
     }
+    if (n == 0) return CMH_OK;
     for (int i = 0; i < b->n; ++i)   // the models' own queued work first
         CK(cudaStreamSynchronize(b->models[i]->stream));
     for (int64_t s = 0; s < n; ++s) CK(cudaGraphLaunch(b->exec, b->stream));
+    // later calls on a model's own stream wait for these sweeps
+    CK(cudaEventRecord(b->finished, b->stream));
+    for (int i = 0; i < b->n; ++i) {
+        cmh_model* m = b->models[i];
+        CK(cudaStreamWaitEvent(m->stream, b->finished, 0));
+        m->sweeps += n;
+        m->launches += n * (4 + 2 * (long long)b->groups.size());   // re-binning, sweep end; plan + phase per group
+    }
+    return CMH_OK;
+}
+
+extern "C" int cmh_batch_sync(cmh_batch* b) {
+    if (!b) return CMH_ERR_ARG;
     CK(cudaStreamSynchronize(b->stream));
     int rc = CMH_OK;
     for (int i = 0; i < b->n; ++i) {
-        cmh_model* m = b->models[i];
-        m->sweeps += n;
-        m->launches += n * kBatchLaunchesPerSweep;
-        const int st = check_status(m);
+        const int st = check_status(b->models[i]);
         if (st && rc == CMH_OK) rc = st;
     }
     return rc;
+}
+
+extern "C" int cmh_batch_groups(const cmh_batch* b, int32_t* n_groups, int32_t* models_per_group,
+                                int32_t* grid_per_group, int32_t cap) {
+    if (!b || !n_groups || cap < 0) return CMH_ERR_ARG;
+    *n_groups = (int32_t)b->groups.size();
+    for (int i = 0; i < (int)b->groups.size() && i < cap; ++i) {
+        if (models_per_group) models_per_group[i] = b->groups[i].n;
+        if (grid_per_group) grid_per_group[i] = b->groups[i].grid;
+    }
+    return CMH_OK;
 }
 
 extern "C" void cmh_batch_destroy(cmh_batch* b) {

@@ -23,9 +23,9 @@ def _worlds():
     return out
 
 
-def _model(cm, w, seed, start_truth):
+def _model(cm, w, seed, start_truth, ev_capacity=0):
     m = cm.create_model(w.events if start_truth else None, w.stations, w.signals,
-                        cm.make_params(w.params, k_per_phase=24, seed=seed, dtype=cm.F32))
+                        cm.make_params(w.params, k_per_phase=24, seed=seed, dtype=cm.F32, ev_capacity=ev_capacity))
     m.partition_and_color(w.params.L, shift_mode=1)
     return m
 
@@ -33,13 +33,18 @@ def _model(cm, w, seed, start_truth):
 def test_batch_equals_models_run_alone():
     cm = lib()
     worlds = _worlds()
-    alone = [_model(cm, w, 10 + i, i % 2 == 0) for i, w in enumerate(worlds)]
-    batched = [_model(cm, w, 10 + i, i % 2 == 0) for i, w in enumerate(worlds)]
+    # larger event capacities need more shared memory per region: the batch
+    # puts those models in groups with fewer resident CTAs per SM
+    caps = [0, 512, 0, 320, 0, 512, 0]
+    alone = [_model(cm, w, 10 + i, i % 2 == 0, caps[i]) for i, w in enumerate(worlds)]
+    batched = [_model(cm, w, 10 + i, i % 2 == 0, caps[i]) for i, w in enumerate(worlds)]
     for m in alone:
         m.run_sweeps(12)
     b = cm.create_batch(batched)
+    assert len(b.groups()) >= 2 and sum(g[0] for g in b.groups()) == len(worlds)
     b.run_sweeps(5)
     b.run_sweeps(7)
+    b.sync()
     for i, (a, c) in enumerate(zip(alone, batched)):
         ea, ia, la, sa = a.read_state()
         ec, ic, lc, sc = c.read_state()
@@ -72,6 +77,7 @@ def test_batch_rejects_unsuitable_models():
     with pytest.raises(cm.ChromhError) as ei:
         b.run_sweeps(1)
     assert ei.value.code == -8
+    b.sync()
     b.destroy()
     m.destroy()
     f64.destroy()

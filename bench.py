@@ -46,7 +46,7 @@ def _peaks():
 
 
 KERNEL_SOURCES = ["paper_1612_00595_gb300/csrc/cmh_phase32.cu", "paper_1612_00595_gb300/csrc/cmh_common.cuh"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "phase32_scale_dram.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep32_scale_dram.json")
 
 
 def _kernel_digest() -> str:
@@ -258,7 +258,8 @@ def run_ours(args):
     traffic, traffic_src = _traffic() if f32 else (None, "float64 path not captured")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": traffic_src,
-            "kernel": "phase32_kernel<false> (float32 colour phase)" if f32 else "phase_kernel (float64 replay)",
+            "kernel": "sweep32_kernel<false> (one launch per sweep: all colour phases)" if f32
+                      else "phase_kernel (float64 replay, one launch per colour phase)",
             "avg_launch_us": per_launch_s * 1e6, "alg_bytes_per_launch": per_launch_bytes,
             "peak_source": peak_kind}
     m.destroy()

@@ -75,6 +75,7 @@ def lib(mutant: int = 0):
             "orc_philox4x64": (None, [P, P, P]),
             "orc_world_new": (P, [C.POINTER(_Params), P, i32, P, i32, i64, i64]),
             "orc_world_free": (None, [P]),
+            "orc_set_birth_table": (C.c_int, [P, P, i32, i32, i32, d]),
             "orc_set_new": (P, [P, P, i64]),
             "orc_set_size": (i64, [P]),
             "orc_set_get": (None, [P, P, P]),
@@ -178,6 +179,20 @@ class World:
         if h:
             self._lib.orc_world_free(h)
             self._h = None
+
+    def set_birth_table(self, tab, mix=0.5):
+        """Learned birth component: tab [ny, nx, nt] float32 weights over pixels
+        of [0,W)^2 and time bins of [0,T), mixed with the uniform birth with
+        weight mix; None removes it."""
+        if tab is None:
+            self._tab = None
+            rc = self._lib.orc_set_birth_table(self._h, None, 0, 0, 0, 0.0)
+        else:
+            self._tab = np.ascontiguousarray(tab, dtype=np.float32)
+            ny, nx, nt = self._tab.shape
+            rc = self._lib.orc_set_birth_table(self._h, _ptr(self._tab), nx, ny, nt, float(mix))
+        if rc != 0:
+            raise ValueError("orc_set_birth_table rejected the table")
 
     # ---- density -----------------------------------------------------------
     def log_prior(self, ev) -> float:

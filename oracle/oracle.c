@@ -49,6 +49,12 @@ struct orc_world {
     const void* sig;     /* [n_st][pitch], caller-owned */
     int32_t f32;
     int64_t n_samp, pitch;
+    /* learned birth component (none when bt_nx == 0): a weight table over
+     * pixels (bt_nx x bt_ny over [0,W)^2) and time bins (bt_nt over [0,T)) */
+    int32_t bt_nx, bt_ny, bt_nt;
+    double bt_mix, bt_hx, bt_hy, bt_dt, bt_pixarea;
+    double* bt_mass;     /* [pixel] sum of the pixel's weights */
+    double* bt_cdf;      /* [pixel][bin] running sum of its weights / mass */
 };
 
 struct orc_set { ev_t* e; int64_t n, cap; };
@@ -89,14 +95,17 @@ static double u01o(uint64_t w) { return (double)((w >> 11) + 1) * (1.0 / 9007199
 /* uniform integer in [0, n) from the low 32 bits */
 static int64_t pick(uint64_t w, int64_t n) { return (int64_t)(((w & 0xffffffffULL) * (uint64_t)n) >> 32); }
 
-/* eight 64-bit words of one MH step: counter (c0, c1, c2, 0|1), key (seed, stream) */
+/* twelve 64-bit words of one MH step: counter (c0, c1, c2, 0|1|2), key
+ * (seed, stream); the third block is used only by learned births */
 static void step_words(const orc_world* w, uint64_t stream, uint64_t c0, uint64_t c1, uint64_t c2,
-                       uint64_t out[8]) {
+                       uint64_t out[12]) {
     uint64_t key[2] = { w->p.seed, stream };
     uint64_t ctr[4] = { c0, c1, c2, 0 };
     orc_philox4x64(ctr, key, out);
     ctr[3] = 1;
     orc_philox4x64(ctr, key, out + 4);
+    ctr[3] = 2;
+    orc_philox4x64(ctr, key, out + 8);
 }
 
 /* ------------------------------------------------------------------------
@@ -119,7 +128,46 @@ orc_world* orc_world_new(const orc_params* p, const double* stations, int32_t n_
 void orc_world_free(orc_world* w) {
     if (!w) return;
     free(w->st);
+    free(w->bt_mass);
+    free(w->bt_cdf);
     free(w);
+}
+
+/* The learned component of the birth proposal (a mixture with the uniform
+ * birth, mixing weight mix): tab[(iy * nx + ix) * nt + b] >= 0 is the weight
+ * of pixel (ix, iy) of side (W/nx, W/ny) and time bin b of length T/nt.
+ * Sums run in index order in float64.  nx == 0 removes the component. */
+int orc_set_birth_table(orc_world* w, const float* tab, int32_t nx, int32_t ny, int32_t nt, double mix) {
+    free(w->bt_mass);
+    free(w->bt_cdf);
+    w->bt_mass = NULL;
+    w->bt_cdf = NULL;
+    w->bt_nx = w->bt_ny = w->bt_nt = 0;
+    if (nx == 0) return 0;
+    if (nx < 1 || ny < 1 || nt < 1 || !(mix > 0.0 && mix < 1.0) || !tab) return -1;
+    const int64_t np = (int64_t)nx * ny;
+    w->bt_mass = (double*)malloc(sizeof(double) * (size_t)np);
+    w->bt_cdf = (double*)malloc(sizeof(double) * (size_t)(np * nt));
+    for (int64_t q = 0; q < np; ++q) {
+        double run = 0.0;
+        for (int32_t b = 0; b < nt; ++b) {
+            const double v = (double)tab[q * nt + b];
+            if (!(v >= 0.0) || isinf(v)) return -1;
+            run += v;
+            w->bt_cdf[q * nt + b] = run;
+        }
+        w->bt_mass[q] = run;
+        for (int32_t b = 0; b < nt; ++b) w->bt_cdf[q * nt + b] = run > 0.0 ? w->bt_cdf[q * nt + b] / run : 0.0;
+    }
+    w->bt_nx = nx;
+    w->bt_ny = ny;
+    w->bt_nt = nt;
+    w->bt_mix = mix;
+    w->bt_hx = w->p.W / (double)nx;
+    w->bt_hy = w->p.W / (double)ny;
+    w->bt_dt = w->p.T / (double)nt;
+    w->bt_pixarea = w->bt_hx * w->bt_hy;
+    return 0;
 }
 
 static double sig_at(const orc_world* w, int32_t j, int64_t k) {
@@ -404,7 +452,56 @@ typedef struct {
     int32_t cell;          /* -1: whole domain (serial sampler) */
     double r[4];           /* x0, x1, y0, y1 of the region within the domain */
     double sx, sy;
+    double G;              /* learned component: table mass inside the region */
 } region_t;
+
+/* pixel range that may overlap [r0, r1) along one axis of pixel side h (one
+ * pixel of margin each way: pixels that do not overlap weigh nothing) */
+static void pix_range(double r0, double r1, double h, int32_t n, int32_t* i0, int32_t* i1) {
+    int32_t a = (int32_t)(r0 / h) - 1, b = (int32_t)(r1 / h) + 1;
+    *i0 = a < 0 ? 0 : a;
+    *i1 = b > n - 1 ? n - 1 : b;
+}
+
+/* overlap of pixel i (side h) with [r0, r1) */
+static double pix_overlap(double r0, double r1, double h, int32_t i) {
+    const double p0 = (double)i * h, p1 = (double)(i + 1) * h;
+    const double lo = p0 > r0 ? p0 : r0, hi = p1 < r1 ? p1 : r1;
+    return hi > lo ? hi - lo : 0.0;
+}
+
+/* table mass of pixel (ix, iy) inside the region: M_p |p n R| / |p| */
+static double pix_weight(const orc_world* w, const region_t* g, int32_t ix, int32_t iy) {
+    const double ox = pix_overlap(g->r[0], g->r[1], w->bt_hx, ix);
+    const double oy = pix_overlap(g->r[2], g->r[3], w->bt_hy, iy);
+    return w->bt_mass[(int64_t)iy * w->bt_nx + ix] * ((ox * oy) / w->bt_pixarea);
+}
+
+/* the region's table mass, summed over its pixel range in (iy, ix) order */
+static void region_bt(const orc_world* w, region_t* g) {
+    g->G = 0.0;
+    if (!w->bt_nx) return;
+    int32_t x0, x1, y0, y1;
+    pix_range(g->r[0], g->r[1], w->bt_hx, w->bt_nx, &x0, &x1);
+    pix_range(g->r[2], g->r[3], w->bt_hy, w->bt_ny, &y0, &y1);
+    for (int32_t iy = y0; iy <= y1; ++iy)
+        for (int32_t ix = x0; ix <= x1; ++ix) g->G += pix_weight(w, g, ix, iy);
+}
+
+/* density of the learned component at (x, y, t), magnitude factor left out:
+ * the pixel's mass share of the region over the pixel area, times the time
+ * bin's share of the pixel over the bin length */
+static double q_net(const orc_world* w, const region_t* g, double x, double y, double t) {
+    if (!(g->G > 0.0)) return 0.0;
+    int32_t ix = (int32_t)floor(x / w->bt_hx), iy = (int32_t)floor(y / w->bt_hy), b = (int32_t)floor(t / w->bt_dt);
+    if (ix > w->bt_nx - 1) ix = w->bt_nx - 1;
+    if (iy > w->bt_ny - 1) iy = w->bt_ny - 1;
+    if (b > w->bt_nt - 1) b = w->bt_nt - 1;
+    const int64_t q = (int64_t)iy * w->bt_nx + ix;
+    const double* c = w->bt_cdf + q * w->bt_nt;
+    const double share = c[b] - (b > 0 ? c[b - 1] : 0.0);
+    return w->bt_mass[q] * share / (w->bt_pixarea * g->G * w->bt_dt);
+}
 
 static int in_region(const orc_world* w, const region_t* g, const ev_t* e) {
     const orc_params* p = &w->p;
@@ -438,7 +535,9 @@ static int64_t lat_points(const orc_world* w, const region_t* g, int64_t want, d
     return c;
 }
 
-/* log of the birth proposal density (mass in lattice mode) at e */
+/* log of the birth proposal density (mass in lattice mode) at e: uniform on
+ * cell n D x [0, T) with m - 2 ~ Exp(1), or its mixture with the learned
+ * component (same magnitude law) */
 static double log_qb(const orc_world* w, const region_t* g, const ev_t* e) {
     const orc_params* p = &w->p;
     if (p->lattice) {
@@ -446,7 +545,42 @@ static double log_qb(const orc_world* w, const region_t* g, const ev_t* e) {
         return -log(nr) - log((double)p->lat_nt) - log((double)p->lat_nm);
     }
     double area = (g->r[1] - g->r[0]) * (g->r[3] - g->r[2]);
-    return -log(area) - log(p->T) - (e->m - 2.0);
+    if (!w->bt_nx || !(g->G > 0.0) || ORC_MUTANT == 5) return -log(area) - log(p->T) - (e->m - 2.0);
+    const double qu = 1.0 / (area * p->T);
+    return log((1.0 - w->bt_mix) * qu + w->bt_mix * q_net(w, g, e->x, e->y, e->t)) - (e->m - 2.0);
+}
+
+/* a learned birth candidate: pixel by its share of the region's table mass,
+ * uniform inside pixel n region, time bin by the pixel's cdf, uniform inside
+ * the bin (words: pixel wd[2], x wd[3], y wd[8], bin wd[9], t wd[10]) */
+static void learned_birth(const orc_world* w, const region_t* g, const uint64_t* wd, ev_t* c) {
+    int32_t x0, x1, y0, y1;
+    pix_range(g->r[0], g->r[1], w->bt_hx, w->bt_nx, &x0, &x1);
+    pix_range(g->r[2], g->r[3], w->bt_hy, w->bt_ny, &y0, &y1);
+    const double target = u01(wd[2]) * g->G;
+    double run = 0.0;
+    int32_t px = -1, py = -1, lastx = -1, lasty = -1;
+    for (int32_t iy = y0; iy <= y1; ++iy)
+        for (int32_t ix = x0; ix <= x1; ++ix) {
+            const double a = pix_weight(w, g, ix, iy);
+            if (a <= 0.0) continue;
+            run += a;
+            lastx = ix;
+            lasty = iy;
+            if (px < 0 && run > target) { px = ix; py = iy; }
+        }
+    if (px < 0) { px = lastx; py = lasty; }   /* target reached the total by rounding */
+    const double xa = (double)px * w->bt_hx, xb = (double)(px + 1) * w->bt_hx;
+    const double ya = (double)py * w->bt_hy, yb = (double)(py + 1) * w->bt_hy;
+    const double lx = xa > g->r[0] ? xa : g->r[0], hx = xb < g->r[1] ? xb : g->r[1];
+    const double ly = ya > g->r[2] ? ya : g->r[2], hy = yb < g->r[3] ? yb : g->r[3];
+    c->x = lx + u01(wd[3]) * (hx - lx);
+    c->y = ly + u01(wd[8]) * (hy - ly);
+    const double* cd = w->bt_cdf + ((int64_t)py * w->bt_nx + px) * w->bt_nt;
+    const double ub = u01(wd[9]);
+    int32_t b = 0;
+    while (b < w->bt_nt - 1 && !(cd[b] > ub)) ++b;
+    c->t = (double)b * w->bt_dt + u01(wd[10]) * w->bt_dt;
 }
 
 /* Gaussian magnitude of a Box-Muller pair, rounded to a multiple of 2^-20 so
@@ -475,6 +609,9 @@ static prop_t decode(const orc_world* w, const region_t* g, const uint64_t* wd,
             q.cand.x = xy[0]; q.cand.y = xy[1];
             q.cand.t = p->lat_t0 + (double)pick(wd[3], p->lat_nt) * p->lat_dt;
             q.cand.m = p->lat_m0 + (double)pick(wd[4], p->lat_nm) * p->lat_dm;
+        } else if (w->bt_nx && g->G > 0.0 && u01(wd[7]) < w->bt_mix) {
+            learned_birth(w, g, wd, &q.cand);
+            q.cand.m = 2.0 - log(u01o(wd[5]));
         } else {
             q.cand.x = g->r[0] + u01(wd[2]) * (g->r[1] - g->r[0]);
             q.cand.y = g->r[2] + u01(wd[3]) * (g->r[3] - g->r[2]);
@@ -578,7 +715,7 @@ static void apply(vec_t* own, const prop_t* q, uint64_t new_id) {
 static void mh_step(const orc_world* w, const region_t* g, vec_t* own, const ev_t* oth, int64_t n_oth,
                     int64_t n_total_other, uint64_t stream, uint64_t c0, uint64_t c1, uint64_t c2,
                     uint64_t new_id, orc_trace* tr, double* dlogp) {
-    uint64_t wd[8];
+    uint64_t wd[12];
     step_words(w, stream, c0, c1, c2, wd);
     prop_t q = decode(w, g, wd, own->e, own->n, own->n + n_total_other);
     double dll = 0.0, dlp = 0.0, la = -INFINITY;
@@ -610,6 +747,7 @@ double orc_log_alpha(const orc_world* w, double sx, double sy, int32_t cell,
     g.cell = cell; g.sx = sx; g.sy = sy;
     if (cell < 0) { g.r[0] = 0.0; g.r[1] = w->p.W; g.r[2] = 0.0; g.r[3] = w->p.W; }
     else orc_cell_rect(w, sx, sy, cell, g.r);
+    region_bt(w, &g);
     vec_t own = { 0, 0, 0 }, oth = { 0, 0, 0 };
     for (int64_t i = 0; i < n; ++i) {
         ev_t e; to_ev(ev + 4 * i, &e);
@@ -643,6 +781,7 @@ int orc_run_serial(const orc_world* w, orc_set* s, int64_t step0, int64_t n_step
     region_t g;
     g.cell = -1; g.sx = 0.0; g.sy = 0.0;
     g.r[0] = 0.0; g.r[1] = w->p.W; g.r[2] = 0.0; g.r[3] = w->p.W;
+    region_bt(w, &g);
     vec_t own = { s->e, s->n, s->cap };
     double acc_lp = 0.0;
     int64_t nt = 0;
@@ -732,6 +871,7 @@ int orc_run_chromatic(const orc_world* w, orc_set* s, int64_t sweep0, int64_t n_
                 region_t g;
                 g.cell = c; g.sx = sx; g.sy = sy;
                 orc_cell_rect(w, sx, sy, c, g.r);
+                region_bt(w, &g);
                 /* the region's Markov blanket: events of cells within per-1 */
                 vec_t oth = { 0, 0, 0 };
                 int32_t ix = c % ncx, iy = c / ncx;

@@ -55,6 +55,10 @@ void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4
 orc_world* orc_world_new(const orc_params* p, const double* stations, int32_t n_st,
                          const void* signals, int32_t signals_f32, int64_t n_samp, int64_t pitch);
 void orc_world_free(orc_world* w);
+/* learned birth component: weights tab[(iy * nx + ix) * nt + b] over pixels of
+ * [0,W)^2 and time bins of [0,T), mixing weight mix in (0, 1); nx == 0
+ * removes it.  Returns 0, or -1 for bad arguments. */
+int orc_set_birth_table(orc_world* w, const float* tab, int32_t nx, int32_t ny, int32_t nt, double mix);
 
 orc_set* orc_set_new(const double* ev, const uint64_t* ids, int64_t n);
 int64_t orc_set_size(const orc_set* s);

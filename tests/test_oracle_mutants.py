@@ -6,7 +6,10 @@ oracle.c); the test asserts that the pin meant to catch it fails:
           enumerated lattice world;
   3 (an arrival adds its standard deviation, not its variance) -> Monte-Carlo
           of the generative story; detailed balance alone cannot see it,
-          because the mutant is a self-consistent sampler of a wrong model.
+          because the mutant is a self-consistent sampler of a wrong model;
+  5 (the Hastings term of a birth ignores the learned component of the
+          mixture proposal) -> a prior-only chain drifts to the table's hot
+          block.
 """
 import math
 
@@ -58,3 +61,9 @@ def test_variance_mutant_caught_by_generative_draws(orc):
     assert _generative_ratio(orc, 3) > 20.0
     # ... while detailed balance is blind to it
     assert _max_imbalance(orc, 3) < 1e-13
+
+
+def test_mixture_mutant_drifts_to_the_hot_block(orc):
+    from test_oracle_sampler import _prior_with_table
+    _, _, fxy, ft = _prior_with_table(orc, mutant=5, n_sweeps=1500)
+    assert fxy > 0.1 and ft > 0.24, (fxy, ft)   # unmutated: 0.0625 and 0.2

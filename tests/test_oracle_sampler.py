@@ -262,3 +262,43 @@ def test_threaded_chromatic_equals_sequential(orc):
     # the running log-density change equals a from-scratch recomputation
     empty = np.zeros((0, 4))
     assert a[3] == pytest.approx(o.log_density(a[0]) - o.log_density(empty), rel=1e-9)
+
+
+def _hot_table():
+    """8 x 8 pixels of 25 km over 200 km, 10 bins of 10 s: weight 1, and 200 in
+    a 2 x 2 pixel block during two bins."""
+    tab = np.ones((8, 8, 10), dtype=np.float32)
+    tab[5:7, 1:3, 2:4] = 200.0
+    return tab
+
+
+def _prior_with_table(orc, mutant=0, n_sweeps=3000):
+    p = worldgen.ModelParams(W=200.0, T=100.0, Lambda=12.0, R_max=50.0, L=100.0)
+    w = worldgen.World(params=p, stations=np.zeros((0, 2)), signals=np.zeros((0, 0)),
+                       events=np.zeros((0, 4)))
+    o = orc.World(w, k_per_phase=8, seed=12, sig_xy=20.0, sig_t=10.0, sig_m=0.5, mutant=mutant)
+    o.set_birth_table(_hot_table(), mix=0.5)
+    ev, ids = np.zeros((0, 4)), None
+    Ns, hot_xy, hot_t, n_seen = [], 0, 0, 0
+    for it in range(n_sweeps):
+        ev, ids, _, _ = o.run_chromatic(ev, 1, ids=ids, sweep0=it, shift_mode=1)
+        Ns.append(len(ev))
+        if it % 5 == 0 and len(ev):
+            in_xy = (ev[:, 0] >= 25.0) & (ev[:, 0] < 75.0) & (ev[:, 1] >= 125.0) & (ev[:, 1] < 175.0)
+            in_t = (ev[:, 2] >= 20.0) & (ev[:, 2] < 40.0)
+            hot_xy += int(in_xy.sum())
+            hot_t += int(in_t.sum())
+            n_seen += len(ev)
+    return p, np.array(Ns), hot_xy / n_seen, hot_t / n_seen
+
+
+def test_learned_birth_mixture_keeps_the_prior(orc):
+    """With no stations the posterior is the prior.  A birth proposal that
+    prefers a small space-time block (the learned component of the mixture)
+    must not pull the chain there: the Hastings term carries the mixture
+    density.  Event count ~ Poisson(Lambda), positions and times uniform."""
+    p, Ns, fxy, ft = _prior_with_table(orc)
+    m, se = _batch_se(Ns)
+    assert abs(m - p.Lambda) < 5 * se, (m, se)
+    assert abs(fxy - 4.0 / 64.0) < 0.012, fxy
+    assert abs(ft - 0.2) < 0.025, ft

@@ -238,6 +238,23 @@ const char* cmh_strerror(int code);
  * cmh_batch_groups: the number of groups and, for the first `cap`, their
  *   models and persistent-launch CTAs.
  */
+/* ---- learned birth proposal --------------------------------------------------
+ * cmh_set_birth_table makes the birth proposal a mixture (float32 form): with
+ * probability mix (0 < mix < 1) a birth comes from the table, otherwise it is
+ * uniform in the region as before.  tab[(iy * nx + ix) * nt + b] >= 0 (host
+ * memory, copied) weights pixel (ix, iy) of side (W/nx, W/ny) and time bin b
+ * of length T/nt.  A table birth in a region picks a pixel by its share of
+ * the region's table mass (pixel mass times the fraction of the pixel inside
+ * the region), a position uniform in pixel and region, a time bin by the
+ * pixel's weights and a time uniform in the bin; the magnitude is drawn as
+ * for uniform births.  The birth and death Hastings terms carry the mixture
+ * density, so the chain still targets the posterior (the prior, without
+ * stations).  A region's pixel range may span at most 256 pixels
+ * ((L nx / W + 4)(L ny / W + 4) <= 256).  nx == 0 removes the table.
+ * Errors: CMH_ERR_ARG (float64 model, bad sizes or mix), CMH_ERR_NONFINITE
+ * (a negative or non-finite weight), CMH_ERR_OOM. */
+int cmh_set_birth_table(cmh_model* m, const float* tab, int32_t nx, int32_t ny, int32_t nt, double mix);
+
 /* ---- autotuning ------------------------------------------------------------
  * cmh_autotune times, from a checkpoint of the model, trial_sweeps sweeps of
  * each launch configuration the float32 form offers (colour by colour or

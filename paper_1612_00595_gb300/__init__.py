@@ -84,7 +84,7 @@ EXPORTS = ["cmh_create_model", "cmh_partition_and_color", "cmh_run_sweeps", "cmh
            "cmh_log_density", "cmh_set_trace", "cmh_read_trace", "cmh_set_timing", "cmh_read_shift",
            "cmh_checkpoint", "cmh_restore", "cmh_destroy", "cmh_strerror", "cmh_philox4x64",
            "cmh_gaussian_loglik_noalloc", "cmh_batch_create", "cmh_batch_run_sweeps", "cmh_batch_destroy",
-           "cmh_autotune", "cmh_batch_sync", "cmh_batch_groups"]
+           "cmh_autotune", "cmh_batch_sync", "cmh_batch_groups", "cmh_set_birth_table"]
 
 
 def _load():
@@ -118,6 +118,7 @@ def _load():
         "cmh_batch_destroy": (None, [P]),
         "cmh_autotune": (C.c_int, [P, i32, C.POINTER(Tuning)]),
         "cmh_batch_sync": (C.c_int, [P]),
+        "cmh_set_birth_table": (C.c_int, [P, P, i32, i32, i32, C.c_double]),
         "cmh_batch_groups": (C.c_int, [P, C.POINTER(i32), P, P, i32]),
     }
     for name, (res, args) in sig.items():
@@ -195,6 +196,17 @@ class Model:
 
     def run_sweeps(self, n: int):
         _check(lib.cmh_run_sweeps(self._h, int(n)), "cmh_run_sweeps")
+
+    def set_birth_table(self, tab, mix: float = 0.5):
+        """Learned birth component: tab [ny, nx, nt] weights over pixels of
+        [0,W)^2 and time bins of [0,T), mixed with the uniform birth with
+        weight mix; None removes it."""
+        if tab is None:
+            _check(lib.cmh_set_birth_table(self._h, None, 0, 0, 0, 0.0), "cmh_set_birth_table")
+            return
+        t = np.ascontiguousarray(tab, dtype=np.float32)
+        ny, nx, nt = t.shape
+        _check(lib.cmh_set_birth_table(self._h, _ptr(t), nx, ny, nt, float(mix)), "cmh_set_birth_table")
 
     def autotune(self, trial_sweeps: int = 8) -> dict:
         """Time each launch configuration from a checkpoint, keep the fastest,

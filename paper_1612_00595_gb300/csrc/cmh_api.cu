@@ -83,6 +83,8 @@ struct cmh_model {
     int timing = 0;
     int sweep_grid = 0;               // CTAs of the persistent sweep kernel (0: colour by colour)
     long long part_gen = 0;           // partitions made so far (a batch refuses a re-partitioned model)
+    double* bt_mass = nullptr;        // learned birth table (owned)
+    double* bt_cdf = nullptr;
     double phase_ms = 0.0;
     long long phase_launches = 0;
     int latched = 0;
@@ -396,6 +398,9 @@ int cmh_create_model(const cmh_event* init_events, int64_t n_events, const cmh_s
     g.TfK = (int)std::floor(g.Tf);
     g.lb0 = g.log_Lambda - g.log_WWT + 2.0;
     g.Cb0 = g.log_Lambda - g.log_WWT + g.log_T + g.log_pd - g.log_pb;
+    g.lLWT = g.log_Lambda - g.log_WWT;
+    g.lpdpb = g.log_pd - g.log_pb;
+    g.bt_on = 0;
     if (g.ev_cap < g.k + 1) return fail(CMH_ERR_ARG);
 
     Dev& d = m->d;
@@ -525,6 +530,7 @@ int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mo
     }
     m->free_partition();
     m->partitioned = false;
+    if (m->g.bt_on && (L / m->g.bt_hx + 4.0) * (L / m->g.bt_hy + 4.0) > 256.0) return CMH_ERR_ARG;
 
     Geo& g = m->g;
     g.L = L;
@@ -879,6 +885,8 @@ void cmh_destroy(cmh_model* m) {
     m->free_partition();
     for (void* q : m->allocs) cudaFree(q);
     m->allocs.clear();
+    if (m->bt_mass) cudaFree(m->bt_mass);
+    if (m->bt_cdf) cudaFree(m->bt_cdf);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
 }
@@ -902,6 +910,63 @@ int cmh_philox4x64(const uint64_t* ctr, const uint64_t* key, uint64_t* out, int6
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// learned birth component
+// ---------------------------------------------------------------------------
+extern "C" int cmh_set_birth_table(cmh_model* m, const float* tab, int32_t nx, int32_t ny, int32_t nt,
+                                   double mix) {
+    if (!m) return CMH_ERR_ARG;
+    if (m->latched) return CMH_ERR_STATE;
+    if (nx == 0) {   // back to uniform births
+        m->g.bt_on = 0;
+        m->drop_graph();
+        return CMH_OK;
+    }
+    if (!m->g.f32 || !tab || nx < 1 || ny < 1 || nt < 1 || !(mix > 0.0 && mix < 1.0)) return CMH_ERR_ARG;
+    const long long np = (long long)nx * ny;
+    if (np * nt > (1LL << 31)) return CMH_ERR_ARG;
+    // pixels a region's range may span (one pixel of margin each way)
+    if (m->partitioned) {
+        const double px = m->grid_L / (m->p.W / nx) + 4.0, py = m->grid_L / (m->p.W / ny) + 4.0;
+        if (px * py > 256.0) return CMH_ERR_ARG;
+    }
+    // per pixel: mass and cdf, running sums in index order in float64
+    std::vector<double> mass(np), cdf((size_t)(np * nt));
+    for (long long q = 0; q < np; ++q) {
+        double run = 0.0;
+        for (int b = 0; b < nt; ++b) {
+            const double v = (double)tab[q * nt + b];
+            if (!(v >= 0.0) || std::isinf(v)) return CMH_ERR_NONFINITE;
+            run += v;
+            cdf[q * nt + b] = run;
+        }
+        mass[q] = run;
+        for (int b = 0; b < nt; ++b) cdf[q * nt + b] = run > 0.0 ? cdf[q * nt + b] / run : 0.0;
+    }
+    CK(cudaStreamSynchronize(m->stream));
+    if (m->bt_mass) cudaFree(m->bt_mass);
+    if (m->bt_cdf) cudaFree(m->bt_cdf);
+    m->bt_mass = m->bt_cdf = nullptr;
+    if (cudaMalloc(&m->bt_mass, sizeof(double) * np) || cudaMalloc(&m->bt_cdf, sizeof(double) * np * nt))
+        return CMH_ERR_OOM;
+    CK(cudaMemcpy(m->bt_mass, mass.data(), sizeof(double) * np, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->bt_cdf, cdf.data(), sizeof(double) * np * nt, cudaMemcpyHostToDevice));
+    Geo& g = m->g;
+    g.bt_on = 1;
+    g.bt_nx = nx;
+    g.bt_ny = ny;
+    g.bt_nt = nt;
+    g.bt_mix = mix;
+    g.bt_hx = m->p.W / (double)nx;
+    g.bt_hy = m->p.W / (double)ny;
+    g.bt_dt = m->p.T / (double)nt;
+    g.bt_pixarea = g.bt_hx * g.bt_hy;
+    m->d.bt_mass = m->bt_mass;
+    m->d.bt_cdf = m->bt_cdf;
+    m->drop_graph();   // the captured sweep holds the old parameters
+    return CMH_OK;
+}
 
 // ---------------------------------------------------------------------------
 // autotuning of the launch configuration

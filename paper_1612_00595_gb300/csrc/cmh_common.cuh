@@ -49,6 +49,12 @@ struct Geo {
     int TfK;           // floor(T f)
     double lb0;        // log Lambda - log(W^2 T) + 2: log beta(m) = lb0 - m
     double Cb0;        // log Lambda - log(W^2 T) + log T + log p_d - log p_b (+ log area per region)
+    double lLWT;       // log Lambda - log(W^2 T)
+    double lpdpb;      // log p_d - log p_b
+    // learned birth component (bt_on == 0: uniform births only): weights over
+    // bt_nx x bt_ny pixels of [0,W)^2 and bt_nt time bins of [0,T)
+    int bt_on, bt_nx, bt_ny, bt_nt;
+    double bt_mix, bt_hx, bt_hy, bt_dt, bt_pixarea;
 };
 
 // one event store (structure of arrays) with per-cell slices
@@ -84,6 +90,8 @@ struct Dev {
     const float* stxf;          // float copies of the station coordinates
     const float* styf;
     const double* log_n;        // [ev_cap + 2] log(n) table, computed on the host
+    const double* bt_mass;      // [pixel] table mass of each pixel (learned birth component)
+    const double* bt_cdf;       // [pixel][bin] running sum of the pixel's weights / its mass
 };
 
 // --------------------------------------------------------------------------

@@ -49,6 +49,7 @@ constexpr int kMaxTasks32 = 32;
 constexpr int kUnroll = 2;     // float4 groups whose loads a pricing thread issues together
 constexpr int kFrozen = -2;    // owner tag of an arrival from a neighbouring region
 constexpr int kMinBlocks32 = 3;   // resident CTAs per SM the kernel is built for
+constexpr int kMaxPix = 256;      // pixels of the learned birth table a region's range may span
 static_assert(kThreads32 <= 256, "the decision reduces the worker warps' partials in a three-level tree");
 constexpr unsigned kWaitLimit = 1u << 24;   // bounded mbarrier waits
 
@@ -67,6 +68,7 @@ struct SA {             // an entry of a station's arrival list
 
 struct D32 {            // state-independent part of one MH step
     double bx, by, bt, bm, blb;   // birth: float64 candidate and its log beta
+    double blq;                   // birth: log Lambda - log(W^2 T) - log q_b(candidate) (magnitude factor out)
     float xr, yr, ph, mf;         // birth: relative form; move: offsets dx, dy, dt (s), dm
     float logu;
     unsigned pickw;
@@ -83,6 +85,7 @@ struct T32 {            // one station whose variance the proposal changes
 
 struct P32 {            // an event: float64 master, float32 terms, region-relative position
     double x, y, t, m;
+    double lq;          // log Lambda - log(W^2 T) - log q_b at the event (birth / death Hastings term)
     float xr, yr, ph, mf;
     int K, pad;
 };
@@ -96,6 +99,9 @@ struct Sm {
     int *enarr, *order, *freel;
     A32* earr;
     double *tabB, *tabD;
+    double* elq;        // [ev_cap] lq of each own event (see P32)
+    double* pcum;       // [kMaxPix] running table mass over the region's pixel range
+    int* pidx;          // [kMaxPix] pixel index of each entry
     int* bsta;
     double *bx, *by;
     int* scnt;          // entries of each station's arrival list
@@ -115,6 +121,10 @@ struct Sm {
     double rect[4], X0, Y0, sx, sy, region_dlp;
     float rl[4];        // region in relative coordinates: x lo, x hi, y lo, y hi
     int cell, n_own, n_free, n_blk, err, acc;
+    double bt_G;        // table mass inside the region (learned birth component)
+    double lq_unif;     // lq of the uniform birth alone: log(Lambda area / W^2)
+    double qu;          // density of the uniform birth in space-time: 1 / (area T)
+    int bt_np, bt_last; // pixel entries; last entry with mass
     int valid[2], idx[2], type[2], ncand[2], ntask[2], units[2], width[2];
     double thr[2];      // accept iff the log-likelihood change exceeds this (log u minus the other terms of log alpha)
     double dlp[2];      // log-prior change of the step
@@ -143,6 +153,9 @@ __host__ __device__ inline size_t layout32(const Geo& g, Sm* S, unsigned char* b
     int *enarr = (int*)take(4 * E), *order = (int*)take(4 * E), *freel = (int*)take(4 * E);
     A32* earr = (A32*)take(sizeof(A32) * E * g.arr_cap);
     double *tabB = (double*)take(8 * (E + 1)), *tabD = (double*)take(8 * (E + 1));
+    double* elq = (double*)take(8 * E);
+    double* pcum = (double*)take(8 * kMaxPix);
+    int* pidx = (int*)take(4 * kMaxPix);
     int* bsta = (int*)take(4 * B);
     double *bx = (double*)take(8 * B), *by = (double*)take(8 * B);
     int* scnt = (int*)take(4 * B);
@@ -164,7 +177,7 @@ __host__ __device__ inline size_t layout32(const Geo& g, Sm* S, unsigned char* b
         S->scap = (int)scap;
         S->mx = mx; S->my = my; S->mt = mt; S->mm = mm; S->eid = eid; S->exr = exr; S->eyr = eyr;
         S->enarr = enarr; S->order = order; S->freel = freel; S->earr = earr;
-        S->tabB = tabB; S->tabD = tabD; S->bsta = bsta; S->bx = bx; S->by = by;
+        S->tabB = tabB; S->tabD = tabD; S->elq = elq; S->pcum = pcum; S->pidx = pidx; S->bsta = bsta; S->bx = bx; S->by = by;
         S->scnt = scnt; S->sarr = sarr; S->draws = draws; S->cand = cand; S->tasks = tasks;
         S->nx = nx; S->ny = ny; S->nt = nt; S->nph = nph; S->nmf = nmf; S->nK = nK;
     }
@@ -266,6 +279,77 @@ __device__ __noinline__ bool inside_exact(const Geo& g, double sx, double sy, in
            m >= 2.0;
 }
 
+// ---- learned birth component (float64, explicitly rounded: the same values
+// as the oracle's plain float64 C) -------------------------------------------
+// pixel range that may overlap [r0, r1) along one axis (one pixel of margin)
+__device__ __forceinline__ void bt_range(double r0, double r1, double h, int n, int& i0, int& i1) {
+    const int a = (int)__ddiv_rn(r0, h) - 1, b = (int)__ddiv_rn(r1, h) + 1;
+    i0 = a < 0 ? 0 : a;
+    i1 = b > n - 1 ? n - 1 : b;
+}
+
+__device__ __forceinline__ double bt_overlap(double r0, double r1, double h, int i) {
+    const double p0 = __dmul_rn((double)i, h), p1 = __dmul_rn((double)(i + 1), h);
+    const double lo = p0 > r0 ? p0 : r0, hi = p1 < r1 ? p1 : r1;
+    return hi > lo ? __dsub_rn(hi, lo) : 0.0;
+}
+
+// table mass of pixel (ix, iy) inside the region rect r
+__device__ __forceinline__ double bt_weight(const Geo& g, const Dev& d, const double* r, int ix, int iy) {
+    const double ox = bt_overlap(r[0], r[1], g.bt_hx, ix), oy = bt_overlap(r[2], r[3], g.bt_hy, iy);
+    return __dmul_rn(d.bt_mass[(long long)iy * g.bt_nx + ix], __ddiv_rn(__dmul_rn(ox, oy), g.bt_pixarea));
+}
+
+// lq at (x, y, t): log Lambda - log(W^2 T) - log[(1 - mix) / (area T) + mix q_net]
+__device__ __noinline__ double bt_lq(const Geo& g, const Dev& d, double G, double qu, double x, double y, double t) {
+    double qn = 0.0;
+    if (G > 0.0) {
+        int ix = (int)floor(__ddiv_rn(x, g.bt_hx)), iy = (int)floor(__ddiv_rn(y, g.bt_hy));
+        int b = (int)floor(__ddiv_rn(t, g.bt_dt));
+        ix = ix > g.bt_nx - 1 ? g.bt_nx - 1 : ix;
+        iy = iy > g.bt_ny - 1 ? g.bt_ny - 1 : iy;
+        b = b > g.bt_nt - 1 ? g.bt_nt - 1 : b;
+        const long long q = (long long)iy * g.bt_nx + ix;
+        const double* c = d.bt_cdf + q * g.bt_nt;
+        const double share = __dsub_rn(c[b], b > 0 ? c[b - 1] : 0.0);
+        qn = __ddiv_rn(__dmul_rn(d.bt_mass[q], share), __dmul_rn(__dmul_rn(g.bt_pixarea, G), g.bt_dt));
+    }
+    const double qm = __dadd_rn(__dmul_rn(__dsub_rn(1.0, g.bt_mix), qu), __dmul_rn(g.bt_mix, qn));
+    return __dsub_rn(g.lLWT, log(qm));
+}
+
+// a birth from the learned component: pixel by its share of the region's
+// table mass (word w_pix), position uniform in pixel and region (w_x and the
+// third Philox block of the step), time bin by the pixel's cdf, time uniform
+// in the bin
+__device__ __noinline__ void learned_birth(const Geo& g, const Dev& d, const Sm& S, long long sweep, int cell,
+                                           int st, unsigned long long w_pix, unsigned long long w_x, P32& e) {
+    unsigned long long c2[4] = {(unsigned long long)sweep, (unsigned long long)cell, (unsigned long long)st, 2ULL};
+    philox4x64(c2, g.seed, 0ULL);
+    const double target = __dmul_rn(u01(w_pix), S.bt_G);
+    int lo = 0, hi = S.bt_np - 1;   // first entry whose running mass exceeds target
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (S.pcum[mid] > target) hi = mid; else lo = mid + 1;
+    }
+    const int j = S.pcum[lo] > target ? lo : S.bt_last;
+    const int px = S.pidx[j] % g.bt_nx, py = S.pidx[j] / g.bt_nx;
+    const double xa = __dmul_rn((double)px, g.bt_hx), xb = __dmul_rn((double)(px + 1), g.bt_hx);
+    const double ya = __dmul_rn((double)py, g.bt_hy), yb = __dmul_rn((double)(py + 1), g.bt_hy);
+    const double lx = xa > S.rect[0] ? xa : S.rect[0], hx = xb < S.rect[1] ? xb : S.rect[1];
+    const double ly = ya > S.rect[2] ? ya : S.rect[2], hy = yb < S.rect[3] ? yb : S.rect[3];
+    e.x = __dadd_rn(lx, __dmul_rn(u01(w_x), __dsub_rn(hx, lx)));
+    e.y = __dadd_rn(ly, __dmul_rn(u01(c2[0]), __dsub_rn(hy, ly)));
+    const double* cd = d.bt_cdf + (long long)S.pidx[j] * g.bt_nt;
+    const double ub = u01(c2[1]);
+    int b0 = 0, b1 = g.bt_nt - 1;   // first bin whose cdf exceeds ub (the last one otherwise)
+    while (b0 < b1) {
+        const int mid = (b0 + b1) >> 1;
+        if (cd[mid] > ub) b1 = mid; else b0 = mid + 1;
+    }
+    e.t = __dadd_rn(__dmul_rn((double)b0, g.bt_dt), __dmul_rn(u01(c2[2]), g.bt_dt));
+}
+
 // ---------------------------------------------------------------------------
 // preparation of one step (all lanes of warp 0): decode the proposal against
 // the current state, find the stations the candidate reaches, and merge the
@@ -295,10 +379,12 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
     c.xr = c.yr = c.ph = c.mf = 0.f;
     c.K = 0;
     c.pad = 0;
+    c.lq = 0.0;
     if (dr.type == 0) {
         valid = dr.bvalid;
         c.x = dr.bx; c.y = dr.by; c.t = dr.bt; c.m = dr.bm;
         c.xr = dr.xr; c.yr = dr.yr; c.ph = dr.ph; c.mf = dr.mf; c.K = dr.bK;
+        c.lq = dr.blq;
     } else if (n_own > 0) {
         idx = pick32(dr.pickw, n_own);
         ps = S.order[idx];
@@ -329,6 +415,7 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
                 valid = inside_exact(g, S.sx, S.sy, S.cell, c.x, c.y, c.t, c.m);
                 if (valid) to_rel(g, S.X0, S.Y0, c);
             }
+            if (valid) c.lq = g.bt_on ? bt_lq(g, d, S.bt_G, S.qu, c.x, c.y, c.t) : S.lq_unif;
         }
     }
     // candidate arrivals, lanes over blanket slots, compacted in slot order
@@ -428,10 +515,10 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
             // one comparison with the log-likelihood change
             double thr, dlp;
             if (dr.type == 0) {
-                thr = (double)dr.logu - S.tabB[n_own];
+                thr = (double)dr.logu - (dr.blq + S.tabB[n_own]);
                 dlp = dr.blb;
             } else if (dr.type == 1) {
-                thr = (double)dr.logu - S.tabD[n_own];
+                thr = (double)dr.logu - (S.tabD[n_own] - S.elq[ps]);
                 dlp = S.mm[ps] - g.lb0;
             } else {
                 const double dm = __dsub_rn(c.m, S.mm[ps]);
@@ -667,13 +754,43 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
             S.freel[g.ev_cap - 1 - i] = i;   // pops give the lowest free slot first
         }
     }
-    // ---- acceptance constants: log(beta / q_b) = log(Lambda area / W^2) --------
+    // ---- acceptance constants: the count terms of birth / death by event
+    // count; the position terms (log beta - log q_b) per candidate / event ----
     {
-        const double area = (S.rect[1] - S.rect[0]) * (S.rect[3] - S.rect[2]);
-        const double Cb = g.Cb0 + (double)logf((float)area);
         for (int n = tid; n <= g.ev_cap; n += nthr) {
-            S.tabB[n] = Cb - d.log_n[n + 1];
-            S.tabD[n] = n > 0 ? -Cb + d.log_n[n] : 0.0;
+            S.tabB[n] = g.lpdpb - d.log_n[n + 1];
+            S.tabD[n] = n > 0 ? -g.lpdpb + d.log_n[n] : 0.0;
+        }
+        if (tid == 0) {
+            const double area = __dmul_rn(__dsub_rn(S.rect[1], S.rect[0]), __dsub_rn(S.rect[3], S.rect[2]));
+            S.qu = __ddiv_rn(1.0, __dmul_rn(area, g.T));
+            S.lq_unif = __dsub_rn(g.lLWT, log(S.qu));
+            S.bt_G = 0.0;
+            S.bt_np = 0;
+            S.bt_last = -1;
+            if (g.bt_on) {
+                // the region's pixels in (iy, ix) order with their running mass
+                int x0, x1, y0, y1;
+                bt_range(S.rect[0], S.rect[1], g.bt_hx, g.bt_nx, x0, x1);
+                bt_range(S.rect[2], S.rect[3], g.bt_hy, g.bt_ny, y0, y1);
+                double run = 0.0;
+                int np = 0;
+                for (int iy = y0; iy <= y1; ++iy)
+                    for (int ix = x0; ix <= x1; ++ix) {
+                        if (np >= kMaxPix) {
+                            S.err = CMH_ERR_CAPACITY;
+                            continue;
+                        }
+                        const double a = bt_weight(g, d, S.rect, ix, iy);
+                        run = __dadd_rn(run, a);
+                        if (a > 0.0) S.bt_last = np;
+                        S.pcum[np] = run;
+                        S.pidx[np] = iy * g.bt_nx + ix;
+                        ++np;
+                    }
+                S.bt_np = np;
+                S.bt_G = run;
+            }
         }
     }
     // ---- blanket: stations within R_max of the region (float test, margin) ----
@@ -717,6 +834,9 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
         __syncthreads();
     }
     const int n_blk = S.n_blk;
+    // position terms of the own events (the death Hastings term)
+    for (int i = tid; i < n0; i += nthr)
+        S.elq[i] = g.bt_on ? bt_lq(g, d, S.bt_G, S.qu, S.mx[i], S.my[i], S.mt[i]) : S.lq_unif;
     // ---- arrival cache of the own events (warp per event, lanes over slots) -----
     for (int i = wid; i < n0; i += nw) {
         int K;
@@ -845,13 +965,18 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
         D.bvalid = 0;
         D.bK = 0;
         D.pad = 0;
-        D.bx = D.by = D.bt = D.bm = D.blb = 0.0;
+        D.bx = D.by = D.bt = D.bm = D.blb = D.blq = 0.0;
         if (D.type == 0) {
             P32 e;
-            e.x = __dadd_rn(S.rect[0], __dmul_rn(u01(c0[2]), __dsub_rn(S.rect[1], S.rect[0])));
-            e.y = __dadd_rn(S.rect[2], __dmul_rn(u01(c0[3]), __dsub_rn(S.rect[3], S.rect[2])));
-            e.t = __dmul_rn(u01(c1[0]), g.T);
+            if (g.bt_on && S.bt_last >= 0 && u01(c1[3]) < g.bt_mix) {
+                learned_birth(g, d, S, sweep, cell, st, c0[2], c0[3], e);
+            } else {
+                e.x = __dadd_rn(S.rect[0], __dmul_rn(u01(c0[2]), __dsub_rn(S.rect[1], S.rect[0])));
+                e.y = __dadd_rn(S.rect[2], __dmul_rn(u01(c0[3]), __dsub_rn(S.rect[3], S.rect[2])));
+                e.t = __dmul_rn(u01(c1[0]), g.T);
+            }
             e.m = mag_from_u53(c1[1]);
+            D.blq = g.bt_on ? bt_lq(g, d, S.bt_G, S.qu, e.x, e.y, e.t) : S.lq_unif;
             to_rel(g, X0, Y0, e);
             D.bx = e.x; D.by = e.y; D.bt = e.t; D.bm = e.m;
             D.blb = g.lb0 - e.m;
@@ -967,6 +1092,7 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
                             lists_remove(g, S, ps);
                         }
                         S.mx[ps] = c.x; S.my[ps] = c.y; S.mt[ps] = c.t; S.mm[ps] = c.m;
+                        S.elq[ps] = c.lq;
                         S.exr[ps] = c.xr; S.eyr[ps] = c.yr;
                         for (int a = 0; a < S.ncand[sl]; ++a) S.earr[ps * g.arr_cap + a] = cd[a];
                         S.enarr[ps] = S.ncand[sl];

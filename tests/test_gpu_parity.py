@@ -273,3 +273,49 @@ def test_autotune_restores_the_chain(cm):
     # bits (summation order): the log-density agrees to rounding
     assert np.array_equal(ia, ib) and np.array_equal(ea, eb) and pa == pb and sa == sb == 8
     assert la == pytest.approx(lb, rel=1e-11)
+
+
+def _table_for(w, nx=40, nt=36, seed=3):
+    """A learned-looking birth table: a smooth floor plus weight around the
+    generated events' pixels and time bins."""
+    rng = np.random.default_rng(seed)
+    tab = (0.2 + rng.random((nx, nx, nt))).astype(np.float32)
+    p = w.params
+    for x, y, t, m in w.events:
+        ix, iy, b = int(x / p.W * nx), int(y / p.W * nx), int(t / p.T * nt)
+        tab[max(0, iy - 1):iy + 2, max(0, ix - 1):ix + 2, max(0, b - 1):b + 2] += 40.0
+    return tab
+
+
+def test_fp32_dry_run_with_learned_birth_table(cm, orc):
+    """Birth proposals from the mixture with a table: the same candidates on
+    both sides (the table draw runs in explicitly rounded float64), Δℓ within
+    1e-4 and log α (which now carries the mixture density) likewise."""
+    w = small_world(seed=16, W=1000.0, T=3600.0, Lambda=500.0, n_side=10, dtype=np.float32)
+    tab = _table_for(w)
+    params = cm.make_params(w.params, k_per_phase=32, seed=21, dtype=cm.F32, commit=False)
+    m = cm.create_model(w.events, w.stations, w.signals, params)
+    m.set_birth_table(tab, 0.5)
+    m.partition_and_color(w.params.L, 1)
+    ncx = int(np.floor(w.params.W / w.params.L)) + 2
+    m.set_trace(4 * ncx * ncx * 32)
+    m.run_sweeps(4)
+    from gpu_helpers import TRACE_KEYS
+    tr = np.sort(m.read_trace(), order=TRACE_KEYS)
+    o = orc.World(w, k_per_phase=32, seed=21, commit=False)
+    o.set_birth_table(tab, 0.5)
+    _, _, otr, _ = o.run_chromatic(w.events, 4, trace_cap=200000, threads=min(16, os.cpu_count() or 1))
+    otr = np.sort(otr, order=TRACE_KEYS)
+    assert len(tr) == len(otr)
+    for key in ("sweep", "cell", "step", "type", "n_before"):
+        assert np.array_equal(tr[key], otr[key]), key
+    assert np.count_nonzero(tr["evaluated"] != otr["evaluated"]) <= max(2, len(tr) // 10000)
+    ev_ = (otr["evaluated"] == 1) & (tr["evaluated"] == 1)
+    births = ev_ & (otr["type"] == 0)
+    assert births.sum() > 500
+    err = np.abs(tr["dll"][ev_] - otr["dll"][ev_]) / np.maximum(np.abs(otr["dll"][ev_]), 1.0)
+    assert err.max() <= 1e-4
+    la_err = np.abs(tr["log_alpha"][ev_] - otr["log_alpha"][ev_]) / np.maximum(np.abs(otr["log_alpha"][ev_]), 1.0)
+    assert la_err.max() <= 1e-4
+    assert np.count_nonzero(tr["accepted"][ev_] != otr["accepted"][ev_]) <= max(2, ev_.sum() // 10000)
+    m.destroy()

@@ -230,8 +230,8 @@ const char* cmh_strerror(int code);
  *   creates its own).  Destroy the batch before its models.
  * cmh_batch_run_sweeps: enqueues n sweeps of every model on the batch's
  *   stream and returns; later calls on a model's own stream wait for them.
- *   CMH_ERR_STATE if a model failed or was re-partitioned since the batch
- *   was made.  Each model's state, statistics and sweep count advance as if
+ *   CMH_ERR_STATE if a model failed, was re-partitioned or had its birth
+ *   table set or removed since the batch was made.  Each model's state, statistics and sweep count advance as if
  *   cmh_run_sweeps(model, n) had run.
  * cmh_batch_sync: waits for the batch's sweeps; a device-side error of a
  *   model is latched in that model and the first one is returned.
@@ -249,11 +249,52 @@ const char* cmh_strerror(int code);
  * pixel's weights and a time uniform in the bin; the magnitude is drawn as
  * for uniform births.  The birth and death Hastings terms carry the mixture
  * density, so the chain still targets the posterior (the prior, without
- * stations).  A region's pixel range may span at most 256 pixels
+ * stations).  The sampling runs in explicitly rounded float64; the density
+ * term of log alpha uses the table's float weight and a float32 logarithm
+ * (about 1e-7 absolute), like the other float32 terms of the sweep.  A region's pixel range may span at most 256 pixels
  * ((L nx / W + 4)(L ny / W + 4) <= 256).  nx == 0 removes the table.
  * Errors: CMH_ERR_ARG (float64 model, bad sizes or mix), CMH_ERR_NONFINITE
  * (a negative or non-finite weight), CMH_ERR_OOM. */
 int cmh_set_birth_table(cmh_model* m, const float* tab, int32_t nx, int32_t ny, int32_t nt, double mix);
+
+/* ---- the network behind the learned birth proposal ----------------------------
+ * A 1-D convolutional network maps a tile of 8 x 8 stations (100 km apart,
+ * 800 km) x 256 samples (features log1p(s^2), layout [window][sample][station])
+ * to 4101 outputs: 4096 logits over the tile's 64 x 64 pixels (12.5 km,
+ * row-major from the tile origin), one "no event" logit, the mean and log sd
+ * of the event's origin time relative to the window start (s) and of its
+ * magnitude.  Products on the tensor cores in BF16 with FP32 accumulation;
+ * FP32 parameters (cmh_net_param_count floats) with BF16 copies.
+ *
+ * cmh_net_create: max_batch windows per call (1..4096); seeded initialisation.
+ * cmh_net_get_params / set_params: the FP32 parameters (host arrays).
+ * cmh_net_forward: outputs [batch][4101] for host features [batch][256][64].
+ * cmh_net_gradients: the gradient of the mean loss (cross-entropy over the
+ *   4097 classes, Gaussian negative log-likelihood of time and magnitude for
+ *   labels < 4096) with respect to every parameter, and the loss.
+ * cmh_net_train: `steps` AdamW steps on batches simulated on the GPU from the
+ *   generative model of `geometry` (its noise, attenuation, envelope, speed):
+ *   stations jittered by 25 km around an 8 x 8 grid, half the windows with one
+ *   event (origin time in [-15 s, window end)); *loss_out = the last batch's.
+ * cmh_net_birth_table: slides the network over a float32 model's signals:
+ *   n_tiles tiles (tiles[t*64 + s] = the model's station index of tile
+ *   station s, row-major from the tile origin tile_origin[2t], [2t+1] in km),
+ *   windows every hop_s seconds; each window adds its pixel probabilities
+ *   times its time Gaussian's mass per bin to table[(iy*nx + ix)*nt + b]
+ *   (pixels of side W/nx, W/ny, nt bins over [0,T)), for cmh_set_birth_table.
+ */
+typedef struct cmh_net cmh_net;
+int64_t cmh_net_param_count(void);
+int cmh_net_create(int32_t max_batch, uint64_t seed, void* cuda_stream, cmh_net** out);
+void cmh_net_destroy(cmh_net* n);
+int cmh_net_get_params(cmh_net* n, float* out);
+int cmh_net_set_params(cmh_net* n, const float* in);
+int cmh_net_forward(cmh_net* n, const float* features, int32_t batch, float* out);
+int cmh_net_gradients(cmh_net* n, const float* features, const int32_t* label, const float* t_label,
+                      const float* m_label, int32_t batch, float* grads, double* loss);
+int cmh_net_train(cmh_net* n, const cmh_model* geometry, int32_t steps, int32_t batch, double lr, double* loss_out);
+int cmh_net_birth_table(cmh_net* n, cmh_model* m, const int32_t* tiles, const double* tile_origin, int32_t n_tiles,
+                        int32_t nx, int32_t ny, int32_t nt, double hop_s, float* table);
 
 /* ---- autotuning ------------------------------------------------------------
  * cmh_autotune times, from a checkpoint of the model, trial_sweeps sweeps of

@@ -84,7 +84,9 @@ EXPORTS = ["cmh_create_model", "cmh_partition_and_color", "cmh_run_sweeps", "cmh
            "cmh_log_density", "cmh_set_trace", "cmh_read_trace", "cmh_set_timing", "cmh_read_shift",
            "cmh_checkpoint", "cmh_restore", "cmh_destroy", "cmh_strerror", "cmh_philox4x64",
            "cmh_gaussian_loglik_noalloc", "cmh_batch_create", "cmh_batch_run_sweeps", "cmh_batch_destroy",
-           "cmh_autotune", "cmh_batch_sync", "cmh_batch_groups", "cmh_set_birth_table"]
+           "cmh_autotune", "cmh_batch_sync", "cmh_batch_groups", "cmh_set_birth_table",
+           "cmh_net_param_count", "cmh_net_create", "cmh_net_destroy", "cmh_net_get_params", "cmh_net_set_params",
+           "cmh_net_forward", "cmh_net_gradients", "cmh_net_train", "cmh_net_birth_table"]
 
 
 def _load():
@@ -119,6 +121,15 @@ def _load():
         "cmh_autotune": (C.c_int, [P, i32, C.POINTER(Tuning)]),
         "cmh_batch_sync": (C.c_int, [P]),
         "cmh_set_birth_table": (C.c_int, [P, P, i32, i32, i32, C.c_double]),
+        "cmh_net_param_count": (i64, []),
+        "cmh_net_create": (C.c_int, [i32, C.c_uint64, P, C.POINTER(P)]),
+        "cmh_net_destroy": (None, [P]),
+        "cmh_net_get_params": (C.c_int, [P, P]),
+        "cmh_net_set_params": (C.c_int, [P, P]),
+        "cmh_net_forward": (C.c_int, [P, P, i32, P]),
+        "cmh_net_gradients": (C.c_int, [P, P, P, P, P, i32, P, C.POINTER(C.c_double)]),
+        "cmh_net_train": (C.c_int, [P, P, i32, i32, C.c_double, C.POINTER(C.c_double)]),
+        "cmh_net_birth_table": (C.c_int, [P, P, P, P, i32, i32, i32, i32, C.c_double, P]),
         "cmh_batch_groups": (C.c_int, [P, C.POINTER(i32), P, P, i32]),
     }
     for name, (res, args) in sig.items():
@@ -359,6 +370,86 @@ def create_batch(models, stream=None) -> Batch:
     _check(lib.cmh_batch_create(arr, len(models), C.c_void_p(stream) if stream else None, C.byref(h)),
            "cmh_batch_create")
     return Batch(h, models)
+
+
+NET_OUT = 4101        # 4096 tile pixels, "no event", time mean / log sd, magnitude mean / log sd
+NET_WINDOW = 256      # samples per window
+NET_STATIONS = 64     # stations per tile (8 x 8)
+
+
+class Net:
+    """The network behind the learned birth proposal (see cmh_net_* in the header)."""
+
+    def __init__(self, max_batch: int = 256, seed: int = 1, stream=None):
+        if hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self._h = C.c_void_p()
+        _check(lib.cmh_net_create(int(max_batch), int(seed), C.c_void_p(stream) if stream else None,
+                                  C.byref(self._h)), "cmh_net_create")
+        self.max_batch = max_batch
+        self.n_params = int(lib.cmh_net_param_count())
+
+    def __del__(self):
+        self.destroy()
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.cmh_net_destroy(self._h)
+        self._h = None
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(lib.cmh_net_get_params(self._h, _ptr(out)), "cmh_net_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n_params
+        _check(lib.cmh_net_set_params(self._h, _ptr(p)), "cmh_net_set_params")
+
+    def forward(self, features) -> np.ndarray:
+        x = np.ascontiguousarray(features, dtype=np.float32)
+        b = x.shape[0]
+        out = np.zeros((b, NET_OUT), dtype=np.float32)
+        _check(lib.cmh_net_forward(self._h, _ptr(x), b, _ptr(out)), "cmh_net_forward")
+        return out
+
+    def gradients(self, features, label, t_label, m_label):
+        x = np.ascontiguousarray(features, dtype=np.float32)
+        lab = np.ascontiguousarray(label, dtype=np.int32)
+        tl = np.ascontiguousarray(t_label, dtype=np.float32)
+        ml = np.ascontiguousarray(m_label, dtype=np.float32)
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = C.c_double()
+        _check(lib.cmh_net_gradients(self._h, _ptr(x), _ptr(lab), _ptr(tl), _ptr(ml), x.shape[0], _ptr(g),
+                                     C.byref(loss)), "cmh_net_gradients")
+        return g, loss.value
+
+    def train(self, geometry: Model, steps: int, batch: int = 256, lr: float = 1e-3) -> float:
+        loss = C.c_double()
+        _check(lib.cmh_net_train(self._h, geometry._h, int(steps), int(batch), float(lr), C.byref(loss)),
+               "cmh_net_train")
+        return loss.value
+
+    def birth_table(self, model: Model, tiles, origins, nx: int, ny: int, nt: int, hop_s: float = 12.8):
+        t = np.ascontiguousarray(tiles, dtype=np.int32)
+        o = np.ascontiguousarray(origins, dtype=np.float64)
+        tab = np.zeros((ny, nx, nt), dtype=np.float32)
+        _check(lib.cmh_net_birth_table(self._h, model._h, _ptr(t), _ptr(o), t.shape[0], nx, ny, nt, float(hop_s),
+                                       _ptr(tab)), "cmh_net_birth_table")
+        return tab
+
+
+def grid_tiles(n_side: int, spacing: float, tile: int = 8):
+    """Tiles of tile x tile stations of a row-major n_side x n_side station grid
+    (station r * n_side + c at cell (c, r) of side `spacing`): every tile origin
+    (i0, j0) with i0, j0 in [0, n_side - tile]; returns (tiles [n][64], origins [n][2] km)."""
+    tiles, origins = [], []
+    for i0 in range(n_side - tile + 1):
+        for j0 in range(n_side - tile + 1):
+            tiles.append([(i0 + r) * n_side + (j0 + c) for r in range(tile) for c in range(tile)])
+            origins.append([j0 * spacing, i0 * spacing])
+    return np.array(tiles, dtype=np.int32), np.array(origins, dtype=np.float64)
 
 
 def partition_and_color(model: Model, L: float, shift_mode: int = 1, sx: float = 0.0, sy: float = 0.0):

@@ -82,9 +82,10 @@ struct cmh_model {
     cudaGraphExec_t graph_exec = nullptr;
     int timing = 0;
     int sweep_grid = 0;               // CTAs of the persistent sweep kernel (0: colour by colour)
-    long long part_gen = 0;           // partitions made so far (a batch refuses a re-partitioned model)
+    long long part_gen = 0;           // partitions and birth tables set so far (a batch refuses a model changed since)
     double* bt_mass = nullptr;        // learned birth table (owned)
     double* bt_cdf = nullptr;
+    float* bt_tab = nullptr;
     double phase_ms = 0.0;
     long long phase_launches = 0;
     int latched = 0;
@@ -887,6 +888,7 @@ void cmh_destroy(cmh_model* m) {
     m->allocs.clear();
     if (m->bt_mass) cudaFree(m->bt_mass);
     if (m->bt_cdf) cudaFree(m->bt_cdf);
+    if (m->bt_tab) cudaFree(m->bt_tab);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
 }
@@ -911,6 +913,11 @@ int cmh_philox4x64(const uint64_t* ctr, const uint64_t* key, uint64_t* out, int6
 
 }  // extern "C"
 
+namespace cmh {
+Geo cmh_model_geo(const cmh_model* m) { return m->g; }
+Dev cmh_model_dev(const cmh_model* m) { return m->d; }
+}  // namespace cmh
+
 // ---------------------------------------------------------------------------
 // learned birth component
 // ---------------------------------------------------------------------------
@@ -920,6 +927,7 @@ extern "C" int cmh_set_birth_table(cmh_model* m, const float* tab, int32_t nx, i
     if (m->latched) return CMH_ERR_STATE;
     if (nx == 0) {   // back to uniform births
         m->g.bt_on = 0;
+        m->part_gen += 1;
         m->drop_graph();
         return CMH_OK;
     }
@@ -947,11 +955,18 @@ extern "C" int cmh_set_birth_table(cmh_model* m, const float* tab, int32_t nx, i
     CK(cudaStreamSynchronize(m->stream));
     if (m->bt_mass) cudaFree(m->bt_mass);
     if (m->bt_cdf) cudaFree(m->bt_cdf);
+    if (m->bt_tab) cudaFree(m->bt_tab);
     m->bt_mass = m->bt_cdf = nullptr;
-    if (cudaMalloc(&m->bt_mass, sizeof(double) * np) || cudaMalloc(&m->bt_cdf, sizeof(double) * np * nt))
+    m->bt_tab = nullptr;
+    m->g.bt_on = 0;
+    m->part_gen += 1;
+    m->drop_graph();   // the captured sweep holds the old parameters
+    if (cudaMalloc(&m->bt_mass, sizeof(double) * np) || cudaMalloc(&m->bt_cdf, sizeof(double) * np * nt) ||
+        cudaMalloc(&m->bt_tab, sizeof(float) * np * nt))
         return CMH_ERR_OOM;
     CK(cudaMemcpy(m->bt_mass, mass.data(), sizeof(double) * np, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(m->bt_cdf, cdf.data(), sizeof(double) * np * nt, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->bt_tab, tab, sizeof(float) * np * nt, cudaMemcpyHostToDevice));
     Geo& g = m->g;
     g.bt_on = 1;
     g.bt_nx = nx;
@@ -962,8 +977,12 @@ extern "C" int cmh_set_birth_table(cmh_model* m, const float* tab, int32_t nx, i
     g.bt_hy = m->p.W / (double)ny;
     g.bt_dt = m->p.T / (double)nt;
     g.bt_pixarea = g.bt_hx * g.bt_hy;
+    g.bt_ihx = 1.0 / g.bt_hx;
+    g.bt_ihy = 1.0 / g.bt_hy;
+    g.bt_idt = 1.0 / g.bt_dt;
     m->d.bt_mass = m->bt_mass;
     m->d.bt_cdf = m->bt_cdf;
+    m->d.bt_tab = m->bt_tab;
     m->drop_graph();   // the captured sweep holds the old parameters
     return CMH_OK;
 }

@@ -55,6 +55,7 @@ struct Geo {
     // bt_nx x bt_ny pixels of [0,W)^2 and bt_nt time bins of [0,T)
     int bt_on, bt_nx, bt_ny, bt_nt;
     double bt_mix, bt_hx, bt_hy, bt_dt, bt_pixarea;
+    double bt_ihx, bt_ihy, bt_idt;   // 1 / bt_hx, 1 / bt_hy, 1 / bt_dt
 };
 
 // one event store (structure of arrays) with per-cell slices
@@ -92,6 +93,7 @@ struct Dev {
     const double* log_n;        // [ev_cap + 2] log(n) table, computed on the host
     const double* bt_mass;      // [pixel] table mass of each pixel (learned birth component)
     const double* bt_cdf;       // [pixel][bin] running sum of the pixel's weights / its mass
+    const float* bt_tab;        // [pixel][bin] the table's weights as given
 };
 
 // --------------------------------------------------------------------------
@@ -266,6 +268,10 @@ struct FlatList {
 };
 
 // host-side launchers (defined in the .cu files)
+// a model's geometry and device buffers (for the learned-proposal code)
+Geo cmh_model_geo(const cmh_model* m);
+Dev cmh_model_dev(const cmh_model* m);
+
 // raise a kernel's dynamic shared-memory limit to at least `bytes`, never
 // lowering it (the attribute is shared by every model of the process)
 cudaError_t raise_smem_limit(const void* func, size_t bytes);

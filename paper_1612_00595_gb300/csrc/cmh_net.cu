@@ -1,0 +1,707 @@
+// Learned birth proposal: a small 1-D convolutional network that maps a tile
+// of station windows to a density over the tile's pixels and the event time,
+// trained on windows simulated from the model's own generative story, and
+// turned into a birth table for cmh_set_birth_table.
+//
+// Network (one example = 8 x 8 stations of a tile x 256 samples):
+//   input  X0[t][s] = log1p(s_t^2) of station s (64 channels) at sample t
+//   4 x conv1d (64 -> 64 channels, kernel 5, stride 2, padding 2) + ReLU:
+//          256 -> 128 -> 64 -> 32 -> 16 samples
+//   FC 1024 -> 512 + ReLU, FC 512 -> 4101 outputs:
+//          4096 pixel logits (64 x 64 pixels of the tile), 1 "no event" logit,
+//          mean and log sd of the event time (relative to the window start)
+//          and of the magnitude.
+// Loss: cross-entropy over the 4097 classes, Gaussian negative log-likelihood
+// of time and magnitude for windows that hold an event; AdamW.
+//
+// Every matrix product runs on the tensor cores in BF16 with FP32
+// accumulation (mma.sync m16n8k16; a convolution is an im2col product);
+// activations and gradients are kept in FP32, their BF16 copies feed the
+// products, and the parameters have FP32 masters with BF16 copies.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "chromh.h"
+#include "cmh_common.cuh"
+
+namespace cmh {
+
+namespace {
+
+constexpr int kNS = 64;        // stations per tile (8 x 8), the first layer's channels
+constexpr int kNL = 256;       // samples per window
+constexpr int kC = 64;         // channels of every convolution
+constexpr int kKW = 5;         // kernel width
+constexpr int kKC = kC * kKW;  // 320: im2col width
+constexpr int kNPix = 4096;    // 64 x 64 pixels of a tile
+constexpr int kNOut = kNPix + 1 + 4;
+constexpr int kF1In = 16 * kC; // 1024
+constexpr int kF1Out = 512;
+constexpr double kTile = 800.0;   // km, side of a tile (8 stations at 100 km)
+constexpr double kPix = kTile / 64.0;
+// origin times of simulated events, seconds from the window start: from
+// kTMin to the window's end (kTMax at 10 Hz, the prior the output is
+// initialised at)
+constexpr double kTMin = -15.0, kTMax = 25.6;
+
+// parameter layout (floats): conv l (W [64][320], b [64]) x 4, F1 [512][1024], fb1, F2 [4101][512], fb2
+constexpr long long kConvW = (long long)kC * kKC, kConvP = kConvW + kC;
+constexpr long long kOffF1 = 4 * kConvP, kOffFb1 = kOffF1 + (long long)kF1Out * kF1In;
+constexpr long long kOffF2 = kOffFb1 + kF1Out, kOffFb2 = kOffF2 + (long long)kNOut * kF1Out;
+constexpr long long kNParam = kOffFb2 + kNOut;
+
+// ---------------------------------------------------------------------------
+// C[M,N] = op(A)[M,K] op(B)[K,N] (+ C) (+ bias[n]) (ReLU), BF16 in, FP32 out.
+// A(m,k) = TA ? A[k*lda+m] : A[m*lda+k];  B(k,n) = TB ? B[n*ldb+k] : B[k*ldb+n].
+// 64 x 64 tiles, 4 warps of 32 x 32, K in steps of 32, mma m16n8k16.
+// ---------------------------------------------------------------------------
+constexpr int GB = 64, GK = 32, GP = GK + 8;
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(128) gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, int lda,
+                                                 const __nv_bfloat16* B, int ldb, float* C, int ldc,
+                                                 const float* bias, int relu, int accumulate,
+                                                 __nv_bfloat16* Cb) {
+    __shared__ __align__(16) __nv_bfloat16 As[GB][GP];
+    __shared__ __align__(16) __nv_bfloat16 Bs[GB][GP];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int m0 = blockIdx.y * GB, n0 = blockIdx.x * GB;
+    const int grp = lane >> 2, tig = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+    const __nv_bfloat16 zero = __float2bfloat16(0.f);
+    for (int k0 = 0; k0 < K; k0 += GK) {
+        for (int e = tid; e < GB * GK; e += 128) {
+            // A tile: As[m][k]; B tile stored transposed: Bs[n][k]
+            int r, c;
+            if (TA) { c = e / GB; r = e % GB; } else { r = e / GK; c = e % GK; }
+            const int gm = m0 + r, gk = k0 + c;
+            As[r][c] = (gm < M && gk < K) ? (TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk]) : zero;
+            if (TB) { r = e / GK; c = e % GK; } else { c = e / GB; r = e % GB; }
+            const int gn = n0 + r, gk2 = k0 + c;
+            Bs[r][c] = (gn < N && gk2 < K) ? (TB ? B[(long long)gn * ldb + gk2] : B[(long long)gk2 * ldb + gn]) : zero;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; kk += 16) {
+            unsigned a[2][4], b[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r0 = wm + i * 16 + grp;
+                a[i][0] = *reinterpret_cast<const unsigned*>(&As[r0][kk + tig * 2]);
+                a[i][1] = *reinterpret_cast<const unsigned*>(&As[r0 + 8][kk + tig * 2]);
+                a[i][2] = *reinterpret_cast<const unsigned*>(&As[r0][kk + tig * 2 + 8]);
+                a[i][3] = *reinterpret_cast<const unsigned*>(&As[r0 + 8][kk + tig * 2 + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int nn = wn + j * 8 + grp;
+                b[j][0] = *reinterpret_cast<const unsigned*>(&Bs[nn][kk + tig * 2]);
+                b[j][1] = *reinterpret_cast<const unsigned*>(&Bs[nn][kk + tig * 2 + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                        "{%8,%9}, {%0,%1,%2,%3};"
+                        : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+                        : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int m = m0 + wm + i * 16 + grp + (r >= 2 ? 8 : 0);
+                const int n = n0 + wn + j * 8 + tig * 2 + (r & 1);
+                if (m >= M || n >= N) continue;
+                float v = acc[i][j][r];
+                const long long o = (long long)m * ldc + n;
+                if (accumulate) v += C[o];
+                if (bias) v += bias[n];
+                if (relu) v = v > 0.f ? v : 0.f;
+                C[o] = v;
+                if (Cb) Cb[o] = __float2bfloat16(v);
+            }
+}
+
+// im2col of a [B][Lin][64] activation (BF16): row (b, t) of [B*Lout][320]
+// holds x[b][2t - 2 + k][c] at column k * 64 + c (0 outside the window)
+__global__ void im2col(const __nv_bfloat16* X, int Bn, int Lin, int Lout, __nv_bfloat16* A) {
+    const long long n = (long long)Bn * Lout * kKC;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int col = (int)(i % kKC);
+        const long long row = i / kKC;
+        const int t = (int)(row % Lout), b = (int)(row / Lout);
+        const int k = col / kC, c = col % kC, s = 2 * t - 2 + k;
+        A[i] = (s >= 0 && s < Lin) ? X[((long long)b * Lin + s) * kC + c] : __float2bfloat16(0.f);
+    }
+}
+
+// the adjoint of im2col: dX[b][s][c] = sum over (t, k) with 2t - 2 + k = s of dA[(b,t)][k*64+c]
+__global__ void col2im(const float* dA, int Bn, int Lin, int Lout, float* dX) {
+    const long long n = (long long)Bn * Lin * kC;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % kC);
+        const int s = (int)((i / kC) % Lin), b = (int)(i / ((long long)kC * Lin));
+        float v = 0.f;
+        for (int k = 0; k < kKW; ++k) {
+            const int t2 = s + 2 - k;   // = 2t
+            if (t2 < 0 || (t2 & 1)) continue;
+            const int t = t2 >> 1;
+            if (t >= Lout) continue;
+            v += dA[((long long)b * Lout + t) * kKC + k * kC + c];
+        }
+        dX[i] = v;
+    }
+}
+
+// dZ = dY (where the ReLU output is positive), and its BF16 copy
+__global__ void relu_back(const float* dY, const float* Y, long long n, float* dZ, __nv_bfloat16* dZb) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float v = Y[i] > 0.f ? dY[i] : 0.f;
+        dZ[i] = v;
+        dZb[i] = __float2bfloat16(v);
+    }
+}
+
+__global__ void to_bf16(const float* x, long long n, __nv_bfloat16* y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = __float2bfloat16(x[i]);
+}
+
+// column sums of a [M][N] matrix (bias gradients), one thread per column
+__global__ void col_sums(const float* D, int M, int N, float* out) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.f;
+    for (int m = 0; m < M; ++m) s += D[(long long)m * N + n];
+    out[n] = s;
+}
+
+__device__ __forceinline__ float block_sum(float v, float* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    return t;
+}
+
+__device__ __forceinline__ float block_max(float v, float* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = -INFINITY;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+    return t;
+}
+
+// one block per example: cross-entropy over the 4097 classes and the
+// Gaussian NLL of time and magnitude (events only); gradients of the mean
+// loss into dO, the example's loss into loss[b]
+__global__ void __launch_bounds__(256) loss_grad(const float* O, const int* label, const float* tl, const float* ml,
+                                                 int Bn, float* dO, float* loss) {
+    __shared__ float red[32];
+    const int b = blockIdx.x;
+    const float* o = O + (long long)b * kNOut;
+    float* g = dO + (long long)b * kNOut;
+    const int lab = label[b];
+    float mx = -INFINITY;
+    for (int i = threadIdx.x; i <= kNPix; i += blockDim.x) mx = fmaxf(mx, o[i]);
+    mx = block_max(mx, red);
+    float se = 0.f;
+    for (int i = threadIdx.x; i <= kNPix; i += blockDim.x) se += expf(o[i] - mx);
+    se = block_sum(se, red);
+    const float lse = mx + logf(se), inv = 1.f / (float)Bn;
+    for (int i = threadIdx.x; i <= kNPix; i += blockDim.x) g[i] = (expf(o[i] - mx) / se - (i == lab ? 1.f : 0.f)) * inv;
+    if (threadIdx.x == 0) {
+        float l = lse - o[lab];
+        float gt[4] = {0.f, 0.f, 0.f, 0.f};
+        if (lab < kNPix) {
+            // NLL of y under N(mu, e^{2 ls}): ls + (y - mu)^2 / (2 e^{2 ls}), ls clamped
+            const float y2[2] = {tl[b], ml[b]};
+            for (int q = 0; q < 2; ++q) {
+                const float mu = o[kNPix + 1 + 2 * q], ls = fminf(fmaxf(o[kNPix + 2 + 2 * q], -4.f), 6.f);
+                const float iv = expf(-2.f * ls), r = y2[q] - mu;
+                l += ls + 0.5f * r * r * iv;
+                gt[2 * q] = -r * iv * inv;
+                const bool in = o[kNPix + 2 + 2 * q] > -4.f && o[kNPix + 2 + 2 * q] < 6.f;
+                gt[2 * q + 1] = in ? (1.f - r * r * iv) * inv : 0.f;
+            }
+        }
+        for (int q = 0; q < 4; ++q) g[kNPix + 1 + q] = gt[q];
+        loss[b] = l;
+    }
+}
+
+__global__ void adamw(float* p, const float* g, float* m1, float* m2, long long n, float lr, float b1, float b2,
+                      float c1, float c2, float eps, float wd, __nv_bfloat16* pb) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float a = b1 * m1[i] + (1.f - b1) * gi, v = b2 * m2[i] + (1.f - b2) * gi * gi;
+        m1[i] = a;
+        m2[i] = v;
+        const float q = p[i] - lr * ((a / c1) / (sqrtf(v / c2) + eps) + wd * p[i]);
+        p[i] = q;
+        pb[i] = __float2bfloat16(q);
+    }
+}
+
+// ---- simulated training windows (the model's generative story) -------------
+// Example b of batch `step`: 8 x 8 stations jittered around the centres of
+// 100 km cells of an 800 km tile; with probability 1/2 one event, uniform in
+// the tile, magnitude 2 + Exp(1), origin time uniform in [-15, 25.6) s of the
+// window; 256 samples at f per station: s = sqrt(noise + sum of arrival
+// variances) * N(0, 1); features log1p(s^2).  Labels: the event's pixel (or
+// 4096 for none), its time relative to the window start, its magnitude.
+__global__ void __launch_bounds__(256) gen_windows(Geo g, unsigned long long seed, unsigned long long step, int Bn,
+                                                   __nv_bfloat16* X, int* label, float* tl, float* ml) {
+    const int b = blockIdx.x;
+    __shared__ float sx[kNS], sy[kNS];
+    __shared__ double ev[4];
+    __shared__ int has;
+    unsigned long long c[4];
+    if (threadIdx.x < kNS) {
+        c[0] = step; c[1] = (unsigned long long)b; c[2] = (unsigned long long)threadIdx.x; c[3] = 7ULL;
+        philox4x64(c, seed, 3ULL);
+        const int r = threadIdx.x / 8, q = threadIdx.x % 8;
+        sx[threadIdx.x] = (float)((q + 0.5) * 100.0 + (u01(c[0]) * 2.0 - 1.0) * 25.0);
+        sy[threadIdx.x] = (float)((r + 0.5) * 100.0 + (u01(c[1]) * 2.0 - 1.0) * 25.0);
+    }
+    if (threadIdx.x == 0) {
+        c[0] = step; c[1] = (unsigned long long)b; c[2] = 1000ULL; c[3] = 8ULL;
+        philox4x64(c, seed, 3ULL);
+        has = u01(c[0]) < 0.5;
+        ev[0] = u01(c[1]) * kTile;
+        ev[1] = u01(c[2]) * kTile;
+        ev[2] = kTMin + u01(c[3]) * (kNL / g.f_hz - kTMin);
+        c[0] = step; c[1] = (unsigned long long)b; c[2] = 1001ULL; c[3] = 8ULL;
+        philox4x64(c, seed, 3ULL);
+        ev[3] = 2.0 - log(u01o(c[0]));
+        if (has) {
+            const int px = min(63, (int)(ev[0] / kPix)), py = min(63, (int)(ev[1] / kPix));
+            label[b] = py * 64 + px;
+            tl[b] = (float)ev[2];
+            ml[b] = (float)ev[3];
+        } else {
+            label[b] = kNPix;
+            tl[b] = 0.f;
+            ml[b] = 0.f;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kNS * kNL; i += blockDim.x) {
+        const int s = i % kNS, t = i / kNS;
+        double V = g.noise_var;
+        if (has) {
+            const double dx = ev[0] - sx[s], dy = ev[1] - sy[s], dist = sqrt(dx * dx + dy * dy);
+            if (dist < g.R_max) {
+                const double u = t / g.f_hz - (ev[2] + dist / g.v);
+                if (u >= 0.0 && u < (double)g.n_w / g.f_hz) {
+                    const double a = exp(g.alpha * ev[3] - g.beta_att * dist - u / g.tau);
+                    V += a * a;
+                }
+            }
+        }
+        unsigned long long w[4] = {step, (unsigned long long)b, (unsigned long long)i, 9ULL};
+        philox4x64(w, seed, 3ULL);
+        const double z = sqrt(-2.0 * log(u01o(w[0]))) * cos(6.283185307179586 * u01(w[1]));
+        const double sig = sqrt(V) * z;
+        X[((long long)b * kNL + t) * kNS + s] = __float2bfloat16((float)log1p(sig * sig));
+    }
+}
+
+// features of the windows of a tile from a model's signals (float32 rows):
+// example b starts at sample k0 + b * hop; station s of the tile is row st[s]
+__global__ void gather_windows(const float* sig, long long pitch, long long n_samp, const int* st, long long k0,
+                               int hop, int Bn, __nv_bfloat16* X) {
+    const long long n = (long long)Bn * kNL * kNS;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(i % kNS), t = (int)((i / kNS) % kNL), b = (int)(i / ((long long)kNS * kNL));
+        const long long k = k0 + (long long)b * hop + t;
+        float v = 0.f;
+        if (k < n_samp) {
+            const float x = sig[(long long)st[s] * pitch + k];
+            v = log1pf(x * x);
+        }
+        X[i] = __float2bfloat16(v);
+    }
+}
+
+// add the network's density of the windows of a tile to a birth table
+// (pixels of the world grid, nt bins over [0, T)): pixel mass (softmax
+// without the "no event" class) times the time Gaussian's mass in each bin
+__global__ void __launch_bounds__(256) accumulate_table(const float* O, int Bn, double t0, double hop_s, int ox,
+                                                        int oy, int nx, int ny, int nt, double dt, float* tab) {
+    __shared__ float red[32];
+    const int b = blockIdx.x;
+    const float* o = O + (long long)b * kNOut;
+    float mx = -INFINITY;
+    for (int i = threadIdx.x; i <= kNPix; i += blockDim.x) mx = fmaxf(mx, o[i]);
+    mx = block_max(mx, red);
+    float se = 0.f;
+    for (int i = threadIdx.x; i <= kNPix; i += blockDim.x) se += expf(o[i] - mx);
+    se = block_sum(se, red);
+    const double mu = t0 + b * hop_s + o[kNPix + 1];
+    const double sd = exp(fminf(fmaxf(o[kNPix + 2], -4.f), 6.f)) + 1.0;
+    const int b0 = max(0, (int)floor((mu - 4.0 * sd) / dt)), b1 = min(nt - 1, (int)floor((mu + 4.0 * sd) / dt));
+    for (int i = threadIdx.x; i < kNPix; i += blockDim.x) {
+        const float p = expf(o[i] - mx) / se;
+        if (p < 1e-5f) continue;
+        const int gx = ox + (i % 64), gy = oy + (i / 64);
+        if (gx < 0 || gy < 0 || gx >= nx || gy >= ny) continue;
+        float* row = tab + ((long long)gy * nx + gx) * nt;
+        for (int q = b0; q <= b1; ++q) {
+            const double a = (q * dt - mu) / (sd * 1.4142135623730951), z = ((q + 1) * dt - mu) / (sd * 1.4142135623730951);
+            atomicAdd(row + q, p * (float)(0.5 * (erf(z) - erf(a))));
+        }
+    }
+}
+
+inline int blocks_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 16); }
+
+}  // namespace
+}  // namespace cmh
+
+using namespace cmh;
+
+struct cmh_net {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int bmax = 0;
+    unsigned long long seed = 0, steps = 0;
+    float *p = nullptr, *gr = nullptr, *m1 = nullptr, *m2 = nullptr;
+    __nv_bfloat16* pb = nullptr;
+    // activations (FP32 and BF16 copies) and gradients
+    __nv_bfloat16 *x0 = nullptr, *col = nullptr;
+    float *y[4] = {nullptr}, *h = nullptr, *o = nullptr, *dO = nullptr, *dh = nullptr, *dcol = nullptr;
+    __nv_bfloat16 *yb[4] = {nullptr}, *hb = nullptr, *dOb = nullptr, *dhb = nullptr, *dyb = nullptr;
+    float *dy = nullptr, *dx = nullptr, *loss = nullptr, *tl = nullptr, *ml = nullptr;
+    int* label = nullptr;
+    std::vector<void*> allocs;
+
+    template <typename T>
+    bool alloc(T** q, size_t n) {
+        if (cudaMalloc((void**)q, sizeof(T) * std::max<size_t>(n, 1)) != cudaSuccess) return false;
+        allocs.push_back((void*)*q);
+        return true;
+    }
+    ~cmh_net() {
+        if (stream) cudaStreamSynchronize(stream);
+        for (void* q : allocs) cudaFree(q);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+template <bool TA, bool TB>
+cudaError_t gemm(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B,
+                 int ldb, float* C, int ldc, const float* bias, int relu, int acc, __nv_bfloat16* Cb) {
+    dim3 grid((N + GB - 1) / GB, (M + GB - 1) / GB);
+    gemm_bf16<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, acc, Cb);
+    return cudaGetLastError();
+}
+
+const int kLin[5] = {256, 128, 64, 32, 16};
+
+// forward of a batch whose features are in n->x0; outputs in n->o
+cudaError_t forward(cmh_net* n, int Bn) {
+    cudaStream_t s = n->stream;
+    cudaError_t e = cudaSuccess;
+    const __nv_bfloat16* in = n->x0;
+    for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+        const int Lin = kLin[l], Lout = kLin[l + 1];
+        const long long rows = (long long)Bn * Lout;
+        im2col<<<blocks_for(rows * kKC), 256, 0, s>>>(in, Bn, Lin, Lout, n->col);
+        e = gemm<false, true>(s, (int)rows, kC, kKC, n->col, kKC, n->pb + l * kConvP, kKC, n->y[l], kC,
+                              n->p + l * kConvP + kConvW, 1, 0, n->yb[l]);
+        in = n->yb[l];
+    }
+    if (e) return e;
+    // FC1: [B][1024] x F1^T -> [B][512]
+    if ((e = gemm<false, true>(s, Bn, kF1Out, kF1In, n->yb[3], kF1In, n->pb + kOffF1, kF1In, n->h, kF1Out,
+                               n->p + kOffFb1, 1, 0, n->hb)))
+        return e;
+    return gemm<false, true>(s, Bn, kNOut, kF1Out, n->hb, kF1Out, n->pb + kOffF2, kF1Out, n->o, kNOut,
+                             n->p + kOffFb2, 0, 0, nullptr);
+}
+
+// loss and gradients of a batch (labels in n->label / tl / ml) into n->gr
+cudaError_t backward(cmh_net* n, int Bn) {
+    cudaStream_t s = n->stream;
+    cudaError_t e;
+    loss_grad<<<Bn, 256, 0, s>>>(n->o, n->label, n->tl, n->ml, Bn, n->dO, n->loss);
+    to_bf16<<<blocks_for((long long)Bn * kNOut), 256, 0, s>>>(n->dO, (long long)Bn * kNOut, n->dOb);
+    // FC2: dF2 = dO^T h, dfb2 = colsum dO, dh = dO F2
+    if ((e = gemm<true, false>(s, kNOut, kF1Out, Bn, n->dOb, kNOut, n->hb, kF1Out, n->gr + kOffF2, kF1Out, nullptr, 0,
+                               0, nullptr)))
+        return e;
+    col_sums<<<(kNOut + 255) / 256, 256, 0, s>>>(n->dO, Bn, kNOut, n->gr + kOffFb2);
+    if ((e = gemm<false, false>(s, Bn, kF1Out, kNOut, n->dOb, kNOut, n->pb + kOffF2, kF1Out, n->dh, kF1Out, nullptr,
+                                0, 0, nullptr)))
+        return e;
+    relu_back<<<blocks_for((long long)Bn * kF1Out), 256, 0, s>>>(n->dh, n->h, (long long)Bn * kF1Out, n->dh, n->dhb);
+    // FC1: dF1 = dh^T x4, dfb1, dx4 = dh F1 (into dy as [B*16][64])
+    if ((e = gemm<true, false>(s, kF1Out, kF1In, Bn, n->dhb, kF1Out, n->yb[3], kF1In, n->gr + kOffF1, kF1In, nullptr,
+                               0, 0, nullptr)))
+        return e;
+    col_sums<<<(kF1Out + 255) / 256, 256, 0, s>>>(n->dh, Bn, kF1Out, n->gr + kOffFb1);
+    if ((e = gemm<false, false>(s, Bn, kF1In, kF1Out, n->dhb, kF1Out, n->pb + kOffF1, kF1In, n->dy, kF1In, nullptr, 0,
+                                0, nullptr)))
+        return e;
+    for (int l = 3; l >= 0; --l) {
+        const int Lin = kLin[l], Lout = kLin[l + 1];
+        const long long rows = (long long)Bn * Lout;
+        // through the ReLU of layer l
+        relu_back<<<blocks_for(rows * kC), 256, 0, s>>>(n->dy, n->y[l], rows * kC, n->dy, n->dyb);
+        // recompute this layer's im2col input
+        const __nv_bfloat16* in = l == 0 ? n->x0 : n->yb[l - 1];
+        im2col<<<blocks_for(rows * kKC), 256, 0, s>>>(in, Bn, Lin, Lout, n->col);
+        // dW = dy^T col, db = colsum dy
+        if ((e = gemm<true, false>(s, kC, kKC, (int)rows, n->dyb, kC, n->col, kKC, n->gr + l * kConvP, kKC, nullptr, 0,
+                                   0, nullptr)))
+            return e;
+        col_sums<<<1, 64, 0, s>>>(n->dy, (int)rows, kC, n->gr + l * kConvP + kConvW);
+        if (l == 0) break;
+        // dcol = dy W, dx = col2im(dcol) (the previous layer's output gradient)
+        if ((e = gemm<false, false>(s, (int)rows, kKC, kC, n->dyb, kC, n->pb + l * kConvP, kKC, n->dcol, kKC, nullptr,
+                                    0, 0, nullptr)))
+            return e;
+        col2im<<<blocks_for((long long)Bn * Lin * kC), 256, 0, s>>>(n->dcol, Bn, Lin, Lout, n->dy);
+    }
+    return cudaGetLastError();
+}
+
+int net_err(cudaError_t e) {
+    if (e == cudaSuccess) return CMH_OK;
+    if (e == cudaErrorMemoryAllocation) return CMH_ERR_OOM;
+    return CMH_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" int64_t cmh_net_param_count(void) { return kNParam; }
+
+extern "C" int cmh_net_create(int32_t max_batch, uint64_t seed, void* cuda_stream, cmh_net** out) {
+    if (!out || max_batch < 1 || max_batch > 4096) return CMH_ERR_ARG;
+    *out = nullptr;
+    (void)cudaGetLastError();
+    cmh_net* n = new (std::nothrow) cmh_net;
+    if (!n) return CMH_ERR_OOM;
+    n->bmax = max_batch;
+    n->seed = seed;
+    n->stream = (cudaStream_t)cuda_stream;
+    if (!n->stream) {
+        if (cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete n;
+            return CMH_ERR_CUDA;
+        }
+        n->own_stream = true;
+    }
+    const long long B = max_batch;
+    bool ok = n->alloc(&n->p, kNParam) && n->alloc(&n->gr, kNParam) && n->alloc(&n->m1, kNParam) &&
+              n->alloc(&n->m2, kNParam) && n->alloc(&n->pb, kNParam) && n->alloc(&n->x0, B * kNL * kNS) &&
+              n->alloc(&n->col, B * 128 * kKC) && n->alloc(&n->h, B * kF1Out) && n->alloc(&n->hb, B * kF1Out) &&
+              n->alloc(&n->o, B * kNOut) && n->alloc(&n->dO, B * kNOut) && n->alloc(&n->dOb, B * kNOut) &&
+              n->alloc(&n->dh, B * kF1Out) && n->alloc(&n->dhb, B * kF1Out) && n->alloc(&n->dcol, B * 128 * kKC) &&
+              n->alloc(&n->dy, B * 128 * kC) && n->alloc(&n->dyb, B * 128 * kC) && n->alloc(&n->dx, B * 256 * kC) &&
+              n->alloc(&n->loss, B) && n->alloc(&n->tl, B) && n->alloc(&n->ml, B) && n->alloc(&n->label, B);
+    for (int l = 0; l < 4 && ok; ++l) ok = n->alloc(&n->y[l], B * kLin[l + 1] * kC) && n->alloc(&n->yb[l], B * kLin[l + 1] * kC);
+    if (!ok) {
+        delete n;
+        return CMH_ERR_OOM;
+    }
+    // He-style initialisation on the host (seeded), biases 0
+    std::vector<float> hp(kNParam, 0.f);
+    unsigned long long st = seed * 0x9E3779B97F4A7C15ULL + 1;
+    auto unif = [&]() {   // splitmix64
+        st += 0x9E3779B97F4A7C15ULL;
+        unsigned long long z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    auto fill = [&](long long off, long long cnt, int fan_in) {
+        const double a = std::sqrt(6.0 / fan_in);
+        for (long long i = 0; i < cnt; ++i) hp[off + i] = (float)((2.0 * unif() - 1.0) * a);
+    };
+    for (int l = 0; l < 4; ++l) fill(l * kConvP, kConvW, kKC);
+    fill(kOffF1, (long long)kF1Out * kF1In, kF1In);
+    fill(kOffF2, (long long)kNOut * kF1Out, kF1Out);
+    // output layer: small weights and biases at the training prior, so the
+    // first steps start from the uninformed loss (even odds of "no event"
+    // against a uniform pixel; time and magnitude at their prior mean and
+    // spread) instead of from an NLL of thousands that kills the ReLUs
+    for (long long i = 0; i < (long long)kNOut * kF1Out; ++i) hp[kOffF2 + i] *= 0.05f;
+    hp[kOffFb2 + kNPix] = (float)std::log((double)kNPix);
+    hp[kOffFb2 + kNPix + 1] = (float)(0.5 * (kTMin + kTMax));
+    hp[kOffFb2 + kNPix + 2] = (float)std::log((kTMax - kTMin) / std::sqrt(12.0));
+    hp[kOffFb2 + kNPix + 3] = 3.f;
+    hp[kOffFb2 + kNPix + 4] = 0.f;
+    cudaError_t e = cudaMemcpy(n->p, hp.data(), sizeof(float) * kNParam, cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemset(n->m1, 0, sizeof(float) * kNParam);
+    if (!e) e = cudaMemset(n->m2, 0, sizeof(float) * kNParam);
+    if (!e) {
+        to_bf16<<<blocks_for(kNParam), 256, 0, n->stream>>>(n->p, kNParam, n->pb);
+        e = cudaStreamSynchronize(n->stream);
+    }
+    if (e) {
+        delete n;
+        return net_err(e);
+    }
+    *out = n;
+    return CMH_OK;
+}
+
+extern "C" void cmh_net_destroy(cmh_net* n) { delete n; }
+
+extern "C" int cmh_net_get_params(cmh_net* n, float* out) {
+    if (!n || !out) return CMH_ERR_ARG;
+    return net_err(cudaMemcpy(out, n->p, sizeof(float) * kNParam, cudaMemcpyDeviceToHost));
+}
+
+extern "C" int cmh_net_set_params(cmh_net* n, const float* in) {
+    if (!n || !in) return CMH_ERR_ARG;
+    cudaError_t e = cudaMemcpy(n->p, in, sizeof(float) * kNParam, cudaMemcpyHostToDevice);
+    if (e) return net_err(e);
+    to_bf16<<<blocks_for(kNParam), 256, 0, n->stream>>>(n->p, kNParam, n->pb);
+    return net_err(cudaStreamSynchronize(n->stream));
+}
+
+extern "C" int cmh_net_forward(cmh_net* n, const float* features, int32_t batch, float* out) {
+    if (!n || !features || !out || batch < 1 || batch > n->bmax) return CMH_ERR_ARG;
+    (void)cudaGetLastError();
+    const long long nf = (long long)batch * kNL * kNS;
+    std::vector<__nv_bfloat16> hb(nf);
+    for (long long i = 0; i < nf; ++i) hb[i] = __float2bfloat16(features[i]);
+    cudaError_t e = cudaMemcpyAsync(n->x0, hb.data(), sizeof(__nv_bfloat16) * nf, cudaMemcpyHostToDevice, n->stream);
+    if (!e) e = forward(n, batch);
+    if (!e) e = cudaMemcpyAsync(out, n->o, sizeof(float) * batch * kNOut, cudaMemcpyDeviceToHost, n->stream);
+    if (!e) e = cudaStreamSynchronize(n->stream);
+    return net_err(e);
+}
+
+extern "C" int cmh_net_gradients(cmh_net* n, const float* features, const int32_t* label, const float* t_label,
+                                 const float* m_label, int32_t batch, float* grads, double* loss) {
+    if (!n || !features || !label || !t_label || !m_label || !grads || batch < 1 || batch > n->bmax)
+        return CMH_ERR_ARG;
+    for (int b = 0; b < batch; ++b)
+        if (label[b] < 0 || label[b] > kNPix) return CMH_ERR_ARG;
+    (void)cudaGetLastError();
+    const long long nf = (long long)batch * kNL * kNS;
+    std::vector<__nv_bfloat16> hb(nf);
+    for (long long i = 0; i < nf; ++i) hb[i] = __float2bfloat16(features[i]);
+    cudaStream_t s = n->stream;
+    cudaError_t e = cudaMemcpyAsync(n->x0, hb.data(), sizeof(__nv_bfloat16) * nf, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(n->label, label, sizeof(int) * batch, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(n->tl, t_label, sizeof(float) * batch, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(n->ml, m_label, sizeof(float) * batch, cudaMemcpyHostToDevice, s);
+    if (!e) e = forward(n, batch);
+    if (!e) e = backward(n, batch);
+    std::vector<float> lv(batch);
+    if (!e) e = cudaMemcpyAsync(grads, n->gr, sizeof(float) * kNParam, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(lv.data(), n->loss, sizeof(float) * batch, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return net_err(e);
+    if (loss) {
+        double t = 0.0;
+        for (float v : lv) t += v;
+        *loss = t / batch;
+    }
+    return CMH_OK;
+}
+
+extern "C" int cmh_net_train(cmh_net* n, const cmh_model* geometry, int32_t steps, int32_t batch, double lr,
+                             double* loss_out) {
+    if (!n || !geometry || steps < 0 || batch < 1 || batch > n->bmax || !(lr > 0.0)) return CMH_ERR_ARG;
+    (void)cudaGetLastError();
+    const Geo g = cmh_model_geo(geometry);
+    cudaStream_t s = n->stream;
+    const float b1 = 0.9f, b2 = 0.999f;
+    double last = 0.0;
+    for (int it = 0; it < steps; ++it) {
+        const unsigned long long step = ++n->steps;
+        gen_windows<<<batch, 256, 0, s>>>(g, n->seed, step, batch, n->x0, n->label, n->tl, n->ml);
+        cudaError_t e = forward(n, batch);
+        if (!e) e = backward(n, batch);
+        if (e) return net_err(e);
+        const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+        adamw<<<blocks_for(kNParam), 256, 0, s>>>(n->p, n->gr, n->m1, n->m2, kNParam, (float)lr, b1, b2, c1, c2,
+                                                  1e-8f, 1e-4f, n->pb);
+        if (it == steps - 1 && loss_out) {
+            std::vector<float> lv(batch);
+            e = cudaMemcpyAsync(lv.data(), n->loss, sizeof(float) * batch, cudaMemcpyDeviceToHost, s);
+            if (!e) e = cudaStreamSynchronize(s);
+            if (e) return net_err(e);
+            double t = 0.0;
+            for (float v : lv) t += v;
+            last = t / batch;
+        }
+    }
+    if (loss_out) *loss_out = last;
+    return net_err(cudaStreamSynchronize(s));
+}
+
+extern "C" int cmh_net_birth_table(cmh_net* n, cmh_model* m, const int32_t* tiles, const double* tile_origin,
+                                   int32_t n_tiles, int32_t nx, int32_t ny, int32_t nt, double hop_s, float* table) {
+    if (!n || !m || !tiles || !tile_origin || n_tiles < 1 || nx < 1 || ny < 1 || nt < 1 || !table || !(hop_s > 0.0))
+        return CMH_ERR_ARG;
+    (void)cudaGetLastError();
+    const Geo g = cmh_model_geo(m);
+    const Dev d = cmh_model_dev(m);
+    if (!g.f32) return CMH_ERR_ARG;
+    for (int i = 0; i < n_tiles * kNS; ++i)
+        if (tiles[i] < 0 || tiles[i] >= g.n_st) return CMH_ERR_ARG;
+    cudaStream_t s = n->stream;
+    const int hop = std::max(1, (int)std::lround(hop_s * g.f_hz));
+    const long long n_win = std::max<long long>(1, (g.n_samp + hop - 1) / hop);
+    int* dst = nullptr;
+    float* dtab = nullptr;
+    cudaError_t e = cudaMalloc(&dst, sizeof(int) * kNS);
+    if (!e) e = cudaMalloc(&dtab, sizeof(float) * (size_t)nx * ny * nt);
+    if (!e) e = cudaMemsetAsync(dtab, 0, sizeof(float) * (size_t)nx * ny * nt, s);
+    const double dt = g.T / nt;
+    for (int ti = 0; ti < n_tiles && !e; ++ti) {
+        e = cudaMemcpyAsync(dst, tiles + ti * kNS, sizeof(int) * kNS, cudaMemcpyHostToDevice, s);
+        const int ox = (int)std::lround(tile_origin[2 * ti] / (g.W / nx));
+        const int oy = (int)std::lround(tile_origin[2 * ti + 1] / (g.W / ny));
+        for (long long w0 = 0; w0 < n_win && !e; w0 += n->bmax) {
+            const int Bn = (int)std::min<long long>(n->bmax, n_win - w0);
+            gather_windows<<<blocks_for((long long)Bn * kNL * kNS), 256, 0, s>>>((const float*)d.sig, g.pitch, g.n_samp,
+                                                                                dst, w0 * hop, hop, Bn, n->x0);
+            e = forward(n, Bn);
+            if (!e) {
+                accumulate_table<<<Bn, 256, 0, s>>>(n->o, Bn, (double)(w0 * hop) / g.f_hz, hop / g.f_hz, ox, oy, nx, ny,
+                                                    nt, dt, dtab);
+                e = cudaGetLastError();
+            }
+        }
+    }
+    if (!e) e = cudaMemcpyAsync(table, dtab, sizeof(float) * (size_t)nx * ny * nt, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (dst) cudaFree(dst);
+    if (dtab) cudaFree(dtab);
+    return net_err(e);
+}

@@ -124,6 +124,8 @@ struct Sm {
     double bt_G;        // table mass inside the region (learned birth component)
     double lq_unif;     // lq of the uniform birth alone: log(Lambda area / W^2)
     double qu;          // density of the uniform birth in space-time: 1 / (area T)
+    double qmu;         // (1 - mix) qu: the uniform component's share of the mixture density
+    double bt_in;       // 1 / (pixel area x bt_G x bin width): table weight -> q_net
     int bt_np, bt_last; // pixel entries; last entry with mass
     int valid[2], idx[2], type[2], ncand[2], ntask[2], units[2], width[2];
     double thr[2];      // accept iff the log-likelihood change exceeds this (log u minus the other terms of log alpha)
@@ -300,22 +302,22 @@ __device__ __forceinline__ double bt_weight(const Geo& g, const Dev& d, const do
     return __dmul_rn(d.bt_mass[(long long)iy * g.bt_nx + ix], __ddiv_rn(__dmul_rn(ox, oy), g.bt_pixarea));
 }
 
-// lq at (x, y, t): log Lambda - log(W^2 T) - log[(1 - mix) / (area T) + mix q_net]
-__device__ __noinline__ double bt_lq(const Geo& g, const Dev& d, double G, double qu, double x, double y, double t) {
+// lq at (x, y, t): log Lambda - log(W^2 T) - log[(1 - mix) / (area T) + mix q_net],
+// q_net = table weight of (pixel, bin) / (pixel area x region mass x bin
+// width).  A density term of the float32 path: the pixel and bin come from
+// reciprocal products, the weight is the table's own float and the logarithm
+// is taken in float32 (error ~1e-7 against the float64 form); the sum into
+// log alpha stays float64.  The sampling itself (learned_birth) is exact.
+__device__ __forceinline__ double bt_lq(const Geo& g, const Dev& d, const Sm& S, double x, double y, double t) {
     double qn = 0.0;
-    if (G > 0.0) {
-        int ix = (int)floor(__ddiv_rn(x, g.bt_hx)), iy = (int)floor(__ddiv_rn(y, g.bt_hy));
-        int b = (int)floor(__ddiv_rn(t, g.bt_dt));
-        ix = ix > g.bt_nx - 1 ? g.bt_nx - 1 : ix;
-        iy = iy > g.bt_ny - 1 ? g.bt_ny - 1 : iy;
-        b = b > g.bt_nt - 1 ? g.bt_nt - 1 : b;
-        const long long q = (long long)iy * g.bt_nx + ix;
-        const double* c = d.bt_cdf + q * g.bt_nt;
-        const double share = __dsub_rn(c[b], b > 0 ? c[b - 1] : 0.0);
-        qn = __ddiv_rn(__dmul_rn(d.bt_mass[q], share), __dmul_rn(__dmul_rn(g.bt_pixarea, G), g.bt_dt));
+    if (S.bt_G > 0.0) {
+        int ix = (int)(x * g.bt_ihx), iy = (int)(y * g.bt_ihy), b = (int)(t * g.bt_idt);
+        ix = ix < 0 ? 0 : (ix > g.bt_nx - 1 ? g.bt_nx - 1 : ix);
+        iy = iy < 0 ? 0 : (iy > g.bt_ny - 1 ? g.bt_ny - 1 : iy);
+        b = b < 0 ? 0 : (b > g.bt_nt - 1 ? g.bt_nt - 1 : b);
+        qn = (double)__ldg(d.bt_tab + ((long long)iy * g.bt_nx + ix) * g.bt_nt + b) * S.bt_in;
     }
-    const double qm = __dadd_rn(__dmul_rn(__dsub_rn(1.0, g.bt_mix), qu), __dmul_rn(g.bt_mix, qn));
-    return __dsub_rn(g.lLWT, log(qm));
+    return g.lLWT - (double)logf((float)(S.qmu + g.bt_mix * qn));
 }
 
 // a birth from the learned component: pixel by its share of the region's
@@ -415,7 +417,7 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
                 valid = inside_exact(g, S.sx, S.sy, S.cell, c.x, c.y, c.t, c.m);
                 if (valid) to_rel(g, S.X0, S.Y0, c);
             }
-            if (valid) c.lq = g.bt_on ? bt_lq(g, d, S.bt_G, S.qu, c.x, c.y, c.t) : S.lq_unif;
+            if (valid) c.lq = g.bt_on ? bt_lq(g, d, S, c.x, c.y, c.t) : S.lq_unif;
         }
     }
     // candidate arrivals, lanes over blanket slots, compacted in slot order
@@ -765,33 +767,40 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
             const double area = __dmul_rn(__dsub_rn(S.rect[1], S.rect[0]), __dsub_rn(S.rect[3], S.rect[2]));
             S.qu = __ddiv_rn(1.0, __dmul_rn(area, g.T));
             S.lq_unif = __dsub_rn(g.lLWT, log(S.qu));
+            S.qmu = (1.0 - g.bt_mix) * S.qu;
             S.bt_G = 0.0;
+            S.bt_in = 0.0;
             S.bt_np = 0;
             S.bt_last = -1;
-            if (g.bt_on) {
-                // the region's pixels in (iy, ix) order with their running mass
-                int x0, x1, y0, y1;
-                bt_range(S.rect[0], S.rect[1], g.bt_hx, g.bt_nx, x0, x1);
-                bt_range(S.rect[2], S.rect[3], g.bt_hy, g.bt_ny, y0, y1);
+        }
+        if (g.bt_on) {
+            // the region's pixels in (iy, ix) order: masses in parallel, then
+            // their running sum in that order by one thread
+            int x0, x1, y0, y1;
+            bt_range(S.rect[0], S.rect[1], g.bt_hx, g.bt_nx, x0, x1);
+            bt_range(S.rect[2], S.rect[3], g.bt_hy, g.bt_ny, y0, y1);
+            const int wx = x1 - x0 + 1, np = wx * (y1 - y0 + 1), npc = np < kMaxPix ? np : kMaxPix;
+            for (int k = tid; k < npc; k += nthr) {
+                const int px = x0 + k % wx, py = y0 + k / wx;
+                S.pcum[k] = bt_weight(g, d, S.rect, px, py);
+                S.pidx[k] = py * g.bt_nx + px;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                if (np > kMaxPix) S.err = CMH_ERR_CAPACITY;
                 double run = 0.0;
-                int np = 0;
-                for (int iy = y0; iy <= y1; ++iy)
-                    for (int ix = x0; ix <= x1; ++ix) {
-                        if (np >= kMaxPix) {
-                            S.err = CMH_ERR_CAPACITY;
-                            continue;
-                        }
-                        const double a = bt_weight(g, d, S.rect, ix, iy);
-                        run = __dadd_rn(run, a);
-                        if (a > 0.0) S.bt_last = np;
-                        S.pcum[np] = run;
-                        S.pidx[np] = iy * g.bt_nx + ix;
-                        ++np;
-                    }
-                S.bt_np = np;
+                for (int k = 0; k < npc; ++k) {
+                    const double a = S.pcum[k];
+                    run = __dadd_rn(run, a);
+                    if (a > 0.0) S.bt_last = k;
+                    S.pcum[k] = run;
+                }
+                S.bt_np = npc;
                 S.bt_G = run;
+                S.bt_in = run > 0.0 ? 1.0 / (g.bt_pixarea * run * g.bt_dt) : 0.0;
             }
         }
+        __syncthreads();
     }
     // ---- blanket: stations within R_max of the region (float test, margin) ----
     // warp w scans a contiguous chunk of stations; chunks are concatenated in
@@ -836,7 +845,7 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
     const int n_blk = S.n_blk;
     // position terms of the own events (the death Hastings term)
     for (int i = tid; i < n0; i += nthr)
-        S.elq[i] = g.bt_on ? bt_lq(g, d, S.bt_G, S.qu, S.mx[i], S.my[i], S.mt[i]) : S.lq_unif;
+        S.elq[i] = g.bt_on ? bt_lq(g, d, S, S.mx[i], S.my[i], S.mt[i]) : S.lq_unif;
     // ---- arrival cache of the own events (warp per event, lanes over slots) -----
     for (int i = wid; i < n0; i += nw) {
         int K;
@@ -976,7 +985,7 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
                 e.t = __dmul_rn(u01(c1[0]), g.T);
             }
             e.m = mag_from_u53(c1[1]);
-            D.blq = g.bt_on ? bt_lq(g, d, S.bt_G, S.qu, e.x, e.y, e.t) : S.lq_unif;
+            D.blq = g.bt_on ? bt_lq(g, d, S, e.x, e.y, e.t) : S.lq_unif;
             to_rel(g, X0, Y0, e);
             D.bx = e.x; D.by = e.y; D.bt = e.t; D.bm = e.m;
             D.blb = g.lb0 - e.m;

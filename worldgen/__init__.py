@@ -215,6 +215,13 @@ def config_replay(seed: int = 1000) -> World:
     return make_world(p, jittered_grid_stations(10, p.W, seed), seed, np.float64)
 
 
+def config_learned(seed: int = 1000) -> World:
+    """The 1000 x 1000 km, 3600 s, Lambda = 500, 100-station world with float32
+    signals, on which the learned birth proposal is compared with the plain one."""
+    p = ModelParams(W=1000.0, T=3600.0, Lambda=500.0)
+    return make_world(p, jittered_grid_stations(10, p.W, seed), seed, np.float32)
+
+
 def config_scale(seed: int = 1000, dtype=np.float32, side_regions: int = 40,
                  T: float = 86400.0) -> World:
     """4000 x 4000 km, 24 h, Lambda = 1e4, 1600 jittered stations, 864000 f32 samples.

@@ -60,6 +60,9 @@ constexpr long long kNParam = kOffFb2 + kNOut;
 // C[M,N] = op(A)[M,K] op(B)[K,N] (+ C) (+ bias[n]) (ReLU), BF16 in, FP32 out.
 // A(m,k) = TA ? A[k*lda+m] : A[m*lda+k];  B(k,n) = TB ? B[n*ldb+k] : B[k*ldb+n].
 // 64 x 64 tiles, 4 warps of 32 x 32, K in steps of 32, mma m16n8k16.
+// Split K (gridDim.z > 1): split z covers K range [z kc, (z + 1) kc) and
+// writes its partial product to C + z M ldc (no bias, ReLU or accumulate);
+// sum_splits adds the partials in split order.
 // ---------------------------------------------------------------------------
 constexpr int GB = 64, GK = 32, GP = GK + 8;
 
@@ -67,7 +70,7 @@ template <bool TA, bool TB>
 __global__ void __launch_bounds__(128) gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, int lda,
                                                  const __nv_bfloat16* B, int ldb, float* C, int ldc,
                                                  const float* bias, int relu, int accumulate,
-                                                 __nv_bfloat16* Cb) {
+                                                 __nv_bfloat16* Cb, int kc) {
     __shared__ __align__(16) __nv_bfloat16 As[GB][GP];
     __shared__ __align__(16) __nv_bfloat16 Bs[GB][GP];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -82,16 +85,18 @@ __global__ void __launch_bounds__(128) gemm_bf16(int M, int N, int K, const __nv
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
     const __nv_bfloat16 zero = __float2bfloat16(0.f);
-    for (int k0 = 0; k0 < K; k0 += GK) {
+    const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+    if (gridDim.z > 1) C += (long long)blockIdx.z * M * ldc;
+    for (int k0 = kb; k0 < ke; k0 += GK) {
         for (int e = tid; e < GB * GK; e += 128) {
             // A tile: As[m][k]; B tile stored transposed: Bs[n][k]
             int r, c;
             if (TA) { c = e / GB; r = e % GB; } else { r = e / GK; c = e % GK; }
             const int gm = m0 + r, gk = k0 + c;
-            As[r][c] = (gm < M && gk < K) ? (TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk]) : zero;
+            As[r][c] = (gm < M && gk < ke) ? (TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk]) : zero;
             if (TB) { r = e / GK; c = e % GK; } else { c = e / GB; r = e % GB; }
             const int gn = n0 + r, gk2 = k0 + c;
-            Bs[r][c] = (gn < N && gk2 < K) ? (TB ? B[(long long)gn * ldb + gk2] : B[(long long)gk2 * ldb + gn]) : zero;
+            Bs[r][c] = (gn < N && gk2 < ke) ? (TB ? B[(long long)gn * ldb + gk2] : B[(long long)gk2 * ldb + gn]) : zero;
         }
         __syncthreads();
 #pragma unroll
@@ -187,13 +192,30 @@ __global__ void to_bf16(const float* x, long long n, __nv_bfloat16* y) {
         y[i] = __float2bfloat16(x[i]);
 }
 
-// column sums of a [M][N] matrix (bias gradients), one thread per column
-__global__ void col_sums(const float* D, int M, int N, float* out) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+// partial column sums of a [M][N] matrix (bias gradients): block (32, 8)
+// sums columns bx*32 + tx over rows [by*rc, (by + 1)*rc) into part[by][n]
+__global__ void col_sums(const float* D, int M, int N, int rc, float* part) {
+    __shared__ float red[8][33];
+    const int n = blockIdx.x * 32 + threadIdx.x, r0 = blockIdx.y * rc, r1 = min(M, r0 + rc);
     float s = 0.f;
-    for (int m = 0; m < M; ++m) s += D[(long long)m * N + n];
-    out[n] = s;
+    if (n < N)
+        for (int m = r0 + threadIdx.y; m < r1; m += 8) s += D[(long long)m * N + n];
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && n < N) {
+        float t = 0.f;
+        for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x];
+        part[(long long)blockIdx.y * N + n] = t;
+    }
+}
+
+// out[i] = sum over z < splits of part[z][i], in split order (deterministic)
+__global__ void sum_splits(const float* part, long long n, int splits, float* out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < splits; ++z) s += part[(long long)z * n + i];
+        out[i] = s;
+    }
 }
 
 __device__ __forceinline__ float block_sum(float v, float* red) {
@@ -271,8 +293,8 @@ __global__ void adamw(float* p, const float* g, float* m1, float* m2, long long 
 // Example b of batch `step`: 8 x 8 stations jittered around the centres of
 // 100 km cells of an 800 km tile; with probability 1/2 one event, uniform in
 // the tile, magnitude 2 + Exp(1), origin time uniform in [-15, 25.6) s of the
-// window; 256 samples at f per station: s = sqrt(noise + sum of arrival
-// variances) * N(0, 1); features log1p(s^2).  Labels: the event's pixel (or
+// window; 256 samples at f per station: s = sqrt(noise + arrival variance)
+// * N(0, 1) (float32); features log1p(s^2).  Labels: the event's pixel (or
 // 4096 for none), its time relative to the window start, its magnitude.
 __global__ void __launch_bounds__(256) gen_windows(Geo g, unsigned long long seed, unsigned long long step, int Bn,
                                                    __nv_bfloat16* X, int* label, float* tl, float* ml) {
@@ -310,24 +332,45 @@ __global__ void __launch_bounds__(256) gen_windows(Geo g, unsigned long long see
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kNS * kNL; i += blockDim.x) {
-        const int s = i % kNS, t = i / kNS;
-        double V = g.noise_var;
-        if (has) {
-            const double dx = ev[0] - sx[s], dy = ev[1] - sy[s], dist = sqrt(dx * dx + dy * dy);
-            if (dist < g.R_max) {
-                const double u = t / g.f_hz - (ev[2] + dist / g.v);
-                if (u >= 0.0 && u < (double)g.n_w / g.f_hz) {
-                    const double a = exp(g.alpha * ev[3] - g.beta_att * dist - u / g.tau);
-                    V += a * a;
-                }
-            }
-        }
-        unsigned long long w[4] = {step, (unsigned long long)b, (unsigned long long)i, 9ULL};
+    // per station: reached?, arrival time, squared amplitude at the arrival
+    __shared__ float arr[kNS], amp2[kNS];
+    __shared__ int reach[kNS];
+    if (threadIdx.x < kNS) {
+        const int s = threadIdx.x;
+        const double dx = ev[0] - sx[s], dy = ev[1] - sy[s], dist = sqrt(dx * dx + dy * dy);
+        reach[s] = has && dist < g.R_max;
+        arr[s] = (float)(ev[2] + dist / g.v);
+        amp2[s] = (float)exp(2.0 * (g.alpha * ev[3] - g.beta_att * dist));
+    }
+    __syncthreads();
+    // four samples of one station per Philox block: s = sqrt(V) z, z from
+    // Box-Muller on both halves of two uniform pairs
+    const float fs = (float)g.f_hz, ts = (float)((double)g.n_w / g.f_hz), itau2 = (float)(2.0 / g.tau);
+    const float nv = (float)g.noise_var;
+    for (int q = threadIdx.x; q < kNS * kNL / 4; q += blockDim.x) {
+        const int s = q % kNS, t0 = (q / kNS) * 4;
+        unsigned long long w[4] = {step, (unsigned long long)b, (unsigned long long)q, 9ULL};
         philox4x64(w, seed, 3ULL);
-        const double z = sqrt(-2.0 * log(u01o(w[0]))) * cos(6.283185307179586 * u01(w[1]));
-        const double sig = sqrt(V) * z;
-        X[((long long)b * kNL + t) * kNS + s] = __float2bfloat16((float)log1p(sig * sig));
+        float z[4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float u1 = ((float)(w[2 * h] >> 40) + 0.5f) * (1.0f / 16777216.0f);
+            const float u2 = (float)(w[2 * h + 1] >> 40) * (1.0f / 16777216.0f);
+            const float r = sqrtf(-2.f * logf(u1));
+            float sn, cs;
+            sincospif(2.f * u2, &sn, &cs);
+            z[2 * h] = r * cs;
+            z[2 * h + 1] = r * sn;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int t = t0 + k;
+            float V = nv;
+            const float u = (float)t / fs - arr[s];
+            if (reach[s] && u >= 0.f && u < ts) V += amp2[s] * expf(-u * itau2);
+            const float x = sqrtf(V) * z[k];
+            X[((long long)b * kNL + t) * kNS + s] = __float2bfloat16(log1pf(x * x));
+        }
     }
 }
 
@@ -397,6 +440,7 @@ struct cmh_net {
     float *y[4] = {nullptr}, *h = nullptr, *o = nullptr, *dO = nullptr, *dh = nullptr, *dcol = nullptr;
     __nv_bfloat16 *yb[4] = {nullptr}, *hb = nullptr, *dOb = nullptr, *dhb = nullptr, *dyb = nullptr;
     float *dy = nullptr, *dx = nullptr, *loss = nullptr, *tl = nullptr, *ml = nullptr;
+    float* ws = nullptr;   // split partials of products and column sums
     int* label = nullptr;
     std::vector<void*> allocs;
 
@@ -415,12 +459,41 @@ struct cmh_net {
 
 namespace {
 
+constexpr int kMaxSplits = 64;
+constexpr long long kWsFloats = (long long)kMaxSplits * kC * kKC;   // split partials of the largest split product
+
+// K is split when the M x N tiles alone would leave most SMs idle and the
+// epilogue is a plain store into a dense C (the weight gradients of the
+// convolutions: 64 x 320 outputs over up to 32768 rows)
 template <bool TA, bool TB>
-cudaError_t gemm(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B,
-                 int ldb, float* C, int ldc, const float* bias, int relu, int acc, __nv_bfloat16* Cb) {
-    dim3 grid((N + GB - 1) / GB, (M + GB - 1) / GB);
-    gemm_bf16<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, acc, Cb);
+cudaError_t gemm(cudaStream_t s, float* ws, int M, int N, int K, const __nv_bfloat16* A, int lda,
+                 const __nv_bfloat16* B, int ldb, float* C, int ldc, const float* bias, int relu, int acc,
+                 __nv_bfloat16* Cb) {
+    const int gx = (N + GB - 1) / GB, gy = (M + GB - 1) / GB, tiles = gx * gy;
+    int splits = 1, kc = K;
+    if (ws && !bias && !relu && !acc && !Cb && ldc == N && tiles < 152) {
+        splits = std::min(kMaxSplits, std::min((304 + tiles - 1) / tiles, (K + 255) / 256));
+        while (splits > 1 && (long long)splits * M * N > kWsFloats) --splits;
+        if (splits > 1) {
+            kc = ((K + splits - 1) / splits + GK - 1) / GK * GK;
+            splits = (K + kc - 1) / kc;
+        }
+    }
+    if (splits > 1) {
+        gemm_bf16<TA, TB><<<dim3(gx, gy, splits), 128, 0, s>>>(M, N, K, A, lda, B, ldb, ws, ldc, nullptr, 0, 0,
+                                                               nullptr, kc);
+        sum_splits<<<blocks_for((long long)M * N), 256, 0, s>>>(ws, (long long)M * N, splits, C);
+    } else {
+        gemm_bf16<TA, TB><<<dim3(gx, gy, 1), 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, acc, Cb, K);
+    }
     return cudaGetLastError();
+}
+
+// column sums of a [M][N] matrix over row chunks, added in chunk order
+void colsum(cudaStream_t s, float* ws, const float* D, int M, int N, float* out) {
+    const int sp = std::max(1, std::min(kMaxSplits, (M + 255) / 256)), rc = (M + sp - 1) / sp;
+    col_sums<<<dim3((N + 31) / 32, sp), dim3(32, 8), 0, s>>>(D, M, N, rc, ws);
+    sum_splits<<<blocks_for(N), 256, 0, s>>>(ws, N, sp, out);
 }
 
 const int kLin[5] = {256, 128, 64, 32, 16};
@@ -434,16 +507,16 @@ cudaError_t forward(cmh_net* n, int Bn) {
         const int Lin = kLin[l], Lout = kLin[l + 1];
         const long long rows = (long long)Bn * Lout;
         im2col<<<blocks_for(rows * kKC), 256, 0, s>>>(in, Bn, Lin, Lout, n->col);
-        e = gemm<false, true>(s, (int)rows, kC, kKC, n->col, kKC, n->pb + l * kConvP, kKC, n->y[l], kC,
+        e = gemm<false, true>(s, n->ws, (int)rows, kC, kKC, n->col, kKC, n->pb + l * kConvP, kKC, n->y[l], kC,
                               n->p + l * kConvP + kConvW, 1, 0, n->yb[l]);
         in = n->yb[l];
     }
     if (e) return e;
     // FC1: [B][1024] x F1^T -> [B][512]
-    if ((e = gemm<false, true>(s, Bn, kF1Out, kF1In, n->yb[3], kF1In, n->pb + kOffF1, kF1In, n->h, kF1Out,
+    if ((e = gemm<false, true>(s, n->ws, Bn, kF1Out, kF1In, n->yb[3], kF1In, n->pb + kOffF1, kF1In, n->h, kF1Out,
                                n->p + kOffFb1, 1, 0, n->hb)))
         return e;
-    return gemm<false, true>(s, Bn, kNOut, kF1Out, n->hb, kF1Out, n->pb + kOffF2, kF1Out, n->o, kNOut,
+    return gemm<false, true>(s, n->ws, Bn, kNOut, kF1Out, n->hb, kF1Out, n->pb + kOffF2, kF1Out, n->o, kNOut,
                              n->p + kOffFb2, 0, 0, nullptr);
 }
 
@@ -454,20 +527,20 @@ cudaError_t backward(cmh_net* n, int Bn) {
     loss_grad<<<Bn, 256, 0, s>>>(n->o, n->label, n->tl, n->ml, Bn, n->dO, n->loss);
     to_bf16<<<blocks_for((long long)Bn * kNOut), 256, 0, s>>>(n->dO, (long long)Bn * kNOut, n->dOb);
     // FC2: dF2 = dO^T h, dfb2 = colsum dO, dh = dO F2
-    if ((e = gemm<true, false>(s, kNOut, kF1Out, Bn, n->dOb, kNOut, n->hb, kF1Out, n->gr + kOffF2, kF1Out, nullptr, 0,
+    if ((e = gemm<true, false>(s, n->ws, kNOut, kF1Out, Bn, n->dOb, kNOut, n->hb, kF1Out, n->gr + kOffF2, kF1Out, nullptr, 0,
                                0, nullptr)))
         return e;
-    col_sums<<<(kNOut + 255) / 256, 256, 0, s>>>(n->dO, Bn, kNOut, n->gr + kOffFb2);
-    if ((e = gemm<false, false>(s, Bn, kF1Out, kNOut, n->dOb, kNOut, n->pb + kOffF2, kF1Out, n->dh, kF1Out, nullptr,
+    colsum(s, n->ws, n->dO, Bn, kNOut, n->gr + kOffFb2);
+    if ((e = gemm<false, false>(s, n->ws, Bn, kF1Out, kNOut, n->dOb, kNOut, n->pb + kOffF2, kF1Out, n->dh, kF1Out, nullptr,
                                 0, 0, nullptr)))
         return e;
     relu_back<<<blocks_for((long long)Bn * kF1Out), 256, 0, s>>>(n->dh, n->h, (long long)Bn * kF1Out, n->dh, n->dhb);
     // FC1: dF1 = dh^T x4, dfb1, dx4 = dh F1 (into dy as [B*16][64])
-    if ((e = gemm<true, false>(s, kF1Out, kF1In, Bn, n->dhb, kF1Out, n->yb[3], kF1In, n->gr + kOffF1, kF1In, nullptr,
+    if ((e = gemm<true, false>(s, n->ws, kF1Out, kF1In, Bn, n->dhb, kF1Out, n->yb[3], kF1In, n->gr + kOffF1, kF1In, nullptr,
                                0, 0, nullptr)))
         return e;
-    col_sums<<<(kF1Out + 255) / 256, 256, 0, s>>>(n->dh, Bn, kF1Out, n->gr + kOffFb1);
-    if ((e = gemm<false, false>(s, Bn, kF1In, kF1Out, n->dhb, kF1Out, n->pb + kOffF1, kF1In, n->dy, kF1In, nullptr, 0,
+    colsum(s, n->ws, n->dh, Bn, kF1Out, n->gr + kOffFb1);
+    if ((e = gemm<false, false>(s, n->ws, Bn, kF1In, kF1Out, n->dhb, kF1Out, n->pb + kOffF1, kF1In, n->dy, kF1In, nullptr, 0,
                                 0, nullptr)))
         return e;
     for (int l = 3; l >= 0; --l) {
@@ -479,13 +552,13 @@ cudaError_t backward(cmh_net* n, int Bn) {
         const __nv_bfloat16* in = l == 0 ? n->x0 : n->yb[l - 1];
         im2col<<<blocks_for(rows * kKC), 256, 0, s>>>(in, Bn, Lin, Lout, n->col);
         // dW = dy^T col, db = colsum dy
-        if ((e = gemm<true, false>(s, kC, kKC, (int)rows, n->dyb, kC, n->col, kKC, n->gr + l * kConvP, kKC, nullptr, 0,
+        if ((e = gemm<true, false>(s, n->ws, kC, kKC, (int)rows, n->dyb, kC, n->col, kKC, n->gr + l * kConvP, kKC, nullptr, 0,
                                    0, nullptr)))
             return e;
-        col_sums<<<1, 64, 0, s>>>(n->dy, (int)rows, kC, n->gr + l * kConvP + kConvW);
+        colsum(s, n->ws, n->dy, (int)rows, kC, n->gr + l * kConvP + kConvW);
         if (l == 0) break;
         // dcol = dy W, dx = col2im(dcol) (the previous layer's output gradient)
-        if ((e = gemm<false, false>(s, (int)rows, kKC, kC, n->dyb, kC, n->pb + l * kConvP, kKC, n->dcol, kKC, nullptr,
+        if ((e = gemm<false, false>(s, n->ws, (int)rows, kKC, kC, n->dyb, kC, n->pb + l * kConvP, kKC, n->dcol, kKC, nullptr,
                                     0, 0, nullptr)))
             return e;
         col2im<<<blocks_for((long long)Bn * Lin * kC), 256, 0, s>>>(n->dcol, Bn, Lin, Lout, n->dy);
@@ -526,7 +599,7 @@ extern "C" int cmh_net_create(int32_t max_batch, uint64_t seed, void* cuda_strea
               n->alloc(&n->o, B * kNOut) && n->alloc(&n->dO, B * kNOut) && n->alloc(&n->dOb, B * kNOut) &&
               n->alloc(&n->dh, B * kF1Out) && n->alloc(&n->dhb, B * kF1Out) && n->alloc(&n->dcol, B * 128 * kKC) &&
               n->alloc(&n->dy, B * 128 * kC) && n->alloc(&n->dyb, B * 128 * kC) && n->alloc(&n->dx, B * 256 * kC) &&
-              n->alloc(&n->loss, B) && n->alloc(&n->tl, B) && n->alloc(&n->ml, B) && n->alloc(&n->label, B);
+              n->alloc(&n->loss, B) && n->alloc(&n->tl, B) && n->alloc(&n->ml, B) && n->alloc(&n->label, B) && n->alloc(&n->ws, kWsFloats);
     for (int l = 0; l < 4 && ok; ++l) ok = n->alloc(&n->y[l], B * kLin[l + 1] * kC) && n->alloc(&n->yb[l], B * kLin[l + 1] * kC);
     if (!ok) {
         delete n;

@@ -104,7 +104,10 @@ def test_forward_and_gradients_match_float64_oracle():
     net.destroy()
 
 
-def test_training_concentrates_the_birth_table_on_events():
+@pytest.fixture(scope="module")
+def trained():
+    """A network trained on 512k simulated windows and the birth table it
+    makes from a 1000 km, 30 min, 100-station world's signals."""
     cm = lib()
     w = small_world(seed=41, W=1000.0, T=1800.0, Lambda=250.0, n_side=10, dtype=np.float32)
     m = cm.create_model(None, w.stations, w.signals,
@@ -112,12 +115,20 @@ def test_training_concentrates_the_birth_table_on_events():
     net = cm.Net(max_batch=256, seed=7)
     l0 = net.train(m, 1, 256, 1e-3)
     l1 = net.train(m, 2000, 256, 3e-4)
+    tiles, origins = cm.grid_tiles(10, 100.0)
+    tab = net.birth_table(m, tiles, origins, 80, 80, 180, hop_s=12.8)
+    yield cm, w, (l0, l1), tab
+    net.destroy()
+    m.destroy()
+
+
+def test_training_concentrates_the_birth_table_on_events(trained):
+    cm, w, (l0, l1), tab = trained
     print("loss %.3f -> %.3f" % (l0, l1))
     assert l1 < l0 - 2.0
-    tiles, origins = cm.grid_tiles(10, 100.0)
-    nx, nt = 80, 180
-    tab = net.birth_table(m, tiles, origins, nx, nx, nt, hop_s=12.8).astype(np.float64)
+    tab = tab.astype(np.float64)
     assert np.all(np.isfinite(tab)) and tab.sum() > 0
+    nx, nt = tab.shape[1], tab.shape[2]
     dens = tab / tab.sum()
     det = np.array([np.min(np.hypot(w.stations[:, 0] - e[0], w.stations[:, 1] - e[1])) < w.params.R_max
                     for e in w.events])
@@ -128,5 +139,26 @@ def test_training_concentrates_the_birth_table_on_events():
     gain = np.mean(vals) / dens.mean()
     print("table density near detectable events / mean density: %.1f" % gain)
     assert gain > 4.0
-    net.destroy()
-    m.destroy()
+
+
+def test_learned_births_find_events_sooner(trained):
+    """What the network gains: from the empty hypothesis, 5 sweeps with the
+    50/50 mixture recover more of the detectable events than 5 plain sweeps
+    (mean over 4 chains; about 0.65 against 0.40 on this kind of world)."""
+    cm, w, _, tab = trained
+    from paper_1612_00595_gb300 import metrics
+    P = w.params
+    rec = {"plain": [], "learned": []}
+    for seed in (7, 8, 9, 10):
+        for kind in rec:
+            m = cm.create_model(None, w.stations, w.signals,
+                                cm.make_params(P, k_per_phase=32, seed=seed, dtype=cm.F32))
+            m.partition_and_color(P.L)
+            if kind == "learned":
+                m.set_birth_table(tab, 0.5)
+            m.run_sweeps(5)
+            sc = metrics.scores(w.events, m.read_state()[0], P.L, P.tau, w.stations, P.R_max)
+            rec[kind].append(sc["recall"])
+            m.destroy()
+    print("recall after 5 sweeps: plain %s learned %s" % (np.round(rec["plain"], 3), np.round(rec["learned"], 3)))
+    assert np.mean(rec["learned"]) > np.mean(rec["plain"]) + 0.1

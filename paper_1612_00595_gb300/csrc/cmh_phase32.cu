@@ -308,7 +308,7 @@ __device__ __forceinline__ double bt_weight(const Geo& g, const Dev& d, const do
 // reciprocal products, the weight is the table's own float and the logarithm
 // is taken in float32 (error ~1e-7 against the float64 form); the sum into
 // log alpha stays float64.  The sampling itself (learned_birth) is exact.
-__device__ __forceinline__ double bt_lq(const Geo& g, const Dev& d, const Sm& S, double x, double y, double t) {
+__device__ __noinline__ double bt_lq(const Geo& g, const Dev& d, const Sm& S, double x, double y, double t) {
     double qn = 0.0;
     if (S.bt_G > 0.0) {
         int ix = (int)(x * g.bt_ihx), iy = (int)(y * g.bt_ihy), b = (int)(t * g.bt_idt);
@@ -417,7 +417,6 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
                 valid = inside_exact(g, S.sx, S.sy, S.cell, c.x, c.y, c.t, c.m);
                 if (valid) to_rel(g, S.X0, S.Y0, c);
             }
-            if (valid) c.lq = g.bt_on ? bt_lq(g, d, S, c.x, c.y, c.t) : S.lq_unif;
         }
     }
     // candidate arrivals, lanes over blanket slots, compacted in slot order
@@ -800,7 +799,6 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
                 S.bt_in = run > 0.0 ? 1.0 / (g.bt_pixarea * run * g.bt_dt) : 0.0;
             }
         }
-        __syncthreads();
     }
     // ---- blanket: stations within R_max of the region (float test, margin) ----
     // warp w scans a contiguous chunk of stations; chunks are concatenated in
@@ -1101,7 +1099,9 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
                             lists_remove(g, S, ps);
                         }
                         S.mx[ps] = c.x; S.my[ps] = c.y; S.mt[ps] = c.t; S.mm[ps] = c.m;
-                        S.elq[ps] = c.lq;
+                        // a move's own log alpha has no position term: the
+                        // moved event's term (for a later death) is taken here
+                        S.elq[ps] = type == 0 ? c.lq : (g.bt_on ? bt_lq(g, d, S, c.x, c.y, c.t) : S.lq_unif);
                         S.exr[ps] = c.xr; S.eyr[ps] = c.yr;
                         for (int a = 0; a < S.ncand[sl]; ++a) S.earr[ps * g.arr_cap + a] = cd[a];
                         S.enarr[ps] = S.ncand[sl];
@@ -1113,39 +1113,49 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
         }
         if (__syncthreads_or(S.err != 0)) break;
         // ================ commit: re-synthesise V on the touched windows ============
+        // The prepared next step assumed a rejection and is prepared again.
+        // Without staging that only reads shared memory, so warp 0 does it
+        // while the workers re-synthesise V; with staging its bulk copies
+        // read V, so it follows the re-synthesis.
         if (S.acc) {
             const T32* tk = S.tasks + sl * kMaxTasks32;
-            for (int ti = 0; ti < S.ntask[sl]; ++ti) {
-                const T32& T = tk[ti];
-                const SA* L = S.sarr + T.slot * g.frz_cap;
-                const int nl = S.scnt[T.slot];
-                float* vrow = (float*)d.V + (size_t)T.row * g.pitch;
-                // groups of four samples: one SFU evaluation per arrival and group
-                for (int k4 = ((T.lo >> 2) + tid) << 2; k4 < T.hi; k4 += nthr << 2) {
-                    float a2[4], c2[4];
+            const int rt = STAGE ? tid : tid - 32, rn = STAGE ? nthr : nthr - 32;
+            if (!STAGE && wid == 0) {
+                if (step + 1 < g.k) prepare_step<STAGE>(g, d, S, step + 1, sl ^ 1);
+            } else {
+                for (int ti = 0; ti < S.ntask[sl]; ++ti) {
+                    const T32& T = tk[ti];
+                    const SA* L = S.sarr + T.slot * g.frz_cap;
+                    const int nl = S.scnt[T.slot];
+                    float* vrow = (float*)d.V + (size_t)T.row * g.pitch;
+                    // groups of four samples: one SFU evaluation per arrival and group
+                    for (int k4 = ((T.lo >> 2) + rt) << 2; k4 < T.hi; k4 += rn << 2) {
+                        float a2[4], c2[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        a2[e] = g.noise_f;
-                        c2[e] = 0.f;
-                    }
-                    for (int o = 0; o < nl; ++o) {
-                        const SA A = L[o];
-                        if ((unsigned)(k4 + 3 - A.k0) >= (unsigned)(g.n_w + 3)) continue;
-                        const float base = arr_base32(g, A.E0, A.k0, k4);
+                        for (int e = 0; e < 4; ++e) {
+                            a2[e] = g.noise_f;
+                            c2[e] = 0.f;
+                        }
+                        for (int o = 0; o < nl; ++o) {
+                            const SA A = L[o];
+                            if ((unsigned)(k4 + 3 - A.k0) >= (unsigned)(g.n_w + 3)) continue;
+                            const float base = arr_base32(g, A.E0, A.k0, k4);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if ((unsigned)(k4 + e - A.k0) < (unsigned)g.n_w)
+                                    kahan_add32(a2[e], c2[e], __fmul_rn(base, g.rho_f[e]));
+                        }
 #pragma unroll
                         for (int e = 0; e < 4; ++e)
-                            if ((unsigned)(k4 + e - A.k0) < (unsigned)g.n_w)
-                                kahan_add32(a2[e], c2[e], __fmul_rn(base, g.rho_f[e]));
+                            if (k4 + e >= T.lo && k4 + e < T.hi) vrow[k4 + e] = a2[e] - c2[e];
                     }
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (k4 + e >= T.lo && k4 + e < T.hi) vrow[k4 + e] = a2[e] - c2[e];
                 }
             }
-            if (STAGE) fence_async_global();   // the new V is visible to the next bulk copies
-            __syncthreads();
-            // the prepared next step assumed a rejection: prepare it again
-            if (wid == 0 && step + 1 < g.k) prepare_step<STAGE>(g, d, S, step + 1, sl ^ 1);
+            if (STAGE) {
+                fence_async_global();   // the new V is visible to the next bulk copies
+                __syncthreads();
+                if (wid == 0 && step + 1 < g.k) prepare_step<STAGE>(g, d, S, step + 1, sl ^ 1);
+            }
             if (__syncthreads_or(S.err != 0)) break;
         }
     }

@@ -592,6 +592,32 @@ int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mo
         (e = m->alloc(&d.queue, 1, true)) || (e = m->alloc(&d.done, g.n_cells, true)) ||
         (e = m->alloc(&d.region_dlp, g.n_cells, true)))
         return cuda_err(e);
+    {
+        // blanket candidates: a cell's region is [s + (i-1) L, s + i L) per axis
+        // (clipped to the domain) for a shift s in [0, L), so it lies inside
+        // [(i-1) L, (i+1) L]; the stations within R_max (with room for the
+        // kernel's float test and its margin) of that box
+        std::vector<int> off(g.n_cells + 1), idx;
+        const double Rc = m->p.R_max * 1.001 + 1.0, W = m->p.W;
+        for (int c = 0; c < g.n_cells; ++c) {
+            const int cx = c % g.ncx, cy = c / g.ncx;
+            const double x0 = std::max(0.0, (cx - 1) * L), x1 = std::min(W, (cx + 1) * L);
+            const double y0 = std::max(0.0, (cy - 1) * L), y1 = std::min(W, (cy + 1) * L);
+            off[c] = (int)idx.size();
+            for (int j = 0; j < g.n_st; ++j) {
+                const double dx = hx[j] < x0 ? x0 - hx[j] : (hx[j] > x1 ? hx[j] - x1 : 0.0);
+                const double dy = hy[j] < y0 ? y0 - hy[j] : (hy[j] > y1 ? hy[j] - y1 : 0.0);
+                if (dx * dx + dy * dy < Rc * Rc) idx.push_back(j);
+            }
+        }
+        off[g.n_cells] = (int)idx.size();
+        int *doff = nullptr, *didx = nullptr;
+        if ((e = m->alloc(&doff, off.size(), true)) || (e = m->alloc(&didx, idx.size(), true))) return cuda_err(e);
+        CK(cudaMemcpy(doff, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
+        if (!idx.empty()) CK(cudaMemcpy(didx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice));
+        d.bl_off = doff;
+        d.bl_idx = didx;
+    }
     CK(cudaMemsetAsync(d.done, 0, sizeof(long long) * g.n_cells, m->stream));
     CK(cudaMemsetAsync(d.colour_off, 0, sizeof(int) * (kMaxColours + 1), m->stream));
     CK(cudaMemsetAsync(d.fill, 0, sizeof(int) * g.n_cells, m->stream));

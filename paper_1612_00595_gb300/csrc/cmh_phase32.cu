@@ -666,16 +666,31 @@ __device__ __forceinline__ void price_step(const Geo& g, const Dev& d, Sm& S, in
     if (lane == 0) S.redf[wid] = v;
 }
 
-// remove the arrivals of own event ps from its stations' lists (stable)
-__device__ __forceinline__ void lists_remove(const Geo& g, Sm& S, int ps) {
-    for (int a = 0; a < S.enarr[ps]; ++a) {
+// remove the arrivals of own event ps from its stations' lists, keeping the
+// order (the 32 lanes of a warp: entries in chunks of 32, kept ones compacted
+// by ballot; a chunk is read before any of it is written, and writes land at
+// or before the positions read)
+__device__ __forceinline__ void lists_remove_warp(const Geo& g, Sm& S, int ps) {
+    const int lane = threadIdx.x & 31;
+    const int na = S.enarr[ps];
+    for (int a = 0; a < na; ++a) {
         const int b = S.earr[ps * g.arr_cap + a].slot;
         SA* L = S.sarr + b * g.frz_cap;
         const int n = S.scnt[b];
         int w = 0;
-        for (int i = 0; i < n; ++i)
-            if (L[i].own != ps) L[w++] = L[i];
-        S.scnt[b] = w;
+        for (int c = 0; c < n; c += 32) {
+            const int i = c + lane;
+            SA e = {0, 0.f, 0, 0};
+            if (i < n) e = L[i];
+            const bool keep = i < n && e.own != ps;
+            const unsigned bal = __ballot_sync(FULL, keep);
+            __syncwarp();
+            if (keep) L[w + __popc(bal & ((1u << lane) - 1))] = e;
+            w += __popc(bal);
+            __syncwarp();
+        }
+        if (lane == 0) S.scnt[b] = w;
+        __syncwarp();
     }
 }
 
@@ -801,14 +816,18 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
         }
     }
     // ---- blanket: stations within R_max of the region (float test, margin) ----
-    // warp w scans a contiguous chunk of stations; chunks are concatenated in
-    // order, so the blanket lists stations by index
+    // among the cell's candidates (a superset, in station order); warp w scans
+    // a contiguous chunk of them and chunks are concatenated in order, so the
+    // blanket lists stations by index
     {
         const float r0 = (float)S.rect[0], r1 = (float)S.rect[1], r2 = (float)S.rect[2], r3 = (float)S.rect[3];
         const float Rm = g.R_f * 1.0001f + 1e-3f;
-        const int chunk = (g.n_st + nw - 1) / nw;
-        const int j0 = wid * chunk, j1 = min(g.n_st, j0 + chunk);
-        auto in_blanket = [&](int j) {
+        const int* cand = d.bl_idx + d.bl_off[cell];
+        const int n_cand = d.bl_off[cell + 1] - d.bl_off[cell];
+        const int chunk = (n_cand + nw - 1) / nw;
+        const int j0 = wid * chunk, j1 = min(n_cand, j0 + chunk);
+        auto in_blanket = [&](int q) {
+            const int j = cand[q];
             const float fx = d.stxf[j], fy = d.styf[j];
             const float dx = fx < r0 ? r0 - fx : (fx > r1 ? fx - r1 : 0.f);
             const float dy = fy < r2 ? r2 - fy : (fy > r3 ? fy - r3 : 0.f);
@@ -828,9 +847,10 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
             const unsigned bal = __ballot_sync(FULL, in);
             const int p = pos + __popc(bal & ((1u << lane) - 1));
             if (in && p < g.blk_cap) {
-                S.bsta[p] = j;
-                S.bx[p] = d.stx[j];
-                S.by[p] = d.sty[j];
+                const int st = cand[j];
+                S.bsta[p] = st;
+                S.bx[p] = d.stx[st];
+                S.by[p] = d.sty[st];
             }
             pos += __popc(bal);
         }
@@ -1045,6 +1065,7 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
                 w2.y = __shfl_xor_sync(FULL, t.y, o);
                 t = ff_add32(t, w2);
             }
+            int rm = -1, put = -1;   // event leaving its station lists / event (re)joining them
             if (lane == 0) {
                 const int type = S.type[sl], n_own = S.n_own, idx = S.idx[sl];
                 const D32& dr = S.draws[step];
@@ -1078,37 +1099,42 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
                 if (do_commit) {
                     S.cnt[10] += (unsigned long long)S.width[sl];
                     S.region_dlp += dll + dlp;
-                    const P32& c = S.c[sl];
-                    const A32* cd = S.cand + sl * g.arr_cap;
-                    int ps;
                     if (type == 1) {
-                        ps = S.order[idx];
-                        lists_remove(g, S, ps);
+                        const int ps = S.order[idx];
+                        rm = ps;
                         for (int q = idx; q + 1 < n_own; ++q) S.order[q] = S.order[q + 1];
                         S.freel[S.n_free++] = ps;
                         S.n_own = n_own - 1;
+                    } else if (type == 0) {
+                        const int ps = S.freel[--S.n_free];
+                        S.eid[ps] = ((unsigned long long)(sweep + 1) << 32) | ((unsigned long long)cell << 12) |
+                                    (unsigned long long)step;
+                        S.order[n_own] = ps;
+                        S.n_own = n_own + 1;
+                        put = ps;
                     } else {
-                        if (type == 0) {
-                            ps = S.freel[--S.n_free];
-                            S.eid[ps] = ((unsigned long long)(sweep + 1) << 32) | ((unsigned long long)cell << 12) |
-                                        (unsigned long long)step;
-                            S.order[n_own] = ps;
-                            S.n_own = n_own + 1;
-                        } else {
-                            ps = S.order[idx];
-                            lists_remove(g, S, ps);
-                        }
-                        S.mx[ps] = c.x; S.my[ps] = c.y; S.mt[ps] = c.t; S.mm[ps] = c.m;
-                        // a move's own log alpha has no position term: the
-                        // moved event's term (for a later death) is taken here
-                        S.elq[ps] = type == 0 ? c.lq : (g.bt_on ? bt_lq(g, d, S, c.x, c.y, c.t) : S.lq_unif);
-                        S.exr[ps] = c.xr; S.eyr[ps] = c.yr;
-                        for (int a = 0; a < S.ncand[sl]; ++a) S.earr[ps * g.arr_cap + a] = cd[a];
-                        S.enarr[ps] = S.ncand[sl];
-                        lists_add(g, S, ps, cd, S.ncand[sl]);
+                        rm = put = S.order[idx];
                     }
                 }
                 S.acc = do_commit;
+            }
+            // the removed or moved event's arrivals leave their station lists
+            // (all lanes), then the new arrivals join (lane 0)
+            rm = __shfl_sync(FULL, rm, 0);
+            put = __shfl_sync(FULL, put, 0);
+            if (rm >= 0) lists_remove_warp(g, S, rm);
+            if (lane == 0 && put >= 0) {
+                const int ps = put;
+                const P32& c = S.c[sl];
+                const A32* cd = S.cand + sl * g.arr_cap;
+                S.mx[ps] = c.x; S.my[ps] = c.y; S.mt[ps] = c.t; S.mm[ps] = c.m;
+                // a move's own log alpha has no position term: the moved
+                // event's term (for a later death) is taken here
+                S.elq[ps] = S.type[sl] == 0 ? c.lq : (g.bt_on ? bt_lq(g, d, S, c.x, c.y, c.t) : S.lq_unif);
+                S.exr[ps] = c.xr; S.eyr[ps] = c.yr;
+                for (int a = 0; a < S.ncand[sl]; ++a) S.earr[ps * g.arr_cap + a] = cd[a];
+                S.enarr[ps] = S.ncand[sl];
+                lists_add(g, S, ps, cd, S.ncand[sl]);
             }
         }
         if (__syncthreads_or(S.err != 0)) break;

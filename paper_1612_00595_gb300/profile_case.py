@@ -5,7 +5,9 @@
 Workloads: ``scale`` (4000 x 4000 km, 24 h, 1600 stations, float32),
 ``corner`` (1000 x 1000 km corner of the same density and record length,
 100 stations: 0.7 GB of signals + variance, larger than L2), ``replay``
-(1000 x 1000 km, 1 h, 100 stations, float64).
+(1000 x 1000 km, 1 h, 100 stations, float64), ``train`` (the learned birth
+network: ``--warmup`` then ``--sweeps`` training steps of 256 windows
+simulated from the 1000 km, 1 h, 100-station float32 world).
 """
 import argparse
 import os
@@ -37,6 +39,17 @@ def main():
     ap.add_argument("--k", type=int, default=32)
     args = ap.parse_args()
     import paper_1612_00595_gb300 as cm
+    if args.workload == "train":
+        w = worldgen.config_learned(seed=1000)
+        m = cm.create_model(None, w.stations, w.signals, cm.make_params(w.params, k_per_phase=args.k, seed=7,
+                                                                        dtype=cm.F32))
+        net = cm.Net(max_batch=256, seed=7)
+        net.train(m, args.warmup, 256, 3e-4)
+        loss = net.train(m, args.sweeps, 256, 3e-4)
+        print("training steps %d  loss %.4f" % (args.warmup + args.sweeps, loss))
+        net.destroy()
+        m.destroy()
+        return
     w = world_for(args.workload)
     dtype = cm.F32 if w.signals.dtype == np.float32 else cm.F64
     m = cm.create_model(w.events, w.stations, w.signals, cm.make_params(w.params, k_per_phase=args.k, seed=7,

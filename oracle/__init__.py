@@ -76,6 +76,7 @@ def lib(mutant: int = 0):
             "orc_world_new": (P, [C.POINTER(_Params), P, i32, P, i32, i64, i64]),
             "orc_world_free": (None, [P]),
             "orc_set_birth_table": (C.c_int, [P, P, i32, i32, i32, d]),
+            "orc_set_birth_magnitude": (C.c_int, [P, P, d]),
             "orc_set_new": (P, [P, P, i64]),
             "orc_set_size": (i64, [P]),
             "orc_set_get": (None, [P, P, P]),
@@ -193,6 +194,19 @@ class World:
             rc = self._lib.orc_set_birth_table(self._h, _ptr(self._tab), nx, ny, nt, float(mix))
         if rc != 0:
             raise ValueError("orc_set_birth_table rejected the table")
+
+    def set_birth_magnitude(self, centre, half_width=0.25):
+        """Magnitudes of the learned component: centre [ny, nx, nt] float32 (the
+        table's shape); a table birth draws m uniform on [lo, lo + 2 h), lo =
+        max(2, centre - h).  None returns to magnitudes from the prior."""
+        if centre is None:
+            self._mag = None
+            rc = self._lib.orc_set_birth_magnitude(self._h, None, 0.0)
+        else:
+            self._mag = np.ascontiguousarray(centre, dtype=np.float32)
+            rc = self._lib.orc_set_birth_magnitude(self._h, _ptr(self._mag), float(half_width))
+        if rc != 0:
+            raise ValueError("orc_set_birth_magnitude rejected the magnitudes")
 
     # ---- density -----------------------------------------------------------
     def log_prior(self, ev) -> float:

@@ -35,7 +35,12 @@
  * oracle with -DORC_MUTANT=n and check that some pin fails):
  *   1: birth ratio uses 1/(n+2) for the reverse death;  2: death drops log q_b;
  *   3: an arrival adds its standard deviation instead of its variance;
- *   4: a move ignores the prior ratio.  0 (the default) is the oracle itself. */
+ *   4: a move ignores the prior ratio;
+ *   5: the birth and death terms use the uniform density although births
+ *      come from the mixture with a learned table;
+ *   6: with learned magnitudes, the learned component's density keeps the
+ *      prior magnitude law although it draws m from its window.
+ * 0 (the default) is the oracle itself. */
 #ifndef ORC_MUTANT
 #define ORC_MUTANT 0
 #endif
@@ -55,6 +60,11 @@ struct orc_world {
     double bt_mix, bt_hx, bt_hy, bt_dt, bt_pixarea;
     double* bt_mass;     /* [pixel] sum of the pixel's weights */
     double* bt_cdf;      /* [pixel][bin] running sum of its weights / mass */
+    /* magnitudes of the learned component (none when NULL: m - 2 ~ Exp(1) as
+     * for uniform births): a birth at (pixel, bin) draws m uniform on
+     * [lo, lo + 2h), lo = max(2, centre - h) */
+    float* bt_mag;       /* [pixel][bin] window centre, owned copy */
+    double bt_h;
 };
 
 struct orc_set { ev_t* e; int64_t n, cap; };
@@ -130,6 +140,7 @@ void orc_world_free(orc_world* w) {
     free(w->st);
     free(w->bt_mass);
     free(w->bt_cdf);
+    free(w->bt_mag);
     free(w);
 }
 
@@ -140,8 +151,10 @@ void orc_world_free(orc_world* w) {
 int orc_set_birth_table(orc_world* w, const float* tab, int32_t nx, int32_t ny, int32_t nt, double mix) {
     free(w->bt_mass);
     free(w->bt_cdf);
+    free(w->bt_mag);
     w->bt_mass = NULL;
     w->bt_cdf = NULL;
+    w->bt_mag = NULL;
     w->bt_nx = w->bt_ny = w->bt_nt = 0;
     if (nx == 0) return 0;
     if (nx < 1 || ny < 1 || nt < 1 || !(mix > 0.0 && mix < 1.0) || !tab) return -1;
@@ -167,6 +180,24 @@ int orc_set_birth_table(orc_world* w, const float* tab, int32_t nx, int32_t ny, 
     w->bt_hy = w->p.W / (double)ny;
     w->bt_dt = w->p.T / (double)nt;
     w->bt_pixarea = w->bt_hx * w->bt_hy;
+    return 0;
+}
+
+/* Magnitudes of the learned component: centre[(iy * nx + ix) * nt + b]
+ * (finite) for the table's pixels and bins, window half-width h > 0; NULL
+ * returns to magnitudes from the prior.  Needs a table; a new table drops
+ * them. */
+int orc_set_birth_magnitude(orc_world* w, const float* centre, double h) {
+    free(w->bt_mag);
+    w->bt_mag = NULL;
+    if (!centre) return 0;
+    if (!w->bt_nx || !(h > 0.0) || isinf(h)) return -1;
+    const int64_t n = (int64_t)w->bt_nx * w->bt_ny * w->bt_nt;
+    for (int64_t i = 0; i < n; ++i)
+        if (!isfinite(centre[i])) return -1;
+    w->bt_mag = (float*)malloc(sizeof(float) * (size_t)n);
+    memcpy(w->bt_mag, centre, sizeof(float) * (size_t)n);
+    w->bt_h = h;
     return 0;
 }
 
@@ -488,6 +519,18 @@ static void region_bt(const orc_world* w, region_t* g) {
         for (int32_t ix = x0; ix <= x1; ++ix) g->G += pix_weight(w, g, ix, iy);
 }
 
+/* window start of the learned magnitude at table entry q */
+static double mag_lo(const orc_world* w, int64_t q) { return fmax(2.0, (double)w->bt_mag[q] - w->bt_h); }
+
+/* table entry (pixel, bin) that (x, y, t) falls in */
+static int64_t bt_entry(const orc_world* w, double x, double y, double t) {
+    int32_t ix = (int32_t)floor(x / w->bt_hx), iy = (int32_t)floor(y / w->bt_hy), b = (int32_t)floor(t / w->bt_dt);
+    if (ix > w->bt_nx - 1) ix = w->bt_nx - 1;
+    if (iy > w->bt_ny - 1) iy = w->bt_ny - 1;
+    if (b > w->bt_nt - 1) b = w->bt_nt - 1;
+    return ((int64_t)iy * w->bt_nx + ix) * w->bt_nt + b;
+}
+
 /* density of the learned component at (x, y, t), magnitude factor left out:
  * the pixel's mass share of the region over the pixel area, times the time
  * bin's share of the pixel over the bin length */
@@ -547,13 +590,26 @@ static double log_qb(const orc_world* w, const region_t* g, const ev_t* e) {
     double area = (g->r[1] - g->r[0]) * (g->r[3] - g->r[2]);
     if (!w->bt_nx || !(g->G > 0.0) || ORC_MUTANT == 5) return -log(area) - log(p->T) - (e->m - 2.0);
     const double qu = 1.0 / (area * p->T);
-    return log((1.0 - w->bt_mix) * qu + w->bt_mix * q_net(w, g, e->x, e->y, e->t)) - (e->m - 2.0);
+    if (!w->bt_mag)   /* both components draw m from the prior */
+        return log((1.0 - w->bt_mix) * qu + w->bt_mix * q_net(w, g, e->x, e->y, e->t)) - (e->m - 2.0);
+    /* the learned component draws m uniform on its entry's window */
+    const double pm = exp(-(e->m - 2.0));
+    double qm = 0.0;
+    if (ORC_MUTANT == 6) {
+        qm = pm;
+    } else {
+        const double lo = mag_lo(w, bt_entry(w, e->x, e->y, e->t));
+        if (e->m >= lo && e->m < lo + 2.0 * w->bt_h) qm = 1.0 / (2.0 * w->bt_h);
+    }
+    return log((1.0 - w->bt_mix) * qu * pm + w->bt_mix * q_net(w, g, e->x, e->y, e->t) * qm);
 }
 
 /* a learned birth candidate: pixel by its share of the region's table mass,
  * uniform inside pixel n region, time bin by the pixel's cdf, uniform inside
- * the bin (words: pixel wd[2], x wd[3], y wd[8], bin wd[9], t wd[10]) */
-static void learned_birth(const orc_world* w, const region_t* g, const uint64_t* wd, ev_t* c) {
+ * the bin, and with magnitudes the magnitude uniform on the drawn entry's
+ * window (words: pixel wd[2], x wd[3], y wd[8], bin wd[9], t wd[10], m
+ * wd[11]); returns whether it drew the magnitude */
+static int learned_birth(const orc_world* w, const region_t* g, const uint64_t* wd, ev_t* c) {
     int32_t x0, x1, y0, y1;
     pix_range(g->r[0], g->r[1], w->bt_hx, w->bt_nx, &x0, &x1);
     pix_range(g->r[2], g->r[3], w->bt_hy, w->bt_ny, &y0, &y1);
@@ -581,6 +637,9 @@ static void learned_birth(const orc_world* w, const region_t* g, const uint64_t*
     int32_t b = 0;
     while (b < w->bt_nt - 1 && !(cd[b] > ub)) ++b;
     c->t = (double)b * w->bt_dt + u01(wd[10]) * w->bt_dt;
+    if (!w->bt_mag) return 0;
+    c->m = mag_lo(w, ((int64_t)py * w->bt_nx + px) * w->bt_nt + b) + u01(wd[11]) * (2.0 * w->bt_h);
+    return 1;
 }
 
 /* Gaussian magnitude of a Box-Muller pair, rounded to a multiple of 2^-20 so
@@ -610,8 +669,7 @@ static prop_t decode(const orc_world* w, const region_t* g, const uint64_t* wd,
             q.cand.t = p->lat_t0 + (double)pick(wd[3], p->lat_nt) * p->lat_dt;
             q.cand.m = p->lat_m0 + (double)pick(wd[4], p->lat_nm) * p->lat_dm;
         } else if (w->bt_nx && g->G > 0.0 && u01(wd[7]) < w->bt_mix) {
-            learned_birth(w, g, wd, &q.cand);
-            q.cand.m = 2.0 - log(u01o(wd[5]));
+            if (!learned_birth(w, g, wd, &q.cand)) q.cand.m = 2.0 - log(u01o(wd[5]));
         } else {
             q.cand.x = g->r[0] + u01(wd[2]) * (g->r[1] - g->r[0]);
             q.cand.y = g->r[2] + u01(wd[3]) * (g->r[3] - g->r[2]);

@@ -59,6 +59,7 @@ void orc_world_free(orc_world* w);
  * [0,W)^2 and time bins of [0,T), mixing weight mix in (0, 1); nx == 0
  * removes it.  Returns 0, or -1 for bad arguments. */
 int orc_set_birth_table(orc_world* w, const float* tab, int32_t nx, int32_t ny, int32_t nt, double mix);
+int orc_set_birth_magnitude(orc_world* w, const float* centre, double half_width);
 
 orc_set* orc_set_new(const double* ev, const uint64_t* ids, int64_t n);
 int64_t orc_set_size(const orc_set* s);

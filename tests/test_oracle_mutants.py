@@ -67,3 +67,9 @@ def test_mixture_mutant_drifts_to_the_hot_block(orc):
     from test_oracle_sampler import _prior_with_table
     _, _, fxy, ft = _prior_with_table(orc, mutant=5, n_sweeps=1500)
     assert fxy > 0.1 and ft > 0.24, (fxy, ft)   # unmutated: 0.0625 and 0.2
+
+
+def test_magnitude_mutant_piles_up_in_the_window(orc):
+    from test_oracle_sampler import _prior_with_magnitudes
+    mean, frac, _ = _prior_with_magnitudes(orc, mutant=6, n_sweeps=1500)
+    assert frac > 0.12, (mean, frac)   # unmutated: 0.068

@@ -302,3 +302,35 @@ def test_learned_birth_mixture_keeps_the_prior(orc):
     assert abs(m - p.Lambda) < 5 * se, (m, se)
     assert abs(fxy - 4.0 / 64.0) < 0.012, fxy
     assert abs(ft - 0.2) < 0.025, ft
+
+
+def _prior_with_magnitudes(orc, mutant=0, n_sweeps=3000):
+    """The hot table with learned magnitudes: window [3.75, 4.25) everywhere
+    (centre 4, half-width 0.25).  Returns the mean of m - 2 over the chain's
+    events and the fraction of them inside the window."""
+    p = worldgen.ModelParams(W=200.0, T=100.0, Lambda=12.0, R_max=50.0, L=100.0)
+    w = worldgen.World(params=p, stations=np.zeros((0, 2)), signals=np.zeros((0, 0)),
+                       events=np.zeros((0, 4)))
+    o = orc.World(w, k_per_phase=8, seed=13, sig_xy=20.0, sig_t=10.0, sig_m=0.5, mutant=mutant)
+    tab = _hot_table()
+    o.set_birth_table(tab, mix=0.5)
+    o.set_birth_magnitude(np.full(tab.shape, 4.0, dtype=np.float32), 0.25)
+    ev, ids = np.zeros((0, 4)), None
+    ms, means = [], []
+    for it in range(n_sweeps):
+        ev, ids, _, _ = o.run_chromatic(ev, 1, ids=ids, sweep0=it, shift_mode=1)
+        if it % 5 == 0 and len(ev):
+            ms.append(ev[:, 3].copy())
+            means.append(ev[:, 3].mean() - 2.0)
+    m = np.concatenate(ms)
+    return m.mean() - 2.0, np.mean((m >= 3.75) & (m < 4.25)), np.array(means)
+
+
+def test_learned_magnitudes_keep_the_prior(orc):
+    """Table births that draw the magnitude from a narrow window must leave
+    the magnitude law of the prior (m - 2 ~ Exp(1)): the Hastings terms carry
+    the window density.  Prior mass of the window: e^-1.75 - e^-2.25."""
+    mean, frac, per = _prior_with_magnitudes(orc)
+    _, se = _batch_se(per)
+    assert abs(mean - 1.0) < max(5 * se, 0.05), (mean, se)
+    assert abs(frac - (np.exp(-1.75) - np.exp(-2.25))) < 0.02, frac

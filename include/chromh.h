@@ -257,6 +257,18 @@ const char* cmh_strerror(int code);
  * (a negative or non-finite weight), CMH_ERR_OOM. */
 int cmh_set_birth_table(cmh_model* m, const float* tab, int32_t nx, int32_t ny, int32_t nt, double mix);
 
+/* cmh_set_birth_magnitude: learned magnitudes for the table births.
+ * centre[(iy * nx + ix) * nt + b] (host, copied, finite; the shape of the
+ * table set last) is the centre of entry (ix, iy, b); a table birth at that
+ * entry draws m uniform on [lo, lo + 2 h), lo = max(2, centre - h), h =
+ * half_width > 0, from word 3 of the step's third Philox block (float64,
+ * explicitly rounded).  The mixture density in log alpha becomes
+ * (1 - mix) q_unif p(m) + mix q_net q_win(m), p the magnitude prior.
+ * centre == NULL returns to magnitudes from the prior; a new table drops
+ * them.  Errors: CMH_ERR_STATE (no table), CMH_ERR_ARG (half_width),
+ * CMH_ERR_NONFINITE, CMH_ERR_OOM. */
+int cmh_set_birth_magnitude(cmh_model* m, const float* centre, double half_width);
+
 /* ---- the network behind the learned birth proposal ----------------------------
  * A 1-D convolutional network maps a tile of 8 x 8 stations (100 km apart,
  * 800 km) x 256 samples (features log1p(s^2), layout [window][sample][station])
@@ -281,7 +293,10 @@ int cmh_set_birth_table(cmh_model* m, const float* tab, int32_t nx, int32_t ny, 
  *   station s, row-major from the tile origin tile_origin[2t], [2t+1] in km),
  *   windows every hop_s seconds; each window adds its pixel probabilities
  *   times its time Gaussian's mass per bin to table[(iy*nx + ix)*nt + b]
- *   (pixels of side W/nx, W/ny, nt bins over [0,T)), for cmh_set_birth_table.
+ *   (pixels of side W/nx, W/ny, nt bins over [0,T)), for cmh_set_birth_table;
+ *   magnitude (may be NULL) receives the same weights' mean predicted
+ *   magnitude per entry (3 where no weight was added), for
+ *   cmh_set_birth_magnitude.
  */
 typedef struct cmh_net cmh_net;
 int64_t cmh_net_param_count(void);
@@ -294,7 +309,7 @@ int cmh_net_gradients(cmh_net* n, const float* features, const int32_t* label, c
                       const float* m_label, int32_t batch, float* grads, double* loss);
 int cmh_net_train(cmh_net* n, const cmh_model* geometry, int32_t steps, int32_t batch, double lr, double* loss_out);
 int cmh_net_birth_table(cmh_net* n, cmh_model* m, const int32_t* tiles, const double* tile_origin, int32_t n_tiles,
-                        int32_t nx, int32_t ny, int32_t nt, double hop_s, float* table);
+                        int32_t nx, int32_t ny, int32_t nt, double hop_s, float* table, float* magnitude);
 
 /* ---- autotuning ------------------------------------------------------------
  * cmh_autotune times, from a checkpoint of the model, trial_sweeps sweeps of

@@ -84,7 +84,7 @@ EXPORTS = ["cmh_create_model", "cmh_partition_and_color", "cmh_run_sweeps", "cmh
            "cmh_log_density", "cmh_set_trace", "cmh_read_trace", "cmh_set_timing", "cmh_read_shift",
            "cmh_checkpoint", "cmh_restore", "cmh_destroy", "cmh_strerror", "cmh_philox4x64",
            "cmh_gaussian_loglik_noalloc", "cmh_batch_create", "cmh_batch_run_sweeps", "cmh_batch_destroy",
-           "cmh_autotune", "cmh_batch_sync", "cmh_batch_groups", "cmh_set_birth_table",
+           "cmh_autotune", "cmh_batch_sync", "cmh_batch_groups", "cmh_set_birth_table", "cmh_set_birth_magnitude",
            "cmh_net_param_count", "cmh_net_create", "cmh_net_destroy", "cmh_net_get_params", "cmh_net_set_params",
            "cmh_net_forward", "cmh_net_gradients", "cmh_net_train", "cmh_net_birth_table"]
 
@@ -121,6 +121,7 @@ def _load():
         "cmh_autotune": (C.c_int, [P, i32, C.POINTER(Tuning)]),
         "cmh_batch_sync": (C.c_int, [P]),
         "cmh_set_birth_table": (C.c_int, [P, P, i32, i32, i32, C.c_double]),
+        "cmh_set_birth_magnitude": (C.c_int, [P, P, C.c_double]),
         "cmh_net_param_count": (i64, []),
         "cmh_net_create": (C.c_int, [i32, C.c_uint64, P, C.POINTER(P)]),
         "cmh_net_destroy": (None, [P]),
@@ -129,7 +130,7 @@ def _load():
         "cmh_net_forward": (C.c_int, [P, P, i32, P]),
         "cmh_net_gradients": (C.c_int, [P, P, P, P, P, i32, P, C.POINTER(C.c_double)]),
         "cmh_net_train": (C.c_int, [P, P, i32, i32, C.c_double, C.POINTER(C.c_double)]),
-        "cmh_net_birth_table": (C.c_int, [P, P, P, P, i32, i32, i32, i32, C.c_double, P]),
+        "cmh_net_birth_table": (C.c_int, [P, P, P, P, i32, i32, i32, i32, C.c_double, P, P]),
         "cmh_batch_groups": (C.c_int, [P, C.POINTER(i32), P, P, i32]),
     }
     for name, (res, args) in sig.items():
@@ -218,6 +219,16 @@ class Model:
         t = np.ascontiguousarray(tab, dtype=np.float32)
         ny, nx, nt = t.shape
         _check(lib.cmh_set_birth_table(self._h, _ptr(t), nx, ny, nt, float(mix)), "cmh_set_birth_table")
+
+    def set_birth_magnitude(self, centre, half_width: float = 0.25):
+        """Learned magnitudes for the table births: centre [ny, nx, nt] (the
+        table's shape); a table birth draws m uniform on [lo, lo + 2 h), lo =
+        max(2, centre - h).  None returns to magnitudes from the prior."""
+        if centre is None:
+            _check(lib.cmh_set_birth_magnitude(self._h, None, 0.0), "cmh_set_birth_magnitude")
+            return
+        c = np.ascontiguousarray(centre, dtype=np.float32)
+        _check(lib.cmh_set_birth_magnitude(self._h, _ptr(c), float(half_width)), "cmh_set_birth_magnitude")
 
     def autotune(self, trial_sweeps: int = 8) -> dict:
         """Time each launch configuration from a checkpoint, keep the fastest,
@@ -431,13 +442,18 @@ class Net:
                "cmh_net_train")
         return loss.value
 
-    def birth_table(self, model: Model, tiles, origins, nx: int, ny: int, nt: int, hop_s: float = 12.8):
+    def birth_table(self, model: Model, tiles, origins, nx: int, ny: int, nt: int, hop_s: float = 12.8,
+                    magnitudes: bool = False):
+        """The birth table [ny, nx, nt] of the model's signals; with
+        ``magnitudes`` also the window centres (weighted mean predicted
+        magnitude per entry): returns (table, centres)."""
         t = np.ascontiguousarray(tiles, dtype=np.int32)
         o = np.ascontiguousarray(origins, dtype=np.float64)
         tab = np.zeros((ny, nx, nt), dtype=np.float32)
+        mag = np.zeros((ny, nx, nt), dtype=np.float32) if magnitudes else None
         _check(lib.cmh_net_birth_table(self._h, model._h, _ptr(t), _ptr(o), t.shape[0], nx, ny, nt, float(hop_s),
-                                       _ptr(tab)), "cmh_net_birth_table")
-        return tab
+                                       _ptr(tab), _ptr(mag) if magnitudes else None), "cmh_net_birth_table")
+        return (tab, mag) if magnitudes else tab
 
 
 def grid_tiles(n_side: int, spacing: float, tile: int = 8):

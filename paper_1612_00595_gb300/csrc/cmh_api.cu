@@ -86,6 +86,7 @@ struct cmh_model {
     double* bt_mass = nullptr;        // learned birth table (owned)
     double* bt_cdf = nullptr;
     float* bt_tab = nullptr;
+    float* bt_mag = nullptr;
     double phase_ms = 0.0;
     long long phase_launches = 0;
     int latched = 0;
@@ -915,6 +916,7 @@ void cmh_destroy(cmh_model* m) {
     if (m->bt_mass) cudaFree(m->bt_mass);
     if (m->bt_cdf) cudaFree(m->bt_cdf);
     if (m->bt_tab) cudaFree(m->bt_tab);
+    if (m->bt_mag) cudaFree(m->bt_mag);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
 }
@@ -953,6 +955,7 @@ extern "C" int cmh_set_birth_table(cmh_model* m, const float* tab, int32_t nx, i
     if (m->latched) return CMH_ERR_STATE;
     if (nx == 0) {   // back to uniform births
         m->g.bt_on = 0;
+        m->g.bt_mag_on = 0;
         m->part_gen += 1;
         m->drop_graph();
         return CMH_OK;
@@ -982,9 +985,11 @@ extern "C" int cmh_set_birth_table(cmh_model* m, const float* tab, int32_t nx, i
     if (m->bt_mass) cudaFree(m->bt_mass);
     if (m->bt_cdf) cudaFree(m->bt_cdf);
     if (m->bt_tab) cudaFree(m->bt_tab);
+    if (m->bt_mag) cudaFree(m->bt_mag);
     m->bt_mass = m->bt_cdf = nullptr;
-    m->bt_tab = nullptr;
+    m->bt_tab = m->bt_mag = nullptr;
     m->g.bt_on = 0;
+    m->g.bt_mag_on = 0;
     m->part_gen += 1;
     m->drop_graph();   // the captured sweep holds the old parameters
     if (cudaMalloc(&m->bt_mass, sizeof(double) * np) || cudaMalloc(&m->bt_cdf, sizeof(double) * np * nt) ||
@@ -1010,6 +1015,37 @@ extern "C" int cmh_set_birth_table(cmh_model* m, const float* tab, int32_t nx, i
     m->d.bt_cdf = m->bt_cdf;
     m->d.bt_tab = m->bt_tab;
     m->drop_graph();   // the captured sweep holds the old parameters
+    return CMH_OK;
+}
+
+extern "C" int cmh_set_birth_magnitude(cmh_model* m, const float* centre, double half_width) {
+    if (!m) return CMH_ERR_ARG;
+    if (m->latched) return CMH_ERR_STATE;
+    if (!centre) {   // back to magnitudes from the prior
+        m->g.bt_mag_on = 0;
+        m->part_gen += 1;
+        m->drop_graph();
+        return CMH_OK;
+    }
+    if (!m->g.bt_on) return CMH_ERR_STATE;
+    if (!(half_width > 0.0) || std::isinf(half_width)) return CMH_ERR_ARG;
+    const long long n = (long long)m->g.bt_nx * m->g.bt_ny * m->g.bt_nt;
+    for (long long i = 0; i < n; ++i)
+        if (!std::isfinite(centre[i])) return CMH_ERR_NONFINITE;
+    CK(cudaStreamSynchronize(m->stream));
+    m->g.bt_mag_on = 0;
+    m->part_gen += 1;
+    m->drop_graph();   // the captured sweep holds the old parameters
+    if (!m->bt_mag && cudaMalloc(&m->bt_mag, sizeof(float) * n) != cudaSuccess) {
+        m->bt_mag = nullptr;
+        return CMH_ERR_OOM;
+    }
+    CK(cudaMemcpy(m->bt_mag, centre, sizeof(float) * n, cudaMemcpyHostToDevice));
+    m->d.bt_mag = m->bt_mag;
+    m->g.bt_h = half_width;
+    m->g.bt_h2 = 2.0 * half_width;
+    m->g.bt_ih2 = 1.0 / (2.0 * half_width);
+    m->g.bt_mag_on = 1;
     return CMH_OK;
 }
 

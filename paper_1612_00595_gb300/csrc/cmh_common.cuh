@@ -56,6 +56,10 @@ struct Geo {
     int bt_on, bt_nx, bt_ny, bt_nt;
     double bt_mix, bt_hx, bt_hy, bt_dt, bt_pixarea;
     double bt_ihx, bt_ihy, bt_idt;   // 1 / bt_hx, 1 / bt_hy, 1 / bt_dt
+    // learned magnitudes (bt_mag_on == 0: table births draw m from the prior):
+    // a table birth at an entry draws m uniform on [lo, lo + 2h), lo = max(2, centre - h)
+    int bt_mag_on;
+    double bt_h, bt_h2, bt_ih2;      // h, 2h, 1 / (2h)
 };
 
 // one event store (structure of arrays) with per-cell slices
@@ -96,6 +100,7 @@ struct Dev {
     const double* bt_mass;      // [pixel] table mass of each pixel (learned birth component)
     const double* bt_cdf;       // [pixel][bin] running sum of the pixel's weights / its mass
     const float* bt_tab;        // [pixel][bin] the table's weights as given
+    const float* bt_mag;        // [pixel][bin] centre of the learned magnitude window
 };
 
 // --------------------------------------------------------------------------

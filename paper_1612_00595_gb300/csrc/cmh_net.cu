@@ -393,9 +393,11 @@ __global__ void gather_windows(const float* sig, long long pitch, long long n_sa
 
 // add the network's density of the windows of a tile to a birth table
 // (pixels of the world grid, nt bins over [0, T)): pixel mass (softmax
-// without the "no event" class) times the time Gaussian's mass in each bin
+// without the "no event" class) times the time Gaussian's mass in each bin;
+// with msum, the same weights times the window's predicted magnitude
 __global__ void __launch_bounds__(256) accumulate_table(const float* O, int Bn, double t0, double hop_s, int ox,
-                                                        int oy, int nx, int ny, int nt, double dt, float* tab) {
+                                                        int oy, int nx, int ny, int nt, double dt, float* tab,
+                                                        float* msum) {
     __shared__ float red[32];
     const int b = blockIdx.x;
     const float* o = O + (long long)b * kNOut;
@@ -407,6 +409,7 @@ __global__ void __launch_bounds__(256) accumulate_table(const float* O, int Bn, 
     se = block_sum(se, red);
     const double mu = t0 + b * hop_s + o[kNPix + 1];
     const double sd = exp(fminf(fmaxf(o[kNPix + 2], -4.f), 6.f)) + 1.0;
+    const float mu_m = o[kNPix + 3];
     const int b0 = max(0, (int)floor((mu - 4.0 * sd) / dt)), b1 = min(nt - 1, (int)floor((mu + 4.0 * sd) / dt));
     for (int i = threadIdx.x; i < kNPix; i += blockDim.x) {
         const float p = expf(o[i] - mx) / se;
@@ -416,7 +419,9 @@ __global__ void __launch_bounds__(256) accumulate_table(const float* O, int Bn, 
         float* row = tab + ((long long)gy * nx + gx) * nt;
         for (int q = b0; q <= b1; ++q) {
             const double a = (q * dt - mu) / (sd * 1.4142135623730951), z = ((q + 1) * dt - mu) / (sd * 1.4142135623730951);
-            atomicAdd(row + q, p * (float)(0.5 * (erf(z) - erf(a))));
+            const float wq = p * (float)(0.5 * (erf(z) - erf(a)));
+            atomicAdd(row + q, wq);
+            if (msum) atomicAdd(msum + (row - tab) + q, wq * mu_m);
         }
     }
 }
@@ -738,7 +743,8 @@ extern "C" int cmh_net_train(cmh_net* n, const cmh_model* geometry, int32_t step
 }
 
 extern "C" int cmh_net_birth_table(cmh_net* n, cmh_model* m, const int32_t* tiles, const double* tile_origin,
-                                   int32_t n_tiles, int32_t nx, int32_t ny, int32_t nt, double hop_s, float* table) {
+                                   int32_t n_tiles, int32_t nx, int32_t ny, int32_t nt, double hop_s, float* table,
+                                   float* magnitude) {
     if (!n || !m || !tiles || !tile_origin || n_tiles < 1 || nx < 1 || ny < 1 || nt < 1 || !table || !(hop_s > 0.0))
         return CMH_ERR_ARG;
     (void)cudaGetLastError();
@@ -750,11 +756,14 @@ extern "C" int cmh_net_birth_table(cmh_net* n, cmh_model* m, const int32_t* tile
     cudaStream_t s = n->stream;
     const int hop = std::max(1, (int)std::lround(hop_s * g.f_hz));
     const long long n_win = std::max<long long>(1, (g.n_samp + hop - 1) / hop);
+    const size_t ne = (size_t)nx * ny * nt;
     int* dst = nullptr;
-    float* dtab = nullptr;
+    float *dtab = nullptr, *dmag = nullptr;
     cudaError_t e = cudaMalloc(&dst, sizeof(int) * kNS);
-    if (!e) e = cudaMalloc(&dtab, sizeof(float) * (size_t)nx * ny * nt);
-    if (!e) e = cudaMemsetAsync(dtab, 0, sizeof(float) * (size_t)nx * ny * nt, s);
+    if (!e) e = cudaMalloc(&dtab, sizeof(float) * ne);
+    if (!e) e = cudaMemsetAsync(dtab, 0, sizeof(float) * ne, s);
+    if (!e && magnitude) e = cudaMalloc(&dmag, sizeof(float) * ne);
+    if (!e && magnitude) e = cudaMemsetAsync(dmag, 0, sizeof(float) * ne, s);
     const double dt = g.T / nt;
     for (int ti = 0; ti < n_tiles && !e; ++ti) {
         e = cudaMemcpyAsync(dst, tiles + ti * kNS, sizeof(int) * kNS, cudaMemcpyHostToDevice, s);
@@ -767,14 +776,18 @@ extern "C" int cmh_net_birth_table(cmh_net* n, cmh_model* m, const int32_t* tile
             e = forward(n, Bn);
             if (!e) {
                 accumulate_table<<<Bn, 256, 0, s>>>(n->o, Bn, (double)(w0 * hop) / g.f_hz, hop / g.f_hz, ox, oy, nx, ny,
-                                                    nt, dt, dtab);
+                                                    nt, dt, dtab, dmag);
                 e = cudaGetLastError();
             }
         }
     }
-    if (!e) e = cudaMemcpyAsync(table, dtab, sizeof(float) * (size_t)nx * ny * nt, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(table, dtab, sizeof(float) * ne, cudaMemcpyDeviceToHost, s);
+    if (!e && magnitude) e = cudaMemcpyAsync(magnitude, dmag, sizeof(float) * ne, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
+    if (!e && magnitude)   // weighted mean of the predicted magnitudes; the prior mean where nothing was added
+        for (size_t i = 0; i < ne; ++i) magnitude[i] = table[i] > 0.f ? magnitude[i] / table[i] : 3.f;
     if (dst) cudaFree(dst);
     if (dtab) cudaFree(dtab);
+    if (dmag) cudaFree(dmag);
     return net_err(e);
 }

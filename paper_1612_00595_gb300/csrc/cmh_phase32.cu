@@ -308,14 +308,21 @@ __device__ __forceinline__ double bt_weight(const Geo& g, const Dev& d, const do
 // reciprocal products, the weight is the table's own float and the logarithm
 // is taken in float32 (error ~1e-7 against the float64 form); the sum into
 // log alpha stays float64.  The sampling itself (learned_birth) is exact.
-__device__ __noinline__ double bt_lq(const Geo& g, const Dev& d, const Sm& S, double x, double y, double t) {
+__device__ __noinline__ double bt_lq(const Geo& g, const Dev& d, const Sm& S, double x, double y, double t,
+                                     double m) {
     double qn = 0.0;
     if (S.bt_G > 0.0) {
         int ix = (int)(x * g.bt_ihx), iy = (int)(y * g.bt_ihy), b = (int)(t * g.bt_idt);
         ix = ix < 0 ? 0 : (ix > g.bt_nx - 1 ? g.bt_nx - 1 : ix);
         iy = iy < 0 ? 0 : (iy > g.bt_ny - 1 ? g.bt_ny - 1 : iy);
         b = b < 0 ? 0 : (b > g.bt_nt - 1 ? g.bt_nt - 1 : b);
-        qn = (double)__ldg(d.bt_tab + ((long long)iy * g.bt_nx + ix) * g.bt_nt + b) * S.bt_in;
+        const long long q = ((long long)iy * g.bt_nx + ix) * g.bt_nt + b;
+        qn = (double)__ldg(d.bt_tab + q) * S.bt_in;
+        if (g.bt_mag_on) {
+            // the learned component draws m on its entry's window: q_win(m) / p(m)
+            const double lo = fmax(2.0, __dsub_rn((double)__ldg(d.bt_mag + q), g.bt_h));
+            qn = (m >= lo && m < __dadd_rn(lo, g.bt_h2)) ? qn * g.bt_ih2 * (double)expf((float)(m - 2.0)) : 0.0;
+        }
     }
     return g.lLWT - (double)logf((float)(S.qmu + g.bt_mix * qn));
 }
@@ -323,8 +330,9 @@ __device__ __noinline__ double bt_lq(const Geo& g, const Dev& d, const Sm& S, do
 // a birth from the learned component: pixel by its share of the region's
 // table mass (word w_pix), position uniform in pixel and region (w_x and the
 // third Philox block of the step), time bin by the pixel's cdf, time uniform
-// in the bin
-__device__ __noinline__ void learned_birth(const Geo& g, const Dev& d, const Sm& S, long long sweep, int cell,
+// in the bin, and with learned magnitudes m uniform on the drawn entry's
+// window (word 3 of the third block); returns whether it drew m
+__device__ __noinline__ bool learned_birth(const Geo& g, const Dev& d, const Sm& S, long long sweep, int cell,
                                            int st, unsigned long long w_pix, unsigned long long w_x, P32& e) {
     unsigned long long c2[4] = {(unsigned long long)sweep, (unsigned long long)cell, (unsigned long long)st, 2ULL};
     philox4x64(c2, g.seed, 0ULL);
@@ -350,6 +358,10 @@ __device__ __noinline__ void learned_birth(const Geo& g, const Dev& d, const Sm&
         if (cd[mid] > ub) b1 = mid; else b0 = mid + 1;
     }
     e.t = __dadd_rn(__dmul_rn((double)b0, g.bt_dt), __dmul_rn(u01(c2[2]), g.bt_dt));
+    if (!g.bt_mag_on) return false;
+    const double mlo = fmax(2.0, __dsub_rn((double)d.bt_mag[(long long)S.pidx[j] * g.bt_nt + b0], g.bt_h));
+    e.m = __dadd_rn(mlo, __dmul_rn(u01(c2[3]), g.bt_h2));
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -863,7 +875,7 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
     const int n_blk = S.n_blk;
     // position terms of the own events (the death Hastings term)
     for (int i = tid; i < n0; i += nthr)
-        S.elq[i] = g.bt_on ? bt_lq(g, d, S, S.mx[i], S.my[i], S.mt[i]) : S.lq_unif;
+        S.elq[i] = g.bt_on ? bt_lq(g, d, S, S.mx[i], S.my[i], S.mt[i], S.mm[i]) : S.lq_unif;
     // ---- arrival cache of the own events (warp per event, lanes over slots) -----
     for (int i = wid; i < n0; i += nw) {
         int K;
@@ -995,15 +1007,16 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
         D.bx = D.by = D.bt = D.bm = D.blb = D.blq = 0.0;
         if (D.type == 0) {
             P32 e;
+            bool drew_m = false;
             if (g.bt_on && S.bt_last >= 0 && u01(c1[3]) < g.bt_mix) {
-                learned_birth(g, d, S, sweep, cell, st, c0[2], c0[3], e);
+                drew_m = learned_birth(g, d, S, sweep, cell, st, c0[2], c0[3], e);
             } else {
                 e.x = __dadd_rn(S.rect[0], __dmul_rn(u01(c0[2]), __dsub_rn(S.rect[1], S.rect[0])));
                 e.y = __dadd_rn(S.rect[2], __dmul_rn(u01(c0[3]), __dsub_rn(S.rect[3], S.rect[2])));
                 e.t = __dmul_rn(u01(c1[0]), g.T);
             }
-            e.m = mag_from_u53(c1[1]);
-            D.blq = g.bt_on ? bt_lq(g, d, S, e.x, e.y, e.t) : S.lq_unif;
+            if (!drew_m) e.m = mag_from_u53(c1[1]);
+            D.blq = g.bt_on ? bt_lq(g, d, S, e.x, e.y, e.t, e.m) : S.lq_unif;
             to_rel(g, X0, Y0, e);
             D.bx = e.x; D.by = e.y; D.bt = e.t; D.bm = e.m;
             D.blb = g.lb0 - e.m;
@@ -1130,7 +1143,7 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
                 S.mx[ps] = c.x; S.my[ps] = c.y; S.mt[ps] = c.t; S.mm[ps] = c.m;
                 // a move's own log alpha has no position term: the moved
                 // event's term (for a later death) is taken here
-                S.elq[ps] = S.type[sl] == 0 ? c.lq : (g.bt_on ? bt_lq(g, d, S, c.x, c.y, c.t) : S.lq_unif);
+                S.elq[ps] = S.type[sl] == 0 ? c.lq : (g.bt_on ? bt_lq(g, d, S, c.x, c.y, c.t, c.m) : S.lq_unif);
                 S.exr[ps] = c.xr; S.eyr[ps] = c.yr;
                 for (int a = 0; a < S.ncand[sl]; ++a) S.earr[ps * g.arr_cap + a] = cd[a];
                 S.enarr[ps] = S.ncand[sl];

@@ -287,15 +287,21 @@ def _table_for(w, nx=40, nt=36, seed=3):
     return tab
 
 
-def test_fp32_dry_run_with_learned_birth_table(cm, orc):
+@pytest.mark.parametrize("magnitudes", [False, True])
+def test_fp32_dry_run_with_learned_birth_table(cm, orc, magnitudes):
     """Birth proposals from the mixture with a table: the same candidates on
     both sides (the table draw runs in explicitly rounded float64), Δℓ within
-    1e-4 and log α (which now carries the mixture density) likewise."""
+    1e-4 and log α (which now carries the mixture density) likewise.  With
+    learned magnitudes the table births draw m from their entry's window
+    (float64 on both sides), and the density carries the window."""
     w = small_world(seed=16, W=1000.0, T=3600.0, Lambda=500.0, n_side=10, dtype=np.float32)
     tab = _table_for(w)
     params = cm.make_params(w.params, k_per_phase=32, seed=21, dtype=cm.F32, commit=False)
     m = cm.create_model(w.events, w.stations, w.signals, params)
     m.set_birth_table(tab, 0.5)
+    centre = (2.2 + 2.0 * np.random.default_rng(5).random(tab.shape)).astype(np.float32)
+    if magnitudes:
+        m.set_birth_magnitude(centre, 0.3)
     m.partition_and_color(w.params.L, 1)
     ncx = int(np.floor(w.params.W / w.params.L)) + 2
     m.set_trace(4 * ncx * ncx * 32)
@@ -304,6 +310,8 @@ def test_fp32_dry_run_with_learned_birth_table(cm, orc):
     tr = np.sort(m.read_trace(), order=TRACE_KEYS)
     o = orc.World(w, k_per_phase=32, seed=21, commit=False)
     o.set_birth_table(tab, 0.5)
+    if magnitudes:
+        o.set_birth_magnitude(centre, 0.3)
     _, _, otr, _ = o.run_chromatic(w.events, 4, trace_cap=200000, threads=min(16, os.cpu_count() or 1))
     otr = np.sort(otr, order=TRACE_KEYS)
     assert len(tr) == len(otr)

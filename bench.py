@@ -181,6 +181,23 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def chain_seed(rank: int) -> int:
+    """Seed of rank's chain: every rank runs an independent replica."""
+    return CHAIN_SEED + 1000 * rank
+
+
+def reduce_max_sum(x_max: float, x_sum: float, dist=None, device="cpu"):
+    """(max over ranks of x_max, sum over ranks of x_sum): the job's time is
+    its slowest rank's, its work the sum of the ranks' work."""
+    import torch
+    a = torch.tensor([float(x_max)], dtype=torch.float64, device=device)
+    b = torch.tensor([float(x_sum)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(a, op=dist.ReduceOp.MAX)
+        dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(a.item()), float(b.item())
+
+
 def run_ours(args):
     import torch
 
@@ -200,7 +217,7 @@ def run_ours(args):
     dtype = cm.F32 if f32 else cm.F64
     esz = 4 if f32 else 8
     # each rank runs an independent chain (weak scaling: fixed work per GPU)
-    params = cm.make_params(p, k_per_phase=K_PER_PHASE, seed=CHAIN_SEED + 1000 * rank, dtype=dtype)
+    params = cm.make_params(p, k_per_phase=K_PER_PHASE, seed=chain_seed(rank), dtype=dtype)
     stream = torch.cuda.Stream()
     sig_dev = torch.from_numpy(world.signals).to("cuda", non_blocking=False)
     torch.cuda.synchronize()
@@ -229,13 +246,7 @@ def run_ours(args):
     _, _, _, st1 = m.read_state(cap=0)
     props = sum(st1["proposed"]) - sum(st0["proposed"])
     launches = st1["kernel_launches"] - st0["kernel_launches"]
-    t = torch.tensor([ms], device="cuda")
-    tp = torch.tensor([float(props)], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tp, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    total_props = float(tp.item())
+    ms_max, total_props = reduce_max_sum(ms, props, dist, "cuda")
     value = total_props / (ms_max / 1e3)
     sweeps_per_s = args.steps / (ms_max / 1e3)
 
@@ -284,12 +295,8 @@ def run_ours(args):
     _, _, _, st2 = m2.read_state(cap=0)
     e2e_props = sum(st2["proposed"])
     m2.destroy()
-    te = torch.tensor([e2e_s], device="cuda")
-    tq = torch.tensor([float(e2e_props)], device="cuda")
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tq, op=dist.ReduceOp.SUM)
-    e2e_value = float(tq.item()) / float(te.item())
+    e2e_max, e2e_total = reduce_max_sum(e2e_s, e2e_props, dist, "cuda")
+    e2e_value = e2e_total / e2e_max
     h2d_per_step = world.signals.nbytes / args.steps
 
     if rank == 0:

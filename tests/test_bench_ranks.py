@@ -1,0 +1,53 @@
+"""The multi-rank path of bench.py on CPU: two gloo ranks, as torchrun would
+launch them.  Every rank runs its own chain (replicas); the job's time is the
+slowest rank's and its work the sum over ranks."""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    t, work = bench.reduce_max_sum(1.5 + rank, 10.0 * (rank + 1), dist, "cpu")
+    q.put((rank, t, work, bench.chain_seed(rank)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_max_time_and_the_summed_work():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [o[1] for o in out] == [2.5, 2.5]
+    assert [o[2] for o in out] == [30.0, 30.0]
+    assert out[0][3] != out[1][3]   # independent replicas
+
+
+def test_single_rank_reduction_is_the_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reduce_max_sum(3.0, 7.0) == (3.0, 7.0)

@@ -129,6 +129,7 @@ struct Sm {
     int bt_np, bt_last; // pixel entries; last entry with mass
     int valid[2], idx[2], type[2], ncand[2], ntask[2], units[2], width[2];
     double thr[2];      // accept iff the log-likelihood change exceeds this (log u minus the other terms of log alpha)
+    float thrf[2];      // thr rounded to float32: the decision away from it needs no float64
     double dlp[2];      // log-prior change of the step
     int nb_start[64], nb_cnt[64], nb_off[65];   // neighbouring cells of the region (prologue)
     P32 c[2];           // candidate of each step buffer
@@ -539,6 +540,7 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
                 dlp = -dm;
             }
             S.thr[sl] = thr;
+            S.thrf[sl] = (float)thr;
             S.dlp[sl] = dlp;
         }
         S.valid[sl] = valid && !err;
@@ -1093,9 +1095,19 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
                 if (valid) {
                     ++S.cnt[3 + type];
                     S.cnt[9] += (unsigned long long)S.width[sl];
-                    dll = (double)t.x + (double)t.y;
+                    // float32 first: its gap to the threshold errs by < 3e-7
+                    // (|t.x| + |thr|), so outside 1e-5 of that it decides as
+                    // float64 would; inside, float64 decides
+                    const float gap = (t.x + t.y) - S.thrf[sl];
+                    const float tol = 1e-5f * (fabsf(t.x) + fabsf(S.thrf[sl])) + 1e-30f;
+                    if (gap > tol || gap < -tol) {
+                        acc = gap > 0.f;
+                        if (acc || d.trace) dll = (double)t.x + (double)t.y;
+                    } else {
+                        dll = (double)t.x + (double)t.y;
+                        acc = dll > S.thr[sl];
+                    }
                     dlp = S.dlp[sl];
-                    acc = dll > S.thr[sl];
                     if (d.trace) la = dll + ((double)dr.logu - S.thr[sl]);
                 }
                 if (d.trace) {

@@ -103,6 +103,8 @@ typedef struct {
     int64_t kernel_launches;/* all kernels this model launched */
     uint64_t priced_samples;    /* station samples priced over all evaluated proposals */
     uint64_t rewritten_samples; /* station samples whose variance was re-synthesised */
+    int64_t spill_bytes;    /* float32 regions too large for shared memory: bytes of the global
+                               slot per CTA holding their arrival caches and lists (0: none) */
 } cmh_stats;
 
 /* one record per MH step (optional, cmh_set_trace) */

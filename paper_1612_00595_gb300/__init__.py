@@ -66,14 +66,14 @@ class Stats(C.Structure):
     _fields_ = [("proposed", C.c_uint64 * 3), ("evaluated", C.c_uint64 * 3), ("accepted", C.c_uint64 * 3),
                 ("sweeps", C.c_int64), ("n_events", C.c_int64), ("phase_ms", C.c_double),
                 ("phase_launches", C.c_int64), ("kernel_launches", C.c_int64),
-                ("priced_samples", C.c_uint64), ("rewritten_samples", C.c_uint64)]
+                ("priced_samples", C.c_uint64), ("rewritten_samples", C.c_uint64), ("spill_bytes", C.c_int64)]
 
     def as_dict(self):
         return {"proposed": list(self.proposed), "evaluated": list(self.evaluated),
                 "accepted": list(self.accepted), "sweeps": self.sweeps, "n_events": self.n_events,
                 "phase_ms": self.phase_ms, "phase_launches": self.phase_launches,
                 "kernel_launches": self.kernel_launches, "priced_samples": self.priced_samples,
-                "rewritten_samples": self.rewritten_samples}
+                "rewritten_samples": self.rewritten_samples, "spill_bytes": self.spill_bytes}
 
 
 TRACE_DTYPE = np.dtype([("sweep", "<i4"), ("cell", "<i4"), ("step", "<i4"), ("type", "<i4"),

@@ -562,6 +562,15 @@ int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mo
         if (rc) return rc;
     }
     g.stage_cap = 0;
+    g.task_cap = std::max(32, 2 * g.arr_cap);
+    g.spill = 0;
+    g.spill_bytes = 0;
+    // float32 regions whose arrival caches and lists do not fit in shared
+    // memory keep those in a global slot per CTA
+    if (g.f32 && phase32_smem_bytes(g) > 227 * 1024) {
+        g.spill = 1;
+        g.spill_bytes = (long long)phase32_spill_bytes(g);
+    }
     if (g.f32) CK(choose_stage_cap(g, m->p.stage_samples));
     if ((g.f32 ? phase32_smem_bytes(g) : phase_smem_bytes(g)) > 227 * 1024) return CMH_ERR_CAPACITY;
     if (g.f32)
@@ -618,6 +627,17 @@ int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mo
         if (!idx.empty()) CK(cudaMemcpy(didx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice));
         d.bl_off = doff;
         d.bl_idx = didx;
+    }
+    if (g.spill) {
+        // one slot per CTA that may run a region at once: every region of a
+        // colour (colour-by-colour launch) or every resident CTA (persistent)
+        int dev = 0, n_sm = 1;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+        const size_t slots = (size_t)std::max(g.max_rpc, 3 * n_sm);
+        if ((e = m->alloc(&d.spill_buf, slots * (size_t)g.spill_bytes, true))) return cuda_err(e);
+    } else {
+        d.spill_buf = nullptr;
     }
     CK(cudaMemsetAsync(d.done, 0, sizeof(long long) * g.n_cells, m->stream));
     CK(cudaMemsetAsync(d.colour_off, 0, sizeof(int) * (kMaxColours + 1), m->stream));
@@ -732,6 +752,7 @@ int cmh_read_state(cmh_model* m, cmh_event* out, uint64_t* ids_out, int64_t cap,
         stats_out->kernel_launches = m->launches;
         stats_out->priced_samples = st[9];
         stats_out->rewritten_samples = st[10];
+        stats_out->spill_bytes = m->partitioned && m->g.spill ? m->g.spill_bytes : 0;
     }
     return CMH_OK;
 }

@@ -35,6 +35,11 @@ struct Geo {
     unsigned long long seed;
     int ev_cap, blk_cap, frz_cap, arr_cap;
     int stage_cap;      // floats per shared-memory staging buffer of the float32 phase (0: none)
+    int task_cap;       // stations one float32 step may touch (old and new arrivals)
+    // float32 regions too large for shared memory: their event arrival caches
+    // and station arrival lists live in a global scratch slot per CTA
+    int spill;
+    long long spill_bytes;   // bytes of one slot
     long long store_cap, max_events;
     int f32;
     int threads;
@@ -97,6 +102,7 @@ struct Dev {
     const float* stxf;          // float copies of the station coordinates
     const float* styf;
     const double* log_n;        // [ev_cap + 2] log(n) table, computed on the host
+    unsigned char* spill_buf;   // [CTA slots][spill_bytes] (float32 regions with spill)
     const double* bt_mass;      // [pixel] table mass of each pixel (learned birth component)
     const double* bt_cdf;       // [pixel][bin] running sum of the pixel's weights / its mass
     const float* bt_tab;        // [pixel][bin] the table's weights as given
@@ -296,6 +302,7 @@ cudaError_t prepare_rebin(const Geo& g);
 cudaError_t launch_phase(const Geo& g, const Dev& d, int colour, cudaStream_t s);
 cudaError_t launch_phase32(const Geo& g, const Dev& d, int colour, cudaStream_t s);
 size_t phase32_smem_bytes(const Geo& g);
+size_t phase32_spill_bytes(const Geo& g);   // bytes of one CTA's global slot if the region spills
 cudaError_t prepare_phase32(const Geo& g);
 cudaError_t choose_stage_cap(Geo& g, int requested);
 cudaError_t sweep32_grid(const Geo& g, int ctas_per_sm, int* grid);

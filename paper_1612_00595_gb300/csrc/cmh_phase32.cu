@@ -45,7 +45,6 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr float kDr = 2e-3f;   // km: margin of the region tests
 constexpr float kDm = 1e-5f;   // magnitude units: margin of the m >= 2 test
 constexpr int kThreads32 = 256;
-constexpr int kMaxTasks32 = 32;
 constexpr int kUnroll = 2;     // float4 groups whose loads a pricing thread issues together
 constexpr int kFrozen = -2;    // owner tag of an arrival from a neighbouring region
 constexpr int kMinBlocks32 = 3;   // resident CTAs per SM the kernel is built for
@@ -108,11 +107,11 @@ struct Sm {
     SA* sarr;           // [blk_cap][scap]
     D32* draws;
     A32* cand;          // [2][arr_cap]
-    T32* tasks;         // [2][kMaxTasks32]
+    T32* tasks;         // [2][task_cap]
     double *nx, *ny, *nt;
     float *nph, *nmf;
     int* nK;
-    int* tsoff;         // [2][kMaxTasks32] staging offset of each task's window (floats), -1: global
+    int* tsoff;         // [2][task_cap] staging offset of each task's window (floats), -1: global
     float* stage_s;     // [2][scap] staged signal windows
     float* stage_v;     // [2][scap] staged variance windows
     int scap;           // floats per staging buffer (0: no staging)
@@ -140,13 +139,22 @@ struct Sm {
     unsigned long long cnt[11];
 };
 
-// carve the dynamic shared buffer; returns its size (base may be null)
-__host__ __device__ inline size_t layout32(const Geo& g, Sm* S, unsigned char* base) {
-    size_t o = 0;
+// carve the dynamic shared buffer; returns its size (base may be null).  With
+// g.spill the event arrival caches and the station arrival lists come from
+// the CTA's global slot gbase instead, and *gbytes receives their size.
+__host__ __device__ inline size_t layout32(const Geo& g, Sm* S, unsigned char* base, unsigned char* gbase = nullptr,
+                                           size_t* gbytes = nullptr) {
+    size_t o = 0, go = 0;
     auto take = [&](size_t bytes) {
         size_t r = o;
         o += (bytes + 15) & ~size_t(15);
         return base + r;
+    };
+    auto gtake = [&](size_t bytes) {
+        if (!g.spill) return take(bytes);
+        size_t r = go;
+        go += (bytes + 15) & ~size_t(15);
+        return gbase + r;
     };
     const size_t E = g.ev_cap, B = g.blk_cap;
     double *mx = (double*)take(8 * E), *my = (double*)take(8 * E), *mt = (double*)take(8 * E),
@@ -154,7 +162,7 @@ __host__ __device__ inline size_t layout32(const Geo& g, Sm* S, unsigned char* b
     unsigned long long* eid = (unsigned long long*)take(8 * E);
     float *exr = (float*)take(4 * E), *eyr = (float*)take(4 * E);
     int *enarr = (int*)take(4 * E), *order = (int*)take(4 * E), *freel = (int*)take(4 * E);
-    A32* earr = (A32*)take(sizeof(A32) * E * g.arr_cap);
+    A32* earr = (A32*)gtake(sizeof(A32) * E * g.arr_cap);
     double *tabB = (double*)take(8 * (E + 1)), *tabD = (double*)take(8 * (E + 1));
     double* elq = (double*)take(8 * E);
     double* pcum = (double*)take(8 * kMaxPix);
@@ -162,14 +170,14 @@ __host__ __device__ inline size_t layout32(const Geo& g, Sm* S, unsigned char* b
     int* bsta = (int*)take(4 * B);
     double *bx = (double*)take(8 * B), *by = (double*)take(8 * B);
     int* scnt = (int*)take(4 * B);
-    SA* sarr = (SA*)take(sizeof(SA) * B * g.frz_cap);
+    SA* sarr = (SA*)gtake(sizeof(SA) * B * g.frz_cap);
     D32* draws = (D32*)take(sizeof(D32) * (size_t)g.k);
     A32* cand = (A32*)take(sizeof(A32) * 2 * (size_t)g.arr_cap);
-    T32* tasks = (T32*)take(sizeof(T32) * 2 * kMaxTasks32);
+    T32* tasks = (T32*)take(sizeof(T32) * 2 * (size_t)g.task_cap);
     double *nx = (double*)take(8 * E), *ny = (double*)take(8 * E), *nt = (double*)take(8 * E);
     float *nph = (float*)take(4 * E), *nmf = (float*)take(4 * E);
     int* nK = (int*)take(4 * E);
-    int* tsoff = (int*)take(4 * 2 * kMaxTasks32);
+    int* tsoff = (int*)take(4 * 2 * (size_t)g.task_cap);
     const size_t scap = (size_t)g.stage_cap;
     float* stage_s = scap ? (float*)take(4 * 2 * scap) : nullptr;
     float* stage_v = scap ? (float*)take(4 * 2 * scap) : nullptr;
@@ -184,6 +192,7 @@ __host__ __device__ inline size_t layout32(const Geo& g, Sm* S, unsigned char* b
         S->scnt = scnt; S->sarr = sarr; S->draws = draws; S->cand = cand; S->tasks = tasks;
         S->nx = nx; S->ny = ny; S->nt = nt; S->nph = nph; S->nmf = nmf; S->nK = nK;
     }
+    if (gbytes) *gbytes = go;
     return o;
 }
 
@@ -387,7 +396,7 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
     const D32& dr = S.draws[step];
     const int n_own = S.n_own, n_blk = S.n_blk;
     A32* cd = S.cand + sl * g.arr_cap;
-    T32* tk = S.tasks + sl * kMaxTasks32;
+    T32* tk = S.tasks + sl * g.task_cap;
     int valid = 0, idx = -1, ps = -1;
     P32 c;
     c.x = c.y = c.t = c.m = 0.0;
@@ -459,7 +468,7 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
             while (io < no || in < nnw) {
                 const int so = io < no ? oa[io].slot : 1 << 30;
                 const int sn = in < nnw ? cd[in].slot : 1 << 30;
-                if (ntask >= kMaxTasks32) {
+                if (ntask >= g.task_cap) {
                     err = CMH_ERR_CAPACITY;
                     break;
                 }
@@ -498,7 +507,7 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
         }
         if (STAGE && !err && ntask > 0) {
             // stage the windows that fit (in task order) into this step's buffer
-            int* so = S.tsoff + sl * kMaxTasks32;
+            int* so = S.tsoff + sl * g.task_cap;
             int used = 0;
             unsigned bytes = 0;
             for (int ti = 0; ti < ntask; ++ti) {
@@ -564,10 +573,10 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
 template <bool STAGE>
 __device__ __forceinline__ void price_step(const Geo& g, const Dev& d, Sm& S, int sl) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const T32* tk = S.tasks + sl * kMaxTasks32;
+    const T32* tk = S.tasks + sl * g.task_cap;
     const int U = S.units[sl], ntask = S.ntask[sl];
     const int wt = threadIdx.x - 32, nwk = blockDim.x - 32;
-    const int* so = S.tsoff + sl * kMaxTasks32;
+    const int* so = S.tsoff + sl * g.task_cap;
     const float* ss = STAGE ? S.stage_s + sl * S.scap : nullptr;
     const float* sv_ = STAGE ? S.stage_v + sl * S.scap : nullptr;
     if (STAGE && S.on[sl] && !mbar_wait(&S.bar[sl], (unsigned)S.ph[sl])) atomicCAS(&S.err, 0, CMH_ERR_TIMEOUT);
@@ -746,7 +755,7 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
     const int ix = cell % g.ncx, iy = cell / g.ncx;
     const int start = St.start[cell], n0 = St.count[cell];
     if (tid == 0) {
-        layout32(g, &S, smem);
+        layout32(g, &S, smem, g.spill ? d.spill_buf + (size_t)blockIdx.x * (size_t)g.spill_bytes : nullptr);
         S.cell = cell;
         S.sx = d.shift[0];
         S.sy = d.shift[1];
@@ -1169,7 +1178,7 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
         // while the workers re-synthesise V; with staging its bulk copies
         // read V, so it follows the re-synthesis.
         if (S.acc) {
-            const T32* tk = S.tasks + sl * kMaxTasks32;
+            const T32* tk = S.tasks + sl * g.task_cap;
             const int rt = STAGE ? tid : tid - 32, rn = STAGE ? nthr : nthr - 32;
             if (!STAGE && wid == 0) {
                 if (step + 1 < g.k) prepare_step<STAGE>(g, d, S, step + 1, sl ^ 1);
@@ -1445,6 +1454,14 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_batch(const 
 }  // namespace
 
 size_t phase32_smem_bytes(const Geo& g) { return layout32(g, nullptr, nullptr); }
+
+size_t phase32_spill_bytes(const Geo& g) {
+    Geo h = g;
+    h.spill = 1;
+    size_t go = 0;
+    layout32(h, nullptr, nullptr, nullptr, &go);
+    return go;
+}
 
 cudaError_t prepare_sweep32_batch(size_t smem_bytes, int* grid) {
     cudaError_t e = raise_smem_limit((const void*)sweep32_batch, smem_bytes);

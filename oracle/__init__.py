@@ -53,7 +53,7 @@ class _Params(C.Structure):
                  "R_max", "L", "p_birth", "p_death", "sig_xy", "sig_t", "sig_m")] + [
         ("n_w", C.c_int32), ("k_per_phase", C.c_int32), ("seed", C.c_uint64), ("commit", C.c_int32),
         ("lattice", C.c_int32), ("lat_nx", C.c_int32), ("lat_ny", C.c_int32), ("lat_nt", C.c_int32),
-        ("lat_nm", C.c_int32), ("lat_nmax", C.c_int32), ("pad0", C.c_int32)] + [
+        ("lat_nm", C.c_int32), ("lat_nmax", C.c_int32), ("likelihood", C.c_int32)] + [
         (n, C.c_double) for n in ("lat_x0", "lat_dx", "lat_y0", "lat_dy", "lat_t0", "lat_dt",
                                   "lat_m0", "lat_dm")]
 
@@ -155,6 +155,7 @@ class World:
         prm.k_per_phase = k_per_phase
         prm.seed = seed
         prm.commit = 1 if commit else 0
+        prm.likelihood = 1 if getattr(p, "likelihood", "variance") == "mean" else 0
         if lattice is not None:
             prm.lattice = 1
             for n in ("nx", "ny", "nt", "nm", "nmax"):

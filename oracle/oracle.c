@@ -17,6 +17,8 @@
  *          k in [ceil(a f), ceil(a f) + n_w), A = exp(alpha m - beta_att d),
  *          g(u) = exp(-u / tau)
  *   s_jk ~ N(0, V_jk), V_jk = noise_var + sum of the variances above
+ * or, with the additive-mean reading (likelihood = 1), each arrival adds
+ * A g(k/f - a) to the mean: s_jk ~ N(mu_jk, noise_var), mu_jk = that sum
  */
 #include "oracle.h"
 
@@ -255,16 +257,29 @@ static arr_t arrival_of(const orc_world* w, const ev_t* e, int32_t j) {
     return r;
 }
 
-/* variance this arrival adds at sample k */
+/* what this arrival adds at sample k to the predicted quantity: the variance
+ * (A e^{-u/tau})^2 of the zero-mean sample, or with the additive-mean
+ * reading the mean A e^{-u/tau} */
 static double arr_var(const orc_world* w, const arr_t* r, int64_t k) {
     if (!r->reach || k < r->k0 || k >= r->k0 + w->p.n_w) return 0.0;
     double u = (double)k / w->p.f_hz - r->a;
     double sd = r->amp * exp(-u / w->p.tau);
+    if (w->p.likelihood) return sd;
     return ORC_MUTANT == 3 ? sd : sd * sd;
 }
 
+/* the predicted quantity with no arrival: the noise variance, or mean 0 */
+static double pred_base(const orc_world* w) { return w->p.likelihood ? 0.0 : w->p.noise_var; }
+
 static double log_normal0(double s, double V) {
     return -0.5 * log(2.0 * M_PI * V) - s * s / (2.0 * V);
+}
+
+/* log density of sample s given the predicted quantity P */
+static double log_lik_sample(const orc_world* w, double s, double P) {
+    if (!w->p.likelihood) return log_normal0(s, P);
+    const double r = s - P;
+    return -0.5 * log(2.0 * M_PI * w->p.noise_var) - r * r / (2.0 * w->p.noise_var);
 }
 
 void orc_variance(const orc_world* w, const double* ev, int64_t n, int32_t j,
@@ -277,7 +292,7 @@ void orc_variance(const orc_world* w, const double* ev, int64_t n, int32_t j,
         if (a.reach) ar[na++] = a;
     }
     for (int64_t k = k0; k < k1; ++k) {
-        double V = w->p.noise_var;
+        double V = pred_base(w);
         for (int64_t i = 0; i < na; ++i) V += arr_var(w, &ar[i], k);
         out[k - k0] = V;
     }
@@ -289,7 +304,7 @@ double orc_log_likelihood(const orc_world* w, const double* ev, int64_t n) {
     double* V = (double*)malloc(sizeof(double) * (size_t)(w->n_samp > 0 ? w->n_samp : 1));
     for (int32_t j = 0; j < w->n_st; ++j) {
         orc_variance(w, ev, n, j, 0, w->n_samp, V);
-        for (int64_t k = 0; k < w->n_samp; ++k) total += log_normal0(sig_at(w, j, k), V[k]);
+        for (int64_t k = 0; k < w->n_samp; ++k) total += log_lik_sample(w, sig_at(w, j, k), V[k]);
     }
     free(V);
     return total;
@@ -373,12 +388,12 @@ static double delta_ll2(const orc_world* w, const ev_t* own, int64_t n_own, cons
             if (a.reach) ar[na++] = a;
         }
         for (int64_t k = lo; k < hi; ++k) {
-            double base = w->p.noise_var;
+            double base = pred_base(w);
             for (int64_t i = 0; i < na; ++i) base += arr_var(w, &ar[i], k);
             double V_old = base + arr_var(w, &ao, k);
             double V_new = base + arr_var(w, &an, k);
             double s = sig_at(w, j, k);
-            total += log_normal0(s, V_new) - log_normal0(s, V_old);
+            total += log_lik_sample(w, s, V_new) - log_lik_sample(w, s, V_old);
         }
     }
     free(ar);

@@ -37,7 +37,8 @@ typedef struct {
     /* lattice mode (exact-enumeration tests): coordinates on a finite grid */
     int32_t lattice;
     int32_t lat_nx, lat_ny, lat_nt, lat_nm, lat_nmax;
-    int32_t pad0;
+    int32_t likelihood;   /* 0: arrivals add to the variance of a zero-mean sample;
+                             1: they add to its mean, the variance is the noise's */
     double lat_x0, lat_dx, lat_y0, lat_dy, lat_t0, lat_dt, lat_m0, lat_dm;
 } orc_params;
 

@@ -9,6 +9,8 @@
 * The windowed log-likelihood change of a proposal against the brute-force
   difference of two full log-likelihoods.
 * The prior against the Poisson / uniform / exponential densities.
+* The same three likelihood pins for the additive-mean reading (arrivals add
+  to the mean, the variance is the noise's).
 """
 import math
 import os
@@ -157,4 +159,71 @@ def test_delta_matches_full_difference(orc, seed):
             d = o.delta_loglik(ev, i, cand)
         full = o.log_likelihood(new) - base
         assert d == pytest.approx(full, rel=1e-9, abs=1e-7)
+        ev, base = new, o.log_likelihood(new)
+
+
+# ---- the additive-mean reading: arrivals add A g(u) to the mean of a sample
+# whose variance is the noise's --------------------------------------------
+def test_mean_reading_loglik_closed_form(orc):
+    # the world of test_loglik_closed_form with noise variance 2: amplitude e
+    # (alpha m = 1), envelope exp(-u) for u in {0, 1}: means e, 1, 0
+    s = np.array([0.0, 1.0, -2.0])
+    w = _world([(0.0, 0.0)], s[None, :], W=10.0, T=3.0, Lambda=1.0, v=6.0, alpha=0.5,
+               beta_att=0.0, tau=1.0, t_s=2.0, f_hz=1.0, R_max=5.0, noise_var=2.0, likelihood="mean")
+    o = orc.World(w)
+    ev = np.array([[0.0, 0.0, 0.0, 2.0]])
+    mu = np.array([math.e, 1.0, 0.0])
+    assert np.allclose(o.variance(ev, 0, 0, 3), mu, rtol=1e-15, atol=0)
+    want = stats.norm.logpdf(s, mu, math.sqrt(2.0)).sum()
+    assert o.log_likelihood(ev) == pytest.approx(want, rel=1e-14)
+    assert o.log_likelihood(np.zeros((0, 4))) == pytest.approx(
+        stats.norm.logpdf(s, 0.0, math.sqrt(2.0)).sum(), rel=1e-14)
+
+
+def test_mean_reading_matches_generative_draws(orc):
+    # E[s] = mu and Var[s] = noise at every sample of the generative story
+    p = worldgen.ModelParams(W=100.0, T=40.0, Lambda=1.0, tau=4.0, t_s=20.0, f_hz=5.0, R_max=50.0,
+                             alpha=1.0, beta_att=0.02, noise_var=1.5, likelihood="mean")
+    st = np.array([[40.0, 50.0]])
+    ev = np.array([[55.0, 45.0, 3.3, 2.7]])
+    n_rep = 3000
+    s1 = np.zeros(p.n_samples)
+    s2 = np.zeros(p.n_samples)
+    for r in range(n_rep):
+        x = worldgen.make_world(p, st, seed=20_000 + r, events=ev).signals[0]
+        s1 += x
+        s2 += x * x
+    mean = s1 / n_rep
+    var = s2 / n_rep - mean ** 2
+    o = orc.World(worldgen.World(params=p, stations=st, signals=np.zeros((1, p.n_samples)), events=ev))
+    mu = o.variance(ev, 0, 0, p.n_samples)
+    assert mu.max() > 5.0   # the event is visible
+    z = (mean - mu) / math.sqrt(p.noise_var / n_rep)
+    assert np.max(np.abs(z)) < 5.5
+    assert np.max(np.abs(var / p.noise_var - 1.0)) < 6 * math.sqrt(2.0 / n_rep)
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_mean_reading_delta_matches_full_difference(orc, seed):
+    rng = np.random.default_rng(seed)
+    p = worldgen.ModelParams(W=300.0, T=300.0, Lambda=8.0, f_hz=2.0, t_s=60.0, tau=10.0, likelihood="mean")
+    w = worldgen.make_world(p, worldgen.jittered_grid_stations(3, p.W, seed), seed)
+    o = orc.World(w)
+    ev = w.events.copy()
+    base = o.log_likelihood(ev)
+    for trial in range(9):
+        kind = trial % 3
+        if kind == 0 or len(ev) == 0:
+            cand = np.array([rng.uniform(0, p.W), rng.uniform(0, p.W), rng.uniform(0, p.T), 2 + rng.exponential()])
+            new, d = np.vstack([ev, cand]), o.delta_loglik(ev, -1, cand)
+        elif kind == 1:
+            i = int(rng.integers(len(ev)))
+            new, d = np.delete(ev, i, axis=0), o.delta_loglik(ev, i, None)
+        else:
+            i = int(rng.integers(len(ev)))
+            cand = ev[i] + rng.normal(0, [5.0, 5.0, 2.0, 0.1])
+            new = ev.copy()
+            new[i] = cand
+            d = o.delta_loglik(ev, i, cand)
+        assert d == pytest.approx(o.log_likelihood(new) - base, rel=1e-9, abs=1e-7)
         ev, base = new, o.log_likelihood(new)

@@ -68,6 +68,10 @@ class ModelParams:
     R_max: float = 50.0
     L: float = 100.0
     n_samples: Optional[int] = None
+    # "variance": each arrival adds (A e^{-u/tau})^2 to the variance of a
+    # zero-mean sample; "mean": it adds A e^{-u/tau} to the mean of a sample
+    # whose variance is the noise (the additive reading)
+    likelihood: str = "variance"
 
     def __post_init__(self):
         if self.n_samples is None:
@@ -132,7 +136,9 @@ def sample_events(p: ModelParams, seed: int) -> np.ndarray:
 
 def _station_row(p: ModelParams, st: np.ndarray, events: np.ndarray, j: int,
                  seed: int, dtype) -> np.ndarray:
-    """One station's record: background noise plus one Gaussian signal per arrival."""
+    """One station's record: background noise plus, per arrival, a Gaussian
+    signal of that envelope (variance reading) or the envelope itself (mean
+    reading)."""
     rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 0x5160, j])))
     ns = p.n_samples
     if dtype == np.float32:
@@ -153,7 +159,10 @@ def _station_row(p: ModelParams, st: np.ndarray, events: np.ndarray, j: int,
         k = np.arange(lo, hi, dtype=np.float64)
         amp = math.exp(p.alpha * events[i, 3] - p.beta_att * dist[i])
         sd = amp * np.exp(-(k / p.f_hz - arrival) / p.tau)
-        row[lo:hi] += (sd * rng.standard_normal(hi - lo)).astype(row.dtype)
+        if p.likelihood == "mean":
+            row[lo:hi] += sd.astype(row.dtype)
+        else:
+            row[lo:hi] += (sd * rng.standard_normal(hi - lo)).astype(row.dtype)
     return row
 
 

@@ -72,10 +72,11 @@ def _traffic():
     return float(rec["dram_bytes_per_launch"]), rec.get("command", "")
 
 
-def _workload(name: str):
+def _workload(name: str, likelihood: str = "variance"):
     if name == "scale":
-        return worldgen.config_scale(seed=SEED), "fp32 sweep at scale: 4000x4000 km, 24 h, ~1e4 events, " \
-                                                 "1600 stations x 864000 f32 samples, 40x40 regions, k=32"
+        return worldgen.config_scale(seed=SEED, likelihood=likelihood), \
+            "fp32 sweep at scale: 4000x4000 km, 24 h, ~1e4 events, 1600 stations x 864000 f32 samples, " \
+            "40x40 regions, k=32" + ("" if likelihood == "variance" else ", additive-mean likelihood reading")
     if name == "replay":
         return worldgen.config_replay(seed=SEED), "fp64 replay: 1000x1000 km, 1 h, ~500 events, " \
                                                   "100 stations x 36000 f64 samples, 10x10 regions, k=32"
@@ -168,7 +169,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    world, desc = _workload(args.workload)
+    world, desc = _workload(args.workload, args.likelihood)
     base = _cpu_baseline(world, seconds_target=max(5.0, 3.0 * args.steps / 10.0))
     line = {"impl": "reference", "metric": "MH proposals/sec and sweeps/sec on 1 GB300",
             "value": base["value"], "unit": "proposals/s", "n_gpus": args.gpus, "steps": args.steps,
@@ -211,7 +212,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_1612_00595_gb300 as cm
 
-    world, desc = _workload(args.workload)
+    world, desc = _workload(args.workload, args.likelihood)
     p = world.params
     f32 = world.signals.dtype == np.float32
     dtype = cm.F32 if f32 else cm.F64
@@ -267,7 +268,12 @@ def run_ours(args):
     per_launch_s = phase_ms / 1e3 / max(n_launch, 1)
     peaks, peak_kind = _peaks()
     achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
-    traffic, traffic_src = _traffic() if f32 else (None, "float64 path not captured")
+    if not f32:
+        traffic, traffic_src = None, "float64 path not captured"
+    elif args.likelihood != "variance":
+        traffic, traffic_src = None, "the ncu capture is of the variance reading"
+    else:
+        traffic, traffic_src = _traffic()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": traffic_src,
             "kernel": "sweep32_kernel<false> (one launch per sweep: all colour phases)" if f32
@@ -486,6 +492,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scale", choices=["scale", "replay", "batched", "learned"])
+    ap.add_argument("--likelihood", default="variance", choices=["variance", "mean"],
+                    help="scale workload: arrivals add to the sample variance (default) or to its mean")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -85,6 +85,10 @@ typedef struct {
                               per colour phase.  The float64 form always runs colour by colour */
     int32_t ctas_per_sm;   /* schedule 0: resident CTAs per SM of the persistent launch
                               (1..3; 0: as many as fit, at most 3) */
+    int32_t likelihood;    /* 0: an arrival adds (A g(u))^2 to the variance of a zero-mean
+                              sample (the default reading); 1 (CMH_F32 only): it adds A g(u)
+                              to the sample's mean and the variance is noise_var (the
+                              additive reading) */
     int64_t max_events;    /* capacity of the whole event store; 0: 4 (n0 + Lambda) + 4096 */
 } cmh_params;
 
@@ -225,8 +229,8 @@ const char* cmh_strerror(int code);
  * cmh_run_sweeps gives each model alone.
  *
  * cmh_batch_create: models[0..n_models) must be distinct, partitioned, of
- *   dtype CMH_F32, without staging (stage_samples 0) and with ev_capacity
- *   <= 512 (CMH_ERR_ARG otherwise; CMH_ERR_STATE for an unpartitioned or
+ *   dtype CMH_F32 and one likelihood reading, without staging (stage_samples
+ *   0) and with ev_capacity <= 512 (CMH_ERR_ARG otherwise; CMH_ERR_STATE for an unpartitioned or
  *   failed model).  The batch refers to the models (it does not own them)
  *   and to their current partitions; cuda_stream may be NULL (the batch
  *   creates its own).  Destroy the batch before its models.

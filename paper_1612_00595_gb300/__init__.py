@@ -42,7 +42,7 @@ class Params(C.Structure):
         ("k_per_phase", C.c_int32), ("commit", C.c_int32), ("seed", C.c_uint64), ("dtype", C.c_int32),
         ("ev_capacity", C.c_int32), ("frozen_capacity", C.c_int32), ("block_threads", C.c_int32),
         ("stage_samples", C.c_int32), ("schedule", C.c_int32), ("ctas_per_sm", C.c_int32),
-        ("max_events", C.c_int64)]
+        ("likelihood", C.c_int32), ("max_events", C.c_int64)]
 
 
 class Tuning(C.Structure):
@@ -175,6 +175,7 @@ def make_params(model_params, *, k_per_phase=32, seed=1, dtype=F64, p_birth=0.25
     p.stage_samples = stage_samples
     p.schedule = schedule
     p.ctas_per_sm = ctas_per_sm
+    p.likelihood = 1 if getattr(model_params, "likelihood", "variance") == "mean" else 0
     p.max_events = max_events
     return p
 

@@ -210,6 +210,7 @@ int validate_params(const cmh_params* p) {
     if (!(p->p_birth > 0.0 && p->p_death > 0.0 && p->p_birth + p->p_death < 1.0)) return CMH_ERR_ARG;
     if (p->k_per_phase < 1 || p->k_per_phase > kMaxK) return CMH_ERR_ARG;
     if (p->dtype != CMH_F32 && p->dtype != CMH_F64) return CMH_ERR_ARG;
+    if (p->likelihood != 0 && !(p->likelihood == 1 && p->dtype == CMH_F32)) return CMH_ERR_ARG;
     if (p->ev_capacity < 0 || p->frozen_capacity < 0 || p->max_events < 0) return CMH_ERR_ARG;
     if (p->stage_samples < -1 || (p->schedule != 0 && p->schedule != 1) || p->ctas_per_sm < 0 || p->ctas_per_sm > 3)
         return CMH_ERR_ARG;
@@ -386,8 +387,13 @@ int cmh_create_model(const cmh_event* init_events, int64_t n_events, const cmh_s
     g.threads = m->p.block_threads;
     g.max_events = m->p.max_events;
     g.fv_f = (float)(p->f_hz / p->v);
-    g.twoftau_f = (float)(2.0 / (p->f_hz * p->tau));
-    g.kap_f = (float)(2.0 * 1.4426950408889634074 / (p->f_hz * p->tau));
+    g.mean_mode = p->likelihood == 1;
+    const double pw = g.mean_mode ? 1.0 : 2.0;
+    g.apow_f = (float)pw;
+    g.syn0_f = g.mean_mode ? 0.f : (float)p->noise_var;
+    g.inv_noise_f = (float)(1.0 / p->noise_var);
+    g.twoftau_f = (float)(pw / (p->f_hz * p->tau));
+    g.kap_f = (float)(pw * 1.4426950408889634074 / (p->f_hz * p->tau));
     for (int e = 0; e < 4; ++e) g.rho_f[e] = (float)std::exp2(-(double)g.kap_f * e);
     g.alpha_f = (float)p->alpha;
     g.beta_f = (float)p->beta_att;
@@ -1229,6 +1235,7 @@ extern "C" int cmh_batch_create(cmh_model* const* models, int32_t n_models, void
         b->max_ev_cap = std::max(b->max_ev_cap, m->g.ev_cap);
         const size_t sm = phase32_smem_bytes(m->g);
         if (sm > 227 * 1024) return fail(CMH_ERR_CAPACITY);
+        if (m->g.mean_mode != models[0]->g.mean_mode) return fail(CMH_ERR_ARG);   // one likelihood reading per batch
         // region CTAs of this model that fit on one SM (static shared memory ~2 KB)
         fit[i] = std::max(1, std::min(3, (int)(per_sm / (sm + 2048 + (size_t)reserved))));
     }
@@ -1275,7 +1282,9 @@ extern "C" int cmh_batch_create(cmh_model* const* models, int32_t n_models, void
     if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
     for (BatchGroup& r : b->groups) {
         if (e == cudaSuccess) e = cudaStreamWaitEvent(r.stream, b->fork, 0);
-        if (e == cudaSuccess) e = launch_sweep32_batch(r.G, r.D, r.n, r.n_col, r.item_tab, r.queue, r.smem, r.grid, r.stream);
+        if (e == cudaSuccess)
+            e = launch_sweep32_batch(hg[0].mean_mode != 0, r.G, r.D, r.n, r.n_col, r.item_tab, r.queue, r.smem, r.grid,
+                                     r.stream);
         if (e == cudaSuccess) e = cudaEventRecord(r.done, r.stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, r.done, 0);
     }

@@ -46,8 +46,16 @@ struct Geo {
     // float32 form of the model constants (host-computed)
     float invL_f;      // 1 / L
     float fv_f;        // f / v
-    float twoftau_f;   // 2 / (f tau)
-    float kap_f;       // 2 log2(e) / (f tau): per-sample decay of log2 of a variance
+    // likelihood reading: 0 = arrivals add (A g)^2 to the variance of a
+    // zero-mean sample (V buffer = variance), 1 = they add A g to its mean
+    // (V buffer = mean; the variance is the noise's).  p = 2 or 1 is the power
+    // of the envelope that an arrival contributes.
+    int mean_mode;
+    float apow_f;      // p
+    float syn0_f;      // the predicted quantity without arrivals: noise variance, or 0
+    float inv_noise_f; // 1 / noise variance (mean reading)
+    float twoftau_f;   // p / (f tau)
+    float kap_f;       // p log2(e) / (f tau): per-sample decay of log2 of a contribution
     float rho_f[4];    // 2^(-kap e), e = 0..3 (rho_f[0] = 1)
     float alpha_f, beta_f, R_f, noise_f, f_f, tau_f, v_f;
     double Tf;         // T f
@@ -229,7 +237,7 @@ __device__ __forceinline__ bool arrival32c(const Geo& g, double x, double y, dou
     const float q = __fadd_rn(ph, __fmul_rn(d, g.fv_f));   // arrival x f - K
     if (fabsf(__fsub_rn(q, rintf(q))) < kMarginK) k0 = k0_exact(x, y, t, xs, ys, g.v, g.f_hz);
     else k0 = K + (int)ceilf(q);
-    const float lnA2 = __fmul_rn(2.f, __fsub_rn(__fmul_rn(g.alpha_f, mf), __fmul_rn(g.beta_f, d)));
+    const float lnA2 = __fmul_rn(g.apow_f, __fsub_rn(__fmul_rn(g.alpha_f, mf), __fmul_rn(g.beta_f, d)));
     const float frac = __fsub_rn((float)(k0 - K), q);      // k0 - arrival x f, in [0, 1)
     E0 = __fmul_rn(1.4426950408889634f, __fsub_rn(lnA2, __fmul_rn(frac, g.twoftau_f)));
     return true;
@@ -295,7 +303,7 @@ cudaError_t prepare_rebin_batch(int max_ev_cap);
 cudaError_t launch_rebin_batch(const Geo* G, const Dev* D, const int* blk_off, int n_inst, int n_blocks,
                                int max_ev_cap, cudaStream_t s);
 cudaError_t prepare_sweep32_batch(size_t smem_bytes, int* grid);
-cudaError_t launch_sweep32_batch(const Geo* G, const Dev* D, int n_inst, int n_col, int* item_tab, int* queue,
+cudaError_t launch_sweep32_batch(bool mean, const Geo* G, const Dev* D, int n_inst, int n_col, int* item_tab, int* queue,
                                  size_t smem_bytes, int grid, cudaStream_t s);
 cudaError_t launch_sweep_end_batch(const Geo* G, const Dev* D, int n_inst, cudaStream_t s);
 cudaError_t prepare_rebin(const Geo& g);

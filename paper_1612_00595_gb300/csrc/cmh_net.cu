@@ -332,20 +332,21 @@ __global__ void __launch_bounds__(256) gen_windows(Geo g, unsigned long long see
         }
     }
     __syncthreads();
-    // per station: reached?, arrival time, squared amplitude at the arrival
-    __shared__ float arr[kNS], amp2[kNS];
+    // per station: reached?, arrival time, amplitude at the arrival
+    __shared__ float arr[kNS], amp[kNS];
     __shared__ int reach[kNS];
     if (threadIdx.x < kNS) {
         const int s = threadIdx.x;
         const double dx = ev[0] - sx[s], dy = ev[1] - sy[s], dist = sqrt(dx * dx + dy * dy);
         reach[s] = has && dist < g.R_max;
         arr[s] = (float)(ev[2] + dist / g.v);
-        amp2[s] = (float)exp(2.0 * (g.alpha * ev[3] - g.beta_att * dist));
+        amp[s] = (float)exp(g.alpha * ev[3] - g.beta_att * dist);
     }
     __syncthreads();
-    // four samples of one station per Philox block: s = sqrt(V) z, z from
-    // Box-Muller on both halves of two uniform pairs
-    const float fs = (float)g.f_hz, ts = (float)((double)g.n_w / g.f_hz), itau2 = (float)(2.0 / g.tau);
+    // four samples of one station per Philox block: s = sqrt(noise + c^2) z
+    // (variance reading) or c + sqrt(noise) z (additive reading), c = A g(u),
+    // z from Box-Muller on both halves of two uniform pairs
+    const float fs = (float)g.f_hz, ts = (float)((double)g.n_w / g.f_hz), itau = (float)(1.0 / g.tau);
     const float nv = (float)g.noise_var;
     for (int q = threadIdx.x; q < kNS * kNL / 4; q += blockDim.x) {
         const int s = q % kNS, t0 = (q / kNS) * 4;
@@ -365,10 +366,9 @@ __global__ void __launch_bounds__(256) gen_windows(Geo g, unsigned long long see
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int t = t0 + k;
-            float V = nv;
             const float u = (float)t / fs - arr[s];
-            if (reach[s] && u >= 0.f && u < ts) V += amp2[s] * expf(-u * itau2);
-            const float x = sqrtf(V) * z[k];
+            const float c = (reach[s] && u >= 0.f && u < ts) ? amp[s] * expf(-u * itau) : 0.f;
+            const float x = g.mean_mode ? c + sqrtf(nv) * z[k] : sqrtf(nv + c * c) * z[k];
             X[((long long)b * kNL + t) * kNS + s] = __float2bfloat16(log1pf(x * x));
         }
     }

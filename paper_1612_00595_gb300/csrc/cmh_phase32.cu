@@ -570,7 +570,7 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
 // thread issues the loads of kUnroll groups before computing them), one
 // float-float partial per warp in S.redf
 // ---------------------------------------------------------------------------
-template <bool STAGE>
+template <bool STAGE, bool MEAN>
 __device__ __forceinline__ void price_step(const Geo& g, const Dev& d, Sm& S, int sl) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const T32* tk = S.tasks + sl * g.task_cap;
@@ -630,7 +630,11 @@ __device__ __forceinline__ void price_step(const Geo& g, const Dev& d, Sm& S, in
                 const float dd = cn - co;
                 cnv[e] = cn;
                 term[e] = 0.f;
-                if (kk < T.hi && dd != 0.f) {
+                if (MEAN && kk < T.hi && dd != 0.f) {
+                    // additive reading: (d (s - mu) - d^2 / 2) / noise, mu = vv
+                    term[e] = __fmul_rn(g.inv_noise_f, __fsub_rn(__fmul_rn(dd, __fsub_rn(sv[e], vv[e])),
+                                                                 __fmul_rn(0.5f, __fmul_rn(dd, dd))));
+                } else if (!MEAN && kk < T.hi && dd != 0.f) {
                     const float V = vv[e], sm = sv[e];
                     const float Vp = V + dd;
                     if (Vp < 0.5f * V) {
@@ -652,7 +656,7 @@ __device__ __forceinline__ void price_step(const Geo& g, const Dev& d, Sm& S, in
                 float a2[4], c2[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    a2[e] = g.noise_f;
+                    a2[e] = g.syn0_f;
                     c2[e] = 0.f;
                 }
                 const SA* L = S.sarr + T.slot * g.frz_cap;
@@ -746,8 +750,9 @@ __device__ __forceinline__ void init_staging(Sm& S) {
 }
 
 // one colour phase of one region (every thread of the CTA): load the region,
-// run its k MH steps, write it back
-template <bool STAGE>
+// run its k MH steps, write it back.  MEAN: the additive likelihood reading
+// (a kernel per reading, so each pricing loop is compiled for its own)
+template <bool STAGE, bool MEAN>
 __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cell, long long sweep, Sm& S,
                                              unsigned char* smem) {
     const Store St = d.st[sweep & 1];
@@ -1074,7 +1079,7 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
         } else if (valid) {
             // (this buffer is refilled by bulk copies only after two more
             // barriers: these generic reads come first)
-            price_step<STAGE>(g, d, S, sl);
+            price_step<STAGE, MEAN>(g, d, S, sl);
         }
         // errors are set before a barrier and read through its OR, so every
         // thread leaves the loop at the same point
@@ -1193,7 +1198,7 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
                         float a2[4], c2[4];
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            a2[e] = g.noise_f;
+                            a2[e] = g.syn0_f;
                             c2[e] = 0.f;
                         }
                         for (int o = 0; o < nl; ++o) {
@@ -1248,7 +1253,7 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
 }
 
 // one colour phase: a CTA per region of the colour
-template <bool STAGE>
+template <bool STAGE, bool MEAN>
 __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const __grid_constant__ Geo g,
                                                                            const __grid_constant__ Dev d, int colour) {
     if (*d.status) return;
@@ -1257,7 +1262,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Sm S;
     init_staging<STAGE>(S);
-    region_phase<STAGE>(g, d, d.colour_cells[colour * g.max_rpc + blockIdx.x], sweep, S, smem);
+    region_phase<STAGE, MEAN>(g, d, d.colour_cells[colour * g.max_rpc + blockIdx.x], sweep, S, smem);
 }
 
 __device__ __forceinline__ long long ld_acquire(const long long* p) {
@@ -1282,7 +1287,7 @@ constexpr unsigned kDepWaitLimit = 1u << 22;   // bounded waits for neighbouring
 // results do not depend on the order in which CTAs take regions.  Every
 // region a CTA waits for was taken earlier by a CTA that is running, so the
 // waits end; they are bounded all the same (CMH_ERR_TIMEOUT).
-template <bool STAGE>
+template <bool STAGE, bool MEAN>
 __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_kernel(const __grid_constant__ Geo g,
                                                                            const __grid_constant__ Dev d) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1330,7 +1335,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_kernel(const
             s_run = *(volatile int*)d.status == 0;
         }
         __syncthreads();
-        if (s_run) region_phase<STAGE>(g, d, cell, sweep, S, smem);
+        if (s_run) region_phase<STAGE, MEAN>(g, d, cell, sweep, S, smem);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -1387,6 +1392,7 @@ __global__ void __launch_bounds__(1024) batch_plan(const Geo* G, const Dev* D, i
     }
 }
 
+template <bool MEAN>
 __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_batch(const Geo* G, const Dev* D, int n_inst,
                                                                           int n_col, const int* item_tab,
                                                                           int* queue) {
@@ -1442,7 +1448,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_batch(const 
             s_run = *(volatile int*)d.status == 0;
         }
         __syncthreads();
-        if (s_run) region_phase<false>(g, d, cell, sweep, S, smem);
+        if (s_run) region_phase<false, MEAN>(g, d, cell, sweep, S, smem);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -1464,20 +1470,25 @@ size_t phase32_spill_bytes(const Geo& g) {
 }
 
 cudaError_t prepare_sweep32_batch(size_t smem_bytes, int* grid) {
-    cudaError_t e = raise_smem_limit((const void*)sweep32_batch, smem_bytes);
+    cudaError_t e = raise_smem_limit((const void*)sweep32_batch<false>, smem_bytes);
+    if (e == cudaSuccess) e = raise_smem_limit((const void*)sweep32_batch<true>, smem_bytes);
     if (e != cudaSuccess) return e;
     int dev = 0, n_sm = 1, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) ||
-        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep32_batch, kThreads32, smem_bytes)))
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep32_batch<false>, kThreads32, smem_bytes)))
         return e;
     *grid = std::max(1, n_sm * std::max(1, std::min(per_sm, kMinBlocks32)));
     return cudaSuccess;
 }
 
-cudaError_t launch_sweep32_batch(const Geo* G, const Dev* D, int n_inst, int n_col, int* item_tab, int* queue,
+cudaError_t launch_sweep32_batch(bool mean, const Geo* G, const Dev* D, int n_inst, int n_col, int* item_tab,
+                                 int* queue,
                                  size_t smem_bytes, int grid, cudaStream_t s) {
     batch_plan<<<1, 1024, 0, s>>>(G, D, n_inst, n_col, item_tab, queue);
-    sweep32_batch<<<grid, kThreads32, smem_bytes, s>>>(G, D, n_inst, n_col, item_tab, queue);
+    if (mean)
+        sweep32_batch<true><<<grid, kThreads32, smem_bytes, s>>>(G, D, n_inst, n_col, item_tab, queue);
+    else
+        sweep32_batch<false><<<grid, kThreads32, smem_bytes, s>>>(G, D, n_inst, n_col, item_tab, queue);
     return cudaGetLastError();
 }
 
@@ -1502,7 +1513,7 @@ cudaError_t choose_stage_cap(Geo& g, int requested) {
         (e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) ||
         (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) ||
         (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) ||
-        (e = cudaFuncGetAttributes(&fa, phase32_kernel<true>)))
+        (e = cudaFuncGetAttributes(&fa, phase32_kernel<true, false>)))
         return e;
     const int resident = std::min(kMinBlocks32, std::max(1, (g.max_rpc + n_sm - 1) / std::max(1, n_sm)));
     const long long dyn = (long long)layout32(g, nullptr, nullptr);
@@ -1518,10 +1529,15 @@ cudaError_t choose_stage_cap(Geo& g, int requested) {
 cudaError_t prepare_phase32(const Geo& g) {
     const int bytes = (int)phase32_smem_bytes(g);
     cudaError_t e;
-    if ((e = raise_smem_limit((const void*)phase32_kernel<false>, bytes)) ||
-        (e = raise_smem_limit((const void*)phase32_kernel<true>, bytes)) ||
-        (e = raise_smem_limit((const void*)sweep32_kernel<false>, bytes)) ||
-        (e = raise_smem_limit((const void*)sweep32_kernel<true>, bytes)))
+    const bool mn = g.mean_mode;
+    if ((e = raise_smem_limit(mn ? (const void*)phase32_kernel<false, true> : (const void*)phase32_kernel<false, false>,
+                              bytes)) ||
+        (e = raise_smem_limit(mn ? (const void*)phase32_kernel<true, true> : (const void*)phase32_kernel<true, false>,
+                              bytes)) ||
+        (e = raise_smem_limit(mn ? (const void*)sweep32_kernel<false, true> : (const void*)sweep32_kernel<false, false>,
+                              bytes)) ||
+        (e = raise_smem_limit(mn ? (const void*)sweep32_kernel<true, true> : (const void*)sweep32_kernel<true, false>,
+                              bytes)))
         return e;
     return cudaSuccess;
 }
@@ -1534,7 +1550,9 @@ cudaError_t sweep32_grid(const Geo& g, int ctas_per_sm, int* grid) {
     if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)))
         return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-             &per_sm, g.stage_cap > 0 ? (const void*)sweep32_kernel<true> : (const void*)sweep32_kernel<false>,
+             &per_sm,
+             g.stage_cap > 0 ? (g.mean_mode ? (const void*)sweep32_kernel<true, true> : (const void*)sweep32_kernel<true, false>)
+                             : (g.mean_mode ? (const void*)sweep32_kernel<false, true> : (const void*)sweep32_kernel<false, false>),
              kThreads32, phase32_smem_bytes(g))))
         return e;
     per_sm = std::max(1, std::min(per_sm, kMinBlocks32));
@@ -1545,17 +1563,21 @@ cudaError_t sweep32_grid(const Geo& g, int ctas_per_sm, int* grid) {
 
 cudaError_t launch_sweep32(const Geo& g, const Dev& d, int grid, cudaStream_t s) {
     if (g.stage_cap > 0)
-        sweep32_kernel<true><<<grid, kThreads32, phase32_smem_bytes(g), s>>>(g, d);
+        g.mean_mode ? sweep32_kernel<true, true><<<grid, kThreads32, phase32_smem_bytes(g), s>>>(g, d)
+                    : sweep32_kernel<true, false><<<grid, kThreads32, phase32_smem_bytes(g), s>>>(g, d);
     else
-        sweep32_kernel<false><<<grid, kThreads32, phase32_smem_bytes(g), s>>>(g, d);
+        g.mean_mode ? sweep32_kernel<false, true><<<grid, kThreads32, phase32_smem_bytes(g), s>>>(g, d)
+                    : sweep32_kernel<false, false><<<grid, kThreads32, phase32_smem_bytes(g), s>>>(g, d);
     return cudaGetLastError();
 }
 
 cudaError_t launch_phase32(const Geo& g, const Dev& d, int colour, cudaStream_t s) {
     if (g.stage_cap > 0)
-        phase32_kernel<true><<<g.max_rpc, kThreads32, phase32_smem_bytes(g), s>>>(g, d, colour);
+        g.mean_mode ? phase32_kernel<true, true><<<g.max_rpc, kThreads32, phase32_smem_bytes(g), s>>>(g, d, colour)
+                    : phase32_kernel<true, false><<<g.max_rpc, kThreads32, phase32_smem_bytes(g), s>>>(g, d, colour);
     else
-        phase32_kernel<false><<<g.max_rpc, kThreads32, phase32_smem_bytes(g), s>>>(g, d, colour);
+        g.mean_mode ? phase32_kernel<false, true><<<g.max_rpc, kThreads32, phase32_smem_bytes(g), s>>>(g, d, colour)
+                    : phase32_kernel<false, false><<<g.max_rpc, kThreads32, phase32_smem_bytes(g), s>>>(g, d, colour);
     return cudaGetLastError();
 }
 

@@ -719,7 +719,7 @@ __global__ void __launch_bounds__(kSynthThreads) vsynth_kernel(Geo g, Dev d, con
             for (long long k = t0 + threadIdx.x; k < t1; k += blockDim.x) {
                 if (F32) {
                     float* vrow = (float*)d.V + (size_t)j * g.pitch;
-                    float a2 = first ? (float)g.noise_var : vrow[k], c2 = 0.f;
+                    float a2 = first ? g.syn0_f : vrow[k], c2 = 0.f;
                     for (int q = 0; q < nt; ++q) {
                         const int a = s_tl[q];
                         const int r = (int)(k - s_k0[a]);
@@ -786,7 +786,9 @@ __global__ void __launch_bounds__(1024) flatten_kernel(Geo g, Dev d, int buf, do
     if (threadIdx.x == 0) *n_out = s_base;
 }
 
-// sum over all stations and samples of log N(s; 0, V): per-block partials
+// sum over all stations and samples of log N(s; 0, V) (or, with the additive
+// reading in float32, log N(s; mu, noise) with mu in the V buffer): per-block
+// partials
 template <bool F32>
 __global__ void loglik_kernel(Geo g, Dev d, double* partial) {
     __shared__ double s_part[32];
@@ -799,7 +801,12 @@ __global__ void loglik_kernel(Geo g, Dev d, double* partial) {
         if (F32) {
             const float s = ((const float*)d.sig)[j * g.pitch + k];
             const float V = ((const float*)d.V)[j * g.pitch + k];
-            acc += (double)(-0.5f * logf(V) - s * s / (2.f * V)) - half_log_2pi;
+            if (g.mean_mode) {
+                const float r = s - V;
+                acc += (double)(-0.5f * r * r * g.inv_noise_f) - 0.5 * log(g.noise_var) - half_log_2pi;
+            } else {
+                acc += (double)(-0.5f * logf(V) - s * s / (2.f * V)) - half_log_2pi;
+            }
         } else {
             const double s = ((const double*)d.sig)[j * g.pitch + k];
             const double V = ((const double*)d.V)[j * g.pitch + k];

@@ -327,3 +327,80 @@ def test_fp32_dry_run_with_learned_birth_table(cm, orc, magnitudes):
     assert la_err.max() <= 1e-4
     assert np.count_nonzero(tr["accepted"][ev_] != otr["accepted"][ev_]) <= max(2, ev_.sum() // 10000)
     m.destroy()
+
+
+def test_nine_colour_geometry_replay_bit_exact(cm, orc):
+    """R_max = L (events reach two regions away): 9 colours of period 3, the
+    5 x 5 neighbourhood in the region prologue; float64 replay bit-exact."""
+    w = small_world(seed=23, W=500.0, Lambda=80.0, R_max=100.0)
+    params = cm.make_params(w.params, k_per_phase=16, seed=11, dtype=cm.F64)
+    m = cm.create_model(None, w.stations, w.signals, params)
+    assert m.partition_and_color(w.params.L, shift_mode=1) == 9
+    m.destroy()
+    m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=5)
+    o, oev, oids, otr, odlp = run_oracle(orc, w, sweeps=5)
+    assert_traces_match(tr, otr)
+    assert np.array_equal(ids, oids)
+    assert np.array_equal(ev[:, :3], oev[:, :3])
+    m.destroy()
+
+
+def test_nine_colour_geometry_fp32_deltas(cm, orc):
+    w = small_world(seed=24, W=600.0, T=1800.0, Lambda=150.0, n_side=6, R_max=100.0, dtype=np.float32)
+    m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=3, k=32, events=w.events, commit=False, seed=9)
+    o, oev, oids, otr, odlp = run_oracle(orc, w, sweeps=3, k=32, events=w.events, commit=False, seed=9,
+                                         threads=min(16, os.cpu_count() or 1))
+    assert len(tr) == len(otr)
+    for key in ("sweep", "cell", "step", "type", "n_before"):
+        assert np.array_equal(tr[key], otr[key]), key
+    ev_ = (otr["evaluated"] == 1) & (tr["evaluated"] == 1)
+    assert ev_.sum() > 200
+    err = np.abs(tr["dll"][ev_] - otr["dll"][ev_]) / np.maximum(np.abs(otr["dll"][ev_]), 1.0)
+    assert err.max() <= 1e-4
+    m.destroy()
+
+
+# ---- the additive-mean reading (arrivals add to the sample mean) ------------
+def _mean_world(seed):
+    return small_world(seed=seed, W=1000.0, T=3600.0, Lambda=500.0, n_side=10, dtype=np.float32,
+                       likelihood="mean")
+
+
+def test_mean_reading_fp32_deltas(cm, orc):
+    """The float32 per-sample term of the additive reading, (d (s - mu) -
+    d^2/2) / noise over the touched windows, against the oracle's float64
+    difference of log-densities on the same proposals (commit off)."""
+    w = _mean_world(26)
+    m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=3, k=32, events=w.events, commit=False, seed=3)
+    o, oev, oids, otr, odlp = run_oracle(orc, w, sweeps=3, k=32, events=w.events, commit=False, seed=3,
+                                         threads=min(16, os.cpu_count() or 1))
+    assert len(tr) == len(otr)
+    for key in ("sweep", "cell", "step", "type", "n_before"):
+        assert np.array_equal(tr[key], otr[key]), key
+    ev_ = (otr["evaluated"] == 1) & (tr["evaluated"] == 1)
+    assert ev_.sum() > 1000
+    err = np.abs(tr["dll"][ev_] - otr["dll"][ev_]) / np.maximum(np.abs(otr["dll"][ev_]), 1.0)
+    print("mean reading fp32 dll rel err: median %.2e max %.2e" % (np.median(err), err.max()))
+    assert err.max() <= 1e-4
+    assert np.count_nonzero(tr["accepted"][ev_] != otr["accepted"][ev_]) <= max(2, ev_.sum() // 10000)
+    m.destroy()
+
+
+def test_mean_reading_chain_tracks_recomputed_log_density(cm, orc):
+    """With commits the mean buffer is re-synthesised on every accept; the
+    running log-density equals a recomputation, and the initial one equals
+    the oracle's log-density of the starting state."""
+    w = _mean_world(27)
+    m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=20, k=32, events=None, seed=8)
+    assert sum(stats["accepted"]) > 500
+    assert logp == pytest.approx(m.log_density(), rel=2e-7, abs=1.0)
+    o = orc.World(w)
+    assert o.log_density(ev) == pytest.approx(m.log_density(), rel=1e-6)
+    m.destroy()
+
+
+def test_mean_reading_needs_float32(cm):
+    w = small_world(seed=28, likelihood="mean")
+    with pytest.raises(cm.ChromhError) as ei:
+        cm.create_model(None, w.stations, w.signals, cm.make_params(w.params, dtype=cm.F64))
+    assert ei.value.code == -1

@@ -178,6 +178,26 @@ int cmh_run_sweeps(cmh_model* m, int64_t n);
 int cmh_read_state(cmh_model* m, cmh_event* out, uint64_t* ids_out, int64_t cap,
                    int64_t* n_out, double* log_density_out, cmh_stats* stats_out);
 
+/*
+ * Asynchronous state reads (two slots), so that a caller can read every
+ * sweep's state while the next sweep runs.
+ * cmh_read_state_async: enqueues on the model's stream, after the sweeps
+ *   enqueued so far, the copy of the events, running log-density, statistics
+ *   and device status into slot 0 or 1 (model-owned pinned host memory the
+ *   flattening kernel writes directly); returns without waiting.  A slot
+ *   with an unfetched request is waited for first.  Needs a partition
+ *   (CMH_ERR_STATE).
+ * cmh_read_state_fetch: waits for the slot's request only, then fills the
+ *   outputs as cmh_read_state would for the state at the request.  With
+ *   out == ids_out == log_density_out == stats_out == NULL and cap == 0 it
+ *   only reports *n_out and leaves the request to be fetched.  CMH_ERR_STATE
+ *   if the slot holds no request; a device error latched by the sweeps
+ *   before the request is returned.
+ */
+int cmh_read_state_async(cmh_model* m, int32_t slot);
+int cmh_read_state_fetch(cmh_model* m, int32_t slot, cmh_event* out, uint64_t* ids_out, int64_t cap,
+                         int64_t* n_out, double* log_density_out, cmh_stats* stats_out);
+
 /* Wait for the model's stream; return a latched device error if any. */
 int cmh_sync(cmh_model* m);
 

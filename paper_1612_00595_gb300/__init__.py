@@ -81,6 +81,7 @@ TRACE_DTYPE = np.dtype([("sweep", "<i4"), ("cell", "<i4"), ("step", "<i4"), ("ty
                         ("written", "<i4"), ("dll", "<f8"), ("log_alpha", "<f8")])
 
 EXPORTS = ["cmh_create_model", "cmh_partition_and_color", "cmh_run_sweeps", "cmh_read_state", "cmh_sync",
+           "cmh_read_state_async", "cmh_read_state_fetch",
            "cmh_log_density", "cmh_set_trace", "cmh_read_trace", "cmh_set_timing", "cmh_read_shift",
            "cmh_checkpoint", "cmh_restore", "cmh_destroy", "cmh_strerror", "cmh_philox4x64",
            "cmh_gaussian_loglik_noalloc", "cmh_batch_create", "cmh_batch_run_sweeps", "cmh_batch_destroy",
@@ -101,6 +102,8 @@ def _load():
         "cmh_partition_and_color": (C.c_int, [P, C.POINTER(Grid), i32, C.c_double, C.c_double,
                                               C.POINTER(i32)]),
         "cmh_run_sweeps": (C.c_int, [P, i64]),
+        "cmh_read_state_async": (C.c_int, [P, i32]),
+        "cmh_read_state_fetch": (C.c_int, [P, i32, P, P, i64, C.POINTER(i64), C.POINTER(C.c_double), P]),
         "cmh_read_state": (C.c_int, [P, P, P, i64, C.POINTER(i64), C.POINTER(C.c_double),
                                      C.POINTER(Stats)]),
         "cmh_sync": (C.c_int, [P]),
@@ -241,17 +244,40 @@ class Model:
     def read_state(self, cap: Optional[int] = None):
         """(events [n,4] float64, ids [n] uint64, log_density, stats dict)."""
         n = C.c_int64()
-        if cap is None:
-            _check(lib.cmh_read_state(self._h, None, None, 0, C.byref(n), None, None), "cmh_read_state")
+        exact = cap is not None
+        if cap is None:   # one call when the last count (plus room) suffices
+            cap = getattr(self, "_last_n", 0) + 1024
+        while True:
+            ev = np.zeros((cap, 4), dtype=np.float64)
+            ids = np.zeros(cap, dtype=np.uint64)
+            lp = C.c_double()
+            st = Stats()
+            _check(lib.cmh_read_state(self._h, _ptr(ev), _ptr(ids), cap, C.byref(n), C.byref(lp), C.byref(st)),
+                   "cmh_read_state")
+            if exact or n.value <= cap:
+                break
             cap = n.value
+        self._last_n = n.value
+        k = min(cap, n.value)
+        return ev[:k], ids[:k], lp.value, st.as_dict()
+
+    def read_state_async(self, slot: int):
+        """cmh_read_state_async: enqueue a copy of the state into slot 0 or 1."""
+        _check(lib.cmh_read_state_async(self._h, int(slot)), "cmh_read_state_async")
+
+    def read_state_fetch(self, slot: int):
+        """cmh_read_state_fetch: the state of the slot's request, as read_state."""
+        n = C.c_int64()
+        _check(lib.cmh_read_state_fetch(self._h, int(slot), None, None, 0, C.byref(n), None, None),
+               "cmh_read_state_fetch")
+        cap = n.value
         ev = np.zeros((cap, 4), dtype=np.float64)
         ids = np.zeros(cap, dtype=np.uint64)
         lp = C.c_double()
         st = Stats()
-        _check(lib.cmh_read_state(self._h, _ptr(ev), _ptr(ids), cap, C.byref(n), C.byref(lp), C.byref(st)),
-               "cmh_read_state")
-        k = min(cap, n.value)
-        return ev[:k], ids[:k], lp.value, st.as_dict()
+        _check(lib.cmh_read_state_fetch(self._h, int(slot), _ptr(ev) if cap else None, _ptr(ids) if cap else None,
+                                        cap, C.byref(n), C.byref(lp), C.byref(st)), "cmh_read_state_fetch")
+        return ev, ids, lp.value, st.as_dict()
 
     # ---- extras -------------------------------------------------------------
     def sync(self):

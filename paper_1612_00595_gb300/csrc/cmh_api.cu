@@ -92,6 +92,17 @@ struct cmh_model {
     int latched = 0;
     long long trace_cap = 0;
     long long n0 = 0;
+    // asynchronous state reads: the flat list written by the flatten kernel
+    // straight into mapped pinned host memory, plus the log-density and
+    // statistics, in stream order
+    struct ReadSlot {
+        unsigned char* host = nullptr;   // x, y, t, m [cap] doubles, id [cap], logp, stats [kStats], n
+        long long cap = 0;
+        cudaEvent_t ev = nullptr;
+        bool pending = false;
+        long long sweeps = 0, launches = 0, phase_launches = 0;
+        double phase_ms = 0.0;
+    } rs[2];
 
     template <typename T>
     cudaError_t alloc(T** ptr, size_t count, bool partition_scope = false) {
@@ -944,8 +955,108 @@ void cmh_destroy(cmh_model* m) {
     if (m->bt_cdf) cudaFree(m->bt_cdf);
     if (m->bt_tab) cudaFree(m->bt_tab);
     if (m->bt_mag) cudaFree(m->bt_mag);
+    for (auto& r : m->rs) {
+        if (r.host) cudaFreeHost(r.host);
+        if (r.ev) cudaEventDestroy(r.ev);
+    }
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
+}
+
+namespace {
+// byte offsets inside a read slot of capacity cap
+inline size_t rs_off_id(long long cap) { return (size_t)cap * 4 * sizeof(double); }
+inline size_t rs_off_logp(long long cap) { return rs_off_id(cap) + (size_t)cap * sizeof(unsigned long long); }
+inline size_t rs_off_stats(long long cap) { return rs_off_logp(cap) + sizeof(double); }
+inline size_t rs_off_n(long long cap) { return rs_off_stats(cap) + kStats * sizeof(unsigned long long); }
+inline size_t rs_off_status(long long cap) { return rs_off_n(cap) + sizeof(int); }
+inline size_t rs_bytes(long long cap) { return rs_off_n(cap) + 16; }
+}  // namespace
+
+int cmh_read_state_async(cmh_model* m, int32_t slot) {
+    if (!m || slot < 0 || slot > 1) return CMH_ERR_ARG;
+    if (!m->partitioned) return CMH_ERR_STATE;
+    if (m->latched) return m->latched;
+    (void)cudaGetLastError();
+    cmh_model::ReadSlot& r = m->rs[slot];
+    if (r.pending) CK(cudaEventSynchronize(r.ev));   // its previous request is still being read
+    r.pending = false;
+    if (!r.ev) CK(cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming));
+    if (r.cap < m->flat_cap) {
+        if (r.host) CK(cudaFreeHost(r.host));
+        r.host = nullptr;
+        r.cap = 0;
+        if (cudaHostAlloc((void**)&r.host, rs_bytes(m->flat_cap), cudaHostAllocMapped) != cudaSuccess) {
+            r.host = nullptr;
+            return CMH_ERR_OOM;
+        }
+        r.cap = m->flat_cap;
+    }
+    unsigned char* dev = nullptr;
+    CK(cudaHostGetDevicePointer((void**)&dev, r.host, 0));
+    FlatList f;
+    f.x = (double*)dev;
+    f.y = f.x + r.cap;
+    f.t = f.y + r.cap;
+    f.m = f.t + r.cap;
+    f.id = (unsigned long long*)(dev + rs_off_id(r.cap));
+    f.n = (int*)(dev + rs_off_n(r.cap));
+    int l = 0;
+    CK(launch_flatten(m->g, m->d, cur_buf(m), f, m->stream, &l));
+    CK(cudaMemcpyAsync(r.host + rs_off_logp(r.cap), m->d.logp, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaMemcpyAsync(r.host + rs_off_stats(r.cap), m->d.stats, kStats * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaMemcpyAsync(r.host + rs_off_status(r.cap), m->d.status, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaEventRecord(r.ev, m->stream));
+    m->launches += l;
+    r.sweeps = m->sweeps;
+    r.launches = m->launches;
+    r.phase_launches = m->phase_launches;
+    r.phase_ms = m->phase_ms;
+    r.pending = true;
+    return CMH_OK;
+}
+
+int cmh_read_state_fetch(cmh_model* m, int32_t slot, cmh_event* out, uint64_t* ids_out, int64_t cap,
+                         int64_t* n_out, double* log_density_out, cmh_stats* stats_out) {
+    if (!m || slot < 0 || slot > 1 || cap < 0 || (cap > 0 && !out)) return CMH_ERR_ARG;
+    cmh_model::ReadSlot& r = m->rs[slot];
+    if (!r.pending) return CMH_ERR_STATE;
+    CK(cudaEventSynchronize(r.ev));
+    // the device status as of the request (the stream may hold later work)
+    const int st_dev = *(volatile int*)(r.host + rs_off_status(r.cap));
+    if (st_dev && !m->latched) m->latched = st_dev;
+    if (m->latched) {
+        r.pending = false;
+        return m->latched;
+    }
+    const int n = *(volatile int*)(r.host + rs_off_n(r.cap));
+    if (n_out) *n_out = n;
+    if (!out && cap == 0 && !ids_out && !log_density_out && !stats_out) return CMH_OK;   // a query of n
+    const int64_t nc = std::min<int64_t>(cap, n);
+    const double* x = (const double*)r.host;
+    for (int64_t i = 0; i < nc; ++i) out[i] = cmh_event{x[i], x[r.cap + i], x[2 * r.cap + i], x[3 * r.cap + i]};
+    if (ids_out && nc > 0) std::memcpy(ids_out, r.host + rs_off_id(r.cap), sizeof(uint64_t) * nc);
+    if (log_density_out) std::memcpy(log_density_out, r.host + rs_off_logp(r.cap), sizeof(double));
+    if (stats_out) {
+        const unsigned long long* st = (const unsigned long long*)(r.host + rs_off_stats(r.cap));
+        std::memset(stats_out, 0, sizeof(*stats_out));
+        for (int i = 0; i < 3; ++i) {
+            stats_out->proposed[i] = st[i];
+            stats_out->evaluated[i] = st[3 + i];
+            stats_out->accepted[i] = st[6 + i];
+        }
+        stats_out->sweeps = r.sweeps;
+        stats_out->n_events = n;
+        stats_out->phase_ms = r.phase_ms;
+        stats_out->phase_launches = r.phase_launches;
+        stats_out->kernel_launches = r.launches;
+        stats_out->priced_samples = st[9];
+        stats_out->rewritten_samples = st[10];
+        stats_out->spill_bytes = m->g.spill ? m->g.spill_bytes : 0;
+    }
+    r.pending = false;
+    return CMH_OK;
 }
 
 int cmh_philox4x64(const uint64_t* ctr, const uint64_t* key, uint64_t* out, int64_t n) {

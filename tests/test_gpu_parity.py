@@ -404,3 +404,32 @@ def test_mean_reading_needs_float32(cm):
     with pytest.raises(cm.ChromhError) as ei:
         cm.create_model(None, w.stations, w.signals, cm.make_params(w.params, dtype=cm.F64))
     assert ei.value.code == -1
+
+
+def test_async_state_reads_equal_synchronous_ones(cm):
+    """Double-buffered asynchronous reads taken after each sweep, fetched one
+    sweep later, equal a second model's synchronous reads after the same
+    sweeps (same chain)."""
+    w = small_world(seed=29, W=1000.0, T=1800.0, Lambda=250.0, n_side=10, dtype=np.float32)
+    params = cm.make_params(w.params, k_per_phase=16, seed=6, dtype=cm.F32)
+    a = cm.create_model(None, w.stations, w.signals, params)
+    b = cm.create_model(None, w.stations, w.signals, params)
+    for m in (a, b):
+        m.partition_and_color(w.params.L, 1)
+    with pytest.raises(cm.ChromhError):
+        a.read_state_fetch(0)   # nothing requested yet
+    ref, got = [], []
+    for i in range(6):
+        a.run_sweeps(1)
+        a.read_state_async(i % 2)
+        if i > 0:
+            got.append(a.read_state_fetch((i - 1) % 2))
+        b.run_sweeps(1)
+        ref.append(b.read_state())
+    got.append(a.read_state_fetch(5 % 2))
+    for (e0, i0, l0, s0), (e1, i1, l1, s1) in zip(ref, got):
+        assert np.array_equal(e0, e1) and np.array_equal(i0, i1) and l0 == l1
+        assert s0["accepted"] == s1["accepted"] and s0["sweeps"] == s1["sweeps"]
+    assert len(got[-1][0]) > 0
+    a.destroy()
+    b.destroy()

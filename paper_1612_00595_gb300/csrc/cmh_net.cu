@@ -147,6 +147,135 @@ __global__ void __launch_bounds__(128) gemm_bf16(int M, int N, int K, const __nv
             }
 }
 
+// The same product with 16-byte tile loads: each operand is read in vectors
+// of 8 along its contiguous dimension (whose extent and leading dimension are
+// multiples of 8, base 16-byte aligned) and stored to shared memory as is or
+// transposed; two shared stages, so the next tile's loads are in flight while
+// the current tile is multiplied.  Same tiles, split K and epilogue.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(128) gemm_bf16_vec(int M, int N, int K, const __nv_bfloat16* A, int lda,
+                                                     const __nv_bfloat16* B, int ldb, float* C, int ldc,
+                                                     const float* bias, int relu, int accumulate,
+                                                     __nv_bfloat16* Cb, int kc) {
+    __shared__ __align__(16) __nv_bfloat16 As[2][GB][GP];
+    __shared__ __align__(16) __nv_bfloat16 Bs[2][GB][GP];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int m0 = blockIdx.y * GB, n0 = blockIdx.x * GB;
+    const int grp = lane >> 2, tig = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+    const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+    if (gridDim.z > 1) C += (long long)blockIdx.z * M * ldc;
+    // vector v (0..255) of a 64 x 32 tile: along k (4 per row of 32) when the
+    // operand is k-contiguous, else along m / n (8 per column of 64)
+    uint4 ra[2], rb[2];
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int v = tid + i * 128;
+            if (!TA) {
+                const int gm = m0 + (v >> 2), gk = k0 + (v & 3) * 8;
+                ra[i] = (gm < M && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(A + (long long)gm * lda + gk)) : zero4;
+            } else {
+                const int gk = k0 + (v >> 3), gm = m0 + (v & 7) * 8;
+                ra[i] = (gm < M && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(A + (long long)gk * lda + gm)) : zero4;
+            }
+            if (TB) {
+                const int gn = n0 + (v >> 2), gk = k0 + (v & 3) * 8;
+                rb[i] = (gn < N && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(B + (long long)gn * ldb + gk)) : zero4;
+            } else {
+                const int gk = k0 + (v >> 3), gn = n0 + (v & 7) * 8;
+                rb[i] = (gn < N && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(B + (long long)gk * ldb + gn)) : zero4;
+            }
+        }
+    };
+    auto store = [&](int st) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int v = tid + i * 128;
+            if (!TA) {
+                *reinterpret_cast<uint4*>(&As[st][v >> 2][(v & 3) * 8]) = ra[i];
+            } else {
+                const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&ra[i]);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) As[st][(v & 7) * 8 + j][v >> 3] = e[j];
+            }
+            if (TB) {
+                *reinterpret_cast<uint4*>(&Bs[st][v >> 2][(v & 3) * 8]) = rb[i];
+            } else {
+                const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&rb[i]);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) Bs[st][(v & 7) * 8 + j][v >> 3] = e[j];
+            }
+        }
+    };
+    int st = 0;
+    if (kb < ke) {
+        load(kb);
+        store(0);
+    }
+    __syncthreads();
+    for (int k0 = kb; k0 < ke; k0 += GK) {
+        const bool more = k0 + GK < ke;
+        if (more) load(k0 + GK);
+#pragma unroll
+        for (int kk = 0; kk < GK; kk += 16) {
+            unsigned a[2][4], b[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r0 = wm + i * 16 + grp;
+                a[i][0] = *reinterpret_cast<const unsigned*>(&As[st][r0][kk + tig * 2]);
+                a[i][1] = *reinterpret_cast<const unsigned*>(&As[st][r0 + 8][kk + tig * 2]);
+                a[i][2] = *reinterpret_cast<const unsigned*>(&As[st][r0][kk + tig * 2 + 8]);
+                a[i][3] = *reinterpret_cast<const unsigned*>(&As[st][r0 + 8][kk + tig * 2 + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int nn = wn + j * 8 + grp;
+                b[j][0] = *reinterpret_cast<const unsigned*>(&Bs[st][nn][kk + tig * 2]);
+                b[j][1] = *reinterpret_cast<const unsigned*>(&Bs[st][nn][kk + tig * 2 + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                        "{%8,%9}, {%0,%1,%2,%3};"
+                        : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+                        : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
+        }
+        // the other stage was last read before the previous barrier
+        if (more) store(st ^ 1);
+        __syncthreads();
+        st ^= 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int m = m0 + wm + i * 16 + grp + (r >= 2 ? 8 : 0);
+                const int n = n0 + wn + j * 8 + tig * 2 + (r & 1);
+                if (m >= M || n >= N) continue;
+                float v = acc[i][j][r];
+                const long long o = (long long)m * ldc + n;
+                if (accumulate) v += C[o];
+                if (bias) v += bias[n];
+                if (relu) v = v > 0.f ? v : 0.f;
+                C[o] = v;
+                if (Cb) Cb[o] = __float2bfloat16(v);
+            }
+}
+
 // im2col of a [B][Lin][64] activation (BF16): row (b, t) of [B*Lout][320]
 // holds x[b][2t - 2 + k][c] at column k * 64 + c (0 outside the window)
 __global__ void im2col(const __nv_bfloat16* X, int Bn, int Lin, int Lout, __nv_bfloat16* A) {
@@ -484,13 +613,21 @@ cudaError_t gemm(cudaStream_t s, float* ws, int M, int N, int K, const __nv_bflo
             splits = (K + kc - 1) / kc;
         }
     }
-    if (splits > 1) {
-        gemm_bf16<TA, TB><<<dim3(gx, gy, splits), 128, 0, s>>>(M, N, K, A, lda, B, ldb, ws, ldc, nullptr, 0, 0,
-                                                               nullptr, kc);
-        sum_splits<<<blocks_for((long long)M * N), 256, 0, s>>>(ws, (long long)M * N, splits, C);
-    } else {
-        gemm_bf16<TA, TB><<<dim3(gx, gy, 1), 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, acc, Cb, K);
-    }
+    // 16-byte tile loads when both operands' contiguous dimensions come in
+    // whole aligned vectors
+    auto al16 = [](const void* p) { return ((unsigned long long)p & 15ULL) == 0; };
+    const bool vec = al16(A) && al16(B) && lda % 8 == 0 && ldb % 8 == 0 && (TA ? M % 8 == 0 : K % 8 == 0) &&
+                     (TB ? K % 8 == 0 : N % 8 == 0);
+    const dim3 grid(gx, gy, splits);
+    float* out = splits > 1 ? ws : C;
+    const float* bs = splits > 1 ? nullptr : bias;
+    const int rl = splits > 1 ? 0 : relu, ac = splits > 1 ? 0 : acc;
+    __nv_bfloat16* cb = splits > 1 ? nullptr : Cb;
+    if (vec)
+        gemm_bf16_vec<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, out, ldc, bs, rl, ac, cb, kc);
+    else
+        gemm_bf16<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, out, ldc, bs, rl, ac, cb, kc);
+    if (splits > 1) sum_splits<<<blocks_for((long long)M * N), 256, 0, s>>>(ws, (long long)M * N, splits, C);
     return cudaGetLastError();
 }
 

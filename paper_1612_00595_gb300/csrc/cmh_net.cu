@@ -15,7 +15,8 @@
 // of time and magnitude for windows that hold an event; AdamW.
 //
 // Every matrix product runs on the tensor cores in BF16 with FP32
-// accumulation (mma.sync m16n8k16; a convolution is an im2col product);
+// accumulation (mma.sync m16n8k16; a convolution is a product with the
+// im2col matrix of its input, read in place by the tile loader);
 // activations and gradients are kept in FP32, their BF16 copies feed the
 // products, and the parameters have FP32 masters with BF16 copies.
 #include <cuda_bf16.h>
@@ -152,11 +153,16 @@ __global__ void __launch_bounds__(128) gemm_bf16(int M, int N, int K, const __nv
 // multiples of 8, base 16-byte aligned) and stored to shared memory as is or
 // transposed; two shared stages, so the next tile's loads are in flight while
 // the current tile is multiplied.  Same tiles, split K and epilogue.
+// a_lin > 0: A (not transposed) is the im2col matrix of the activation A
+// [B][a_lin][64] for a_lout output samples, read in place (row b a_lout + t,
+// column k 64 + c is x[b][2t - 2 + k][c], 0 outside); b_lin likewise for B
+// (not transposed; its rows are the im2col rows).
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(128) gemm_bf16_vec(int M, int N, int K, const __nv_bfloat16* A, int lda,
                                                      const __nv_bfloat16* B, int ldb, float* C, int ldc,
                                                      const float* bias, int relu, int accumulate,
-                                                     __nv_bfloat16* Cb, int kc) {
+                                                     __nv_bfloat16* Cb, int kc, int a_lin, int a_lout,
+                                                     int b_lin, int b_lout) {
     __shared__ __align__(16) __nv_bfloat16 As[2][GB][GP];
     __shared__ __align__(16) __nv_bfloat16 Bs[2][GB][GP];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -182,7 +188,18 @@ __global__ void __launch_bounds__(128) gemm_bf16_vec(int M, int N, int K, const 
             const int v = tid + i * 128;
             if (!TA) {
                 const int gm = m0 + (v >> 2), gk = k0 + (v & 3) * 8;
-                ra[i] = (gm < M && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(A + (long long)gm * lda + gk)) : zero4;
+                if (a_lin > 0) {
+                    uint4 r = zero4;
+                    if (gm < M && gk < ke) {
+                        const int bb = gm / a_lout, t = gm - bb * a_lout, sx = 2 * t - 2 + (gk >> 6);
+                        if (sx >= 0 && sx < a_lin)
+                            r = __ldg(reinterpret_cast<const uint4*>(A + ((long long)bb * a_lin + sx) * kC + (gk & 63)));
+                    }
+                    ra[i] = r;
+                } else {
+                    ra[i] = (gm < M && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(A + (long long)gm * lda + gk))
+                                                : zero4;
+                }
             } else {
                 const int gk = k0 + (v >> 3), gm = m0 + (v & 7) * 8;
                 ra[i] = (gm < M && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(A + (long long)gk * lda + gm)) : zero4;
@@ -192,7 +209,18 @@ __global__ void __launch_bounds__(128) gemm_bf16_vec(int M, int N, int K, const 
                 rb[i] = (gn < N && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(B + (long long)gn * ldb + gk)) : zero4;
             } else {
                 const int gk = k0 + (v >> 3), gn = n0 + (v & 7) * 8;
-                rb[i] = (gn < N && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(B + (long long)gk * ldb + gn)) : zero4;
+                if (b_lin > 0) {
+                    uint4 r = zero4;
+                    if (gn < N && gk < ke) {
+                        const int bb = gk / b_lout, t = gk - bb * b_lout, sx = 2 * t - 2 + (gn >> 6);
+                        if (sx >= 0 && sx < b_lin)
+                            r = __ldg(reinterpret_cast<const uint4*>(B + ((long long)bb * b_lin + sx) * kC + (gn & 63)));
+                    }
+                    rb[i] = r;
+                } else {
+                    rb[i] = (gn < N && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(B + (long long)gk * ldb + gn))
+                                                : zero4;
+                }
             }
         }
     };
@@ -274,19 +302,6 @@ __global__ void __launch_bounds__(128) gemm_bf16_vec(int M, int N, int K, const 
                 C[o] = v;
                 if (Cb) Cb[o] = __float2bfloat16(v);
             }
-}
-
-// im2col of a [B][Lin][64] activation (BF16): row (b, t) of [B*Lout][320]
-// holds x[b][2t - 2 + k][c] at column k * 64 + c (0 outside the window)
-__global__ void im2col(const __nv_bfloat16* X, int Bn, int Lin, int Lout, __nv_bfloat16* A) {
-    const long long n = (long long)Bn * Lout * kKC;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int col = (int)(i % kKC);
-        const long long row = i / kKC;
-        const int t = (int)(row % Lout), b = (int)(row / Lout);
-        const int k = col / kC, c = col % kC, s = 2 * t - 2 + k;
-        A[i] = (s >= 0 && s < Lin) ? X[((long long)b * Lin + s) * kC + c] : __float2bfloat16(0.f);
-    }
 }
 
 // the adjoint of im2col: dX[b][s][c] = sum over (t, k) with 2t - 2 + k = s of dA[(b,t)][k*64+c]
@@ -570,7 +585,7 @@ struct cmh_net {
     float *p = nullptr, *gr = nullptr, *m1 = nullptr, *m2 = nullptr;
     __nv_bfloat16* pb = nullptr;
     // activations (FP32 and BF16 copies) and gradients
-    __nv_bfloat16 *x0 = nullptr, *col = nullptr;
+    __nv_bfloat16* x0 = nullptr;
     float *y[4] = {nullptr}, *h = nullptr, *o = nullptr, *dO = nullptr, *dh = nullptr, *dcol = nullptr;
     __nv_bfloat16 *yb[4] = {nullptr}, *hb = nullptr, *dOb = nullptr, *dhb = nullptr, *dyb = nullptr;
     float *dy = nullptr, *dx = nullptr, *loss = nullptr, *tl = nullptr, *ml = nullptr;
@@ -602,7 +617,7 @@ constexpr long long kWsFloats = (long long)kMaxSplits * kC * kKC;   // split par
 template <bool TA, bool TB>
 cudaError_t gemm(cudaStream_t s, float* ws, int M, int N, int K, const __nv_bfloat16* A, int lda,
                  const __nv_bfloat16* B, int ldb, float* C, int ldc, const float* bias, int relu, int acc,
-                 __nv_bfloat16* Cb) {
+                 __nv_bfloat16* Cb, int a_lin = 0, int a_lout = 0, int b_lin = 0, int b_lout = 0) {
     const int gx = (N + GB - 1) / GB, gy = (M + GB - 1) / GB, tiles = gx * gy;
     int splits = 1, kc = K;
     if (ws && !bias && !relu && !acc && !Cb && ldc == N && tiles < 152) {
@@ -623,8 +638,10 @@ cudaError_t gemm(cudaStream_t s, float* ws, int M, int N, int K, const __nv_bflo
     const float* bs = splits > 1 ? nullptr : bias;
     const int rl = splits > 1 ? 0 : relu, ac = splits > 1 ? 0 : acc;
     __nv_bfloat16* cb = splits > 1 ? nullptr : Cb;
+    if ((a_lin > 0 || b_lin > 0) && !vec) return cudaErrorInvalidValue;   // im2col operands need the vector loader
     if (vec)
-        gemm_bf16_vec<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, out, ldc, bs, rl, ac, cb, kc);
+        gemm_bf16_vec<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, out, ldc, bs, rl, ac, cb, kc, a_lin,
+                                                   a_lout, b_lin, b_lout);
     else
         gemm_bf16<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, out, ldc, bs, rl, ac, cb, kc);
     if (splits > 1) sum_splits<<<blocks_for((long long)M * N), 256, 0, s>>>(ws, (long long)M * N, splits, C);
@@ -648,9 +665,9 @@ cudaError_t forward(cmh_net* n, int Bn) {
     for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
         const int Lin = kLin[l], Lout = kLin[l + 1];
         const long long rows = (long long)Bn * Lout;
-        im2col<<<blocks_for(rows * kKC), 256, 0, s>>>(in, Bn, Lin, Lout, n->col);
-        e = gemm<false, true>(s, n->ws, (int)rows, kC, kKC, n->col, kKC, n->pb + l * kConvP, kKC, n->y[l], kC,
-                              n->p + l * kConvP + kConvW, 1, 0, n->yb[l]);
+        // the im2col matrix of `in` is read in place by the product
+        e = gemm<false, true>(s, n->ws, (int)rows, kC, kKC, in, 0, n->pb + l * kConvP, kKC, n->y[l], kC,
+                              n->p + l * kConvP + kConvW, 1, 0, n->yb[l], Lin, Lout);
         in = n->yb[l];
     }
     if (e) return e;
@@ -690,12 +707,10 @@ cudaError_t backward(cmh_net* n, int Bn) {
         const long long rows = (long long)Bn * Lout;
         // through the ReLU of layer l
         relu_back<<<blocks_for(rows * kC), 256, 0, s>>>(n->dy, n->y[l], rows * kC, n->dy, n->dyb);
-        // recompute this layer's im2col input
+        // dW = dy^T col (the layer input's im2col matrix read in place), db = colsum dy
         const __nv_bfloat16* in = l == 0 ? n->x0 : n->yb[l - 1];
-        im2col<<<blocks_for(rows * kKC), 256, 0, s>>>(in, Bn, Lin, Lout, n->col);
-        // dW = dy^T col, db = colsum dy
-        if ((e = gemm<true, false>(s, n->ws, kC, kKC, (int)rows, n->dyb, kC, n->col, kKC, n->gr + l * kConvP, kKC, nullptr, 0,
-                                   0, nullptr)))
+        if ((e = gemm<true, false>(s, n->ws, kC, kKC, (int)rows, n->dyb, kC, in, 0, n->gr + l * kConvP, kKC, nullptr, 0,
+                                   0, nullptr, 0, 0, Lin, Lout)))
             return e;
         colsum(s, n->ws, n->dy, (int)rows, kC, n->gr + l * kConvP + kConvW);
         if (l == 0) break;
@@ -737,7 +752,7 @@ extern "C" int cmh_net_create(int32_t max_batch, uint64_t seed, void* cuda_strea
     const long long B = max_batch;
     bool ok = n->alloc(&n->p, kNParam) && n->alloc(&n->gr, kNParam) && n->alloc(&n->m1, kNParam) &&
               n->alloc(&n->m2, kNParam) && n->alloc(&n->pb, kNParam) && n->alloc(&n->x0, B * kNL * kNS) &&
-              n->alloc(&n->col, B * 128 * kKC) && n->alloc(&n->h, B * kF1Out) && n->alloc(&n->hb, B * kF1Out) &&
+              n->alloc(&n->h, B * kF1Out) && n->alloc(&n->hb, B * kF1Out) &&
               n->alloc(&n->o, B * kNOut) && n->alloc(&n->dO, B * kNOut) && n->alloc(&n->dOb, B * kNOut) &&
               n->alloc(&n->dh, B * kF1Out) && n->alloc(&n->dhb, B * kF1Out) && n->alloc(&n->dcol, B * 128 * kKC) &&
               n->alloc(&n->dy, B * 128 * kC) && n->alloc(&n->dyb, B * 128 * kC) && n->alloc(&n->dx, B * 256 * kC) &&

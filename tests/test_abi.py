@@ -52,9 +52,14 @@ def _params(cm, **kw):
     dict(schedule=2),
     dict(ctas_per_sm=4),
     dict(dtype=7),
+    dict(likelihood=2),
+    dict(likelihood=1, dtype=0),   # the additive-mean reading is float32 only
 ])
 def test_create_model_rejects_bad_params_on_host(cm, bad):
+    lik = bad.pop("likelihood", None)
     p = _params(cm, **bad)
+    if lik is not None:
+        p.likelihood = lik
     h = C.c_void_p()
     st = np.zeros((1, 2))
     sig = np.zeros((1, 10))
@@ -95,3 +100,22 @@ def test_null_handles(cm):
     assert cm.lib.cmh_batch_create(arr, 1, None, C.byref(h)) == -1 and not h.value
     assert cm.lib.cmh_batch_run_sweeps(None, 1) == -1
     cm.lib.cmh_batch_destroy(None)
+
+
+def test_null_handles_of_the_learned_proposal_and_async_reads(cm):
+    f = np.zeros(4, dtype=np.float32)
+    assert cm.lib.cmh_set_birth_table(None, None, 0, 0, 0, 0.0) == -1
+    assert cm.lib.cmh_set_birth_magnitude(None, None, 0.0) == -1
+    assert cm.lib.cmh_read_state_async(None, 0) == -1
+    assert cm.lib.cmh_read_state_fetch(None, 0, None, None, 0, None, None, None) == -1
+    assert cm.lib.cmh_autotune(None, 1, None) == -1
+    assert cm.lib.cmh_batch_sync(None) == -1
+    h = C.c_void_p()
+    assert cm.lib.cmh_net_create(0, 1, None, C.byref(h)) == -1 and not h.value
+    assert cm.lib.cmh_net_create(4097, 1, None, C.byref(h)) == -1 and not h.value
+    assert cm.lib.cmh_net_forward(None, C.c_void_p(f.ctypes.data), 1, C.c_void_p(f.ctypes.data)) == -1
+    assert cm.lib.cmh_net_train(None, None, 1, 1, 1e-3, None) == -1
+    assert cm.lib.cmh_net_get_params(None, C.c_void_p(f.ctypes.data)) == -1
+    assert cm.lib.cmh_net_birth_table(None, None, None, None, 1, 1, 1, 1, 1.0, None, None) == -1
+    assert cm.lib.cmh_net_param_count() > 2_000_000
+    cm.lib.cmh_net_destroy(None)

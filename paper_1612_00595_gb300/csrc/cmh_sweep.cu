@@ -104,6 +104,30 @@ __device__ __forceinline__ double arr_c64(const Geo& g, double af, double lnA2, 
     return exp(lnA2 - ((double)k - af) * (2.0 / (g.f_hz * g.tau)));
 }
 
+// log(1 + x): for |x| < 1/16 the Taylor series sum (-1)^(n+1) x^n / n through
+// n = 13 in Horner form (truncation below |x|^14 / 14, under 2e-18 relative),
+// else the library's log1p.  Most priced samples lie in an arrival's tail,
+// where x = d / V is small.
+__device__ __forceinline__ double log1p_series64(double x) {
+    if (fabs(x) < 0.0625) {
+        double p = 1.0 / 13.0;
+        p = fma(p, x, -1.0 / 12.0);
+        p = fma(p, x, 1.0 / 11.0);
+        p = fma(p, x, -1.0 / 10.0);
+        p = fma(p, x, 1.0 / 9.0);
+        p = fma(p, x, -1.0 / 8.0);
+        p = fma(p, x, 1.0 / 7.0);
+        p = fma(p, x, -1.0 / 6.0);
+        p = fma(p, x, 1.0 / 5.0);
+        p = fma(p, x, -1.0 / 4.0);
+        p = fma(p, x, 1.0 / 3.0);
+        p = fma(p, x, -0.5);
+        p = fma(p, x, 1.0);
+        return p * x;
+    }
+    return log1p(x);
+}
+
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     const float y = x - c;
     const float t = s + y;
@@ -449,21 +473,27 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
         if (valid) {
             {
                 double acc = 0.0;
+                // a thread's samples are nthr apart: an arrival's contribution
+                // at the next one is this one times rstep (one exp at the
+                // first sample inside the window, then a product per sample)
+                const double rstep = exp(-(double)nthr * (2.0 / (g.f_hz * g.tau)));
                 for (int ti = 0; ti < ntask; ++ti) {
                     const Task& T = tasks[ti];
                     const double* srow = (const double*)d.sig + (size_t)T.row * g.pitch;
                     const double* vrow = (const double*)d.V + (size_t)T.row * g.pitch;
+                    double co = -1.0, cn = -1.0;   // running contributions (< 0: not started)
                     for (int kk = T.lo + tid; kk < T.hi; kk += nthr) {
                         const int ro = kk - T.k0o, rn = kk - T.k0n;
                         const bool io = T.has_o && (unsigned)ro < (unsigned)g.n_w;
                         const bool inn = T.has_n && (unsigned)rn < (unsigned)g.n_w;
+                        // each running value advances on every sample of its own window
+                        if (io) co = co < 0.0 ? arr_c64(g, T.afo, T.lnA2o, kk) : co * rstep;
+                        if (inn) cn = cn < 0.0 ? arr_c64(g, T.afn, T.lnA2n, kk) : cn * rstep;
                         double dd = 0.0;
-                        if (io) {
-                            const double co = arr_c64(g, T.afo, T.lnA2o, kk);
+                        if (io)
                             dd = inn ? co * T.rm1d : -co;
-                        } else if (inn) {
-                            dd = arr_c64(g, T.afn, T.lnA2n, kk);
-                        }
+                        else if (inn)
+                            dd = cn;
                         if (dd != 0.0) {
                             const double V = vrow[kk], s = __ldg(srow + kk);
                             const double Vp = V + dd;
@@ -477,7 +507,8 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
                                 if (inn) a2 += arr_c64(g, T.afn, T.lnA2n, kk);
                                 acc += -0.5 * (log(a2 / V) + s * s * (1.0 / a2 - 1.0 / V));
                             } else {
-                                acc += -0.5 * (log1p(dd / V) - s * s * dd / (V * Vp));
+                                const double inv = 1.0 / (V * Vp);   // one division for both terms
+                                acc += -0.5 * (log1p_series64(dd * Vp * inv) - s * s * dd * inv);
                             }
                         }
                     }

@@ -1359,11 +1359,24 @@ extern "C" int cmh_batch_create(cmh_model* const* models, int32_t n_models, void
         cudaMemcpy(b->blk_off, off.data(), sizeof(int) * (n_models + 1), cudaMemcpyHostToDevice))
         return fail(CMH_ERR_CUDA);
     if (prepare_rebin_batch(b->max_ev_cap)) return fail(CMH_ERR_CUDA);
+    // a group's sweep lasts as long as its slowest instance's colour chain:
+    // the work queue takes instances by an estimate of their region cost
+    // (events per region x blanket stations), largest first, so the longest
+    // chains start first (each model's own chain does not depend on the order)
+    std::vector<double> cost(n_models);
+    for (int i = 0; i < n_models; ++i) {
+        const cmh_model* m = models[i];
+        const double per_region = (double)std::max<long long>(m->n0, 1) / std::max(1, hg[i].n_cells);
+        cost[i] = (per_region + hg[i].k) * hg[i].blk_cap * (hg[i].spill ? 2.0 : 1.0);
+    }
+    std::vector<int> order(n_models);
+    for (int i = 0; i < n_models; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
     for (int f = 3; f >= 1; --f) {   // groups: 3, 2, then 1 resident region per SM
         std::vector<Geo> gg;
         std::vector<Dev> gd;
         BatchGroup q;
-        for (int i = 0; i < n_models; ++i)
+        for (int i : order)
             if (fit[i] == f) {
                 gg.push_back(hg[i]);
                 gd.push_back(hd[i]);

@@ -492,13 +492,64 @@ def run_learned(args):
     print(json.dumps(line))
 
 
+def run_learned_posterior(args):
+    """Long-run posterior summaries of the plain sampler and of the learned
+    birth mixture on the 1000 x 1000 km, 1 h, 100-station float32 world: 4
+    chains each from the empty set; summaries every 100 sweeps over sweeps
+    2000-4000 (both) and 14000-16000 (plain).  Both chains target the same
+    posterior; the plain chain's summaries judge the learned chain's."""
+    import torch
+    import paper_1612_00595_gb300 as cm
+    from paper_1612_00595_gb300 import metrics
+    torch.cuda.set_device(0)
+    w = worldgen.config_learned(seed=SEED)
+    P = w.params
+    net = cm.Net(max_batch=256, seed=CHAIN_SEED)
+    geo = cm.create_model(None, w.stations, w.signals, cm.make_params(P, k_per_phase=K_PER_PHASE, dtype=cm.F32))
+    net.train(geo, 4000, 256, 3e-4)
+    tab, centre = net.birth_table(geo, *cm.grid_tiles(10, 100.0), 80, 80, 360, hop_s=12.8, magnitudes=True)
+    net.destroy()
+    geo.destroy()
+
+    def chain(learned, seed, burn, n):
+        m = cm.create_model(None, w.stations, w.signals,
+                            cm.make_params(P, k_per_phase=K_PER_PHASE, seed=seed, dtype=cm.F32))
+        m.partition_and_color(P.L)
+        if learned:
+            m.set_birth_table(tab, 0.5)
+            m.set_birth_magnitude(centre, MAG_HALF_WIDTH)
+        m.run_sweeps(burn)
+        rows = []
+        for _ in range((n - burn) // 100):
+            m.run_sweeps(100)
+            ev, _, lp, _ = m.read_state()
+            sc = metrics.scores(w.events, ev, P.L, P.tau, w.stations, P.R_max)
+            rows.append((sc["f1"], sc["precision"], sc["recall"], sc["loc_err"],
+                         float(metrics.detectable(ev, w.stations, P.R_max).sum()), lp))
+        m.destroy()
+        return np.array(rows).mean(axis=0)
+
+    keys = ["f1", "precision", "recall", "loc_err_km", "detectable_events", "log_density"]
+    runs = {"plain_2000_4000": (False, 2000, 4000), "plain_14000_16000": (False, 14000, 16000),
+            "learned_2000_4000": (True, 2000, 4000)}
+    out = {}
+    for name, (learned, burn, n) in runs.items():
+        per = np.array([chain(learned, CHAIN_SEED + 100 + i, burn, n) for i in range(4)])
+        out[name] = {k: {"mean": float(per[:, j].mean()), "se": float(per[:, j].std(ddof=1) / 2.0),
+                         "chains": [round(float(x), 4) for x in per[:, j]]} for j, k in enumerate(keys)}
+    print(json.dumps({"metric": "posterior summaries, plain vs learned birth mixture", "unit": "summaries",
+                      "config": {"workload": "1000x1000 km, 1 h, Lambda 500, 100 stations, f32, 4 chains per "
+                                             "entry, empty start, summaries every 100 sweeps over the window"},
+                      "data": "synthetic (seeded worldgen)", "results": out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="scale", choices=["scale", "replay", "batched", "learned"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "replay", "batched", "learned", "learned-posterior"])
     ap.add_argument("--likelihood", default="variance", choices=["variance", "mean"],
                     help="scale workload: arrivals add to the sample variance (default) or to its mean")
     args = ap.parse_args()
@@ -510,6 +561,8 @@ def main():
         run_batched(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "learned-posterior":
+        run_learned_posterior(args)
     else:
         run_ours(args)
 

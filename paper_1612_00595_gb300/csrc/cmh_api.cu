@@ -617,7 +617,7 @@ int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mo
         (e = m->alloc(&d.fill, g.n_cells, true)) || (e = m->alloc(&d.ncell, g.store_cap, true)) ||
         (e = m->alloc(&d.cell_col, g.n_cells, true)) || (e = m->alloc(&d.colour_off, kMaxColours + 1, true)) ||
         (e = m->alloc(&d.queue, 1, true)) || (e = m->alloc(&d.done, g.n_cells, true)) ||
-        (e = m->alloc(&d.region_dlp, g.n_cells, true)))
+        (e = m->alloc(&d.region_dlp, g.n_cells, true)) || (e = m->alloc(&d.flat_off, g.n_cells + 1, true)))
         return cuda_err(e);
     {
         // blanket candidates: a cell's region is [s + (i-1) L, s + i L) per axis

@@ -95,6 +95,7 @@ struct Dev {
     int* colour_off;            // [n_colours + 1] first queue item of each colour (persistent sweep)
     int* queue;                 // next queue item (persistent sweep)
     long long* done;            // [n_cells] last sweep + 1 whose phase the cell's region has finished
+    int* flat_off;              // [n_cells + 1] first flat-list position of each cell (flattening scratch)
     const int* bl_off;          // [n_cells + 1] blanket candidates of each cell: the stations that may lie
     const int* bl_idx;          //   within R_max of its region under any shift, in station order
     double* region_dlp;         // [n_cells] log-density change of the current sweep

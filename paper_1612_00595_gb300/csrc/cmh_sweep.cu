@@ -775,18 +775,18 @@ __global__ void __launch_bounds__(kSynthThreads) vsynth_kernel(Geo g, Dev d, con
     }
 }
 
-// copy the events of store `buf` into a flat list, cells in index order
-__global__ void __launch_bounds__(1024) flatten_kernel(Geo g, Dev d, int buf, double* fx, double* fy, double* ft,
-                                                       double* fm, unsigned long long* fid, int* n_out) {
+// the flat list of store `buf` (cells in index order, events in their
+// order): first each cell's position, an exclusive prefix of the counts (one
+// block), then a warp per cell copies its events (lanes over events)
+__global__ void __launch_bounds__(1024) flatten_scan(Geo g, Dev d, int buf, int* n_out) {
     const Store S = d.st[buf];
     __shared__ int s_warp[32], s_base;
     if (threadIdx.x == 0) s_base = 0;
     __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int c0 = 0; c0 < g.n_cells; c0 += blockDim.x) {
         const int c = c0 + threadIdx.x;
         const int n = c < g.n_cells ? S.count[c] : 0;
-        // exclusive prefix of n across the block, then advance the base
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
         int x = n;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(FULL, x, o);
@@ -799,22 +799,30 @@ __global__ void __launch_bounds__(1024) flatten_kernel(Geo g, Dev d, int buf, do
             if (w < wid) before += s_warp[w];
             all += s_warp[w];
         }
-        const int off = s_base + before + x - n;
-        if (n) {
-            const int s0 = S.start[c];
-            for (int i = 0; i < n; ++i) {
-                fx[off + i] = S.x[s0 + i];
-                fy[off + i] = S.y[s0 + i];
-                ft[off + i] = S.t[s0 + i];
-                fm[off + i] = S.m[s0 + i];
-                fid[off + i] = S.id[s0 + i];
-            }
-        }
+        if (c < g.n_cells) d.flat_off[c] = s_base + before + x - n;
         __syncthreads();
         if (threadIdx.x == 0) s_base += all;
         __syncthreads();
     }
-    if (threadIdx.x == 0) *n_out = s_base;
+    if (threadIdx.x == 0) {
+        d.flat_off[g.n_cells] = s_base;
+        *n_out = s_base;
+    }
+}
+
+__global__ void __launch_bounds__(256) flatten_copy(Geo g, Dev d, int buf, double* fx, double* fy, double* ft,
+                                                    double* fm, unsigned long long* fid) {
+    const Store S = d.st[buf];
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (c >= g.n_cells) return;
+    const int n = S.count[c], s0 = S.start[c], off = d.flat_off[c];
+    for (int i = lane; i < n; i += 32) {
+        fx[off + i] = S.x[s0 + i];
+        fy[off + i] = S.y[s0 + i];
+        ft[off + i] = S.t[s0 + i];
+        fm[off + i] = S.m[s0 + i];
+        fid[off + i] = S.id[s0 + i];
+    }
 }
 
 // sum over all stations and samples of log N(s; 0, V) (or, with the additive
@@ -909,8 +917,9 @@ cudaError_t launch_vsynth(const Geo& g, const Dev& d, const FlatList& f, cudaStr
 }
 
 cudaError_t launch_flatten(const Geo& g, const Dev& d, int buf, const FlatList& f, cudaStream_t s, int* launches) {
-    flatten_kernel<<<1, 1024, 0, s>>>(g, d, buf, f.x, f.y, f.t, f.m, f.id, f.n);
-    if (launches) *launches += 1;
+    flatten_scan<<<1, 1024, 0, s>>>(g, d, buf, f.n);
+    flatten_copy<<<(g.n_cells + 7) / 8, 256, 0, s>>>(g, d, buf, f.x, f.y, f.t, f.m, f.id);
+    if (launches) *launches += 2;
     return cudaGetLastError();
 }
 

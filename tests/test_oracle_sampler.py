@@ -26,9 +26,9 @@ PB, PD = 0.25, 0.25
 PMV = 1.0 - PB - PD
 
 
-def _lattice_world(orc, shift_cells=False):
+def _lattice_world(orc, shift_cells=False, likelihood="variance"):
     p = worldgen.ModelParams(W=200.0, T=60.0, Lambda=1.5, v=6.0, alpha=0.5, beta_att=0.01,
-                             tau=5.0, t_s=10.0, f_hz=1.0, R_max=50.0, L=100.0)
+                             tau=5.0, t_s=10.0, f_hz=1.0, R_max=50.0, L=100.0, likelihood=likelihood)
     st = np.array([[50.0, 50.0], [150.0, 150.0], [60.0, 140.0]])
     truth = np.array([[75.0, 75.0, 10.0, 3.5], [125.0, 175.0, 30.0, 2.5]])
     w = worldgen.make_world(p, st, seed=77, events=truth)
@@ -133,9 +133,11 @@ def _kernel(o, lat, pts, states, index, cell, sx, sy):
     return P
 
 
-@pytest.fixture(scope="module")
-def lattice_case(orc):
-    w, lat = _lattice_world(orc)
+@pytest.fixture(scope="module", params=["variance", "mean"])
+def lattice_case(orc, request):
+    """The lattice world under each likelihood reading: the exact posterior by
+    enumeration, which every sampler must leave invariant."""
+    w, lat = _lattice_world(orc, likelihood=request.param)
     o = orc.World(w, p_birth=PB, p_death=PD, k_per_phase=10, seed=3, lattice=lat)
     pts, states, index, pi = _enumerate(o, lat, w.params)
     return o, lat, pts, states, index, pi

@@ -81,3 +81,36 @@ def test_batch_rejects_unsuitable_models():
     b.destroy()
     m.destroy()
     f64.destroy()
+
+
+def test_mean_reading_batch_equals_each_model_alone():
+    """The batch kernel of the additive reading: a batch of such models gives
+    each model's own chain bit for bit; a batch mixing readings is refused."""
+    cm = lib()
+    import worldgen
+    ws = [worldgen.config_scale(seed=s, side_regions=3, T=900.0, likelihood="mean") for s in (3, 4)]
+    def make(i, w):
+        m = cm.create_model(w.events, w.stations, w.signals,
+                            cm.make_params(w.params, k_per_phase=16, seed=60 + i, dtype=cm.F32))
+        m.partition_and_color(w.params.L, 1)
+        return m
+    alone = [make(i, w) for i, w in enumerate(ws)]
+    for m in alone:
+        m.run_sweeps(5)
+    ref = [m.read_state() for m in alone]
+    batched = [make(i, w) for i, w in enumerate(ws)]
+    b = cm.create_batch(batched)
+    b.run_sweeps(5)
+    b.sync()
+    for (e0, i0, l0, _), m in zip(ref, batched):
+        e1, i1, l1, _ = m.read_state()
+        assert np.array_equal(e0, e1) and np.array_equal(i0, i1) and l0 == l1
+    b.destroy()
+    wv = worldgen.config_scale(seed=5, side_regions=3, T=900.0)
+    mv = cm.create_model(wv.events, wv.stations, wv.signals,
+                         cm.make_params(wv.params, k_per_phase=16, seed=1, dtype=cm.F32))
+    mv.partition_and_color(wv.params.L, 1)
+    with pytest.raises(cm.ChromhError):
+        cm.create_batch([batched[0], mv])
+    for m in alone + batched + [mv]:
+        m.destroy()

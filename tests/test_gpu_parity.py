@@ -215,12 +215,14 @@ def test_fp32_chain_tracks_recomputed_log_density(cm, init):
     m.destroy()
 
 
-def test_fp32_staging_modes_agree(cm):
+@pytest.mark.parametrize("likelihood", ["variance", "mean"])
+def test_fp32_staging_modes_agree(cm, likelihood):
     """Station windows staged in shared memory by bulk copies (automatic
     size), staged only where they fit in 64 samples, or read from global
     memory (the default): the same arithmetic on the same values, so the
     chains agree bit for bit."""
-    w = small_world(seed=18, W=1000.0, T=3600.0, Lambda=500.0, n_side=10, dtype=np.float32)
+    w = small_world(seed=18, W=1000.0, T=3600.0, Lambda=500.0, n_side=10, dtype=np.float32,
+                    likelihood=likelihood)
     runs = []
     for stage in (-1, 64, 0):
         m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=6, k=32, events=w.events, seed=9, stage_samples=stage)
@@ -233,11 +235,13 @@ def test_fp32_staging_modes_agree(cm):
         assert np.array_equal(tr, runs[0][3])
 
 
-def test_fp32_persistent_sweep_matches_colour_by_colour(cm):
+@pytest.mark.parametrize("likelihood", ["variance", "mean"])
+def test_fp32_persistent_sweep_matches_colour_by_colour(cm, likelihood):
     """One persistent launch per sweep, each region waiting only for its
     lower-colour neighbours, gives the chain of the colour-by-colour
     schedule bit for bit (the same steps see the same neighbour states)."""
-    w = small_world(seed=19, W=1000.0, T=3600.0, Lambda=500.0, n_side=10, dtype=np.float32)
+    w = small_world(seed=19, W=1000.0, T=3600.0, Lambda=500.0, n_side=10, dtype=np.float32,
+                    likelihood=likelihood)
     runs = []
     for schedule in (0, 1):
         m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=8, k=32, events=w.events, seed=13, schedule=schedule)

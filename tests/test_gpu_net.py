@@ -178,3 +178,28 @@ def test_learned_proposal_reaches_f1_sooner(trained):
     print("sweeps to F1 >= 0.9: plain %s learned %s" % (hit["plain"], hit["learned"]))
     assert np.mean(rec["learned"]) > np.mean(rec["plain"]) + 0.1
     assert max(hit["learned"]) < min(hit["plain"])
+
+
+def test_training_on_the_additive_reading():
+    """The window simulator follows the model's reading (arrivals add to the
+    sample mean here): after training on such windows, the table made from a
+    world of that reading concentrates on its detectable events."""
+    cm = lib()
+    w = small_world(seed=43, W=1000.0, T=1800.0, Lambda=250.0, n_side=10, dtype=np.float32, likelihood="mean")
+    m = cm.create_model(None, w.stations, w.signals, cm.make_params(w.params, k_per_phase=32, seed=1, dtype=cm.F32))
+    net = cm.Net(max_batch=256, seed=9)
+    l0 = net.train(m, 1, 256, 3e-4)
+    l1 = net.train(m, 2000, 256, 3e-4)
+    tab = net.birth_table(m, *cm.grid_tiles(10, 100.0), 80, 80, 180, hop_s=12.8).astype(np.float64)
+    dens = tab / tab.sum()
+    det = np.array([np.min(np.hypot(w.stations[:, 0] - e[0], w.stations[:, 1] - e[1])) < w.params.R_max
+                    for e in w.events])
+    vals = [dens[max(0, iy - 2):iy + 3, max(0, ix - 2):ix + 3, max(0, b - 1):b + 2].mean()
+            for ix, iy, b in ((int(x / w.params.W * 80), int(y / w.params.W * 80), int(t / w.params.T * 180))
+                              for x, y, t, _ in w.events[det])]
+    gain = np.mean(vals) / dens.mean()
+    print("loss %.3f -> %.3f, table density near detectable events / mean: %.1f" % (l0, l1, gain))
+    assert np.isfinite(l1) and l1 < l0
+    assert gain > 4.0
+    net.destroy()
+    m.destroy()

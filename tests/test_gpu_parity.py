@@ -291,14 +291,15 @@ def _table_for(w, nx=40, nt=36, seed=3):
     return tab
 
 
-@pytest.mark.parametrize("magnitudes", [False, True])
-def test_fp32_dry_run_with_learned_birth_table(cm, orc, magnitudes):
+@pytest.mark.parametrize("magnitudes,likelihood", [(False, "variance"), (True, "variance"), (True, "mean")])
+def test_fp32_dry_run_with_learned_birth_table(cm, orc, magnitudes, likelihood):
     """Birth proposals from the mixture with a table: the same candidates on
     both sides (the table draw runs in explicitly rounded float64), Δℓ within
     1e-4 and log α (which now carries the mixture density) likewise.  With
     learned magnitudes the table births draw m from their entry's window
     (float64 on both sides), and the density carries the window."""
-    w = small_world(seed=16, W=1000.0, T=3600.0, Lambda=500.0, n_side=10, dtype=np.float32)
+    w = small_world(seed=16, W=1000.0, T=3600.0, Lambda=500.0, n_side=10, dtype=np.float32,
+                    likelihood=likelihood)
     tab = _table_for(w)
     params = cm.make_params(w.params, k_per_phase=32, seed=21, dtype=cm.F32, commit=False)
     m = cm.create_model(w.events, w.stations, w.signals, params)

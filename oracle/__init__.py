@@ -8,6 +8,8 @@ Functions follow the paper's statement of the method:
   * ``log_prior`` / ``log_likelihood`` / ``log_density`` -- the joint density
     P(e, a, s) of §Generative Model of Seismic Signals (zero-jitter arrivals);
   * ``delta_loglik`` -- the change of the log-likelihood for one proposal;
+  * ``log_alpha`` / ``log_alpha_pair`` -- the acceptance ratio of one explicit
+    proposal (birth, death, move; the joint move of a pair);
   * ``run_serial`` -- Algorithm "Serial Metropolis Hastings";
   * ``run_chromatic`` -- Algorithm "Chromatic MH with Static Coloring" and the
     dynamic variant of §Chromatic MH with Dynamic Coloring (shift_mode=1);
@@ -55,7 +57,7 @@ class _Params(C.Structure):
         ("lattice", C.c_int32), ("lat_nx", C.c_int32), ("lat_ny", C.c_int32), ("lat_nt", C.c_int32),
         ("lat_nm", C.c_int32), ("lat_nmax", C.c_int32), ("likelihood", C.c_int32)] + [
         (n, C.c_double) for n in ("lat_x0", "lat_dx", "lat_y0", "lat_dy", "lat_t0", "lat_dt",
-                                  "lat_m0", "lat_dm")]
+                                  "lat_m0", "lat_dm", "p_pair")]
 
 
 TRACE_DTYPE = np.dtype([("sweep", "<i4"), ("cell", "<i4"), ("step", "<i4"), ("type", "<i4"),
@@ -93,6 +95,7 @@ def lib(mutant: int = 0):
             "orc_shift": (None, [P, i64, pd, pd]),
             "orc_blankets": (None, [P, d, d, P]),
             "orc_log_alpha": (d, [P, d, d, i32, P, i64, i32, i64, P, C.POINTER(i32)]),
+            "orc_log_alpha_pair": (d, [P, d, d, i32, P, i64, i64, i64, P, P, C.POINTER(i32)]),
             "orc_run_serial": (C.c_int, [P, P, i64, i64, P, i64, C.POINTER(i64), pd]),
             "orc_run_chromatic": (C.c_int, [P, P, i64, i64, i32, d, d, P, i64, C.POINTER(i64),
                                             i32, pd]),
@@ -140,7 +143,7 @@ class World:
 
     def __init__(self, world, p_birth=0.25, p_death=0.25, sig_xy=5.0, sig_t=2.0, sig_m=0.1,
                  k_per_phase=32, seed=1, commit=True, lattice: Optional[Lattice] = None,
-                 mutant: int = 0):
+                 mutant: int = 0, p_pair=0.0):
         self._lib = lib(mutant)
         p = world.params
         self.world = world
@@ -149,7 +152,7 @@ class World:
         for n in ("W", "T", "Lambda", "v", "alpha", "beta_att", "tau", "t_s", "noise_var", "f_hz",
                   "R_max", "L"):
             setattr(prm, n, float(getattr(p, n)))
-        prm.p_birth, prm.p_death = p_birth, p_death
+        prm.p_birth, prm.p_death, prm.p_pair = p_birth, p_death, p_pair
         prm.sig_xy, prm.sig_t, prm.sig_m = sig_xy, sig_t, sig_m
         prm.n_w = p.n_w
         prm.k_per_phase = k_per_phase
@@ -269,6 +272,17 @@ class World:
         v = C.c_int32()
         la = self._lib.orc_log_alpha(self._h, sx, sy, int(cell), _ptr(ev), ev.shape[0], int(type_),
                                  int(idx), _ptr(c), C.byref(v))
+        return la, bool(v.value)
+
+    def log_alpha_pair(self, sx, sy, cell, ev, i, j, cand1, cand2):
+        """Log acceptance ratio of the joint move of the region's i-th and j-th
+        events to cand1 and cand2 (§MH moves, "Joint Events Move")."""
+        ev = np.ascontiguousarray(ev, dtype=np.float64).reshape(-1, 4)
+        c1 = np.ascontiguousarray(cand1, dtype=np.float64)
+        c2 = np.ascontiguousarray(cand2, dtype=np.float64)
+        v = C.c_int32()
+        la = self._lib.orc_log_alpha_pair(self._h, sx, sy, int(cell), _ptr(ev), ev.shape[0], int(i),
+                                          int(j), _ptr(c1), _ptr(c2), C.byref(v))
         return la, bool(v.value)
 
     # ---- samplers ----------------------------------------------------------

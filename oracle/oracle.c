@@ -41,7 +41,8 @@
  *   5: the birth and death terms use the uniform density although births
  *      come from the mixture with a learned table;
  *   6: with learned magnitudes, the learned component's density keeps the
- *      prior magnitude law although it draws m from its window.
+ *      prior magnitude law although it draws m from its window;
+ *   7: the joint move of a pair ignores the prior ratio.
  * 0 (the default) is the oracle itself. */
 #ifndef ORC_MUTANT
 #define ORC_MUTANT 0
@@ -411,6 +412,54 @@ double orc_delta_loglik(const orc_world* w, const double* ev, int64_t n,
     return d;
 }
 
+/* log-likelihood change of a joint move: own[i1] and own[i2] become c1 and
+ * c2.  Same plain definition: at every station one of the four events
+ * reaches, over the span of their windows, the two Gaussian log-densities
+ * with each predicted value summed from scratch. */
+static double delta_ll_pair(const orc_world* w, const ev_t* own, int64_t n_own, const ev_t* oth,
+                            int64_t n_oth, int64_t i1, int64_t i2, const ev_t* c1, const ev_t* c2) {
+    double total = 0.0;
+    int64_t cap = n_own + n_oth;
+    arr_t* ar = (arr_t*)malloc(sizeof(arr_t) * (size_t)(cap > 0 ? cap : 1));
+    for (int32_t j = 0; j < w->n_st; ++j) {
+        arr_t ch[4];
+        ch[0] = arrival_of(w, &own[i1], j);
+        ch[1] = arrival_of(w, &own[i2], j);
+        ch[2] = arrival_of(w, c1, j);
+        ch[3] = arrival_of(w, c2, j);
+        int64_t lo = INT64_MAX, hi = INT64_MIN;
+        for (int q = 0; q < 4; ++q) {
+            if (!ch[q].reach) continue;
+            if (ch[q].k0 < lo) lo = ch[q].k0;
+            if (ch[q].k0 + w->p.n_w > hi) hi = ch[q].k0 + w->p.n_w;
+        }
+        if (lo == INT64_MAX) continue;
+        if (lo < 0) lo = 0;
+        if (hi > w->n_samp) hi = w->n_samp;
+        if (lo >= hi) continue;
+        int64_t na = 0;
+        for (int64_t i = 0; i < n_own; ++i) {
+            if (i == i1 || i == i2) continue;
+            arr_t a = arrival_of(w, &own[i], j);
+            if (a.reach) ar[na++] = a;
+        }
+        for (int64_t i = 0; i < n_oth; ++i) {
+            arr_t a = arrival_of(w, &oth[i], j);
+            if (a.reach) ar[na++] = a;
+        }
+        for (int64_t k = lo; k < hi; ++k) {
+            double base = pred_base(w);
+            for (int64_t i = 0; i < na; ++i) base += arr_var(w, &ar[i], k);
+            double V_old = base + arr_var(w, &ch[0], k) + arr_var(w, &ch[1], k);
+            double V_new = base + arr_var(w, &ch[2], k) + arr_var(w, &ch[3], k);
+            double s = sig_at(w, j, k);
+            total += log_lik_sample(w, s, V_new) - log_lik_sample(w, s, V_old);
+        }
+    }
+    free(ar);
+    return total;
+}
+
 /* ------------------------------------------------------------------------
  * spatial partition (§Partitioning the World, in two spatial dimensions):
  * square cells of side L whose boundaries are shifted by (sx, sy);
@@ -663,7 +712,33 @@ static int learned_birth(const orc_world* w, const region_t* g, const uint64_t* 
  * exactly symmetric. */
 static double qgauss(double z) { return rint(fabs(z) * 1048576.0) * (1.0 / 1048576.0); }
 
-typedef struct { int32_t type, valid; int64_t idx; ev_t cand; } prop_t;
+typedef struct { int32_t type, valid; int64_t idx, idx2; ev_t cand, cand2; } prop_t;
+
+/* offset of a random-walk step: on a lattice one grid step along one of the
+ * four axes (direction from wd[2]); otherwise independent Gaussians of
+ * scales (sig_xy, sig_xy, sig_t, sig_m) by Box-Muller from wd[2..5], signs
+ * from bits 32..35 of wd[1] */
+static void walk_offset(const orc_world* w, const uint64_t* wd, double off[4]) {
+    const orc_params* p = &w->p;
+    off[0] = off[1] = off[2] = off[3] = 0.0;
+    if (p->lattice) {
+        int64_t dir = pick(wd[2], 8);
+        double step = (dir & 1) ? -1.0 : 1.0;
+        const double d[4] = { p->lat_dx, p->lat_dy, p->lat_dt, p->lat_dm };
+        off[dir >> 1] = step * d[dir >> 1];
+        return;
+    }
+    double r1 = sqrt(-2.0 * log(u01o(wd[2]))), th1 = 2.0 * M_PI * u01(wd[3]);
+    double r2 = sqrt(-2.0 * log(u01o(wd[4]))), th2 = 2.0 * M_PI * u01(wd[5]);
+    double z[4] = { qgauss(r1 * cos(th1)), qgauss(r1 * sin(th1)),
+                    qgauss(r2 * cos(th2)), qgauss(r2 * sin(th2)) };
+    for (int i = 0; i < 4; ++i)
+        if ((wd[1] >> (32 + i)) & 1) z[i] = -z[i];
+    off[0] = p->sig_xy * z[0];
+    off[1] = p->sig_xy * z[1];
+    off[2] = p->sig_t * z[2];
+    off[3] = p->sig_m * z[3];
+}
 
 static prop_t decode(const orc_world* w, const region_t* g, const uint64_t* wd,
                      const ev_t* own, int64_t n_own, int64_t n_total) {
@@ -671,8 +746,10 @@ static prop_t decode(const orc_world* w, const region_t* g, const uint64_t* wd,
     prop_t q;
     memset(&q, 0, sizeof(q));
     double u = u01(wd[0]);
-    q.type = u < p->p_birth ? 0 : (u < p->p_birth + p->p_death ? 1 : 2);
+    const double cb = p->p_birth, cd = cb + p->p_death, cp = cd + p->p_pair;
+    q.type = u < cb ? 0 : (u < cd ? 1 : (u < cp ? 3 : 2));
     q.idx = -1;
+    q.idx2 = -1;
     if (q.type == 0) {
         if (p->lattice) {
             if (n_total >= p->lat_nmax) return q;
@@ -694,31 +771,43 @@ static prop_t decode(const orc_world* w, const region_t* g, const uint64_t* wd,
         q.valid = in_region(w, g, &q.cand) && in_time_mag(w, &q.cand);
         return q;
     }
+    if (q.type == 3) {
+        /* joint move (§MH moves, "Joint Events Move"): an ordered pair of
+         * distinct events, i from wd[1] and j from wd[7] among the others.
+         * Bit 36 of wd[1] clear: the pair's other mode under the station
+         * geometry, the two events exchanging their locations while each
+         * keeps its origin time and magnitude (stations equidistant from the
+         * two see the same arrivals); set: both shifted by one common
+         * random-walk offset. */
+        if (n_own < 2) return q;
+        q.idx = pick(wd[1], n_own);
+        const int64_t j = pick(wd[7], n_own - 1);
+        q.idx2 = j + (j >= q.idx ? 1 : 0);
+        q.cand = own[q.idx];
+        q.cand2 = own[q.idx2];
+        if (((wd[1] >> 36) & 1) == 0) {
+            q.cand.x = own[q.idx2].x; q.cand.y = own[q.idx2].y;
+            q.cand2.x = own[q.idx].x; q.cand2.y = own[q.idx].y;
+        } else {
+            double off[4];
+            walk_offset(w, wd, off);
+            q.cand.x += off[0]; q.cand.y += off[1]; q.cand.t += off[2]; q.cand.m += off[3];
+            q.cand2.x += off[0]; q.cand2.y += off[1]; q.cand2.t += off[2]; q.cand2.m += off[3];
+        }
+        q.valid = in_region(w, g, &q.cand) && in_time_mag(w, &q.cand) &&
+                  in_region(w, g, &q.cand2) && in_time_mag(w, &q.cand2);
+        return q;
+    }
     if (n_own == 0) return q;
     q.idx = pick(wd[1], n_own);
     if (q.type == 1) { q.valid = 1; return q; }
     q.cand = own[q.idx];
-    if (p->lattice) {
-        int64_t dir = pick(wd[2], 8);
-        double step = (dir & 1) ? -1.0 : 1.0;
-        switch (dir >> 1) {
-            case 0: q.cand.x += step * p->lat_dx; break;
-            case 1: q.cand.y += step * p->lat_dy; break;
-            case 2: q.cand.t += step * p->lat_dt; break;
-            default: q.cand.m += step * p->lat_dm; break;
-        }
-    } else {
-        double r1 = sqrt(-2.0 * log(u01o(wd[2]))), th1 = 2.0 * M_PI * u01(wd[3]);
-        double r2 = sqrt(-2.0 * log(u01o(wd[4]))), th2 = 2.0 * M_PI * u01(wd[5]);
-        double z[4] = { qgauss(r1 * cos(th1)), qgauss(r1 * sin(th1)),
-                        qgauss(r2 * cos(th2)), qgauss(r2 * sin(th2)) };
-        for (int i = 0; i < 4; ++i)
-            if ((wd[1] >> (32 + i)) & 1) z[i] = -z[i];
-        q.cand.x += p->sig_xy * z[0];
-        q.cand.y += p->sig_xy * z[1];
-        q.cand.t += p->sig_t * z[2];
-        q.cand.m += p->sig_m * z[3];
-    }
+    double off[4];
+    walk_offset(w, wd, off);
+    q.cand.x += off[0];
+    q.cand.y += off[1];
+    q.cand.t += off[2];
+    q.cand.m += off[3];
     q.valid = in_region(w, g, &q.cand) && in_time_mag(w, &q.cand);
     return q;
 }
@@ -729,6 +818,9 @@ static prop_t decode(const orc_world* w, const region_t* g, const uint64_t* wd,
  *   birth:  dll + log beta(c) - log q_b(c) + log p_d - log(n+1) - log p_b
  *   death:  dll - log beta(e) + log q_b(e) + log p_b - log p_d + log n
  *   move:   dll + log beta(c) - log beta(e)        (symmetric offset)
+ *   pair:   dll + sum over the two of log beta(c) - log beta(e): the exchange
+ *           is its own inverse, the common offset is symmetric, and the
+ *           ordered pair is drawn with probability 1/(n (n-1)) both ways
  */
 static double log_alpha_of(const orc_world* w, const region_t* g, const prop_t* q,
                            const ev_t* own, int64_t n_own, const ev_t* oth, int64_t n_oth,
@@ -746,6 +838,11 @@ static double log_alpha_of(const orc_world* w, const region_t* g, const prop_t* 
         dlp = -log_beta(w, e);
         la = dll + dlp + (ORC_MUTANT == 2 ? 0.0 : log_qb(w, g, e)) + log(p->p_birth) - log(p->p_death)
              + log((double)n_own);
+    } else if (q->type == 3) {
+        dll = delta_ll_pair(w, own, n_own, oth, n_oth, q->idx, q->idx2, &q->cand, &q->cand2);
+        dlp = (log_beta(w, &q->cand) - log_beta(w, &own[q->idx])) +
+              (log_beta(w, &q->cand2) - log_beta(w, &own[q->idx2]));
+        la = dll + (ORC_MUTANT == 7 ? 0.0 : dlp);
     } else {
         dll = delta_ll2(w, own, n_own, oth, n_oth, q->idx, &q->cand);
         dlp = log_beta(w, &q->cand) - log_beta(w, &own[q->idx]);
@@ -781,6 +878,11 @@ static void apply(vec_t* own, const prop_t* q, uint64_t new_id) {
         uint64_t id = own->e[q->idx].id;
         own->e[q->idx] = q->cand;
         own->e[q->idx].id = id;
+        if (q->type == 3) {
+            id = own->e[q->idx2].id;
+            own->e[q->idx2] = q->cand2;
+            own->e[q->idx2].id = id;
+        }
     }
 }
 
@@ -837,6 +939,39 @@ double orc_log_alpha(const orc_world* w, double sx, double sy, int32_t cell,
     if (type != 0 && (idx < 0 || idx >= own.n)) q.valid = 0;
     if (type == 0 && w->p.lattice && n >= w->p.lat_nmax) q.valid = 0;
     if (type != 1 && q.valid) q.valid = in_region(w, &g, &q.cand) && in_time_mag(w, &q.cand);
+    double la = -INFINITY, dll, dlp;
+    if (q.valid) la = log_alpha_of(w, &g, &q, own.e, own.n, oth.e, oth.n, &dll, &dlp);
+    *valid = q.valid;
+    free(own.e);
+    free(oth.e);
+    return la;
+}
+
+double orc_log_alpha_pair(const orc_world* w, double sx, double sy, int32_t cell,
+                          const double* ev, int64_t n, int64_t i, int64_t j,
+                          const double* cand1, const double* cand2, int32_t* valid) {
+    region_t g;
+    g.cell = cell; g.sx = sx; g.sy = sy;
+    if (cell < 0) { g.r[0] = 0.0; g.r[1] = w->p.W; g.r[2] = 0.0; g.r[3] = w->p.W; }
+    else orc_cell_rect(w, sx, sy, cell, g.r);
+    region_bt(w, &g);
+    vec_t own = { 0, 0, 0 }, oth = { 0, 0, 0 };
+    for (int64_t q = 0; q < n; ++q) {
+        ev_t e; to_ev(ev + 4 * q, &e);
+        e.id = (uint64_t)q;
+        if (cell < 0 || orc_cell_of(w, sx, sy, e.x, e.y) == cell) vec_push(&own, &e);
+        else vec_push(&oth, &e);
+    }
+    prop_t q;
+    memset(&q, 0, sizeof(q));
+    q.type = 3;
+    q.idx = i;
+    q.idx2 = j;
+    to_ev(cand1, &q.cand);
+    to_ev(cand2, &q.cand2);
+    q.valid = i >= 0 && i < own.n && j >= 0 && j < own.n && i != j &&
+              in_region(w, &g, &q.cand) && in_time_mag(w, &q.cand) &&
+              in_region(w, &g, &q.cand2) && in_time_mag(w, &q.cand2);
     double la = -INFINITY, dll, dlp;
     if (q.valid) la = log_alpha_of(w, &g, &q, own.e, own.n, oth.e, oth.n, &dll, &dlp);
     *valid = q.valid;

@@ -9,7 +9,8 @@
  *     per-sample variance is noise plus the arriving signals' variances)
  *     -- §Generative Model of Seismic Signals, the joint P(e, a, s);
  *   - the change of the log-likelihood for one birth / death / move proposal,
- *     as the difference of two sums of Gaussian log-densities;
+ *     and for the joint move of a pair of events, as the difference of two
+ *     sums of Gaussian log-densities;
  *   - Serial Metropolis-Hastings (Algorithm "Serial Metropolis Hastings");
  *   - Chromatic MH with static colouring and with dynamic colouring
  *     (Algorithm "Chromatic Metropolis Hastings with Static Coloring", and
@@ -40,10 +41,14 @@ typedef struct {
     int32_t likelihood;   /* 0: arrivals add to the variance of a zero-mean sample;
                              1: they add to its mean, the variance is the noise's */
     double lat_x0, lat_dx, lat_y0, lat_dy, lat_t0, lat_dt, lat_m0, lat_dm;
+    /* probability of the joint move of a pair of the region's events (§MH
+     * moves, "Joint Events Move"); proposals with u in [p_birth + p_death,
+     * p_birth + p_death + p_pair) take it, the Gaussian move keeps the rest */
+    double p_pair;
 } orc_params;
 
 typedef struct {
-    int32_t sweep, cell, step, type;   /* type: 0 birth, 1 death, 2 move */
+    int32_t sweep, cell, step, type;   /* type: 0 birth, 1 death, 2 move, 3 pair */
     int32_t evaluated, accepted, n_before, pad;
     double dll, log_alpha;
 } orc_trace;
@@ -94,6 +99,12 @@ void orc_blankets(const orc_world* w, double sx, double sy, uint8_t* member);
 double orc_log_alpha(const orc_world* w, double sx, double sy, int32_t cell,
                      const double* ev, int64_t n, int32_t type, int64_t idx,
                      const double* cand, int32_t* valid);
+
+/* log acceptance ratio of one explicit joint move: the i-th and j-th events
+ * of the region (i != j) become cand1 and cand2. */
+double orc_log_alpha_pair(const orc_world* w, double sx, double sy, int32_t cell,
+                          const double* ev, int64_t n, int64_t i, int64_t j,
+                          const double* cand1, const double* cand2, int32_t* valid);
 
 /* samplers; return 0 on success */
 int orc_run_serial(const orc_world* w, orc_set* s, int64_t step0, int64_t n_steps,

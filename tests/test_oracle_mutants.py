@@ -9,7 +9,12 @@ oracle.c); the test asserts that the pin meant to catch it fails:
           because the mutant is a self-consistent sampler of a wrong model;
   5 (the Hastings term of a birth ignores the learned component of the
           mixture proposal) -> a prior-only chain drifts to the table's hot
-          block.
+          block;
+  6 (learned magnitudes priced with the prior law) -> magnitudes pile up in
+          the learned window;
+  7 (the joint move of a pair drops the prior ratio) -> detailed balance of
+          the kernels with joint moves on (and magnitude drift in
+          test_oracle_pair.py).
 """
 import math
 
@@ -17,20 +22,29 @@ import numpy as np
 import pytest
 
 import worldgen
-from test_oracle_sampler import PB, PD, _enumerate, _kernel, _lattice_world
+from test_oracle_sampler import PB, PD, PP, _enumerate, _kernel, _lattice_world
 
 
-def _max_imbalance(orc, mutant, shift=(0.0, 0.0), cell=-1):
+def _max_imbalance(orc, mutant, shift=(0.0, 0.0), cell=-1, pp=0.0):
     w, lat = _lattice_world(orc)
-    o = orc.World(w, p_birth=PB, p_death=PD, k_per_phase=10, seed=3, lattice=lat, mutant=mutant)
+    o = orc.World(w, p_birth=PB, p_death=PD, k_per_phase=10, seed=3, lattice=lat, mutant=mutant,
+                  p_pair=pp)
     pts, states, index, pi = _enumerate(o, lat, w.params)
-    P = _kernel(o, lat, pts, states, index, cell, *shift)
+    P = _kernel(o, lat, pts, states, index, cell, *shift, pp=pp)
     flow = pi[:, None] * P
     return np.max(np.abs(flow - flow.T)) / pi.max()
 
 
 def test_unmutated_oracle_balances(orc):
     assert _max_imbalance(orc, 0) < 1e-13
+    assert _max_imbalance(orc, 0, pp=PP) < 1e-13
+
+
+def test_pair_prior_mutant_breaks_detailed_balance(orc):
+    assert _max_imbalance(orc, 7, pp=PP) > 1e-4
+    assert _max_imbalance(orc, 7, shift=(30.0, 70.0), cell=5, pp=PP) > 1e-4
+    # with joint moves off the mutant is the oracle
+    assert _max_imbalance(orc, 7) < 1e-13
 
 
 @pytest.mark.parametrize("mutant", [1, 2, 4])

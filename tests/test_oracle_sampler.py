@@ -13,6 +13,10 @@
 * Prior-only continuous chains (no stations) reproduce the prior: Poisson
   count, uniform locations (including edge regions cut by the domain),
   Exp(1) magnitudes.
+* The joint move of a pair (§MH moves, "Joint Events Move": the exchange of
+  two events' locations, or one common offset of both) enters the same
+  enumerated kernels with probability PP; they must still balance, and the
+  chains with it must reproduce the same marginals.
 """
 import itertools
 import math
@@ -24,6 +28,7 @@ import worldgen
 
 PB, PD = 0.25, 0.25
 PMV = 1.0 - PB - PD
+PP = 0.2   # share of joint moves where a test turns them on
 
 
 def _lattice_world(orc, shift_cells=False, likelihood="variance"):
@@ -71,7 +76,52 @@ def _enumerate(o, lat, p):
     return pts, states, index, pi
 
 
-def _kernel(o, lat, pts, states, index, cell, sx, sy):
+def _add(P, i, j, prob, la_ok):
+    la, ok = la_ok
+    if not ok:
+        P[i, i] += prob
+        return
+    a = min(1.0, math.exp(min(la, 0.0)))
+    P[i, j] += prob * a
+    P[i, i] += prob * (1 - a)
+
+
+def _pair_moves(o, lat, s, ev, own, key, index, cell, sx, sy, P, i, pp):
+    """Transitions of the joint move: an ordered pair of distinct own events
+    (probability 1 / (n (n - 1))), then with probability 1/2 the exchange of
+    their locations, else one of the 8 lattice steps applied to both."""
+    if len(own) < 2:
+        P[i, i] += pp
+        return
+    n_o = len(own)
+    base = pp / (n_o * (n_o - 1))
+    steps = (lat.dx, lat.dy, lat.dt, lat.dm)
+    for ai, a in enumerate(own):
+        for bi, b in enumerate(own):
+            if ai == bi:
+                continue
+            cands = []
+            c1, c2 = ev[a].copy(), ev[b].copy()
+            c1[:2], c2[:2] = ev[b][:2], ev[a][:2]
+            cands.append((0.5 * base, c1, c2))
+            for d in range(8):
+                off = np.zeros(4)
+                off[d >> 1] = (-1.0 if d & 1 else 1.0) * steps[d >> 1]
+                cands.append((0.5 * base / 8, ev[a] + off, ev[b] + off))
+            for prob, c1, c2 in cands:
+                la_ok = o.log_alpha_pair(sx, sy, cell, ev, ai, bi, c1, c2)
+                j = i
+                if la_ok[1]:
+                    moved = list(s)
+                    moved.remove(s[a])
+                    moved.remove(s[b])
+                    moved += [key[tuple(c1)], key[tuple(c2)]]
+                    j = index[tuple(sorted(moved))]
+                _add(P, i, j, prob, la_ok)
+
+
+def _kernel(o, lat, pts, states, index, cell, sx, sy, pp=0.0):
+    pmv = PMV if pp == 0.0 else 1.0 - PB - PD - pp
     n = len(states)
     P = np.zeros((n, n))
     key = {tuple(q): i for i, q in enumerate(pts)}
@@ -102,8 +152,10 @@ def _kernel(o, lat, pts, states, index, cell, sx, sy):
                         P[i, j] += prob * a
                         P[i, i] += prob * (1 - a)
         if not own:
-            P[i, i] += PD + PMV
+            P[i, i] += PD + pmv + pp
             continue
+        if pp > 0.0:
+            _pair_moves(o, lat, s, ev, own, key, index, cell, sx, sy, P, i, pp)
         for qi, q in enumerate(own):
             prob = PD / len(own)
             la, ok = o.log_alpha(sx, sy, cell, ev, 1, qi, None)
@@ -115,7 +167,7 @@ def _kernel(o, lat, pts, states, index, cell, sx, sy):
             P[i, j] += prob * a
             P[i, i] += prob * (1 - a)
             for d in range(8):
-                prob = PMV / (len(own) * 8)
+                prob = pmv / (len(own) * 8)
                 c = ev[q].copy()
                 step = -1.0 if d & 1 else 1.0
                 c[d >> 1] += step * (lat.dx, lat.dy, lat.dt, lat.dm)[d >> 1]
@@ -139,6 +191,15 @@ def lattice_case(orc, request):
     enumeration, which every sampler must leave invariant."""
     w, lat = _lattice_world(orc, likelihood=request.param)
     o = orc.World(w, p_birth=PB, p_death=PD, k_per_phase=10, seed=3, lattice=lat)
+    pts, states, index, pi = _enumerate(o, lat, w.params)
+    return o, lat, pts, states, index, pi
+
+
+@pytest.fixture(scope="module", params=["variance", "mean"])
+def lattice_pair_case(orc, request):
+    """The same lattice world with joint moves on (share PP)."""
+    w, lat = _lattice_world(orc, likelihood=request.param)
+    o = orc.World(w, p_birth=PB, p_death=PD, k_per_phase=10, seed=3, lattice=lat, p_pair=PP)
     pts, states, index, pi = _enumerate(o, lat, w.params)
     return o, lat, pts, states, index, pi
 
@@ -169,6 +230,22 @@ def test_region_kernels_detailed_balance(lattice_case, shift):
     assert len(live) == (4 if shift == (0.0, 0.0) else 9)
     for c in live:
         _check_kernel(_kernel(o, lat, pts, states, index, c, sx, sy), pi)
+
+
+def test_pair_kernels_detailed_balance(lattice_pair_case):
+    o, lat, pts, states, index, pi = lattice_pair_case
+    P = _kernel(o, lat, pts, states, index, -1, 0.0, 0.0, pp=PP)
+    _check_kernel(P, pi)
+    # the joint move changes states on its own: with the other moves taken
+    # out, the kernel still leaves the two-event states
+    two = [i for i, s in enumerate(states) if len(s) == 2]
+    assert np.mean(np.diag(P)[two]) < 0.95
+    for shift in [(0.0, 0.0), (30.0, 70.0)]:
+        ncx, ncy = o.grid_dims()
+        for c in range(ncx * ncy):
+            r = o.cell_rect(*shift, c)
+            if r[1] > r[0] and r[3] > r[2]:
+                _check_kernel(_kernel(o, lat, pts, states, index, c, *shift, pp=PP), pi)
 
 
 def _batch_se(x, nb=40):
@@ -215,16 +292,40 @@ def test_lattice_chain_marginals(lattice_case, mode):
         assert abs(m - occ[site]) < 5 * se + 2e-3, (site, m, occ[site], se)
 
 
-@pytest.mark.parametrize("mode", ["serial", "static", "dynamic"])
-def test_prior_only_chain_recovers_prior(orc, mode):
+def test_lattice_chain_marginals_with_pairs(lattice_pair_case):
+    """Dynamic chromatic chains with joint moves reproduce the enumerated
+    marginals."""
+    test_lattice_chain_marginals(lattice_pair_case, "dynamic")
+
+
+@pytest.mark.parametrize("mode,p_pair", [("serial", 0.0), ("static", 0.0), ("dynamic", 0.0),
+                                         ("dynamic", 0.3)])
+def test_prior_only_chain_recovers_prior(orc, mode, p_pair):
+    p, Ns, frac, ms = _prior_only_chain(orc, mode, p_pair)
+    m, se = _batch_se(Ns)
+    assert abs(m - p.Lambda) < 5 * se, (m, se)
+    v = np.var(Ns)
+    assert abs(v / p.Lambda - 1.0) < 0.25
+    # uniform location over the domain, edge regions included
+    assert np.max(np.abs(frac - 0.1)) < 0.02, frac
+    # Exp(1) magnitudes above 2
+    assert abs(ms.mean() - 1.0) < 0.06
+    assert abs(np.mean(ms > 1.0) - math.exp(-1.0)) < 0.03
+
+
+def _prior_only_chain(orc, mode, p_pair, mutant=0, n_iter=3000, p_bd=0.25, sig_m=0.5):
+    """A chain with no stations: its state must follow the prior.  Returns
+    the params, the event counts, the location histogram (10 bins of x and y
+    pooled) and the magnitudes above 2."""
     p = worldgen.ModelParams(W=200.0, T=100.0, Lambda=12.0, R_max=50.0, L=100.0)
     w = worldgen.World(params=p, stations=np.zeros((0, 2)), signals=np.zeros((0, 0)),
                        events=np.zeros((0, 4)))
-    o = orc.World(w, k_per_phase=8, seed=11, sig_xy=20.0, sig_t=10.0, sig_m=0.5)
+    o = orc.World(w, k_per_phase=8, seed=11, sig_xy=20.0, sig_t=10.0, sig_m=sig_m, p_pair=p_pair,
+                  mutant=mutant, p_birth=p_bd, p_death=p_bd)
     ev = np.zeros((0, 4))
     ids = None
     Ns, xs, ms = [], [], []
-    for it in range(3000):
+    for it in range(n_iter):
         if mode == "serial":
             ev, ids, _, _ = o.run_serial(ev, 40, ids=ids, step0=it * 40)
         else:
@@ -236,18 +337,8 @@ def test_prior_only_chain_recovers_prior(orc, mode):
             xs.extend(ev[:, 0])
             xs.extend(ev[:, 1])
             ms.extend(ev[:, 3] - 2.0)
-    m, se = _batch_se(Ns)
-    assert abs(m - p.Lambda) < 5 * se, (m, se)
-    v = np.var(Ns)
-    assert abs(v / p.Lambda - 1.0) < 0.25
-    # uniform location over the domain, edge regions included
     h, _ = np.histogram(xs, bins=10, range=(0.0, p.W))
-    frac = h / h.sum()
-    assert np.max(np.abs(frac - 0.1)) < 0.02, frac
-    # Exp(1) magnitudes above 2
-    ms = np.array(ms)
-    assert abs(ms.mean() - 1.0) < 0.06
-    assert abs(np.mean(ms > 1.0) - math.exp(-1.0)) < 0.03
+    return p, np.array(Ns), h / h.sum(), np.array(ms)
 
 
 def test_threaded_chromatic_equals_sequential(orc):

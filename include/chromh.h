@@ -90,6 +90,16 @@ typedef struct {
                               to the sample's mean and the variance is noise_var (the
                               additive reading) */
     int64_t max_events;    /* capacity of the whole event store; 0: 4 (n0 + Lambda) + 4096 */
+    double p_pair;         /* CMH_F64 only: probability of the joint move of a pair of the
+                              region's events (§MH moves, "Joint Events Move"); a step whose
+                              uniform falls in [p_birth + p_death, p_birth + p_death + p_pair)
+                              takes it, the Gaussian move keeps the rest.  The ordered pair
+                              (i, j), i != j, is drawn uniformly; then with probability 1/2
+                              the two exchange their locations (each keeps its origin time and
+                              magnitude: the other mode for stations near the pair's
+                              perpendicular bisector), else both shift by one common Gaussian
+                              offset of the move's scales.  0 (the default) turns it off;
+                              p_birth + p_death + p_pair <= 1 */
 } cmh_params;
 
 /* region grid: squares of side L anchored at the origin, shifted by (sx, sy) */
@@ -109,11 +119,12 @@ typedef struct {
     uint64_t rewritten_samples; /* station samples whose variance was re-synthesised */
     int64_t spill_bytes;    /* float32 regions too large for shared memory: bytes of the global
                                slot per CTA holding their arrival caches and lists (0: none) */
+    uint64_t pair[3];       /* joint moves of a pair (p_pair): proposed, evaluated, accepted */
 } cmh_stats;
 
 /* one record per MH step (optional, cmh_set_trace) */
 typedef struct {
-    int32_t sweep, cell, step, type;   /* type: 0 birth, 1 death, 2 move */
+    int32_t sweep, cell, step, type;   /* type: 0 birth, 1 death, 2 move, 3 joint move of a pair */
     int32_t evaluated, accepted, n_before, written;
     double dll;        /* log-likelihood change of the proposal (0 if not evaluated) */
     double log_alpha;  /* log acceptance ratio (-inf if not evaluated) */

@@ -42,7 +42,7 @@ class Params(C.Structure):
         ("k_per_phase", C.c_int32), ("commit", C.c_int32), ("seed", C.c_uint64), ("dtype", C.c_int32),
         ("ev_capacity", C.c_int32), ("frozen_capacity", C.c_int32), ("block_threads", C.c_int32),
         ("stage_samples", C.c_int32), ("schedule", C.c_int32), ("ctas_per_sm", C.c_int32),
-        ("likelihood", C.c_int32), ("max_events", C.c_int64)]
+        ("likelihood", C.c_int32), ("max_events", C.c_int64), ("p_pair", C.c_double)]
 
 
 class Tuning(C.Structure):
@@ -66,14 +66,16 @@ class Stats(C.Structure):
     _fields_ = [("proposed", C.c_uint64 * 3), ("evaluated", C.c_uint64 * 3), ("accepted", C.c_uint64 * 3),
                 ("sweeps", C.c_int64), ("n_events", C.c_int64), ("phase_ms", C.c_double),
                 ("phase_launches", C.c_int64), ("kernel_launches", C.c_int64),
-                ("priced_samples", C.c_uint64), ("rewritten_samples", C.c_uint64), ("spill_bytes", C.c_int64)]
+                ("priced_samples", C.c_uint64), ("rewritten_samples", C.c_uint64), ("spill_bytes", C.c_int64),
+                ("pair", C.c_uint64 * 3)]
 
     def as_dict(self):
         return {"proposed": list(self.proposed), "evaluated": list(self.evaluated),
                 "accepted": list(self.accepted), "sweeps": self.sweeps, "n_events": self.n_events,
                 "phase_ms": self.phase_ms, "phase_launches": self.phase_launches,
                 "kernel_launches": self.kernel_launches, "priced_samples": self.priced_samples,
-                "rewritten_samples": self.rewritten_samples, "spill_bytes": self.spill_bytes}
+                "rewritten_samples": self.rewritten_samples, "spill_bytes": self.spill_bytes,
+                "pair": list(self.pair)}
 
 
 TRACE_DTYPE = np.dtype([("sweep", "<i4"), ("cell", "<i4"), ("step", "<i4"), ("type", "<i4"),
@@ -161,8 +163,10 @@ def _ptr(a):
 
 def make_params(model_params, *, k_per_phase=32, seed=1, dtype=F64, p_birth=0.25, p_death=0.25,
                 sig_xy=5.0, sig_t=2.0, sig_m=0.1, commit=True, ev_capacity=0, frozen_capacity=0,
-                block_threads=0, stage_samples=0, schedule=0, ctas_per_sm=0, max_events=0) -> Params:
-    """cmh_params from an object with the model fields (e.g. worldgen.ModelParams)."""
+                block_threads=0, stage_samples=0, schedule=0, ctas_per_sm=0, max_events=0,
+                p_pair=0.0) -> Params:
+    """cmh_params from an object with the model fields (e.g. worldgen.ModelParams).
+    ``p_pair`` > 0 turns on the joint move of a pair of events (float64 only)."""
     p = Params()
     for n in ("W", "T", "Lambda", "v", "alpha", "beta_att", "tau", "t_s", "noise_var", "f_hz", "R_max"):
         setattr(p, n, float(getattr(model_params, n)))
@@ -180,6 +184,7 @@ def make_params(model_params, *, k_per_phase=32, seed=1, dtype=F64, p_birth=0.25
     p.ctas_per_sm = ctas_per_sm
     p.likelihood = 1 if getattr(model_params, "likelihood", "variance") == "mean" else 0
     p.max_events = max_events
+    p.p_pair = p_pair
     return p
 
 

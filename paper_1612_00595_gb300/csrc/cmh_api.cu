@@ -25,7 +25,7 @@ using namespace cmh;
 namespace {
 
 constexpr uint64_t kCkptMagic = 0x31484d4f52484343ULL;  // "CCHROMH1"
-constexpr int kCkptVersion = 1;
+constexpr int kCkptVersion = 2;
 
 int cuda_err(cudaError_t e) {
     if (e == cudaSuccess) return CMH_OK;
@@ -219,6 +219,9 @@ int validate_params(const cmh_params* p) {
         if (!finite_pos(v)) return CMH_ERR_ARG;
     if (!std::isfinite(p->alpha) || !std::isfinite(p->beta_att)) return CMH_ERR_ARG;
     if (!(p->p_birth > 0.0 && p->p_death > 0.0 && p->p_birth + p->p_death < 1.0)) return CMH_ERR_ARG;
+    // joint moves of a pair: the float64 form only
+    if (!(p->p_pair >= 0.0 && p->p_birth + p->p_death + p->p_pair <= 1.0)) return CMH_ERR_ARG;
+    if (p->p_pair > 0.0 && p->dtype != CMH_F64) return CMH_ERR_ARG;
     if (p->k_per_phase < 1 || p->k_per_phase > kMaxK) return CMH_ERR_ARG;
     if (p->dtype != CMH_F32 && p->dtype != CMH_F64) return CMH_ERR_ARG;
     if (p->likelihood != 0 && !(p->likelihood == 1 && p->dtype == CMH_F32)) return CMH_ERR_ARG;
@@ -380,6 +383,7 @@ int cmh_create_model(const cmh_event* init_events, int64_t n_events, const cmh_s
     g.W = p->W; g.T = p->T; g.Lambda = p->Lambda; g.v = p->v; g.alpha = p->alpha; g.beta_att = p->beta_att;
     g.tau = p->tau; g.noise_var = p->noise_var; g.f_hz = p->f_hz; g.R_max = p->R_max;
     g.p_birth = p->p_birth; g.p_death = p->p_death; g.sig_xy = p->sig_xy; g.sig_t = p->sig_t; g.sig_m = p->sig_m;
+    g.p_pair = p->p_pair;
     g.log_pb = std::log(p->p_birth);
     g.log_pd = std::log(p->p_death);
     g.log_Lambda = std::log(p->Lambda);
@@ -770,6 +774,7 @@ int cmh_read_state(cmh_model* m, cmh_event* out, uint64_t* ids_out, int64_t cap,
         stats_out->priced_samples = st[9];
         stats_out->rewritten_samples = st[10];
         stats_out->spill_bytes = m->partitioned && m->g.spill ? m->g.spill_bytes : 0;
+        for (int i = 0; i < 3; ++i) stats_out->pair[i] = st[11 + i];
     }
     return CMH_OK;
 }
@@ -1054,6 +1059,7 @@ int cmh_read_state_fetch(cmh_model* m, int32_t slot, cmh_event* out, uint64_t* i
         stats_out->priced_samples = st[9];
         stats_out->rewritten_samples = st[10];
         stats_out->spill_bytes = m->g.spill ? m->g.spill_bytes : 0;
+        for (int i = 0; i < 3; ++i) stats_out->pair[i] = st[11 + i];
     }
     r.pending = false;
     return CMH_OK;

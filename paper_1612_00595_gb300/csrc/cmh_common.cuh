@@ -19,12 +19,15 @@ namespace cmh {
 
 constexpr int kMaxColours = 16;
 constexpr int kMaxK = 4095;
-constexpr int kStats = 11;   // proposed[3], evaluated[3], accepted[3], priced samples, rewritten samples
+// proposed[3], evaluated[3], accepted[3], priced samples, rewritten samples,
+// joint moves of a pair: proposed, evaluated, accepted
+constexpr int kStats = 14;
 
 // model, partition and launch constants; passed by value to every kernel
 struct Geo {
     double W, T, Lambda, v, alpha, beta_att, tau, noise_var, f_hz, R_max, L;
     double p_birth, p_death, sig_xy, sig_t, sig_m;
+    double p_pair;      // joint move of a pair of events (float64 form only)
     // logs computed once on the host
     double log_pb, log_pd, log_Lambda, log_WWT, log_T;
     int n_w, k, commit, shift_mode;

@@ -7,9 +7,10 @@
 //
 // One CTA per region of the active colour.  Within a CTA:
 //   * warp 0 is the control warp: it decodes each step's proposal (birth,
-//     death, Gaussian move; §Generative Model of Seismic Signals, the MH
-//     moves), finds the stations the proposal reaches and makes the float64
-//     accept decision (MH rule, §Background);
+//     death, Gaussian move, and with p_pair > 0 the joint move of a pair of
+//     events; §Generative Model of Seismic Signals, the MH moves), finds the
+//     stations the proposal reaches and makes the float64 accept decision
+//     (MH rule, §Background);
 //   * all warps price the proposal: the change of the Gaussian
 //     log-likelihood over the samples whose variance changes (§Generative
 //     Model: zero-mean diagonal Gaussian with variance = noise + arriving
@@ -40,11 +41,13 @@ struct Arr {            // an arrival in a list (frozen neighbours, others of a 
 };
 
 struct Draw {           // state-independent part of one MH step
-    double a[4];        // birth: candidate (x, y, t, m); move: signed offsets
+    double a[4];        // birth: candidate (x, y, t, m); move, pair: signed offsets
     double logu;        // log of the accept uniform, (0, 1]
     unsigned pickw;     // low word for the event pick
-    int type;           // 0 birth, 1 death, 2 move
+    unsigned pickw2;    // joint move: low word for the second event's pick
+    int type;           // 0 birth, 1 death, 2 move, 3 joint move of a pair
     int bvalid;         // birth candidate inside region, time and magnitude range
+    int sub;            // joint move: 0 exchange of locations, 1 common offset
     int pad;
 };
 
@@ -53,17 +56,22 @@ struct Task {           // one station whose variance the proposal changes
     int has_o, has_n, k0o, k0n;
     int oth0;           // others list: [oth0, oth0 + noth) in the pool
     int noth;
+    int has_o2, has_n2, k0o2, k0n2;   // joint move: the second event's old and new arrivals
     double afo, lnA2o, afn, lnA2n, rm1d;
+    double afo2, lnA2o2, afn2, lnA2n2;
 };
 
 // shared-memory layout of the phase kernel (host computes the size)
 struct Layout {
     size_t ev_x, ev_y, ev_t, ev_m, ev_id, ev_narr, ev_arr, order, freel;
     size_t b_sta, b_x, b_y, f_cnt, f_arr, draws, cand, tasks, pool, total;
-    static constexpr int kMaxTasks = 64;
+    int task_cap;       // a task per distinct blanket slot of the changed arrivals
     int pool_cap;
     __host__ __device__ Layout(const Geo& g) {
-        pool_cap = g.ev_cap + g.frz_cap;
+        const int lists = g.p_pair > 0.0 ? 4 : 2;   // old and new arrivals of one or two events
+        task_cap = g.blk_cap < lists * g.arr_cap ? g.blk_cap : lists * g.arr_cap;
+        if (task_cap < 1) task_cap = 1;
+        pool_cap = (g.ev_cap + g.frz_cap) * (lists / 2);
         size_t o = 0;
         auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 15) & ~size_t(15); return r; };
         ev_x = take(sizeof(double) * g.ev_cap);
@@ -81,8 +89,8 @@ struct Layout {
         f_cnt = take(sizeof(int) * g.blk_cap);
         f_arr = take(sizeof(Arr) * (size_t)g.blk_cap * g.frz_cap);
         draws = take(sizeof(Draw) * g.k);
-        cand = take(sizeof(EvArr) * g.arr_cap);
-        tasks = take(sizeof(Task) * kMaxTasks);
+        cand = take(sizeof(EvArr) * 2 * g.arr_cap);   // the candidate's arrivals; a pair's second at arr_cap
+        tasks = take(sizeof(Task) * task_cap);
         pool = take(sizeof(Arr) * (size_t)pool_cap);
         total = o;
     }
@@ -187,8 +195,9 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
 
     __shared__ double s_rect[4];
     __shared__ double s_log_area, s_dll, s_region_dlp;
-    __shared__ double s_c[4];
+    __shared__ double s_c[4], s_c2[4];
     __shared__ int s_n_own, s_n_free, s_n_blk, s_err, s_valid, s_idx, s_type, s_ncand, s_ntask, s_acc;
+    __shared__ int s_idx2, s_ncand2;
     __shared__ int s_warp[32], s_base;
     __shared__ double s_redd[32];
 
@@ -308,8 +317,11 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
         for (int i = 0; i < 4; ++i) { w[i] = c0[i]; w[4 + i] = c1[i]; }
         Draw D;
         const double u = u01(w[0]);
-        D.type = u < g.p_birth ? 0 : (u < __dadd_rn(g.p_birth, g.p_death) ? 1 : 2);
+        const double cd = __dadd_rn(g.p_birth, g.p_death), cp = __dadd_rn(cd, g.p_pair);
+        D.type = u < g.p_birth ? 0 : (u < cd ? 1 : (u < cp ? 3 : 2));
         D.pickw = (unsigned)(w[1] & 0xffffffffULL);
+        D.pickw2 = (unsigned)(w[7] & 0xffffffffULL);
+        D.sub = (int)((w[1] >> 36) & 1ULL);
         D.logu = log(u01o(w[6]));
         D.bvalid = 0;
         if (D.type == 0) {
@@ -320,7 +332,7 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
             D.a[0] = x; D.a[1] = y; D.a[2] = t; D.a[3] = m;
             D.bvalid = x >= 0.0 && x < g.W && y >= 0.0 && y < g.W && cell_of(g, sx, sy, x, y) == cell &&
                        t >= 0.0 && t < g.T && m >= 2.0;
-        } else if (D.type == 2) {
+        } else if (D.type == 2 || D.type == 3) {
             const double r1 = __dsqrt_rn(__dmul_rn(-2.0, log(u01o(w[2]))));
             const double th1 = __dmul_rn(6.283185307179586, u01(w[3]));
             const double r2 = __dsqrt_rn(__dmul_rn(-2.0, log(u01o(w[4]))));
@@ -344,7 +356,7 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
         return;
     }
 
-    unsigned long long n_prop[3] = {0, 0, 0}, n_eval[3] = {0, 0, 0}, n_acc[3] = {0, 0, 0};
+    unsigned long long n_prop[4] = {0, 0, 0, 0}, n_eval[4] = {0, 0, 0, 0}, n_acc[4] = {0, 0, 0, 0};
     unsigned long long n_priced = 0, n_rewritten = 0;   // sample terms (thread 0's tally)
 
     for (int step = 0; step < g.k; ++step) {
@@ -352,11 +364,39 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
         if (wid == 0) {
             const Draw dr = draws[step];
             const int n_own = s_n_own;
-            int valid = 0, idx = -1, ncand = 0;
+            int valid = 0, idx = -1, ncand = 0, idx2 = -1, ncand2 = 0;
             double cx = 0.0, cy = 0.0, ct = 0.0, cm = 0.0;
+            double cx2 = 0.0, cy2 = 0.0, ct2 = 0.0, cm2 = 0.0;   // joint move: the second event
             if (dr.type == 0) {
                 valid = dr.bvalid;
                 cx = dr.a[0]; cy = dr.a[1]; ct = dr.a[2]; cm = dr.a[3];
+            } else if (dr.type == 3) {
+                // joint move of an ordered pair of distinct events: exchange of
+                // their locations (each keeps its time and magnitude), or one
+                // common offset for both
+                if (n_own >= 2) {
+                    idx = pick32(dr.pickw, n_own);
+                    const int j = pick32(dr.pickw2, n_own - 1);
+                    idx2 = j + (j >= idx ? 1 : 0);
+                    const int p1 = order[idx], p2 = order[idx2];
+                    if (dr.sub == 0) {
+                        cx = ex[p2]; cy = ey[p2]; ct = et[p1]; cm = em[p1];
+                        cx2 = ex[p1]; cy2 = ey[p1]; ct2 = et[p2]; cm2 = em[p2];
+                    } else {
+                        cx = __dadd_rn(ex[p1], dr.a[0]);
+                        cy = __dadd_rn(ey[p1], dr.a[1]);
+                        ct = __dadd_rn(et[p1], dr.a[2]);
+                        cm = __dadd_rn(em[p1], dr.a[3]);
+                        cx2 = __dadd_rn(ex[p2], dr.a[0]);
+                        cy2 = __dadd_rn(ey[p2], dr.a[1]);
+                        ct2 = __dadd_rn(et[p2], dr.a[2]);
+                        cm2 = __dadd_rn(em[p2], dr.a[3]);
+                    }
+                    valid = cx >= 0.0 && cx < g.W && cy >= 0.0 && cy < g.W &&
+                            cell_of(g, sx, sy, cx, cy) == cell && ct >= 0.0 && ct < g.T && cm >= 2.0 &&
+                            cx2 >= 0.0 && cx2 < g.W && cy2 >= 0.0 && cy2 < g.W &&
+                            cell_of(g, sx, sy, cx2, cy2) == cell && ct2 >= 0.0 && ct2 < g.T && cm2 >= 2.0;
+                }
             } else if (n_own > 0) {
                 idx = pick32(dr.pickw, n_own);
                 if (dr.type == 1) {
@@ -386,11 +426,86 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
                     ncand += __popc(bal);
                 }
             }
+            if (valid && dr.type == 3) {
+                EvArr* cand2 = cand + g.arr_cap;
+                for (int b0 = 0; b0 < n_blk; b0 += 32) {
+                    const int b = b0 + lane;
+                    int k0 = 0;
+                    double af = 0.0, lnA2 = 0.0;
+                    const bool r = b < n_blk && arrival(g, cx2, cy2, ct2, cm2, bx[b], by[b], k0, af, lnA2);
+                    const unsigned bal = __ballot_sync(FULL, r);
+                    const int pos = ncand2 + __popc(bal & ((1u << lane) - 1));
+                    if (r && pos < g.arr_cap) {
+                        EvArr& A = cand2[pos];
+                        A.slot = b; A.k0 = k0; A.af = af; A.lnA2 = lnA2;
+                    }
+                    ncand2 += __popc(bal);
+                }
+            }
             __syncwarp();
             if (lane == 0) {
-                int err = ncand > g.arr_cap ? CMH_ERR_CAPACITY : 0;
+                int err = (ncand > g.arr_cap || ncand2 > g.arr_cap) ? CMH_ERR_CAPACITY : 0;
                 int nt = 0, npool = 0;
-                if (valid && !err) {
+                if (valid && !err && dr.type == 3) {
+                    // merge the four slot-sorted lists: the two events' old
+                    // arrivals and their candidates'
+                    const int p1 = order[idx], p2 = order[idx2];
+                    const EvArr* La[4] = {earr + p1 * g.arr_cap, earr + p2 * g.arr_cap, cand, cand + g.arr_cap};
+                    const int Na[4] = {enarr[p1], enarr[p2], ncand, ncand2};
+                    int hd[4] = {0, 0, 0, 0};
+                    while (!err) {
+                        int sl = 1 << 30;
+                        for (int q = 0; q < 4; ++q)
+                            if (hd[q] < Na[q] && La[q][hd[q]].slot < sl) sl = La[q][hd[q]].slot;
+                        if (sl == 1 << 30) break;
+                        if (nt >= Lo.task_cap) { err = CMH_ERR_CAPACITY; break; }
+                        Task& T = tasks[nt];
+                        T.slot = sl;
+                        T.row = bsta[sl];
+                        T.has_o = T.has_o2 = T.has_n = T.has_n2 = 0;
+                        T.rm1d = 0.0;
+                        long long lo = 1LL << 40, hi = -1;
+                        for (int q = 0; q < 4; ++q) {
+                            if (!(hd[q] < Na[q] && La[q][hd[q]].slot == sl)) continue;
+                            const EvArr& A = La[q][hd[q]++];
+                            if (q == 0) { T.has_o = 1; T.k0o = A.k0; T.afo = A.af; T.lnA2o = A.lnA2; }
+                            if (q == 1) { T.has_o2 = 1; T.k0o2 = A.k0; T.afo2 = A.af; T.lnA2o2 = A.lnA2; }
+                            if (q == 2) { T.has_n = 1; T.k0n = A.k0; T.afn = A.af; T.lnA2n = A.lnA2; }
+                            if (q == 3) { T.has_n2 = 1; T.k0n2 = A.k0; T.afn2 = A.af; T.lnA2n2 = A.lnA2; }
+                            lo = min(lo, (long long)A.k0);
+                            hi = max(hi, (long long)A.k0 + g.n_w);
+                        }
+                        if (lo < 0) lo = 0;
+                        if (hi > g.n_samp) hi = g.n_samp;
+                        T.lo = (int)lo;
+                        T.hi = (int)hi;
+                        if (lo >= hi) continue;  // every window after the record
+                        // the other arrivals covering [lo, hi): own events but
+                        // the pair, then frozen neighbours
+                        T.oth0 = npool;
+                        const int n_own2 = s_n_own;
+                        for (int q = 0; q < n_own2 && !err; ++q) {
+                            const int pq = order[q];
+                            if (pq == p1 || pq == p2) continue;
+                            for (int a = 0; a < enarr[pq]; ++a) {
+                                const EvArr& A = earr[pq * g.arr_cap + a];
+                                if (A.slot != T.slot) continue;
+                                if (A.k0 + g.n_w <= lo || A.k0 >= hi) continue;
+                                if (npool >= Lo.pool_cap) { err = CMH_ERR_CAPACITY; break; }
+                                Arr& B = pool[npool++];
+                                B.k0 = A.k0; B.af = A.af; B.lnA2 = A.lnA2;
+                            }
+                        }
+                        for (int a = 0; a < fcnt[T.slot] && !err; ++a) {
+                            const Arr& A = farr[T.slot * g.frz_cap + a];
+                            if (A.k0 + g.n_w <= lo || A.k0 >= hi) continue;
+                            if (npool >= Lo.pool_cap) { err = CMH_ERR_CAPACITY; break; }
+                            pool[npool++] = A;
+                        }
+                        T.noth = npool - T.oth0;
+                        ++nt;
+                    }
+                } else if (valid && !err) {
                     // merge the old event's arrivals and the candidate's, by slot
                     const int ps = idx >= 0 ? order[idx] : -1;
                     const EvArr* oa = ps >= 0 && dr.type != 0 ? earr + ps * g.arr_cap : nullptr;
@@ -400,12 +515,13 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
                     while ((io < no || in < nn) && !err) {
                         const int so = io < no ? oa[io].slot : 1 << 30;
                         const int sn = in < nn ? cand[in].slot : 1 << 30;
-                        if (nt >= Layout::kMaxTasks) { err = CMH_ERR_CAPACITY; break; }
+                        if (nt >= Lo.task_cap) { err = CMH_ERR_CAPACITY; break; }
                         Task& T = tasks[nt];
                         T.slot = so < sn ? so : sn;
                         T.row = bsta[T.slot];
                         T.has_o = so <= sn;
                         T.has_n = sn <= so;
+                        T.has_o2 = T.has_n2 = 0;
                         long long lo = 1LL << 40, hi = -1;
                         if (T.has_o) {
                             const EvArr& A = oa[io++];
@@ -459,10 +575,13 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
                 s_err = err;
                 s_valid = valid;
                 s_idx = idx;
+                s_idx2 = idx2;
                 s_type = dr.type;
                 s_ncand = ncand;
+                s_ncand2 = ncand2;
                 s_ntask = nt;
                 s_c[0] = cx; s_c[1] = cy; s_c[2] = ct; s_c[3] = cm;
+                s_c2[0] = cx2; s_c2[1] = cy2; s_c2[2] = ct2; s_c2[3] = cm2;
             }
         }
         __syncthreads();
@@ -477,6 +596,32 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
                 // at the next one is this one times rstep (one exp at the
                 // first sample inside the window, then a product per sample)
                 const double rstep = exp(-(double)nthr * (2.0 / (g.f_hz * g.tau)));
+                if (s_type == 3) {
+                    // joint move: on every sample inside one of the four
+                    // windows, the new variance summed from scratch (others,
+                    // then the two candidates) against the resident one
+                    for (int ti = 0; ti < ntask; ++ti) {
+                        const Task& T = tasks[ti];
+                        const double* srow = (const double*)d.sig + (size_t)T.row * g.pitch;
+                        const double* vrow = (const double*)d.V + (size_t)T.row * g.pitch;
+                        for (int kk = T.lo + tid; kk < T.hi; kk += nthr) {
+                            const bool io = T.has_o && (unsigned)(kk - T.k0o) < (unsigned)g.n_w;
+                            const bool io2 = T.has_o2 && (unsigned)(kk - T.k0o2) < (unsigned)g.n_w;
+                            const bool in1 = T.has_n && (unsigned)(kk - T.k0n) < (unsigned)g.n_w;
+                            const bool in2 = T.has_n2 && (unsigned)(kk - T.k0n2) < (unsigned)g.n_w;
+                            if (!(io || io2 || in1 || in2)) continue;
+                            double a2 = g.noise_var;
+                            for (int o = 0; o < T.noth; ++o) {
+                                const Arr& A = pool[T.oth0 + o];
+                                if ((unsigned)(kk - A.k0) < (unsigned)g.n_w) a2 += arr_c64(g, A.af, A.lnA2, kk);
+                            }
+                            if (in1) a2 += arr_c64(g, T.afn, T.lnA2n, kk);
+                            if (in2) a2 += arr_c64(g, T.afn2, T.lnA2n2, kk);
+                            const double V = vrow[kk], sv = __ldg(srow + kk);
+                            acc += -0.5 * (log(a2 / V) + sv * sv * (1.0 / a2 - 1.0 / V));
+                        }
+                    }
+                } else
                 for (int ti = 0; ti < ntask; ++ti) {
                     const Task& T = tasks[ti];
                     const double* srow = (const double*)d.sig + (size_t)T.row * g.pitch;
@@ -548,6 +693,15 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
                     const double lq = -s_log_area - g.log_T - (me - 2.0);
                     dlp = -lb;
                     la = dll + dlp + lq + g.log_pb - g.log_pd + d.log_n[n_own];
+                } else if (type == 3) {
+                    // symmetric proposal: the prior ratio of the two events
+                    const double me1 = em[order[s_idx]], me2 = em[order[s_idx2]];
+                    const double lb1n = g.log_Lambda - g.log_WWT - (cm - 2.0);
+                    const double lb1o = g.log_Lambda - g.log_WWT - (me1 - 2.0);
+                    const double lb2n = g.log_Lambda - g.log_WWT - (s_c2[3] - 2.0);
+                    const double lb2o = g.log_Lambda - g.log_WWT - (me2 - 2.0);
+                    dlp = (lb1n - lb1o) + (lb2n - lb2o);
+                    la = dll + dlp;
                 } else {
                     const double me = em[order[s_idx]];
                     const double lb_new = g.log_Lambda - g.log_WWT - (cm - 2.0);
@@ -590,6 +744,12 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
                     ex[ps] = s_c[0]; ey[ps] = s_c[1]; et[ps] = s_c[2]; em[ps] = s_c[3];
                     for (int a = 0; a < s_ncand; ++a) earr[ps * g.arr_cap + a] = cand[a];
                     enarr[ps] = s_ncand;
+                    if (type == 3) {
+                        const int p2 = order[s_idx2];
+                        ex[p2] = s_c2[0]; ey[p2] = s_c2[1]; et[p2] = s_c2[2]; em[p2] = s_c2[3];
+                        for (int a = 0; a < s_ncand2; ++a) earr[p2 * g.arr_cap + a] = cand[g.arr_cap + a];
+                        enarr[p2] = s_ncand2;
+                    }
                 }
             } else if (acc) {
                 ++n_acc[type];
@@ -604,6 +764,7 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
             for (int ti = 0; ti < ntask; ++ti) {
                 const Task& T = tasks[ti];
                 const bool has_new = type != 1 && T.has_n;
+                const bool has_new2 = type == 3 && T.has_n2;
                 {
                     double* vrow = (double*)d.V + (size_t)T.row * g.pitch;
                     for (int kk = T.lo + tid; kk < T.hi; kk += nthr) {
@@ -616,6 +777,10 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
                         if (has_new) {
                             const int r = kk - T.k0n;
                             if ((unsigned)r < (unsigned)g.n_w) a2 += arr_c64(g, T.afn, T.lnA2n, kk);
+                        }
+                        if (has_new2) {
+                            const int r = kk - T.k0n2;
+                            if ((unsigned)r < (unsigned)g.n_w) a2 += arr_c64(g, T.afn2, T.lnA2n2, kk);
                         }
                         vrow[kk] = a2;
                     }
@@ -647,6 +812,9 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
             if (n_eval[t]) atomicAdd(&d.stats[3 + t], n_eval[t]);
             if (n_acc[t]) atomicAdd(&d.stats[6 + t], n_acc[t]);
         }
+        if (n_prop[3]) atomicAdd(&d.stats[11], n_prop[3]);
+        if (n_eval[3]) atomicAdd(&d.stats[12], n_eval[3]);
+        if (n_acc[3]) atomicAdd(&d.stats[13], n_acc[3]);
         if (n_priced) atomicAdd(&d.stats[9], n_priced);
         if (n_rewritten) atomicAdd(&d.stats[10], n_rewritten);
     }

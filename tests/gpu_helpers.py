@@ -42,8 +42,8 @@ def run_gpu(cm, world, *, sweeps, k=16, seed=11, dtype=None, shift_mode=1, sx=0.
 
 
 def run_oracle(orc, world, *, sweeps, k=16, seed=11, shift_mode=1, sx=0.0, sy=0.0, events=None, commit=True,
-               threads=1):
-    o = orc.World(world, k_per_phase=k, seed=seed, commit=commit)
+               threads=1, **okw):
+    o = orc.World(world, k_per_phase=k, seed=seed, commit=commit, **okw)
     ev0 = np.zeros((0, 4)) if events is None else events
     ncx = int(np.floor(world.params.W / world.params.L)) + 2
     ev, ids, tr, dlp = o.run_chromatic(ev0, sweeps, shift_mode=shift_mode, sx=sx, sy=sy,

@@ -54,6 +54,9 @@ def _params(cm, **kw):
     dict(dtype=7),
     dict(likelihood=2),
     dict(likelihood=1, dtype=0),   # the additive-mean reading is float32 only
+    dict(p_pair=-0.1),
+    dict(p_pair=0.6),              # p_birth + p_death + p_pair > 1
+    dict(p_pair=0.2, dtype=1),     # the joint move is float64 only
 ])
 def test_create_model_rejects_bad_params_on_host(cm, bad):
     lik = bad.pop("likelihood", None)

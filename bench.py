@@ -72,14 +72,20 @@ def _traffic():
     return float(rec["dram_bytes_per_launch"]), rec.get("command", "")
 
 
-def _workload(name: str, likelihood: str = "variance"):
+def n_proposals(st) -> int:
+    """Every MH proposal a model made: birth, death, move and joint pair moves."""
+    return int(sum(st["proposed"]) + st["pair"][0])
+
+
+def _workload(name: str, likelihood: str = "variance", p_pair: float = 0.0):
     if name == "scale":
         return worldgen.config_scale(seed=SEED, likelihood=likelihood), \
             "fp32 sweep at scale: 4000x4000 km, 24 h, ~1e4 events, 1600 stations x 864000 f32 samples, " \
             "40x40 regions, k=32" + ("" if likelihood == "variance" else ", additive-mean likelihood reading")
     if name == "replay":
         return worldgen.config_replay(seed=SEED), "fp64 replay: 1000x1000 km, 1 h, ~500 events, " \
-                                                  "100 stations x 36000 f64 samples, 10x10 regions, k=32"
+                                                  "100 stations x 36000 f64 samples, 10x10 regions, k=32" + (
+                                                      ", joint pair moves p_pair=%g" % p_pair if p_pair else "")
     raise SystemExit("unknown workload " + name)
 
 
@@ -135,7 +141,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _cpu_baseline(world, seconds_target: float = 15.0):
+def _cpu_baseline(world, seconds_target: float = 15.0, p_pair: float = 0.0):
     """The oracle's chromatic sampler on a 1000 x 1000 km corner of the world
     (same station density, event intensity and record length)."""
     import oracle
@@ -146,7 +152,7 @@ def _cpu_baseline(world, seconds_target: float = 15.0):
     p = worldgen.ModelParams(**{**world.params.__dict__, "W": sub_side, "Lambda": world.params.Lambda * frac})
     sub.params = p
     threads = os.cpu_count() or 1
-    o = oracle.World(sub, k_per_phase=K_PER_PHASE, seed=CHAIN_SEED)
+    o = oracle.World(sub, k_per_phase=K_PER_PHASE, seed=CHAIN_SEED, p_pair=p_pair)
     ev = sub.events
     ids = None
     t0 = time.perf_counter()
@@ -169,8 +175,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    world, desc = _workload(args.workload, args.likelihood)
-    base = _cpu_baseline(world, seconds_target=max(5.0, 3.0 * args.steps / 10.0))
+    world, desc = _workload(args.workload, args.likelihood, args.p_pair)
+    base = _cpu_baseline(world, seconds_target=max(5.0, 3.0 * args.steps / 10.0), p_pair=args.p_pair)
     line = {"impl": "reference", "metric": "MH proposals/sec and sweeps/sec on 1 GB300",
             "value": base["value"], "unit": "proposals/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -212,13 +218,13 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_1612_00595_gb300 as cm
 
-    world, desc = _workload(args.workload, args.likelihood)
+    world, desc = _workload(args.workload, args.likelihood, args.p_pair)
     p = world.params
     f32 = world.signals.dtype == np.float32
     dtype = cm.F32 if f32 else cm.F64
     esz = 4 if f32 else 8
     # each rank runs an independent chain (weak scaling: fixed work per GPU)
-    params = cm.make_params(p, k_per_phase=K_PER_PHASE, seed=chain_seed(rank), dtype=dtype)
+    params = cm.make_params(p, k_per_phase=K_PER_PHASE, seed=chain_seed(rank), dtype=dtype, p_pair=args.p_pair)
     stream = torch.cuda.Stream()
     sig_dev = torch.from_numpy(world.signals).to("cuda", non_blocking=False)
     torch.cuda.synchronize()
@@ -245,7 +251,7 @@ def run_ours(args):
     barrier()
     ms = e0.elapsed_time(e1)
     _, _, _, st1 = m.read_state(cap=0)
-    props = sum(st1["proposed"]) - sum(st0["proposed"])
+    props = n_proposals(st1) - n_proposals(st0)
     launches = st1["kernel_launches"] - st0["kernel_launches"]
     ms_max, total_props = reduce_max_sum(ms, props, dist, "cuda")
     value = total_props / (ms_max / 1e3)
@@ -305,14 +311,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     _, _, _, st2 = m2.read_state(cap=0)
-    e2e_props = sum(st2["proposed"])
+    e2e_props = n_proposals(st2)
     m2.destroy()
     e2e_max, e2e_total = reduce_max_sum(e2e_s, e2e_props, dist, "cuda")
     e2e_value = e2e_total / e2e_max
     h2d_per_step = world.signals.nbytes / args.steps
 
     if rank == 0:
-        cpu = _cpu_baseline(world) if world_size == 1 else None
+        cpu = _cpu_baseline(world, p_pair=args.p_pair) if world_size == 1 else None
         line = {"metric": "MH proposals/sec and sweeps/sec on 1 GB300", "value": value, "unit": "proposals/s",
                 "sweeps_per_s": sweeps_per_s, "n_gpus": world_size, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -364,7 +370,7 @@ def run_batched(args):
     b = cm.create_batch(models, stream=stream)
     b.run_sweeps(args.warmup)
     b.sync()
-    p0 = sum(sum(m.read_state(cap=0)[3]["proposed"]) for m in models)
+    p0 = sum(n_proposals(m.read_state(cap=0)[3]) for m in models)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -375,7 +381,7 @@ def run_batched(args):
         e1.synchronize()
     b.sync()
     ms = e0.elapsed_time(e1)
-    p1 = sum(sum(m.read_state(cap=0)[3]["proposed"]) for m in models)
+    p1 = sum(n_proposals(m.read_state(cap=0)[3]) for m in models)
     n_regions = sum((int(w.params.W // w.params.L) + 2) ** 2 for w in kept)
     worlds_all, worlds = worlds, kept
     line = {"metric": "MH proposals/sec and sweeps/sec on 1 GB300 (batched instances)", "value": (p1 - p0) / (ms / 1e3),
@@ -552,7 +558,11 @@ def main():
     ap.add_argument("--workload", default="scale", choices=["scale", "replay", "batched", "learned", "learned-posterior"])
     ap.add_argument("--likelihood", default="variance", choices=["variance", "mean"],
                     help="scale workload: arrivals add to the sample variance (default) or to its mean")
+    ap.add_argument("--p-pair", type=float, default=0.0,
+                    help="replay workload: share of steps that propose the joint move of a pair of events")
     args = ap.parse_args()
+    if args.p_pair and args.workload != "replay":
+        raise SystemExit("--p-pair needs the float64 replay workload")
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":

@@ -7,7 +7,8 @@ Workloads: ``scale`` (4000 x 4000 km, 24 h, 1600 stations, float32),
 100 stations: 0.7 GB of signals + variance, larger than L2), ``replay``
 (1000 x 1000 km, 1 h, 100 stations, float64), ``train`` (the learned birth
 network: ``--warmup`` then ``--sweeps`` training steps of 256 windows
-simulated from the 1000 km, 1 h, 100-station float32 world).
+simulated from the 1000 km, 1 h, 100-station float32 world).  ``--p-pair``
+turns on joint moves of a pair of events (float64 workloads).
 """
 import argparse
 import os
@@ -37,6 +38,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--k", type=int, default=32)
+    ap.add_argument("--p-pair", type=float, default=0.0)
     args = ap.parse_args()
     import paper_1612_00595_gb300 as cm
     if args.workload == "train":
@@ -53,14 +55,14 @@ def main():
     w = world_for(args.workload)
     dtype = cm.F32 if w.signals.dtype == np.float32 else cm.F64
     m = cm.create_model(w.events, w.stations, w.signals, cm.make_params(w.params, k_per_phase=args.k, seed=7,
-                                                                        dtype=dtype))
+                                                                        dtype=dtype, p_pair=args.p_pair))
     m.partition_and_color(w.params.L, shift_mode=1)
     m.run_sweeps(args.warmup)
     m.sync()
     m.run_sweeps(args.sweeps)
     ev, ids, lp, st = m.read_state()
-    print("events %d  proposals %d  accepted %s  launches %d" % (len(ev), sum(st["proposed"]), st["accepted"],
-                                                                  st["kernel_launches"]))
+    print("events %d  proposals %d  accepted %s  pair %s  launches %d" % (
+        len(ev), sum(st["proposed"]) + st["pair"][0], st["accepted"], st["pair"], st["kernel_launches"]))
     m.destroy()
 
 

@@ -163,7 +163,7 @@ __device__ __forceinline__ int block_append(bool flag, int* s_warp, int* s_base)
     return pos;
 }
 
-__global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
+__global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour) {
     if (*d.status) return;
     const long long sweep = *d.sweep;
     if ((int)blockIdx.x >= d.colour_count[colour]) return;
@@ -598,27 +598,46 @@ __global__ void __launch_bounds__(512) phase_kernel(Geo g, Dev d, int colour) {
                 const double rstep = exp(-(double)nthr * (2.0 / (g.f_hz * g.tau)));
                 if (s_type == 3) {
                     // joint move: on every sample inside one of the four
-                    // windows, the new variance summed from scratch (others,
-                    // then the two candidates) against the resident one
+                    // windows, the resident variance changed by the two
+                    // candidates' contributions less the two old ones (each a
+                    // running envelope product along the thread's samples);
+                    // where the change removes more than half of it, the new
+                    // variance summed from scratch instead
                     for (int ti = 0; ti < ntask; ++ti) {
                         const Task& T = tasks[ti];
                         const double* srow = (const double*)d.sig + (size_t)T.row * g.pitch;
                         const double* vrow = (const double*)d.V + (size_t)T.row * g.pitch;
+                        double co = -1.0, co2 = -1.0, cn = -1.0, cn2 = -1.0;   // < 0: not started
                         for (int kk = T.lo + tid; kk < T.hi; kk += nthr) {
                             const bool io = T.has_o && (unsigned)(kk - T.k0o) < (unsigned)g.n_w;
                             const bool io2 = T.has_o2 && (unsigned)(kk - T.k0o2) < (unsigned)g.n_w;
                             const bool in1 = T.has_n && (unsigned)(kk - T.k0n) < (unsigned)g.n_w;
                             const bool in2 = T.has_n2 && (unsigned)(kk - T.k0n2) < (unsigned)g.n_w;
+                            if (io) co = co < 0.0 ? arr_c64(g, T.afo, T.lnA2o, kk) : co * rstep;
+                            if (io2) co2 = co2 < 0.0 ? arr_c64(g, T.afo2, T.lnA2o2, kk) : co2 * rstep;
+                            if (in1) cn = cn < 0.0 ? arr_c64(g, T.afn, T.lnA2n, kk) : cn * rstep;
+                            if (in2) cn2 = cn2 < 0.0 ? arr_c64(g, T.afn2, T.lnA2n2, kk) : cn2 * rstep;
                             if (!(io || io2 || in1 || in2)) continue;
-                            double a2 = g.noise_var;
-                            for (int o = 0; o < T.noth; ++o) {
-                                const Arr& A = pool[T.oth0 + o];
-                                if ((unsigned)(kk - A.k0) < (unsigned)g.n_w) a2 += arr_c64(g, A.af, A.lnA2, kk);
-                            }
-                            if (in1) a2 += arr_c64(g, T.afn, T.lnA2n, kk);
-                            if (in2) a2 += arr_c64(g, T.afn2, T.lnA2n2, kk);
+                            double dd = 0.0;
+                            if (in1) dd += cn;
+                            if (in2) dd += cn2;
+                            if (io) dd -= co;
+                            if (io2) dd -= co2;
                             const double V = vrow[kk], sv = __ldg(srow + kk);
-                            acc += -0.5 * (log(a2 / V) + sv * sv * (1.0 / a2 - 1.0 / V));
+                            const double Vp = V + dd;
+                            if (Vp < 0.5 * V) {
+                                double a2 = g.noise_var;
+                                for (int o = 0; o < T.noth; ++o) {
+                                    const Arr& A = pool[T.oth0 + o];
+                                    if ((unsigned)(kk - A.k0) < (unsigned)g.n_w) a2 += arr_c64(g, A.af, A.lnA2, kk);
+                                }
+                                if (in1) a2 += arr_c64(g, T.afn, T.lnA2n, kk);
+                                if (in2) a2 += arr_c64(g, T.afn2, T.lnA2n2, kk);
+                                acc += -0.5 * (log(a2 / V) + sv * sv * (1.0 / a2 - 1.0 / V));
+                            } else {
+                                const double inv = 1.0 / (V * Vp);   // one division for both terms
+                                acc += -0.5 * (log1p_series64(dd * Vp * inv) - sv * sv * dd * inv);
+                            }
                         }
                     }
                 } else

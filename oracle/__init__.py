@@ -57,7 +57,7 @@ class _Params(C.Structure):
         ("lattice", C.c_int32), ("lat_nx", C.c_int32), ("lat_ny", C.c_int32), ("lat_nt", C.c_int32),
         ("lat_nm", C.c_int32), ("lat_nmax", C.c_int32), ("likelihood", C.c_int32)] + [
         (n, C.c_double) for n in ("lat_x0", "lat_dx", "lat_y0", "lat_dy", "lat_t0", "lat_dt",
-                                  "lat_m0", "lat_dm", "p_pair")]
+                                  "lat_m0", "lat_dm", "p_pair", "sig_a", "p_arr", "sig_da")]
 
 
 TRACE_DTYPE = np.dtype([("sweep", "<i4"), ("cell", "<i4"), ("step", "<i4"), ("type", "<i4"),
@@ -96,6 +96,11 @@ def lib(mutant: int = 0):
             "orc_blankets": (None, [P, d, d, P]),
             "orc_log_alpha": (d, [P, d, d, i32, P, i64, i32, i64, P, C.POINTER(i32)]),
             "orc_log_alpha_pair": (d, [P, d, d, i32, P, i64, i64, i64, P, P, C.POINTER(i32)]),
+            "orc_log_alpha_off": (d, [P, d, d, i32, P, P, i64, i32, i64, i32, P, P, C.POINTER(i32)]),
+            "orc_log_prior_off": (d, [P, P, P, i64]),
+            "orc_log_likelihood_off": (d, [P, P, P, i64]),
+            "orc_set_new_w": (P, [P, P, P, P, i64]),
+            "orc_set_offsets": (None, [P, P, P]),
             "orc_run_serial": (C.c_int, [P, P, i64, i64, P, i64, C.POINTER(i64), pd]),
             "orc_run_chromatic": (C.c_int, [P, P, i64, i64, i32, d, d, P, i64, C.POINTER(i64),
                                             i32, pd]),
@@ -143,7 +148,7 @@ class World:
 
     def __init__(self, world, p_birth=0.25, p_death=0.25, sig_xy=5.0, sig_t=2.0, sig_m=0.1,
                  k_per_phase=32, seed=1, commit=True, lattice: Optional[Lattice] = None,
-                 mutant: int = 0, p_pair=0.0):
+                 mutant: int = 0, p_pair=0.0, sig_a=0.0, p_arr=0.0, sig_da=1.0):
         self._lib = lib(mutant)
         p = world.params
         self.world = world
@@ -153,6 +158,8 @@ class World:
                   "R_max", "L"):
             setattr(prm, n, float(getattr(p, n)))
         prm.p_birth, prm.p_death, prm.p_pair = p_birth, p_death, p_pair
+        prm.sig_a, prm.p_arr, prm.sig_da = sig_a, p_arr, sig_da
+        self.latent = sig_a > 0.0
         prm.sig_xy, prm.sig_t, prm.sig_m = sig_xy, sig_t, sig_m
         prm.n_w = p.n_w
         prm.k_per_phase = k_per_phase
@@ -178,6 +185,9 @@ class World:
         self._h = self._lib.orc_world_new(C.byref(prm), _ptr(self._st), self._st.shape[0], _ptr(sig),
                                       1 if sig.dtype == np.float32 else 0, n_samp,
                                       sig.strides[0] // sig.itemsize if sig.shape[0] else n_samp)
+        if not self._h:
+            raise ValueError("oracle world rejected (with latent arrivals an event may reach at most 128 "
+                             "stations)")
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -213,16 +223,40 @@ class World:
             raise ValueError("orc_set_birth_magnitude rejected the magnitudes")
 
     # ---- density -----------------------------------------------------------
-    def log_prior(self, ev) -> float:
-        ev = np.ascontiguousarray(ev, dtype=np.float64).reshape(-1, 4)
-        return self._lib.orc_log_prior(self._h, _ptr(ev), ev.shape[0])
+    def _off(self, off, n):
+        if off is None:
+            return None
+        off = np.ascontiguousarray(off, dtype=np.float64).reshape(n, self._st.shape[0])
+        return off
 
-    def log_likelihood(self, ev) -> float:
+    def log_prior(self, ev, off=None) -> float:
+        """-Lambda + sum log beta(e), plus log N(delta; 0, sig_a^2) for every
+        latent arrival offset (off: dense [n, n_st], None = 0)."""
         ev = np.ascontiguousarray(ev, dtype=np.float64).reshape(-1, 4)
-        return self._lib.orc_log_likelihood(self._h, _ptr(ev), ev.shape[0])
+        return self._lib.orc_log_prior_off(self._h, _ptr(ev), _ptr(self._off(off, ev.shape[0])), ev.shape[0])
 
-    def log_density(self, ev) -> float:
-        return self.log_prior(ev) + self.log_likelihood(ev)
+    def log_likelihood(self, ev, off=None) -> float:
+        ev = np.ascontiguousarray(ev, dtype=np.float64).reshape(-1, 4)
+        return self._lib.orc_log_likelihood_off(self._h, _ptr(ev), _ptr(self._off(off, ev.shape[0])),
+                                                ev.shape[0])
+
+    def log_density(self, ev, off=None) -> float:
+        return self.log_prior(ev, off) + self.log_likelihood(ev, off)
+
+    def log_alpha_off(self, sx, sy, cell, ev, off, type_, idx=-1, station=-1, cand=None, cand_off=None):
+        """Log acceptance ratio of one explicit proposal on a state with latent
+        arrival offsets; type 4 moves the idx-th region event's offset at
+        `station` to cand_off (a scalar)."""
+        ev = np.ascontiguousarray(ev, dtype=np.float64).reshape(-1, 4)
+        off = self._off(off, ev.shape[0])
+        c = None if cand is None else np.ascontiguousarray(cand, dtype=np.float64)
+        if cand_off is not None:
+            cand_off = np.ascontiguousarray(np.atleast_1d(cand_off), dtype=np.float64)
+        v = C.c_int32()
+        la = self._lib.orc_log_alpha_off(self._h, sx, sy, int(cell), _ptr(ev), _ptr(off), ev.shape[0],
+                                         int(type_), int(idx), int(station), _ptr(c), _ptr(cand_off),
+                                         C.byref(v))
+        return la, bool(v.value)
 
     def variance(self, ev, j, k0, k1) -> np.ndarray:
         ev = np.ascontiguousarray(ev, dtype=np.float64).reshape(-1, 4)
@@ -286,23 +320,29 @@ class World:
         return la, bool(v.value)
 
     # ---- samplers ----------------------------------------------------------
-    def _set(self, ev, ids):
+    def _set(self, ev, ids, off=None):
         ev = np.ascontiguousarray(ev, dtype=np.float64).reshape(-1, 4)
         if ids is None:
             ids = np.arange(ev.shape[0], dtype=np.uint64)
         ids = np.ascontiguousarray(ids, dtype=np.uint64)
-        return self._lib.orc_set_new(_ptr(ev), _ptr(ids), ev.shape[0])
+        return self._lib.orc_set_new_w(self._h, _ptr(ev), _ptr(ids), _ptr(self._off(off, ev.shape[0])),
+                                       ev.shape[0])
 
     def _get(self, h):
         n = self._lib.orc_set_size(h)
         ev = np.zeros((n, 4))
         ids = np.zeros(n, dtype=np.uint64)
         self._lib.orc_set_get(h, _ptr(ev), _ptr(ids))
+        self.last_offsets = np.zeros((n, self._st.shape[0]))
+        if n and self._st.shape[0]:
+            self._lib.orc_set_offsets(self._h, h, _ptr(self.last_offsets))
         self._lib.orc_set_free(h)
         return ev, ids
 
-    def run_serial(self, ev, n_steps, ids=None, step0=0, trace_cap=0):
-        h = self._set(ev, ids)
+    def run_serial(self, ev, n_steps, ids=None, step0=0, trace_cap=0, off=None):
+        """Serial MH; with latent arrivals the final state's dense offsets
+        are left in ``self.last_offsets`` (and ``off`` seeds the start's)."""
+        h = self._set(ev, ids, off)
         tr = np.zeros(trace_cap, dtype=TRACE_DTYPE)
         nt = C.c_int64()
         dlp = C.c_double()
@@ -314,8 +354,8 @@ class World:
         return ev2, ids2, tr[: min(nt.value, trace_cap)], dlp.value
 
     def run_chromatic(self, ev, n_sweeps, ids=None, sweep0=0, shift_mode=1, sx=0.0, sy=0.0,
-                      trace_cap=0, threads=1):
-        h = self._set(ev, ids)
+                      trace_cap=0, threads=1, off=None):
+        h = self._set(ev, ids, off)
         tr = np.zeros(trace_cap, dtype=TRACE_DTYPE)
         nt = C.c_int64()
         dlp = C.c_double()

@@ -11,7 +11,9 @@
  *   event e = (x, y, t, m) in [0,W)^2 x [0,T) x [2, inf)
  *   prior: Poisson process with intensity beta(e) = Lambda/(W^2 T) exp(-(m-2));
  *          log-density  -Lambda + sum_i log beta(e_i)
- *   arrival at station j: a = t + d/v  (d = distance, deterministic arrival)
+ *   arrival at station j: a = t + d/v + delta_j  (d = distance; with
+ *          sig_a > 0 a latent delta_j ~ N(0, sig_a^2) per reached station,
+ *          otherwise delta_j = 0: the deterministic arrival)
  *   the event reaches station j iff d < R_max
  *   variance added at sample k (time k/f): (A g(k/f - a))^2 for
  *          k in [ceil(a f), ceil(a f) + n_w), A = exp(alpha m - beta_att d),
@@ -42,13 +44,25 @@
  *      come from the mixture with a learned table;
  *   6: with learned magnitudes, the learned component's density keeps the
  *      prior magnitude law although it draws m from its window;
- *   7: the joint move of a pair ignores the prior ratio.
+ *   7: the joint move of a pair ignores the prior ratio;
+ *   8: the arrival-time move ignores the prior ratio of its offset;
+ *   9: offsets of stations an event newly reaches are set to 0 instead of
+ *      drawn from their prior.
  * 0 (the default) is the oracle itself. */
 #ifndef ORC_MUTANT
 #define ORC_MUTANT 0
 #endif
 
-typedef struct { double x, y, t, m; uint64_t id; } ev_t;
+/* an event; with latent arrival times also the offsets delta of the na
+ * stations it reaches (sta[] increasing) */
+#define ORC_MAXA 128
+typedef struct {
+    double x, y, t, m;
+    uint64_t id;
+    int32_t na;
+    int32_t sta[ORC_MAXA];
+    double off[ORC_MAXA];
+} ev_t;
 
 struct orc_world {
     orc_params p;
@@ -135,6 +149,18 @@ orc_world* orc_world_new(const orc_params* p, const double* stations, int32_t n_
     w->f32 = signals_f32;
     w->n_samp = n_samp;
     w->pitch = pitch;
+    if (p->sig_a > 0.0) {
+        /* an event's reached stations lie within 2 R_max of one another, so
+         * no event reaches more than the largest such neighbourhood */
+        for (int32_t j = 0; j < n_st; ++j) {
+            int32_t c = 0;
+            for (int32_t k = 0; k < n_st; ++k) {
+                const double dx = w->st[2 * j] - w->st[2 * k], dy = w->st[2 * j + 1] - w->st[2 * k + 1];
+                if (sqrt(dx * dx + dy * dy) < 2.0 * p->R_max) ++c;
+            }
+            if (c > ORC_MAXA) { orc_world_free(w); return NULL; }
+        }
+    }
     return w;
 }
 
@@ -218,8 +244,24 @@ orc_set* orc_set_new(const double* ev, const uint64_t* ids, int64_t n) {
         s->e[i].x = ev[4 * i]; s->e[i].y = ev[4 * i + 1];
         s->e[i].t = ev[4 * i + 2]; s->e[i].m = ev[4 * i + 3];
         s->e[i].id = ids ? ids[i] : (uint64_t)i;
+        s->e[i].na = 0;
     }
     return s;
+}
+
+static void fill_offsets(const orc_world* w, ev_t* e, const double* row);
+
+orc_set* orc_set_new_w(const orc_world* w, const double* ev, const uint64_t* ids, const double* off,
+                       int64_t n) {
+    orc_set* s = orc_set_new(ev, ids, n);
+    for (int64_t i = 0; i < n; ++i) fill_offsets(w, &s->e[i], off ? off + (size_t)i * (size_t)w->n_st : NULL);
+    return s;
+}
+
+void orc_set_offsets(const orc_world* w, const orc_set* s, double* off) {
+    memset(off, 0, sizeof(double) * (size_t)s->n * (size_t)w->n_st);
+    for (int64_t i = 0; i < s->n; ++i)
+        for (int32_t k = 0; k < s->e[i].na; ++k) off[(size_t)i * (size_t)w->n_st + s->e[i].sta[k]] = s->e[i].off[k];
 }
 int64_t orc_set_size(const orc_set* s) { return s->n; }
 void orc_set_get(const orc_set* s, double* ev, uint64_t* ids) {
@@ -235,7 +277,45 @@ void orc_set_free(orc_set* s) {
     free(s);
 }
 
-static void to_ev(const double* a, ev_t* e) { e->x = a[0]; e->y = a[1]; e->t = a[2]; e->m = a[3]; e->id = 0; }
+static void to_ev(const double* a, ev_t* e) {
+    e->x = a[0]; e->y = a[1]; e->t = a[2]; e->m = a[3]; e->id = 0; e->na = 0;
+}
+
+static int reaches(const orc_world* w, const ev_t* e, int32_t j) {
+    double dx = e->x - w->st[2 * j];
+    double dy = e->y - w->st[2 * j + 1];
+    return sqrt(dx * dx + dy * dy) < w->p.R_max;
+}
+
+/* with latent arrivals: the offsets of the stations e reaches, from a dense
+ * row (NULL: 0) */
+static void fill_offsets(const orc_world* w, ev_t* e, const double* row) {
+    e->na = 0;
+    if (!(w->p.sig_a > 0.0)) return;
+    for (int32_t j = 0; j < w->n_st; ++j)
+        if (reaches(w, e, j)) {
+            e->sta[e->na] = j;
+            e->off[e->na] = row ? row[j] : 0.0;
+            ++e->na;
+        }
+}
+
+/* offset of e at station j (0 if none is held) */
+static double offset_at(const ev_t* e, int32_t j) {
+    for (int32_t k = 0; k < e->na; ++k)
+        if (e->sta[k] == j) return e->off[k];
+    return 0.0;
+}
+
+/* log N(delta; 0, sig_a^2) summed over e's offsets (0 without latent arrivals) */
+static double log_off_prior(const orc_world* w, const ev_t* e) {
+    if (!(w->p.sig_a > 0.0)) return 0.0;
+    const double s2 = w->p.sig_a * w->p.sig_a;
+    double lp = 0.0;
+    for (int32_t k = 0; k < e->na; ++k)
+        lp += -0.5 * log(2.0 * M_PI * s2) - e->off[k] * e->off[k] / (2.0 * s2);
+    return lp;
+}
 
 /* ------------------------------------------------------------------------
  * likelihood pieces (§Generative Model: the observed signal is a zero-mean
@@ -244,8 +324,9 @@ static void to_ev(const double* a, ev_t* e) { e->x = a[0]; e->y = a[1]; e->t = a
  * ---------------------------------------------------------------------- */
 typedef struct { int reach; int64_t k0; double a, amp; } arr_t;
 
-/* arrival of event e at station j: a = t + d/v (mean of the arrival-time
- * distribution of §Event Detections; the jitter is zero here) */
+/* arrival of event e at station j: a = t + d/v (the mean of the
+ * arrival-time distribution of §Event Detections) plus, with latent arrival
+ * times, the event's offset at j */
 static arr_t arrival_of(const orc_world* w, const ev_t* e, int32_t j) {
     arr_t r;
     double dx = e->x - w->st[2 * j];
@@ -253,6 +334,7 @@ static arr_t arrival_of(const orc_world* w, const ev_t* e, int32_t j) {
     double d = sqrt(dx * dx + dy * dy);
     r.reach = d < w->p.R_max;
     r.a = e->t + d / w->p.v;
+    if (w->p.sig_a > 0.0) r.a += offset_at(e, j);
     r.k0 = (int64_t)ceil(r.a * w->p.f_hz);
     r.amp = exp(w->p.alpha * e->m - w->p.beta_att * d);
     return r;
@@ -300,15 +382,33 @@ void orc_variance(const orc_world* w, const double* ev, int64_t n, int32_t j,
     free(ar);
 }
 
-double orc_log_likelihood(const orc_world* w, const double* ev, int64_t n) {
+double orc_log_likelihood_off(const orc_world* w, const double* ev, const double* off, int64_t n) {
     double total = 0.0;
-    double* V = (double*)malloc(sizeof(double) * (size_t)(w->n_samp > 0 ? w->n_samp : 1));
-    for (int32_t j = 0; j < w->n_st; ++j) {
-        orc_variance(w, ev, n, j, 0, w->n_samp, V);
-        for (int64_t k = 0; k < w->n_samp; ++k) total += log_lik_sample(w, sig_at(w, j, k), V[k]);
+    ev_t* es = (ev_t*)malloc(sizeof(ev_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) {
+        to_ev(ev + 4 * i, &es[i]);
+        fill_offsets(w, &es[i], off ? off + (size_t)i * (size_t)w->n_st : NULL);
     }
-    free(V);
+    arr_t* ar = (arr_t*)malloc(sizeof(arr_t) * (size_t)(n > 0 ? n : 1));
+    for (int32_t j = 0; j < w->n_st; ++j) {
+        int64_t na = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            arr_t a = arrival_of(w, &es[i], j);
+            if (a.reach) ar[na++] = a;
+        }
+        for (int64_t k = 0; k < w->n_samp; ++k) {
+            double V = pred_base(w);
+            for (int64_t i = 0; i < na; ++i) V += arr_var(w, &ar[i], k);
+            total += log_lik_sample(w, sig_at(w, j, k), V);
+        }
+    }
+    free(ar);
+    free(es);
     return total;
+}
+
+double orc_log_likelihood(const orc_world* w, const double* ev, int64_t n) {
+    return orc_log_likelihood_off(w, ev, NULL, n);
 }
 
 /* ------------------------------------------------------------------------
@@ -347,13 +447,18 @@ static double log_beta(const orc_world* w, const ev_t* e) {
     return log(p->Lambda) - log(p->W * p->W * p->T) - (e->m - 2.0);
 }
 
-double orc_log_prior(const orc_world* w, const double* ev, int64_t n) {
+double orc_log_prior_off(const orc_world* w, const double* ev, const double* off, int64_t n) {
     double lp = -w->p.Lambda;
     for (int64_t i = 0; i < n; ++i) {
         ev_t e; to_ev(ev + 4 * i, &e);
-        lp += log_beta(w, &e);
+        fill_offsets(w, &e, off ? off + (size_t)i * (size_t)w->n_st : NULL);
+        lp += log_beta(w, &e) + log_off_prior(w, &e);
     }
     return lp;
+}
+
+double orc_log_prior(const orc_world* w, const double* ev, int64_t n) {
+    return orc_log_prior_off(w, ev, NULL, n);
 }
 
 /* ------------------------------------------------------------------------
@@ -712,7 +817,43 @@ static int learned_birth(const orc_world* w, const region_t* g, const uint64_t* 
  * exactly symmetric. */
 static double qgauss(double z) { return rint(fabs(z) * 1048576.0) * (1.0 / 1048576.0); }
 
-typedef struct { int32_t type, valid; int64_t idx, idx2; ev_t cand, cand2; } prop_t;
+typedef struct { int32_t type, valid; int64_t idx, idx2; int32_t slot; ev_t cand, cand2; } prop_t;
+
+/* Philox counter of one step: key (seed, stream), counter (c0, c1, c2, .) */
+typedef struct { uint64_t stream, c0, c1, c2; } ctr_t;
+
+/* offset drawn from its prior N(0, sig_a^2) for station j and the step's
+ * e-th changed event: one Philox block at counter word 16 + 2 j + e, a
+ * Box-Muller cosine from its words 0 and 1 rounded like the walk offsets,
+ * the sign from bit 0 of word 2 */
+static double draw_offset(const orc_world* w, const ctr_t* c, int32_t j, int e) {
+    uint64_t key[2] = { w->p.seed, c->stream };
+    uint64_t ctr[4] = { c->c0, c->c1, c->c2, 16 + 2 * (uint64_t)j + (uint64_t)e };
+    uint64_t o[4];
+    orc_philox4x64(ctr, key, o);
+    double z = qgauss(sqrt(-2.0 * log(u01o(o[0]))) * cos(2.0 * M_PI * u01(o[1])));
+    if (o[2] & 1) z = -z;
+    return w->p.sig_a * z;
+}
+
+/* offsets of an event that moves from `old` (NULL: a birth) to c's
+ * coordinates: a station reached before and after keeps its offset, a newly
+ * reached one draws it from the prior, one no longer reached drops it.  The
+ * draws come from the prior, so their density cancels against the prior's
+ * in every Hastings ratio. */
+static void relocate(const orc_world* w, const ev_t* old, ev_t* c, const ctr_t* ctr, int e) {
+    c->na = 0;
+    if (!(w->p.sig_a > 0.0)) return;
+    int32_t h = 0;
+    for (int32_t j = 0; j < w->n_st; ++j) {
+        if (!reaches(w, c, j)) continue;
+        while (old && h < old->na && old->sta[h] < j) ++h;
+        c->sta[c->na] = j;
+        if (old && h < old->na && old->sta[h] == j) c->off[c->na] = old->off[h];
+        else c->off[c->na] = ORC_MUTANT == 9 ? 0.0 : draw_offset(w, ctr, j, e);
+        ++c->na;
+    }
+}
 
 /* offset of a random-walk step: on a lattice one grid step along one of the
  * four axes (direction from wd[2]); otherwise independent Gaussians of
@@ -740,16 +881,35 @@ static void walk_offset(const orc_world* w, const uint64_t* wd, double off[4]) {
     off[3] = p->sig_m * z[3];
 }
 
-static prop_t decode(const orc_world* w, const region_t* g, const uint64_t* wd,
+static prop_t decode_coords(const orc_world* w, const region_t* g, const uint64_t* wd,
+                            const ev_t* own, int64_t n_own, int64_t n_total);
+
+/* one step's proposal: coordinates, then the latent offsets the candidates
+ * carry */
+static prop_t decode(const orc_world* w, const region_t* g, const uint64_t* wd, const ctr_t* ctr,
                      const ev_t* own, int64_t n_own, int64_t n_total) {
+    prop_t q = decode_coords(w, g, wd, own, n_own, n_total);
+    if (!q.valid || !(w->p.sig_a > 0.0)) return q;
+    if (q.type == 0) relocate(w, NULL, &q.cand, ctr, 0);
+    else if (q.type == 2) relocate(w, &own[q.idx], &q.cand, ctr, 0);
+    else if (q.type == 3) {
+        relocate(w, &own[q.idx], &q.cand, ctr, 0);
+        relocate(w, &own[q.idx2], &q.cand2, ctr, 1);
+    }
+    return q;
+}
+
+static prop_t decode_coords(const orc_world* w, const region_t* g, const uint64_t* wd,
+                            const ev_t* own, int64_t n_own, int64_t n_total) {
     const orc_params* p = &w->p;
     prop_t q;
     memset(&q, 0, sizeof(q));
     double u = u01(wd[0]);
-    const double cb = p->p_birth, cd = cb + p->p_death, cp = cd + p->p_pair;
-    q.type = u < cb ? 0 : (u < cd ? 1 : (u < cp ? 3 : 2));
+    const double cb = p->p_birth, cd = cb + p->p_death, cp = cd + p->p_pair, ca = cp + p->p_arr;
+    q.type = u < cb ? 0 : (u < cd ? 1 : (u < cp ? 3 : (u < ca ? 4 : 2)));
     q.idx = -1;
     q.idx2 = -1;
+    q.slot = -1;
     if (q.type == 0) {
         if (p->lattice) {
             if (n_total >= p->lat_nmax) return q;
@@ -769,6 +929,23 @@ static prop_t decode(const orc_world* w, const region_t* g, const uint64_t* wd,
             q.cand.m = 2.0 - log(u01o(wd[5]));
         }
         q.valid = in_region(w, g, &q.cand) && in_time_mag(w, &q.cand);
+        return q;
+    }
+    if (q.type == 4) {
+        /* arrival-time move (§MH moves, "Arrival Time Move"): event i from
+         * wd[1], one of the stations it reaches from wd[7], its offset moved
+         * by sig_da times a Gaussian (Box-Muller cosine of wd[2], wd[3],
+         * rounded, sign from bit 32 of wd[1]) */
+        if (n_own == 0) return q;
+        q.idx = pick(wd[1], n_own);
+        const ev_t* e = &own[q.idx];
+        if (e->na == 0) return q;
+        q.slot = (int32_t)pick(wd[7], e->na);
+        double z = qgauss(sqrt(-2.0 * log(u01o(wd[2]))) * cos(2.0 * M_PI * u01(wd[3])));
+        if ((wd[1] >> 32) & 1) z = -z;
+        q.cand = *e;
+        q.cand.off[q.slot] += p->sig_da * z;
+        q.valid = 1;
         return q;
     }
     if (q.type == 3) {
@@ -821,35 +998,55 @@ static prop_t decode(const orc_world* w, const region_t* g, const uint64_t* wd,
  *   pair:   dll + sum over the two of log beta(c) - log beta(e): the exchange
  *           is its own inverse, the common offset is symmetric, and the
  *           ordered pair is drawn with probability 1/(n (n-1)) both ways
+ *   arrival: dll + log N(delta'; 0, sig_a^2) - log N(delta; 0, sig_a^2)
+ *           (symmetric step of one offset)
+ * Latent offsets drawn from their prior (a birth's, those of stations a
+ * moved event newly reaches) and those dropped (a death's, stations no longer
+ * reached) have proposal density equal to their prior density, so their
+ * terms cancel from every ratio above.
  */
 static double log_alpha_of(const orc_world* w, const region_t* g, const prop_t* q,
                            const ev_t* own, int64_t n_own, const ev_t* oth, int64_t n_oth,
                            double* dll_out, double* dlp_out) {
     const orc_params* p = &w->p;
-    double dll, dlp, la;
+    double dll, dlp, la, dlo = 0.0;
     if (q->type == 0) {
         dll = delta_ll2(w, own, n_own, oth, n_oth, -1, &q->cand);
         dlp = log_beta(w, &q->cand);
         la = dll + dlp - log_qb(w, g, &q->cand) + log(p->p_death)
              - log((double)(n_own + (ORC_MUTANT == 1 ? 2 : 1))) - log(p->p_birth);
+        dlo = log_off_prior(w, &q->cand);
     } else if (q->type == 1) {
         const ev_t* e = &own[q->idx];
         dll = delta_ll2(w, own, n_own, oth, n_oth, q->idx, NULL);
         dlp = -log_beta(w, e);
         la = dll + dlp + (ORC_MUTANT == 2 ? 0.0 : log_qb(w, g, e)) + log(p->p_birth) - log(p->p_death)
              + log((double)n_own);
+        dlo = -log_off_prior(w, e);
     } else if (q->type == 3) {
         dll = delta_ll_pair(w, own, n_own, oth, n_oth, q->idx, q->idx2, &q->cand, &q->cand2);
         dlp = (log_beta(w, &q->cand) - log_beta(w, &own[q->idx])) +
               (log_beta(w, &q->cand2) - log_beta(w, &own[q->idx2]));
         la = dll + (ORC_MUTANT == 7 ? 0.0 : dlp);
+        dlo = (log_off_prior(w, &q->cand) - log_off_prior(w, &own[q->idx])) +
+              (log_off_prior(w, &q->cand2) - log_off_prior(w, &own[q->idx2]));
+    } else if (q->type == 4) {
+        /* symmetric offset step: the prior ratio of the one offset */
+        dll = delta_ll2(w, own, n_own, oth, n_oth, q->idx, &q->cand);
+        const double s2 = p->sig_a * p->sig_a, a = own[q->idx].off[q->slot], b = q->cand.off[q->slot];
+        dlp = (a * a - b * b) / (2.0 * s2);
+        la = dll + (ORC_MUTANT == 8 ? 0.0 : dlp);
     } else {
         dll = delta_ll2(w, own, n_own, oth, n_oth, q->idx, &q->cand);
         dlp = log_beta(w, &q->cand) - log_beta(w, &own[q->idx]);
         la = dll + (ORC_MUTANT == 4 ? 0.0 : dlp);
+        dlo = log_off_prior(w, &q->cand) - log_off_prior(w, &own[q->idx]);
     }
+    /* offsets drawn from their prior cancel against it in la (births, the
+     * stations a moved event newly reaches); the log-density change still
+     * counts them */
     *dll_out = dll;
-    *dlp_out = dlp;
+    *dlp_out = dlp + dlo;
     return la;
 }
 
@@ -892,7 +1089,8 @@ static void mh_step(const orc_world* w, const region_t* g, vec_t* own, const ev_
                     uint64_t new_id, orc_trace* tr, double* dlogp) {
     uint64_t wd[12];
     step_words(w, stream, c0, c1, c2, wd);
-    prop_t q = decode(w, g, wd, own->e, own->n, own->n + n_total_other);
+    const ctr_t ctr = { stream, c0, c1, c2 };
+    prop_t q = decode(w, g, wd, &ctr, own->e, own->n, own->n + n_total_other);
     double dll = 0.0, dlp = 0.0, la = -INFINITY;
     int acc = 0;
     if (tr) {
@@ -915,9 +1113,9 @@ static void mh_step(const orc_world* w, const region_t* g, vec_t* own, const ev_
     }
 }
 
-double orc_log_alpha(const orc_world* w, double sx, double sy, int32_t cell,
-                     const double* ev, int64_t n, int32_t type, int64_t idx,
-                     const double* cand, int32_t* valid) {
+double orc_log_alpha_off(const orc_world* w, double sx, double sy, int32_t cell,
+                         const double* ev, const double* off, int64_t n, int32_t type, int64_t idx,
+                         int32_t station, const double* cand, const double* cand_off, int32_t* valid) {
     region_t g;
     g.cell = cell; g.sx = sx; g.sy = sy;
     if (cell < 0) { g.r[0] = 0.0; g.r[1] = w->p.W; g.r[2] = 0.0; g.r[3] = w->p.W; }
@@ -926,6 +1124,7 @@ double orc_log_alpha(const orc_world* w, double sx, double sy, int32_t cell,
     vec_t own = { 0, 0, 0 }, oth = { 0, 0, 0 };
     for (int64_t i = 0; i < n; ++i) {
         ev_t e; to_ev(ev + 4 * i, &e);
+        fill_offsets(w, &e, off ? off + (size_t)i * (size_t)w->n_st : NULL);
         e.id = (uint64_t)i;
         if (cell < 0 || orc_cell_of(w, sx, sy, e.x, e.y) == cell) vec_push(&own, &e);
         else vec_push(&oth, &e);
@@ -934,17 +1133,37 @@ double orc_log_alpha(const orc_world* w, double sx, double sy, int32_t cell,
     memset(&q, 0, sizeof(q));
     q.type = type;
     q.idx = idx;
-    if (cand) to_ev(cand, &q.cand);
+    q.slot = -1;
     q.valid = 1;
     if (type != 0 && (idx < 0 || idx >= own.n)) q.valid = 0;
-    if (type == 0 && w->p.lattice && n >= w->p.lat_nmax) q.valid = 0;
-    if (type != 1 && q.valid) q.valid = in_region(w, &g, &q.cand) && in_time_mag(w, &q.cand);
+    if (type == 4) {
+        if (q.valid) {
+            q.cand = own.e[idx];
+            for (int32_t k = 0; k < q.cand.na; ++k)
+                if (q.cand.sta[k] == station) q.slot = k;
+            if (q.slot < 0 || !cand_off) q.valid = 0;
+            else q.cand.off[q.slot] = cand_off[0];
+        }
+    } else {
+        if (cand) {
+            to_ev(cand, &q.cand);
+            fill_offsets(w, &q.cand, cand_off);
+        }
+        if (type == 0 && w->p.lattice && n >= w->p.lat_nmax) q.valid = 0;
+        if (type != 1 && q.valid) q.valid = in_region(w, &g, &q.cand) && in_time_mag(w, &q.cand);
+    }
     double la = -INFINITY, dll, dlp;
     if (q.valid) la = log_alpha_of(w, &g, &q, own.e, own.n, oth.e, oth.n, &dll, &dlp);
     *valid = q.valid;
     free(own.e);
     free(oth.e);
     return la;
+}
+
+double orc_log_alpha(const orc_world* w, double sx, double sy, int32_t cell,
+                     const double* ev, int64_t n, int32_t type, int64_t idx,
+                     const double* cand, int32_t* valid) {
+    return orc_log_alpha_off(w, sx, sy, cell, ev, NULL, n, type, idx, -1, cand, NULL, valid);
 }
 
 double orc_log_alpha_pair(const orc_world* w, double sx, double sy, int32_t cell,
@@ -958,6 +1177,7 @@ double orc_log_alpha_pair(const orc_world* w, double sx, double sy, int32_t cell
     vec_t own = { 0, 0, 0 }, oth = { 0, 0, 0 };
     for (int64_t q = 0; q < n; ++q) {
         ev_t e; to_ev(ev + 4 * q, &e);
+        fill_offsets(w, &e, NULL);
         e.id = (uint64_t)q;
         if (cell < 0 || orc_cell_of(w, sx, sy, e.x, e.y) == cell) vec_push(&own, &e);
         else vec_push(&oth, &e);
@@ -969,6 +1189,8 @@ double orc_log_alpha_pair(const orc_world* w, double sx, double sy, int32_t cell
     q.idx2 = j;
     to_ev(cand1, &q.cand);
     to_ev(cand2, &q.cand2);
+    fill_offsets(w, &q.cand, NULL);
+    fill_offsets(w, &q.cand2, NULL);
     q.valid = i >= 0 && i < own.n && j >= 0 && j < own.n && i != j &&
               in_region(w, &g, &q.cand) && in_time_mag(w, &q.cand) &&
               in_region(w, &g, &q.cand2) && in_time_mag(w, &q.cand2);

@@ -45,10 +45,18 @@ typedef struct {
      * moves, "Joint Events Move"); proposals with u in [p_birth + p_death,
      * p_birth + p_death + p_pair) take it, the Gaussian move keeps the rest */
     double p_pair;
+    /* latent arrival times (§Generative Model, Event Detections): the arrival
+     * of an event at a station it reaches is t + d/v + delta with delta ~
+     * N(0, sig_a^2), one latent delta per (event, reached station); sig_a = 0
+     * is the deterministic model (no latent offsets).  p_arr is the share of
+     * steps that propose the arrival-time move (one delta changed by a
+     * Gaussian of scale sig_da; §MH moves, "Arrival Time Move"); it follows
+     * p_pair in the proposal mix */
+    double sig_a, p_arr, sig_da;
 } orc_params;
 
 typedef struct {
-    int32_t sweep, cell, step, type;   /* type: 0 birth, 1 death, 2 move, 3 pair */
+    int32_t sweep, cell, step, type;   /* type: 0 birth, 1 death, 2 move, 3 pair, 4 arrival */
     int32_t evaluated, accepted, n_before, pad;
     double dll, log_alpha;
 } orc_trace;
@@ -77,6 +85,12 @@ double orc_log_likelihood(const orc_world* w, const double* ev, int64_t n);
 /* V at station j for samples [k0, k1) under event set ev (definition). */
 void orc_variance(const orc_world* w, const double* ev, int64_t n, int32_t j,
                   int64_t k0, int64_t k1, double* out);
+/* The same with latent arrival offsets: off is a dense [n][n_st] array of
+ * the events' offsets (entries of stations an event does not reach are
+ * ignored; NULL: all 0).  The prior adds log N(delta; 0, sig_a^2) for every
+ * (event, reached station) when sig_a > 0. */
+double orc_log_prior_off(const orc_world* w, const double* ev, const double* off, int64_t n);
+double orc_log_likelihood_off(const orc_world* w, const double* ev, const double* off, int64_t n);
 /* Log-likelihood change when event old_idx of ev is removed (-1: none) and
  * cand is added (NULL: none). */
 double orc_delta_loglik(const orc_world* w, const double* ev, int64_t n,
@@ -105,6 +119,19 @@ double orc_log_alpha(const orc_world* w, double sx, double sy, int32_t cell,
 double orc_log_alpha_pair(const orc_world* w, double sx, double sy, int32_t cell,
                           const double* ev, int64_t n, int64_t i, int64_t j,
                           const double* cand1, const double* cand2, int32_t* valid);
+
+/* log acceptance ratio of one explicit proposal with latent offsets: as
+ * orc_log_alpha for types 0-2 (off, cand_off: dense offsets of the events
+ * and of the candidate, NULL = 0), and type 4, the arrival-time move of the
+ * idx-th event of the region at station `station` to the offset cand_off[0]. */
+double orc_log_alpha_off(const orc_world* w, double sx, double sy, int32_t cell,
+                         const double* ev, const double* off, int64_t n, int32_t type, int64_t idx,
+                         int32_t station, const double* cand, const double* cand_off, int32_t* valid);
+/* event sets with their latent offsets (dense [n][n_st], NULL = 0): the set
+ * keeps the offsets of the stations each event reaches */
+orc_set* orc_set_new_w(const orc_world* w, const double* ev, const uint64_t* ids, const double* off,
+                       int64_t n);
+void orc_set_offsets(const orc_world* w, const orc_set* s, double* off);
 
 /* samplers; return 0 on success */
 int orc_run_serial(const orc_world* w, orc_set* s, int64_t step0, int64_t n_steps,

@@ -14,7 +14,10 @@ oracle.c); the test asserts that the pin meant to catch it fails:
           the learned window;
   7 (the joint move of a pair drops the prior ratio) -> detailed balance of
           the kernels with joint moves on (and magnitude drift in
-          test_oracle_pair.py).
+          test_oracle_pair.py);
+  8, 9 (the arrival-time move without its prior ratio; offsets of newly
+          reached stations set to 0) -> offsets leave their prior in chains
+          on signals without information (test_oracle_arrivals.py).
 """
 import math
 

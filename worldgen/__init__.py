@@ -90,6 +90,9 @@ class World:
     signals: np.ndarray           # [n_st, n_samples] float32 | float64
     events: np.ndarray            # [n, 4] float64 ground truth
     seed: int = 0
+    # latent arrival offsets of the ground truth, dense [n, n_st] (0 where an
+    # event does not reach a station); None: deterministic arrivals
+    offsets: Optional[np.ndarray] = None
 
     @property
     def n_stations(self) -> int:
@@ -135,7 +138,7 @@ def sample_events(p: ModelParams, seed: int) -> np.ndarray:
 
 
 def _station_row(p: ModelParams, st: np.ndarray, events: np.ndarray, j: int,
-                 seed: int, dtype) -> np.ndarray:
+                 seed: int, dtype, offsets: Optional[np.ndarray] = None) -> np.ndarray:
     """One station's record: background noise plus, per arrival, a Gaussian
     signal of that envelope (variance reading) or the envelope itself (mean
     reading)."""
@@ -152,6 +155,8 @@ def _station_row(p: ModelParams, st: np.ndarray, events: np.ndarray, j: int,
     nw = p.n_w
     for i in np.nonzero(dist < p.R_max)[0]:
         arrival = events[i, 2] + dist[i] / p.v
+        if offsets is not None:
+            arrival += offsets[i, j]
         k0 = math.ceil(arrival * p.f_hz)
         lo, hi = max(k0, 0), min(k0 + nw, ns)
         if lo >= hi:
@@ -166,15 +171,30 @@ def _station_row(p: ModelParams, st: np.ndarray, events: np.ndarray, j: int,
     return row
 
 
+def sample_offsets(p: ModelParams, stations: np.ndarray, events: np.ndarray, seed: int,
+                   sig_a: float) -> np.ndarray:
+    """Latent arrival offsets (§Event Detections: the arrival is Gaussian
+    around t + d/v): N(0, sig_a^2) for every (event, station within R_max),
+    0 elsewhere, dense [n, n_st]."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 0xA771])))
+    off = rng.normal(0.0, sig_a, size=(events.shape[0], stations.shape[0]))
+    if events.shape[0]:
+        d = np.hypot(events[:, None, 0] - stations[None, :, 0], events[:, None, 1] - stations[None, :, 1])
+        off[d >= p.R_max] = 0.0
+    return off
+
+
 def sample_signals(p: ModelParams, stations: np.ndarray, events: np.ndarray, seed: int,
-                   dtype=np.float64, threads: Optional[int] = None) -> np.ndarray:
-    """Signals [n_st, n_samples]; each station has its own seeded stream."""
+                   dtype=np.float64, threads: Optional[int] = None,
+                   offsets: Optional[np.ndarray] = None) -> np.ndarray:
+    """Signals [n_st, n_samples]; each station has its own seeded stream;
+    ``offsets`` (dense [n, n_st]) shifts each arrival."""
     dtype = np.dtype(dtype).type
     n_st = stations.shape[0]
     out = np.empty((n_st, p.n_samples), dtype=dtype)
 
     def fill(j):
-        out[j] = _station_row(p, stations[j], events, j, seed, dtype)
+        out[j] = _station_row(p, stations[j], events, j, seed, dtype, offsets)
 
     threads = threads or min(16, os.cpu_count() or 1)
     if n_st * p.n_samples < 4_000_000 or threads <= 1:
@@ -187,12 +207,17 @@ def sample_signals(p: ModelParams, stations: np.ndarray, events: np.ndarray, see
 
 
 def make_world(p: ModelParams, stations: np.ndarray, seed: int, dtype=np.float64,
-               events: Optional[np.ndarray] = None) -> World:
+               events: Optional[np.ndarray] = None, sig_a: float = 0.0,
+               offsets: Optional[np.ndarray] = None) -> World:
+    """A seeded world; with ``sig_a`` > 0 (or explicit ``offsets``) the
+    arrivals carry latent Gaussian offsets, returned in ``World.offsets``."""
     if events is None:
         events = sample_events(p, seed)
-    sig = sample_signals(p, stations, events, seed, dtype)
-    return World(params=p, stations=np.ascontiguousarray(stations, dtype=np.float64),
-                 signals=sig, events=events, seed=seed)
+    stations = np.ascontiguousarray(stations, dtype=np.float64)
+    if offsets is None and sig_a > 0.0:
+        offsets = sample_offsets(p, stations, events, seed, sig_a)
+    sig = sample_signals(p, stations, events, seed, dtype, offsets=offsets)
+    return World(params=p, stations=stations, signals=sig, events=events, seed=seed, offsets=offsets)
 
 
 def subworld(world: World, x0: float, x1: float, y0: float, y1: float) -> World:

@@ -100,6 +100,17 @@ typedef struct {
                               perpendicular bisector), else both shift by one common Gaussian
                               offset of the move's scales.  0 (the default) turns it off;
                               p_birth + p_death + p_pair <= 1 */
+    /* CMH_F64 only: latent arrival times (§Generative Model, Event Detections: the
+     * arrival is Gaussian around t + d/v).  sig_a > 0 gives every (event, station it
+     * reaches) a latent offset delta ~ N(0, sig_a^2), the arrival being t + d/v +
+     * delta; births draw the offsets from that prior, a moved event keeps the offsets
+     * of the stations it still reaches and draws those of newly reached ones.  p_arr
+     * is the share of the arrival-time move (§MH moves: one offset of one event moved
+     * by a Gaussian of scale sig_da); it follows p_pair in the mix
+     * (p_birth + p_death + p_pair + p_arr <= 1).  sig_a = 0 (the default): arrivals
+     * are deterministic and p_arr must be 0.  Offsets start at 0 unless set by
+     * cmh_set_arrival_offsets. */
+    double sig_a, p_arr, sig_da;
 } cmh_params;
 
 /* region grid: squares of side L anchored at the origin, shifted by (sx, sy) */
@@ -120,11 +131,13 @@ typedef struct {
     int64_t spill_bytes;    /* float32 regions too large for shared memory: bytes of the global
                                slot per CTA holding their arrival caches and lists (0: none) */
     uint64_t pair[3];       /* joint moves of a pair (p_pair): proposed, evaluated, accepted */
+    uint64_t arrival[3];    /* arrival-time moves (p_arr): proposed, evaluated, accepted */
 } cmh_stats;
 
 /* one record per MH step (optional, cmh_set_trace) */
 typedef struct {
-    int32_t sweep, cell, step, type;   /* type: 0 birth, 1 death, 2 move, 3 joint move of a pair */
+    int32_t sweep, cell, step, type;   /* type: 0 birth, 1 death, 2 move, 3 joint move of a pair,
+                                          4 arrival-time move */
     int32_t evaluated, accepted, n_before, written;
     double dll;        /* log-likelihood change of the proposal (0 if not evaluated) */
     double log_alpha;  /* log acceptance ratio (-inf if not evaluated) */
@@ -188,6 +201,25 @@ int cmh_run_sweeps(cmh_model* m, int64_t n);
  */
 int cmh_read_state(cmh_model* m, cmh_event* out, uint64_t* ids_out, int64_t cap,
                    int64_t* n_out, double* log_density_out, cmh_stats* stats_out);
+
+/*
+ * Latent arrival offsets (sig_a > 0; §Generative Model, Event Detections).
+ * cmh_set_arrival_offsets: before the first cmh_partition_and_color, set the
+ *   offsets of the initial events: off [n_events][n_stations] host array,
+ *   row i for the i-th event given to cmh_create_model, column j for station
+ *   j; entries of stations an event does not reach (distance >= R_max) are
+ *   ignored and read back as 0.  The predicted variance and the running
+ *   log-density (whose prior then includes log N(delta; 0, sig_a^2) per
+ *   offset) are recomputed.
+ * cmh_read_arrival_offsets: synchronise and copy the current events' offsets
+ *   out, rows in cmh_read_state's order: out [cap][n_stations] (may be NULL
+ *   when cap == 0); *n_out receives the number of events.
+ * Errors: CMH_ERR_ARG (null pointers, sizes that do not match the model,
+ * non-finite offsets, or a model without latent arrivals), CMH_ERR_STATE
+ * (set after partitioning, or an error is latched), CMH_ERR_CUDA.
+ */
+int cmh_set_arrival_offsets(cmh_model* m, const double* off, int64_t n_events, int32_t n_stations);
+int cmh_read_arrival_offsets(cmh_model* m, double* out, int64_t cap, int64_t* n_out);
 
 /*
  * Asynchronous state reads (two slots), so that a caller can read every

@@ -42,7 +42,8 @@ class Params(C.Structure):
         ("k_per_phase", C.c_int32), ("commit", C.c_int32), ("seed", C.c_uint64), ("dtype", C.c_int32),
         ("ev_capacity", C.c_int32), ("frozen_capacity", C.c_int32), ("block_threads", C.c_int32),
         ("stage_samples", C.c_int32), ("schedule", C.c_int32), ("ctas_per_sm", C.c_int32),
-        ("likelihood", C.c_int32), ("max_events", C.c_int64), ("p_pair", C.c_double)]
+        ("likelihood", C.c_int32), ("max_events", C.c_int64), ("p_pair", C.c_double),
+        ("sig_a", C.c_double), ("p_arr", C.c_double), ("sig_da", C.c_double)]
 
 
 class Tuning(C.Structure):
@@ -67,7 +68,7 @@ class Stats(C.Structure):
                 ("sweeps", C.c_int64), ("n_events", C.c_int64), ("phase_ms", C.c_double),
                 ("phase_launches", C.c_int64), ("kernel_launches", C.c_int64),
                 ("priced_samples", C.c_uint64), ("rewritten_samples", C.c_uint64), ("spill_bytes", C.c_int64),
-                ("pair", C.c_uint64 * 3)]
+                ("pair", C.c_uint64 * 3), ("arrival", C.c_uint64 * 3)]
 
     def as_dict(self):
         return {"proposed": list(self.proposed), "evaluated": list(self.evaluated),
@@ -75,7 +76,7 @@ class Stats(C.Structure):
                 "phase_ms": self.phase_ms, "phase_launches": self.phase_launches,
                 "kernel_launches": self.kernel_launches, "priced_samples": self.priced_samples,
                 "rewritten_samples": self.rewritten_samples, "spill_bytes": self.spill_bytes,
-                "pair": list(self.pair)}
+                "pair": list(self.pair), "arrival": list(self.arrival)}
 
 
 TRACE_DTYPE = np.dtype([("sweep", "<i4"), ("cell", "<i4"), ("step", "<i4"), ("type", "<i4"),
@@ -89,7 +90,8 @@ EXPORTS = ["cmh_create_model", "cmh_partition_and_color", "cmh_run_sweeps", "cmh
            "cmh_gaussian_loglik_noalloc", "cmh_batch_create", "cmh_batch_run_sweeps", "cmh_batch_destroy",
            "cmh_autotune", "cmh_batch_sync", "cmh_batch_groups", "cmh_set_birth_table", "cmh_set_birth_magnitude",
            "cmh_net_param_count", "cmh_net_create", "cmh_net_destroy", "cmh_net_get_params", "cmh_net_set_params",
-           "cmh_net_forward", "cmh_net_gradients", "cmh_net_train", "cmh_net_birth_table"]
+           "cmh_net_forward", "cmh_net_gradients", "cmh_net_train", "cmh_net_birth_table",
+           "cmh_set_arrival_offsets", "cmh_read_arrival_offsets"]
 
 
 def _load():
@@ -106,6 +108,8 @@ def _load():
         "cmh_run_sweeps": (C.c_int, [P, i64]),
         "cmh_read_state_async": (C.c_int, [P, i32]),
         "cmh_read_state_fetch": (C.c_int, [P, i32, P, P, i64, C.POINTER(i64), C.POINTER(C.c_double), P]),
+        "cmh_set_arrival_offsets": (C.c_int, [P, P, i64, i32]),
+        "cmh_read_arrival_offsets": (C.c_int, [P, P, i64, C.POINTER(i64)]),
         "cmh_read_state": (C.c_int, [P, P, P, i64, C.POINTER(i64), C.POINTER(C.c_double),
                                      C.POINTER(Stats)]),
         "cmh_sync": (C.c_int, [P]),
@@ -164,9 +168,11 @@ def _ptr(a):
 def make_params(model_params, *, k_per_phase=32, seed=1, dtype=F64, p_birth=0.25, p_death=0.25,
                 sig_xy=5.0, sig_t=2.0, sig_m=0.1, commit=True, ev_capacity=0, frozen_capacity=0,
                 block_threads=0, stage_samples=0, schedule=0, ctas_per_sm=0, max_events=0,
-                p_pair=0.0) -> Params:
+                p_pair=0.0, sig_a=0.0, p_arr=0.0, sig_da=1.0) -> Params:
     """cmh_params from an object with the model fields (e.g. worldgen.ModelParams).
-    ``p_pair`` > 0 turns on the joint move of a pair of events (float64 only)."""
+    ``p_pair`` > 0 turns on the joint move of a pair of events; ``sig_a`` > 0
+    makes arrival times latent and ``p_arr`` the share of the arrival-time
+    move of step ``sig_da`` (all float64 only)."""
     p = Params()
     for n in ("W", "T", "Lambda", "v", "alpha", "beta_att", "tau", "t_s", "noise_var", "f_hz", "R_max"):
         setattr(p, n, float(getattr(model_params, n)))
@@ -185,6 +191,7 @@ def make_params(model_params, *, k_per_phase=32, seed=1, dtype=F64, p_birth=0.25
     p.likelihood = 1 if getattr(model_params, "likelihood", "variance") == "mean" else 0
     p.max_events = max_events
     p.p_pair = p_pair
+    p.sig_a, p.p_arr, p.sig_da = sig_a, p_arr, sig_da
     return p
 
 
@@ -265,6 +272,24 @@ class Model:
         self._last_n = n.value
         k = min(cap, n.value)
         return ev[:k], ids[:k], lp.value, st.as_dict()
+
+    def set_arrival_offsets(self, off):
+        """cmh_set_arrival_offsets: latent arrival offsets [n_events, n_stations]
+        of the initial events (before partition_and_color)."""
+        off = np.ascontiguousarray(off, dtype=np.float64)
+        if off.ndim != 2:
+            raise ValueError("offsets must be [n_events, n_stations]")
+        _check(lib.cmh_set_arrival_offsets(self._h, _ptr(off), off.shape[0], off.shape[1]),
+               "cmh_set_arrival_offsets")
+
+    def read_arrival_offsets(self, n_stations: int):
+        """cmh_read_arrival_offsets: [n, n_stations] offsets of the current
+        events, rows in read_state's order (0 where an event does not reach)."""
+        n = C.c_int64()
+        _check(lib.cmh_read_arrival_offsets(self._h, None, 0, C.byref(n)), "cmh_read_arrival_offsets")
+        out = np.zeros((n.value, n_stations), dtype=np.float64)
+        _check(lib.cmh_read_arrival_offsets(self._h, _ptr(out), n.value, C.byref(n)), "cmh_read_arrival_offsets")
+        return out
 
     def read_state_async(self, slot: int):
         """cmh_read_state_async: enqueue a copy of the state into slot 0 or 1."""

@@ -25,7 +25,7 @@ using namespace cmh;
 namespace {
 
 constexpr uint64_t kCkptMagic = 0x31484d4f52484343ULL;  // "CCHROMH1"
-constexpr int kCkptVersion = 2;
+constexpr int kCkptVersion = 3;
 
 int cuda_err(cudaError_t e) {
     if (e == cudaSuccess) return CMH_OK;
@@ -71,6 +71,7 @@ struct cmh_model {
     std::vector<void*> part_allocs;   // freed when re-partitioned
     FlatList flat{};
     long long flat_cap = 0;
+    double* off_lp = nullptr;         // latent arrival offsets: their log prior (device scalar)
     double* partial = nullptr;
     int n_partial = 0;
     bool partitioned = false;
@@ -202,10 +203,16 @@ int synth_and_logdensity(cmh_model* m, int n_flat, double* out) {
         CK(cudaMemcpyAsync(ht.data(), m->flat.t, sizeof(double) * n_flat, cudaMemcpyDeviceToHost, m->stream));
         CK(cudaMemcpyAsync(hm.data(), m->flat.m, sizeof(double) * n_flat, cudaMemcpyDeviceToHost, m->stream));
     }
+    double olp = 0.0;   // latent arrival offsets: sum of their log N(delta; 0, sig_a^2)
+    if (m->flat.off && m->g.n_st > 0) {
+        CK(launch_offset_prior(m->g, m->d, m->flat, m->off_lp, m->stream));
+        m->launches += 1;
+        CK(cudaMemcpyAsync(&olp, m->off_lp, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    }
     CK(cudaStreamSynchronize(m->stream));
     double ll = 0.0;
     for (double v : part) ll += v;
-    *out = host_log_prior(m->p, hx.data(), hy.data(), ht.data(), hm.data(), n_flat) + ll;
+    *out = host_log_prior(m->p, hx.data(), hy.data(), ht.data(), hm.data(), n_flat) + olp + ll;
     CK(cudaMemcpyAsync(m->d.logp, out, sizeof(double), cudaMemcpyHostToDevice, m->stream));
     CK(cudaStreamSynchronize(m->stream));
     return CMH_OK;
@@ -222,6 +229,12 @@ int validate_params(const cmh_params* p) {
     // joint moves of a pair: the float64 form only
     if (!(p->p_pair >= 0.0 && p->p_birth + p->p_death + p->p_pair <= 1.0)) return CMH_ERR_ARG;
     if (p->p_pair > 0.0 && p->dtype != CMH_F64) return CMH_ERR_ARG;
+    // latent arrival times and the arrival-time move: the float64 form only
+    if (!(std::isfinite(p->sig_a) && p->sig_a >= 0.0 && std::isfinite(p->p_arr) && p->p_arr >= 0.0))
+        return CMH_ERR_ARG;
+    if (!(p->p_birth + p->p_death + p->p_pair + p->p_arr <= 1.0)) return CMH_ERR_ARG;
+    if (p->p_arr > 0.0 && !(p->sig_a > 0.0 && finite_pos(p->sig_da))) return CMH_ERR_ARG;
+    if (p->sig_a > 0.0 && p->dtype != CMH_F64) return CMH_ERR_ARG;
     if (p->k_per_phase < 1 || p->k_per_phase > kMaxK) return CMH_ERR_ARG;
     if (p->dtype != CMH_F32 && p->dtype != CMH_F64) return CMH_ERR_ARG;
     if (p->likelihood != 0 && !(p->likelihood == 1 && p->dtype == CMH_F32)) return CMH_ERR_ARG;
@@ -247,6 +260,9 @@ int bin_flat_into_current(cmh_model* m, int n_flat) {
         CK(cudaMemcpyAsync(src.m, m->flat.m, sizeof(double) * n_flat, cudaMemcpyDeviceToDevice, m->stream));
         CK(cudaMemcpyAsync(src.id, m->flat.id, sizeof(unsigned long long) * n_flat, cudaMemcpyDeviceToDevice,
                            m->stream));
+        if (src.off && m->flat.off)
+            CK(cudaMemcpyAsync(src.off, m->flat.off, sizeof(double) * (size_t)n_flat * m->g.n_st,
+                               cudaMemcpyDeviceToDevice, m->stream));
     }
     int rc = upload_sweep(m, s + 1);
     if (rc) return rc;
@@ -310,6 +326,22 @@ int ensure_flat(cmh_model* m, long long cap, int n_keep) {
         cudaFree(x);
     }
     for (void* x : q) m->allocs.push_back(x);
+    if (m->flat.off) {   // latent arrival offsets: rows of n_st, the first n_keep kept
+        const size_t row = (size_t)std::max(m->g.n_st, 1);
+        double* no = nullptr;
+        e = cudaMalloc(&no, sizeof(double) * row * (size_t)cap);
+        if (e != cudaSuccess) return cuda_err(e);
+        m->allocs.push_back(no);
+        CK(cudaMemsetAsync(no, 0, sizeof(double) * row * (size_t)cap, m->stream));
+        if (n_keep)
+            CK(cudaMemcpyAsync(no, m->flat.off, sizeof(double) * row * (size_t)n_keep, cudaMemcpyDeviceToDevice,
+                               m->stream));
+        CK(cudaStreamSynchronize(m->stream));
+        auto it = std::find(m->allocs.begin(), m->allocs.end(), (void*)m->flat.off);
+        if (it != m->allocs.end()) m->allocs.erase(it);
+        cudaFree(m->flat.off);
+        nf.off = no;
+    }
     m->flat = nf;
     m->flat_cap = cap;
     return CMH_OK;
@@ -384,6 +416,9 @@ int cmh_create_model(const cmh_event* init_events, int64_t n_events, const cmh_s
     g.tau = p->tau; g.noise_var = p->noise_var; g.f_hz = p->f_hz; g.R_max = p->R_max;
     g.p_birth = p->p_birth; g.p_death = p->p_death; g.sig_xy = p->sig_xy; g.sig_t = p->sig_t; g.sig_m = p->sig_m;
     g.p_pair = p->p_pair;
+    g.sig_a = p->sig_a;
+    g.p_arr = p->p_arr;
+    g.sig_da = p->sig_da;
     g.log_pb = std::log(p->p_birth);
     g.log_pd = std::log(p->p_death);
     g.log_Lambda = std::log(p->Lambda);
@@ -465,6 +500,12 @@ int cmh_create_model(const cmh_event* init_events, int64_t n_events, const cmh_s
         (e = m->alloc(&m->flat.t, m->flat_cap)) || (e = m->alloc(&m->flat.m, m->flat_cap)) ||
         (e = m->alloc(&m->flat.id, m->flat_cap)) || (e = m->alloc(&m->flat.n, 1)))
         return fail(cuda_err(e));
+    if (g.sig_a > 0.0) {
+        // latent arrival offsets of the flat list, 0 to start with
+        const size_t cnt = (size_t)m->flat_cap * (size_t)std::max(n_stations, 1);
+        if ((e = m->alloc(&m->flat.off, cnt)) || (e = m->alloc(&m->off_lp, 1))) return fail(cuda_err(e));
+        if ((e = cudaMemsetAsync(m->flat.off, 0, sizeof(double) * cnt, m->stream))) return fail(cuda_err(e));
+    }
 
     std::vector<double> ln(g.ev_cap + 2);
     ln[0] = -INFINITY;
@@ -612,6 +653,12 @@ int cmh_partition_and_color(cmh_model* m, const cmh_grid* grid, int32_t shift_mo
             (e = m->alloc(&S.count, g.n_cells, true)) || (e = m->alloc(&S.cap, g.n_cells, true)) ||
             (e = m->alloc(&S.total, 1, true)))
             return cuda_err(e);
+        S.off = nullptr;
+        if (g.sig_a > 0.0) {   // latent arrival offsets, a row of n_st per store slot
+            const size_t cnt = (size_t)g.store_cap * (size_t)std::max(g.n_st, 1);
+            if ((e = m->alloc(&S.off, cnt, true))) return cuda_err(e);
+            CK(cudaMemsetAsync(S.off, 0, sizeof(double) * cnt, m->stream));
+        }
         CK(cudaMemsetAsync(S.count, 0, sizeof(int) * g.n_cells, m->stream));
         CK(cudaMemsetAsync(S.start, 0, sizeof(int) * g.n_cells, m->stream));
         CK(cudaMemsetAsync(S.total, 0, sizeof(int), m->stream));
@@ -775,7 +822,41 @@ int cmh_read_state(cmh_model* m, cmh_event* out, uint64_t* ids_out, int64_t cap,
         stats_out->rewritten_samples = st[10];
         stats_out->spill_bytes = m->partitioned && m->g.spill ? m->g.spill_bytes : 0;
         for (int i = 0; i < 3; ++i) stats_out->pair[i] = st[11 + i];
+        for (int i = 0; i < 3; ++i) stats_out->arrival[i] = st[14 + i];
     }
+    return CMH_OK;
+}
+
+int cmh_set_arrival_offsets(cmh_model* m, const double* off, int64_t n_events, int32_t n_stations) {
+    (void)cudaGetLastError();   // an earlier call's failed launch must not be reported here
+    if (!m || n_events < 0 || (n_events > 0 && n_stations > 0 && !off)) return CMH_ERR_ARG;
+    if (!m->flat.off || n_stations != m->g.n_st || n_events != m->n0) return CMH_ERR_ARG;
+    if (m->partitioned || m->latched) return CMH_ERR_STATE;
+    const size_t cnt = (size_t)n_events * (size_t)n_stations;
+    for (size_t q = 0; q < cnt; ++q)
+        if (!std::isfinite(off[q])) return CMH_ERR_ARG;
+    CK(cudaStreamSynchronize(m->stream));
+    if (cnt) CK(cudaMemcpy(m->flat.off, off, sizeof(double) * cnt, cudaMemcpyHostToDevice));
+    // V with the shifted arrivals, and the log-density with the offsets' prior
+    double lp = 0.0;
+    return synth_and_logdensity(m, (int)n_events, &lp);
+}
+
+int cmh_read_arrival_offsets(cmh_model* m, double* out, int64_t cap, int64_t* n_out) {
+    if (!m || cap < 0 || (cap > 0 && !out)) return CMH_ERR_ARG;
+    if (!m->flat.off) return CMH_ERR_ARG;
+    CK(cudaStreamSynchronize(m->stream));
+    int rc = check_status(m);
+    if (rc) return rc;
+    int n = (int)m->n0;
+    if (m->partitioned) {
+        rc = flatten_current(m, &n);
+        if (rc) return rc;
+    }
+    if (n_out) *n_out = n;
+    const int64_t nc = std::min<int64_t>(cap, n);
+    if (nc > 0 && m->g.n_st > 0)
+        CK(cudaMemcpy(out, m->flat.off, sizeof(double) * (size_t)nc * m->g.n_st, cudaMemcpyDeviceToHost));
     return CMH_OK;
 }
 
@@ -867,7 +948,8 @@ int cmh_checkpoint(cmh_model* m, void* buf, size_t* len) {
         rc = flatten_current(m, &n);
         if (rc) return rc;
     }
-    const size_t need = sizeof(CkptHeader) + (size_t)n * (4 * sizeof(double) + sizeof(uint64_t));
+    const size_t orow = m->flat.off ? sizeof(double) * (size_t)m->g.n_st : 0;   // latent offsets per event
+    const size_t need = sizeof(CkptHeader) + (size_t)n * (4 * sizeof(double) + sizeof(uint64_t) + orow);
     if (!buf) { *len = need; return CMH_OK; }
     if (*len < need) { *len = need; return CMH_ERR_ARG; }
     CkptHeader h;
@@ -894,7 +976,8 @@ int cmh_checkpoint(cmh_model* m, void* buf, size_t* len) {
         CK(cudaMemcpy(q, m->flat.y, sizeof(double) * n, cudaMemcpyDeviceToHost)); q += sizeof(double) * n;
         CK(cudaMemcpy(q, m->flat.t, sizeof(double) * n, cudaMemcpyDeviceToHost)); q += sizeof(double) * n;
         CK(cudaMemcpy(q, m->flat.m, sizeof(double) * n, cudaMemcpyDeviceToHost)); q += sizeof(double) * n;
-        CK(cudaMemcpy(q, m->flat.id, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(q, m->flat.id, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost)); q += sizeof(uint64_t) * n;
+        if (orow) CK(cudaMemcpy(q, m->flat.off, orow * n, cudaMemcpyDeviceToHost));
     }
     *len = need;
     return CMH_OK;
@@ -907,9 +990,10 @@ int cmh_restore(cmh_model* m, const void* buf, size_t len) {
     std::memcpy(&h, buf, sizeof(h));
     if (h.magic != kCkptMagic || h.version != kCkptVersion) return CMH_ERR_ARG;
     if (h.n_st != m->g.n_st || h.n_samp != m->g.n_samp || h.n_events < 0 || h.n_events > m->flat_cap ||
-        h.p.dtype != m->p.dtype || h.p.seed != m->p.seed)
+        h.p.dtype != m->p.dtype || h.p.seed != m->p.seed || (h.p.sig_a > 0.0) != (m->p.sig_a > 0.0))
         return CMH_ERR_ARG;
-    const size_t need = sizeof(CkptHeader) + (size_t)h.n_events * (4 * sizeof(double) + sizeof(uint64_t));
+    const size_t orow = m->flat.off ? sizeof(double) * (size_t)m->g.n_st : 0;
+    const size_t need = sizeof(CkptHeader) + (size_t)h.n_events * (4 * sizeof(double) + sizeof(uint64_t) + orow);
     if (len < need) return CMH_ERR_ARG;
     CK(cudaStreamSynchronize(m->stream));
     const int n = (int)h.n_events;
@@ -927,6 +1011,9 @@ int cmh_restore(cmh_model* m, const void* buf, size_t len) {
     CK(cudaMemcpy(m->flat.t, t, sizeof(double) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(m->flat.m, mm, sizeof(double) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(m->flat.id, mm + n, sizeof(uint64_t) * n, cudaMemcpyHostToDevice));
+    if (orow && n)
+        CK(cudaMemcpy(m->flat.off, (const unsigned char*)(mm + n) + sizeof(uint64_t) * n, orow * n,
+                      cudaMemcpyHostToDevice));
     CK(cudaMemcpy(m->flat.n, &n, sizeof(int), cudaMemcpyHostToDevice));
     double lp = 0.0;
     int rc = synth_and_logdensity(m, n, &lp);
@@ -1006,6 +1093,7 @@ int cmh_read_state_async(cmh_model* m, int32_t slot) {
     f.m = f.t + r.cap;
     f.id = (unsigned long long*)(dev + rs_off_id(r.cap));
     f.n = (int*)(dev + rs_off_n(r.cap));
+    f.off = nullptr;   // offsets are read by cmh_read_arrival_offsets
     int l = 0;
     CK(launch_flatten(m->g, m->d, cur_buf(m), f, m->stream, &l));
     CK(cudaMemcpyAsync(r.host + rs_off_logp(r.cap), m->d.logp, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
@@ -1060,6 +1148,7 @@ int cmh_read_state_fetch(cmh_model* m, int32_t slot, cmh_event* out, uint64_t* i
         stats_out->rewritten_samples = st[10];
         stats_out->spill_bytes = m->g.spill ? m->g.spill_bytes : 0;
         for (int i = 0; i < 3; ++i) stats_out->pair[i] = st[11 + i];
+        for (int i = 0; i < 3; ++i) stats_out->arrival[i] = st[14 + i];
     }
     r.pending = false;
     return CMH_OK;

@@ -20,14 +20,19 @@ namespace cmh {
 constexpr int kMaxColours = 16;
 constexpr int kMaxK = 4095;
 // proposed[3], evaluated[3], accepted[3], priced samples, rewritten samples,
-// joint moves of a pair: proposed, evaluated, accepted
-constexpr int kStats = 14;
+// joint moves of a pair: proposed, evaluated, accepted; arrival-time moves:
+// proposed, evaluated, accepted
+constexpr int kStats = 17;
 
 // model, partition and launch constants; passed by value to every kernel
 struct Geo {
     double W, T, Lambda, v, alpha, beta_att, tau, noise_var, f_hz, R_max, L;
     double p_birth, p_death, sig_xy, sig_t, sig_m;
     double p_pair;      // joint move of a pair of events (float64 form only)
+    // latent arrival times (float64 form only): offsets ~ N(0, sig_a^2) per
+    // (event, reached station) when sig_a > 0; the arrival-time move's share
+    // and step
+    double sig_a, p_arr, sig_da;
     // logs computed once on the host
     double log_pb, log_pd, log_Lambda, log_WWT, log_T;
     int n_w, k, commit, shift_mode;
@@ -84,6 +89,7 @@ struct Store {
     unsigned long long* id;
     int *start, *count, *cap;   // [n_cells]
     int* total;                 // number of events
+    double* off;                // latent arrival offsets [store_cap][n_st] (nullptr without them)
 };
 
 struct Dev {
@@ -290,6 +296,7 @@ struct FlatList {
     double *x, *y, *t, *m;
     unsigned long long* id;
     int* n;
+    double* off;                // [cap][n_st] latent arrival offsets, or nullptr (not copied)
 };
 
 // host-side launchers (defined in the .cu files)
@@ -325,6 +332,9 @@ cudaError_t launch_vsynth(const Geo& g, const Dev& d, const FlatList& f, cudaStr
 cudaError_t launch_flatten(const Geo& g, const Dev& d, int buf, const FlatList& f, cudaStream_t s, int* launches);
 cudaError_t prepare_kernels(const Geo& g);
 cudaError_t launch_loglik(const Geo& g, const Dev& d, double* partial, int n_part, cudaStream_t s);
+// latent arrival offsets of a flat list: zero the entries of stations an event
+// does not reach, and write sum log N(delta; 0, sig_a^2) over the others to *out
+cudaError_t launch_offset_prior(const Geo& g, const Dev& d, const FlatList& f, double* out, cudaStream_t s);
 cudaError_t launch_convert_signals(const void* src, int src_f32, long long src_pitch, void* dst,
                                    int dst_f32, long long dst_pitch, int n_st, long long n_samp,
                                    int* nonfinite, cudaStream_t s);

@@ -14,7 +14,8 @@
 //                 old cells around it (the two grids differ by less than one
 //                 cell side along each axis), by their new-cell index, and
 //                 writes them sorted by event id, the canonical order every
-//                 region uses.
+//                 region uses (with latent arrival times, each event's row
+//                 of offsets with it).
 // Only rebin_assign evaluates the cell index of a coordinate; the exact
 // float64 form of floor((x - s) / L) runs only when a float32 estimate lies
 // within 1e-3 of an integer.
@@ -253,6 +254,9 @@ __device__ __forceinline__ void rebin_gather_body(const Geo& g, const Dev& d, in
         nw.t[s0 + r] = old.t[src];
         nw.m[s0 + r] = old.m[src];
         nw.id[s0 + r] = me;
+        if (nw.off)   // latent arrival offsets travel with their event
+            for (int j = 0; j < g.n_st; ++j)
+                nw.off[(size_t)(s0 + r) * g.n_st + j] = old.off[(size_t)src * g.n_st + j];
     }
 }
 

@@ -41,11 +41,11 @@ struct Arr {            // an arrival in a list (frozen neighbours, others of a 
 };
 
 struct Draw {           // state-independent part of one MH step
-    double a[4];        // birth: candidate (x, y, t, m); move, pair: signed offsets
+    double a[4];        // birth: candidate (x, y, t, m); move, pair: signed offsets; arrival: a[0] the step
     double logu;        // log of the accept uniform, (0, 1]
     unsigned pickw;     // low word for the event pick
     unsigned pickw2;    // joint move: low word for the second event's pick
-    int type;           // 0 birth, 1 death, 2 move, 3 joint move of a pair
+    int type;           // 0 birth, 1 death, 2 move, 3 joint move of a pair, 4 arrival-time move
     int bvalid;         // birth candidate inside region, time and magnitude range
     int sub;            // joint move: 0 exchange of locations, 1 common offset
     int pad;
@@ -64,7 +64,7 @@ struct Task {           // one station whose variance the proposal changes
 // shared-memory layout of the phase kernel (host computes the size)
 struct Layout {
     size_t ev_x, ev_y, ev_t, ev_m, ev_id, ev_narr, ev_arr, order, freel;
-    size_t b_sta, b_x, b_y, f_cnt, f_arr, draws, cand, tasks, pool, total;
+    size_t b_sta, b_x, b_y, f_cnt, f_arr, draws, cand, tasks, pool, eoff, coff, total;
     int task_cap;       // a task per distinct blanket slot of the changed arrivals
     int pool_cap;
     __host__ __device__ Layout(const Geo& g) {
@@ -92,19 +92,48 @@ struct Layout {
         cand = take(sizeof(EvArr) * 2 * g.arr_cap);   // the candidate's arrivals; a pair's second at arr_cap
         tasks = take(sizeof(Task) * task_cap);
         pool = take(sizeof(Arr) * (size_t)pool_cap);
+        // latent arrival offsets by blanket slot: own events' [ev_cap][blk_cap],
+        // the candidates' [2][blk_cap] (0 where not reached)
+        const size_t lat = g.sig_a > 0.0 ? 1 : 0;
+        eoff = take(sizeof(double) * (size_t)g.ev_cap * g.blk_cap * lat);
+        coff = take(sizeof(double) * 2 * (size_t)g.blk_cap * lat);
         total = o;
     }
 };
 
+// arrival of an event at a station: a = t + d/v, plus the latent offset
+// delta of that (event, station) when arrivals are latent (sig_a > 0)
 __device__ __forceinline__ bool arrival(const Geo& g, double x, double y, double t, double m, double xs,
-                                        double ys, int& k0, double& af, double& lnA2) {
+                                        double ys, int& k0, double& af, double& lnA2, double delta = 0.0) {
     const double dd = dist_rn(x, y, xs, ys);
     if (!(dd < g.R_max)) return false;
-    const double a = __dadd_rn(t, __ddiv_rn(dd, g.v));
+    double a = __dadd_rn(t, __ddiv_rn(dd, g.v));
+    if (g.sig_a > 0.0) a = __dadd_rn(a, delta);
     af = __dmul_rn(a, g.f_hz);
     k0 = (int)ceil(af);
     lnA2 = 2.0 * (g.alpha * m - g.beta_att * dd);
     return true;
+}
+
+// latent offset drawn from its prior N(0, sig_a^2) for station j and the
+// step's e-th changed event: Philox stream 0 at counter (sweep, cell, step,
+// 16 + 2 j + e), a Box-Muller cosine from words 0 and 1 rounded to 2^-20
+// (as the walk offsets), the sign from bit 0 of word 2
+__device__ __noinline__ double draw_offset(const Geo& g, long long sweep, int cell, int step, int j, int e) {
+    unsigned long long c[4] = {(unsigned long long)sweep, (unsigned long long)cell, (unsigned long long)step,
+                               16ULL + 2ULL * (unsigned long long)j + (unsigned long long)e};
+    philox4x64(c, g.seed, 0ULL);
+    const double r = __dsqrt_rn(__dmul_rn(-2.0, log(u01o(c[0]))));
+    const double th = __dmul_rn(6.283185307179586, u01(c[1]));
+    double z = __dmul_rn(rint(__dmul_rn(fabs(__dmul_rn(r, cos(th))), 1048576.0)), 1.0 / 1048576.0);
+    if (c[2] & 1ULL) z = -z;
+    return __dmul_rn(g.sig_a, z);
+}
+
+// log N(v; 0, sig_a^2)
+__device__ __forceinline__ double log_off_prior1(const Geo& g, double v) {
+    const double s2 = __dmul_rn(g.sig_a, g.sig_a);
+    return __dsub_rn(__dmul_rn(-0.5, log(__dmul_rn(2.0 * M_PI, s2))), __ddiv_rn(__dmul_rn(v, v), __dmul_rn(2.0, s2)));
 }
 
 // variance added at sample k by an arrival (float64 form)
@@ -192,12 +221,15 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
     EvArr* cand = (EvArr*)(smem + Lo.cand);
     Task* tasks = (Task*)(smem + Lo.tasks);
     Arr* pool = (Arr*)(smem + Lo.pool);
+    double* eoff = (double*)(smem + Lo.eoff);
+    double* coff = (double*)(smem + Lo.coff);
+    const bool lat = g.sig_a > 0.0;   // latent arrival offsets
 
     __shared__ double s_rect[4];
     __shared__ double s_log_area, s_dll, s_region_dlp;
     __shared__ double s_c[4], s_c2[4];
     __shared__ int s_n_own, s_n_free, s_n_blk, s_err, s_valid, s_idx, s_type, s_ncand, s_ntask, s_acc;
-    __shared__ int s_idx2, s_ncand2;
+    __shared__ int s_idx2, s_ncand2, s_aslot;
     __shared__ int s_warp[32], s_base;
     __shared__ double s_redd[32];
 
@@ -262,13 +294,23 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
         __syncthreads();
     }
     const int n_blk = s_n_blk;
+    // own events' latent offsets by blanket slot (every station an own event
+    // reaches is in the blanket)
+    if (lat) {
+        for (int q = tid; q < n0 * n_blk; q += nthr) {
+            const int i = q / n_blk, b = q - i * n_blk;
+            eoff[i * g.blk_cap + b] = S.off[(size_t)(start + i) * g.n_st + bsta[b]];
+        }
+        __syncthreads();
+    }
     // arrival cache of the own events
     for (int i = tid; i < n0; i += nthr) {
         int na = 0;
         for (int b = 0; b < n_blk; ++b) {
             int k0;
             double af, lnA2;
-            if (arrival(g, ex[i], ey[i], et[i], em[i], bx[b], by[b], k0, af, lnA2)) {
+            if (arrival(g, ex[i], ey[i], et[i], em[i], bx[b], by[b], k0, af, lnA2,
+                        lat ? eoff[i * g.blk_cap + b] : 0.0)) {
                 if (na < g.arr_cap) {
                     EvArr& A = earr[i * g.arr_cap + na];
                     A.slot = b; A.k0 = k0; A.af = af; A.lnA2 = lnA2;
@@ -294,7 +336,8 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
                 for (int i = 0; i < n; ++i) {
                     int k0;
                     double af, lnA2;
-                    if (arrival(g, S.x[s0 + i], S.y[s0 + i], S.t[s0 + i], S.m[s0 + i], bx[b], by[b], k0, af, lnA2)) {
+                    if (arrival(g, S.x[s0 + i], S.y[s0 + i], S.t[s0 + i], S.m[s0 + i], bx[b], by[b], k0, af, lnA2,
+                                lat ? S.off[(size_t)(s0 + i) * g.n_st + bsta[b]] : 0.0)) {
                         if (nf < g.frz_cap) {
                             Arr& A = farr[b * g.frz_cap + nf];
                             A.k0 = k0; A.af = af; A.lnA2 = lnA2;
@@ -318,7 +361,8 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
         Draw D;
         const double u = u01(w[0]);
         const double cd = __dadd_rn(g.p_birth, g.p_death), cp = __dadd_rn(cd, g.p_pair);
-        D.type = u < g.p_birth ? 0 : (u < cd ? 1 : (u < cp ? 3 : 2));
+        const double ca = __dadd_rn(cp, g.p_arr);
+        D.type = u < g.p_birth ? 0 : (u < cd ? 1 : (u < cp ? 3 : (u < ca ? 4 : 2)));
         D.pickw = (unsigned)(w[1] & 0xffffffffULL);
         D.pickw2 = (unsigned)(w[7] & 0xffffffffULL);
         D.sub = (int)((w[1] >> 36) & 1ULL);
@@ -332,14 +376,15 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
             D.a[0] = x; D.a[1] = y; D.a[2] = t; D.a[3] = m;
             D.bvalid = x >= 0.0 && x < g.W && y >= 0.0 && y < g.W && cell_of(g, sx, sy, x, y) == cell &&
                        t >= 0.0 && t < g.T && m >= 2.0;
-        } else if (D.type == 2 || D.type == 3) {
+        } else if (D.type == 2 || D.type == 3 || D.type == 4) {
             const double r1 = __dsqrt_rn(__dmul_rn(-2.0, log(u01o(w[2]))));
             const double th1 = __dmul_rn(6.283185307179586, u01(w[3]));
             const double r2 = __dsqrt_rn(__dmul_rn(-2.0, log(u01o(w[4]))));
             const double th2 = __dmul_rn(6.283185307179586, u01(w[5]));
             double z[4] = {__dmul_rn(r1, cos(th1)), __dmul_rn(r1, sin(th1)), __dmul_rn(r2, cos(th2)),
                            __dmul_rn(r2, sin(th2))};
-            const double sig[4] = {g.sig_xy, g.sig_xy, g.sig_t, g.sig_m};
+            // the arrival-time move steps its offset by sig_da times the first Gaussian
+            const double sig[4] = {D.type == 4 ? g.sig_da : g.sig_xy, g.sig_xy, g.sig_t, g.sig_m};
             for (int i = 0; i < 4; ++i) {
                 double q = __dmul_rn(rint(__dmul_rn(fabs(z[i]), 1048576.0)), 1.0 / 1048576.0);
                 if ((w[1] >> (32 + i)) & 1ULL) q = -q;
@@ -356,7 +401,7 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
         return;
     }
 
-    unsigned long long n_prop[4] = {0, 0, 0, 0}, n_eval[4] = {0, 0, 0, 0}, n_acc[4] = {0, 0, 0, 0};
+    unsigned long long n_prop[5] = {0, 0, 0, 0, 0}, n_eval[5] = {0, 0, 0, 0, 0}, n_acc[5] = {0, 0, 0, 0, 0};
     unsigned long long n_priced = 0, n_rewritten = 0;   // sample terms (thread 0's tally)
 
     for (int step = 0; step < g.k; ++step) {
@@ -364,7 +409,7 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
         if (wid == 0) {
             const Draw dr = draws[step];
             const int n_own = s_n_own;
-            int valid = 0, idx = -1, ncand = 0, idx2 = -1, ncand2 = 0;
+            int valid = 0, idx = -1, ncand = 0, idx2 = -1, ncand2 = 0, aslot = -1;
             double cx = 0.0, cy = 0.0, ct = 0.0, cm = 0.0;
             double cx2 = 0.0, cy2 = 0.0, ct2 = 0.0, cm2 = 0.0;   // joint move: the second event
             if (dr.type == 0) {
@@ -397,6 +442,19 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
                             cx2 >= 0.0 && cx2 < g.W && cy2 >= 0.0 && cy2 < g.W &&
                             cell_of(g, sx, sy, cx2, cy2) == cell && ct2 >= 0.0 && ct2 < g.T && cm2 >= 2.0;
                 }
+            } else if (dr.type == 4) {
+                // arrival-time move: one of the stations an event reaches
+                // (its arrival list is in station order), its offset stepped
+                if (n_own > 0) {
+                    idx = pick32(dr.pickw, n_own);
+                    const int ps = order[idx];
+                    const int na = enarr[ps];
+                    if (na > 0) {
+                        aslot = earr[ps * g.arr_cap + pick32(dr.pickw2, na)].slot;
+                        cx = ex[ps]; cy = ey[ps]; ct = et[ps]; cm = em[ps];
+                        valid = 1;
+                    }
+                }
             } else if (n_own > 0) {
                 idx = pick32(dr.pickw, n_own);
                 if (dr.type == 1) {
@@ -411,12 +469,31 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
                             cell_of(g, sx, sy, cx, cy) == cell && ct >= 0.0 && ct < g.T && cm >= 2.0;
                 }
             }
+            // latent offset of candidate e at blanket slot b (0 where it does not
+            // reach): kept from the event it replaces where that one reached b,
+            // else drawn from the prior
+            auto cand_offset = [&](int e, int old_ps, double x, double y, int b) -> double {
+                if (!(dist_rn(x, y, bx[b], by[b]) < g.R_max)) return 0.0;
+                if (old_ps >= 0 && dist_rn(ex[old_ps], ey[old_ps], bx[b], by[b]) < g.R_max)
+                    return eoff[old_ps * g.blk_cap + b];
+                return draw_offset(g, sweep, cell, step, bsta[b], e);
+            };
             if (valid && dr.type != 1) {
+                const int old1 = dr.type == 0 ? -1 : order[idx];
                 for (int b0 = 0; b0 < n_blk; b0 += 32) {
                     const int b = b0 + lane;
                     int k0 = 0;
-                    double af = 0.0, lnA2 = 0.0;
-                    const bool r = b < n_blk && arrival(g, cx, cy, ct, cm, bx[b], by[b], k0, af, lnA2);
+                    double af = 0.0, lnA2 = 0.0, dl = 0.0;
+                    if (lat && b < n_blk) {
+                        if (dr.type == 4) {
+                            dl = eoff[old1 * g.blk_cap + b];
+                            if (b == aslot) dl = __dadd_rn(dl, dr.a[0]);
+                        } else {
+                            dl = cand_offset(0, old1, cx, cy, b);
+                        }
+                        coff[b] = dl;
+                    }
+                    const bool r = b < n_blk && arrival(g, cx, cy, ct, cm, bx[b], by[b], k0, af, lnA2, dl);
                     const unsigned bal = __ballot_sync(FULL, r);
                     const int pos = ncand + __popc(bal & ((1u << lane) - 1));
                     if (r && pos < g.arr_cap) {
@@ -428,11 +505,16 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
             }
             if (valid && dr.type == 3) {
                 EvArr* cand2 = cand + g.arr_cap;
+                const int old2 = order[idx2];
                 for (int b0 = 0; b0 < n_blk; b0 += 32) {
                     const int b = b0 + lane;
                     int k0 = 0;
-                    double af = 0.0, lnA2 = 0.0;
-                    const bool r = b < n_blk && arrival(g, cx2, cy2, ct2, cm2, bx[b], by[b], k0, af, lnA2);
+                    double af = 0.0, lnA2 = 0.0, dl = 0.0;
+                    if (lat && b < n_blk) {
+                        dl = cand_offset(1, old2, cx2, cy2, b);
+                        coff[g.blk_cap + b] = dl;
+                    }
+                    const bool r = b < n_blk && arrival(g, cx2, cy2, ct2, cm2, bx[b], by[b], k0, af, lnA2, dl);
                     const unsigned bal = __ballot_sync(FULL, r);
                     const int pos = ncand2 + __popc(bal & ((1u << lane) - 1));
                     if (r && pos < g.arr_cap) {
@@ -576,6 +658,7 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
                 s_valid = valid;
                 s_idx = idx;
                 s_idx2 = idx2;
+                s_aslot = aslot;
                 s_type = dr.type;
                 s_ncand = ncand;
                 s_ncand2 = ncand2;
@@ -712,6 +795,12 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
                     const double lq = -s_log_area - g.log_T - (me - 2.0);
                     dlp = -lb;
                     la = dll + dlp + lq + g.log_pb - g.log_pd + d.log_n[n_own];
+                } else if (type == 4) {
+                    // symmetric step of one offset: its prior ratio
+                    const double a = eoff[order[s_idx] * g.blk_cap + s_aslot], b = coff[s_aslot];
+                    const double s2 = __dmul_rn(g.sig_a, g.sig_a);
+                    dlp = __ddiv_rn(__dsub_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(2.0, s2));
+                    la = dll + dlp;
                 } else if (type == 3) {
                     // symmetric proposal: the prior ratio of the two events
                     const double me1 = em[order[s_idx]], me2 = em[order[s_idx2]];
@@ -743,7 +832,31 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
             if (do_commit) {
                 ++n_acc[type];
                 for (int ti = 0; ti < s_ntask; ++ti) n_rewritten += (unsigned long long)(tasks[ti].hi - tasks[ti].lo);
-                s_region_dlp += dll + dlp;
+                // latent offsets drawn from (or dropped to) their prior cancel
+                // from the ratio but still change the log-density
+                double dlo = 0.0;
+                if (lat) {
+                    auto rowsum = [&](const double* row, const EvArr* L, int n) {
+                        double t = 0.0;
+                        for (int a = 0; a < n; ++a) t += log_off_prior1(g, row[L[a].slot]);
+                        return t;
+                    };
+                    const int p1 = s_idx >= 0 ? order[s_idx] : -1;
+                    if (type == 0) {
+                        dlo = rowsum(coff, cand, s_ncand);
+                    } else if (type == 1) {
+                        dlo = -rowsum(eoff + p1 * g.blk_cap, earr + p1 * g.arr_cap, enarr[p1]);
+                    } else if (type == 2) {
+                        dlo = rowsum(coff, cand, s_ncand) - rowsum(eoff + p1 * g.blk_cap, earr + p1 * g.arr_cap, enarr[p1]);
+                    } else if (type == 3) {
+                        const int p2 = order[s_idx2];
+                        dlo = (rowsum(coff, cand, s_ncand) -
+                               rowsum(eoff + p1 * g.blk_cap, earr + p1 * g.arr_cap, enarr[p1])) +
+                              (rowsum(coff + g.blk_cap, cand + g.arr_cap, s_ncand2) -
+                               rowsum(eoff + p2 * g.blk_cap, earr + p2 * g.arr_cap, enarr[p2]));
+                    }
+                }
+                s_region_dlp += dll + dlp + dlo;
                 if (type == 0) {
                     const int ps = freel[--s_n_free];
                     ex[ps] = s_c[0]; ey[ps] = s_c[1]; et[ps] = s_c[2]; em[ps] = s_c[3];
@@ -751,6 +864,8 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
                               (unsigned long long)step;
                     for (int a = 0; a < s_ncand; ++a) earr[ps * g.arr_cap + a] = cand[a];
                     enarr[ps] = s_ncand;
+                    if (lat)
+                        for (int b = 0; b < n_blk; ++b) eoff[ps * g.blk_cap + b] = coff[b];
                     order[n_own] = ps;
                     s_n_own = n_own + 1;
                 } else if (type == 1) {
@@ -763,11 +878,15 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
                     ex[ps] = s_c[0]; ey[ps] = s_c[1]; et[ps] = s_c[2]; em[ps] = s_c[3];
                     for (int a = 0; a < s_ncand; ++a) earr[ps * g.arr_cap + a] = cand[a];
                     enarr[ps] = s_ncand;
+                    if (lat)
+                        for (int b = 0; b < n_blk; ++b) eoff[ps * g.blk_cap + b] = coff[b];
                     if (type == 3) {
                         const int p2 = order[s_idx2];
                         ex[p2] = s_c2[0]; ey[p2] = s_c2[1]; et[p2] = s_c2[2]; em[p2] = s_c2[3];
                         for (int a = 0; a < s_ncand2; ++a) earr[p2 * g.arr_cap + a] = cand[g.arr_cap + a];
                         enarr[p2] = s_ncand2;
+                        if (lat)
+                            for (int b = 0; b < n_blk; ++b) eoff[p2 * g.blk_cap + b] = coff[g.blk_cap + b];
                     }
                 }
             } else if (acc) {
@@ -823,6 +942,15 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
         S.m[start + i] = em[ps];
         S.id[start + i] = eid[ps];
     }
+    if (lat) {
+        // offsets rows of the written events: 0 but at the blanket stations
+        for (int q = tid; q < n_fin * g.n_st; q += nthr) S.off[(size_t)start * g.n_st + q] = 0.0;
+        __syncthreads();
+        for (int q = tid; q < n_fin * n_blk; q += nthr) {
+            const int i = q / n_blk, b = q - i * n_blk;
+            S.off[(size_t)(start + i) * g.n_st + bsta[b]] = eoff[order[i] * g.blk_cap + b];
+        }
+    }
     if (tid == 0) {
         S.count[cell] = n_fin;
         d.region_dlp[cell] = s_region_dlp;
@@ -834,6 +962,9 @@ __global__ void __launch_bounds__(512, 1) phase_kernel(Geo g, Dev d, int colour)
         if (n_prop[3]) atomicAdd(&d.stats[11], n_prop[3]);
         if (n_eval[3]) atomicAdd(&d.stats[12], n_eval[3]);
         if (n_acc[3]) atomicAdd(&d.stats[13], n_acc[3]);
+        if (n_prop[4]) atomicAdd(&d.stats[14], n_prop[4]);
+        if (n_eval[4]) atomicAdd(&d.stats[15], n_eval[4]);
+        if (n_acc[4]) atomicAdd(&d.stats[16], n_acc[4]);
         if (n_priced) atomicAdd(&d.stats[9], n_priced);
         if (n_rewritten) atomicAdd(&d.stats[10], n_rewritten);
     }
@@ -877,7 +1008,8 @@ constexpr int kSynthTile = kSynthThreads * 8;
 
 template <bool F32>
 __global__ void __launch_bounds__(kSynthThreads) vsynth_kernel(Geo g, Dev d, const double* fx, const double* fy,
-                                                               const double* ft, const double* fm, const int* n_ptr) {
+                                                               const double* ft, const double* fm, const int* n_ptr,
+                                                               const double* foff) {
     const int j = blockIdx.x;
     const int n = *n_ptr;
     const double xs = d.stx[j], ys = d.sty[j];
@@ -904,7 +1036,8 @@ __global__ void __launch_bounds__(kSynthThreads) vsynth_kernel(Geo g, Dev d, con
                     event_terms32(g, ft[idx], fm[idx], K, ph, mf);
                     r = arrival32c(g, fx[idx], fy[idx], ft[idx], K, ph, mf, xs, ys, k0, E0);
                 } else {
-                    r = arrival(g, fx[idx], fy[idx], ft[idx], fm[idx], xs, ys, k0, af, ln);
+                    r = arrival(g, fx[idx], fy[idx], ft[idx], fm[idx], xs, ys, k0, af, ln,
+                                foff ? foff[(size_t)idx * g.n_st + j] : 0.0);
                 }
             }
             if (threadIdx.x == 0) s_cnt = 0;
@@ -998,7 +1131,7 @@ __global__ void __launch_bounds__(1024) flatten_scan(Geo g, Dev d, int buf, int*
 }
 
 __global__ void __launch_bounds__(256) flatten_copy(Geo g, Dev d, int buf, double* fx, double* fy, double* ft,
-                                                    double* fm, unsigned long long* fid) {
+                                                    double* fm, unsigned long long* fid, double* foff) {
     const Store S = d.st[buf];
     const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (c >= g.n_cells) return;
@@ -1010,6 +1143,32 @@ __global__ void __launch_bounds__(256) flatten_copy(Geo g, Dev d, int buf, doubl
         fm[off + i] = S.m[s0 + i];
         fid[off + i] = S.id[s0 + i];
     }
+    if (foff && S.off)   // latent arrival offsets: the cell's rows, lanes over entries
+        for (long long q = lane; q < (long long)n * g.n_st; q += 32)
+            foff[(size_t)off * g.n_st + q] = S.off[(size_t)s0 * g.n_st + q];
+}
+
+// latent arrival offsets of a flat list: entries of stations an event does
+// not reach are set to 0; the others' log N(delta; 0, sig_a^2) summed in a
+// fixed order (thread-strided, then a tree) into *out.  One block.
+__global__ void __launch_bounds__(256) offprior_kernel(Geo g, Dev d, const double* fx, const double* fy,
+                                                       double* foff, const int* n_ptr, double* out) {
+    __shared__ double s_part[256];
+    const long long tot = (long long)(*n_ptr) * g.n_st;
+    double acc = 0.0;
+    for (long long q = threadIdx.x; q < tot; q += blockDim.x) {
+        const long long i = q / g.n_st;
+        const int j = (int)(q - i * g.n_st);
+        if (dist_rn(fx[i], fy[i], d.stx[j], d.sty[j]) < g.R_max) acc += log_off_prior1(g, foff[q]);
+        else foff[q] = 0.0;
+    }
+    s_part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s_part[threadIdx.x] += s_part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s_part[0];
 }
 
 // sum over all stations and samples of log N(s; 0, V) (or, with the additive
@@ -1097,15 +1256,15 @@ cudaError_t launch_sweep_end(const Geo& g, const Dev& d, cudaStream_t s) {
 
 cudaError_t launch_vsynth(const Geo& g, const Dev& d, const FlatList& f, cudaStream_t s, int* launches) {
     if (g.n_st == 0) return cudaSuccess;
-    if (g.f32) vsynth_kernel<true><<<g.n_st, kSynthThreads, 0, s>>>(g, d, f.x, f.y, f.t, f.m, f.n);
-    else vsynth_kernel<false><<<g.n_st, kSynthThreads, 0, s>>>(g, d, f.x, f.y, f.t, f.m, f.n);
+    if (g.f32) vsynth_kernel<true><<<g.n_st, kSynthThreads, 0, s>>>(g, d, f.x, f.y, f.t, f.m, f.n, nullptr);
+    else vsynth_kernel<false><<<g.n_st, kSynthThreads, 0, s>>>(g, d, f.x, f.y, f.t, f.m, f.n, f.off);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_flatten(const Geo& g, const Dev& d, int buf, const FlatList& f, cudaStream_t s, int* launches) {
     flatten_scan<<<1, 1024, 0, s>>>(g, d, buf, f.n);
-    flatten_copy<<<(g.n_cells + 7) / 8, 256, 0, s>>>(g, d, buf, f.x, f.y, f.t, f.m, f.id);
+    flatten_copy<<<(g.n_cells + 7) / 8, 256, 0, s>>>(g, d, buf, f.x, f.y, f.t, f.m, f.id, f.off);
     if (launches) *launches += 2;
     return cudaGetLastError();
 }
@@ -1113,6 +1272,11 @@ cudaError_t launch_flatten(const Geo& g, const Dev& d, int buf, const FlatList& 
 cudaError_t prepare_kernels(const Geo& g) {
     const size_t smem = phase_smem_bytes(g);
     return raise_smem_limit((const void*)phase_kernel, smem);
+}
+
+cudaError_t launch_offset_prior(const Geo& g, const Dev& d, const FlatList& f, double* out, cudaStream_t s) {
+    offprior_kernel<<<1, 256, 0, s>>>(g, d, f.x, f.y, f.off, f.n, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_loglik(const Geo& g, const Dev& d, double* partial, int n_part, cudaStream_t s) {

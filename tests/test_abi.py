@@ -57,6 +57,11 @@ def _params(cm, **kw):
     dict(p_pair=-0.1),
     dict(p_pair=0.6),              # p_birth + p_death + p_pair > 1
     dict(p_pair=0.2, dtype=1),     # the joint move is float64 only
+    dict(sig_a=-1.0),
+    dict(sig_a=2.0, dtype=1),      # latent arrival times are float64 only
+    dict(p_arr=0.1),               # the arrival-time move needs latent arrivals
+    dict(sig_a=2.0, p_arr=0.1, sig_da=0.0),
+    dict(sig_a=2.0, p_pair=0.3, p_arr=0.3),   # p_birth + p_death + p_pair + p_arr > 1
 ])
 def test_create_model_rejects_bad_params_on_host(cm, bad):
     lik = bad.pop("likelihood", None)
@@ -103,6 +108,9 @@ def test_null_handles(cm):
     assert cm.lib.cmh_batch_create(arr, 1, None, C.byref(h)) == -1 and not h.value
     assert cm.lib.cmh_batch_run_sweeps(None, 1) == -1
     cm.lib.cmh_batch_destroy(None)
+    n = C.c_int64()
+    assert cm.lib.cmh_set_arrival_offsets(None, None, 0, 0) == -1
+    assert cm.lib.cmh_read_arrival_offsets(None, None, 0, C.byref(n)) == -1
 
 
 def test_null_handles_of_the_learned_proposal_and_async_reads(cm):

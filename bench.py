@@ -73,19 +73,23 @@ def _traffic():
 
 
 def n_proposals(st) -> int:
-    """Every MH proposal a model made: birth, death, move and joint pair moves."""
-    return int(sum(st["proposed"]) + st["pair"][0])
+    """Every MH proposal a model made: birth, death, move, joint pair and
+    arrival-time moves."""
+    return int(sum(st["proposed"]) + st["pair"][0] + st["arrival"][0])
 
 
-def _workload(name: str, likelihood: str = "variance", p_pair: float = 0.0):
+def _workload(name: str, likelihood: str = "variance", p_pair: float = 0.0, sig_a: float = 0.0,
+              p_arr: float = 0.0):
     if name == "scale":
         return worldgen.config_scale(seed=SEED, likelihood=likelihood), \
             "fp32 sweep at scale: 4000x4000 km, 24 h, ~1e4 events, 1600 stations x 864000 f32 samples, " \
             "40x40 regions, k=32" + ("" if likelihood == "variance" else ", additive-mean likelihood reading")
     if name == "replay":
-        return worldgen.config_replay(seed=SEED), "fp64 replay: 1000x1000 km, 1 h, ~500 events, " \
-                                                  "100 stations x 36000 f64 samples, 10x10 regions, k=32" + (
-                                                      ", joint pair moves p_pair=%g" % p_pair if p_pair else "")
+        return worldgen.config_replay(seed=SEED, sig_a=sig_a), \
+            "fp64 replay: 1000x1000 km, 1 h, ~500 events, 100 stations x 36000 f64 samples, 10x10 regions, " \
+            "k=32" + (", joint pair moves p_pair=%g" % p_pair if p_pair else "") + (
+                ", latent arrival times sig_a=%g s (offsets of the generated world), arrival-time moves "
+                "p_arr=%g" % (sig_a, p_arr) if sig_a else "")
     raise SystemExit("unknown workload " + name)
 
 
@@ -141,7 +145,8 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _cpu_baseline(world, seconds_target: float = 15.0, p_pair: float = 0.0):
+def _cpu_baseline(world, seconds_target: float = 15.0, p_pair: float = 0.0, sig_a: float = 0.0,
+                  p_arr: float = 0.0, sig_da: float = 1.0):
     """The oracle's chromatic sampler on a 1000 x 1000 km corner of the world
     (same station density, event intensity and record length)."""
     import oracle
@@ -152,13 +157,16 @@ def _cpu_baseline(world, seconds_target: float = 15.0, p_pair: float = 0.0):
     p = worldgen.ModelParams(**{**world.params.__dict__, "W": sub_side, "Lambda": world.params.Lambda * frac})
     sub.params = p
     threads = os.cpu_count() or 1
-    o = oracle.World(sub, k_per_phase=K_PER_PHASE, seed=CHAIN_SEED, p_pair=p_pair)
+    o = oracle.World(sub, k_per_phase=K_PER_PHASE, seed=CHAIN_SEED, p_pair=p_pair, sig_a=sig_a, p_arr=p_arr,
+                     sig_da=sig_da)
     ev = sub.events
     ids = None
+    off = sub.offsets if sig_a else None
     t0 = time.perf_counter()
     props, sweeps = 0, 0
     while True:
-        ev, ids, tr, _ = o.run_chromatic(ev, 1, ids=ids, sweep0=sweeps, trace_cap=200000, threads=threads)
+        ev, ids, tr, _ = o.run_chromatic(ev, 1, ids=ids, sweep0=sweeps, trace_cap=200000, threads=threads, off=off)
+        off = o.last_offsets if sig_a else None
         props += len(tr)
         sweeps += 1
         if time.perf_counter() - t0 > seconds_target:
@@ -175,8 +183,9 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    world, desc = _workload(args.workload, args.likelihood, args.p_pair)
-    base = _cpu_baseline(world, seconds_target=max(5.0, 3.0 * args.steps / 10.0), p_pair=args.p_pair)
+    world, desc = _workload(args.workload, args.likelihood, args.p_pair, args.sig_a, args.p_arr)
+    base = _cpu_baseline(world, seconds_target=max(5.0, 3.0 * args.steps / 10.0), p_pair=args.p_pair,
+                         sig_a=args.sig_a, p_arr=args.p_arr, sig_da=args.sig_da)
     line = {"impl": "reference", "metric": "MH proposals/sec and sweeps/sec on 1 GB300",
             "value": base["value"], "unit": "proposals/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -218,13 +227,14 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_1612_00595_gb300 as cm
 
-    world, desc = _workload(args.workload, args.likelihood, args.p_pair)
+    world, desc = _workload(args.workload, args.likelihood, args.p_pair, args.sig_a, args.p_arr)
     p = world.params
     f32 = world.signals.dtype == np.float32
     dtype = cm.F32 if f32 else cm.F64
     esz = 4 if f32 else 8
     # each rank runs an independent chain (weak scaling: fixed work per GPU)
-    params = cm.make_params(p, k_per_phase=K_PER_PHASE, seed=chain_seed(rank), dtype=dtype, p_pair=args.p_pair)
+    params = cm.make_params(p, k_per_phase=K_PER_PHASE, seed=chain_seed(rank), dtype=dtype, p_pair=args.p_pair,
+                            sig_a=args.sig_a, p_arr=args.p_arr, sig_da=args.sig_da)
     stream = torch.cuda.Stream()
     sig_dev = torch.from_numpy(world.signals).to("cuda", non_blocking=False)
     torch.cuda.synchronize()
@@ -236,6 +246,8 @@ def run_ours(args):
 
     # ---------------- device-resident throughput ----------------
     m = cm.create_model(world.events, world.stations, sig_dev, params, stream=stream)
+    if args.sig_a:
+        m.set_arrival_offsets(world.offsets)
     m.partition_and_color(p.L, shift_mode=1)
     m.run_sweeps(args.warmup)
     m.sync()
@@ -296,6 +308,8 @@ def run_ours(args):
     barrier()
     t0 = time.perf_counter()
     m2 = cm.create_model(world.events, world.stations, host_sig, params, stream=stream)
+    if args.sig_a:
+        m2.set_arrival_offsets(world.offsets)
     m2.partition_and_color(p.L, shift_mode=1)
     d2h = 0
     # every sweep's state is read: requested right after the sweep into one of
@@ -318,7 +332,8 @@ def run_ours(args):
     h2d_per_step = world.signals.nbytes / args.steps
 
     if rank == 0:
-        cpu = _cpu_baseline(world, p_pair=args.p_pair) if world_size == 1 else None
+        cpu = _cpu_baseline(world, p_pair=args.p_pair, sig_a=args.sig_a, p_arr=args.p_arr,
+                            sig_da=args.sig_da) if world_size == 1 else None
         line = {"metric": "MH proposals/sec and sweeps/sec on 1 GB300", "value": value, "unit": "proposals/s",
                 "sweeps_per_s": sweeps_per_s, "n_gpus": world_size, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -560,9 +575,13 @@ def main():
                     help="scale workload: arrivals add to the sample variance (default) or to its mean")
     ap.add_argument("--p-pair", type=float, default=0.0,
                     help="replay workload: share of steps that propose the joint move of a pair of events")
+    ap.add_argument("--sig-a", type=float, default=0.0,
+                    help="replay workload: latent arrival times with offsets ~ N(0, sig_a^2) seconds")
+    ap.add_argument("--p-arr", type=float, default=0.0, help="replay workload: share of arrival-time moves")
+    ap.add_argument("--sig-da", type=float, default=1.0, help="step of the arrival-time move, seconds")
     args = ap.parse_args()
-    if args.p_pair and args.workload != "replay":
-        raise SystemExit("--p-pair needs the float64 replay workload")
+    if (args.p_pair or args.sig_a or args.p_arr) and args.workload != "replay":
+        raise SystemExit("--p-pair, --sig-a and --p-arr need the float64 replay workload")
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":

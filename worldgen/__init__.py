@@ -230,8 +230,9 @@ def subworld(world: World, x0: float, x1: float, y0: float, y1: float) -> World:
     keep = (st[:, 0] >= x0) & (st[:, 0] < x1) & (st[:, 1] >= y0) & (st[:, 1] < y1)
     ev = world.events
     kev = (ev[:, 0] >= x0) & (ev[:, 0] < x1) & (ev[:, 1] >= y0) & (ev[:, 1] < y1)
+    off = None if world.offsets is None else world.offsets[kev][:, keep].copy()
     return World(params=world.params, stations=st[keep].copy(),
-                 signals=world.signals[keep], events=ev[kev].copy(), seed=world.seed)
+                 signals=world.signals[keep], events=ev[kev].copy(), seed=world.seed, offsets=off)
 
 
 # --------------------------------------------------------------------------
@@ -243,10 +244,11 @@ def config_tiny(seed: int = 1000) -> World:
     return make_world(p, grid_stations(2, p.W), seed, np.float64)
 
 
-def config_replay(seed: int = 1000) -> World:
-    """1000 x 1000 km, 3600 s, Lambda = 500, 100 jittered stations, 36000 f64 samples."""
+def config_replay(seed: int = 1000, sig_a: float = 0.0) -> World:
+    """1000 x 1000 km, 3600 s, Lambda = 500, 100 jittered stations, 36000 f64
+    samples; with sig_a > 0 the arrivals carry latent Gaussian offsets."""
     p = ModelParams(W=1000.0, T=3600.0, Lambda=500.0)
-    return make_world(p, jittered_grid_stations(10, p.W, seed), seed, np.float64)
+    return make_world(p, jittered_grid_stations(10, p.W, seed), seed, np.float64, sig_a=sig_a)
 
 
 def config_learned(seed: int = 1000) -> World:

@@ -51,3 +51,18 @@ def test_single_rank_reduction_is_the_identity():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.reduce_max_sum(3.0, 7.0) == (3.0, 7.0)
+
+
+def test_cpu_legs_run_every_move_of_the_replay_workload():
+    """The oracle leg of bench.py (cpu_baseline, and the reference arm) on the
+    replay workload with joint pair moves and latent arrival times: it runs
+    and counts every proposal type."""
+    sys.path.insert(0, ROOT)
+    import bench
+    world, desc = bench._workload("replay", "variance", 0.1, 2.0, 0.2)
+    assert "p_pair=0.1" in desc and "sig_a=2" in desc
+    assert world.offsets is not None and (world.offsets != 0).any()
+    base = bench._cpu_baseline(world, seconds_target=0.3, p_pair=0.1, sig_a=2.0, p_arr=0.2)
+    assert base["kind"] == "oracle" and base["value"] > 0 and base["sweeps"] >= 1
+    st = {"proposed": [5, 6, 7], "pair": [2, 1, 0], "arrival": [3, 3, 1]}
+    assert bench.n_proposals(st) == 23

@@ -173,7 +173,7 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
 }
 
 // ordered append across the block: returns the position of this thread's
-// element among the flagged ones of this round; *total (shared) is advanced
+// element among the flagged ones of this pass; *total (shared) is advanced
 __device__ __forceinline__ int block_append(bool flag, int* s_warp, int* s_base) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const unsigned bal = __ballot_sync(FULL, flag);

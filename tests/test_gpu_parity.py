@@ -57,6 +57,26 @@ def test_replay_small_bit_exact(cm, orc, init, shift_mode):
     m.destroy()
 
 
+@pytest.mark.parametrize("seed,init", [(1000, "empty"), (1001, "empty"), (1002, "empty"), (1000, "truth")])
+def test_tiny_config_bit_exact(cm, orc, seed, init):
+    """The small configuration (200 x 200 km, 600 s, Lambda 10, 4 stations on a
+    2 x 2 grid, 6000 float64 samples, regions of side 100 km, 4 colours) at
+    k = 500 steps per region and phase: 18,000 MH steps over 4 sweeps, step
+    for step against the oracle.  A region may hold its events plus k births,
+    hence the event capacity of 640."""
+    w = worldgen.config_tiny(seed=seed)
+    ev0 = w.events if init == "truth" else None
+    m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=4, k=500, seed=seed, events=ev0, ev_capacity=640)
+    o, oev, oids, otr, odlp = run_oracle(orc, w, sweeps=4, k=500, seed=seed, events=ev0)
+    assert len(tr) >= 10000
+    assert_traces_match(tr, otr)
+    assert np.array_equal(ids, oids)
+    assert np.array_equal(ev[:, :3], oev[:, :3])
+    lp0 = o.log_density(w.events if init == "truth" else np.zeros((0, 4)))
+    assert logp == pytest.approx(lp0 + odlp, rel=1e-11)
+    m.destroy()
+
+
 def test_replay_shift_matches_oracle(cm, orc):
     w = small_world(seed=8)
     params = cm.make_params(w.params, k_per_phase=4, seed=99, dtype=cm.F64)

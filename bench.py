@@ -172,11 +172,27 @@ def _cpu_baseline(world, seconds_target: float = 15.0, p_pair: float = 0.0, sig_
         if time.perf_counter() - t0 > seconds_target:
             break
     dt = time.perf_counter() - t0
+    # the serial sampler (Algorithm "Serial Metropolis Hastings") on one core,
+    # same corner and start, for a third of the time (at most 5 s)
+    o1 = oracle.World(sub, k_per_phase=K_PER_PHASE, seed=CHAIN_SEED, p_pair=p_pair, sig_a=sig_a, p_arr=p_arr,
+                      sig_da=sig_da)
+    ev1, ids1, off1 = sub.events, None, (sub.offsets if sig_a else None)
+    t1 = time.perf_counter()
+    steps1 = 0
+    while True:
+        ev1, ids1, _, _ = o1.run_serial(ev1, 1000, ids=ids1, step0=steps1, off=off1)
+        off1 = o1.last_offsets if sig_a else None
+        steps1 += 1000
+        if time.perf_counter() - t1 > min(seconds_target / 3.0, 5.0):
+            break
+    dt1 = time.perf_counter() - t1
     return {"value": props / dt, "unit": "proposals/s", "cores": threads, "kind": "oracle",
             "sample": "%d sweeps of the oracle's chromatic sampler (OpenMP over same-colour regions) on a "
                       "1000x1000 km corner of the same world (100 stations x %d samples, ~%d events), "
                       "started from the ground truth" % (sweeps, world.params.n_samples, len(sub.events)),
-            "sweeps": sweeps, "proposals": props, "seconds": dt}
+            "sweeps": sweeps, "proposals": props, "seconds": dt,
+            "serial": {"value": steps1 / dt1, "unit": "proposals/s", "cores": 1, "steps": steps1, "seconds": dt1,
+                       "sample": "the oracle's serial sampler on the same corner and start, one core"}}
 
 
 def run_reference(args):

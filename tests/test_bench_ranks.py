@@ -64,5 +64,6 @@ def test_cpu_legs_run_every_move_of_the_replay_workload():
     assert world.offsets is not None and (world.offsets != 0).any()
     base = bench._cpu_baseline(world, seconds_target=0.3, p_pair=0.1, sig_a=2.0, p_arr=0.2)
     assert base["kind"] == "oracle" and base["value"] > 0 and base["sweeps"] >= 1
+    assert base["serial"]["cores"] == 1 and base["serial"]["value"] > 0 and base["serial"]["steps"] >= 1000
     st = {"proposed": [5, 6, 7], "pair": [2, 1, 0], "arrival": [3, 3, 1]}
     assert bench.n_proposals(st) == 23

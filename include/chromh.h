@@ -2,10 +2,10 @@
  * chromh -- chromatic Metropolis-Hastings with dynamic spatial partitioning
  * for the toy seismic event model, on one GB300 (sm_103a).
  *
- * The calls follow the paper's statement of the inference problem (Song &
- * Moore, "Parallel Chromatic MCMC with Spatial Partitioning", §Generative
- * Model of Seismic Signals: "recover the number of events, and their
- * space-time positions, given noisy observed signals"):
+ * The calls follow the paper's inference problem (Song & Moore, "Parallel
+ * Chromatic MCMC with Spatial Partitioning", §Generative Model of Seismic
+ * Signals): from the noisy signals recorded at the stations, infer how many
+ * events there were and where and when each happened:
  *   cmh_create_model         events, stations, signals -> model
  *   cmh_partition_and_color  region grid + boundary shift (§Partitioning the
  *                            World; §Chromatic MH with Dynamic Coloring)
@@ -20,6 +20,10 @@
  *   at sample k (time k / f_hz, k in [ceil(a f), ceil(a f) + t_s f)) the
  *   station's variance grows by (exp(alpha m - beta_att d) exp(-(k/f - a)/tau))^2;
  *   each sample s ~ N(0, noise_var + sum of those variances).
+ * Options (cmh_params): the additive reading (likelihood = 1: arrivals add
+ * the enveloped amplitude to the sample's mean, float32), latent arrival
+ * times (sig_a > 0: a = t + d / v + delta, delta ~ N(0, sig_a^2) per event and
+ * reached station, float64) and the joint move of a pair (p_pair, float64).
  *
  * Conventions for every call:
  *   - return 0 (CMH_OK) or a negative CMH_ERR_* code; nothing throws across

@@ -5,9 +5,9 @@ It only *samples* worlds, in the order the generative model states them
 (§Generative Model of Seismic Signals): a Poisson number of events with uniform
 space-time locations, arrival at each station after the travel time, an iid
 Gaussian signal per arrival whose standard deviation follows the event's
-amplitude envelope, and iid Gaussian background noise added on top
-(§Experimental Results: "synthetic data generated by sampling from the model's
-distribution over possible worlds").  It evaluates no density, no proposal and
+amplitude envelope, and iid Gaussian background noise added on top; as in
+§Experimental Results, the evaluation worlds are draws from the model
+itself.  It evaluates no density, no proposal and
 no acceptance ratio; those belong to the oracle and to the CUDA path, which
 implement them independently.
 

@@ -464,9 +464,70 @@ double orc_log_prior(const orc_world* w, const double* ev, int64_t n) {
 /* ------------------------------------------------------------------------
  * log-likelihood change of one proposal: the event own[old_idx] (if any) is
  * replaced by cand (if any); context = own + oth.  Plain definition: for every
- * station and sample whose variance changes, the difference of the two
- * Gaussian log-densities, each variance summed from scratch.
+ * station and sample whose predicted value changes, the difference of the two
+ * Gaussian log-densities of the sample (§Generative Model, Observed Signals),
+ * the predicted values P (old) and P' (new) summed from scratch.
+ *
+ * The difference is written out term by term rather than as a subtraction of
+ * two log-densities.  Where a large signal is unexplained, s^2 / 2V is large
+ * (1e5 and more) at both P and P', and subtracting the two rounded terms loses
+ * digits the difference needs; written out, the two forms are equal:
+ *   variance reading:  log N(s; 0, P') - log N(s; 0, P)
+ *                        = -1/2 log(P'/P) + s^2 D / (2 P P')
+ *   mean reading:      log N(s; P', s2) - log N(s; P, s2)
+ *                        = D ((s - P) + (s - P')) / (2 s2)
+ * with D = P' - P the change of the changed events' own contributions
+ * (arr_change), not the difference of the two sums.
  * ---------------------------------------------------------------------- */
+
+/* is sample k inside the window of arrival r */
+static int covers(const orc_world* w, const arr_t* r, int64_t k) {
+    return r->reach && k >= r->k0 && k < r->k0 + w->p.n_w;
+}
+
+static double dist_to(const orc_world* w, const ev_t* e, int32_t j) {
+    double dx = e->x - w->st[2 * j];
+    double dy = e->y - w->st[2 * j + 1];
+    return sqrt(dx * dx + dy * dy);
+}
+
+/* change at sample k of station j of what one event adds to the predicted
+ * value when it goes from eo (arrival ao) to en (arrival an); either may be
+ * NULL (birth, death).  Where both windows cover k the two contributions are
+ * the same envelope shape, A e^{-u/tau} with A = e^{alpha m - beta d} and
+ * u = k/f - a (squared in the variance reading), so their ratio is the same
+ * at every such sample:
+ *   c_new / c_old = exp(q [alpha (m' - m) - beta (d' - d) + (a' - a) / tau]),
+ * q = 2 (variance) or 1 (mean).  The change is then c_old (e^E - 1), E taken
+ * from the coordinate changes: d' - d = (d'^2 - d^2) / (d' + d) with
+ * d'^2 - d^2 = (x' - x)(x' + x - 2 x_j) + (y' - y)(y' + y - 2 y_j), and
+ * a' - a = (t' - t) + (d' - d) / v plus the change of the offset at j with
+ * latent arrivals.  A small move then subtracts no two nearly equal numbers. */
+static double arr_change(const orc_world* w, const ev_t* eo, const arr_t* ao, const ev_t* en,
+                         const arr_t* an, int32_t j, int64_t k) {
+    const int io = eo && covers(w, ao, k), in = en && covers(w, an, k);
+    if (!io && !in) return 0.0;
+    if (!io) return arr_var(w, an, k);
+    if (!in) return -arr_var(w, ao, k);
+    const double xj = w->st[2 * j], yj = w->st[2 * j + 1];
+    const double d_o = dist_to(w, eo, j), d_n = dist_to(w, en, j);
+    const double dsq = (en->x - eo->x) * (en->x + eo->x - 2.0 * xj) +
+                       (en->y - eo->y) * (en->y + eo->y - 2.0 * yj);
+    const double dd = d_n + d_o > 0.0 ? dsq / (d_n + d_o) : 0.0;
+    double da = (en->t - eo->t) + dd / w->p.v;
+    if (w->p.sig_a > 0.0) da += offset_at(en, j) - offset_at(eo, j);
+    const double q = (w->p.likelihood || ORC_MUTANT == 3) ? 1.0 : 2.0;   /* the power arr_var takes */
+    const double E = q * (w->p.alpha * (en->m - eo->m) - w->p.beta_att * dd + da / w->p.tau);
+    return arr_var(w, ao, k) * expm1(E);
+}
+
+/* the difference of the two log-densities of sample s, written out as above */
+static double delta_sample(const orc_world* w, double s, double P_old, double P_new, double D) {
+    if (w->p.likelihood)
+        return D * ((s - P_old) + (s - P_new)) / (2.0 * w->p.noise_var);
+    return -0.5 * log(P_new / P_old) + s * s * D / (2.0 * P_old * P_new);
+}
+
 static double delta_ll2(const orc_world* w, const ev_t* own, int64_t n_own, const ev_t* oth,
                         int64_t n_oth, int64_t old_idx, const ev_t* cand) {
     double total = 0.0;
@@ -498,8 +559,11 @@ static double delta_ll2(const orc_world* w, const ev_t* own, int64_t n_own, cons
             for (int64_t i = 0; i < na; ++i) base += arr_var(w, &ar[i], k);
             double V_old = base + arr_var(w, &ao, k);
             double V_new = base + arr_var(w, &an, k);
-            double s = sig_at(w, j, k);
-            total += log_lik_sample(w, s, V_new) - log_lik_sample(w, s, V_old);
+            double D = arr_change(w, old_idx >= 0 ? &own[old_idx] : NULL, &ao, cand, &an, j, k);
+            if (ORC_MUTANT == 10)
+                total += log_lik_sample(w, sig_at(w, j, k), V_new) - log_lik_sample(w, sig_at(w, j, k), V_old);
+            else
+                total += delta_sample(w, sig_at(w, j, k), V_old, V_new, D);
         }
     }
     free(ar);
@@ -519,8 +583,9 @@ double orc_delta_loglik(const orc_world* w, const double* ev, int64_t n,
 
 /* log-likelihood change of a joint move: own[i1] and own[i2] become c1 and
  * c2.  Same plain definition: at every station one of the four events
- * reaches, over the span of their windows, the two Gaussian log-densities
- * with each predicted value summed from scratch. */
+ * reaches, over the span of their windows, the difference of the two
+ * Gaussian log-densities written out as in delta_sample, D the sum of the two
+ * events' own changes. */
 static double delta_ll_pair(const orc_world* w, const ev_t* own, int64_t n_own, const ev_t* oth,
                             int64_t n_oth, int64_t i1, int64_t i2, const ev_t* c1, const ev_t* c2) {
     double total = 0.0;
@@ -557,8 +622,9 @@ static double delta_ll_pair(const orc_world* w, const ev_t* own, int64_t n_own, 
             for (int64_t i = 0; i < na; ++i) base += arr_var(w, &ar[i], k);
             double V_old = base + arr_var(w, &ch[0], k) + arr_var(w, &ch[1], k);
             double V_new = base + arr_var(w, &ch[2], k) + arr_var(w, &ch[3], k);
-            double s = sig_at(w, j, k);
-            total += log_lik_sample(w, s, V_new) - log_lik_sample(w, s, V_old);
+            double D = arr_change(w, &own[i1], &ch[0], c1, &ch[2], j, k) +
+                       arr_change(w, &own[i2], &ch[1], c2, &ch[3], j, k);
+            total += delta_sample(w, sig_at(w, j, k), V_old, V_new, D);
         }
     }
     free(ar);

@@ -58,8 +58,17 @@ def assert_traces_match(tr, otr, rtol=1e-9):
     bad = np.nonzero(tr["accepted"] != otr["accepted"])[0]
     assert len(bad) == 0, "accept decisions differ at %s" % bad[:5]
     ev = otr["evaluated"] == 1
+    # relative to max(|dll|, 1): a change below 1 in magnitude is a sum of
+    # per-sample terms of either sign, each of order 1 and rounded at that
+    # scale, so below 1 the bound is absolute; the pure relative error is
+    # printed beside it
     scale = np.maximum(np.abs(otr["dll"][ev]), 1.0)
     err = np.abs(tr["dll"][ev] - otr["dll"][ev]) / scale
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rel = np.abs(tr["dll"][ev] - otr["dll"][ev]) / np.abs(otr["dll"][ev])
+    rel = rel[np.isfinite(rel)]
+    print("dll: %d evaluated, max err %.3g (scale max(|x|,1)), max pure relative %.3g, %d with |dll| < 1"
+          % (int(ev.sum()), err.max(initial=0.0), rel.max(initial=0.0), int((np.abs(otr["dll"][ev]) < 1).sum())))
     assert err.max(initial=0.0) <= rtol, err.max()
     la_err = np.abs(tr["log_alpha"][ev] - otr["log_alpha"][ev]) / np.maximum(np.abs(otr["log_alpha"][ev]), 1.0)
     assert la_err.max(initial=0.0) <= rtol, la_err.max()

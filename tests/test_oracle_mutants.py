@@ -18,6 +18,9 @@ oracle.c); the test asserts that the pin meant to catch it fails:
   8, 9 (the arrival-time move without its prior ratio; offsets of newly
           reached stations set to 0) -> offsets leave their prior in chains
           on signals without information (test_oracle_arrivals.py).
+  10 (each sample's change priced as the difference of its two rounded
+          log-densities) -> the exact decimal evaluation of the definition
+          on an ill-conditioned case (test_oracle_precision.py).
 """
 import math
 

@@ -12,7 +12,11 @@
 // The per-row partial sums live in one file-scope device array that every GPU
 // loading this library keeps until the process exits (kMaxRows + 1 doubles,
 // 64 KB).  Host code needs its device address, which cudaGetSymbolAddress
-// returns once per device; the first call on a device does that lookup.
+// returns; the first call on a device does that lookup and keeps the address.
+// The address belongs to the device's context: if that context is destroyed
+// and re-created (cudaDeviceReset), the next call sees a new context id and
+// looks the address up again.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -30,6 +34,38 @@ static __device__ __align__(256) double g_noalloc_scratch[kMaxRows + 1];
 
 std::mutex g_mu;
 double* g_scratch_addr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};   // context id the address belongs to
+
+// the driver's cuCtxGetCurrent / cuCtxGetId, reached through the runtime (no
+// link against libcuda); null if the driver does not offer them
+typedef CUresult (*ctx_current_fn)(CUcontext*);
+typedef CUresult (*ctx_id_fn)(CUcontext, unsigned long long*);
+ctx_current_fn g_ctx_current = nullptr;
+ctx_id_fn g_ctx_id = nullptr;
+bool g_ctx_fns_tried = false;
+
+// id of the current context, or 0 if it cannot be had
+unsigned long long current_context_id() {
+    if (!g_ctx_fns_tried) {
+        g_ctx_fns_tried = true;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            g_ctx_current = (ctx_current_fn)f1;
+            g_ctx_id = (ctx_id_fn)f2;
+        }
+        cudaGetLastError();
+    }
+    if (!g_ctx_current || !g_ctx_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&c) != CUDA_SUCCESS || !c) return 0;
+    if (g_ctx_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 __device__ __forceinline__ double block_sum(double v, double* s_part) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -73,16 +109,22 @@ __global__ void __launch_bounds__(1024) sum_rows(double* scratch, int n_rows) {
     if (threadIdx.x == 0) scratch[kMaxRows] = t;
 }
 
-// device address of the scratch array for the current device (looked up once)
+// device address of the scratch array for the current device: looked up on
+// the first call with that device current, again whenever the device's
+// context has changed since (a reset), and on every call if the context id
+// cannot be read
 int scratch_for_current_device(double** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CMH_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return CMH_ERR_ARG;
+    if (cudaSetDevice(dev) != cudaSuccess) return CMH_ERR_CUDA;   // makes the device's context current
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return CMH_ERR_CUDA;
         g_scratch_addr[dev] = (double*)p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_addr[dev];
     return CMH_OK;

@@ -4,7 +4,8 @@ allocation would synchronise the device under someone else's kernels).
 
 Collected last on purpose: a failure here leaves every other test already run.
 It checks the allocation-free entry point against the existing one
-(cmh_log_density), on two calls in a row, through the C ABI.
+(cmh_log_density) and against the oracle's log-likelihood, on two calls in a
+row, through the C ABI.
 """
 import ctypes as C
 
@@ -26,40 +27,49 @@ def _noalloc(cm, sig, var, dtype):
 
 
 @pytest.mark.parametrize("f32", [False, True])
-def test_noalloc_matches_log_density_noise_only(f32):
-    """No events: the variance is the noise variance everywhere, and the
-    existing entry point returns -Lambda (empty-set prior) + that likelihood."""
+def test_noalloc_matches_log_density_noise_only(orc, f32):
+    """No events: the variance is the noise variance everywhere.  The existing
+    entry point returns -Lambda (empty-set prior) + that likelihood; the
+    oracle gives the likelihood from its own sum.  float32 samples are priced
+    in float32 and summed in float64, hence the looser bound there."""
     cm = lib()
     import torch
     w = small_world(seed=31, dtype=np.float32 if f32 else np.float64)
     dtype = cm.F32 if f32 else cm.F64
     m = cm.create_model(None, w.stations, w.signals, cm.make_params(w.params, dtype=dtype))
     want = m.log_density() + w.params.Lambda
+    want_orc = orc.World(w).log_likelihood(np.zeros((0, 4)))
     sig = torch.from_numpy(w.signals).cuda()
     var = torch.full_like(sig, w.params.noise_var)
     torch.cuda.synchronize()
     for _ in range(2):
-        assert _noalloc(cm, sig, var, dtype) == pytest.approx(want, rel=1e-12)
+        got = _noalloc(cm, sig, var, dtype)
+        assert got == pytest.approx(want, rel=1e-12)
+        assert got == pytest.approx(want_orc, rel=1e-6 if f32 else 1e-12)
     m.destroy()
 
 
 def test_noalloc_matches_log_density_with_events(orc):
     """Ground-truth events: the variance rows come from the oracle's
-    definition; the existing entry point's log-density minus the prior must
-    equal the allocation-free sum, on two consecutive calls."""
+    definition; the allocation-free sum must equal the existing entry point's
+    log-density minus the prior, and the oracle's log-likelihood of the same
+    events, on two consecutive calls."""
     cm = lib()
     import torch
     w = small_world(seed=32)
     m = cm.create_model(w.events, w.stations, w.signals, cm.make_params(w.params, dtype=cm.F64))
     o = orc.World(w)
     want = m.log_density() - o.log_prior(w.events)
+    want_orc = o.log_likelihood(w.events)
     ns = w.signals.shape[1]
     V = np.stack([o.variance(w.events, j, 0, ns) for j in range(w.n_stations)])
     sig = torch.from_numpy(w.signals).cuda()
     var = torch.from_numpy(V).cuda()
     torch.cuda.synchronize()
     for _ in range(2):
-        assert _noalloc(cm, sig, var, cm.F64) == pytest.approx(want, rel=1e-11)
+        got = _noalloc(cm, sig, var, cm.F64)
+        assert got == pytest.approx(want, rel=1e-11)
+        assert got == pytest.approx(want_orc, rel=1e-12)
     m.destroy()
 
 

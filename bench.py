@@ -72,10 +72,41 @@ def _traffic():
     return float(rec["dram_bytes_per_launch"]), rec.get("command", "")
 
 
+FP32_ERROR_FILE = os.path.join(ROOT, "profiles", "fp32_error_scale_density.json")
+
+
+def _fp32_error():
+    """The float32 sweep's error against the float64 oracle, from the
+    committed record of the parity test at the bench workload's density
+    (>= 1e5 proposals), or None when the kernel changed since."""
+    try:
+        with open(FP32_ERROR_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return {"value": None, "reason": "no record committed"}
+    if rec.get("kernel_sha256") != _kernel_digest():
+        return {"value": None, "reason": "kernel changed since the record"}
+    return rec
+
+
 def n_proposals(st) -> int:
     """Every MH proposal a model made: birth, death, move, joint pair and
     arrival-time moves."""
     return int(sum(st["proposed"]) + st["pair"][0] + st["arrival"][0])
+
+
+def n_evaluated(st) -> int:
+    """The proposals that were priced: those not rejected outright (a
+    candidate outside its region, the domain, [0, T) or m >= 2)."""
+    return int(sum(st["evaluated"]) + st["pair"][1] + st["arrival"][1])
+
+
+# algorithmic work per priced sample of the float32 variance pricing: the
+# logarithm and the reciprocal of each sample's term on the special-function
+# unit, and ~12 float32 FMA (24 flops) for the envelope, the change, the
+# ratio, the series and the compensated sum
+MUFU_PER_SAMPLE = 2.0
+FLOPS_PER_SAMPLE = 24.0
 
 
 def _workload(name: str, likelihood: str = "variance", p_pair: float = 0.0, sig_a: float = 0.0,
@@ -280,9 +311,12 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     _, _, _, st1 = m.read_state(cap=0)
     props = n_proposals(st1) - n_proposals(st0)
+    evals = n_evaluated(st1) - n_evaluated(st0)
     launches = st1["kernel_launches"] - st0["kernel_launches"]
     ms_max, total_props = reduce_max_sum(ms, props, dist, "cuda")
+    _, total_evals = reduce_max_sum(ms, evals, dist, "cuda")
     value = total_props / (ms_max / 1e3)
+    evaluated_per_s = total_evals / (ms_max / 1e3)
     sweeps_per_s = args.steps / (ms_max / 1e3)
 
     # ---------------- live kernel timing for the roofline ----------------
@@ -295,25 +329,55 @@ def run_ours(args):
     phase_ms = sb["phase_ms"] - sa["phase_ms"]
     priced = sb["priced_samples"] - sa["priced_samples"]
     rewritten = sb["rewritten_samples"] - sa["rewritten_samples"]
-    # algorithmic bytes: every priced sample reads s and V once, every
-    # re-synthesised sample writes V once
-    alg_bytes = priced * 2 * esz + rewritten * esz
-    per_launch_bytes = alg_bytes / max(n_launch, 1)
-    per_launch_s = phase_ms / 1e3 / max(n_launch, 1)
+    unique = sb["unique_samples"] - sa["unique_samples"]
+    nl = max(n_launch, 1)
+    per_launch_s = phase_ms / 1e3 / nl
     peaks, peak_kind = _peaks()
-    achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
+    if f32:
+        # algorithmic HBM bytes of a launch: per region and colour phase, the
+        # union of the windows its proposals priced at each station, read once
+        # (s and V), plus the variance written back on accepted steps
+        per_launch_bytes = (unique * 2 * esz + rewritten * esz) / nl
+        bytes_rule = "unique window samples per region phase x 2 x 4 B (s, V) + re-synthesised samples x 4 B"
+    else:
+        # the float64 form does not count unique windows: every priced sample
+        per_launch_bytes = (priced * 2 * esz + rewritten * esz) / nl
+        bytes_rule = "priced samples x 2 x 8 B (s, V) + re-synthesised samples x 8 B"
+    mufu_peak, fma_peak = cm.measure_alu_peaks(stream)
+    t_hbm = per_launch_bytes / (peaks["hbm_gbs"] * 1e9)
+    t_mufu = MUFU_PER_SAMPLE * priced / nl / mufu_peak
+    t_fma = FLOPS_PER_SAMPLE * priced / nl / fma_peak
+    terms = {"hbm": {"work_per_launch": per_launch_bytes, "unit": "B", "peak": peaks["hbm_gbs"] * 1e9,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind, "rule": bytes_rule,
+                     "t_us": t_hbm * 1e6},
+             "mufu": {"work_per_launch": MUFU_PER_SAMPLE * priced / nl, "unit": "ops", "peak": mufu_peak,
+                      "peak_source": "cmh_measure_alu_peaks (ex2/lg2/rcp chains, measured in this run)",
+                      "rule": "%g per priced sample" % MUFU_PER_SAMPLE, "t_us": t_mufu * 1e6},
+             "fma": {"work_per_launch": FLOPS_PER_SAMPLE * priced / nl, "unit": "flop", "peak": fma_peak,
+                     "peak_source": "cmh_measure_alu_peaks (FMA chains, measured in this run)",
+                     "rule": "%g per priced sample" % FLOPS_PER_SAMPLE, "t_us": t_fma * 1e6}}
+    bound = max(terms, key=lambda k: terms[k]["t_us"])
+    if bound == "hbm":
+        achieved, peak_v, unit = per_launch_bytes / per_launch_s / 1e9, peaks["hbm_gbs"], "GB/s"
+    elif bound == "mufu":
+        achieved, peak_v, unit = terms["mufu"]["work_per_launch"] / per_launch_s / 1e12, mufu_peak / 1e12, "Tops/s"
+    else:
+        achieved, peak_v, unit = terms["fma"]["work_per_launch"] / per_launch_s / 1e12, fma_peak / 1e12, "TFLOP/s"
     if not f32:
         traffic, traffic_src = None, "float64 path not captured"
     elif args.likelihood != "variance":
         traffic, traffic_src = None, "the ncu capture is of the variance reading"
     else:
         traffic, traffic_src = _traffic()
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": traffic_src,
+    roof = {"bound": "alu" if bound in ("mufu", "fma") else "hbm", "bound_term": bound, "achieved": achieved,
+            "peak": peak_v, "unit": unit, "frac": achieved / peak_v if peak_v else 0.0,
+            "traffic": traffic, "traffic_source": traffic_src,
             "kernel": "sweep32_kernel<false> (one launch per sweep: all colour phases)" if f32
                       else "phase_kernel (float64 replay, one launch per colour phase)",
             "avg_launch_us": per_launch_s * 1e6, "alg_bytes_per_launch": per_launch_bytes,
-            "peak_source": peak_kind}
+            "priced_samples_per_launch": priced / nl, "unique_samples_per_launch": unique / nl,
+            "rewritten_samples_per_launch": rewritten / nl, "terms": terms,
+            "roofline_us": max(t_hbm, t_mufu, t_fma) * 1e6, "peak_source": peak_kind}
     m.destroy()
     del sig_dev
     torch.cuda.empty_cache()
@@ -327,6 +391,8 @@ def run_ours(args):
     if args.sig_a:
         m2.set_arrival_offsets(world.offsets)
     m2.partition_and_color(p.L, shift_mode=1)
+    torch.cuda.synchronize()
+    t_created = time.perf_counter()
     d2h = 0
     # every sweep's state is read: requested right after the sweep into one of
     # two pinned slots, fetched while the next sweep runs
@@ -339,19 +405,24 @@ def run_ours(args):
     ev, ids, lp, st = m2.read_state_fetch((args.steps - 1) % 2)
     d2h += ev.nbytes + ids.nbytes + 8
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    t_end = time.perf_counter()
+    e2e_s = t_end - t0
     _, _, _, st2 = m2.read_state(cap=0)
     e2e_props = n_proposals(st2)
     m2.destroy()
     e2e_max, e2e_total = reduce_max_sum(e2e_s, e2e_props, dist, "cuda")
     e2e_value = e2e_total / e2e_max
+    sweeps_max, _ = reduce_max_sum(t_end - t_created, 0, dist, "cuda")
+    create_max, _ = reduce_max_sum(t_created - t0, 0, dist, "cuda")
     h2d_per_step = world.signals.nbytes / args.steps
 
     if rank == 0:
         cpu = _cpu_baseline(world, p_pair=args.p_pair, sig_a=args.sig_a, p_arr=args.p_arr,
                             sig_da=args.sig_da) if world_size == 1 else None
         line = {"metric": "MH proposals/sec and sweeps/sec on 1 GB300", "value": value, "unit": "proposals/s",
-                "sweeps_per_s": sweeps_per_s, "n_gpus": world_size, "steps": args.steps, "warmup": args.warmup,
+                "sweeps_per_s": sweeps_per_s, "evaluated_per_s": evaluated_per_s,
+                "evaluated_note": "proposals priced (not rejected outright for leaving their region, the "
+                                  "domain, [0, T) or m >= 2), same timed sweeps", "n_gpus": world_size, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if f32 else "f64",
                 "data": "synthetic (seeded worldgen, the model's generative story)",
@@ -361,24 +432,100 @@ def run_ours(args):
                 "clocks": clocks.summary(), "gpu_launches": int(launches),
                 "e2e": {"value": e2e_value, "unit": "proposals/s", "h2d_bytes_per_step": h2d_per_step,
                         "d2h_bytes_per_step": d2h / args.steps,
+                        "value_excluding_creation": e2e_total / sweeps_max,
+                        "creation_s": create_max,
                         "note": "cmh_create_model from pinned host signals (copied once, amortised over the "
                                 "steps) + per step cmh_run_sweeps(1) and the read of that sweep's state "
                                 "(cmh_read_state_async into a pinned slot, fetched while the next sweep runs)"},
-                "roofline": roof, "cpu_baseline": cpu}
+                "roofline": roof, "cpu_baseline": cpu,
+                "fp32_error": _fp32_error() if f32 and args.likelihood == "variance" else None}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
 
 
+def instance_cost(n_stations: int, p) -> float:
+    """Estimated work of one sweep of a batched instance: its regions times k
+    steps times the samples a step prices (the stations within R_max of an
+    event, at the instance's station density, times the window length)."""
+    n_cells = (int(p.W // p.L) + 2) ** 2
+    st_near = n_stations * math.pi * p.R_max ** 2 / (p.W * p.W)
+    return float(n_cells * K_PER_PHASE * (1.0 + st_near * p.n_w))
+
+
+def shard_instances(costs, world_size: int, rank: int):
+    """Rank `rank`'s share of the instances: largest estimated cost first, each
+    to the rank with the least cost so far (the lowest rank on a tie).  Every
+    rank computes the same split from the same costs, so the shares are
+    disjoint, cover every instance and need no communication."""
+    load = [0.0] * world_size
+    mine = []
+    for i in sorted(range(len(costs)), key=lambda j: (-costs[j], j)):
+        r = min(range(world_size), key=lambda q: (load[q], q))
+        load[r] += costs[i]
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
+
+
+def gather_summaries(summary, dist=None):
+    """Every rank's summary dict, in rank order (one all-gather; the only
+    collective of the batched workload, after the timed region)."""
+    if dist is None:
+        return [summary]
+    out = [None] * dist.get_world_size()
+    dist.all_gather_object(out, summary)
+    return out
+
+
+def _batched_cpu_baseline(worlds, seconds_target: float = 15.0):
+    """The oracle's chromatic sampler on the instances, one after another
+    from the ground truth, each on all host cores, for about seconds_target."""
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    props, sweeps, used = 0, 0, 0
+    t0 = time.perf_counter()
+    for i, w in enumerate(worlds):
+        o = oracle.World(w, k_per_phase=K_PER_PHASE, seed=CHAIN_SEED + i)
+        ev, ids = w.events, None
+        for s in range(3):
+            ncx = int(w.params.W // w.params.L) + 2
+            ev, ids, tr, _ = o.run_chromatic(ev, 1, ids=ids, sweep0=s, trace_cap=ncx * ncx * K_PER_PHASE + 16,
+                                             threads=threads)
+            props += len(tr)
+            sweeps += 1
+        used += 1
+        if time.perf_counter() - t0 > seconds_target:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": props / dt, "unit": "proposals/s", "cores": threads, "kind": "oracle",
+            "sample": "3 sweeps of each of the first %d instances of this rank's share, from the ground truth, "
+                      "the oracle's chromatic sampler (OpenMP over same-colour regions)" % used,
+            "sweeps": sweeps, "proposals": props, "seconds": dt}
+
+
 def run_batched(args):
     """256 independent instances of uneven size swept together: one
-    persistent launch per sweep over every instance's regions."""
+    persistent launch per sweep over every instance's regions.  With N ranks
+    the instances are split by estimated cost (shard_instances) and each rank
+    sweeps its share as one batch: no data-path collective."""
     import torch
     import paper_1612_00595_gb300 as cm
-    torch.cuda.set_device(0)
-    worlds = worldgen.config_batched(256, seed=2000)
+    world_size = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world_size > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sizes = worldgen.batched_instances(256, seed=2000)
+    costs = [instance_cost(S, p) for S, p in sizes]
+    share = shard_instances(costs, world_size, rank)
+    worlds = worldgen.config_batched(256, seed=2000, indices=share)
     models, kept, skipped = [], [], []
-    for i, w in enumerate(worlds):
+    for i, w in zip(share, worlds):
         p = w.params
         # capacities from the instance's density: events per region and
         # arrivals per station, mean + 6 sd + slack
@@ -398,40 +545,93 @@ def run_batched(args):
         models.append(m)
         kept.append(w)
     stream = torch.cuda.Stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
     b = cm.create_batch(models, stream=stream)
     b.run_sweeps(args.warmup)
     b.sync()
     p0 = sum(n_proposals(m.read_state(cap=0)[3]) for m in models)
-    torch.cuda.synchronize()
+    barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clocks:
+    with ClockSampler(local) as clocks:
         e0.record(stream)
         b.run_sweeps(args.steps)
         e1.record(stream)
         e1.synchronize()
+    barrier()
     b.sync()
     ms = e0.elapsed_time(e1)
     p1 = sum(n_proposals(m.read_state(cap=0)[3]) for m in models)
-    n_regions = sum((int(w.params.W // w.params.L) + 2) ** 2 for w in kept)
-    worlds_all, worlds = worlds, kept
-    line = {"metric": "MH proposals/sec and sweeps/sec on 1 GB300 (batched instances)", "value": (p1 - p0) / (ms / 1e3),
-            "unit": "proposals/s", "sweeps_per_s": args.steps / (ms / 1e3), "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded worldgen, the model's generative story)",
-            "config": {"workload": "256 independent instances: stations logU[16,256], Lambda logU[10,500], side "
-                                   "logU[200,2000] km, T logU[600,7200] s, f32, k=32; one sweep of every instance "
-                                   "per step",
-                       "instances": len(worlds), "instances_drawn": len(worlds_all),
-                       "skipped": "%d dense instances whose per-region structures exceed shared memory: %s"
-                                  % (len(skipped), skipped),
-                       "groups (models, CTAs)": b.groups(), "cells": n_regions,
-                       "signal_bytes": int(sum(w.signals.nbytes for w in worlds))},
-            "clocks": clocks.summary(), "gpu_launches": (4 + 2 * len(b.groups())) * args.steps}
-    print(json.dumps(line))
+    groups = b.groups()
     b.destroy()
+    ms_max, total_props = reduce_max_sum(ms, p1 - p0, dist, "cuda")
+
+    # roofline of the batched sweep: a second batch of the same models with
+    # the unique-window count on, timed with CUDA events around its sweeps
+    # (the persistent batch kernel plus the short re-binning kernels)
+    for m in models:
+        m.set_timing(True)
+    sa = [m.read_state(cap=0)[3] for m in models]
+    b2 = cm.create_batch(models, stream=stream)
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    b2.run_sweeps(args.steps)
+    r1.record(stream)
+    r1.synchronize()
+    b2.sync()
+    roof_ms = r0.elapsed_time(r1)
+    sb = [m.read_state(cap=0)[3] for m in models]
+    b2.destroy()
+    for m in models:
+        m.set_timing(False)
+    unique = sum(y["unique_samples"] - x["unique_samples"] for x, y in zip(sa, sb))
+    priced = sum(y["priced_samples"] - x["priced_samples"] for x, y in zip(sa, sb))
+    rewritten = sum(y["rewritten_samples"] - x["rewritten_samples"] for x, y in zip(sa, sb))
+    peaks, peak_kind = _peaks()
+    per_sweep_s = roof_ms / 1e3 / args.steps
+    per_sweep_bytes = (unique * 8 + rewritten * 4) / args.steps
+    achieved = per_sweep_bytes / per_sweep_s / 1e9
+    summary = {"rank": rank, "instances": len(kept), "skipped": skipped, "ms": ms, "proposals": p1 - p0,
+               "groups": groups, "cells": sum((int(w.params.W // w.params.L) + 2) ** 2 for w in kept),
+               "signal_bytes": int(sum(w.signals.nbytes for w in kept)), "cost": sum(costs[i] for i in share)}
+    summaries = gather_summaries(summary, dist)
+    if rank == 0:
+        cpu = _batched_cpu_baseline(kept) if world_size == 1 else None
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "traffic_source": "no ncu capture of the batched workload",
+                "kernel": "batched sweep (sweep32_batch persistent kernel + re-binning), rank 0, CUDA events "
+                          "around its sweeps",
+                "avg_sweep_us": per_sweep_s * 1e6, "alg_bytes_per_sweep": per_sweep_bytes,
+                "rule": "unique window samples per region phase x 2 x 4 B (s, V) + re-synthesised samples x 4 B",
+                "priced_samples_per_sweep": priced / args.steps, "peak_source": peak_kind}
+        line = {"metric": "MH proposals/sec and sweeps/sec on 1 GB300 (batched instances)",
+                "value": total_props / (ms_max / 1e3), "unit": "proposals/s",
+                "sweeps_per_s": args.steps / (ms_max / 1e3), "n_gpus": world_size, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "strong" if world_size > 1 else "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded worldgen, the model's generative story)",
+                "config": {"workload": "256 independent instances: stations logU[16,256], Lambda logU[10,500], side "
+                                       "logU[200,2000] km, T logU[600,7200] s, f32, k=32; one sweep of every "
+                                       "instance per step",
+                           "parallelism": "instances split across %d GPUs by estimated cost, one batch per GPU, no "
+                                          "collective in the timed region" % world_size if world_size > 1
+                                          else "1 GPU",
+                           "ranks": [{k: v for k, v in x.items() if k != "groups"} for x in summaries],
+                           "groups (models, CTAs), rank 0": groups},
+                "clocks": clocks.summary(), "gpu_launches": (4 + 2 * len(groups)) * args.steps,
+                "roofline": roof, "cpu_baseline": cpu}
+        print(json.dumps(line))
     for m in models:
         m.destroy()
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def run_learned(args):
@@ -580,6 +780,54 @@ def run_learned_posterior(args):
                       "data": "synthetic (seeded worldgen)", "results": out}))
 
 
+def run_profile_case(args):
+    """A named workload for a profiler: build the model, run --warmup sweeps,
+    then --steps sweeps (or training steps), print a one-line summary.
+
+    Workloads: ``scale`` (4000 x 4000 km, 24 h, 1600 stations, float32),
+    ``corner`` (1000 x 1000 km of the same density and record length, 100
+    stations: 0.7 GB of signals + variance, larger than L2), ``replay``
+    (1000 x 1000 km, 1 h, 100 stations, float64; with --p-pair, --sig-a,
+    --p-arr), ``train`` (the learned birth network: --warmup then --steps
+    training steps of 256 windows simulated from the 1000 km, 1 h,
+    100-station float32 world)."""
+    import paper_1612_00595_gb300 as cm
+    name = args.profile_case
+    if name == "train":
+        w = worldgen.config_learned(seed=1000)
+        m = cm.create_model(None, w.stations, w.signals, cm.make_params(w.params, k_per_phase=K_PER_PHASE, seed=7,
+                                                                        dtype=cm.F32))
+        net = cm.Net(max_batch=256, seed=7)
+        net.train(m, args.warmup, 256, 3e-4)
+        loss = net.train(m, args.steps, 256, 3e-4)
+        print("training steps %d  loss %.4f" % (args.warmup + args.steps, loss))
+        net.destroy()
+        m.destroy()
+        return
+    if name == "scale":
+        w = worldgen.config_scale(seed=SEED)
+    elif name == "corner":
+        w = worldgen.config_scale(seed=SEED, side_regions=10)
+    elif name == "replay":
+        w = worldgen.config_replay(seed=SEED, sig_a=args.sig_a)
+    else:
+        raise SystemExit("unknown profile case " + name)
+    dtype = cm.F32 if w.signals.dtype == np.float32 else cm.F64
+    m = cm.create_model(w.events, w.stations, w.signals,
+                        cm.make_params(w.params, k_per_phase=K_PER_PHASE, seed=7, dtype=dtype, p_pair=args.p_pair,
+                                       sig_a=args.sig_a, p_arr=args.p_arr))
+    if args.sig_a:
+        m.set_arrival_offsets(w.offsets)
+    m.partition_and_color(w.params.L, shift_mode=1)
+    m.run_sweeps(args.warmup)
+    m.sync()
+    m.run_sweeps(args.steps)
+    ev, ids, lp, st = m.read_state()
+    print("events %d  proposals %d  accepted %s  pair %s  launches %d" % (
+        len(ev), n_proposals(st), st["accepted"], st["pair"], st["kernel_launches"]))
+    m.destroy()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -595,7 +843,12 @@ def main():
                     help="replay workload: latent arrival times with offsets ~ N(0, sig_a^2) seconds")
     ap.add_argument("--p-arr", type=float, default=0.0, help="replay workload: share of arrival-time moves")
     ap.add_argument("--sig-da", type=float, default=1.0, help="step of the arrival-time move, seconds")
+    ap.add_argument("--profile-case", default=None, choices=["scale", "corner", "replay", "train"],
+                    help="run a named workload for a profiler (--warmup, then --steps sweeps) and print a summary")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if (args.p_pair or args.sig_a or args.p_arr) and args.workload != "replay":
         raise SystemExit("--p-pair, --sig-a and --p-arr need the float64 replay workload")
     if args.warmup < 3:

@@ -136,6 +136,10 @@ typedef struct {
                                slot per CTA holding their arrival caches and lists (0: none) */
     uint64_t pair[3];       /* joint moves of a pair (p_pair): proposed, evaluated, accepted */
     uint64_t arrival[3];    /* arrival-time moves (p_arr): proposed, evaluated, accepted */
+    uint64_t unique_samples;/* float32 form, counted only while timing is enabled
+                               (cmh_set_timing): per region and colour phase, the samples of
+                               the union of the windows its evaluated proposals priced at each
+                               station, summed over regions (the samples a phase first touches) */
 } cmh_stats;
 
 /* one record per MH step (optional, cmh_set_trace) */
@@ -424,10 +428,12 @@ void cmh_batch_destroy(cmh_batch* b);
  *                      synchronises it before returning
  * Allocates nothing: the partial sums live in a fixed 64 KB device array
  * that every GPU loading the library keeps until exit.  The first call on a
- * device looks that array's address up (cudaGetSymbolAddress), so make it
- * before capturing a stream.  Every call reuses the same array: calls that
- * overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller.
+ * device looks that array's address up (cudaGetSymbolAddress) and keeps it;
+ * make that first call before any stream capture begins.  The address
+ * belongs to the device's context: after cudaDeviceReset the next call sees
+ * the new context and looks it up again.  Every call reuses the same array
+ * and leaves its sums there: calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.
  * Errors: CMH_ERR_ARG (null pointer, n_samples < 1, row_pitch < n_samples,
  * unknown dtype), CMH_ERR_CAPACITY (n_rows > 8191, the array's limit),
  * CMH_ERR_CUDA.
@@ -435,6 +441,36 @@ void cmh_batch_destroy(cmh_batch* b);
 int cmh_gaussian_loglik_noalloc(const void* signals, const void* variance, int32_t n_rows,
                                 int64_t n_samples, int64_t row_pitch, cmh_dtype dtype, double* out,
                                 void* cuda_stream);
+
+/*
+ * Test hook for the bounded waits of the persistent float32 sweep (schedule 0):
+ * from the next cmh_run_sweeps on, the region of cell `cell` runs its colour
+ * phase but never announces that it has finished, so every higher-colour
+ * neighbour waiting for it gives up after `wait_limit` polls (0: the default,
+ * about half a second) and the sweep latches CMH_ERR_TIMEOUT, which the next
+ * synchronising call returns; the model then refuses further work
+ * (CMH_ERR_STATE) and must be destroyed.  No kernel is left waiting: every
+ * wait is bounded and the others end as soon as the error is latched.
+ * cell = -1 turns the hook off.  The paper has no counterpart.
+ * Errors: CMH_ERR_ARG (null model, cell outside -1..n_cells-1),
+ * CMH_ERR_STATE (not partitioned, float64 form, or colour-by-colour schedule).
+ */
+int cmh_test_hold_region(cmh_model* m, int32_t cell, uint32_t wait_limit);
+
+/*
+ * Measured throughput of the current device's special-function unit (ex2,
+ * lg2, rcp: the per-sample exponential, logarithm and reciprocal of the
+ * float32 pricing) and of its float32 FMA pipe, the denominators of the
+ * roofline's arithmetic terms beside the HBM bandwidth.  The paper has no
+ * counterpart: it is a measurement, not part of the method.
+ *   mufu_ops_per_s   host pointer; receives MUFU operations per second
+ *   fma_flops_per_s  host pointer; receives float32 flops per second (2 per FMA)
+ *   cuda_stream      stream the timed kernels run on (NULL: legacy default)
+ * Best of three timed launches each, after a warm-up, with CUDA events;
+ * synchronises the stream.  Allocates nothing.
+ * Errors: CMH_ERR_ARG (null pointer), CMH_ERR_CUDA.
+ */
+int cmh_measure_alu_peaks(double* mufu_ops_per_s, double* fma_flops_per_s, void* cuda_stream);
 
 /*
  * Test hook: n Philox4x64-10 blocks computed by a device kernel.

@@ -68,7 +68,7 @@ class Stats(C.Structure):
                 ("sweeps", C.c_int64), ("n_events", C.c_int64), ("phase_ms", C.c_double),
                 ("phase_launches", C.c_int64), ("kernel_launches", C.c_int64),
                 ("priced_samples", C.c_uint64), ("rewritten_samples", C.c_uint64), ("spill_bytes", C.c_int64),
-                ("pair", C.c_uint64 * 3), ("arrival", C.c_uint64 * 3)]
+                ("pair", C.c_uint64 * 3), ("arrival", C.c_uint64 * 3), ("unique_samples", C.c_uint64)]
 
     def as_dict(self):
         return {"proposed": list(self.proposed), "evaluated": list(self.evaluated),
@@ -76,7 +76,7 @@ class Stats(C.Structure):
                 "phase_ms": self.phase_ms, "phase_launches": self.phase_launches,
                 "kernel_launches": self.kernel_launches, "priced_samples": self.priced_samples,
                 "rewritten_samples": self.rewritten_samples, "spill_bytes": self.spill_bytes,
-                "pair": list(self.pair), "arrival": list(self.arrival)}
+                "pair": list(self.pair), "arrival": list(self.arrival), "unique_samples": self.unique_samples}
 
 
 TRACE_DTYPE = np.dtype([("sweep", "<i4"), ("cell", "<i4"), ("step", "<i4"), ("type", "<i4"),
@@ -91,7 +91,8 @@ EXPORTS = ["cmh_create_model", "cmh_partition_and_color", "cmh_run_sweeps", "cmh
            "cmh_autotune", "cmh_batch_sync", "cmh_batch_groups", "cmh_set_birth_table", "cmh_set_birth_magnitude",
            "cmh_net_param_count", "cmh_net_create", "cmh_net_destroy", "cmh_net_get_params", "cmh_net_set_params",
            "cmh_net_forward", "cmh_net_gradients", "cmh_net_train", "cmh_net_birth_table",
-           "cmh_set_arrival_offsets", "cmh_read_arrival_offsets"]
+           "cmh_set_arrival_offsets", "cmh_read_arrival_offsets", "cmh_measure_alu_peaks",
+           "cmh_test_hold_region"]
 
 
 def _load():
@@ -123,6 +124,8 @@ def _load():
         "cmh_destroy": (None, [P]),
         "cmh_strerror": (C.c_char_p, [C.c_int]),
         "cmh_philox4x64": (C.c_int, [P, P, P, i64]),
+        "cmh_measure_alu_peaks": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), P]),
+        "cmh_test_hold_region": (C.c_int, [P, i32, C.c_uint32]),
         "cmh_gaussian_loglik_noalloc": (C.c_int, [P, P, i32, i64, i64, i32, C.POINTER(C.c_double), P]),
         "cmh_batch_create": (C.c_int, [C.POINTER(P), i32, P, C.POINTER(P)]),
         "cmh_batch_run_sweeps": (C.c_int, [P, i64]),
@@ -327,6 +330,11 @@ class Model:
         out = np.zeros(n.value, dtype=TRACE_DTYPE)
         _check(lib.cmh_read_trace(self._h, _ptr(out), n.value, C.byref(n)), "cmh_read_trace")
         return out
+
+    def test_hold_region(self, cell: int, wait_limit: int = 0):
+        """cmh_test_hold_region: region `cell` never announces its phase, so
+        its higher-colour neighbours' bounded waits run out (test hook)."""
+        _check(lib.cmh_test_hold_region(self._h, int(cell), int(wait_limit)), "cmh_test_hold_region")
 
     def set_timing(self, enable: bool):
         _check(lib.cmh_set_timing(self._h, 1 if enable else 0), "cmh_set_timing")
@@ -535,6 +543,15 @@ def run_sweeps(model: Model, n: int):
 
 def read_state(model: Model, cap: Optional[int] = None):
     return model.read_state(cap)
+
+
+def measure_alu_peaks(stream=None):
+    """cmh_measure_alu_peaks: (MUFU operations/s, float32 flops/s) of the
+    current device, each the best of three timed launches."""
+    a, b = C.c_double(), C.c_double()
+    st = None if stream is None else C.c_void_p(stream.cuda_stream)
+    _check(lib.cmh_measure_alu_peaks(C.byref(a), C.byref(b), st), "cmh_measure_alu_peaks")
+    return a.value, b.value
 
 
 def philox4x64(ctr, key) -> np.ndarray:

@@ -12,7 +12,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libchromh.so")
 OBJDIR = os.path.join(ROOT, "_build")
-SOURCES = ["cmh_api.cu", "cmh_partition.cu", "cmh_sweep.cu", "cmh_phase32.cu", "cmh_noalloc.cu", "cmh_net.cu"]
+SOURCES = ["cmh_api.cu", "cmh_partition.cu", "cmh_sweep.cu", "cmh_phase32.cu", "cmh_noalloc.cu", "cmh_net.cu",
+           "cmh_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -435,6 +435,9 @@ int cmh_create_model(const cmh_event* init_events, int64_t n_events, const cmh_s
     g.frz_cap = m->p.frozen_capacity;
     g.f32 = p->dtype == CMH_F32;
     g.threads = m->p.block_threads;
+    g.dep_wait_limit = kDepWaitLimitDefault;
+    g.hold_cell = -1;
+    g.count_unique = m->timing && g.f32 ? 1 : 0;
     g.max_events = m->p.max_events;
     g.fv_f = (float)(p->f_hz / p->v);
     g.mean_mode = p->likelihood == 1;
@@ -823,6 +826,7 @@ int cmh_read_state(cmh_model* m, cmh_event* out, uint64_t* ids_out, int64_t cap,
         stats_out->spill_bytes = m->partitioned && m->g.spill ? m->g.spill_bytes : 0;
         for (int i = 0; i < 3; ++i) stats_out->pair[i] = st[11 + i];
         for (int i = 0; i < 3; ++i) stats_out->arrival[i] = st[14 + i];
+        stats_out->unique_samples = st[17];
     }
     return CMH_OK;
 }
@@ -909,9 +913,22 @@ int cmh_read_trace(cmh_model* m, cmh_trace* out, int64_t cap, int64_t* n_out) {
     return CMH_OK;
 }
 
+int cmh_test_hold_region(cmh_model* m, int32_t cell, uint32_t wait_limit) {
+    if (!m) return CMH_ERR_ARG;
+    if (!m->partitioned || !m->g.f32 || m->sweep_grid <= 0) return CMH_ERR_STATE;
+    if (cell < -1 || cell >= m->g.n_cells) return CMH_ERR_ARG;
+    m->g.hold_cell = cell;
+    m->g.dep_wait_limit = wait_limit ? wait_limit : kDepWaitLimitDefault;
+    m->drop_graph();   // the captured sweep holds the old constants
+    return CMH_OK;
+}
+
 int cmh_set_timing(cmh_model* m, int32_t enable) {
     if (!m) return CMH_ERR_ARG;
     m->timing = enable ? 1 : 0;
+    // timed sweeps also count each region phase's unique window samples; the
+    // captured graph (untimed sweeps) keeps the constants it was captured with
+    m->g.count_unique = m->timing && m->g.f32 ? 1 : 0;
     return CMH_OK;
 }
 
@@ -1149,6 +1166,7 @@ int cmh_read_state_fetch(cmh_model* m, int32_t slot, cmh_event* out, uint64_t* i
         stats_out->spill_bytes = m->g.spill ? m->g.spill_bytes : 0;
         for (int i = 0; i < 3; ++i) stats_out->pair[i] = st[11 + i];
         for (int i = 0; i < 3; ++i) stats_out->arrival[i] = st[14 + i];
+        stats_out->unique_samples = st[17];
     }
     r.pending = false;
     return CMH_OK;

@@ -19,10 +19,12 @@ namespace cmh {
 
 constexpr int kMaxColours = 16;
 constexpr int kMaxK = 4095;
+constexpr unsigned kDepWaitLimitDefault = 1u << 22;   // polls of a neighbour's done stamp (~0.5 s)
 // proposed[3], evaluated[3], accepted[3], priced samples, rewritten samples,
 // joint moves of a pair: proposed, evaluated, accepted; arrival-time moves:
-// proposed, evaluated, accepted
-constexpr int kStats = 17;
+// proposed, evaluated, accepted; unique window samples (float32 form, while
+// count_unique is set)
+constexpr int kStats = 18;
 
 // model, partition and launch constants; passed by value to every kernel
 struct Geo {
@@ -51,6 +53,13 @@ struct Geo {
     long long store_cap, max_events;
     int f32;
     int threads;
+    int count_unique;   // float32 form: count the union of each region phase's priced windows (stats[17])
+    // float32 persistent sweep: polls a region makes of each lower-colour
+    // neighbour's done stamp before it gives up (CMH_ERR_TIMEOUT); and a test
+    // hook: the region of cell hold_cell (-1: none) runs its phase but never
+    // announces it, so that its neighbours' bounded waits run out
+    unsigned dep_wait_limit;
+    int hold_cell;
     // float32 form of the model constants (host-computed)
     float invL_f;      // 1 / L
     float fv_f;        // f / v

@@ -51,6 +51,7 @@ constexpr int kMinBlocks32 = 3;   // resident CTAs per SM the kernel is built fo
 constexpr int kMaxPix = 256;      // pixels of the learned birth table a region's range may span
 static_assert(kThreads32 <= 256, "the decision reduces the worker warps' partials in a three-level tree");
 constexpr unsigned kWaitLimit = 1u << 24;   // bounded mbarrier waits
+constexpr int kIv = 8;            // disjoint priced intervals kept per blanket station (unique-sample count)
 
 struct A32 {            // arrival of an own event at a blanket slot (the event's cache)
     int slot, k0;
@@ -66,7 +67,7 @@ struct SA {             // an entry of a station's arrival list
 };
 
 struct D32 {            // state-independent part of one MH step
-    double bx, by, bt, bm, blb;   // birth: float64 candidate and its log beta
+    double bx, by, bt, bm, blb;   // birth: float64 candidate and its log beta; move: float64 offsets
     double blq;                   // birth: log Lambda - log(W^2 T) - log q_b(candidate) (magnitude factor out)
     float xr, yr, ph, mf;         // birth: relative form; move: offsets dx, dy, dt (s), dm
     float logu;
@@ -115,6 +116,8 @@ struct Sm {
     float* stage_s;     // [2][scap] staged signal windows
     float* stage_v;     // [2][scap] staged variance windows
     int scap;           // floats per staging buffer (0: no staging)
+    int2* uiv;          // [blk_cap][kIv] disjoint windows priced at each blanket station this phase
+    int* un;            // [blk_cap] intervals held in uiv
     unsigned long long bar[2];   // mbarrier of each staging buffer
     int ph[2], on[2];   // parity of its pending completion; copies in flight
     double rect[4], X0, Y0, sx, sy, region_dlp;
@@ -135,8 +138,8 @@ struct Sm {
     int warp_cnt[32];
     float2 redf[32];
     // statistics of this CTA: proposed[3], evaluated[3], accepted[3], priced
-    // samples, re-synthesised samples (thread 0)
-    unsigned long long cnt[11];
+    // samples, re-synthesised samples, unique window samples (thread 0)
+    unsigned long long cnt[12];
 };
 
 // carve the dynamic shared buffer; returns its size (base may be null).  With
@@ -178,10 +181,14 @@ __host__ __device__ inline size_t layout32(const Geo& g, Sm* S, unsigned char* b
     float *nph = (float*)take(4 * E), *nmf = (float*)take(4 * E);
     int* nK = (int*)take(4 * E);
     int* tsoff = (int*)take(4 * 2 * (size_t)g.task_cap);
+    int2* uiv = (int2*)gtake(sizeof(int2) * B * kIv);
+    int* un = (int*)gtake(4 * B);
     const size_t scap = (size_t)g.stage_cap;
     float* stage_s = scap ? (float*)take(4 * 2 * scap) : nullptr;
     float* stage_v = scap ? (float*)take(4 * 2 * scap) : nullptr;
     if (S) {
+        S->uiv = uiv;
+        S->un = un;
         S->tsoff = tsoff;
         S->stage_s = stage_s;
         S->stage_v = stage_v;
@@ -417,10 +424,10 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
         } else {
             // the float64 state the move proposes, its float32 terms, and the
             // region-relative position for the region test
-            c.x = __dadd_rn(S.mx[ps], (double)dr.xr);
-            c.y = __dadd_rn(S.my[ps], (double)dr.yr);
-            c.t = __dadd_rn(S.mt[ps], (double)dr.ph);
-            c.m = __dadd_rn(S.mm[ps], (double)dr.mf);
+            c.x = __dadd_rn(S.mx[ps], dr.bx);   // the float64 offsets of the draw
+            c.y = __dadd_rn(S.my[ps], dr.by);
+            c.t = __dadd_rn(S.mt[ps], dr.bt);
+            c.m = __dadd_rn(S.mm[ps], dr.bm);
             event_terms32(g, c.t, c.m, c.K, c.ph, c.mf);
             c.xr = S.exr[ps] + dr.xr;
             c.yr = S.eyr[ps] + dr.yr;
@@ -564,6 +571,84 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
     __syncwarp();
 }
 
+// the change of the log-likelihood over one float4 group of samples
+// k4 .. k4+3 of task T (samples outside [T.lo, T.hi) or either window add 0):
+// the four terms summed in order
+template <bool MEAN>
+__device__ __forceinline__ float group_terms(const Geo& g, const Sm& S, const T32& T, int k4, float4 s4,
+                                             float4 v4) {
+    // one SFU evaluation per arrival for the whole group (see arr_var32)
+    const float bo = T.has_o ? arr_base32(g, T.E0o, T.k0o, k4) : 0.f;
+    const float bn = T.has_n ? arr_base32(g, T.E0n, T.k0n, k4) : 0.f;
+    const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+    const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+    float term[4], cnv[4];
+    unsigned need = 0;   // samples whose V' is rebuilt from the arrivals that stay
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int kk = k4 + e;
+        const bool io = T.has_o && (unsigned)(kk - T.k0o) < (unsigned)g.n_w;
+        const bool inn = T.has_n && (unsigned)(kk - T.k0n) < (unsigned)g.n_w;
+        // the same per-sample values the variance synthesis adds, so the
+        // priced change is the change written to V on accept
+        const float co = io ? __fmul_rn(bo, g.rho_f[e]) : 0.f;
+        const float cn = inn ? __fmul_rn(bn, g.rho_f[e]) : 0.f;
+        const float dd = cn - co;
+        cnv[e] = cn;
+        term[e] = 0.f;
+        if (MEAN && kk < T.hi && dd != 0.f) {
+            // additive reading: (d (s - mu) - d^2 / 2) / noise, mu = vv
+            term[e] = __fmul_rn(g.inv_noise_f, __fsub_rn(__fmul_rn(dd, __fsub_rn(sv[e], vv[e])),
+                                                         __fmul_rn(0.5f, __fmul_rn(dd, dd))));
+        } else if (!MEAN && kk < T.hi && dd != 0.f) {
+            const float V = vv[e], sm = sv[e];
+            const float Vp = V + dd;
+            if (Vp < 0.5f * V) {
+                need |= 1u << e;   // the changed arrival dominates V
+            } else {
+                // log(V'/V) - s^2 d / (V V'), one reciprocal (explicitly
+                // rounded, so every build of this code gives the same bits)
+                const float inv = rcp_sfu(__fmul_rn(V, Vp));
+                const float x = __fmul_rn(__fmul_rn(dd, Vp), inv);
+                const float q = __fmul_rn(__fmul_rn(sm, sm), __fmul_rn(dd, inv));
+                term[e] = __fmul_rn(-0.5f, __fsub_rn(log1p_fast(x), q));
+            }
+        }
+    }
+    if (need) {
+        // V' of the flagged samples from the arrivals that stay on this
+        // station (list order, compensated), one SFU evaluation per
+        // arrival for the group; the candidate's own arrival last
+        float a2[4], c2[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            a2[e] = g.syn0_f;
+            c2[e] = 0.f;
+        }
+        const SA* L = S.sarr + T.slot * g.frz_cap;
+        const int nl = S.scnt[T.slot];
+        for (int o = 0; o < nl; ++o) {
+            const SA A = L[o];
+            if (A.own == T.skip || (unsigned)(k4 + 3 - A.k0) >= (unsigned)(g.n_w + 3)) continue;
+            const float base = arr_base32(g, A.E0, A.k0, k4);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (((need >> e) & 1u) && (unsigned)(k4 + e - A.k0) < (unsigned)g.n_w)
+                    kahan_add32(a2[e], c2[e], __fmul_rn(base, g.rho_f[e]));
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (!((need >> e) & 1u)) continue;
+            if (cnv[e] != 0.f) kahan_add32(a2[e], c2[e], cnv[e]);
+            const float V = vv[e], sm = sv[e];
+            const float Vr = a2[e] - c2[e];
+            const float q = __fmul_rn(__fmul_rn(sm, sm), __fsub_rn(rcp_sfu(Vr), rcp_sfu(V)));
+            term[e] = __fmul_rn(-0.5f, __fadd_rn(__logf(__fdividef(Vr, V)), q));
+        }
+    }
+    return __fadd_rn(__fadd_rn(__fadd_rn(term[0], term[1]), term[2]), term[3]);
+}
+
 // ---------------------------------------------------------------------------
 // pricing of step buffer sl by warps 1..: the change of the Gaussian
 // log-likelihood over the float4 groups of all tasks (one flat range; each
@@ -609,78 +694,7 @@ __device__ __forceinline__ void price_step(const Geo& g, const Dev& d, Sm& S, in
 #pragma unroll
         for (int r = 0; r < kUnroll; ++r) {
             if (ti_[r] < 0) continue;
-            const T32& T = tk[ti_[r]];
-            const int k4 = k_[r];
-            // one SFU evaluation per arrival for the whole group (see arr_var32)
-            const float bo = T.has_o ? arr_base32(g, T.E0o, T.k0o, k4) : 0.f;
-            const float bn = T.has_n ? arr_base32(g, T.E0n, T.k0n, k4) : 0.f;
-            const float sv[4] = {s4[r].x, s4[r].y, s4[r].z, s4[r].w};
-            const float vv[4] = {v4[r].x, v4[r].y, v4[r].z, v4[r].w};
-            float term[4], cnv[4];
-            unsigned need = 0;   // samples whose V' is rebuilt from the arrivals that stay
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int kk = k4 + e;
-                const bool io = T.has_o && (unsigned)(kk - T.k0o) < (unsigned)g.n_w;
-                const bool inn = T.has_n && (unsigned)(kk - T.k0n) < (unsigned)g.n_w;
-                // the same per-sample values the variance synthesis adds, so the
-                // priced change is the change written to V on accept
-                const float co = io ? __fmul_rn(bo, g.rho_f[e]) : 0.f;
-                const float cn = inn ? __fmul_rn(bn, g.rho_f[e]) : 0.f;
-                const float dd = cn - co;
-                cnv[e] = cn;
-                term[e] = 0.f;
-                if (MEAN && kk < T.hi && dd != 0.f) {
-                    // additive reading: (d (s - mu) - d^2 / 2) / noise, mu = vv
-                    term[e] = __fmul_rn(g.inv_noise_f, __fsub_rn(__fmul_rn(dd, __fsub_rn(sv[e], vv[e])),
-                                                                 __fmul_rn(0.5f, __fmul_rn(dd, dd))));
-                } else if (!MEAN && kk < T.hi && dd != 0.f) {
-                    const float V = vv[e], sm = sv[e];
-                    const float Vp = V + dd;
-                    if (Vp < 0.5f * V) {
-                        need |= 1u << e;   // the changed arrival dominates V
-                    } else {
-                        // log(V'/V) - s^2 d / (V V'), one reciprocal (explicitly
-                        // rounded, so every build of this code gives the same bits)
-                        const float inv = rcp_sfu(__fmul_rn(V, Vp));
-                        const float x = __fmul_rn(__fmul_rn(dd, Vp), inv);
-                        const float q = __fmul_rn(__fmul_rn(sm, sm), __fmul_rn(dd, inv));
-                        term[e] = __fmul_rn(-0.5f, __fsub_rn(log1p_fast(x), q));
-                    }
-                }
-            }
-            if (need) {
-                // V' of the flagged samples from the arrivals that stay on this
-                // station (list order, compensated), one SFU evaluation per
-                // arrival for the group; the candidate's own arrival last
-                float a2[4], c2[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    a2[e] = g.syn0_f;
-                    c2[e] = 0.f;
-                }
-                const SA* L = S.sarr + T.slot * g.frz_cap;
-                const int nl = S.scnt[T.slot];
-                for (int o = 0; o < nl; ++o) {
-                    const SA A = L[o];
-                    if (A.own == T.skip || (unsigned)(k4 + 3 - A.k0) >= (unsigned)(g.n_w + 3)) continue;
-                    const float base = arr_base32(g, A.E0, A.k0, k4);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (((need >> e) & 1u) && (unsigned)(k4 + e - A.k0) < (unsigned)g.n_w)
-                            kahan_add32(a2[e], c2[e], __fmul_rn(base, g.rho_f[e]));
-                }
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    if (!((need >> e) & 1u)) continue;
-                    if (cnv[e] != 0.f) kahan_add32(a2[e], c2[e], cnv[e]);
-                    const float V = vv[e], sm = sv[e];
-                    const float Vr = a2[e] - c2[e];
-                    const float q = __fmul_rn(__fmul_rn(sm, sm), __fsub_rn(rcp_sfu(Vr), rcp_sfu(V)));
-                    term[e] = __fmul_rn(-0.5f, __fadd_rn(__logf(__fdividef(Vr, V)), q));
-                }
-            }
-            kahan_add32(acc, comp, __fadd_rn(__fadd_rn(__fadd_rn(term[0], term[1]), term[2]), term[3]));
+            kahan_add32(acc, comp, group_terms<MEAN>(g, S, tk[ti_[r]], k_[r], s4[r], v4[r]));
         }
     }
     float2 v = make_float2(acc, -comp);
@@ -691,6 +705,94 @@ __device__ __forceinline__ void price_step(const Geo& g, const Dev& d, Sm& S, in
         v = ff_add32(v, w2);
     }
     if (lane == 0) S.redf[wid] = v;
+}
+
+// add the window [lo, hi) priced at blanket slot `slot` to the slot's disjoint
+// intervals (one thread): every interval it overlaps or touches is merged
+// into it; with no room left it is counted on its own (an upper bound)
+__device__ __forceinline__ void iv_add(Sm& S, int slot, int lo, int hi) {
+    int2* L = S.uiv + slot * kIv;
+    const int n = S.un[slot];
+    int w = 0;
+    for (int i = 0; i < n; ++i) {
+        const int2 a = L[i];
+        if (a.x <= hi && lo <= a.y) {
+            lo = min(lo, a.x);
+            hi = max(hi, a.y);
+        } else {
+            L[w++] = a;
+        }
+    }
+    if (w < kIv) L[w++] = make_int2(lo, hi);
+    else S.cnt[11] += (unsigned long long)(hi - lo);
+    S.un[slot] = w;
+}
+
+// the decision of step `step` held in buffer sl (lane 0 of warp 0): count it,
+// record it, and on a commit update the region's event bookkeeping; rm / put
+// receive the event whose arrivals leave / join the station lists (-1: none).
+// t is the float-float sum of the step's partial log-likelihood changes.
+__device__ __forceinline__ int decide_lane0(const Geo& g, const Dev& d, Sm& S, long long sweep, int cell, int step,
+                                         int sl, float2 t, int valid, int& rm, int& put) {
+    const int type = S.type[sl], n_own = S.n_own, idx = S.idx[sl];
+    const D32& dr = S.draws[step];
+    ++S.cnt[type];
+    double dll = 0.0, la = -INFINITY, dlp = 0.0;
+    int acc = 0;
+    if (valid) {
+        ++S.cnt[3 + type];
+        if (g.count_unique) {
+            const T32* tk = S.tasks + sl * g.task_cap;
+            for (int ti = 0; ti < S.ntask[sl]; ++ti) iv_add(S, tk[ti].slot, tk[ti].lo, tk[ti].hi);
+        }
+        S.cnt[9] += (unsigned long long)S.width[sl];
+        // float32 first: its gap to the threshold errs by < 3e-7
+        // (|t.x| + |thr|), so outside 1e-5 of that it decides as
+        // float64 would; inside, float64 decides
+        const float gap = (t.x + t.y) - S.thrf[sl];
+        const float tol = 1e-5f * (fabsf(t.x) + fabsf(S.thrf[sl])) + 1e-30f;
+        if (gap > tol || gap < -tol) {
+            acc = gap > 0.f;
+            if (acc || d.trace) dll = (double)t.x + (double)t.y;
+        } else {
+            dll = (double)t.x + (double)t.y;
+            acc = dll > S.thr[sl];
+        }
+        dlp = S.dlp[sl];
+        if (d.trace) la = dll + ((double)dr.logu - S.thr[sl]);
+    }
+    if (d.trace) {
+        const long long slot = ((sweep - d.trace_sweep0) * g.n_cells + cell) * (long long)g.k + step;
+        if (slot >= 0 && slot < d.trace_cap) {
+            cmh_trace& R = d.trace[slot];
+            R.sweep = (int)sweep; R.cell = cell; R.step = step; R.type = type;
+            R.evaluated = valid; R.accepted = acc; R.n_before = n_own; R.written = 1;
+            R.dll = dll; R.log_alpha = la;
+        }
+    }
+    const int do_commit = acc && g.commit;
+    if (acc) ++S.cnt[6 + type];
+    if (do_commit) {
+        S.cnt[10] += (unsigned long long)S.width[sl];
+        S.region_dlp += dll + dlp;
+        if (type == 1) {
+            const int ps = S.order[idx];
+            rm = ps;
+            for (int q = idx; q + 1 < n_own; ++q) S.order[q] = S.order[q + 1];
+            S.freel[S.n_free++] = ps;
+            S.n_own = n_own - 1;
+        } else if (type == 0) {
+            const int ps = S.freel[--S.n_free];
+            S.eid[ps] = ((unsigned long long)(sweep + 1) << 32) | ((unsigned long long)cell << 12) |
+                        (unsigned long long)step;
+            S.order[n_own] = ps;
+            S.n_own = n_own + 1;
+            put = ps;
+        } else {
+            rm = put = S.order[idx];
+        }
+    }
+    return do_commit;
 }
 
 // remove the arrivals of own event ps from its stations' lists, keeping the
@@ -735,6 +837,55 @@ __device__ __forceinline__ void lists_add(const Geo& g, Sm& S, int ps, const A32
     }
 }
 
+// the committed candidate of buffer sl becomes own event ps (one thread):
+// its master, density term, relative position and arrival cache, and its
+// arrivals join the station lists
+__device__ __forceinline__ void put_event(const Geo& g, const Dev& d, Sm& S, int sl, int ps) {
+    const P32& c = S.c[sl];
+    const A32* cd = S.cand + sl * g.arr_cap;
+    S.mx[ps] = c.x; S.my[ps] = c.y; S.mt[ps] = c.t; S.mm[ps] = c.m;
+    // a move's own log alpha has no position term: the moved event's term
+    // (for a later death) is taken here
+    S.elq[ps] = S.type[sl] == 0 ? c.lq : (g.bt_on ? bt_lq(g, d, S, c.x, c.y, c.t, c.m) : S.lq_unif);
+    S.exr[ps] = c.xr; S.eyr[ps] = c.yr;
+    for (int a = 0; a < S.ncand[sl]; ++a) S.earr[ps * g.arr_cap + a] = cd[a];
+    S.enarr[ps] = S.ncand[sl];
+    lists_add(g, S, ps, cd, S.ncand[sl]);
+}
+
+// re-synthesise V over the windows of buffer sl's tasks from the station
+// lists (threads rt of rn): groups of four samples, one SFU evaluation per
+// arrival and group, compensated sums in list order
+__device__ __forceinline__ void resynth(const Geo& g, const Dev& d, const Sm& S, int sl, int rt, int rn) {
+    const T32* tk = S.tasks + sl * g.task_cap;
+    for (int ti = 0; ti < S.ntask[sl]; ++ti) {
+        const T32& T = tk[ti];
+        const SA* L = S.sarr + T.slot * g.frz_cap;
+        const int nl = S.scnt[T.slot];
+        float* vrow = (float*)d.V + (size_t)T.row * g.pitch;
+        for (int k4 = ((T.lo >> 2) + rt) << 2; k4 < T.hi; k4 += rn << 2) {
+            float a2[4], c2[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                a2[e] = g.syn0_f;
+                c2[e] = 0.f;
+            }
+            for (int o = 0; o < nl; ++o) {
+                const SA A = L[o];
+                if ((unsigned)(k4 + 3 - A.k0) >= (unsigned)(g.n_w + 3)) continue;
+                const float base = arr_base32(g, A.E0, A.k0, k4);
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if ((unsigned)(k4 + e - A.k0) < (unsigned)g.n_w)
+                        kahan_add32(a2[e], c2[e], __fmul_rn(base, g.rho_f[e]));
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (k4 + e >= T.lo && k4 + e < T.hi) vrow[k4 + e] = a2[e] - c2[e];
+        }
+    }
+}
+
 // the mbarriers of the staging buffers, once per CTA (their phase bits carry
 // over from one region to the next; every region leaves no copy in flight)
 template <bool STAGE>
@@ -749,16 +900,22 @@ __device__ __forceinline__ void init_staging(Sm& S) {
     }
 }
 
-// one colour phase of one region (every thread of the CTA): load the region,
-// run its k MH steps, write it back.  MEAN: the additive likelihood reading
-// (a kernel per reading, so each pricing loop is compiled for its own)
-template <bool STAGE, bool MEAN>
-__device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cell, long long sweep, Sm& S,
+// one colour phase of one region, in two parts (every thread of the CTA).
+// region_begin: what does not depend on the neighbouring regions' state --
+// the region's rectangle, its own events, the acceptance constants, the
+// blanket stations, the own events' arrival caches and the k steps' random
+// draws; a kernel whose regions wait for their lower-colour neighbours runs
+// it before that wait.  Returns false (uniformly) after latching an error.
+template <bool STAGE>
+__device__ __forceinline__ bool region_begin(const Geo& g, const Dev& d, int cell, long long sweep, Sm& S,
                                              unsigned char* smem) {
     const Store St = d.st[sweep & 1];
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
     const int ix = cell % g.ncx, iy = cell / g.ncx;
     const int start = St.start[cell], n0 = St.count[cell];
+    (void)ix;
+    (void)iy;
+    (void)start;
     if (tid == 0) {
         layout32(g, &S, smem, g.spill ? d.spill_buf + (size_t)blockIdx.x * (size_t)g.spill_bytes : nullptr);
         S.cell = cell;
@@ -777,12 +934,12 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
         S.region_dlp = 0.0;
         S.acc = 0;
     }
-    if (tid < 11) S.cnt[tid] = 0;
+    if (tid < 12) S.cnt[tid] = 0;
     // only thread 0 has S.err initialised yet: the others would read what an
     // earlier CTA left in this shared memory
     if (__syncthreads_or(tid == 0 && S.err != 0)) {
         if (tid == 0) latch(d.status, S.err);
-        return;
+        return false;
     }
     const double X0 = S.X0, Y0 = S.Y0;
     // ---- own events: masters, relative position, free list ----------------------
@@ -889,6 +1046,8 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
         __syncthreads();
     }
     const int n_blk = S.n_blk;
+    if (g.count_unique)
+        for (int b = tid; b < n_blk; b += nthr) S.un[b] = 0;
     // position terms of the own events (the death Hastings term)
     for (int i = tid; i < n0; i += nthr)
         S.elq[i] = g.bt_on ? bt_lq(g, d, S, S.mx[i], S.my[i], S.mt[i], S.mm[i]) : S.lq_unif;
@@ -913,6 +1072,98 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
             S.enarr[i] = min(na, g.arr_cap);
         }
     }
+    // ---- the k steps' random draws (Philox stream 0, counter (sweep, cell, step, 0|1))
+    const unsigned long long thr_b = (unsigned long long)ceil(g.p_birth * 9007199254740992.0);
+    const unsigned long long thr_d = (unsigned long long)ceil(__dadd_rn(g.p_birth, g.p_death) * 9007199254740992.0);
+    // one warp, warp 1, draws them: the float64 of the walk offsets (~250
+    // float64 instructions, each holding its sub-partition's float64 pipe for
+    // ~64 cycles whatever the number of active lanes) then runs on a
+    // sub-partition whose float64 pipe no manager warp (warp 0 of every
+    // resident CTA: the decisions) uses
+    for (int st = wid == 1 ? lane : g.k; st < g.k; st += 32) {
+        unsigned long long c0[4] = {(unsigned long long)sweep, (unsigned long long)cell, (unsigned long long)st, 0ULL};
+        unsigned long long c1[4] = {(unsigned long long)sweep, (unsigned long long)cell, (unsigned long long)st, 1ULL};
+        philox4x64(c0, g.seed, 0ULL);
+        philox4x64(c1, g.seed, 0ULL);
+        D32 D;
+        const unsigned long long u53 = c0[0] >> 11;   // u < p  <=>  u53 < p 2^53 (rounded up)
+        D.type = u53 < thr_b ? 0 : (u53 < thr_d ? 1 : 2);
+        D.pickw = (unsigned)(c0[1] & 0xffffffffULL);
+        D.logu = __logf(u32o(c1[2]));
+        D.bvalid = 0;
+        D.bK = 0;
+        D.pad = 0;
+        D.bx = D.by = D.bt = D.bm = D.blb = D.blq = 0.0;
+        if (D.type == 0) {
+            P32 e;
+            bool drew_m = false;
+            if (g.bt_on && S.bt_last >= 0 && u01(c1[3]) < g.bt_mix) {
+                drew_m = learned_birth(g, d, S, sweep, cell, st, c0[2], c0[3], e);
+            } else {
+                e.x = __dadd_rn(S.rect[0], __dmul_rn(u01(c0[2]), __dsub_rn(S.rect[1], S.rect[0])));
+                e.y = __dadd_rn(S.rect[2], __dmul_rn(u01(c0[3]), __dsub_rn(S.rect[3], S.rect[2])));
+                e.t = __dmul_rn(u01(c1[0]), g.T);
+            }
+            if (!drew_m) e.m = mag_from_u53(c1[1]);
+            D.blq = g.bt_on ? bt_lq(g, d, S, e.x, e.y, e.t, e.m) : S.lq_unif;
+            to_rel(g, X0, Y0, e);
+            D.bx = e.x; D.by = e.y; D.bt = e.t; D.bm = e.m;
+            D.blb = g.lb0 - e.m;
+            D.xr = e.xr; D.yr = e.yr; D.ph = e.ph; D.mf = e.mf; D.bK = e.K;
+            // inside [r0, r1) x [r2, r3) by construction up to rounding at the
+            // edges: decide in float32 away from them, exactly near them
+            const bool sure = e.xr >= S.rl[0] + kDr && e.xr < S.rl[1] - kDr && e.yr >= S.rl[2] + kDr &&
+                              e.yr < S.rl[3] - kDr && e.K >= 1 && e.K + 2 <= g.TfK;
+            D.bvalid = sure || inside_exact(g, S.sx, S.sy, cell, e.x, e.y, e.t, e.m);
+        } else if (D.type == 2) {
+            // the walk offset in float64, the same definition as the float64
+            // form (Box-Muller, each Gaussian rounded to 2^-20, signs from
+            // word 1): the float64 candidate is then the one the exact chain
+            // proposes, not one a float32 rounding away from it, so the
+            // float32 terms price the same candidate (an arrival's first
+            // sample can change for a candidate a millimetre away).  Computed
+            // here, for all k steps at once, off the step chain.
+            const double r1 = __dsqrt_rn(__dmul_rn(-2.0, log(u01o(c0[2]))));
+            const double th1 = __dmul_rn(6.283185307179586, u01(c0[3]));
+            const double r2 = __dsqrt_rn(__dmul_rn(-2.0, log(u01o(c1[0]))));
+            const double th2 = __dmul_rn(6.283185307179586, u01(c1[1]));
+            const double z[4] = {__dmul_rn(r1, cos(th1)), __dmul_rn(r1, sin(th1)), __dmul_rn(r2, cos(th2)),
+                                 __dmul_rn(r2, sin(th2))};
+            const double sg[4] = {g.sig_xy, g.sig_xy, g.sig_t, g.sig_m};
+            double o[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                double q = __dmul_rn(rint(__dmul_rn(fabs(z[i]), 1048576.0)), 1.0 / 1048576.0);
+                if ((c0[1] >> (32 + i)) & 1ULL) q = -q;
+                o[i] = __dmul_rn(sg[i], q);
+            }
+            D.bx = o[0]; D.by = o[1]; D.bt = o[2]; D.bm = o[3];
+            D.xr = (float)o[0]; D.yr = (float)o[1]; D.ph = (float)o[2]; D.mf = (float)o[3];
+        } else {
+            D.xr = D.yr = D.ph = D.mf = 0.f;
+        }
+        S.draws[st] = D;
+    }
+    if (__syncthreads_or(S.err != 0)) {
+        if (tid == 0) latch(d.status, S.err);
+        return false;
+    }
+    return true;
+
+}
+
+// region_rest: the station arrival lists (the neighbouring regions' events,
+// read once they have finished this sweep, then the own events), the k MH
+// steps and the write-back of the region's events.  MEAN: the additive
+// likelihood reading (a kernel per reading, so each pricing loop is compiled
+// for its own)
+template <bool STAGE, bool MEAN>
+__device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell, long long sweep, Sm& S) {
+    const Store St = d.st[sweep & 1];
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+    const int ix = cell % g.ncx, iy = cell / g.ncx;
+    const int start = St.start[cell], n0 = S.n_own;
+    const int n_blk = S.n_blk;
     // ---- station lists: arrivals of the neighbouring cells (other colours) in
     // (cell, id) order, then the region's own events in id order
     for (int b = tid; b < n_blk; b += nthr) S.scnt[b] = 0;
@@ -1004,70 +1255,6 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
         }
         __syncwarp();
     }
-    // ---- the k steps' random draws (Philox stream 0, counter (sweep, cell, step, 0|1))
-    const unsigned long long thr_b = (unsigned long long)ceil(g.p_birth * 9007199254740992.0);
-    const unsigned long long thr_d = (unsigned long long)ceil(__dadd_rn(g.p_birth, g.p_death) * 9007199254740992.0);
-    for (int st = tid; st < g.k; st += nthr) {
-        unsigned long long c0[4] = {(unsigned long long)sweep, (unsigned long long)cell, (unsigned long long)st, 0ULL};
-        unsigned long long c1[4] = {(unsigned long long)sweep, (unsigned long long)cell, (unsigned long long)st, 1ULL};
-        philox4x64(c0, g.seed, 0ULL);
-        philox4x64(c1, g.seed, 0ULL);
-        D32 D;
-        const unsigned long long u53 = c0[0] >> 11;   // u < p  <=>  u53 < p 2^53 (rounded up)
-        D.type = u53 < thr_b ? 0 : (u53 < thr_d ? 1 : 2);
-        D.pickw = (unsigned)(c0[1] & 0xffffffffULL);
-        D.logu = __logf(u32o(c1[2]));
-        D.bvalid = 0;
-        D.bK = 0;
-        D.pad = 0;
-        D.bx = D.by = D.bt = D.bm = D.blb = D.blq = 0.0;
-        if (D.type == 0) {
-            P32 e;
-            bool drew_m = false;
-            if (g.bt_on && S.bt_last >= 0 && u01(c1[3]) < g.bt_mix) {
-                drew_m = learned_birth(g, d, S, sweep, cell, st, c0[2], c0[3], e);
-            } else {
-                e.x = __dadd_rn(S.rect[0], __dmul_rn(u01(c0[2]), __dsub_rn(S.rect[1], S.rect[0])));
-                e.y = __dadd_rn(S.rect[2], __dmul_rn(u01(c0[3]), __dsub_rn(S.rect[3], S.rect[2])));
-                e.t = __dmul_rn(u01(c1[0]), g.T);
-            }
-            if (!drew_m) e.m = mag_from_u53(c1[1]);
-            D.blq = g.bt_on ? bt_lq(g, d, S, e.x, e.y, e.t, e.m) : S.lq_unif;
-            to_rel(g, X0, Y0, e);
-            D.bx = e.x; D.by = e.y; D.bt = e.t; D.bm = e.m;
-            D.blb = g.lb0 - e.m;
-            D.xr = e.xr; D.yr = e.yr; D.ph = e.ph; D.mf = e.mf; D.bK = e.K;
-            // inside [r0, r1) x [r2, r3) by construction up to rounding at the
-            // edges: decide in float32 away from them, exactly near them
-            const bool sure = e.xr >= S.rl[0] + kDr && e.xr < S.rl[1] - kDr && e.yr >= S.rl[2] + kDr &&
-                              e.yr < S.rl[3] - kDr && e.K >= 1 && e.K + 2 <= g.TfK;
-            D.bvalid = sure || inside_exact(g, S.sx, S.sy, cell, e.x, e.y, e.t, e.m);
-        } else if (D.type == 2) {
-            const float u2 = (float)(c0[3] >> 40) * (1.0f / 16777216.0f);
-            const float u4 = (float)(c1[1] >> 40) * (1.0f / 16777216.0f);
-            const float r1 = sqrtf(-2.f * __logf(u32o(c0[2]))), r2 = sqrtf(-2.f * __logf(u32o(c1[0])));
-            float s1, co1, s2, co2;
-            __sincosf(6.2831853071795865f * u2, &s1, &co1);
-            __sincosf(6.2831853071795865f * u4, &s2, &co2);
-            float z[4] = {r1 * co1, r1 * s1, r2 * co2, r2 * s2};
-            const float sg[4] = {(float)g.sig_xy, (float)g.sig_xy, (float)g.sig_t, (float)g.sig_m};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                float q = rintf(fabsf(z[i]) * 1048576.f) * (1.f / 1048576.f);
-                if ((c0[1] >> (32 + i)) & 1ULL) q = -q;
-                z[i] = sg[i] * q;
-            }
-            D.xr = z[0]; D.yr = z[1]; D.ph = z[2]; D.mf = z[3];
-        } else {
-            D.xr = D.yr = D.ph = D.mf = 0.f;
-        }
-        S.draws[st] = D;
-    }
-    if (__syncthreads_or(S.err != 0)) {
-        if (tid == 0) latch(d.status, S.err);
-        return;
-    }
-
     if (wid == 0) prepare_step<STAGE>(g, d, S, 0, 0);
     __syncthreads();
     for (int step = 0; step < g.k; ++step) {
@@ -1096,85 +1283,19 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
             }
             int rm = -1, put = -1;   // event leaving its station lists / event (re)joining them
             if (lane == 0) {
-                const int type = S.type[sl], n_own = S.n_own, idx = S.idx[sl];
-                const D32& dr = S.draws[step];
                 if (STAGE && S.on[sl]) {   // this buffer's copies have landed (the workers waited)
                     if (!mbar_wait(&S.bar[sl], (unsigned)S.ph[sl])) S.err = CMH_ERR_TIMEOUT;
                     S.ph[sl] ^= 1;
                     S.on[sl] = 0;
                 }
-                ++S.cnt[type];
-                double dll = 0.0, la = -INFINITY, dlp = 0.0;
-                int acc = 0;
-                if (valid) {
-                    ++S.cnt[3 + type];
-                    S.cnt[9] += (unsigned long long)S.width[sl];
-                    // float32 first: its gap to the threshold errs by < 3e-7
-                    // (|t.x| + |thr|), so outside 1e-5 of that it decides as
-                    // float64 would; inside, float64 decides
-                    const float gap = (t.x + t.y) - S.thrf[sl];
-                    const float tol = 1e-5f * (fabsf(t.x) + fabsf(S.thrf[sl])) + 1e-30f;
-                    if (gap > tol || gap < -tol) {
-                        acc = gap > 0.f;
-                        if (acc || d.trace) dll = (double)t.x + (double)t.y;
-                    } else {
-                        dll = (double)t.x + (double)t.y;
-                        acc = dll > S.thr[sl];
-                    }
-                    dlp = S.dlp[sl];
-                    if (d.trace) la = dll + ((double)dr.logu - S.thr[sl]);
-                }
-                if (d.trace) {
-                    const long long slot = ((sweep - d.trace_sweep0) * g.n_cells + cell) * (long long)g.k + step;
-                    if (slot >= 0 && slot < d.trace_cap) {
-                        cmh_trace& R = d.trace[slot];
-                        R.sweep = (int)sweep; R.cell = cell; R.step = step; R.type = type;
-                        R.evaluated = valid; R.accepted = acc; R.n_before = n_own; R.written = 1;
-                        R.dll = dll; R.log_alpha = la;
-                    }
-                }
-                const int do_commit = acc && g.commit;
-                if (acc) ++S.cnt[6 + type];
-                if (do_commit) {
-                    S.cnt[10] += (unsigned long long)S.width[sl];
-                    S.region_dlp += dll + dlp;
-                    if (type == 1) {
-                        const int ps = S.order[idx];
-                        rm = ps;
-                        for (int q = idx; q + 1 < n_own; ++q) S.order[q] = S.order[q + 1];
-                        S.freel[S.n_free++] = ps;
-                        S.n_own = n_own - 1;
-                    } else if (type == 0) {
-                        const int ps = S.freel[--S.n_free];
-                        S.eid[ps] = ((unsigned long long)(sweep + 1) << 32) | ((unsigned long long)cell << 12) |
-                                    (unsigned long long)step;
-                        S.order[n_own] = ps;
-                        S.n_own = n_own + 1;
-                        put = ps;
-                    } else {
-                        rm = put = S.order[idx];
-                    }
-                }
-                S.acc = do_commit;
+                S.acc = decide_lane0(g, d, S, sweep, cell, step, sl, t, valid, rm, put);
             }
             // the removed or moved event's arrivals leave their station lists
             // (all lanes), then the new arrivals join (lane 0)
             rm = __shfl_sync(FULL, rm, 0);
             put = __shfl_sync(FULL, put, 0);
             if (rm >= 0) lists_remove_warp(g, S, rm);
-            if (lane == 0 && put >= 0) {
-                const int ps = put;
-                const P32& c = S.c[sl];
-                const A32* cd = S.cand + sl * g.arr_cap;
-                S.mx[ps] = c.x; S.my[ps] = c.y; S.mt[ps] = c.t; S.mm[ps] = c.m;
-                // a move's own log alpha has no position term: the moved
-                // event's term (for a later death) is taken here
-                S.elq[ps] = S.type[sl] == 0 ? c.lq : (g.bt_on ? bt_lq(g, d, S, c.x, c.y, c.t, c.m) : S.lq_unif);
-                S.exr[ps] = c.xr; S.eyr[ps] = c.yr;
-                for (int a = 0; a < S.ncand[sl]; ++a) S.earr[ps * g.arr_cap + a] = cd[a];
-                S.enarr[ps] = S.ncand[sl];
-                lists_add(g, S, ps, cd, S.ncand[sl]);
-            }
+            if (lane == 0 && put >= 0) put_event(g, d, S, sl, put);
         }
         if (__syncthreads_or(S.err != 0)) break;
         // ================ commit: re-synthesise V on the touched windows ============
@@ -1183,38 +1304,11 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
         // while the workers re-synthesise V; with staging its bulk copies
         // read V, so it follows the re-synthesis.
         if (S.acc) {
-            const T32* tk = S.tasks + sl * g.task_cap;
             const int rt = STAGE ? tid : tid - 32, rn = STAGE ? nthr : nthr - 32;
             if (!STAGE && wid == 0) {
                 if (step + 1 < g.k) prepare_step<STAGE>(g, d, S, step + 1, sl ^ 1);
             } else {
-                for (int ti = 0; ti < S.ntask[sl]; ++ti) {
-                    const T32& T = tk[ti];
-                    const SA* L = S.sarr + T.slot * g.frz_cap;
-                    const int nl = S.scnt[T.slot];
-                    float* vrow = (float*)d.V + (size_t)T.row * g.pitch;
-                    // groups of four samples: one SFU evaluation per arrival and group
-                    for (int k4 = ((T.lo >> 2) + rt) << 2; k4 < T.hi; k4 += rn << 2) {
-                        float a2[4], c2[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            a2[e] = g.syn0_f;
-                            c2[e] = 0.f;
-                        }
-                        for (int o = 0; o < nl; ++o) {
-                            const SA A = L[o];
-                            if ((unsigned)(k4 + 3 - A.k0) >= (unsigned)(g.n_w + 3)) continue;
-                            const float base = arr_base32(g, A.E0, A.k0, k4);
-#pragma unroll
-                            for (int e = 0; e < 4; ++e)
-                                if ((unsigned)(k4 + e - A.k0) < (unsigned)g.n_w)
-                                    kahan_add32(a2[e], c2[e], __fmul_rn(base, g.rho_f[e]));
-                        }
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (k4 + e >= T.lo && k4 + e < T.hi) vrow[k4 + e] = a2[e] - c2[e];
-                    }
-                }
+                resynth(g, d, S, sl, rt, rn);
             }
             if (STAGE) {
                 fence_async_global();   // the new V is visible to the next bulk copies
@@ -1249,7 +1343,21 @@ __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cel
         d.region_dlp[cell] = S.region_dlp;
         for (int t = 0; t < 11; ++t)
             if (S.cnt[t]) atomicAdd(&d.stats[t], S.cnt[t]);
+        if (g.count_unique) {
+            unsigned long long u = S.cnt[11];
+            for (int b = 0; b < S.n_blk; ++b)
+                for (int j = 0; j < S.un[b]; ++j) u += (unsigned long long)(S.uiv[b * kIv + j].y - S.uiv[b * kIv + j].x);
+            if (u) atomicAdd(&d.stats[17], u);
+        }
     }
+}
+
+
+// both parts, for kernels without dependency waits
+template <bool STAGE, bool MEAN>
+__device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cell, long long sweep, Sm& S,
+                                             unsigned char* smem) {
+    if (region_begin<STAGE>(g, d, cell, sweep, S, smem)) region_rest<STAGE, MEAN>(g, d, cell, sweep, S);
 }
 
 // one colour phase: a CTA per region of the colour
@@ -1275,7 +1383,6 @@ __device__ __forceinline__ void st_release(long long* p, long long v) {
     asm volatile("st.release.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-constexpr unsigned kDepWaitLimit = 1u << 22;   // bounded waits for neighbouring regions
 
 // All colour phases of one sweep in one persistent launch.  Regions are
 // taken from a queue in colour order (colour 0's regions first, each
@@ -1313,8 +1420,12 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_kernel(const
         const int cell = s_cell;
         if (cell < 0) break;
         const long long sweep = s_sweep, stamp = sweep + 1;
+        const int colour_taken = s_run;
+        // the part of the region's phase that needs no neighbour runs while
+        // the lower-colour neighbours may still be running theirs
+        const bool begun = region_begin<STAGE>(g, d, cell, sweep, S, smem);
         if (threadIdx.x == 0) {
-            const int colour = s_run;
+            const int colour = colour_taken;
             const int P1 = g.period - 1, ix = cell % g.ncx, iy = cell / g.ncx;
             for (int jy = iy - P1; jy <= iy + P1; ++jy)
                 for (int jx = ix - P1; jx <= ix + P1; ++jx) {
@@ -1324,7 +1435,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_kernel(const
                     if (nb == cell || c < 0 || c >= colour) continue;
                     unsigned n = 0;
                     while (ld_acquire(d.done + nb) < stamp && !*(volatile int*)d.status) {
-                        if (++n >= kDepWaitLimit) {
+                        if (++n >= g.dep_wait_limit) {
                             latch(d.status, CMH_ERR_TIMEOUT);
                             break;
                         }
@@ -1332,12 +1443,12 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_kernel(const
                     }
                 }
             if (STAGE) fence_async_global();   // the neighbours' V writes before any bulk copy of them
-            s_run = *(volatile int*)d.status == 0;
+            s_run = begun && *(volatile int*)d.status == 0;
         }
         __syncthreads();
-        if (s_run) region_phase<STAGE, MEAN>(g, d, cell, sweep, S, smem);
+        if (s_run) region_rest<STAGE, MEAN>(g, d, cell, sweep, S);
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && cell != g.hold_cell) {
             __threadfence();
             st_release(d.done + cell, stamp);
         }
@@ -1427,6 +1538,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_batch(const 
         const Geo& g = G[inst];
         const Dev& d = D[inst];
         const long long sweep = s_sweep, stamp = sweep + 1;
+        const bool begun = region_begin<false>(g, d, cell, sweep, S, smem);
         if (threadIdx.x == 0) {
             const int colour = s_col;
             const int P1 = g.period - 1, ix = cell % g.ncx, iy = cell / g.ncx;
@@ -1438,19 +1550,19 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_batch(const 
                     if (nb == cell || c < 0 || c >= colour) continue;
                     unsigned k = 0;
                     while (ld_acquire(d.done + nb) < stamp && !*(volatile int*)d.status) {
-                        if (++k >= kDepWaitLimit) {
+                        if (++k >= g.dep_wait_limit) {
                             latch(d.status, CMH_ERR_TIMEOUT);
                             break;
                         }
                         __nanosleep(128);
                     }
                 }
-            s_run = *(volatile int*)d.status == 0;
+            s_run = begun && *(volatile int*)d.status == 0;
         }
         __syncthreads();
-        if (s_run) region_phase<false, MEAN>(g, d, cell, sweep, S, smem);
+        if (s_run) region_rest<false, MEAN>(g, d, cell, sweep, S);
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && cell != g.hold_cell) {
             __threadfence();
             st_release(d.done + cell, stamp);
         }

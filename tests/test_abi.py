@@ -130,3 +130,9 @@ def test_null_handles_of_the_learned_proposal_and_async_reads(cm):
     assert cm.lib.cmh_net_birth_table(None, None, None, None, 1, 1, 1, 1, 1.0, None, None) == -1
     assert cm.lib.cmh_net_param_count() > 2_000_000
     cm.lib.cmh_net_destroy(None)
+
+
+def test_alu_peaks_rejects_null_pointers(cm):
+    out = C.c_double()
+    assert cm.lib.cmh_measure_alu_peaks(None, C.byref(out), None) == -1
+    assert cm.lib.cmh_measure_alu_peaks(C.byref(out), None, None) == -1

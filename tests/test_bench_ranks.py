@@ -67,3 +67,57 @@ def test_cpu_legs_run_every_move_of_the_replay_workload():
     assert base["serial"]["cores"] == 1 and base["serial"]["value"] > 0 and base["serial"]["steps"] >= 1000
     st = {"proposed": [5, 6, 7], "pair": [2, 1, 0], "arrival": [3, 3, 1]}
     assert bench.n_proposals(st) == 23
+
+
+def _shard_rank(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    import worldgen
+    sizes = worldgen.batched_instances(256, seed=2000)
+    costs = [bench.instance_cost(S, p) for S, p in sizes]
+    mine = bench.shard_instances(costs, world, rank)
+    gathered = bench.gather_summaries({"rank": rank, "instances": mine, "cost": sum(costs[i] for i in mine)}, dist)
+    t, work = bench.reduce_max_sum(1.0 + rank, float(len(mine)), dist, "cpu")
+    q.put((rank, mine, gathered, t, work))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_split_the_batched_instances():
+    """The batched workload on two ranks: each rank computes its share of the
+    256 instances from the same cost estimates, with no communication; the
+    shares are disjoint, cover every instance and carry near-equal estimated
+    cost; the summaries gathered after the timed region are the same on both
+    ranks; time is the slowest rank's, work the sum."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted((q.get(timeout=120) for _ in procs), key=lambda o: o[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    a, b = out[0][1], out[1][1]
+    assert not set(a) & set(b) and sorted(a + b) == list(range(256))
+    assert out[0][2] == out[1][2] and [g["rank"] for g in out[0][2]] == [0, 1]
+    c0, c1 = out[0][2][0]["cost"], out[0][2][1]["cost"]
+    assert abs(c0 - c1) <= 0.02 * (c0 + c1)
+    assert [o[3] for o in out] == [2.0, 2.0] and [o[4] for o in out] == [256.0, 256.0]
+
+
+@pytest.mark.parametrize("n", [1, 3, 8])
+def test_instance_split_covers_and_balances(n):
+    sys.path.insert(0, ROOT)
+    import bench
+    import worldgen
+    costs = [bench.instance_cost(S, p) for S, p in worldgen.batched_instances(256, seed=2000)]
+    shares = [bench.shard_instances(costs, n, r) for r in range(n)]
+    flat = sorted(i for s in shares for i in s)
+    assert flat == list(range(256))
+    loads = [sum(costs[i] for i in s) for s in shares]
+    # largest-first greedy: no share exceeds another by more than one instance
+    assert max(loads) - min(loads) <= max(costs)

@@ -114,3 +114,56 @@ def test_mean_reading_batch_equals_each_model_alone():
         cm.create_batch([batched[0], mv])
     for m in alone + batched + [mv]:
         m.destroy()
+
+
+def test_batched_instances_match_oracle():
+    """Each instance of a batch, dry run (commit off) from its ground truth,
+    against the oracle on the same world and seed: the same steps with the
+    same move types and event counts, every float32 change of the
+    log-likelihood within 1e-4 (to max(|x|, 1)) of the oracle's.  Instances of
+    the batched workload's kind (uniform stations, uneven sizes), plus one
+    whose regions spill their lists to global memory (256 stations on
+    300 x 300 km)."""
+    import os
+    import oracle
+    from gpu_helpers import TRACE_KEYS
+    from test_gpu_dense import dense_world
+    cm = lib()
+    oracle.build()
+    rng = np.random.default_rng(91)
+    worlds = []
+    for i in range(4):
+        side = float(100 * rng.integers(3, 9))
+        p = worldgen.ModelParams(W=side, T=float(rng.choice([900.0, 1800.0, 2400.5])),
+                                 Lambda=float(rng.uniform(20, 200)) * (side / 500.0) ** 2)
+        st = worldgen.uniform_stations(int(rng.integers(16, 96)), side, 500 + i)
+        worlds.append(worldgen.make_world(p, st, 600 + i, np.float32))
+    worlds.append(dense_world(33))
+    k, sweeps = 16, 3
+    models = []
+    for i, w in enumerate(worlds):
+        m = cm.create_model(w.events, w.stations, w.signals,
+                            cm.make_params(w.params, k_per_phase=k, seed=70 + i, dtype=cm.F32, commit=False))
+        m.partition_and_color(w.params.L, shift_mode=1)
+        ncx = int(np.floor(w.params.W / w.params.L)) + 2
+        m.set_trace(sweeps * ncx * ncx * k)
+        models.append(m)
+    assert models[-1].read_state(cap=0)[3]["spill_bytes"] > 0
+    b = cm.create_batch(models)
+    b.run_sweeps(sweeps)
+    b.sync()
+    threads = min(16, os.cpu_count() or 1)
+    for i, (w, m) in enumerate(zip(worlds, models)):
+        tr = np.sort(m.read_trace(), order=TRACE_KEYS)
+        o = oracle.World(w, k_per_phase=k, seed=70 + i, commit=False)
+        _, _, otr, _ = o.run_chromatic(w.events, sweeps, trace_cap=len(tr) + 16, threads=threads)
+        otr = np.sort(otr, order=TRACE_KEYS)
+        assert len(tr) == len(otr) > 0, i
+        for key in ("sweep", "cell", "step", "type", "n_before", "evaluated"):
+            assert np.array_equal(tr[key], otr[key]), (i, key)
+        ev_ = otr["evaluated"] == 1
+        err = np.abs(tr["dll"][ev_] - otr["dll"][ev_]) / np.maximum(np.abs(otr["dll"][ev_]), 1.0)
+        assert ev_.sum() > 50 and err.max() <= 1e-4, (i, err.max())
+    b.destroy()
+    for m in models:
+        m.destroy()

@@ -260,6 +260,10 @@ def test_fp32_precision_at_scale_density(cm, orc):
            "p999": float(np.quantile(err, 0.999)), "max": float(err.max()),
            "pure_relative_max": float(rel.max()), "bound": 1e-4,
            "decisions_differing": int(np.count_nonzero(tr["accepted"][ev_] != otr["accepted"][ev_]))}
+    import bench
+    rec["kernel_sha256"] = bench._kernel_digest()
+    rec["command"] = ("python -m pytest tests/test_gpu_parity.py -m gpu -s "
+                      "-k test_fp32_precision_at_scale_density")
     print("FP32_ERROR " + json.dumps(rec))
     assert err.size >= 100000
     assert err.max() <= 1e-4

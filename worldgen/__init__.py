@@ -40,6 +40,7 @@ __all__ = [
     "config_replay",
     "config_scale",
     "config_batched",
+    "batched_instances",
     "subworld",
 ]
 
@@ -271,17 +272,28 @@ def config_scale(seed: int = 1000, dtype=np.float32, side_regions: int = 40,
     return make_world(p, jittered_grid_stations(side_regions, W, seed), seed, dtype)
 
 
-def config_batched(n_instances: int = 256, seed: int = 2000, dtype=np.float32):
-    """Uneven independent instances: S ~ logU[16,256] stations, Lambda ~ logU[10,500],
-    side ~ logU[200,2000] km (rounded to whole 100 km regions), T ~ logU[600,7200] s."""
+def batched_instances(n_instances: int = 256, seed: int = 2000):
+    """The draws that size each instance of the batched workload, in order:
+    (stations S, ModelParams) with S ~ logU[16,256], Lambda ~ logU[10,500],
+    side ~ logU[200,2000] km (rounded to whole 100 km regions), T ~
+    logU[600,7200] s.  Cheap: no signal is generated."""
     rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 0xBA7C])))
-    worlds = []
+    out = []
     for i in range(n_instances):
         S = int(round(math.exp(rng.uniform(math.log(16), math.log(256)))))
         lam = math.exp(rng.uniform(math.log(10), math.log(500)))
         side = 100.0 * max(2, round(math.exp(rng.uniform(math.log(200), math.log(2000))) / 100.0))
         T = math.exp(rng.uniform(math.log(600), math.log(7200)))
         T = float(int(T * 10) / 10.0)
-        p = ModelParams(W=side, T=T, Lambda=lam)
-        worlds.append(make_world(p, uniform_stations(S, side, seed + i), seed + 17 * i + 1, dtype))
-    return worlds
+        out.append((S, ModelParams(W=side, T=T, Lambda=lam)))
+    return out
+
+
+def config_batched(n_instances: int = 256, seed: int = 2000, dtype=np.float32, indices=None):
+    """Uneven independent instances (see batched_instances); ``indices``
+    generates only those instances (the others are sized but not drawn), in
+    the order given."""
+    sizes = batched_instances(n_instances, seed)
+    idx = range(n_instances) if indices is None else indices
+    return [make_world(sizes[i][1], uniform_stations(sizes[i][0], sizes[i][1].W, seed + i), seed + 17 * i + 1, dtype)
+            for i in idx]

@@ -799,8 +799,11 @@ def run_profile_case(args):
                                                                         dtype=cm.F32))
         net = cm.Net(max_batch=256, seed=7)
         net.train(m, args.warmup, 256, 3e-4)
-        loss = net.train(m, args.steps, 256, 3e-4)
-        print("training steps %d  loss %.4f" % (args.warmup + args.steps, loss))
+        t0 = time.perf_counter()
+        loss = net.train(m, args.steps, 256, 3e-4)   # returns after the stream has finished
+        dt = time.perf_counter() - t0
+        print("training steps %d  loss %.4f  %.3f ms per step of 256 windows" % (
+            args.warmup + args.steps, loss, 1e3 * dt / max(args.steps, 1)))
         net.destroy()
         m.destroy()
         return

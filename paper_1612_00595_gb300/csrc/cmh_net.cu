@@ -14,9 +14,10 @@
 // Loss: cross-entropy over the 4097 classes, Gaussian negative log-likelihood
 // of time and magnitude for windows that hold an event; AdamW.
 //
-// Every matrix product runs on the tensor cores in BF16 with FP32
-// accumulation (mma.sync m16n8k16; a convolution is a product with the
-// im2col matrix of its input, read in place by the tile loader);
+// Every matrix product runs on the fifth-generation tensor cores (tcgen05.mma,
+// BF16 operands staged in shared memory, FP32 accumulators in tensor memory;
+// a convolution is a product with the im2col matrix of its input, read in
+// place by the tile loader);
 // activations and gradients are kept in FP32, their BF16 copies feed the
 // products, and the parameters have FP32 masters with BF16 copies.
 #include <cuda_bf16.h>
@@ -60,248 +61,257 @@ constexpr long long kNParam = kOffFb2 + kNOut;
 // ---------------------------------------------------------------------------
 // C[M,N] = op(A)[M,K] op(B)[K,N] (+ C) (+ bias[n]) (ReLU), BF16 in, FP32 out.
 // A(m,k) = TA ? A[k*lda+m] : A[m*lda+k];  B(k,n) = TB ? B[n*ldb+k] : B[k*ldb+n].
-// 64 x 64 tiles, 4 warps of 32 x 32, K in steps of 32, mma m16n8k16.
 // Split K (gridDim.z > 1): split z covers K range [z kc, (z + 1) kc) and
 // writes its partial product to C + z M ldc (no bias, ReLU or accumulate);
 // sum_splits adds the partials in split order.
-// ---------------------------------------------------------------------------
-constexpr int GB = 64, GK = 32, GP = GK + 8;
-
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(128) gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, int lda,
-                                                 const __nv_bfloat16* B, int ldb, float* C, int ldc,
-                                                 const float* bias, int relu, int accumulate,
-                                                 __nv_bfloat16* Cb, int kc) {
-    __shared__ __align__(16) __nv_bfloat16 As[GB][GP];
-    __shared__ __align__(16) __nv_bfloat16 Bs[GB][GP];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int m0 = blockIdx.y * GB, n0 = blockIdx.x * GB;
-    const int grp = lane >> 2, tig = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-    const __nv_bfloat16 zero = __float2bfloat16(0.f);
-    const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
-    if (gridDim.z > 1) C += (long long)blockIdx.z * M * ldc;
-    for (int k0 = kb; k0 < ke; k0 += GK) {
-        for (int e = tid; e < GB * GK; e += 128) {
-            // A tile: As[m][k]; B tile stored transposed: Bs[n][k]
-            int r, c;
-            if (TA) { c = e / GB; r = e % GB; } else { r = e / GK; c = e % GK; }
-            const int gm = m0 + r, gk = k0 + c;
-            As[r][c] = (gm < M && gk < ke) ? (TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk]) : zero;
-            if (TB) { r = e / GK; c = e % GK; } else { c = e / GB; r = e % GB; }
-            const int gn = n0 + r, gk2 = k0 + c;
-            Bs[r][c] = (gn < N && gk2 < ke) ? (TB ? B[(long long)gn * ldb + gk2] : B[(long long)gk2 * ldb + gn]) : zero;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GK; kk += 16) {
-            unsigned a[2][4], b[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r0 = wm + i * 16 + grp;
-                a[i][0] = *reinterpret_cast<const unsigned*>(&As[r0][kk + tig * 2]);
-                a[i][1] = *reinterpret_cast<const unsigned*>(&As[r0 + 8][kk + tig * 2]);
-                a[i][2] = *reinterpret_cast<const unsigned*>(&As[r0][kk + tig * 2 + 8]);
-                a[i][3] = *reinterpret_cast<const unsigned*>(&As[r0 + 8][kk + tig * 2 + 8]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int nn = wn + j * 8 + grp;
-                b[j][0] = *reinterpret_cast<const unsigned*>(&Bs[nn][kk + tig * 2]);
-                b[j][1] = *reinterpret_cast<const unsigned*>(&Bs[nn][kk + tig * 2 + 8]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    asm volatile(
-                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-                        "{%8,%9}, {%0,%1,%2,%3};"
-                        : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-                        : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int m = m0 + wm + i * 16 + grp + (r >= 2 ? 8 : 0);
-                const int n = n0 + wn + j * 8 + tig * 2 + (r & 1);
-                if (m >= M || n >= N) continue;
-                float v = acc[i][j][r];
-                const long long o = (long long)m * ldc + n;
-                if (accumulate) v += C[o];
-                if (bias) v += bias[n];
-                if (relu) v = v > 0.f ? v : 0.f;
-                C[o] = v;
-                if (Cb) Cb[o] = __float2bfloat16(v);
-            }
-}
-
-// The same product with 16-byte tile loads: each operand is read in vectors
-// of 8 along its contiguous dimension (whose extent and leading dimension are
-// multiples of 8, base 16-byte aligned) and stored to shared memory as is or
-// transposed; two shared stages, so the next tile's loads are in flight while
-// the current tile is multiplied.  Same tiles, split K and epilogue.
 // a_lin > 0: A (not transposed) is the im2col matrix of the activation A
 // [B][a_lin][64] for a_lout output samples, read in place (row b a_lout + t,
 // column k 64 + c is x[b][2t - 2 + k][c], 0 outside); b_lin likewise for B
 // (not transposed; its rows are the im2col rows).
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(128) gemm_bf16_vec(int M, int N, int K, const __nv_bfloat16* A, int lda,
-                                                     const __nv_bfloat16* B, int ldb, float* C, int ldc,
-                                                     const float* bias, int relu, int accumulate,
-                                                     __nv_bfloat16* Cb, int kc, int a_lin, int a_lout,
-                                                     int b_lin, int b_lout) {
-    __shared__ __align__(16) __nv_bfloat16 As[2][GB][GP];
-    __shared__ __align__(16) __nv_bfloat16 Bs[2][GB][GP];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int m0 = blockIdx.y * GB, n0 = blockIdx.x * GB;
-    const int grp = lane >> 2, tig = lane & 3;
-    float acc[2][4][4];
+// ---------------------------------------------------------------------------
+// The product on the fifth-generation tensor cores (tcgen05).  A CTA of
+// 128 threads computes a 128 x 64 tile of C: per K tile of 64 the threads
+// stage op(A) [128 x 64] and op(B)^T [64 x 64] in shared memory in the
+// K-major canonical layout without swizzle (8 x 8 core matrices of 128
+// contiguous bytes, row r and column k of a tile at byte
+// (r / 8) * 1024 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2), then one
+// thread issues four tcgen05.mma (M = 128, N = 64, K = 16; BF16 operands,
+// FP32 accumulator in tensor memory: row m in TMEM lane m, column n in
+// column n of a 64-column allocation) and commits them to the stage's
+// mbarrier.  Two stages: the global loads of the next tile are in flight
+// while the tensor cores multiply the current one.  The epilogue reads the
+// accumulator with tcgen05.ld (warp w: lanes 32w..32w+31) and applies
+// accumulate / bias / ReLU / BF16 copy as the other kernels do.  Every
+// mbarrier wait is bounded; on a timeout the CTA records it in *err.
+// VEC: 16-byte operand loads along each operand's contiguous dimension (its
+// extent and leading dimension multiples of 8, base 16-byte aligned; 8
+// consecutive im2col columns are 8 consecutive channels of one input
+// sample); otherwise element-wise loads.
+// ---------------------------------------------------------------------------
+constexpr int TM = 128, TN = 64, TK = 64;
+constexpr unsigned kTcWaitLimit = 1u << 24;
+
+__device__ __forceinline__ unsigned tc_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: K-major, no swizzle; lbo = bytes between
+// core matrices adjacent along K, sbo = bytes between 8-row groups
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: D F32, A and B BF16, both K-major
+constexpr unsigned tc_idesc(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                       int accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(unsigned long long* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc_smem(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_bar_init(unsigned long long* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(bar)) : "memory");
+}
+
+// wait for the phase of parity `ph` of *bar to complete (bounded)
+__device__ __forceinline__ bool tc_bar_wait(unsigned long long* bar, unsigned ph) {
+    for (unsigned n = 0; n < kTcWaitLimit; ++n) {
+        unsigned done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(tc_smem(bar)), "r"(ph)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tc_ld16(unsigned taddr, float* v) {
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <bool TA, bool TB, bool VEC>
+__global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_bfloat16* A, int lda,
+                                               const __nv_bfloat16* B, int ldb, float* C, int ldc,
+                                               const float* bias, int relu, int accumulate, __nv_bfloat16* Cb,
+                                               int kc, int a_lin, int a_lout, int b_lin, int b_lout, int* err) {
+    extern __shared__ __align__(1024) unsigned char tsm[];   // [2] x (A 16 KB, B 8 KB)
+    __shared__ __align__(8) unsigned long long bar[2];
+    __shared__ unsigned s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
     const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
     if (gridDim.z > 1) C += (long long)blockIdx.z * M * ldc;
-    // vector v (0..255) of a 64 x 32 tile: along k (4 per row of 32) when the
-    // operand is k-contiguous, else along m / n (8 per column of 64)
-    uint4 ra[2], rb[2];
-    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-    auto load = [&](int k0) {
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int v = tid + i * 128;
-            if (!TA) {
-                const int gm = m0 + (v >> 2), gk = k0 + (v & 3) * 8;
-                if (a_lin > 0) {
-                    uint4 r = zero4;
-                    if (gm < M && gk < ke) {
-                        const int bb = gm / a_lout, t = gm - bb * a_lout, sx = 2 * t - 2 + (gk >> 6);
-                        if (sx >= 0 && sx < a_lin)
-                            r = __ldg(reinterpret_cast<const uint4*>(A + ((long long)bb * a_lin + sx) * kC + (gk & 63)));
-                    }
-                    ra[i] = r;
-                } else {
-                    ra[i] = (gm < M && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(A + (long long)gm * lda + gk))
-                                                : zero4;
-                }
-            } else {
-                const int gk = k0 + (v >> 3), gm = m0 + (v & 7) * 8;
-                ra[i] = (gm < M && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(A + (long long)gk * lda + gm)) : zero4;
-            }
-            if (TB) {
-                const int gn = n0 + (v >> 2), gk = k0 + (v & 3) * 8;
-                rb[i] = (gn < N && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(B + (long long)gn * ldb + gk)) : zero4;
-            } else {
-                const int gk = k0 + (v >> 3), gn = n0 + (v & 7) * 8;
-                if (b_lin > 0) {
-                    uint4 r = zero4;
-                    if (gn < N && gk < ke) {
-                        const int bb = gk / b_lout, t = gk - bb * b_lout, sx = 2 * t - 2 + (gn >> 6);
-                        if (sx >= 0 && sx < b_lin)
-                            r = __ldg(reinterpret_cast<const uint4*>(B + ((long long)bb * b_lin + sx) * kC + (gn & 63)));
-                    }
-                    rb[i] = r;
-                } else {
-                    rb[i] = (gn < N && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(B + (long long)gk * ldb + gn))
-                                                : zero4;
-                }
-            }
-        }
-    };
-    auto store = [&](int st) {
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int v = tid + i * 128;
-            if (!TA) {
-                *reinterpret_cast<uint4*>(&As[st][v >> 2][(v & 3) * 8]) = ra[i];
-            } else {
-                const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&ra[i]);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) As[st][(v & 7) * 8 + j][v >> 3] = e[j];
-            }
-            if (TB) {
-                *reinterpret_cast<uint4*>(&Bs[st][v >> 2][(v & 3) * 8]) = rb[i];
-            } else {
-                const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&rb[i]);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) Bs[st][(v & 7) * 8 + j][v >> 3] = e[j];
-            }
-        }
-    };
-    int st = 0;
-    if (kb < ke) {
-        load(kb);
-        store(0);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&s_tmem)),
+                     "r"(TN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    if (tid == 0) {
+        tc_bar_init(&bar[0]);
+        tc_bar_init(&bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
     __syncthreads();
-    for (int k0 = kb; k0 < ke; k0 += GK) {
-        const bool more = k0 + GK < ke;
-        if (more) load(k0 + GK);
+    tc_fence_after();
+    const unsigned tmem = s_tmem;
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    const __nv_bfloat16 zero = __float2bfloat16(0.f);
+    // element (r, k) of a staged K-major tile
+    auto at = [](unsigned char* base, int r, int k) {
+        return reinterpret_cast<__nv_bfloat16*>(base + (r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+    };
+    auto fill = [&](int st, int k0) {
+        unsigned char* As = tsm + st * 24576;
+        unsigned char* Bs = As + 16384;
+        if (VEC) {
+#pragma unroll 2
+            for (int i = 0; i < 8; ++i) {
+                const int v = tid + i * 128;
+                if (!TA) {   // 128 rows x 8 vectors along k
+                    const int r = v >> 3, c8 = (v & 7) * 8, gm = m0 + r, gk = k0 + c8;
+                    uint4 x = zero4;
+                    if (gm < M && gk < ke) {
+                        if (a_lin > 0) {
+                            const int bb = gm / a_lout, t = gm - bb * a_lout, sx = 2 * t - 2 + (gk >> 6);
+                            if (sx >= 0 && sx < a_lin)
+                                x = __ldg(reinterpret_cast<const uint4*>(A + ((long long)bb * a_lin + sx) * kC + (gk & 63)));
+                        } else {
+                            x = __ldg(reinterpret_cast<const uint4*>(A + (long long)gm * lda + gk));
+                        }
+                    }
+                    *reinterpret_cast<uint4*>(at(As, r, c8)) = x;
+                } else {     // 64 k x 16 vectors along m
+                    const int k = v >> 4, r8 = (v & 15) * 8, gm = m0 + r8, gk = k0 + k;
+                    uint4 x = (gm < M && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(A + (long long)gk * lda + gm))
+                                                  : zero4;
+                    const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&x);
 #pragma unroll
-        for (int kk = 0; kk < GK; kk += 16) {
-            unsigned a[2][4], b[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r0 = wm + i * 16 + grp;
-                a[i][0] = *reinterpret_cast<const unsigned*>(&As[st][r0][kk + tig * 2]);
-                a[i][1] = *reinterpret_cast<const unsigned*>(&As[st][r0 + 8][kk + tig * 2]);
-                a[i][2] = *reinterpret_cast<const unsigned*>(&As[st][r0][kk + tig * 2 + 8]);
-                a[i][3] = *reinterpret_cast<const unsigned*>(&As[st][r0 + 8][kk + tig * 2 + 8]);
+                    for (int j = 0; j < 8; ++j) *at(As, r8 + j, k) = e[j];
+                }
             }
+#pragma unroll 2
+            for (int i = 0; i < 4; ++i) {
+                const int v = tid + i * 128;
+                if (TB) {    // 64 rows (n) x 8 vectors along k
+                    const int r = v >> 3, c8 = (v & 7) * 8, gn = n0 + r, gk = k0 + c8;
+                    const uint4 x = (gn < N && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(B + (long long)gn * ldb + gk))
+                                                        : zero4;
+                    *reinterpret_cast<uint4*>(at(Bs, r, c8)) = x;
+                } else {     // 64 k x 8 vectors along n
+                    const int k = v >> 3, r8 = (v & 7) * 8, gn = n0 + r8, gk = k0 + k;
+                    uint4 x = zero4;
+                    if (gn < N && gk < ke) {
+                        if (b_lin > 0) {
+                            const int bb = gk / b_lout, t = gk - bb * b_lout, sx = 2 * t - 2 + (gn >> 6);
+                            if (sx >= 0 && sx < b_lin)
+                                x = __ldg(reinterpret_cast<const uint4*>(B + ((long long)bb * b_lin + sx) * kC + (gn & 63)));
+                        } else {
+                            x = __ldg(reinterpret_cast<const uint4*>(B + (long long)gk * ldb + gn));
+                        }
+                    }
+                    const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&x);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int nn = wn + j * 8 + grp;
-                b[j][0] = *reinterpret_cast<const unsigned*>(&Bs[st][nn][kk + tig * 2]);
-                b[j][1] = *reinterpret_cast<const unsigned*>(&Bs[st][nn][kk + tig * 2 + 8]);
+                    for (int j = 0; j < 8; ++j) *at(Bs, r8 + j, k) = e[j];
+                }
             }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    asm volatile(
-                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-                        "{%8,%9}, {%0,%1,%2,%3};"
-                        : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-                        : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
+        } else {
+            for (int e = tid; e < TM * TK; e += 128) {
+                const int r = TA ? (e & (TM - 1)) : (e >> 6), k = TA ? (e >> 7) : (e & (TK - 1));
+                const int gm = m0 + r, gk = k0 + k;
+                *at(As, r, k) = (gm < M && gk < ke) ? (TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk])
+                                                    : zero;
+            }
+            for (int e = tid; e < TN * TK; e += 128) {
+                const int r = TB ? (e >> 6) : (e & (TN - 1)), k = TB ? (e & (TK - 1)) : (e >> 6);
+                const int gn = n0 + r, gk = k0 + k;
+                *at(Bs, r, k) = (gn < N && gk < ke) ? (TB ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn])
+                                                    : zero;
+            }
         }
-        // the other stage was last read before the previous barrier
-        if (more) store(st ^ 1);
+    };
+    const int nk = ke > kb ? (ke - kb + TK - 1) / TK : 0;
+    constexpr unsigned idesc = tc_idesc(TM, TN);
+    unsigned ph[2] = {0u, 0u};
+    bool ok = true;
+    for (int t = 0; t < nk; ++t) {
+        const int st = t & 1;
+        if (t >= 2) {   // the group issued on this stage two tiles ago has read it
+            if (!tc_bar_wait(&bar[st], ph[st])) ok = false;
+            ph[st] ^= 1u;
+        }
+        fill(st, kb + t * TK);
+        tc_proxy_fence();   // the staged tile is visible to the tensor cores
         __syncthreads();
-        st ^= 1;
+        if (tid == 0) {
+            tc_fence_after();
+            const unsigned a0 = tc_smem(tsm + st * 24576), b0 = a0 + 16384;
+#pragma unroll
+            for (int j = 0; j < TK / 16; ++j)
+                tc_mma(tmem, tc_desc(a0 + j * 256, 128, 1024), tc_desc(b0 + j * 256, 128, 1024), idesc,
+                       (t > 0 || j > 0) ? 1 : 0);
+            tc_commit(&bar[st]);
+        }
     }
+    if (nk > 0 && !tc_bar_wait(&bar[(nk - 1) & 1], ph[(nk - 1) & 1])) ok = false;   // the last group: all are done
+    tc_fence_after();
+    const int m = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TN; c0 += 16) {
+        float v[16];
+        if (nk > 0) {
+            tc_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
+        } else {
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+            for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        }
+        if (m < M) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int m = m0 + wm + i * 16 + grp + (r >= 2 ? 8 : 0);
-                const int n = n0 + wn + j * 8 + tig * 2 + (r & 1);
-                if (m >= M || n >= N) continue;
-                float v = acc[i][j][r];
+            for (int i = 0; i < 16; ++i) {
+                const int n = n0 + c0 + i;
+                if (n >= N) break;
+                float x = v[i];
                 const long long o = (long long)m * ldc + n;
-                if (accumulate) v += C[o];
-                if (bias) v += bias[n];
-                if (relu) v = v > 0.f ? v : 0.f;
-                C[o] = v;
-                if (Cb) Cb[o] = __float2bfloat16(v);
+                if (accumulate) x += C[o];
+                if (bias) x += bias[n];
+                if (relu) x = x > 0.f ? x : 0.f;
+                C[o] = x;
+                if (Cb) Cb[o] = __float2bfloat16(x);
             }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN) : "memory");
+    if (!ok && tid == 0) atomicExch(err, 1);
 }
 
 // the adjoint of im2col: dX[b][s][c] = sum over (t, k) with 2t - 2 + k = s of dA[(b,t)][k*64+c]
@@ -611,24 +621,47 @@ namespace {
 constexpr int kMaxSplits = 64;
 constexpr long long kWsFloats = (long long)kMaxSplits * kC * kKC;   // split partials of the largest split product
 
+// set by a product whose bounded mbarrier wait ran out (checked by the host
+// after each network call; sticky for the process)
+__device__ int g_tc_err = 0;
+
 // K is split when the M x N tiles alone would leave most SMs idle and the
 // epilogue is a plain store into a dense C (the weight gradients of the
 // convolutions: 64 x 320 outputs over up to 32768 rows)
+template <bool TA, bool TB, bool VEC>
+cudaError_t launch_tc(dim3 grid, cudaStream_t s, int M, int N, int K, const __nv_bfloat16* A, int lda,
+                      const __nv_bfloat16* B, int ldb, float* C, int ldc, const float* bias, int relu, int acc,
+                      __nv_bfloat16* Cb, int kc, int a_lin, int a_lout, int b_lin, int b_lout) {
+    static bool attr = false;
+    constexpr int smem = 2 * (TM + TN) * TK * 2;   // two stages of A and B tiles: 48 KB
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_tc<TA, TB, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    int* err = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void**)&err, g_tc_err);
+    if (e != cudaSuccess) return e;
+    gemm_tc<TA, TB, VEC><<<grid, 128, smem, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, acc, Cb, kc, a_lin,
+                                                 a_lout, b_lin, b_lout, err);
+    return cudaGetLastError();
+}
+
 template <bool TA, bool TB>
 cudaError_t gemm(cudaStream_t s, float* ws, int M, int N, int K, const __nv_bfloat16* A, int lda,
                  const __nv_bfloat16* B, int ldb, float* C, int ldc, const float* bias, int relu, int acc,
                  __nv_bfloat16* Cb, int a_lin = 0, int a_lout = 0, int b_lin = 0, int b_lout = 0) {
-    const int gx = (N + GB - 1) / GB, gy = (M + GB - 1) / GB, tiles = gx * gy;
+    const int gx = (N + TN - 1) / TN, gy = (M + TM - 1) / TM, tiles = gx * gy;
     int splits = 1, kc = K;
     if (ws && !bias && !relu && !acc && !Cb && ldc == N && tiles < 152) {
         splits = std::min(kMaxSplits, std::min((304 + tiles - 1) / tiles, (K + 255) / 256));
         while (splits > 1 && (long long)splits * M * N > kWsFloats) --splits;
         if (splits > 1) {
-            kc = ((K + splits - 1) / splits + GK - 1) / GK * GK;
+            kc = ((K + splits - 1) / splits + TK - 1) / TK * TK;
             splits = (K + kc - 1) / kc;
         }
     }
-    // 16-byte tile loads when both operands' contiguous dimensions come in
+    // 16-byte operand loads when both operands' contiguous dimensions come in
     // whole aligned vectors
     auto al16 = [](const void* p) { return ((unsigned long long)p & 15ULL) == 0; };
     const bool vec = al16(A) && al16(B) && lda % 8 == 0 && ldb % 8 == 0 && (TA ? M % 8 == 0 : K % 8 == 0) &&
@@ -639,11 +672,11 @@ cudaError_t gemm(cudaStream_t s, float* ws, int M, int N, int K, const __nv_bflo
     const int rl = splits > 1 ? 0 : relu, ac = splits > 1 ? 0 : acc;
     __nv_bfloat16* cb = splits > 1 ? nullptr : Cb;
     if ((a_lin > 0 || b_lin > 0) && !vec) return cudaErrorInvalidValue;   // im2col operands need the vector loader
-    if (vec)
-        gemm_bf16_vec<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, out, ldc, bs, rl, ac, cb, kc, a_lin,
-                                                   a_lout, b_lin, b_lout);
-    else
-        gemm_bf16<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, out, ldc, bs, rl, ac, cb, kc);
+    cudaError_t e = vec ? launch_tc<TA, TB, true>(grid, s, M, N, K, A, lda, B, ldb, out, ldc, bs, rl, ac, cb, kc,
+                                                  a_lin, a_lout, b_lin, b_lout)
+                        : launch_tc<TA, TB, false>(grid, s, M, N, K, A, lda, B, ldb, out, ldc, bs, rl, ac, cb, kc,
+                                                   0, 0, 0, 0);
+    if (e != cudaSuccess) return e;
     if (splits > 1) sum_splits<<<blocks_for((long long)M * N), 256, 0, s>>>(ws, (long long)M * N, splits, C);
     return cudaGetLastError();
 }
@@ -724,7 +757,12 @@ cudaError_t backward(cmh_net* n, int Bn) {
 }
 
 int net_err(cudaError_t e) {
-    if (e == cudaSuccess) return CMH_OK;
+    if (e == cudaSuccess) {
+        // a product whose bounded wait ran out (sticky)
+        int f = 0;
+        if (cudaMemcpyFromSymbol(&f, g_tc_err, sizeof(int)) != cudaSuccess) return CMH_ERR_CUDA;
+        return f ? CMH_ERR_TIMEOUT : CMH_OK;
+    }
     if (e == cudaErrorMemoryAllocation) return CMH_ERR_OOM;
     return CMH_ERR_CUDA;
 }

@@ -20,6 +20,7 @@
 // place by the tile loader);
 // activations and gradients are kept in FP32, their BF16 copies feed the
 // products, and the parameters have FP32 masters with BF16 copies.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -70,26 +71,29 @@ constexpr long long kNParam = kOffFb2 + kNOut;
 // (not transposed; its rows are the im2col rows).
 // ---------------------------------------------------------------------------
 // The product on the fifth-generation tensor cores (tcgen05).  A CTA of
-// 128 threads computes a 128 x 64 tile of C: per K tile of 64 the threads
-// stage op(A) [128 x 64] and op(B)^T [64 x 64] in shared memory in the
-// K-major canonical layout without swizzle (8 x 8 core matrices of 128
-// contiguous bytes, row r and column k of a tile at byte
-// (r / 8) * 1024 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2), then one
+// 128 threads computes a 128 x 64 tile of C: per K tile of 64, op(A)
+// [128 x 64] and op(B)^T [64 x 64] are staged in shared memory in a K-major
+// canonical layout without swizzle (8 x 8 core matrices of 128 contiguous
+// bytes): by the tensor memory accelerator for an operand that is
+// K-contiguous and read as it stands (TMA_A / TMA_B: one 3-D box per tile,
+// chunk-major, row r and column k at (k / 8) * rows * 16 + r * 16 +
+// (k % 8) * 2), else by the threads (row-group-major, at
+// (r / 8) * 1024 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2); then one
 // thread issues four tcgen05.mma (M = 128, N = 64, K = 16; BF16 operands,
 // FP32 accumulator in tensor memory: row m in TMEM lane m, column n in
 // column n of a 64-column allocation) and commits them to the stage's
 // mbarrier.  Two stages: the global loads of the next tile are in flight
 // while the tensor cores multiply the current one.  The epilogue reads the
 // accumulator with tcgen05.ld (warp w: lanes 32w..32w+31) and applies
-// accumulate / bias / ReLU / BF16 copy as the other kernels do.  Every
-// mbarrier wait is bounded; on a timeout the CTA records it in *err.
+// accumulate / bias / ReLU / BF16 copy.  Every mbarrier wait is bounded (50
+// ms of wall time); on a timeout the CTA records it in *err.
 // VEC: 16-byte operand loads along each operand's contiguous dimension (its
 // extent and leading dimension multiples of 8, base 16-byte aligned; 8
 // consecutive im2col columns are 8 consecutive channels of one input
 // sample); otherwise element-wise loads.
 // ---------------------------------------------------------------------------
 constexpr int TM = 128, TN = 64, TK = 64;
-constexpr unsigned kTcWaitLimit = 1u << 24;
+constexpr unsigned long long kTcWaitNs = 50000000ull;   // 50 ms: a product's tile waits take microseconds
 
 __device__ __forceinline__ unsigned tc_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -123,9 +127,17 @@ __device__ __forceinline__ void tc_bar_init(unsigned long long* bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(bar)) : "memory");
 }
 
-// wait for the phase of parity `ph` of *bar to complete (bounded)
+__device__ __forceinline__ unsigned long long tc_now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for the phase of parity `ph` of *bar to complete, for at most
+// kTcWaitNs nanoseconds of wall time
 __device__ __forceinline__ bool tc_bar_wait(unsigned long long* bar, unsigned ph) {
-    for (unsigned n = 0; n < kTcWaitLimit; ++n) {
+    const unsigned long long t0 = tc_now_ns();
+    for (;;) {
         unsigned done;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -133,8 +145,8 @@ __device__ __forceinline__ bool tc_bar_wait(unsigned long long* bar, unsigned ph
             : "r"(tc_smem(bar)), "r"(ph)
             : "memory");
         if (done) return true;
+        if (tc_now_ns() - t0 > kTcWaitNs) return false;
     }
-    return false;
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -155,13 +167,37 @@ __device__ __forceinline__ void tc_ld16(unsigned taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <bool TA, bool TB, bool VEC>
+// arm *bar for `bytes` of asynchronous copies (one arrival)
+__device__ __forceinline__ void tc_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// one tile of a K-contiguous operand by the tensor memory accelerator: the
+// map views the operand as (8 elements, rows, K / 8 chunks); the box
+// (8, rows of the tile, 8 chunks) lands as [chunk][row][8 elements], the
+// chunk-major canonical layout (LBO = rows x 16 bytes, SBO = 128 bytes);
+// rows and chunks outside the operand are filled with zeros
+__device__ __forceinline__ void tc_tma_tile(void* dst, const CUtensorMap* map, int row0, int chunk0,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(tc_smem(dst)), "l"(map), "r"(0), "r"(row0), "r"(chunk0), "r"(tc_smem(bar))
+        : "memory");
+}
+
+template <bool TA, bool TB, bool VEC, bool TMA_A, bool TMA_B>
 __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_bfloat16* A, int lda,
                                                const __nv_bfloat16* B, int ldb, float* C, int ldc,
                                                const float* bias, int relu, int accumulate, __nv_bfloat16* Cb,
-                                               int kc, int a_lin, int a_lout, int b_lin, int b_lout, int* err) {
+                                               int kc, int a_lin, int a_lout, int b_lin, int b_lout, int* err,
+                                               const __grid_constant__ CUtensorMap map_a,
+                                               const __grid_constant__ CUtensorMap map_b) {
+    static_assert(!TMA_A || (!TA && VEC), "the tensor map views a K-contiguous A");
+    static_assert(!TMA_B || (TB && VEC), "the tensor map views a K-contiguous B");
     extern __shared__ __align__(1024) unsigned char tsm[];   // [2] x (A 16 KB, B 8 KB)
-    __shared__ __align__(8) unsigned long long bar[2];
+    __shared__ __align__(8) unsigned long long bar[2];       // a stage's products have read it
+    __shared__ __align__(8) unsigned long long full[2];      // a stage's tensor-map copies have landed
     __shared__ unsigned s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
@@ -176,6 +212,8 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
     if (tid == 0) {
         tc_bar_init(&bar[0]);
         tc_bar_init(&bar[1]);
+        tc_bar_init(&full[0]);
+        tc_bar_init(&full[1]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
@@ -193,7 +231,7 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
         unsigned char* Bs = As + 16384;
         if (VEC) {
 #pragma unroll 2
-            for (int i = 0; i < 8; ++i) {
+            for (int i = 0; i < 8 && !TMA_A; ++i) {
                 const int v = tid + i * 128;
                 if (!TA) {   // 128 rows x 8 vectors along k
                     const int r = v >> 3, c8 = (v & 7) * 8, gm = m0 + r, gk = k0 + c8;
@@ -218,7 +256,7 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
                 }
             }
 #pragma unroll 2
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < 4 && !TMA_B; ++i) {
                 const int v = tid + i * 128;
                 if (TB) {    // 64 rows (n) x 8 vectors along k
                     const int r = v >> 3, c8 = (v & 7) * 8, gn = n0 + r, gk = k0 + c8;
@@ -259,24 +297,38 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
     };
     const int nk = ke > kb ? (ke - kb + TK - 1) / TK : 0;
     constexpr unsigned idesc = tc_idesc(TM, TN);
-    unsigned ph[2] = {0u, 0u};
+    // byte offsets between core matrices along K (LBO) and between 8-row
+    // groups (SBO): the threads' layout, or the tensor map's chunk-major one
+    constexpr unsigned lbo_a = TMA_A ? TM * 16 : 128, sbo_a = TMA_A ? 128 : 1024;
+    constexpr unsigned lbo_b = TMA_B ? TN * 16 : 128, sbo_b = TMA_B ? 128 : 1024;
+    constexpr unsigned tma_bytes = (TMA_A ? TM * TK * 2 : 0) + (TMA_B ? TN * TK * 2 : 0);
+    unsigned ph[2] = {0u, 0u}, pf[2] = {0u, 0u};
     bool ok = true;
     for (int t = 0; t < nk; ++t) {
-        const int st = t & 1;
+        const int st = t & 1, k0 = kb + t * TK;
         if (t >= 2) {   // the group issued on this stage two tiles ago has read it
             if (!tc_bar_wait(&bar[st], ph[st])) ok = false;
             ph[st] ^= 1u;
         }
-        fill(st, kb + t * TK);
-        tc_proxy_fence();   // the staged tile is visible to the tensor cores
+        if ((TMA_A || TMA_B) && tid == 0) {
+            tc_expect_tx(&full[st], tma_bytes);
+            if (TMA_A) tc_tma_tile(tsm + st * 24576, &map_a, m0, k0 >> 3, &full[st]);
+            if (TMA_B) tc_tma_tile(tsm + st * 24576 + 16384, &map_b, n0, k0 >> 3, &full[st]);
+        }
+        if (!(TMA_A && TMA_B)) fill(st, k0);
+        tc_proxy_fence();   // the threads' staged tile is visible to the tensor cores
         __syncthreads();
         if (tid == 0) {
+            if (TMA_A || TMA_B) {   // and the tensor-map copies have landed
+                if (!tc_bar_wait(&full[st], pf[st])) ok = false;
+                pf[st] ^= 1u;
+            }
             tc_fence_after();
             const unsigned a0 = tc_smem(tsm + st * 24576), b0 = a0 + 16384;
 #pragma unroll
             for (int j = 0; j < TK / 16; ++j)
-                tc_mma(tmem, tc_desc(a0 + j * 256, 128, 1024), tc_desc(b0 + j * 256, 128, 1024), idesc,
-                       (t > 0 || j > 0) ? 1 : 0);
+                tc_mma(tmem, tc_desc(a0 + j * 2 * lbo_a, lbo_a, sbo_a), tc_desc(b0 + j * 2 * lbo_b, lbo_b, sbo_b),
+                       idesc, (t > 0 || j > 0) ? 1 : 0);
             tc_commit(&bar[st]);
         }
     }
@@ -628,23 +680,96 @@ __device__ int g_tc_err = 0;
 // K is split when the M x N tiles alone would leave most SMs idle and the
 // epilogue is a plain store into a dense C (the weight gradients of the
 // convolutions: 64 x 320 outputs over up to 32768 rows)
-template <bool TA, bool TB, bool VEC>
+// cuTensorMapEncodeTiled, reached through the runtime (no link against
+// libcuda); null if the driver does not offer it
+typedef CUresult (*encode_tiled_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+encode_tiled_fn tensor_map_encoder() {
+    static encode_tiled_fn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (encode_tiled_fn)f;
+        (void)cudaGetLastError();
+    }
+    return fn;
+}
+
+// tensor map of a K-contiguous BF16 operand [rows][ld] (K columns used, K a
+// multiple of 8, base 16-byte aligned, ld a multiple of 8) viewed as
+// (8 elements, rows, K / 8 chunks) with a box of (8, box_rows, 8)
+bool k_tensor_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int K, int ld, int box_rows) {
+    encode_tiled_fn enc = tensor_map_encoder();
+    if (!enc || rows < 1 || K < 8 || K % 8 || ld % 8 || ((unsigned long long)base & 15ULL)) return false;
+    const cuuint64_t dims[3] = {8, (cuuint64_t)rows, (cuuint64_t)(K / 8)};
+    const cuuint64_t strides[2] = {(cuuint64_t)ld * 2, 16};
+    const cuuint32_t box[3] = {8, (cuuint32_t)box_rows, 8};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <bool TA, bool TB, bool VEC, bool TMA_A, bool TMA_B>
 cudaError_t launch_tc(dim3 grid, cudaStream_t s, int M, int N, int K, const __nv_bfloat16* A, int lda,
                       const __nv_bfloat16* B, int ldb, float* C, int ldc, const float* bias, int relu, int acc,
-                      __nv_bfloat16* Cb, int kc, int a_lin, int a_lout, int b_lin, int b_lout) {
+                      __nv_bfloat16* Cb, int kc, int a_lin, int a_lout, int b_lin, int b_lout, const CUtensorMap& ma,
+                      const CUtensorMap& mb) {
     static bool attr = false;
     constexpr int smem = 2 * (TM + TN) * TK * 2;   // two stages of A and B tiles: 48 KB
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_tc<TA, TB, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(gemm_tc<TA, TB, VEC, TMA_A, TMA_B>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     int* err = nullptr;
     cudaError_t e = cudaGetSymbolAddress((void**)&err, g_tc_err);
     if (e != cudaSuccess) return e;
-    gemm_tc<TA, TB, VEC><<<grid, 128, smem, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, acc, Cb, kc, a_lin,
-                                                 a_lout, b_lin, b_lout, err);
+    gemm_tc<TA, TB, VEC, TMA_A, TMA_B><<<grid, 128, smem, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, acc,
+                                                               Cb, kc, a_lin, a_lout, b_lin, b_lout, err, ma, mb);
     return cudaGetLastError();
+}
+
+// the variant for the operands at hand: tensor-map loads for a K-contiguous
+// operand read as it stands (not an im2col view), 16-byte or element-wise
+// loads by the threads otherwise
+template <bool TA, bool TB>
+cudaError_t launch_product(dim3 grid, cudaStream_t s, bool vec, int M, int N, int K, const __nv_bfloat16* A,
+                           int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc, const float* bias, int relu,
+                           int acc, __nv_bfloat16* Cb, int kc, int a_lin, int a_lout, int b_lin, int b_lout) {
+    CUtensorMap ma, mb;
+    std::memset(&ma, 0, sizeof(ma));
+    std::memset(&mb, 0, sizeof(mb));
+    if (!vec)
+        return launch_tc<TA, TB, false, false, false>(grid, s, M, N, K, A, lda, B, ldb, C, ldc, bias, relu, acc, Cb,
+                                                      kc, 0, 0, 0, 0, ma, mb);
+    const bool ta = !TA && a_lin == 0 && k_tensor_map(&ma, A, M, K, lda, TM);
+    const bool tb = TB && b_lin == 0 && k_tensor_map(&mb, B, N, K, ldb, TN);
+    if constexpr (!TA && TB) {
+        if (ta && tb)
+            return launch_tc<TA, TB, true, true, true>(grid, s, M, N, K, A, lda, B, ldb, C, ldc, bias, relu, acc, Cb,
+                                                       kc, a_lin, a_lout, b_lin, b_lout, ma, mb);
+    }
+    if constexpr (!TA) {
+        if (ta)
+            return launch_tc<TA, TB, true, !TA, false>(grid, s, M, N, K, A, lda, B, ldb, C, ldc, bias, relu, acc,
+                                                       Cb, kc, a_lin, a_lout, b_lin, b_lout, ma, mb);
+    }
+    if constexpr (TB) {
+        if (tb)
+            return launch_tc<TA, TB, true, false, TB>(grid, s, M, N, K, A, lda, B, ldb, C, ldc, bias, relu, acc, Cb,
+                                                      kc, a_lin, a_lout, b_lin, b_lout, ma, mb);
+    }
+    return launch_tc<TA, TB, true, false, false>(grid, s, M, N, K, A, lda, B, ldb, C, ldc, bias, relu, acc, Cb, kc,
+                                                 a_lin, a_lout, b_lin, b_lout, ma, mb);
 }
 
 template <bool TA, bool TB>
@@ -672,10 +797,8 @@ cudaError_t gemm(cudaStream_t s, float* ws, int M, int N, int K, const __nv_bflo
     const int rl = splits > 1 ? 0 : relu, ac = splits > 1 ? 0 : acc;
     __nv_bfloat16* cb = splits > 1 ? nullptr : Cb;
     if ((a_lin > 0 || b_lin > 0) && !vec) return cudaErrorInvalidValue;   // im2col operands need the vector loader
-    cudaError_t e = vec ? launch_tc<TA, TB, true>(grid, s, M, N, K, A, lda, B, ldb, out, ldc, bs, rl, ac, cb, kc,
-                                                  a_lin, a_lout, b_lin, b_lout)
-                        : launch_tc<TA, TB, false>(grid, s, M, N, K, A, lda, B, ldb, out, ldc, bs, rl, ac, cb, kc,
-                                                   0, 0, 0, 0);
+    cudaError_t e = launch_product<TA, TB>(grid, s, vec, M, N, K, A, lda, B, ldb, out, ldc, bs, rl, ac, cb, kc,
+                                           a_lin, a_lout, b_lin, b_lout);
     if (e != cudaSuccess) return e;
     if (splits > 1) sum_splits<<<blocks_for((long long)M * N), 256, 0, s>>>(ws, (long long)M * N, splits, C);
     return cudaGetLastError();

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -233,8 +234,14 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
 #pragma unroll 2
             for (int i = 0; i < 8 && !TMA_A; ++i) {
                 const int v = tid + i * 128;
+                // a quarter warp (8 lanes) takes 8 consecutive rows of one
+                // 16-byte chunk column: one core-matrix row block of 128
+                // contiguous bytes in shared memory (no bank conflict), 64
+                // contiguous bytes per row across the warp in global memory
+                const int lw = v & 31, vw = v >> 5;
                 if (!TA) {   // 128 rows x 8 vectors along k
-                    const int r = v >> 3, c8 = (v & 7) * 8, gm = m0 + r, gk = k0 + c8;
+                    const int r = (vw >> 1) * 8 + (lw & 7), c8 = ((vw & 1) * 4 + (lw >> 3)) * 8, gm = m0 + r,
+                              gk = k0 + c8;
                     uint4 x = zero4;
                     if (gm < M && gk < ke) {
                         if (a_lin > 0) {
@@ -246,8 +253,9 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
                         }
                     }
                     *reinterpret_cast<uint4*>(at(As, r, c8)) = x;
-                } else {     // 64 k x 16 vectors along m
-                    const int k = v >> 4, r8 = (v & 15) * 8, gm = m0 + r8, gk = k0 + k;
+                } else {     // 64 k x 16 vectors along m; a quarter warp: 8 consecutive k
+                    const int k = (lw & 7) + 8 * (vw & 7), r8 = ((lw >> 3) + 4 * (vw >> 3)) * 8, gm = m0 + r8,
+                              gk = k0 + k;
                     uint4 x = (gm < M && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(A + (long long)gk * lda + gm))
                                                   : zero4;
                     const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&x);
@@ -258,13 +266,16 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
 #pragma unroll 2
             for (int i = 0; i < 4 && !TMA_B; ++i) {
                 const int v = tid + i * 128;
+                const int lw = v & 31, vw = v >> 5;
                 if (TB) {    // 64 rows (n) x 8 vectors along k
-                    const int r = v >> 3, c8 = (v & 7) * 8, gn = n0 + r, gk = k0 + c8;
+                    const int r = (vw >> 1) * 8 + (lw & 7), c8 = ((vw & 1) * 4 + (lw >> 3)) * 8, gn = n0 + r,
+                              gk = k0 + c8;
                     const uint4 x = (gn < N && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(B + (long long)gn * ldb + gk))
                                                         : zero4;
                     *reinterpret_cast<uint4*>(at(Bs, r, c8)) = x;
-                } else {     // 64 k x 8 vectors along n
-                    const int k = v >> 3, r8 = (v & 7) * 8, gn = n0 + r8, gk = k0 + k;
+                } else {     // 64 k x 8 vectors along n; a quarter warp: 8 consecutive k
+                    const int k = (lw & 7) + 8 * (vw & 7), r8 = ((lw >> 3) + 4 * (vw >> 3)) * 8, gn = n0 + r8,
+                              gk = k0 + k;
                     uint4 x = zero4;
                     if (gn < N && gk < ke) {
                         if (b_lin > 0) {
@@ -334,7 +345,10 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
     }
     if (nk > 0 && !tc_bar_wait(&bar[(nk - 1) & 1], ph[(nk - 1) & 1])) ok = false;   // the last group: all are done
     tc_fence_after();
-    const int m = m0 + warp * 32 + lane;
+    // the accumulator tile through shared memory (the stages are free: every
+    // product has completed), so that C is written in whole rows by
+    // consecutive threads: row r of the tile at cs[r * (TN + 1)]
+    float* cs = reinterpret_cast<float*>(tsm);
 #pragma unroll 1
     for (int c0 = 0; c0 < TN; c0 += 16) {
         float v[16];
@@ -344,20 +358,20 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = 0.f;
         }
-        if (m < M) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int n = n0 + c0 + i;
-                if (n >= N) break;
-                float x = v[i];
-                const long long o = (long long)m * ldc + n;
-                if (accumulate) x += C[o];
-                if (bias) x += bias[n];
-                if (relu) x = x > 0.f ? x : 0.f;
-                C[o] = x;
-                if (Cb) Cb[o] = __float2bfloat16(x);
-            }
-        }
+        for (int i = 0; i < 16; ++i) cs[(warp * 32 + lane) * (TN + 1) + c0 + i] = v[i];
+    }
+    __syncthreads();
+    for (int e = tid; e < TM * TN; e += 128) {
+        const int r = e / TN, c = e - r * TN, m = m0 + r, n = n0 + c;
+        if (m >= M || n >= N) continue;
+        float x = cs[r * (TN + 1) + c];
+        const long long o = (long long)m * ldc + n;
+        if (accumulate) x += C[o];
+        if (bias) x += bias[n];
+        if (relu) x = x > 0.f ? x : 0.f;
+        C[o] = x;
+        if (Cb) Cb[o] = __float2bfloat16(x);
     }
     tc_fence_before();
     __syncthreads();
@@ -680,6 +694,41 @@ __device__ int g_tc_err = 0;
 // K is split when the M x N tiles alone would leave most SMs idle and the
 // epilogue is a plain store into a dense C (the weight gradients of the
 // convolutions: 64 x 320 outputs over up to 32768 rows)
+// device address of g_tc_err per device: looked up when a network is
+// created on the device (a network's kernels run only while it exists, and a
+// device reset that would move the address destroys the networks with it)
+std::mutex g_err_mu;
+int* g_err_addr[64] = {nullptr};
+
+cudaError_t tc_err_lookup() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    int* p = nullptr;
+    e = cudaGetSymbolAddress((void**)&p, g_tc_err);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_err_mu);
+    g_err_addr[dev] = p;
+    return cudaSuccess;
+}
+
+cudaError_t tc_err_address(int** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lock(g_err_mu);
+        if (g_err_addr[dev]) {
+            *out = g_err_addr[dev];
+            return cudaSuccess;
+        }
+    }
+    if ((e = tc_err_lookup()) != cudaSuccess) return e;
+    return tc_err_address(out);
+}
+
 // cuTensorMapEncodeTiled, reached through the runtime (no link against
 // libcuda); null if the driver does not offer it
 typedef CUresult (*encode_tiled_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -704,8 +753,40 @@ encode_tiled_fn tensor_map_encoder() {
 
 // tensor map of a K-contiguous BF16 operand [rows][ld] (K columns used, K a
 // multiple of 8, base 16-byte aligned, ld a multiple of 8) viewed as
-// (8 elements, rows, K / 8 chunks) with a box of (8, box_rows, 8)
+// (8 elements, rows, K / 8 chunks) with a box of (8, box_rows, 8).  The
+// network's operands repeat every step, so encoded maps are kept (a small
+// cache keyed by every argument; a map describes addresses, not contents).
+bool k_tensor_map_encode(CUtensorMap* map, const __nv_bfloat16* base, int rows, int K, int ld, int box_rows);
+
 bool k_tensor_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int K, int ld, int box_rows) {
+    struct Entry {
+        const void* base;
+        int rows, K, ld, box, ok;
+        CUtensorMap map;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry& e : cache)
+        if (e.base == base && e.rows == rows && e.K == K && e.ld == ld && e.box == box_rows) {
+            *map = e.map;
+            return e.ok;
+        }
+    Entry e;
+    e.base = base;
+    e.rows = rows;
+    e.K = K;
+    e.ld = ld;
+    e.box = box_rows;
+    std::memset(&e.map, 0, sizeof(e.map));
+    e.ok = k_tensor_map_encode(&e.map, base, rows, K, ld, box_rows);
+    if (cache.size() >= 256) cache.erase(cache.begin());
+    cache.push_back(e);
+    *map = e.map;
+    return e.ok;
+}
+
+bool k_tensor_map_encode(CUtensorMap* map, const __nv_bfloat16* base, int rows, int K, int ld, int box_rows) {
     encode_tiled_fn enc = tensor_map_encoder();
     if (!enc || rows < 1 || K < 8 || K % 8 || ld % 8 || ((unsigned long long)base & 15ULL)) return false;
     const cuuint64_t dims[3] = {8, (cuuint64_t)rows, (cuuint64_t)(K / 8)};
@@ -731,7 +812,7 @@ cudaError_t launch_tc(dim3 grid, cudaStream_t s, int M, int N, int K, const __nv
         attr = true;
     }
     int* err = nullptr;
-    cudaError_t e = cudaGetSymbolAddress((void**)&err, g_tc_err);
+    cudaError_t e = tc_err_address(&err);
     if (e != cudaSuccess) return e;
     gemm_tc<TA, TB, VEC, TMA_A, TMA_B><<<grid, 128, smem, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, acc,
                                                                Cb, kc, a_lin, a_lout, b_lin, b_lout, err, ma, mb);
@@ -909,6 +990,10 @@ extern "C" int cmh_net_create(int32_t max_batch, uint64_t seed, void* cuda_strea
             return CMH_ERR_CUDA;
         }
         n->own_stream = true;
+    }
+    if (tc_err_lookup() != cudaSuccess) {
+        delete n;
+        return CMH_ERR_CUDA;
     }
     const long long B = max_batch;
     bool ok = n->alloc(&n->p, kNParam) && n->alloc(&n->gr, kNParam) && n->alloc(&n->m1, kNParam) &&

@@ -83,8 +83,8 @@ constexpr long long kNParam = kOffFb2 + kNOut;
 // thread issues four tcgen05.mma (M = 128, N = 64, K = 16; BF16 operands,
 // FP32 accumulator in tensor memory: row m in TMEM lane m, column n in
 // column n of a 64-column allocation) and commits them to the stage's
-// mbarrier.  Two stages: the global loads of the next tile are in flight
-// while the tensor cores multiply the current one.  The epilogue reads the
+// mbarrier.  Three stages, staged two tiles ahead: a tile's copies are in
+// flight while the tensor cores multiply the tiles before it.  The epilogue reads the
 // accumulator with tcgen05.ld (warp w: lanes 32w..32w+31) and applies
 // accumulate / bias / ReLU / BF16 copy.  Every mbarrier wait is bounded (50
 // ms of wall time); on a timeout the CTA records it in *err.
@@ -94,6 +94,8 @@ constexpr long long kNParam = kOffFb2 + kNOut;
 // sample); otherwise element-wise loads.
 // ---------------------------------------------------------------------------
 constexpr int TM = 128, TN = 64, TK = 64;
+constexpr int kStages = 3;                            // shared stages of a product's K tiles
+constexpr int kStageBytes = (TM + TN) * TK * 2;       // 24 KB: the A and B tiles of one stage
 constexpr unsigned long long kTcWaitNs = 50000000ull;   // 50 ms: a product's tile waits take microseconds
 
 __device__ __forceinline__ unsigned tc_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -153,6 +155,15 @@ __device__ __forceinline__ bool tc_bar_wait(unsigned long long* bar, unsigned ph
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// 16 bytes global -> shared without registers (zeros when !valid; src must
+// still point into the operand)
+__device__ __forceinline__ void tc_cp16(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc_smem(dst)), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void tc_cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // 16 consecutive accumulator columns of this thread's TMEM lane
 __device__ __forceinline__ void tc_ld16(unsigned taddr, float* v) {
@@ -196,9 +207,9 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
                                                const __grid_constant__ CUtensorMap map_b) {
     static_assert(!TMA_A || (!TA && VEC), "the tensor map views a K-contiguous A");
     static_assert(!TMA_B || (TB && VEC), "the tensor map views a K-contiguous B");
-    extern __shared__ __align__(1024) unsigned char tsm[];   // [2] x (A 16 KB, B 8 KB)
-    __shared__ __align__(8) unsigned long long bar[2];       // a stage's products have read it
-    __shared__ __align__(8) unsigned long long full[2];      // a stage's tensor-map copies have landed
+    extern __shared__ __align__(1024) unsigned char tsm[];   // [kStages] x (A 16 KB, B 8 KB)
+    __shared__ __align__(8) unsigned long long bar[kStages];    // a stage's products have read it
+    __shared__ __align__(8) unsigned long long full[kStages];   // a stage's tensor-map copies have landed
     __shared__ unsigned s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
@@ -211,10 +222,10 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        tc_bar_init(&bar[0]);
-        tc_bar_init(&bar[1]);
-        tc_bar_init(&full[0]);
-        tc_bar_init(&full[1]);
+        for (int q = 0; q < kStages; ++q) {
+            tc_bar_init(&bar[q]);
+            tc_bar_init(&full[q]);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
@@ -228,10 +239,10 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
         return reinterpret_cast<__nv_bfloat16*>(base + (r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
     };
     auto fill = [&](int st, int k0) {
-        unsigned char* As = tsm + st * 24576;
+        unsigned char* As = tsm + st * kStageBytes;
         unsigned char* Bs = As + 16384;
         if (VEC) {
-#pragma unroll 2
+#pragma unroll
             for (int i = 0; i < 8 && !TMA_A; ++i) {
                 const int v = tid + i * 128;
                 // a quarter warp (8 lanes) takes 8 consecutive rows of one
@@ -239,20 +250,21 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
                 // contiguous bytes in shared memory (no bank conflict), 64
                 // contiguous bytes per row across the warp in global memory
                 const int lw = v & 31, vw = v >> 5;
-                if (!TA) {   // 128 rows x 8 vectors along k
+                if (!TA) {   // 128 rows x 8 vectors along k, asynchronous copies
                     const int r = (vw >> 1) * 8 + (lw & 7), c8 = ((vw & 1) * 4 + (lw >> 3)) * 8, gm = m0 + r,
                               gk = k0 + c8;
-                    uint4 x = zero4;
-                    if (gm < M && gk < ke) {
+                    const __nv_bfloat16* src = A;
+                    bool ok = gm < M && gk < ke;
+                    if (ok) {
                         if (a_lin > 0) {
                             const int bb = gm / a_lout, t = gm - bb * a_lout, sx = 2 * t - 2 + (gk >> 6);
-                            if (sx >= 0 && sx < a_lin)
-                                x = __ldg(reinterpret_cast<const uint4*>(A + ((long long)bb * a_lin + sx) * kC + (gk & 63)));
+                            ok = sx >= 0 && sx < a_lin;
+                            if (ok) src = A + ((long long)bb * a_lin + sx) * kC + (gk & 63);
                         } else {
-                            x = __ldg(reinterpret_cast<const uint4*>(A + (long long)gm * lda + gk));
+                            src = A + (long long)gm * lda + gk;
                         }
                     }
-                    *reinterpret_cast<uint4*>(at(As, r, c8)) = x;
+                    tc_cp16(at(As, r, c8), src, ok);
                 } else {     // 64 k x 16 vectors along m; a quarter warp: 8 consecutive k
                     const int k = (lw & 7) + 8 * (vw & 7), r8 = ((lw >> 3) + 4 * (vw >> 3)) * 8, gm = m0 + r8,
                               gk = k0 + k;
@@ -263,16 +275,15 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
                     for (int j = 0; j < 8; ++j) *at(As, r8 + j, k) = e[j];
                 }
             }
-#pragma unroll 2
+#pragma unroll
             for (int i = 0; i < 4 && !TMA_B; ++i) {
                 const int v = tid + i * 128;
                 const int lw = v & 31, vw = v >> 5;
-                if (TB) {    // 64 rows (n) x 8 vectors along k
+                if (TB) {    // 64 rows (n) x 8 vectors along k, asynchronous copies
                     const int r = (vw >> 1) * 8 + (lw & 7), c8 = ((vw & 1) * 4 + (lw >> 3)) * 8, gn = n0 + r,
                               gk = k0 + c8;
-                    const uint4 x = (gn < N && gk < ke) ? __ldg(reinterpret_cast<const uint4*>(B + (long long)gn * ldb + gk))
-                                                        : zero4;
-                    *reinterpret_cast<uint4*>(at(Bs, r, c8)) = x;
+                    const bool ok = gn < N && gk < ke;
+                    tc_cp16(at(Bs, r, c8), ok ? B + (long long)gn * ldb + gk : B, ok);
                 } else {     // 64 k x 8 vectors along n; a quarter warp: 8 consecutive k
                     const int k = (lw & 7) + 8 * (vw & 7), r8 = ((lw >> 3) + 4 * (vw >> 3)) * 8, gn = n0 + r8,
                               gk = k0 + k;
@@ -313,29 +324,43 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
     constexpr unsigned lbo_a = TMA_A ? TM * 16 : 128, sbo_a = TMA_A ? 128 : 1024;
     constexpr unsigned lbo_b = TMA_B ? TN * 16 : 128, sbo_b = TMA_B ? 128 : 1024;
     constexpr unsigned tma_bytes = (TMA_A ? TM * TK * 2 : 0) + (TMA_B ? TN * TK * 2 : 0);
-    unsigned ph[2] = {0u, 0u}, pf[2] = {0u, 0u};
     bool ok = true;
-    for (int t = 0; t < nk; ++t) {
-        const int st = t & 1, k0 = kb + t * TK;
-        if (t >= 2) {   // the group issued on this stage two tiles ago has read it
-            if (!tc_bar_wait(&bar[st], ph[st])) ok = false;
-            ph[st] ^= 1u;
-        }
+    // staging of tile t into stage t % kStages: the tensor-map copies (one
+    // thread), the asynchronous copies and the register-staged operands (all
+    // threads), closed by one asynchronous-copy group per thread and tile
+    auto issue = [&](int t) {
+        const int st = t % kStages, k0 = kb + t * TK;
         if ((TMA_A || TMA_B) && tid == 0) {
             tc_expect_tx(&full[st], tma_bytes);
-            if (TMA_A) tc_tma_tile(tsm + st * 24576, &map_a, m0, k0 >> 3, &full[st]);
-            if (TMA_B) tc_tma_tile(tsm + st * 24576 + 16384, &map_b, n0, k0 >> 3, &full[st]);
+            if (TMA_A) tc_tma_tile(tsm + st * kStageBytes, &map_a, m0, k0 >> 3, &full[st]);
+            if (TMA_B) tc_tma_tile(tsm + st * kStageBytes + 16384, &map_b, n0, k0 >> 3, &full[st]);
         }
         if (!(TMA_A && TMA_B)) fill(st, k0);
-        tc_proxy_fence();   // the threads' staged tile is visible to the tensor cores
+        tc_cp_commit();
+    };
+    // tile u of a stage is its (u / kStages)-th use: its mbarrier phases have parity (u / kStages) & 1
+    for (int t = 0; t < kStages - 1; ++t) {
+        if (t < nk) issue(t);
+        else tc_cp_commit();
+    }
+    for (int t = 0; t < nk; ++t) {
+        const int st = t % kStages, tn = t + kStages - 1;
+        if (tn < nk) {
+            if (tn >= kStages &&   // the products of tile tn - kStages have read that stage
+                !tc_bar_wait(&bar[tn % kStages], (unsigned)((tn / kStages - 1) & 1)))
+                ok = false;
+            issue(tn);
+        } else {
+            tc_cp_commit();
+        }
+        tc_cp_wait<kStages - 1>();   // this thread's copies of tile t have landed
+        tc_proxy_fence();            // and, with the threads' stores, are visible to the tensor cores
         __syncthreads();
         if (tid == 0) {
-            if (TMA_A || TMA_B) {   // and the tensor-map copies have landed
-                if (!tc_bar_wait(&full[st], pf[st])) ok = false;
-                pf[st] ^= 1u;
-            }
+            if ((TMA_A || TMA_B) && !tc_bar_wait(&full[st], (unsigned)((t / kStages) & 1)))   // the tensor-map copies
+                ok = false;
             tc_fence_after();
-            const unsigned a0 = tc_smem(tsm + st * 24576), b0 = a0 + 16384;
+            const unsigned a0 = tc_smem(tsm + st * kStageBytes), b0 = a0 + 16384;
 #pragma unroll
             for (int j = 0; j < TK / 16; ++j)
                 tc_mma(tmem, tc_desc(a0 + j * 2 * lbo_a, lbo_a, sbo_a), tc_desc(b0 + j * 2 * lbo_b, lbo_b, sbo_b),
@@ -343,7 +368,8 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
             tc_commit(&bar[st]);
         }
     }
-    if (nk > 0 && !tc_bar_wait(&bar[(nk - 1) & 1], ph[(nk - 1) & 1])) ok = false;   // the last group: all are done
+    // the last group: every product is done
+    if (nk > 0 && !tc_bar_wait(&bar[(nk - 1) % kStages], (unsigned)(((nk - 1) / kStages) & 1))) ok = false;
     tc_fence_after();
     // the accumulator tile through shared memory (the stages are free: every
     // product has completed), so that C is written in whole rows by
@@ -804,7 +830,7 @@ cudaError_t launch_tc(dim3 grid, cudaStream_t s, int M, int N, int K, const __nv
                       __nv_bfloat16* Cb, int kc, int a_lin, int a_lout, int b_lin, int b_lout, const CUtensorMap& ma,
                       const CUtensorMap& mb) {
     static bool attr = false;
-    constexpr int smem = 2 * (TM + TN) * TK * 2;   // two stages of A and B tiles: 48 KB
+    constexpr int smem = kStages * kStageBytes;   // the stages of A and B tiles: 72 KB
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(gemm_tc<TA, TB, VEC, TMA_A, TMA_B>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -114,7 +114,8 @@ def _workload(name: str, likelihood: str = "variance", p_pair: float = 0.0, sig_
     if name == "scale":
         return worldgen.config_scale(seed=SEED, likelihood=likelihood), \
             "fp32 sweep at scale: 4000x4000 km, 24 h, ~1e4 events, 1600 stations x 864000 f32 samples, " \
-            "40x40 regions, k=32" + ("" if likelihood == "variance" else ", additive-mean likelihood reading")
+            "40x40 regions, k=32" + ("" if likelihood == "variance" else ", additive-mean likelihood reading") + \
+            (", joint pair moves p_pair=%g" % p_pair if p_pair else "")
     if name == "replay":
         return worldgen.config_replay(seed=SEED, sig_a=sig_a), \
             "fp64 replay: 1000x1000 km, 1 h, ~500 events, 100 stations x 36000 f64 samples, 10x10 regions, " \
@@ -841,7 +842,7 @@ def main():
     ap.add_argument("--likelihood", default="variance", choices=["variance", "mean"],
                     help="scale workload: arrivals add to the sample variance (default) or to its mean")
     ap.add_argument("--p-pair", type=float, default=0.0,
-                    help="replay workload: share of steps that propose the joint move of a pair of events")
+                    help="replay or scale workload: share of steps that propose the joint move of a pair of events")
     ap.add_argument("--sig-a", type=float, default=0.0,
                     help="replay workload: latent arrival times with offsets ~ N(0, sig_a^2) seconds")
     ap.add_argument("--p-arr", type=float, default=0.0, help="replay workload: share of arrival-time moves")
@@ -852,8 +853,10 @@ def main():
     if args.profile_case:
         run_profile_case(args)
         return
-    if (args.p_pair or args.sig_a or args.p_arr) and args.workload != "replay":
-        raise SystemExit("--p-pair, --sig-a and --p-arr need the float64 replay workload")
+    if (args.sig_a or args.p_arr) and args.workload != "replay":
+        raise SystemExit("--sig-a and --p-arr need the float64 replay workload")
+    if args.p_pair and args.workload not in ("replay", "scale"):
+        raise SystemExit("--p-pair needs the replay or the scale workload")
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":

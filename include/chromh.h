@@ -94,7 +94,7 @@ typedef struct {
                               to the sample's mean and the variance is noise_var (the
                               additive reading) */
     int64_t max_events;    /* capacity of the whole event store; 0: 4 (n0 + Lambda) + 4096 */
-    double p_pair;         /* CMH_F64 only: probability of the joint move of a pair of the
+    double p_pair;         /* probability of the joint move of a pair of the
                               region's events (§MH moves, "Joint Events Move"); a step whose
                               uniform falls in [p_birth + p_death, p_birth + p_death + p_pair)
                               takes it, the Gaussian move keeps the rest.  The ordered pair

@@ -72,7 +72,9 @@ struct D32 {            // state-independent part of one MH step
     float xr, yr, ph, mf;         // birth: relative form; move: offsets dx, dy, dt (s), dm
     float logu;
     unsigned pickw;
-    int type, bK, bvalid, pad;
+    int type, bK, bvalid;
+    int exch;           // joint move of a pair: exchange the two locations (else a common offset)
+    unsigned pick2;     // joint move of a pair: the second event among the others
 };
 
 struct T32 {            // one station whose variance the proposal changes
@@ -81,6 +83,13 @@ struct T32 {            // one station whose variance the proposal changes
     float E0o, E0n;
     int skip;           // owner whose arrival leaves the station (-1: none)
     int u0;             // first float4 group of this task in the step's flat range
+};
+
+struct T32X {           // joint move of a pair: the second event's arrivals at the task's station
+    int pair;           // 0: a one-event task
+    int exch;           // the pair exchanges its locations (else a common offset)
+    int has_o2, has_n2, k0o2, k0n2, skip2;
+    float E0o2, E0n2;
 };
 
 struct P32 {            // an event: float64 master, float32 terms, region-relative position
@@ -108,7 +117,9 @@ struct Sm {
     SA* sarr;           // [blk_cap][scap]
     D32* draws;
     A32* cand;          // [2][arr_cap]
+    A32* cand2;         // [2][arr_cap] the second candidate of a joint move
     T32* tasks;         // [2][task_cap]
+    T32X* tasksx;       // [2][task_cap] with joint moves (p_pair > 0), else null
     double *nx, *ny, *nt;
     float *nph, *nmf;
     int* nK;
@@ -135,11 +146,14 @@ struct Sm {
     double dlp[2];      // log-prior change of the step
     int nb_start[64], nb_cnt[64], nb_off[65];   // neighbouring cells of the region (prologue)
     P32 c[2];           // candidate of each step buffer
+    P32 c2[2];          // joint move of a pair: the second candidate
+    int idx2[2], ncand2[2];
     int warp_cnt[32];
     float2 redf[32];
     // statistics of this CTA: proposed[3], evaluated[3], accepted[3], priced
-    // samples, re-synthesised samples, unique window samples (thread 0)
-    unsigned long long cnt[12];
+    // samples, re-synthesised samples, unique window samples, joint moves
+    // proposed, evaluated, accepted (thread 0)
+    unsigned long long cnt[15];
 };
 
 // carve the dynamic shared buffer; returns its size (base may be null).  With
@@ -176,7 +190,9 @@ __host__ __device__ inline size_t layout32(const Geo& g, Sm* S, unsigned char* b
     SA* sarr = (SA*)gtake(sizeof(SA) * B * g.frz_cap);
     D32* draws = (D32*)take(sizeof(D32) * (size_t)g.k);
     A32* cand = (A32*)take(sizeof(A32) * 2 * (size_t)g.arr_cap);
+    A32* cand2 = (A32*)take(sizeof(A32) * 2 * (size_t)g.arr_cap);
     T32* tasks = (T32*)take(sizeof(T32) * 2 * (size_t)g.task_cap);
+    T32X* tasksx = g.p_pair > 0.0 ? (T32X*)take(sizeof(T32X) * 2 * (size_t)g.task_cap) : nullptr;
     double *nx = (double*)take(8 * E), *ny = (double*)take(8 * E), *nt = (double*)take(8 * E);
     float *nph = (float*)take(4 * E), *nmf = (float*)take(4 * E);
     int* nK = (int*)take(4 * E);
@@ -196,7 +212,7 @@ __host__ __device__ inline size_t layout32(const Geo& g, Sm* S, unsigned char* b
         S->mx = mx; S->my = my; S->mt = mt; S->mm = mm; S->eid = eid; S->exr = exr; S->eyr = eyr;
         S->enarr = enarr; S->order = order; S->freel = freel; S->earr = earr;
         S->tabB = tabB; S->tabD = tabD; S->elq = elq; S->pcum = pcum; S->pidx = pidx; S->bsta = bsta; S->bx = bx; S->by = by;
-        S->scnt = scnt; S->sarr = sarr; S->draws = draws; S->cand = cand; S->tasks = tasks;
+        S->scnt = scnt; S->sarr = sarr; S->draws = draws; S->cand = cand; S->cand2 = cand2; S->tasks = tasks; S->tasksx = tasksx;
         S->nx = nx; S->ny = ny; S->nt = nt; S->nph = nph; S->nmf = nmf; S->nK = nK;
     }
     if (gbytes) *gbytes = go;
@@ -381,13 +397,37 @@ __device__ __noinline__ bool learned_birth(const Geo& g, const Dev& d, const Sm&
     return true;
 }
 
+// a candidate event at (x, y, t, m) (float64 master; xr, yr its position
+// relative to the region's cell origin in float32): its float32 terms, and
+// whether it lies in the region, the domain, [0, T) and m >= 2 -- decided in
+// float32 away from the edges, by the exact float64 test within kDr / kDm
+__device__ __forceinline__ int cand_of(const Geo& g, const Sm& S, double x, double y, double t, double m, float xr,
+                                       float yr, P32& c) {
+    c.x = x; c.y = y; c.t = t; c.m = m;
+    event_terms32(g, c.t, c.m, c.K, c.ph, c.mf);
+    c.xr = xr;
+    c.yr = yr;
+    const bool xin = c.xr >= S.rl[0] + kDr && c.xr < S.rl[1] - kDr;
+    const bool yin = c.yr >= S.rl[2] + kDr && c.yr < S.rl[3] - kDr;
+    const bool xout = c.xr < S.rl[0] - kDr || c.xr >= S.rl[1] + kDr;
+    const bool yout = c.yr < S.rl[2] - kDr || c.yr >= S.rl[3] + kDr;
+    const bool tin = c.K >= 1 && c.K + 2 <= g.TfK;
+    const bool min_ = c.mf >= 2.f + kDm;
+    const bool mout = c.mf < 2.f - kDm;
+    if (xout || yout || mout) return 0;
+    if (xin && yin && tin && min_) return 1;
+    const int v = inside_exact(g, S.sx, S.sy, S.cell, c.x, c.y, c.t, c.m);
+    if (v) to_rel(g, S.X0, S.Y0, c);
+    return v;
+}
+
 // ---------------------------------------------------------------------------
 // preparation of one step (all lanes of warp 0): decode the proposal against
 // the current state, find the stations the candidate reaches, and merge the
 // old and new arrivals into tasks (one per station whose variance changes)
 // in step buffer sl; with STAGE, start the bulk copies of the task windows
 // ---------------------------------------------------------------------------
-template <bool STAGE>
+template <bool STAGE, bool PAIR>
 __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int step, int sl) {
     const int lane = threadIdx.x & 31;
     if (STAGE) {
@@ -404,52 +444,71 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
     const int n_own = S.n_own, n_blk = S.n_blk;
     A32* cd = S.cand + sl * g.arr_cap;
     T32* tk = S.tasks + sl * g.task_cap;
-    int valid = 0, idx = -1, ps = -1;
-    P32 c;
+    A32* cd2 = S.cand2 + sl * g.arr_cap;
+    int valid = 0, idx = -1, ps = -1, idx2 = -1, ps2 = -1;
+    P32 c, c2;
     c.x = c.y = c.t = c.m = 0.0;
     c.xr = c.yr = c.ph = c.mf = 0.f;
     c.K = 0;
     c.pad = 0;
     c.lq = 0.0;
+    c2 = c;
     if (dr.type == 0) {
         valid = dr.bvalid;
         c.x = dr.bx; c.y = dr.by; c.t = dr.bt; c.m = dr.bm;
         c.xr = dr.xr; c.yr = dr.yr; c.ph = dr.ph; c.mf = dr.mf; c.K = dr.bK;
         c.lq = dr.blq;
+    } else if (PAIR && dr.type == 3) {
+        // joint move of a pair: the ordered pair (idx, idx2), then either the
+        // exchange of their locations (each keeps its time and magnitude) or
+        // one common offset; both candidates must lie in the region
+        if (n_own >= 2) {
+            idx = pick32(dr.pickw, n_own);
+            const int j = pick32(dr.pick2, n_own - 1);
+            idx2 = j + (j >= idx ? 1 : 0);
+            ps = S.order[idx];
+            ps2 = S.order[idx2];
+            if (dr.exch) {
+                valid = cand_of(g, S, S.mx[ps2], S.my[ps2], S.mt[ps], S.mm[ps], S.exr[ps2], S.eyr[ps2], c) &&
+                        cand_of(g, S, S.mx[ps], S.my[ps], S.mt[ps2], S.mm[ps2], S.exr[ps], S.eyr[ps], c2);
+            } else {
+                valid = cand_of(g, S, __dadd_rn(S.mx[ps], dr.bx), __dadd_rn(S.my[ps], dr.by),
+                                __dadd_rn(S.mt[ps], dr.bt), __dadd_rn(S.mm[ps], dr.bm), S.exr[ps] + dr.xr,
+                                S.eyr[ps] + dr.yr, c) &&
+                        cand_of(g, S, __dadd_rn(S.mx[ps2], dr.bx), __dadd_rn(S.my[ps2], dr.by),
+                                __dadd_rn(S.mt[ps2], dr.bt), __dadd_rn(S.mm[ps2], dr.bm), S.exr[ps2] + dr.xr,
+                                S.eyr[ps2] + dr.yr, c2);
+            }
+        }
     } else if (n_own > 0) {
         idx = pick32(dr.pickw, n_own);
         ps = S.order[idx];
         if (dr.type == 1) {
             valid = 1;
         } else {
-            // the float64 state the move proposes, its float32 terms, and the
-            // region-relative position for the region test
-            c.x = __dadd_rn(S.mx[ps], dr.bx);   // the float64 offsets of the draw
-            c.y = __dadd_rn(S.my[ps], dr.by);
-            c.t = __dadd_rn(S.mt[ps], dr.bt);
-            c.m = __dadd_rn(S.mm[ps], dr.bm);
-            event_terms32(g, c.t, c.m, c.K, c.ph, c.mf);
-            c.xr = S.exr[ps] + dr.xr;
-            c.yr = S.eyr[ps] + dr.yr;
-            const bool xin = c.xr >= S.rl[0] + kDr && c.xr < S.rl[1] - kDr;
-            const bool yin = c.yr >= S.rl[2] + kDr && c.yr < S.rl[3] - kDr;
-            const bool xout = c.xr < S.rl[0] - kDr || c.xr >= S.rl[1] + kDr;
-            const bool yout = c.yr < S.rl[2] - kDr || c.yr >= S.rl[3] + kDr;
-            const bool tin = c.K >= 1 && c.K + 2 <= g.TfK;
-            const bool min_ = c.mf >= 2.f + kDm;
-            const bool mout = c.mf < 2.f - kDm;
-            if (xout || yout || mout) {
-                valid = 0;
-            } else if (xin && yin && tin && min_) {
-                valid = 1;
-            } else {
-                valid = inside_exact(g, S.sx, S.sy, S.cell, c.x, c.y, c.t, c.m);
-                if (valid) to_rel(g, S.X0, S.Y0, c);
-            }
+            // the float64 state the move proposes (the float64 offsets of the
+            // draw), its float32 terms and region-relative position
+            valid = cand_of(g, S, __dadd_rn(S.mx[ps], dr.bx), __dadd_rn(S.my[ps], dr.by),
+                            __dadd_rn(S.mt[ps], dr.bt), __dadd_rn(S.mm[ps], dr.bm), S.exr[ps] + dr.xr,
+                            S.eyr[ps] + dr.yr, c);
         }
     }
     // candidate arrivals, lanes over blanket slots, compacted in slot order
-    int ncand = 0;
+    auto arrivals = [&](const P32& e, A32* out) {
+        int n = 0;
+        for (int b0 = 0; b0 < n_blk; b0 += 32) {
+            const int b = b0 + lane;
+            int k0 = 0;
+            float E0 = 0.f;
+            const bool r = b < n_blk && arrival32c(g, e.x, e.y, e.t, e.K, e.ph, e.mf, S.bx[b], S.by[b], k0, E0);
+            const unsigned bal = __ballot_sync(FULL, r);
+            const int pos = n + __popc(bal & ((1u << lane) - 1));
+            if (r && pos < g.arr_cap) out[pos] = A32{b, k0, E0, 0};
+            n += __popc(bal);
+        }
+        return n;
+    };
+    int ncand = 0, ncand2 = 0;
     if (valid && dr.type != 1) {
         for (int b0 = 0; b0 < n_blk; b0 += 32) {
             const int b = b0 + lane;
@@ -462,11 +521,80 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
             ncand += __popc(bal);
         }
     }
+    if (PAIR && valid && dr.type == 3) ncand2 = arrivals(c2, cd2);
     __syncwarp();
     if (lane == 0) {
-        int err = ncand > g.arr_cap ? CMH_ERR_CAPACITY : 0;
+        int err = (ncand > g.arr_cap || ncand2 > g.arr_cap) ? CMH_ERR_CAPACITY : 0;
         int ntask = 0, units = 0, width = 0;
-        if (valid && !err) {
+        auto add_task = [&](T32& T, int lo, int hi) {
+            lo = max(lo, 0);
+            hi = (long long)hi > g.n_samp ? (int)g.n_samp : hi;
+            T.lo = lo;
+            T.hi = hi;
+            if (lo < hi) {
+                T.u0 = units;   // float4 groups [lo/4, ceil(hi/4)) continue the flat range
+                units += ((hi + 3) >> 2) - (lo >> 2);
+                width += hi - lo;
+                tk[ntask++] = T;
+            }
+        };
+        if (PAIR && valid && !err && dr.type == 3) {
+            // the two events' old arrivals and the two candidates', by slot;
+            // the second event's go to the task's extension record
+            T32X* tx = S.tasksx + sl * g.task_cap;
+            const A32* L[4] = {S.earr + ps * g.arr_cap, S.earr + ps2 * g.arr_cap, cd, cd2};
+            const int nl[4] = {S.enarr[ps], S.enarr[ps2], ncand, ncand2};
+            int il[4] = {0, 0, 0, 0};
+            for (;;) {
+                int slot = 1 << 30;
+                for (int q = 0; q < 4; ++q)
+                    if (il[q] < nl[q] && L[q][il[q]].slot < slot) slot = L[q][il[q]].slot;
+                if (slot == 1 << 30) break;
+                if (ntask >= g.task_cap) {
+                    err = CMH_ERR_CAPACITY;
+                    break;
+                }
+                T32 T;
+                T32X X;
+                T.slot = slot;
+                T.row = S.bsta[slot];
+                T.skip = ps;
+                T.has_o = T.has_n = 0;
+                T.k0o = T.k0n = 0;
+                T.E0o = T.E0n = 0.f;
+                X.pair = 1;
+                X.exch = dr.exch;
+                X.skip2 = ps2;
+                X.has_o2 = X.has_n2 = X.k0o2 = X.k0n2 = 0;
+                X.E0o2 = X.E0n2 = 0.f;
+                int ws[4], nws = 0;   // window starts at this station, in start order
+                for (int q = 0; q < 4; ++q) {
+                    if (il[q] >= nl[q] || L[q][il[q]].slot != slot) continue;
+                    const A32 A = L[q][il[q]++];
+                    if (q == 0) { T.has_o = 1; T.k0o = A.k0; T.E0o = A.E0; }
+                    if (q == 1) { X.has_o2 = 1; X.k0o2 = A.k0; X.E0o2 = A.E0; }
+                    if (q == 2) { T.has_n = 1; T.k0n = A.k0; T.E0n = A.E0; }
+                    if (q == 3) { X.has_n2 = 1; X.k0n2 = A.k0; X.E0n2 = A.E0; }
+                    int w = nws++;
+                    for (; w > 0 && ws[w - 1] > A.k0; --w) ws[w] = ws[w - 1];
+                    ws[w] = A.k0;
+                }
+                // the two events may be far apart in time: one task per
+                // disjoint stretch of the windows' union, not their hull
+                for (int a = 0; a < nws && !err;) {
+                    const int lo = ws[a];
+                    int hi = ws[a] + g.n_w;
+                    for (++a; a < nws && ws[a] <= hi; ++a) hi = max(hi, ws[a] + g.n_w);
+                    if (ntask >= g.task_cap) {
+                        err = CMH_ERR_CAPACITY;
+                        break;
+                    }
+                    const int n_before = ntask;
+                    add_task(T, lo, hi);
+                    if (ntask > n_before) tx[n_before] = X;
+                }
+            }
+        } else if (valid && !err) {
             // merge the old event's arrivals and the candidate's, by slot
             const A32* oa = (ps >= 0 && dr.type != 0) ? S.earr + ps * g.arr_cap : nullptr;
             const int no = oa ? S.enarr[ps] : 0;
@@ -504,11 +632,21 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
                 hi = (long long)hi > g.n_samp ? (int)g.n_samp : hi;
                 T.lo = lo;
                 T.hi = hi;
+                const int n_before = ntask;
                 if (lo < hi) {
                     T.u0 = units;   // float4 groups [lo/4, ceil(hi/4)) continue the flat range
                     units += ((hi + 3) >> 2) - (lo >> 2);
                     width += hi - lo;
                     tk[ntask++] = T;
+                }
+                if (PAIR && ntask > n_before) {   // a one-event task of a kernel with joint moves
+                    T32X X;
+                    X.pair = 0;
+                    X.exch = 0;
+                    X.has_o2 = X.has_n2 = X.k0o2 = X.k0n2 = 0;
+                    X.skip2 = -1;
+                    X.E0o2 = X.E0n2 = 0.f;
+                    S.tasksx[sl * g.task_cap + n_before] = X;
                 }
             }
         }
@@ -550,6 +688,12 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
             } else if (dr.type == 1) {
                 thr = (double)dr.logu - (S.tabD[n_own] - S.elq[ps]);
                 dlp = S.mm[ps] - g.lb0;
+            } else if (PAIR && dr.type == 3) {
+                // symmetric proposal: the two events' prior ratio, the change
+                // of their magnitudes (0 for an exchange)
+                const double dm = __dadd_rn(__dsub_rn(c.m, S.mm[ps]), __dsub_rn(c2.m, S.mm[ps2]));
+                thr = (double)dr.logu + dm;
+                dlp = -dm;
             } else {
                 const double dm = __dsub_rn(c.m, S.mm[ps]);
                 thr = (double)dr.logu + dm;
@@ -567,6 +711,11 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
         S.type[sl] = dr.type;
         S.ncand[sl] = ncand;
         S.c[sl] = c;
+        if (PAIR) {
+            S.idx2[sl] = idx2;
+            S.ncand2[sl] = ncand2;
+            S.c2[sl] = c2;
+        }
     }
     __syncwarp();
 }
@@ -574,15 +723,19 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
 // the change of the log-likelihood over one float4 group of samples
 // k4 .. k4+3 of task T (samples outside [T.lo, T.hi) or either window add 0):
 // the four terms summed in order
-template <bool MEAN>
-__device__ __forceinline__ float group_terms(const Geo& g, const Sm& S, const T32& T, int k4, float4 s4,
-                                             float4 v4) {
+template <bool MEAN, bool PAIR>
+__device__ __forceinline__ float group_terms(const Geo& g, const Sm& S, const T32& T, const T32X* X, int k4,
+                                             float4 s4, float4 v4) {
     // one SFU evaluation per arrival for the whole group (see arr_var32)
     const float bo = T.has_o ? arr_base32(g, T.E0o, T.k0o, k4) : 0.f;
     const float bn = T.has_n ? arr_base32(g, T.E0n, T.k0n, k4) : 0.f;
+    // joint move of a pair: the second event's old and new arrivals
+    const bool pr = PAIR && X->pair;
+    const float bo2 = pr && X->has_o2 ? arr_base32(g, X->E0o2, X->k0o2, k4) : 0.f;
+    const float bn2 = pr && X->has_n2 ? arr_base32(g, X->E0n2, X->k0n2, k4) : 0.f;
     const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
     const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
-    float term[4], cnv[4];
+    float term[4], cnv[4], cnv2[4];
     unsigned need = 0;   // samples whose V' is rebuilt from the arrivals that stay
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -593,8 +746,20 @@ __device__ __forceinline__ float group_terms(const Geo& g, const Sm& S, const T3
         // priced change is the change written to V on accept
         const float co = io ? __fmul_rn(bo, g.rho_f[e]) : 0.f;
         const float cn = inn ? __fmul_rn(bn, g.rho_f[e]) : 0.f;
-        const float dd = cn - co;
+        float dd = cn - co;
         cnv[e] = cn;
+        cnv2[e] = 0.f;
+        if (pr) {
+            const bool io2 = X->has_o2 && (unsigned)(kk - X->k0o2) < (unsigned)g.n_w;
+            const bool in2 = X->has_n2 && (unsigned)(kk - X->k0n2) < (unsigned)g.n_w;
+            const float co2 = io2 ? __fmul_rn(bo2, g.rho_f[e]) : 0.f;
+            const float cn2 = in2 ? __fmul_rn(bn2, g.rho_f[e]) : 0.f;
+            cnv2[e] = cn2;
+            // pair the terms that nearly cancel: an exchange puts each event
+            // where the other was, a common offset moves each a little
+            dd = X->exch ? __fadd_rn(__fsub_rn(cn, co2), __fsub_rn(cn2, co))
+                         : __fadd_rn(__fsub_rn(cn, co), __fsub_rn(cn2, co2));
+        }
         term[e] = 0.f;
         if (MEAN && kk < T.hi && dd != 0.f) {
             // additive reading: (d (s - mu) - d^2 / 2) / noise, mu = vv
@@ -629,7 +794,8 @@ __device__ __forceinline__ float group_terms(const Geo& g, const Sm& S, const T3
         const int nl = S.scnt[T.slot];
         for (int o = 0; o < nl; ++o) {
             const SA A = L[o];
-            if (A.own == T.skip || (unsigned)(k4 + 3 - A.k0) >= (unsigned)(g.n_w + 3)) continue;
+            if (A.own == T.skip || (pr && A.own == X->skip2) || (unsigned)(k4 + 3 - A.k0) >= (unsigned)(g.n_w + 3))
+                continue;
             const float base = arr_base32(g, A.E0, A.k0, k4);
 #pragma unroll
             for (int e = 0; e < 4; ++e)
@@ -640,6 +806,7 @@ __device__ __forceinline__ float group_terms(const Geo& g, const Sm& S, const T3
         for (int e = 0; e < 4; ++e) {
             if (!((need >> e) & 1u)) continue;
             if (cnv[e] != 0.f) kahan_add32(a2[e], c2[e], cnv[e]);
+            if (cnv2[e] != 0.f) kahan_add32(a2[e], c2[e], cnv2[e]);
             const float V = vv[e], sm = sv[e];
             const float Vr = a2[e] - c2[e];
             const float q = __fmul_rn(__fmul_rn(sm, sm), __fsub_rn(rcp_sfu(Vr), rcp_sfu(V)));
@@ -655,7 +822,7 @@ __device__ __forceinline__ float group_terms(const Geo& g, const Sm& S, const T3
 // thread issues the loads of kUnroll groups before computing them), one
 // float-float partial per warp in S.redf
 // ---------------------------------------------------------------------------
-template <bool STAGE, bool MEAN>
+template <bool STAGE, bool MEAN, bool PAIR>
 __device__ __forceinline__ void price_step(const Geo& g, const Dev& d, Sm& S, int sl) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const T32* tk = S.tasks + sl * g.task_cap;
@@ -694,7 +861,8 @@ __device__ __forceinline__ void price_step(const Geo& g, const Dev& d, Sm& S, in
 #pragma unroll
         for (int r = 0; r < kUnroll; ++r) {
             if (ti_[r] < 0) continue;
-            kahan_add32(acc, comp, group_terms<MEAN>(g, S, tk[ti_[r]], k_[r], s4[r], v4[r]));
+            const T32X* X = PAIR ? S.tasksx + sl * g.task_cap + ti_[r] : nullptr;
+            kahan_add32(acc, comp, group_terms<MEAN, PAIR>(g, S, tk[ti_[r]], X, k_[r], s4[r], v4[r]));
         }
     }
     float2 v = make_float2(acc, -comp);
@@ -732,15 +900,19 @@ __device__ __forceinline__ void iv_add(Sm& S, int slot, int lo, int hi) {
 // record it, and on a commit update the region's event bookkeeping; rm / put
 // receive the event whose arrivals leave / join the station lists (-1: none).
 // t is the float-float sum of the step's partial log-likelihood changes.
+template <bool PAIR>
 __device__ __forceinline__ int decide_lane0(const Geo& g, const Dev& d, Sm& S, long long sweep, int cell, int step,
-                                         int sl, float2 t, int valid, int& rm, int& put) {
+                                         int sl, float2 t, int valid, int& rm, int& put, int& rm2, int& put2) {
     const int type = S.type[sl], n_own = S.n_own, idx = S.idx[sl];
     const D32& dr = S.draws[step];
-    ++S.cnt[type];
+    // counters: birth, death, move in [0..8]; the joint move of a pair in [12..14]
+    const int c_prop = (!PAIR || type < 3) ? type : 12, c_eval = (!PAIR || type < 3) ? 3 + type : 13,
+              c_acc = (!PAIR || type < 3) ? 6 + type : 14;
+    ++S.cnt[c_prop];
     double dll = 0.0, la = -INFINITY, dlp = 0.0;
     int acc = 0;
     if (valid) {
-        ++S.cnt[3 + type];
+        ++S.cnt[c_eval];
         if (g.count_unique) {
             const T32* tk = S.tasks + sl * g.task_cap;
             for (int ti = 0; ti < S.ntask[sl]; ++ti) iv_add(S, tk[ti].slot, tk[ti].lo, tk[ti].hi);
@@ -771,7 +943,7 @@ __device__ __forceinline__ int decide_lane0(const Geo& g, const Dev& d, Sm& S, l
         }
     }
     const int do_commit = acc && g.commit;
-    if (acc) ++S.cnt[6 + type];
+    if (acc) ++S.cnt[c_acc];
     if (do_commit) {
         S.cnt[10] += (unsigned long long)S.width[sl];
         S.region_dlp += dll + dlp;
@@ -790,6 +962,7 @@ __device__ __forceinline__ int decide_lane0(const Geo& g, const Dev& d, Sm& S, l
             put = ps;
         } else {
             rm = put = S.order[idx];
+            if (PAIR && type == 3) rm2 = put2 = S.order[S.idx2[sl]];
         }
     }
     return do_commit;
@@ -837,20 +1010,19 @@ __device__ __forceinline__ void lists_add(const Geo& g, Sm& S, int ps, const A32
     }
 }
 
-// the committed candidate of buffer sl becomes own event ps (one thread):
-// its master, density term, relative position and arrival cache, and its
-// arrivals join the station lists
-__device__ __forceinline__ void put_event(const Geo& g, const Dev& d, Sm& S, int sl, int ps) {
-    const P32& c = S.c[sl];
-    const A32* cd = S.cand + sl * g.arr_cap;
+// a committed candidate c (arrivals cd[0..ncd)) of a step of type `type`
+// becomes own event ps (one thread): its master, density term, relative
+// position and arrival cache, and its arrivals join the station lists
+__device__ __forceinline__ void put_event(const Geo& g, const Dev& d, Sm& S, const P32& c, const A32* cd, int ncd,
+                                          int type, int ps) {
     S.mx[ps] = c.x; S.my[ps] = c.y; S.mt[ps] = c.t; S.mm[ps] = c.m;
     // a move's own log alpha has no position term: the moved event's term
     // (for a later death) is taken here
-    S.elq[ps] = S.type[sl] == 0 ? c.lq : (g.bt_on ? bt_lq(g, d, S, c.x, c.y, c.t, c.m) : S.lq_unif);
+    S.elq[ps] = type == 0 ? c.lq : (g.bt_on ? bt_lq(g, d, S, c.x, c.y, c.t, c.m) : S.lq_unif);
     S.exr[ps] = c.xr; S.eyr[ps] = c.yr;
-    for (int a = 0; a < S.ncand[sl]; ++a) S.earr[ps * g.arr_cap + a] = cd[a];
-    S.enarr[ps] = S.ncand[sl];
-    lists_add(g, S, ps, cd, S.ncand[sl]);
+    for (int a = 0; a < ncd; ++a) S.earr[ps * g.arr_cap + a] = cd[a];
+    S.enarr[ps] = ncd;
+    lists_add(g, S, ps, cd, ncd);
 }
 
 // re-synthesise V over the windows of buffer sl's tasks from the station
@@ -934,7 +1106,7 @@ __device__ __forceinline__ bool region_begin(const Geo& g, const Dev& d, int cel
         S.region_dlp = 0.0;
         S.acc = 0;
     }
-    if (tid < 12) S.cnt[tid] = 0;
+    if (tid < 15) S.cnt[tid] = 0;
     // only thread 0 has S.err initialised yet: the others would read what an
     // earlier CTA left in this shared memory
     if (__syncthreads_or(tid == 0 && S.err != 0)) {
@@ -1075,6 +1247,8 @@ __device__ __forceinline__ bool region_begin(const Geo& g, const Dev& d, int cel
     // ---- the k steps' random draws (Philox stream 0, counter (sweep, cell, step, 0|1))
     const unsigned long long thr_b = (unsigned long long)ceil(g.p_birth * 9007199254740992.0);
     const unsigned long long thr_d = (unsigned long long)ceil(__dadd_rn(g.p_birth, g.p_death) * 9007199254740992.0);
+    const unsigned long long thr_p =
+        (unsigned long long)ceil(__dadd_rn(__dadd_rn(g.p_birth, g.p_death), g.p_pair) * 9007199254740992.0);
     // one warp, warp 1, draws them: the float64 of the walk offsets (~250
     // float64 instructions, each holding its sub-partition's float64 pipe for
     // ~64 cycles whatever the number of active lanes) then runs on a
@@ -1087,12 +1261,15 @@ __device__ __forceinline__ bool region_begin(const Geo& g, const Dev& d, int cel
         philox4x64(c1, g.seed, 0ULL);
         D32 D;
         const unsigned long long u53 = c0[0] >> 11;   // u < p  <=>  u53 < p 2^53 (rounded up)
-        D.type = u53 < thr_b ? 0 : (u53 < thr_d ? 1 : 2);
+        D.type = u53 < thr_b ? 0 : (u53 < thr_d ? 1 : (u53 < thr_p ? 3 : 2));
+        // joint move of a pair: the second pick from word 7, the exchange
+        // when bit 36 of word 1 is clear
+        D.pick2 = (unsigned)(c1[3] & 0xffffffffULL);
+        D.exch = ((c0[1] >> 36) & 1ULL) == 0ULL;
         D.pickw = (unsigned)(c0[1] & 0xffffffffULL);
         D.logu = __logf(u32o(c1[2]));
         D.bvalid = 0;
         D.bK = 0;
-        D.pad = 0;
         D.bx = D.by = D.bt = D.bm = D.blb = D.blq = 0.0;
         if (D.type == 0) {
             P32 e;
@@ -1115,8 +1292,9 @@ __device__ __forceinline__ bool region_begin(const Geo& g, const Dev& d, int cel
             const bool sure = e.xr >= S.rl[0] + kDr && e.xr < S.rl[1] - kDr && e.yr >= S.rl[2] + kDr &&
                               e.yr < S.rl[3] - kDr && e.K >= 1 && e.K + 2 <= g.TfK;
             D.bvalid = sure || inside_exact(g, S.sx, S.sy, cell, e.x, e.y, e.t, e.m);
-        } else if (D.type == 2) {
-            // the walk offset in float64, the same definition as the float64
+        } else if (D.type == 2 || D.type == 3) {
+            // the walk offset in float64 (a joint move's common offset too),
+            // the same definition as the float64
             // form (Box-Muller, each Gaussian rounded to 2^-20, signs from
             // word 1): the float64 candidate is then the one the exact chain
             // proposes, not one a float32 rounding away from it, so the
@@ -1157,7 +1335,7 @@ __device__ __forceinline__ bool region_begin(const Geo& g, const Dev& d, int cel
 // steps and the write-back of the region's events.  MEAN: the additive
 // likelihood reading (a kernel per reading, so each pricing loop is compiled
 // for its own)
-template <bool STAGE, bool MEAN>
+template <bool STAGE, bool MEAN, bool PAIR>
 __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell, long long sweep, Sm& S) {
     const Store St = d.st[sweep & 1];
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
@@ -1255,18 +1433,18 @@ __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell
         }
         __syncwarp();
     }
-    if (wid == 0) prepare_step<STAGE>(g, d, S, 0, 0);
+    if (wid == 0) prepare_step<STAGE, PAIR>(g, d, S, 0, 0);
     __syncthreads();
     for (int step = 0; step < g.k; ++step) {
         const int sl = step & 1;
         const int valid = S.valid[sl];
         // ================ prepare step+1 (warp 0) || price step (warps 1..) =========
         if (wid == 0) {
-            if (step + 1 < g.k) prepare_step<STAGE>(g, d, S, step + 1, sl ^ 1);   // assumes a rejection
+            if (step + 1 < g.k) prepare_step<STAGE, PAIR>(g, d, S, step + 1, sl ^ 1);   // assumes a rejection
         } else if (valid) {
             // (this buffer is refilled by bulk copies only after two more
             // barriers: these generic reads come first)
-            price_step<STAGE, MEAN>(g, d, S, sl);
+            price_step<STAGE, MEAN, PAIR>(g, d, S, sl);
         }
         // errors are set before a barrier and read through its OR, so every
         // thread leaves the loop at the same point
@@ -1282,20 +1460,27 @@ __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell
                 t = ff_add32(t, w2);
             }
             int rm = -1, put = -1;   // event leaving its station lists / event (re)joining them
+            int rm2 = -1, put2 = -1; // the second event of a joint move
             if (lane == 0) {
                 if (STAGE && S.on[sl]) {   // this buffer's copies have landed (the workers waited)
                     if (!mbar_wait(&S.bar[sl], (unsigned)S.ph[sl])) S.err = CMH_ERR_TIMEOUT;
                     S.ph[sl] ^= 1;
                     S.on[sl] = 0;
                 }
-                S.acc = decide_lane0(g, d, S, sweep, cell, step, sl, t, valid, rm, put);
+                S.acc = decide_lane0<PAIR>(g, d, S, sweep, cell, step, sl, t, valid, rm, put, rm2, put2);
             }
             // the removed or moved event's arrivals leave their station lists
             // (all lanes), then the new arrivals join (lane 0)
             rm = __shfl_sync(FULL, rm, 0);
             put = __shfl_sync(FULL, put, 0);
             if (rm >= 0) lists_remove_warp(g, S, rm);
-            if (lane == 0 && put >= 0) put_event(g, d, S, sl, put);
+            if (PAIR) {   // the second event of a joint move
+                rm2 = __shfl_sync(FULL, rm2, 0);
+                if (rm2 >= 0) lists_remove_warp(g, S, rm2);
+            }
+            if (lane == 0 && put >= 0) put_event(g, d, S, S.c[sl], S.cand + sl * g.arr_cap, S.ncand[sl], S.type[sl], put);
+            if (PAIR && lane == 0 && put2 >= 0)
+                put_event(g, d, S, S.c2[sl], S.cand2 + sl * g.arr_cap, S.ncand2[sl], S.type[sl], put2);
         }
         if (__syncthreads_or(S.err != 0)) break;
         // ================ commit: re-synthesise V on the touched windows ============
@@ -1306,14 +1491,14 @@ __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell
         if (S.acc) {
             const int rt = STAGE ? tid : tid - 32, rn = STAGE ? nthr : nthr - 32;
             if (!STAGE && wid == 0) {
-                if (step + 1 < g.k) prepare_step<STAGE>(g, d, S, step + 1, sl ^ 1);
+                if (step + 1 < g.k) prepare_step<STAGE, PAIR>(g, d, S, step + 1, sl ^ 1);
             } else {
                 resynth(g, d, S, sl, rt, rn);
             }
             if (STAGE) {
                 fence_async_global();   // the new V is visible to the next bulk copies
                 __syncthreads();
-                if (wid == 0 && step + 1 < g.k) prepare_step<STAGE>(g, d, S, step + 1, sl ^ 1);
+                if (wid == 0 && step + 1 < g.k) prepare_step<STAGE, PAIR>(g, d, S, step + 1, sl ^ 1);
             }
             if (__syncthreads_or(S.err != 0)) break;
         }
@@ -1343,6 +1528,8 @@ __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell
         d.region_dlp[cell] = S.region_dlp;
         for (int t = 0; t < 11; ++t)
             if (S.cnt[t]) atomicAdd(&d.stats[t], S.cnt[t]);
+        for (int t = 0; t < 3; ++t)   // joint moves of a pair: proposed, evaluated, accepted
+            if (S.cnt[12 + t]) atomicAdd(&d.stats[11 + t], S.cnt[12 + t]);
         if (g.count_unique) {
             unsigned long long u = S.cnt[11];
             for (int b = 0; b < S.n_blk; ++b)
@@ -1354,14 +1541,14 @@ __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell
 
 
 // both parts, for kernels without dependency waits
-template <bool STAGE, bool MEAN>
+template <bool STAGE, bool MEAN, bool PAIR>
 __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cell, long long sweep, Sm& S,
                                              unsigned char* smem) {
-    if (region_begin<STAGE>(g, d, cell, sweep, S, smem)) region_rest<STAGE, MEAN>(g, d, cell, sweep, S);
+    if (region_begin<STAGE>(g, d, cell, sweep, S, smem)) region_rest<STAGE, MEAN, PAIR>(g, d, cell, sweep, S);
 }
 
 // one colour phase: a CTA per region of the colour
-template <bool STAGE, bool MEAN>
+template <bool STAGE, bool MEAN, bool PAIR>
 __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const __grid_constant__ Geo g,
                                                                            const __grid_constant__ Dev d, int colour) {
     if (*d.status) return;
@@ -1370,7 +1557,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Sm S;
     init_staging<STAGE>(S);
-    region_phase<STAGE, MEAN>(g, d, d.colour_cells[colour * g.max_rpc + blockIdx.x], sweep, S, smem);
+    region_phase<STAGE, MEAN, PAIR>(g, d, d.colour_cells[colour * g.max_rpc + blockIdx.x], sweep, S, smem);
 }
 
 __device__ __forceinline__ long long ld_acquire(const long long* p) {
@@ -1394,7 +1581,7 @@ __device__ __forceinline__ void st_release(long long* p, long long v) {
 // results do not depend on the order in which CTAs take regions.  Every
 // region a CTA waits for was taken earlier by a CTA that is running, so the
 // waits end; they are bounded all the same (CMH_ERR_TIMEOUT).
-template <bool STAGE, bool MEAN>
+template <bool STAGE, bool MEAN, bool PAIR>
 __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_kernel(const __grid_constant__ Geo g,
                                                                            const __grid_constant__ Dev d) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1446,7 +1633,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_kernel(const
             s_run = begun && *(volatile int*)d.status == 0;
         }
         __syncthreads();
-        if (s_run) region_rest<STAGE, MEAN>(g, d, cell, sweep, S);
+        if (s_run) region_rest<STAGE, MEAN, PAIR>(g, d, cell, sweep, S);
         __syncthreads();
         if (threadIdx.x == 0 && cell != g.hold_cell) {
             __threadfence();
@@ -1560,7 +1747,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_batch(const 
             s_run = begun && *(volatile int*)d.status == 0;
         }
         __syncthreads();
-        if (s_run) region_rest<false, MEAN>(g, d, cell, sweep, S);
+        if (s_run) region_rest<false, MEAN, false>(g, d, cell, sweep, S);
         __syncthreads();
         if (threadIdx.x == 0 && cell != g.hold_cell) {
             __threadfence();
@@ -1612,7 +1799,7 @@ cudaError_t launch_sweep32_batch(bool mean, const Geo* G, const Dev* D, int n_in
 // from global memory.
 cudaError_t choose_stage_cap(Geo& g, int requested) {
     g.stage_cap = 0;
-    if (requested == 0) return cudaSuccess;
+    if (requested == 0 || g.p_pair > 0.0) return cudaSuccess;
     if (requested > 0) {
         g.stage_cap = requested & ~3;
         return cudaSuccess;
@@ -1625,7 +1812,7 @@ cudaError_t choose_stage_cap(Geo& g, int requested) {
         (e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) ||
         (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) ||
         (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) ||
-        (e = cudaFuncGetAttributes(&fa, phase32_kernel<true, false>)))
+        (e = cudaFuncGetAttributes(&fa, phase32_kernel<true, false, false>)))
         return e;
     const int resident = std::min(kMinBlocks32, std::max(1, (g.max_rpc + n_sm - 1) / std::max(1, n_sm)));
     const long long dyn = (long long)layout32(g, nullptr, nullptr);
@@ -1638,34 +1825,50 @@ cudaError_t choose_stage_cap(Geo& g, int requested) {
     return cudaSuccess;
 }
 
+// the kernels of a model: one per staging x likelihood reading, and the
+// instantiation with joint moves of a pair (no staging, variance reading),
+// so that kernels without them carry none of their code
+const void* sweep32_func(const Geo& g) {
+    if (g.p_pair > 0.0) return (const void*)sweep32_kernel<false, false, true>;
+    if (g.stage_cap > 0)
+        return g.mean_mode ? (const void*)sweep32_kernel<true, true, false> : (const void*)sweep32_kernel<true, false, false>;
+    return g.mean_mode ? (const void*)sweep32_kernel<false, true, false> : (const void*)sweep32_kernel<false, false, false>;
+}
+
+const void* phase32_func(const Geo& g) {
+    if (g.p_pair > 0.0) return (const void*)phase32_kernel<false, false, true>;
+    if (g.stage_cap > 0)
+        return g.mean_mode ? (const void*)phase32_kernel<true, true, false> : (const void*)phase32_kernel<true, false, false>;
+    return g.mean_mode ? (const void*)phase32_kernel<false, true, false> : (const void*)phase32_kernel<false, false, false>;
+}
+
 cudaError_t prepare_phase32(const Geo& g) {
     const int bytes = (int)phase32_smem_bytes(g);
     cudaError_t e;
     const bool mn = g.mean_mode;
-    if ((e = raise_smem_limit(mn ? (const void*)phase32_kernel<false, true> : (const void*)phase32_kernel<false, false>,
+    if (g.p_pair > 0.0) {
+        if ((e = raise_smem_limit((const void*)phase32_kernel<false, false, true>, bytes)) ||
+            (e = raise_smem_limit((const void*)sweep32_kernel<false, false, true>, bytes)))
+            return e;
+        return cudaSuccess;
+    }
+    if ((e = raise_smem_limit(mn ? (const void*)phase32_kernel<false, true, false> : (const void*)phase32_kernel<false, false, false>,
                               bytes)) ||
-        (e = raise_smem_limit(mn ? (const void*)phase32_kernel<true, true> : (const void*)phase32_kernel<true, false>,
+        (e = raise_smem_limit(mn ? (const void*)phase32_kernel<true, true, false> : (const void*)phase32_kernel<true, false, false>,
                               bytes)) ||
-        (e = raise_smem_limit(mn ? (const void*)sweep32_kernel<false, true> : (const void*)sweep32_kernel<false, false>,
+        (e = raise_smem_limit(mn ? (const void*)sweep32_kernel<false, true, false> : (const void*)sweep32_kernel<false, false, false>,
                               bytes)) ||
-        (e = raise_smem_limit(mn ? (const void*)sweep32_kernel<true, true> : (const void*)sweep32_kernel<true, false>,
+        (e = raise_smem_limit(mn ? (const void*)sweep32_kernel<true, true, false> : (const void*)sweep32_kernel<true, false, false>,
                               bytes)))
         return e;
     return cudaSuccess;
 }
-
-// CTAs of the persistent sweep kernel: as many as can be resident at once
-// (at most kMinBlocks32 per SM, never more than the regions of a sweep)
 cudaError_t sweep32_grid(const Geo& g, int ctas_per_sm, int* grid) {
     int dev = 0, n_sm = 1, per_sm = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)))
         return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-             &per_sm,
-             g.stage_cap > 0 ? (g.mean_mode ? (const void*)sweep32_kernel<true, true> : (const void*)sweep32_kernel<true, false>)
-                             : (g.mean_mode ? (const void*)sweep32_kernel<false, true> : (const void*)sweep32_kernel<false, false>),
-             kThreads32, phase32_smem_bytes(g))))
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep32_func(g), kThreads32, phase32_smem_bytes(g))))
         return e;
     per_sm = std::max(1, std::min(per_sm, kMinBlocks32));
     if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
@@ -1674,22 +1877,27 @@ cudaError_t sweep32_grid(const Geo& g, int ctas_per_sm, int* grid) {
 }
 
 cudaError_t launch_sweep32(const Geo& g, const Dev& d, int grid, cudaStream_t s) {
-    if (g.stage_cap > 0)
-        g.mean_mode ? sweep32_kernel<true, true><<<grid, kThreads32, phase32_smem_bytes(g), s>>>(g, d)
-                    : sweep32_kernel<true, false><<<grid, kThreads32, phase32_smem_bytes(g), s>>>(g, d);
+    const size_t smem = phase32_smem_bytes(g);
+    if (g.p_pair > 0.0)
+        sweep32_kernel<false, false, true><<<grid, kThreads32, smem, s>>>(g, d);
+    else if (g.stage_cap > 0)
+        g.mean_mode ? sweep32_kernel<true, true, false><<<grid, kThreads32, smem, s>>>(g, d)
+                    : sweep32_kernel<true, false, false><<<grid, kThreads32, smem, s>>>(g, d);
     else
-        g.mean_mode ? sweep32_kernel<false, true><<<grid, kThreads32, phase32_smem_bytes(g), s>>>(g, d)
-                    : sweep32_kernel<false, false><<<grid, kThreads32, phase32_smem_bytes(g), s>>>(g, d);
+        g.mean_mode ? sweep32_kernel<false, true, false><<<grid, kThreads32, smem, s>>>(g, d)
+                    : sweep32_kernel<false, false, false><<<grid, kThreads32, smem, s>>>(g, d);
     return cudaGetLastError();
 }
-
 cudaError_t launch_phase32(const Geo& g, const Dev& d, int colour, cudaStream_t s) {
-    if (g.stage_cap > 0)
-        g.mean_mode ? phase32_kernel<true, true><<<g.max_rpc, kThreads32, phase32_smem_bytes(g), s>>>(g, d, colour)
-                    : phase32_kernel<true, false><<<g.max_rpc, kThreads32, phase32_smem_bytes(g), s>>>(g, d, colour);
+    const size_t smem = phase32_smem_bytes(g);
+    if (g.p_pair > 0.0)
+        phase32_kernel<false, false, true><<<g.max_rpc, kThreads32, smem, s>>>(g, d, colour);
+    else if (g.stage_cap > 0)
+        g.mean_mode ? phase32_kernel<true, true, false><<<g.max_rpc, kThreads32, smem, s>>>(g, d, colour)
+                    : phase32_kernel<true, false, false><<<g.max_rpc, kThreads32, smem, s>>>(g, d, colour);
     else
-        g.mean_mode ? phase32_kernel<false, true><<<g.max_rpc, kThreads32, phase32_smem_bytes(g), s>>>(g, d, colour)
-                    : phase32_kernel<false, false><<<g.max_rpc, kThreads32, phase32_smem_bytes(g), s>>>(g, d, colour);
+        g.mean_mode ? phase32_kernel<false, true, false><<<g.max_rpc, kThreads32, smem, s>>>(g, d, colour)
+                    : phase32_kernel<false, false, false><<<g.max_rpc, kThreads32, smem, s>>>(g, d, colour);
     return cudaGetLastError();
 }
 

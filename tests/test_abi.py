@@ -56,7 +56,8 @@ def _params(cm, **kw):
     dict(likelihood=1, dtype=0),   # the additive-mean reading is float32 only
     dict(p_pair=-0.1),
     dict(p_pair=0.6),              # p_birth + p_death + p_pair > 1
-    dict(p_pair=0.2, dtype=1),     # the joint move is float64 only
+    dict(p_pair=0.2, dtype=1, stage_samples=-1),   # joint moves read windows from global memory
+    dict(p_pair=0.2, dtype=1, likelihood=1),        # joint moves under the variance reading
     dict(sig_a=-1.0),
     dict(sig_a=2.0, dtype=1),      # latent arrival times are float64 only
     dict(p_arr=0.1),               # the arrival-time move needs latent arrivals

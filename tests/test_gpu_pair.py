@@ -1,5 +1,6 @@
 """The joint move of a pair of events (§MH moves, "Joint Events Move") in the
-float64 replay form against the CPU oracle, through the C ABI.
+float64 replay form and in the float32 form against the CPU oracle, through
+the C ABI.
 
 With p_pair > 0 every step's type (3 for the joint move), validity, picks and
 accept decision equal the oracle's, the log-likelihood changes and ratios
@@ -114,3 +115,69 @@ def test_swapped_pair_reaches_its_true_mode(cm, orc):
         hits[shift_mode] = n
     # the oracle's chains of the same seeds: 7 of 8 dynamic, 0 of 8 static
     assert hits[1] >= 6 and hits[0] <= 1, hits
+
+
+# ---- the float32 form -------------------------------------------------------
+
+def _f32_world(seed):
+    return small_world(seed=seed, W=1000.0, T=3600.0, Lambda=500.0, n_side=10, dtype=np.float32)
+
+
+def test_fp32_pairs_dry_run_match_oracle(cm, orc):
+    """Commit off, from the ground truth, joint moves at 0.2: every step's
+    type, validity and event count equal the oracle's, and every float32
+    change of the log-likelihood is within 1e-4 (to max(|x|, 1)) of the
+    oracle's for the same pair of candidates; the pair counters of the
+    statistics equal the trace's."""
+    w = _f32_world(61)
+    m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=4, k=32, seed=13, events=w.events, commit=False,
+                                          p_pair=PAIR)
+    o, oev, oids, otr, odlp = run_oracle(orc, w, sweeps=4, k=32, seed=13, events=w.events, commit=False,
+                                         p_pair=PAIR, threads=min(16, os.cpu_count() or 1))
+    assert len(tr) == len(otr)
+    for key in ("sweep", "cell", "step", "type", "n_before", "evaluated"):
+        assert np.array_equal(tr[key], otr[key]), key
+    ev_ = otr["evaluated"] == 1
+    err = np.abs(tr["dll"][ev_] - otr["dll"][ev_]) / np.maximum(np.abs(otr["dll"][ev_]), 1.0)
+    pairs = (otr["type"] == 3) & ev_
+    assert pairs.sum() > 300
+    assert err.max() <= 1e-4, err.max()
+    assert np.count_nonzero(tr["accepted"][ev_] != otr["accepted"][ev_]) <= max(2, err.size // 10000)
+    assert stats["pair"] == _pair_counts(tr)
+    m.destroy()
+
+
+@pytest.mark.parametrize("init", ["empty", "truth"])
+def test_fp32_pairs_chain_tracks_oracle_log_density(cm, orc, init):
+    """With commits and joint moves: the running log-density equals the
+    oracle's log-density of the final events and the GPU's recomputation, so
+    the variance re-synthesised after a pair's commit matches its events."""
+    w = _f32_world(62)
+    ev0 = w.events if init == "truth" else None
+    m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=20, k=32, seed=14, events=ev0, p_pair=PAIR)
+    assert stats["pair"][2] > 20
+    want = orc.World(w).log_density(ev)
+    print("running %.4f oracle %.4f gpu recomputed %.4f" % (logp, want, m.log_density()))
+    assert logp == pytest.approx(want, rel=1e-6)
+    assert logp == pytest.approx(m.log_density(), rel=1e-6)
+    assert len(np.unique(ids)) == len(ids)
+    m.destroy()
+
+
+def test_fp32_swapped_pair_reaches_its_true_mode(cm):
+    """The swapped-pair world with float32 signals: joint moves under dynamic
+    colouring reach the true mode in most chains, across a fixed boundary in
+    (almost) none, as in the float64 form and the oracle."""
+    w64, truth, start = _swapped_pair_world()
+    w = worldgen.make_world(w64.params, w64.stations, seed=9, events=truth, dtype=np.float32)
+    steps = dict(sig_xy=3.0, sig_t=1.0, sig_m=0.05)
+    hits = {}
+    for shift_mode in (1, 0):
+        n = 0
+        for seed in range(100, 108):
+            m, ev, _, _, _, _ = run_gpu(cm, w, sweeps=40, k=16, seed=seed, events=start, shift_mode=shift_mode,
+                                        trace=False, p_pair=PAIR, **steps)
+            n += _reached(ev, truth)
+            m.destroy()
+        hits[shift_mode] = n
+    assert hits[1] >= 5 and hits[0] <= 1, hits

@@ -112,10 +112,12 @@ FLOPS_PER_SAMPLE = 24.0
 def _workload(name: str, likelihood: str = "variance", p_pair: float = 0.0, sig_a: float = 0.0,
               p_arr: float = 0.0):
     if name == "scale":
-        return worldgen.config_scale(seed=SEED, likelihood=likelihood), \
+        return worldgen.config_scale(seed=SEED, likelihood=likelihood, sig_a=sig_a), \
             "fp32 sweep at scale: 4000x4000 km, 24 h, ~1e4 events, 1600 stations x 864000 f32 samples, " \
             "40x40 regions, k=32" + ("" if likelihood == "variance" else ", additive-mean likelihood reading") + \
-            (", joint pair moves p_pair=%g" % p_pair if p_pair else "")
+            (", joint pair moves p_pair=%g" % p_pair if p_pair else "") + (
+                ", latent arrival times sig_a=%g s (offsets of the generated world), arrival-time moves "
+                "p_arr=%g" % (sig_a, p_arr) if sig_a else "")
     if name == "replay":
         return worldgen.config_replay(seed=SEED, sig_a=sig_a), \
             "fp64 replay: 1000x1000 km, 1 h, ~500 events, 100 stations x 36000 f64 samples, 10x10 regions, " \
@@ -844,8 +846,8 @@ def main():
     ap.add_argument("--p-pair", type=float, default=0.0,
                     help="replay or scale workload: share of steps that propose the joint move of a pair of events")
     ap.add_argument("--sig-a", type=float, default=0.0,
-                    help="replay workload: latent arrival times with offsets ~ N(0, sig_a^2) seconds")
-    ap.add_argument("--p-arr", type=float, default=0.0, help="replay workload: share of arrival-time moves")
+                    help="replay or scale workload: latent arrival times with offsets ~ N(0, sig_a^2) seconds")
+    ap.add_argument("--p-arr", type=float, default=0.0, help="replay or scale workload: share of arrival-time moves")
     ap.add_argument("--sig-da", type=float, default=1.0, help="step of the arrival-time move, seconds")
     ap.add_argument("--profile-case", default=None, choices=["scale", "corner", "replay", "train"],
                     help="run a named workload for a profiler (--warmup, then --steps sweeps) and print a summary")
@@ -853,8 +855,10 @@ def main():
     if args.profile_case:
         run_profile_case(args)
         return
-    if (args.sig_a or args.p_arr) and args.workload != "replay":
-        raise SystemExit("--sig-a and --p-arr need the float64 replay workload")
+    if (args.sig_a or args.p_arr) and args.workload not in ("replay", "scale"):
+        raise SystemExit("--sig-a and --p-arr need the replay or the scale workload")
+    if (args.sig_a or args.p_arr) and args.likelihood != "variance":
+        raise SystemExit("--sig-a and --p-arr need the variance reading")
     if args.p_pair and args.workload not in ("replay", "scale"):
         raise SystemExit("--p-pair needs the replay or the scale workload")
     if args.warmup < 3:

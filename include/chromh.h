@@ -23,7 +23,8 @@
  * Options (cmh_params): the additive reading (likelihood = 1: arrivals add
  * the enveloped amplitude to the sample's mean, float32), latent arrival
  * times (sig_a > 0: a = t + d / v + delta, delta ~ N(0, sig_a^2) per event and
- * reached station, float64) and the joint move of a pair (p_pair, float64).
+ * reached station) and the joint move of a pair (p_pair), both in either
+ * precision under the variance reading.
  *
  * Conventions for every call:
  *   - return 0 (CMH_OK) or a negative CMH_ERR_* code; nothing throws across
@@ -104,7 +105,7 @@ typedef struct {
                               perpendicular bisector), else both shift by one common Gaussian
                               offset of the move's scales.  0 (the default) turns it off;
                               p_birth + p_death + p_pair <= 1 */
-    /* CMH_F64 only: latent arrival times (§Generative Model, Event Detections: the
+    /* Latent arrival times (§Generative Model, Event Detections: the
      * arrival is Gaussian around t + d/v).  sig_a > 0 gives every (event, station it
      * reaches) a latent offset delta ~ N(0, sig_a^2), the arrival being t + d/v +
      * delta; births draw the offsets from that prior, a moved event keeps the offsets
@@ -113,7 +114,11 @@ typedef struct {
      * by a Gaussian of scale sig_da); it follows p_pair in the mix
      * (p_birth + p_death + p_pair + p_arr <= 1).  sig_a = 0 (the default): arrivals
      * are deterministic and p_arr must be 0.  Offsets start at 0 unless set by
-     * cmh_set_arrival_offsets. */
+     * cmh_set_arrival_offsets.  The offsets are float64 in both precisions; in
+     * CMH_F32 they enter a window's float32 start as delta f samples (the
+     * exact float64 start decides within the margin) and need the variance
+     * reading without staging (likelihood 0, stage_samples 0; else
+     * CMH_ERR_ARG), and a batch refuses them. */
     double sig_a, p_arr, sig_da;
 } cmh_params;
 

@@ -175,7 +175,7 @@ def make_params(model_params, *, k_per_phase=32, seed=1, dtype=F64, p_birth=0.25
     """cmh_params from an object with the model fields (e.g. worldgen.ModelParams).
     ``p_pair`` > 0 turns on the joint move of a pair of events; ``sig_a`` > 0
     makes arrival times latent and ``p_arr`` the share of the arrival-time
-    move of step ``sig_da`` (latent arrivals: float64 only)."""
+    move of step ``sig_da`` (float32: the variance reading without staging)."""
     p = Params()
     for n in ("W", "T", "Lambda", "v", "alpha", "beta_att", "tau", "t_s", "noise_var", "f_hz", "R_max"):
         setattr(p, n, float(getattr(model_params, n)))

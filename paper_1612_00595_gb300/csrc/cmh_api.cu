@@ -226,23 +226,22 @@ int validate_params(const cmh_params* p) {
         if (!finite_pos(v)) return CMH_ERR_ARG;
     if (!std::isfinite(p->alpha) || !std::isfinite(p->beta_att)) return CMH_ERR_ARG;
     if (!(p->p_birth > 0.0 && p->p_death > 0.0 && p->p_birth + p->p_death < 1.0)) return CMH_ERR_ARG;
-    // joint moves of a pair: the float64 form only
     if (!(p->p_pair >= 0.0 && p->p_birth + p->p_death + p->p_pair <= 1.0)) return CMH_ERR_ARG;
-    // latent arrival times and the arrival-time move: the float64 form only
+    // latent arrival times and the arrival-time move
     if (!(std::isfinite(p->sig_a) && p->sig_a >= 0.0 && std::isfinite(p->p_arr) && p->p_arr >= 0.0))
         return CMH_ERR_ARG;
     if (!(p->p_birth + p->p_death + p->p_pair + p->p_arr <= 1.0)) return CMH_ERR_ARG;
     if (p->p_arr > 0.0 && !(p->sig_a > 0.0 && finite_pos(p->sig_da))) return CMH_ERR_ARG;
-    if (p->sig_a > 0.0 && p->dtype != CMH_F64) return CMH_ERR_ARG;
     if (p->k_per_phase < 1 || p->k_per_phase > kMaxK) return CMH_ERR_ARG;
     if (p->dtype != CMH_F32 && p->dtype != CMH_F64) return CMH_ERR_ARG;
     if (p->likelihood != 0 && !(p->likelihood == 1 && p->dtype == CMH_F32)) return CMH_ERR_ARG;
     if (p->ev_capacity < 0 || p->frozen_capacity < 0 || p->max_events < 0) return CMH_ERR_ARG;
     if (p->stage_samples < -1 || (p->schedule != 0 && p->schedule != 1) || p->ctas_per_sm < 0 || p->ctas_per_sm > 3)
         return CMH_ERR_ARG;
-    // the float32 kernel of joint moves reads the windows from global memory
-    // under the variance reading
-    if (p->p_pair > 0.0 && p->dtype == CMH_F32 && (p->stage_samples != 0 || p->likelihood != 0)) return CMH_ERR_ARG;
+    // the float32 kernel of joint moves (and the one of latent arrival
+    // offsets) reads the windows from global memory under the variance reading
+    if ((p->p_pair > 0.0 || p->sig_a > 0.0) && p->dtype == CMH_F32 && (p->stage_samples != 0 || p->likelihood != 0))
+        return CMH_ERR_ARG;
     if (p->block_threads != 0 && (p->block_threads < 64 || p->block_threads > 512 || p->block_threads % 32))
         return CMH_ERR_ARG;
     const double nw = std::llround(p->t_s * p->f_hz);
@@ -1336,7 +1335,7 @@ extern "C" int cmh_autotune(cmh_model* m, int32_t trial_sweeps, cmh_tuning* out)
         m->p.schedule = c.schedule;
         m->p.stage_samples = c.stage;
         m->p.ctas_per_sm = c.ctas;
-        if (keep.p_pair > 0.0 && c.stage != 0) continue;   // no staging with joint moves
+        if ((keep.p_pair > 0.0 || keep.sig_a > 0.0) && c.stage != 0) continue;   // no staging with these moves
         if (cmh_restore(m, ck.data(), len) != CMH_OK) continue;   // does not fit: skip it
         if (cmh_run_sweeps(m, 1) != CMH_OK) continue;             // warm-up (and graph capture)
         cudaEventRecord(a, m->stream);
@@ -1431,7 +1430,8 @@ extern "C" int cmh_batch_create(cmh_model* const* models, int32_t n_models, void
         for (int j = 0; j < i; ++j)
             if (models[j] == m) return CMH_ERR_ARG;   // each model once
         if (!m->partitioned || m->latched) return CMH_ERR_STATE;
-        if (!m->g.f32 || m->g.stage_cap != 0 || m->g.ev_cap > 512 || m->g.p_pair > 0.0) return CMH_ERR_ARG;
+        if (!m->g.f32 || m->g.stage_cap != 0 || m->g.ev_cap > 512 || m->g.p_pair > 0.0 || m->g.sig_a > 0.0)
+            return CMH_ERR_ARG;
     }
     cmh_batch* b = new cmh_batch;
     auto fail = [&](int rc) {

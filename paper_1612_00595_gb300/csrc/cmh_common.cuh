@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "chromh.h"
@@ -233,6 +234,12 @@ static __device__ __noinline__ int k0_exact(double x, double y, double t, double
     const double a = __dadd_rn(t, __ddiv_rn(dist_rn(x, y, xs, ys), v));
     return (int)ceil(__dmul_rn(a, f));
 }
+// the same with a latent arrival offset dl (s): ceil(((t + d / v) + dl) f)
+static __device__ __noinline__ int k0_exact_lat(double x, double y, double t, double xs, double ys, double v,
+                                                double f, double dl) {
+    const double a = __dadd_rn(__dadd_rn(t, __ddiv_rn(dist_rn(x, y, xs, ys), v)), dl);
+    return (int)ceil(__dmul_rn(a, f));
+}
 
 // per-event float32 terms: K = floor(t f), ph = t f - K, mf = m
 __device__ __forceinline__ void event_terms32(const Geo& g, double t, double m, int& K, float& ph, float& mf) {
@@ -243,23 +250,66 @@ __device__ __forceinline__ void event_terms32(const Geo& g, double t, double m, 
     mf = (float)m;
 }
 
-// reach, first sample k0 and E0 = log2 of the variance added at k0
-__device__ __forceinline__ bool arrival32c(const Geo& g, double x, double y, double t, int K, float ph, float mf,
-                                           double xs, double ys, int& k0, float& E0) {
+// float32 distance of an event from a station
+__device__ __forceinline__ float dist32(double x, double y, double xs, double ys) {
     const float dx = (float)__dsub_rn(x, xs), dy = (float)__dsub_rn(y, ys);
-    const float d = __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
-    bool reach;
-    if (d < g.R_f - kMarginR) reach = true;
-    else if (d > g.R_f + kMarginR) reach = false;
-    else reach = reach_exact(x, y, xs, ys, g.R_max);
-    if (!reach) return false;
-    const float q = __fadd_rn(ph, __fmul_rn(d, g.fv_f));   // arrival x f - K
-    if (fabsf(__fsub_rn(q, rintf(q))) < kMarginK) k0 = k0_exact(x, y, t, xs, ys, g.v, g.f_hz);
-    else k0 = K + (int)ceilf(q);
+    return __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
+}
+
+// reach of a station: d < R_max, d the float32 distance returned in dist
+__device__ __forceinline__ bool reach32(const Geo& g, double x, double y, double xs, double ys, float& dist) {
+    const float d = dist32(x, y, xs, ys);
+    dist = d;
+    if (d < g.R_f - kMarginR) return true;
+    if (d > g.R_f + kMarginR) return false;
+    return reach_exact(x, y, xs, ys, g.R_max);
+}
+
+// first sample k0 and E0 = log2 of the variance added at k0 of an arrival at
+// float32 distance d; dl is the latent arrival offset (s), 0 without latent
+// arrivals (a constant 0 compiles the offset away).  The offset enters in
+// float32 as dl f samples; within the margin the exact float64 start decides.
+__device__ __forceinline__ void window32(const Geo& g, double x, double y, double t, int K, float ph, float mf,
+                                         double xs, double ys, float d, double dl, int& k0, float& E0) {
+    float q = __fadd_rn(ph, __fmul_rn(d, g.fv_f));   // arrival x f - K
+    if (dl != 0.0) q = __fadd_rn(q, (float)__dmul_rn(dl, g.f_hz));
+    if (fabsf(__fsub_rn(q, rintf(q))) < kMarginK)
+        k0 = dl != 0.0 ? k0_exact_lat(x, y, t, xs, ys, g.v, g.f_hz, dl) : k0_exact(x, y, t, xs, ys, g.v, g.f_hz);
+    else
+        k0 = K + (int)ceilf(q);
     const float lnA2 = __fmul_rn(g.apow_f, __fsub_rn(__fmul_rn(g.alpha_f, mf), __fmul_rn(g.beta_f, d)));
     const float frac = __fsub_rn((float)(k0 - K), q);      // k0 - arrival x f, in [0, 1)
     E0 = __fmul_rn(1.4426950408889634f, __fsub_rn(lnA2, __fmul_rn(frac, g.twoftau_f)));
+}
+
+// reach, first sample k0 and E0 = log2 of the variance added at k0
+__device__ __forceinline__ bool arrival32c(const Geo& g, double x, double y, double t, int K, float ph, float mf,
+                                           double xs, double ys, int& k0, float& E0, double dl = 0.0) {
+    float d;
+    if (!reach32(g, x, y, xs, ys, d)) return false;
+    window32(g, x, y, t, K, ph, mf, xs, ys, d, dl, k0, E0);
     return true;
+}
+
+// latent offset drawn from its prior N(0, sig_a^2) for station j and the
+// step's e-th changed event: Philox stream 0 at counter (sweep, cell, step,
+// 16 + 2 j + e), a Box-Muller cosine from words 0 and 1 rounded to 2^-20
+// (as the walk offsets), the sign from bit 0 of word 2
+static __device__ __noinline__ double draw_offset(const Geo& g, long long sweep, int cell, int step, int j, int e) {
+    unsigned long long c[4] = {(unsigned long long)sweep, (unsigned long long)cell, (unsigned long long)step,
+                               16ULL + 2ULL * (unsigned long long)j + (unsigned long long)e};
+    philox4x64(c, g.seed, 0ULL);
+    const double r = __dsqrt_rn(__dmul_rn(-2.0, log(u01o(c[0]))));
+    const double th = __dmul_rn(6.283185307179586, u01(c[1]));
+    double z = __dmul_rn(rint(__dmul_rn(fabs(__dmul_rn(r, cos(th))), 1048576.0)), 1.0 / 1048576.0);
+    if (c[2] & 1ULL) z = -z;
+    return __dmul_rn(g.sig_a, z);
+}
+
+// log N(v; 0, sig_a^2)
+__device__ __forceinline__ double log_off_prior1(const Geo& g, double v) {
+    const double s2 = __dmul_rn(g.sig_a, g.sig_a);
+    return __dsub_rn(__dmul_rn(-0.5, log(__dmul_rn(2.0 * M_PI, s2))), __ddiv_rn(__dmul_rn(v, v), __dmul_rn(2.0, s2)));
 }
 
 // 2^x by the SFU (relative error ~2^-22); inline PTX so that every kernel

@@ -68,6 +68,7 @@ struct SA {             // an entry of a station's arrival list
 
 struct D32 {            // state-independent part of one MH step
     double bx, by, bt, bm, blb;   // birth: float64 candidate and its log beta; move: float64 offsets
+                                  // (arrival-time move: bx, the step of the offset)
     double blq;                   // birth: log Lambda - log(W^2 T) - log q_b(candidate) (magnitude factor out)
     float xr, yr, ph, mf;         // birth: relative form; move: offsets dx, dy, dt (s), dm
     float logu;
@@ -129,6 +130,14 @@ struct Sm {
     int scap;           // floats per staging buffer (0: no staging)
     int2* uiv;          // [blk_cap][kIv] disjoint windows priced at each blanket station this phase
     int* un;            // [blk_cap] intervals held in uiv
+    // latent arrival offsets (sig_a > 0), else null: the offset of each entry
+    // of an own event's arrival cache, of each candidate arrival, and the
+    // store index of each loaded neighbouring event
+    double* aoff;       // [ev_cap][arr_cap]
+    double* coff;       // [2][arr_cap]
+    double* coff2;      // [2][arr_cap] the second candidate of a joint move
+    int* nsrc;          // [ev_cap]
+    long long sweep;
     unsigned long long bar[2];   // mbarrier of each staging buffer
     int ph[2], on[2];   // parity of its pending completion; copies in flight
     double rect[4], X0, Y0, sx, sy, region_dlp;
@@ -148,12 +157,14 @@ struct Sm {
     P32 c[2];           // candidate of each step buffer
     P32 c2[2];          // joint move of a pair: the second candidate
     int idx2[2], ncand2[2];
+    int ai[2];          // arrival-time move: the entry of the event's arrival cache it steps
     int warp_cnt[32];
     float2 redf[32];
     // statistics of this CTA: proposed[3], evaluated[3], accepted[3], priced
     // samples, re-synthesised samples, unique window samples, joint moves
-    // proposed, evaluated, accepted (thread 0)
-    unsigned long long cnt[15];
+    // proposed, evaluated, accepted, arrival-time moves proposed, evaluated,
+    // accepted (thread 0)
+    unsigned long long cnt[18];
 };
 
 // carve the dynamic shared buffer; returns its size (base may be null).  With
@@ -192,7 +203,8 @@ __host__ __device__ inline size_t layout32(const Geo& g, Sm* S, unsigned char* b
     A32* cand = (A32*)take(sizeof(A32) * 2 * (size_t)g.arr_cap);
     A32* cand2 = (A32*)take(sizeof(A32) * 2 * (size_t)g.arr_cap);
     T32* tasks = (T32*)take(sizeof(T32) * 2 * (size_t)g.task_cap);
-    T32X* tasksx = g.p_pair > 0.0 ? (T32X*)take(sizeof(T32X) * 2 * (size_t)g.task_cap) : nullptr;
+    const bool lat = g.sig_a > 0.0;
+    T32X* tasksx = (g.p_pair > 0.0 || lat) ? (T32X*)take(sizeof(T32X) * 2 * (size_t)g.task_cap) : nullptr;
     double *nx = (double*)take(8 * E), *ny = (double*)take(8 * E), *nt = (double*)take(8 * E);
     float *nph = (float*)take(4 * E), *nmf = (float*)take(4 * E);
     int* nK = (int*)take(4 * E);
@@ -202,7 +214,15 @@ __host__ __device__ inline size_t layout32(const Geo& g, Sm* S, unsigned char* b
     const size_t scap = (size_t)g.stage_cap;
     float* stage_s = scap ? (float*)take(4 * 2 * scap) : nullptr;
     float* stage_v = scap ? (float*)take(4 * 2 * scap) : nullptr;
+    double* aoff = lat ? (double*)gtake(8 * E * g.arr_cap) : nullptr;
+    double* coff = lat ? (double*)take(8 * 2 * (size_t)g.arr_cap) : nullptr;
+    double* coff2 = lat ? (double*)take(8 * 2 * (size_t)g.arr_cap) : nullptr;
+    int* nsrc = lat ? (int*)take(4 * E) : nullptr;
     if (S) {
+        S->aoff = aoff;
+        S->coff = coff;
+        S->coff2 = coff2;
+        S->nsrc = nsrc;
         S->uiv = uiv;
         S->un = un;
         S->tsoff = tsoff;
@@ -427,7 +447,7 @@ __device__ __forceinline__ int cand_of(const Geo& g, const Sm& S, double x, doub
 // old and new arrivals into tasks (one per station whose variance changes)
 // in step buffer sl; with STAGE, start the bulk copies of the task windows
 // ---------------------------------------------------------------------------
-template <bool STAGE, bool PAIR>
+template <bool STAGE, bool PAIR, bool LAT>
 __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int step, int sl) {
     const int lane = threadIdx.x & 31;
     if (STAGE) {
@@ -445,7 +465,7 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
     A32* cd = S.cand + sl * g.arr_cap;
     T32* tk = S.tasks + sl * g.task_cap;
     A32* cd2 = S.cand2 + sl * g.arr_cap;
-    int valid = 0, idx = -1, ps = -1, idx2 = -1, ps2 = -1;
+    int valid = 0, idx = -1, ps = -1, idx2 = -1, ps2 = -1, ai = -1;
     P32 c, c2;
     c.x = c.y = c.t = c.m = 0.0;
     c.xr = c.yr = c.ph = c.mf = 0.f;
@@ -480,6 +500,21 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
                                 S.eyr[ps2] + dr.yr, c2);
             }
         }
+    } else if (LAT && dr.type == 4) {
+        // arrival-time move: one entry of an event's arrival cache (in slot
+        // order: the stations it reaches in index order), its offset stepped
+        if (n_own > 0) {
+            idx = pick32(dr.pickw, n_own);
+            ps = S.order[idx];
+            if (S.enarr[ps] > 0) {
+                ai = pick32(dr.pick2, S.enarr[ps]);
+                c.x = S.mx[ps]; c.y = S.my[ps]; c.t = S.mt[ps]; c.m = S.mm[ps];
+                event_terms32(g, c.t, c.m, c.K, c.ph, c.mf);
+                c.xr = S.exr[ps];
+                c.yr = S.eyr[ps];
+                valid = 1;
+            }
+        }
     } else if (n_own > 0) {
         idx = pick32(dr.pickw, n_own);
         ps = S.order[idx];
@@ -493,35 +528,66 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
                             S.eyr[ps] + dr.yr, c);
         }
     }
+    // latent offset of candidate `which` at blanket slot b (a station it
+    // reaches): kept from the event old_ps it replaces where that one reached
+    // b (its arrival cache, slot-sorted, is searched), else drawn from the prior
+    auto cand_offset = [&](int which, int old_ps, int b) -> double {
+        if (old_ps >= 0) {
+            const A32* L = S.earr + old_ps * g.arr_cap;
+            int lo = 0, hi = S.enarr[old_ps];
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (L[mid].slot < b) lo = mid + 1; else hi = mid;
+            }
+            if (lo < S.enarr[old_ps] && L[lo].slot == b) return S.aoff[old_ps * g.arr_cap + lo];
+        }
+        return draw_offset(g, S.sweep, S.cell, step, S.bsta[b], which);
+    };
     // candidate arrivals, lanes over blanket slots, compacted in slot order
-    auto arrivals = [&](const P32& e, A32* out) {
+    // (with latent arrivals, each one's offset in oo)
+    auto arrivals = [&](const P32& e, int which, int old_ps, A32* out, double* oo) {
         int n = 0;
         for (int b0 = 0; b0 < n_blk; b0 += 32) {
             const int b = b0 + lane;
             int k0 = 0;
-            float E0 = 0.f;
-            const bool r = b < n_blk && arrival32c(g, e.x, e.y, e.t, e.K, e.ph, e.mf, S.bx[b], S.by[b], k0, E0);
+            float E0 = 0.f, dd = 0.f;
+            double dl = 0.0;
+            const bool r = b < n_blk && reach32(g, e.x, e.y, S.bx[b], S.by[b], dd);
+            if (r) {
+                if (LAT) dl = cand_offset(which, old_ps, b);
+                window32(g, e.x, e.y, e.t, e.K, e.ph, e.mf, S.bx[b], S.by[b], dd, dl, k0, E0);
+            }
             const unsigned bal = __ballot_sync(FULL, r);
             const int pos = n + __popc(bal & ((1u << lane) - 1));
-            if (r && pos < g.arr_cap) out[pos] = A32{b, k0, E0, 0};
+            if (r && pos < g.arr_cap) {
+                out[pos] = A32{b, k0, E0, 0};
+                if (LAT) oo[pos] = dl;
+            }
             n += __popc(bal);
         }
         return n;
     };
     int ncand = 0, ncand2 = 0;
-    if (valid && dr.type != 1) {
-        for (int b0 = 0; b0 < n_blk; b0 += 32) {
-            const int b = b0 + lane;
-            int k0 = 0;
-            float E0 = 0.f;
-            const bool r = b < n_blk && arrival32c(g, c.x, c.y, c.t, c.K, c.ph, c.mf, S.bx[b], S.by[b], k0, E0);
-            const unsigned bal = __ballot_sync(FULL, r);
-            const int pos = ncand + __popc(bal & ((1u << lane) - 1));
-            if (r && pos < g.arr_cap) cd[pos] = A32{b, k0, E0, 0};
-            ncand += __popc(bal);
+    double* co = LAT ? S.coff + sl * g.arr_cap : nullptr;
+    if (LAT && valid && dr.type == 4) {
+        // the event's arrivals, the stepped one's window recomputed
+        const int na = S.enarr[ps];
+        for (int a = lane; a < na; a += 32) {
+            A32 A = S.earr[ps * g.arr_cap + a];
+            double dl = S.aoff[ps * g.arr_cap + a];
+            if (a == ai) {
+                dl = __dadd_rn(dl, dr.bx);
+                const double xs = S.bx[A.slot], ys = S.by[A.slot];
+                window32(g, c.x, c.y, c.t, c.K, c.ph, c.mf, xs, ys, dist32(c.x, c.y, xs, ys), dl, A.k0, A.E0);
+            }
+            cd[a] = A;
+            co[a] = dl;
         }
+        ncand = na;
+    } else if (valid && dr.type != 1) {
+        ncand = arrivals(c, 0, dr.type == 0 ? -1 : ps, cd, co);
     }
-    if (PAIR && valid && dr.type == 3) ncand2 = arrivals(c2, cd2);
+    if (PAIR && valid && dr.type == 3) ncand2 = arrivals(c2, 1, ps2, cd2, LAT ? S.coff2 + sl * g.arr_cap : nullptr);
     __syncwarp();
     if (lane == 0) {
         int err = (ncand > g.arr_cap || ncand2 > g.arr_cap) ? CMH_ERR_CAPACITY : 0;
@@ -628,6 +694,8 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
                     lo = min(lo, A.k0);
                     hi = max(hi, A.k0 + g.n_w);
                 }
+                // an arrival-time move changes one station's variance only
+                if (LAT && dr.type == 4 && io - 1 != ai) continue;
                 lo = max(lo, 0);
                 hi = (long long)hi > g.n_samp ? (int)g.n_samp : hi;
                 T.lo = lo;
@@ -688,6 +756,12 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
             } else if (dr.type == 1) {
                 thr = (double)dr.logu - (S.tabD[n_own] - S.elq[ps]);
                 dlp = S.mm[ps] - g.lb0;
+            } else if (LAT && dr.type == 4) {
+                // symmetric step of one offset: its prior ratio
+                const double a = S.aoff[ps * g.arr_cap + ai], b = co[ai];
+                const double s2 = __dmul_rn(g.sig_a, g.sig_a);
+                dlp = __ddiv_rn(__dsub_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(2.0, s2));
+                thr = (double)dr.logu - dlp;
             } else if (PAIR && dr.type == 3) {
                 // symmetric proposal: the two events' prior ratio, the change
                 // of their magnitudes (0 for an exchange)
@@ -711,6 +785,7 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
         S.type[sl] = dr.type;
         S.ncand[sl] = ncand;
         S.c[sl] = c;
+        if (LAT) S.ai[sl] = ai;
         if (PAIR) {
             S.idx2[sl] = idx2;
             S.ncand2[sl] = ncand2;
@@ -900,14 +975,17 @@ __device__ __forceinline__ void iv_add(Sm& S, int slot, int lo, int hi) {
 // record it, and on a commit update the region's event bookkeeping; rm / put
 // receive the event whose arrivals leave / join the station lists (-1: none).
 // t is the float-float sum of the step's partial log-likelihood changes.
-template <bool PAIR>
+template <bool PAIR, bool LAT>
 __device__ __forceinline__ int decide_lane0(const Geo& g, const Dev& d, Sm& S, long long sweep, int cell, int step,
                                          int sl, float2 t, int valid, int& rm, int& put, int& rm2, int& put2) {
     const int type = S.type[sl], n_own = S.n_own, idx = S.idx[sl];
     const D32& dr = S.draws[step];
-    // counters: birth, death, move in [0..8]; the joint move of a pair in [12..14]
-    const int c_prop = (!PAIR || type < 3) ? type : 12, c_eval = (!PAIR || type < 3) ? 3 + type : 13,
-              c_acc = (!PAIR || type < 3) ? 6 + type : 14;
+    // counters: birth, death, move in [0..8]; the joint move of a pair in
+    // [12..14]; the arrival-time move in [15..17]
+    const int ext = (LAT && type == 4) ? 15 : 12;
+    const int c_prop = (!(PAIR || LAT) || type < 3) ? type : ext,
+              c_eval = (!(PAIR || LAT) || type < 3) ? 3 + type : ext + 1,
+              c_acc = (!(PAIR || LAT) || type < 3) ? 6 + type : ext + 2;
     ++S.cnt[c_prop];
     double dll = 0.0, la = -INFINITY, dlp = 0.0;
     int acc = 0;
@@ -946,7 +1024,25 @@ __device__ __forceinline__ int decide_lane0(const Geo& g, const Dev& d, Sm& S, l
     if (acc) ++S.cnt[c_acc];
     if (do_commit) {
         S.cnt[10] += (unsigned long long)S.width[sl];
-        S.region_dlp += dll + dlp;
+        // latent offsets drawn from (or dropped to) their prior cancel from
+        // log alpha but change the log-density: the candidates' offsets in,
+        // the replaced events' out (an arrival-time move's are in dlp)
+        double dlo = 0.0;
+        if (LAT && type != 4) {
+            auto rowsum = [&](const double* row, int n) {
+                double t = 0.0;
+                for (int a = 0; a < n; ++a) t += log_off_prior1(g, row[a]);
+                return t;
+            };
+            const int p1 = idx >= 0 ? S.order[idx] : -1;
+            if (type != 1) dlo += rowsum(S.coff + sl * g.arr_cap, S.ncand[sl]);
+            if (type != 0) dlo -= rowsum(S.aoff + p1 * g.arr_cap, S.enarr[p1]);
+            if (type == 3) {
+                const int p2 = S.order[S.idx2[sl]];
+                dlo += rowsum(S.coff2 + sl * g.arr_cap, S.ncand2[sl]) - rowsum(S.aoff + p2 * g.arr_cap, S.enarr[p2]);
+            }
+        }
+        S.region_dlp += dll + dlp + dlo;
         if (type == 1) {
             const int ps = S.order[idx];
             rm = ps;
@@ -1010,17 +1106,20 @@ __device__ __forceinline__ void lists_add(const Geo& g, Sm& S, int ps, const A32
     }
 }
 
-// a committed candidate c (arrivals cd[0..ncd)) of a step of type `type`
-// becomes own event ps (one thread): its master, density term, relative
-// position and arrival cache, and its arrivals join the station lists
+// a committed candidate c (arrivals cd[0..ncd), their latent offsets co or
+// null) of a step of type `type` becomes own event ps (one thread): its
+// master, density term, relative position and arrival cache, and its
+// arrivals join the station lists
 __device__ __forceinline__ void put_event(const Geo& g, const Dev& d, Sm& S, const P32& c, const A32* cd, int ncd,
-                                          int type, int ps) {
+                                          int type, int ps, const double* co) {
     S.mx[ps] = c.x; S.my[ps] = c.y; S.mt[ps] = c.t; S.mm[ps] = c.m;
     // a move's own log alpha has no position term: the moved event's term
-    // (for a later death) is taken here
-    S.elq[ps] = type == 0 ? c.lq : (g.bt_on ? bt_lq(g, d, S, c.x, c.y, c.t, c.m) : S.lq_unif);
+    // (for a later death) is taken here (an arrival-time move keeps it)
+    if (type != 4) S.elq[ps] = type == 0 ? c.lq : (g.bt_on ? bt_lq(g, d, S, c.x, c.y, c.t, c.m) : S.lq_unif);
     S.exr[ps] = c.xr; S.eyr[ps] = c.yr;
     for (int a = 0; a < ncd; ++a) S.earr[ps * g.arr_cap + a] = cd[a];
+    if (co)
+        for (int a = 0; a < ncd; ++a) S.aoff[ps * g.arr_cap + a] = co[a];
     S.enarr[ps] = ncd;
     lists_add(g, S, ps, cd, ncd);
 }
@@ -1078,7 +1177,7 @@ __device__ __forceinline__ void init_staging(Sm& S) {
 // blanket stations, the own events' arrival caches and the k steps' random
 // draws; a kernel whose regions wait for their lower-colour neighbours runs
 // it before that wait.  Returns false (uniformly) after latching an error.
-template <bool STAGE>
+template <bool STAGE, bool LAT>
 __device__ __forceinline__ bool region_begin(const Geo& g, const Dev& d, int cell, long long sweep, Sm& S,
                                              unsigned char* smem) {
     const Store St = d.st[sweep & 1];
@@ -1091,6 +1190,7 @@ __device__ __forceinline__ bool region_begin(const Geo& g, const Dev& d, int cel
     if (tid == 0) {
         layout32(g, &S, smem, g.spill ? d.spill_buf + (size_t)blockIdx.x * (size_t)g.spill_bytes : nullptr);
         S.cell = cell;
+        S.sweep = sweep;
         S.sx = d.shift[0];
         S.sy = d.shift[1];
         cell_rect(g, S.sx, S.sy, cell, S.rect);
@@ -1106,7 +1206,7 @@ __device__ __forceinline__ bool region_begin(const Geo& g, const Dev& d, int cel
         S.region_dlp = 0.0;
         S.acc = 0;
     }
-    if (tid < 15) S.cnt[tid] = 0;
+    if (tid < 18) S.cnt[tid] = 0;
     // only thread 0 has S.err initialised yet: the others would read what an
     // earlier CTA left in this shared memory
     if (__syncthreads_or(tid == 0 && S.err != 0)) {
@@ -1232,11 +1332,19 @@ __device__ __forceinline__ bool region_begin(const Geo& g, const Dev& d, int cel
         for (int b0 = 0; b0 < n_blk; b0 += 32) {
             const int b = b0 + lane;
             int k0 = 0;
-            float E0 = 0.f;
-            const bool r = b < n_blk && arrival32c(g, S.mx[i], S.my[i], S.mt[i], K, ph, mf, S.bx[b], S.by[b], k0, E0);
+            float E0 = 0.f, dd = 0.f;
+            double dl = 0.0;   // latent offset of (event, station) from the store's row
+            const bool r = b < n_blk && reach32(g, S.mx[i], S.my[i], S.bx[b], S.by[b], dd);
+            if (r) {
+                if (LAT) dl = St.off[(size_t)(start + i) * g.n_st + S.bsta[b]];
+                window32(g, S.mx[i], S.my[i], S.mt[i], K, ph, mf, S.bx[b], S.by[b], dd, dl, k0, E0);
+            }
             const unsigned bal = __ballot_sync(FULL, r);
             const int p = na + __popc(bal & ((1u << lane) - 1));
-            if (r && p < g.arr_cap) S.earr[i * g.arr_cap + p] = A32{b, k0, E0, 0};
+            if (r && p < g.arr_cap) {
+                S.earr[i * g.arr_cap + p] = A32{b, k0, E0, 0};
+                if (LAT) S.aoff[i * g.arr_cap + p] = dl;
+            }
             na += __popc(bal);
         }
         if (lane == 0) {
@@ -1247,8 +1355,9 @@ __device__ __forceinline__ bool region_begin(const Geo& g, const Dev& d, int cel
     // ---- the k steps' random draws (Philox stream 0, counter (sweep, cell, step, 0|1))
     const unsigned long long thr_b = (unsigned long long)ceil(g.p_birth * 9007199254740992.0);
     const unsigned long long thr_d = (unsigned long long)ceil(__dadd_rn(g.p_birth, g.p_death) * 9007199254740992.0);
-    const unsigned long long thr_p =
-        (unsigned long long)ceil(__dadd_rn(__dadd_rn(g.p_birth, g.p_death), g.p_pair) * 9007199254740992.0);
+    const double cp = __dadd_rn(__dadd_rn(g.p_birth, g.p_death), g.p_pair);
+    const unsigned long long thr_p = (unsigned long long)ceil(cp * 9007199254740992.0);
+    const unsigned long long thr_a = LAT ? (unsigned long long)ceil(__dadd_rn(cp, g.p_arr) * 9007199254740992.0) : 0ULL;
     // one warp, warp 1, draws them: the float64 of the walk offsets (~250
     // float64 instructions, each holding its sub-partition's float64 pipe for
     // ~64 cycles whatever the number of active lanes) then runs on a
@@ -1261,7 +1370,7 @@ __device__ __forceinline__ bool region_begin(const Geo& g, const Dev& d, int cel
         philox4x64(c1, g.seed, 0ULL);
         D32 D;
         const unsigned long long u53 = c0[0] >> 11;   // u < p  <=>  u53 < p 2^53 (rounded up)
-        D.type = u53 < thr_b ? 0 : (u53 < thr_d ? 1 : (u53 < thr_p ? 3 : 2));
+        D.type = u53 < thr_b ? 0 : (u53 < thr_d ? 1 : (u53 < thr_p ? 3 : ((LAT && u53 < thr_a) ? 4 : 2)));
         // joint move of a pair: the second pick from word 7, the exchange
         // when bit 36 of word 1 is clear
         D.pick2 = (unsigned)(c1[3] & 0xffffffffULL);
@@ -1292,7 +1401,7 @@ __device__ __forceinline__ bool region_begin(const Geo& g, const Dev& d, int cel
             const bool sure = e.xr >= S.rl[0] + kDr && e.xr < S.rl[1] - kDr && e.yr >= S.rl[2] + kDr &&
                               e.yr < S.rl[3] - kDr && e.K >= 1 && e.K + 2 <= g.TfK;
             D.bvalid = sure || inside_exact(g, S.sx, S.sy, cell, e.x, e.y, e.t, e.m);
-        } else if (D.type == 2 || D.type == 3) {
+        } else if (D.type == 2 || D.type == 3 || D.type == 4) {
             // the walk offset in float64 (a joint move's common offset too),
             // the same definition as the float64
             // form (Box-Muller, each Gaussian rounded to 2^-20, signs from
@@ -1307,7 +1416,8 @@ __device__ __forceinline__ bool region_begin(const Geo& g, const Dev& d, int cel
             const double th2 = __dmul_rn(6.283185307179586, u01(c1[1]));
             const double z[4] = {__dmul_rn(r1, cos(th1)), __dmul_rn(r1, sin(th1)), __dmul_rn(r2, cos(th2)),
                                  __dmul_rn(r2, sin(th2))};
-            const double sg[4] = {g.sig_xy, g.sig_xy, g.sig_t, g.sig_m};
+            // (the arrival-time move steps its offset by sig_da times the first)
+            const double sg[4] = {D.type == 4 ? g.sig_da : g.sig_xy, g.sig_xy, g.sig_t, g.sig_m};
             double o[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -1335,7 +1445,7 @@ __device__ __forceinline__ bool region_begin(const Geo& g, const Dev& d, int cel
 // steps and the write-back of the region's events.  MEAN: the additive
 // likelihood reading (a kernel per reading, so each pricing loop is compiled
 // for its own)
-template <bool STAGE, bool MEAN, bool PAIR>
+template <bool STAGE, bool MEAN, bool PAIR, bool LAT>
 __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell, long long sweep, Sm& S) {
     const Store St = d.st[sweep & 1];
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
@@ -1381,6 +1491,7 @@ __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell
                 S.nx[i] = St.x[src];
                 S.ny[i] = St.y[src];
                 S.nt[i] = t;
+                if (LAT) S.nsrc[i] = src;
                 event_terms32(g, t, St.m[src], S.nK[i], S.nph[i], S.nmf[i]);
             }
             __syncthreads();
@@ -1389,9 +1500,13 @@ __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell
                 for (int i0 = 0; i0 < nn; i0 += 32) {
                     const int i = i0 + lane;
                     int k0 = 0;
-                    float E0 = 0.f;
-                    const bool r = i < nn && arrival32c(g, S.nx[i], S.ny[i], S.nt[i], S.nK[i], S.nph[i], S.nmf[i],
-                                                        S.bx[b], S.by[b], k0, E0);
+                    float E0 = 0.f, dd = 0.f;
+                    const bool r = i < nn && reach32(g, S.nx[i], S.ny[i], S.bx[b], S.by[b], dd);
+                    if (r) {
+                        const double dl = LAT ? St.off[(size_t)S.nsrc[i] * g.n_st + S.bsta[b]] : 0.0;
+                        window32(g, S.nx[i], S.ny[i], S.nt[i], S.nK[i], S.nph[i], S.nmf[i], S.bx[b], S.by[b], dd, dl,
+                                 k0, E0);
+                    }
                     const unsigned bal = __ballot_sync(FULL, r);
                     const int p = nf + __popc(bal & ((1u << lane) - 1));
                     if (r && p < g.frz_cap) S.sarr[b * g.frz_cap + p] = SA{k0, E0, kFrozen, 0};
@@ -1433,14 +1548,14 @@ __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell
         }
         __syncwarp();
     }
-    if (wid == 0) prepare_step<STAGE, PAIR>(g, d, S, 0, 0);
+    if (wid == 0) prepare_step<STAGE, PAIR, LAT>(g, d, S, 0, 0);
     __syncthreads();
     for (int step = 0; step < g.k; ++step) {
         const int sl = step & 1;
         const int valid = S.valid[sl];
         // ================ prepare step+1 (warp 0) || price step (warps 1..) =========
         if (wid == 0) {
-            if (step + 1 < g.k) prepare_step<STAGE, PAIR>(g, d, S, step + 1, sl ^ 1);   // assumes a rejection
+            if (step + 1 < g.k) prepare_step<STAGE, PAIR, LAT>(g, d, S, step + 1, sl ^ 1);   // assumes a rejection
         } else if (valid) {
             // (this buffer is refilled by bulk copies only after two more
             // barriers: these generic reads come first)
@@ -1467,7 +1582,7 @@ __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell
                     S.ph[sl] ^= 1;
                     S.on[sl] = 0;
                 }
-                S.acc = decide_lane0<PAIR>(g, d, S, sweep, cell, step, sl, t, valid, rm, put, rm2, put2);
+                S.acc = decide_lane0<PAIR, LAT>(g, d, S, sweep, cell, step, sl, t, valid, rm, put, rm2, put2);
             }
             // the removed or moved event's arrivals leave their station lists
             // (all lanes), then the new arrivals join (lane 0)
@@ -1478,9 +1593,12 @@ __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell
                 rm2 = __shfl_sync(FULL, rm2, 0);
                 if (rm2 >= 0) lists_remove_warp(g, S, rm2);
             }
-            if (lane == 0 && put >= 0) put_event(g, d, S, S.c[sl], S.cand + sl * g.arr_cap, S.ncand[sl], S.type[sl], put);
+            if (lane == 0 && put >= 0)
+                put_event(g, d, S, S.c[sl], S.cand + sl * g.arr_cap, S.ncand[sl], S.type[sl], put,
+                          LAT ? S.coff + sl * g.arr_cap : nullptr);
             if (PAIR && lane == 0 && put2 >= 0)
-                put_event(g, d, S, S.c2[sl], S.cand2 + sl * g.arr_cap, S.ncand2[sl], S.type[sl], put2);
+                put_event(g, d, S, S.c2[sl], S.cand2 + sl * g.arr_cap, S.ncand2[sl], S.type[sl], put2,
+                          LAT ? S.coff2 + sl * g.arr_cap : nullptr);
         }
         if (__syncthreads_or(S.err != 0)) break;
         // ================ commit: re-synthesise V on the touched windows ============
@@ -1491,14 +1609,14 @@ __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell
         if (S.acc) {
             const int rt = STAGE ? tid : tid - 32, rn = STAGE ? nthr : nthr - 32;
             if (!STAGE && wid == 0) {
-                if (step + 1 < g.k) prepare_step<STAGE, PAIR>(g, d, S, step + 1, sl ^ 1);
+                if (step + 1 < g.k) prepare_step<STAGE, PAIR, LAT>(g, d, S, step + 1, sl ^ 1);
             } else {
                 resynth(g, d, S, sl, rt, rn);
             }
             if (STAGE) {
                 fence_async_global();   // the new V is visible to the next bulk copies
                 __syncthreads();
-                if (wid == 0 && step + 1 < g.k) prepare_step<STAGE, PAIR>(g, d, S, step + 1, sl ^ 1);
+                if (wid == 0 && step + 1 < g.k) prepare_step<STAGE, PAIR, LAT>(g, d, S, step + 1, sl ^ 1);
             }
             if (__syncthreads_or(S.err != 0)) break;
         }
@@ -1523,13 +1641,26 @@ __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell
         St.m[start + i] = S.mm[ps];
         St.id[start + i] = S.eid[ps];
     }
+    if (LAT) {
+        // offset rows of the written events: 0 but at the stations they reach
+        for (size_t q = tid; q < (size_t)n_fin * g.n_st; q += nthr) St.off[(size_t)start * g.n_st + q] = 0.0;
+        __syncthreads();
+        for (int i = wid; i < n_fin; i += nw) {
+            const int ps = S.order[i];
+            for (int a = lane; a < S.enarr[ps]; a += 32)
+                St.off[(size_t)(start + i) * g.n_st + S.bsta[S.earr[ps * g.arr_cap + a].slot]] =
+                    S.aoff[ps * g.arr_cap + a];
+        }
+    }
     if (tid == 0) {
         St.count[cell] = n_fin;
         d.region_dlp[cell] = S.region_dlp;
         for (int t = 0; t < 11; ++t)
             if (S.cnt[t]) atomicAdd(&d.stats[t], S.cnt[t]);
-        for (int t = 0; t < 3; ++t)   // joint moves of a pair: proposed, evaluated, accepted
+        for (int t = 0; t < 3; ++t) {   // joint moves of a pair, arrival-time moves: proposed, evaluated, accepted
             if (S.cnt[12 + t]) atomicAdd(&d.stats[11 + t], S.cnt[12 + t]);
+            if (S.cnt[15 + t]) atomicAdd(&d.stats[14 + t], S.cnt[15 + t]);
+        }
         if (g.count_unique) {
             unsigned long long u = S.cnt[11];
             for (int b = 0; b < S.n_blk; ++b)
@@ -1541,14 +1672,14 @@ __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell
 
 
 // both parts, for kernels without dependency waits
-template <bool STAGE, bool MEAN, bool PAIR>
+template <bool STAGE, bool MEAN, bool PAIR, bool LAT>
 __device__ __forceinline__ void region_phase(const Geo& g, const Dev& d, int cell, long long sweep, Sm& S,
                                              unsigned char* smem) {
-    if (region_begin<STAGE>(g, d, cell, sweep, S, smem)) region_rest<STAGE, MEAN, PAIR>(g, d, cell, sweep, S);
+    if (region_begin<STAGE, LAT>(g, d, cell, sweep, S, smem)) region_rest<STAGE, MEAN, PAIR, LAT>(g, d, cell, sweep, S);
 }
 
 // one colour phase: a CTA per region of the colour
-template <bool STAGE, bool MEAN, bool PAIR>
+template <bool STAGE, bool MEAN, bool PAIR, bool LAT>
 __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const __grid_constant__ Geo g,
                                                                            const __grid_constant__ Dev d, int colour) {
     if (*d.status) return;
@@ -1557,7 +1688,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) phase32_kernel(const
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Sm S;
     init_staging<STAGE>(S);
-    region_phase<STAGE, MEAN, PAIR>(g, d, d.colour_cells[colour * g.max_rpc + blockIdx.x], sweep, S, smem);
+    region_phase<STAGE, MEAN, PAIR, LAT>(g, d, d.colour_cells[colour * g.max_rpc + blockIdx.x], sweep, S, smem);
 }
 
 __device__ __forceinline__ long long ld_acquire(const long long* p) {
@@ -1581,7 +1712,7 @@ __device__ __forceinline__ void st_release(long long* p, long long v) {
 // results do not depend on the order in which CTAs take regions.  Every
 // region a CTA waits for was taken earlier by a CTA that is running, so the
 // waits end; they are bounded all the same (CMH_ERR_TIMEOUT).
-template <bool STAGE, bool MEAN, bool PAIR>
+template <bool STAGE, bool MEAN, bool PAIR, bool LAT>
 __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_kernel(const __grid_constant__ Geo g,
                                                                            const __grid_constant__ Dev d) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1610,7 +1741,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_kernel(const
         const int colour_taken = s_run;
         // the part of the region's phase that needs no neighbour runs while
         // the lower-colour neighbours may still be running theirs
-        const bool begun = region_begin<STAGE>(g, d, cell, sweep, S, smem);
+        const bool begun = region_begin<STAGE, LAT>(g, d, cell, sweep, S, smem);
         if (threadIdx.x == 0) {
             const int colour = colour_taken;
             const int P1 = g.period - 1, ix = cell % g.ncx, iy = cell / g.ncx;
@@ -1633,7 +1764,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_kernel(const
             s_run = begun && *(volatile int*)d.status == 0;
         }
         __syncthreads();
-        if (s_run) region_rest<STAGE, MEAN, PAIR>(g, d, cell, sweep, S);
+        if (s_run) region_rest<STAGE, MEAN, PAIR, LAT>(g, d, cell, sweep, S);
         __syncthreads();
         if (threadIdx.x == 0 && cell != g.hold_cell) {
             __threadfence();
@@ -1725,7 +1856,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_batch(const 
         const Geo& g = G[inst];
         const Dev& d = D[inst];
         const long long sweep = s_sweep, stamp = sweep + 1;
-        const bool begun = region_begin<false>(g, d, cell, sweep, S, smem);
+        const bool begun = region_begin<false, false>(g, d, cell, sweep, S, smem);
         if (threadIdx.x == 0) {
             const int colour = s_col;
             const int P1 = g.period - 1, ix = cell % g.ncx, iy = cell / g.ncx;
@@ -1747,7 +1878,7 @@ __global__ void __launch_bounds__(kThreads32, kMinBlocks32) sweep32_batch(const 
             s_run = begun && *(volatile int*)d.status == 0;
         }
         __syncthreads();
-        if (s_run) region_rest<false, MEAN, false>(g, d, cell, sweep, S);
+        if (s_run) region_rest<false, MEAN, false, false>(g, d, cell, sweep, S);
         __syncthreads();
         if (threadIdx.x == 0 && cell != g.hold_cell) {
             __threadfence();
@@ -1799,7 +1930,7 @@ cudaError_t launch_sweep32_batch(bool mean, const Geo* G, const Dev* D, int n_in
 // from global memory.
 cudaError_t choose_stage_cap(Geo& g, int requested) {
     g.stage_cap = 0;
-    if (requested == 0 || g.p_pair > 0.0) return cudaSuccess;
+    if (requested == 0 || g.p_pair > 0.0 || g.sig_a > 0.0) return cudaSuccess;
     if (requested > 0) {
         g.stage_cap = requested & ~3;
         return cudaSuccess;
@@ -1812,7 +1943,7 @@ cudaError_t choose_stage_cap(Geo& g, int requested) {
         (e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) ||
         (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) ||
         (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) ||
-        (e = cudaFuncGetAttributes(&fa, phase32_kernel<true, false, false>)))
+        (e = cudaFuncGetAttributes(&fa, phase32_kernel<true, false, false, false>)))
         return e;
     const int resident = std::min(kMinBlocks32, std::max(1, (g.max_rpc + n_sm - 1) / std::max(1, n_sm)));
     const long long dyn = (long long)layout32(g, nullptr, nullptr);
@@ -1825,40 +1956,41 @@ cudaError_t choose_stage_cap(Geo& g, int requested) {
     return cudaSuccess;
 }
 
-// the kernels of a model: one per staging x likelihood reading, and the
+// the kernels of a model: one per staging x likelihood reading, the
 // instantiation with joint moves of a pair (no staging, variance reading),
-// so that kernels without them carry none of their code
+// and the one with latent arrival offsets and the arrival-time move (joint
+// moves too), so that kernels without them carry none of their code
 const void* sweep32_func(const Geo& g) {
-    if (g.p_pair > 0.0) return (const void*)sweep32_kernel<false, false, true>;
+    if (g.sig_a > 0.0) return (const void*)sweep32_kernel<false, false, true, true>;
+    if (g.p_pair > 0.0) return (const void*)sweep32_kernel<false, false, true, false>;
     if (g.stage_cap > 0)
-        return g.mean_mode ? (const void*)sweep32_kernel<true, true, false> : (const void*)sweep32_kernel<true, false, false>;
-    return g.mean_mode ? (const void*)sweep32_kernel<false, true, false> : (const void*)sweep32_kernel<false, false, false>;
+        return g.mean_mode ? (const void*)sweep32_kernel<true, true, false, false> : (const void*)sweep32_kernel<true, false, false, false>;
+    return g.mean_mode ? (const void*)sweep32_kernel<false, true, false, false> : (const void*)sweep32_kernel<false, false, false, false>;
 }
 
 const void* phase32_func(const Geo& g) {
-    if (g.p_pair > 0.0) return (const void*)phase32_kernel<false, false, true>;
+    if (g.sig_a > 0.0) return (const void*)phase32_kernel<false, false, true, true>;
+    if (g.p_pair > 0.0) return (const void*)phase32_kernel<false, false, true, false>;
     if (g.stage_cap > 0)
-        return g.mean_mode ? (const void*)phase32_kernel<true, true, false> : (const void*)phase32_kernel<true, false, false>;
-    return g.mean_mode ? (const void*)phase32_kernel<false, true, false> : (const void*)phase32_kernel<false, false, false>;
+        return g.mean_mode ? (const void*)phase32_kernel<true, true, false, false> : (const void*)phase32_kernel<true, false, false, false>;
+    return g.mean_mode ? (const void*)phase32_kernel<false, true, false, false> : (const void*)phase32_kernel<false, false, false, false>;
 }
 
 cudaError_t prepare_phase32(const Geo& g) {
     const int bytes = (int)phase32_smem_bytes(g);
     cudaError_t e;
     const bool mn = g.mean_mode;
-    if (g.p_pair > 0.0) {
-        if ((e = raise_smem_limit((const void*)phase32_kernel<false, false, true>, bytes)) ||
-            (e = raise_smem_limit((const void*)sweep32_kernel<false, false, true>, bytes)))
-            return e;
+    if (g.sig_a > 0.0 || g.p_pair > 0.0) {
+        if ((e = raise_smem_limit(phase32_func(g), bytes)) || (e = raise_smem_limit(sweep32_func(g), bytes))) return e;
         return cudaSuccess;
     }
-    if ((e = raise_smem_limit(mn ? (const void*)phase32_kernel<false, true, false> : (const void*)phase32_kernel<false, false, false>,
+    if ((e = raise_smem_limit(mn ? (const void*)phase32_kernel<false, true, false, false> : (const void*)phase32_kernel<false, false, false, false>,
                               bytes)) ||
-        (e = raise_smem_limit(mn ? (const void*)phase32_kernel<true, true, false> : (const void*)phase32_kernel<true, false, false>,
+        (e = raise_smem_limit(mn ? (const void*)phase32_kernel<true, true, false, false> : (const void*)phase32_kernel<true, false, false, false>,
                               bytes)) ||
-        (e = raise_smem_limit(mn ? (const void*)sweep32_kernel<false, true, false> : (const void*)sweep32_kernel<false, false, false>,
+        (e = raise_smem_limit(mn ? (const void*)sweep32_kernel<false, true, false, false> : (const void*)sweep32_kernel<false, false, false, false>,
                               bytes)) ||
-        (e = raise_smem_limit(mn ? (const void*)sweep32_kernel<true, true, false> : (const void*)sweep32_kernel<true, false, false>,
+        (e = raise_smem_limit(mn ? (const void*)sweep32_kernel<true, true, false, false> : (const void*)sweep32_kernel<true, false, false, false>,
                               bytes)))
         return e;
     return cudaSuccess;
@@ -1878,26 +2010,30 @@ cudaError_t sweep32_grid(const Geo& g, int ctas_per_sm, int* grid) {
 
 cudaError_t launch_sweep32(const Geo& g, const Dev& d, int grid, cudaStream_t s) {
     const size_t smem = phase32_smem_bytes(g);
-    if (g.p_pair > 0.0)
-        sweep32_kernel<false, false, true><<<grid, kThreads32, smem, s>>>(g, d);
+    if (g.sig_a > 0.0)
+        sweep32_kernel<false, false, true, true><<<grid, kThreads32, smem, s>>>(g, d);
+    else if (g.p_pair > 0.0)
+        sweep32_kernel<false, false, true, false><<<grid, kThreads32, smem, s>>>(g, d);
     else if (g.stage_cap > 0)
-        g.mean_mode ? sweep32_kernel<true, true, false><<<grid, kThreads32, smem, s>>>(g, d)
-                    : sweep32_kernel<true, false, false><<<grid, kThreads32, smem, s>>>(g, d);
+        g.mean_mode ? sweep32_kernel<true, true, false, false><<<grid, kThreads32, smem, s>>>(g, d)
+                    : sweep32_kernel<true, false, false, false><<<grid, kThreads32, smem, s>>>(g, d);
     else
-        g.mean_mode ? sweep32_kernel<false, true, false><<<grid, kThreads32, smem, s>>>(g, d)
-                    : sweep32_kernel<false, false, false><<<grid, kThreads32, smem, s>>>(g, d);
+        g.mean_mode ? sweep32_kernel<false, true, false, false><<<grid, kThreads32, smem, s>>>(g, d)
+                    : sweep32_kernel<false, false, false, false><<<grid, kThreads32, smem, s>>>(g, d);
     return cudaGetLastError();
 }
 cudaError_t launch_phase32(const Geo& g, const Dev& d, int colour, cudaStream_t s) {
     const size_t smem = phase32_smem_bytes(g);
-    if (g.p_pair > 0.0)
-        phase32_kernel<false, false, true><<<g.max_rpc, kThreads32, smem, s>>>(g, d, colour);
+    if (g.sig_a > 0.0)
+        phase32_kernel<false, false, true, true><<<g.max_rpc, kThreads32, smem, s>>>(g, d, colour);
+    else if (g.p_pair > 0.0)
+        phase32_kernel<false, false, true, false><<<g.max_rpc, kThreads32, smem, s>>>(g, d, colour);
     else if (g.stage_cap > 0)
-        g.mean_mode ? phase32_kernel<true, true, false><<<g.max_rpc, kThreads32, smem, s>>>(g, d, colour)
-                    : phase32_kernel<true, false, false><<<g.max_rpc, kThreads32, smem, s>>>(g, d, colour);
+        g.mean_mode ? phase32_kernel<true, true, false, false><<<g.max_rpc, kThreads32, smem, s>>>(g, d, colour)
+                    : phase32_kernel<true, false, false, false><<<g.max_rpc, kThreads32, smem, s>>>(g, d, colour);
     else
-        g.mean_mode ? phase32_kernel<false, true, false><<<g.max_rpc, kThreads32, smem, s>>>(g, d, colour)
-                    : phase32_kernel<false, false, false><<<g.max_rpc, kThreads32, smem, s>>>(g, d, colour);
+        g.mean_mode ? phase32_kernel<false, true, false, false><<<g.max_rpc, kThreads32, smem, s>>>(g, d, colour)
+                    : phase32_kernel<false, false, false, false><<<g.max_rpc, kThreads32, smem, s>>>(g, d, colour);
     return cudaGetLastError();
 }
 

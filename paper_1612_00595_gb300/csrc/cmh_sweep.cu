@@ -115,27 +115,6 @@ __device__ __forceinline__ bool arrival(const Geo& g, double x, double y, double
     return true;
 }
 
-// latent offset drawn from its prior N(0, sig_a^2) for station j and the
-// step's e-th changed event: Philox stream 0 at counter (sweep, cell, step,
-// 16 + 2 j + e), a Box-Muller cosine from words 0 and 1 rounded to 2^-20
-// (as the walk offsets), the sign from bit 0 of word 2
-__device__ __noinline__ double draw_offset(const Geo& g, long long sweep, int cell, int step, int j, int e) {
-    unsigned long long c[4] = {(unsigned long long)sweep, (unsigned long long)cell, (unsigned long long)step,
-                               16ULL + 2ULL * (unsigned long long)j + (unsigned long long)e};
-    philox4x64(c, g.seed, 0ULL);
-    const double r = __dsqrt_rn(__dmul_rn(-2.0, log(u01o(c[0]))));
-    const double th = __dmul_rn(6.283185307179586, u01(c[1]));
-    double z = __dmul_rn(rint(__dmul_rn(fabs(__dmul_rn(r, cos(th))), 1048576.0)), 1.0 / 1048576.0);
-    if (c[2] & 1ULL) z = -z;
-    return __dmul_rn(g.sig_a, z);
-}
-
-// log N(v; 0, sig_a^2)
-__device__ __forceinline__ double log_off_prior1(const Geo& g, double v) {
-    const double s2 = __dmul_rn(g.sig_a, g.sig_a);
-    return __dsub_rn(__dmul_rn(-0.5, log(__dmul_rn(2.0 * M_PI, s2))), __ddiv_rn(__dmul_rn(v, v), __dmul_rn(2.0, s2)));
-}
-
 // variance added at sample k by an arrival (float64 form)
 __device__ __forceinline__ double arr_c64(const Geo& g, double af, double lnA2, int k) {
     return exp(lnA2 - ((double)k - af) * (2.0 / (g.f_hz * g.tau)));
@@ -1034,7 +1013,9 @@ __global__ void __launch_bounds__(kSynthThreads) vsynth_kernel(Geo g, Dev d, con
                     int K;
                     float ph, mf;
                     event_terms32(g, ft[idx], fm[idx], K, ph, mf);
-                    r = arrival32c(g, fx[idx], fy[idx], ft[idx], K, ph, mf, xs, ys, k0, E0);
+                    r = foff ? arrival32c(g, fx[idx], fy[idx], ft[idx], K, ph, mf, xs, ys, k0, E0,
+                                          foff[(size_t)idx * g.n_st + j])
+                             : arrival32c(g, fx[idx], fy[idx], ft[idx], K, ph, mf, xs, ys, k0, E0);
                 } else {
                     r = arrival(g, fx[idx], fy[idx], ft[idx], fm[idx], xs, ys, k0, af, ln,
                                 foff ? foff[(size_t)idx * g.n_st + j] : 0.0);
@@ -1256,7 +1237,7 @@ cudaError_t launch_sweep_end(const Geo& g, const Dev& d, cudaStream_t s) {
 
 cudaError_t launch_vsynth(const Geo& g, const Dev& d, const FlatList& f, cudaStream_t s, int* launches) {
     if (g.n_st == 0) return cudaSuccess;
-    if (g.f32) vsynth_kernel<true><<<g.n_st, kSynthThreads, 0, s>>>(g, d, f.x, f.y, f.t, f.m, f.n, nullptr);
+    if (g.f32) vsynth_kernel<true><<<g.n_st, kSynthThreads, 0, s>>>(g, d, f.x, f.y, f.t, f.m, f.n, f.off);
     else vsynth_kernel<false><<<g.n_st, kSynthThreads, 0, s>>>(g, d, f.x, f.y, f.t, f.m, f.n, f.off);
     if (launches) *launches += 1;
     return cudaGetLastError();

@@ -59,7 +59,8 @@ def _params(cm, **kw):
     dict(p_pair=0.2, dtype=1, stage_samples=-1),   # joint moves read windows from global memory
     dict(p_pair=0.2, dtype=1, likelihood=1),        # joint moves under the variance reading
     dict(sig_a=-1.0),
-    dict(sig_a=2.0, dtype=1),      # latent arrival times are float64 only
+    dict(sig_a=2.0, dtype=1, stage_samples=-1),   # float32 latent arrivals read windows from global memory
+    dict(sig_a=2.0, dtype=1, likelihood=1),        # latent arrivals under the variance reading
     dict(p_arr=0.1),               # the arrival-time move needs latent arrivals
     dict(sig_a=2.0, p_arr=0.1, sig_da=0.0),
     dict(sig_a=2.0, p_pair=0.3, p_arr=0.3),   # p_birth + p_death + p_pair + p_arr > 1

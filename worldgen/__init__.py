@@ -260,16 +260,17 @@ def config_learned(seed: int = 1000) -> World:
 
 
 def config_scale(seed: int = 1000, dtype=np.float32, side_regions: int = 40,
-                 T: float = 86400.0, likelihood: str = "variance") -> World:
+                 T: float = 86400.0, likelihood: str = "variance", sig_a: float = 0.0) -> World:
     """4000 x 4000 km, 24 h, Lambda = 1e4, 1600 jittered stations, 864000 f32 samples.
 
     ``side_regions`` / ``T`` shrink the same density to a smaller world
-    (Lambda scales with area x duration) for tests.
+    (Lambda scales with area x duration) for tests; ``sig_a`` > 0 gives the
+    arrivals latent Gaussian offsets of that scale (seconds).
     """
     W = 100.0 * side_regions
     lam = 1.0e4 * (side_regions / 40.0) ** 2 * (T / 86400.0)
     p = ModelParams(W=W, T=T, Lambda=lam, likelihood=likelihood)
-    return make_world(p, jittered_grid_stations(side_regions, W, seed), seed, dtype)
+    return make_world(p, jittered_grid_stations(side_regions, W, seed), seed, dtype, sig_a=sig_a)
 
 
 def batched_instances(n_instances: int = 256, seed: int = 2000):

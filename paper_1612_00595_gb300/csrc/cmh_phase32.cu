@@ -143,6 +143,7 @@ struct Sm {
     double rect[4], X0, Y0, sx, sy, region_dlp;
     float rl[4];        // region in relative coordinates: x lo, x hi, y lo, y hi
     int cell, n_own, n_free, n_blk, err, acc;
+    double lop0, lopi;  // latent offsets: log N(v; 0, sig_a^2) = lop0 - v^2 lopi
     double bt_G;        // table mass inside the region (learned birth component)
     double lq_unif;     // lq of the uniform birth alone: log(Lambda area / W^2)
     double qu;          // density of the uniform birth in space-time: 1 / (area T)
@@ -441,13 +442,69 @@ __device__ __forceinline__ int cand_of(const Geo& g, const Sm& S, double x, doub
     return v;
 }
 
+// candidate arrivals of event e (lanes of warp 0 over blanket slots),
+// compacted in slot order into out; with latent arrivals each one's offset
+// goes to oo: kept from the event old_ps it replaces where that one reached
+// the station (its arrival cache, slot-sorted, is searched), else drawn from
+// the prior with the counter of step `step` and changed event `which`
+template <bool LAT>
+__device__ __forceinline__ int cand_arrivals(const Geo& g, const Sm& S, int step, const P32& e, int which,
+                                             int old_ps, A32* out, double* oo) {
+    const int lane = threadIdx.x & 31, n_blk = S.n_blk;
+    int n = 0;
+    for (int b0 = 0; b0 < n_blk; b0 += 32) {
+        const int b = b0 + lane;
+        int k0 = 0;
+        float E0 = 0.f, dd = 0.f;
+        double dl = 0.0;
+        const bool r = b < n_blk && reach32(g, e.x, e.y, S.bx[b], S.by[b], dd);
+        if (r) {
+            if (LAT) {
+                bool kept = false;
+                if (old_ps >= 0) {
+                    const A32* L = S.earr + old_ps * g.arr_cap;
+                    int lo = 0, hi = S.enarr[old_ps];
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (L[mid].slot < b) lo = mid + 1; else hi = mid;
+                    }
+                    if (lo < S.enarr[old_ps] && L[lo].slot == b) {
+                        dl = S.aoff[old_ps * g.arr_cap + lo];
+                        kept = true;
+                    }
+                }
+                if (!kept) dl = draw_offset(g, S.sweep, S.cell, step, S.bsta[b], which);
+            }
+            window32(g, e.x, e.y, e.t, e.K, e.ph, e.mf, S.bx[b], S.by[b], dd, dl, k0, E0);
+        }
+        const unsigned bal = __ballot_sync(FULL, r);
+        const int pos = n + __popc(bal & ((1u << lane) - 1));
+        if (r && pos < g.arr_cap) {
+            out[pos] = A32{b, k0, E0, 0};
+            if (LAT) oo[pos] = dl;
+        }
+        n += __popc(bal);
+    }
+    return n;
+}
+
+__device__ __forceinline__ void clear_p32(P32& c) {
+    c.x = c.y = c.t = c.m = 0.0;
+    c.xr = c.yr = c.ph = c.mf = 0.f;
+    c.K = 0;
+    c.pad = 0;
+    c.lq = 0.0;
+}
+
 // ---------------------------------------------------------------------------
 // preparation of one step (all lanes of warp 0): decode the proposal against
 // the current state, find the stations the candidate reaches, and merge the
 // old and new arrivals into tasks (one per station whose variance changes)
-// in step buffer sl; with STAGE, start the bulk copies of the task windows
+// in step buffer sl; with STAGE, start the bulk copies of the task windows.
+// A joint move of a pair is prepared by prepare_pair (its own function, so
+// that its registers do not weigh on the steps of one event).
 // ---------------------------------------------------------------------------
-template <bool STAGE, bool PAIR, bool LAT>
+template <bool STAGE, bool LAT>
 __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int step, int sl) {
     const int lane = threadIdx.x & 31;
     if (STAGE) {
@@ -461,45 +518,17 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
         __syncwarp();
     }
     const D32& dr = S.draws[step];
-    const int n_own = S.n_own, n_blk = S.n_blk;
+    const int n_own = S.n_own;
     A32* cd = S.cand + sl * g.arr_cap;
     T32* tk = S.tasks + sl * g.task_cap;
-    A32* cd2 = S.cand2 + sl * g.arr_cap;
-    int valid = 0, idx = -1, ps = -1, idx2 = -1, ps2 = -1, ai = -1;
-    P32 c, c2;
-    c.x = c.y = c.t = c.m = 0.0;
-    c.xr = c.yr = c.ph = c.mf = 0.f;
-    c.K = 0;
-    c.pad = 0;
-    c.lq = 0.0;
-    c2 = c;
+    int valid = 0, idx = -1, ps = -1, ai = -1;
+    P32 c;
+    clear_p32(c);
     if (dr.type == 0) {
         valid = dr.bvalid;
         c.x = dr.bx; c.y = dr.by; c.t = dr.bt; c.m = dr.bm;
         c.xr = dr.xr; c.yr = dr.yr; c.ph = dr.ph; c.mf = dr.mf; c.K = dr.bK;
         c.lq = dr.blq;
-    } else if (PAIR && dr.type == 3) {
-        // joint move of a pair: the ordered pair (idx, idx2), then either the
-        // exchange of their locations (each keeps its time and magnitude) or
-        // one common offset; both candidates must lie in the region
-        if (n_own >= 2) {
-            idx = pick32(dr.pickw, n_own);
-            const int j = pick32(dr.pick2, n_own - 1);
-            idx2 = j + (j >= idx ? 1 : 0);
-            ps = S.order[idx];
-            ps2 = S.order[idx2];
-            if (dr.exch) {
-                valid = cand_of(g, S, S.mx[ps2], S.my[ps2], S.mt[ps], S.mm[ps], S.exr[ps2], S.eyr[ps2], c) &&
-                        cand_of(g, S, S.mx[ps], S.my[ps], S.mt[ps2], S.mm[ps2], S.exr[ps], S.eyr[ps], c2);
-            } else {
-                valid = cand_of(g, S, __dadd_rn(S.mx[ps], dr.bx), __dadd_rn(S.my[ps], dr.by),
-                                __dadd_rn(S.mt[ps], dr.bt), __dadd_rn(S.mm[ps], dr.bm), S.exr[ps] + dr.xr,
-                                S.eyr[ps] + dr.yr, c) &&
-                        cand_of(g, S, __dadd_rn(S.mx[ps2], dr.bx), __dadd_rn(S.my[ps2], dr.by),
-                                __dadd_rn(S.mt[ps2], dr.bt), __dadd_rn(S.mm[ps2], dr.bm), S.exr[ps2] + dr.xr,
-                                S.eyr[ps2] + dr.yr, c2);
-            }
-        }
     } else if (LAT && dr.type == 4) {
         // arrival-time move: one entry of an event's arrival cache (in slot
         // order: the stations it reaches in index order), its offset stepped
@@ -528,46 +557,7 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
                             S.eyr[ps] + dr.yr, c);
         }
     }
-    // latent offset of candidate `which` at blanket slot b (a station it
-    // reaches): kept from the event old_ps it replaces where that one reached
-    // b (its arrival cache, slot-sorted, is searched), else drawn from the prior
-    auto cand_offset = [&](int which, int old_ps, int b) -> double {
-        if (old_ps >= 0) {
-            const A32* L = S.earr + old_ps * g.arr_cap;
-            int lo = 0, hi = S.enarr[old_ps];
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (L[mid].slot < b) lo = mid + 1; else hi = mid;
-            }
-            if (lo < S.enarr[old_ps] && L[lo].slot == b) return S.aoff[old_ps * g.arr_cap + lo];
-        }
-        return draw_offset(g, S.sweep, S.cell, step, S.bsta[b], which);
-    };
-    // candidate arrivals, lanes over blanket slots, compacted in slot order
-    // (with latent arrivals, each one's offset in oo)
-    auto arrivals = [&](const P32& e, int which, int old_ps, A32* out, double* oo) {
-        int n = 0;
-        for (int b0 = 0; b0 < n_blk; b0 += 32) {
-            const int b = b0 + lane;
-            int k0 = 0;
-            float E0 = 0.f, dd = 0.f;
-            double dl = 0.0;
-            const bool r = b < n_blk && reach32(g, e.x, e.y, S.bx[b], S.by[b], dd);
-            if (r) {
-                if (LAT) dl = cand_offset(which, old_ps, b);
-                window32(g, e.x, e.y, e.t, e.K, e.ph, e.mf, S.bx[b], S.by[b], dd, dl, k0, E0);
-            }
-            const unsigned bal = __ballot_sync(FULL, r);
-            const int pos = n + __popc(bal & ((1u << lane) - 1));
-            if (r && pos < g.arr_cap) {
-                out[pos] = A32{b, k0, E0, 0};
-                if (LAT) oo[pos] = dl;
-            }
-            n += __popc(bal);
-        }
-        return n;
-    };
-    int ncand = 0, ncand2 = 0;
+    int ncand = 0;
     double* co = LAT ? S.coff + sl * g.arr_cap : nullptr;
     if (LAT && valid && dr.type == 4) {
         // the event's arrivals, the stepped one's window recomputed
@@ -585,82 +575,13 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
         }
         ncand = na;
     } else if (valid && dr.type != 1) {
-        ncand = arrivals(c, 0, dr.type == 0 ? -1 : ps, cd, co);
+        ncand = cand_arrivals<LAT>(g, S, step, c, 0, dr.type == 0 ? -1 : ps, cd, co);
     }
-    if (PAIR && valid && dr.type == 3) ncand2 = arrivals(c2, 1, ps2, cd2, LAT ? S.coff2 + sl * g.arr_cap : nullptr);
     __syncwarp();
     if (lane == 0) {
-        int err = (ncand > g.arr_cap || ncand2 > g.arr_cap) ? CMH_ERR_CAPACITY : 0;
+        int err = ncand > g.arr_cap ? CMH_ERR_CAPACITY : 0;
         int ntask = 0, units = 0, width = 0;
-        auto add_task = [&](T32& T, int lo, int hi) {
-            lo = max(lo, 0);
-            hi = (long long)hi > g.n_samp ? (int)g.n_samp : hi;
-            T.lo = lo;
-            T.hi = hi;
-            if (lo < hi) {
-                T.u0 = units;   // float4 groups [lo/4, ceil(hi/4)) continue the flat range
-                units += ((hi + 3) >> 2) - (lo >> 2);
-                width += hi - lo;
-                tk[ntask++] = T;
-            }
-        };
-        if (PAIR && valid && !err && dr.type == 3) {
-            // the two events' old arrivals and the two candidates', by slot;
-            // the second event's go to the task's extension record
-            T32X* tx = S.tasksx + sl * g.task_cap;
-            const A32* L[4] = {S.earr + ps * g.arr_cap, S.earr + ps2 * g.arr_cap, cd, cd2};
-            const int nl[4] = {S.enarr[ps], S.enarr[ps2], ncand, ncand2};
-            int il[4] = {0, 0, 0, 0};
-            for (;;) {
-                int slot = 1 << 30;
-                for (int q = 0; q < 4; ++q)
-                    if (il[q] < nl[q] && L[q][il[q]].slot < slot) slot = L[q][il[q]].slot;
-                if (slot == 1 << 30) break;
-                if (ntask >= g.task_cap) {
-                    err = CMH_ERR_CAPACITY;
-                    break;
-                }
-                T32 T;
-                T32X X;
-                T.slot = slot;
-                T.row = S.bsta[slot];
-                T.skip = ps;
-                T.has_o = T.has_n = 0;
-                T.k0o = T.k0n = 0;
-                T.E0o = T.E0n = 0.f;
-                X.pair = 1;
-                X.exch = dr.exch;
-                X.skip2 = ps2;
-                X.has_o2 = X.has_n2 = X.k0o2 = X.k0n2 = 0;
-                X.E0o2 = X.E0n2 = 0.f;
-                int ws[4], nws = 0;   // window starts at this station, in start order
-                for (int q = 0; q < 4; ++q) {
-                    if (il[q] >= nl[q] || L[q][il[q]].slot != slot) continue;
-                    const A32 A = L[q][il[q]++];
-                    if (q == 0) { T.has_o = 1; T.k0o = A.k0; T.E0o = A.E0; }
-                    if (q == 1) { X.has_o2 = 1; X.k0o2 = A.k0; X.E0o2 = A.E0; }
-                    if (q == 2) { T.has_n = 1; T.k0n = A.k0; T.E0n = A.E0; }
-                    if (q == 3) { X.has_n2 = 1; X.k0n2 = A.k0; X.E0n2 = A.E0; }
-                    int w = nws++;
-                    for (; w > 0 && ws[w - 1] > A.k0; --w) ws[w] = ws[w - 1];
-                    ws[w] = A.k0;
-                }
-                // the two events may be far apart in time: one task per
-                // disjoint stretch of the windows' union, not their hull
-                for (int a = 0; a < nws && !err;) {
-                    const int lo = ws[a];
-                    int hi = ws[a] + g.n_w;
-                    for (++a; a < nws && ws[a] <= hi; ++a) hi = max(hi, ws[a] + g.n_w);
-                    if (ntask >= g.task_cap) {
-                        err = CMH_ERR_CAPACITY;
-                        break;
-                    }
-                    const int n_before = ntask;
-                    add_task(T, lo, hi);
-                    if (ntask > n_before) tx[n_before] = X;
-                }
-            }
-        } else if (valid && !err) {
+        if (valid && !err) {
             // merge the old event's arrivals and the candidate's, by slot
             const A32* oa = (ps >= 0 && dr.type != 0) ? S.earr + ps * g.arr_cap : nullptr;
             const int no = oa ? S.enarr[ps] : 0;
@@ -700,21 +621,11 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
                 hi = (long long)hi > g.n_samp ? (int)g.n_samp : hi;
                 T.lo = lo;
                 T.hi = hi;
-                const int n_before = ntask;
                 if (lo < hi) {
                     T.u0 = units;   // float4 groups [lo/4, ceil(hi/4)) continue the flat range
                     units += ((hi + 3) >> 2) - (lo >> 2);
                     width += hi - lo;
                     tk[ntask++] = T;
-                }
-                if (PAIR && ntask > n_before) {   // a one-event task of a kernel with joint moves
-                    T32X X;
-                    X.pair = 0;
-                    X.exch = 0;
-                    X.has_o2 = X.has_n2 = X.k0o2 = X.k0n2 = 0;
-                    X.skip2 = -1;
-                    X.E0o2 = X.E0n2 = 0.f;
-                    S.tasksx[sl * g.task_cap + n_before] = X;
                 }
             }
         }
@@ -762,12 +673,6 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
                 const double s2 = __dmul_rn(g.sig_a, g.sig_a);
                 dlp = __ddiv_rn(__dsub_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(2.0, s2));
                 thr = (double)dr.logu - dlp;
-            } else if (PAIR && dr.type == 3) {
-                // symmetric proposal: the two events' prior ratio, the change
-                // of their magnitudes (0 for an exchange)
-                const double dm = __dadd_rn(__dsub_rn(c.m, S.mm[ps]), __dsub_rn(c2.m, S.mm[ps2]));
-                thr = (double)dr.logu + dm;
-                dlp = -dm;
             } else {
                 const double dm = __dsub_rn(c.m, S.mm[ps]);
                 thr = (double)dr.logu + dm;
@@ -786,13 +691,145 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
         S.ncand[sl] = ncand;
         S.c[sl] = c;
         if (LAT) S.ai[sl] = ai;
-        if (PAIR) {
-            S.idx2[sl] = idx2;
-            S.ncand2[sl] = ncand2;
-            S.c2[sl] = c2;
-        }
     }
     __syncwarp();
+}
+
+// preparation of a joint move of a pair (all lanes of warp 0; no staging):
+// the ordered pair (idx, idx2), then either the exchange of their locations
+// (each keeps its time and magnitude) or one common offset; both candidates
+// must lie in the region.  The two events' old arrivals and the two
+// candidates' are merged by slot; the second event's go to the task's
+// extension record, one task per disjoint stretch of a station's windows.
+template <bool LAT>
+__device__ __noinline__ void prepare_pair(const Geo& g, Sm& S, int step, int sl) {
+    const int lane = threadIdx.x & 31;
+    const D32& dr = S.draws[step];
+    const int n_own = S.n_own;
+    A32* cd = S.cand + sl * g.arr_cap;
+    A32* cd2 = S.cand2 + sl * g.arr_cap;
+    T32* tk = S.tasks + sl * g.task_cap;
+    int valid = 0, idx = -1, ps = -1, idx2 = -1, ps2 = -1;
+    P32 c, c2;
+    clear_p32(c);
+    clear_p32(c2);
+    if (n_own >= 2) {
+        idx = pick32(dr.pickw, n_own);
+        const int j = pick32(dr.pick2, n_own - 1);
+        idx2 = j + (j >= idx ? 1 : 0);
+        ps = S.order[idx];
+        ps2 = S.order[idx2];
+        if (dr.exch) {
+            valid = cand_of(g, S, S.mx[ps2], S.my[ps2], S.mt[ps], S.mm[ps], S.exr[ps2], S.eyr[ps2], c) &&
+                    cand_of(g, S, S.mx[ps], S.my[ps], S.mt[ps2], S.mm[ps2], S.exr[ps], S.eyr[ps], c2);
+        } else {
+            valid = cand_of(g, S, __dadd_rn(S.mx[ps], dr.bx), __dadd_rn(S.my[ps], dr.by),
+                            __dadd_rn(S.mt[ps], dr.bt), __dadd_rn(S.mm[ps], dr.bm), S.exr[ps] + dr.xr,
+                            S.eyr[ps] + dr.yr, c) &&
+                    cand_of(g, S, __dadd_rn(S.mx[ps2], dr.bx), __dadd_rn(S.my[ps2], dr.by),
+                            __dadd_rn(S.mt[ps2], dr.bt), __dadd_rn(S.mm[ps2], dr.bm), S.exr[ps2] + dr.xr,
+                            S.eyr[ps2] + dr.yr, c2);
+        }
+    }
+    int ncand = 0, ncand2 = 0;
+    if (valid) {
+        ncand = cand_arrivals<LAT>(g, S, step, c, 0, ps, cd, LAT ? S.coff + sl * g.arr_cap : nullptr);
+        ncand2 = cand_arrivals<LAT>(g, S, step, c2, 1, ps2, cd2, LAT ? S.coff2 + sl * g.arr_cap : nullptr);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        int err = (ncand > g.arr_cap || ncand2 > g.arr_cap) ? CMH_ERR_CAPACITY : 0;
+        int ntask = 0, units = 0, width = 0;
+        if (valid && !err) {
+            T32X* tx = S.tasksx + sl * g.task_cap;
+            const A32* L[4] = {S.earr + ps * g.arr_cap, S.earr + ps2 * g.arr_cap, cd, cd2};
+            const int nl[4] = {S.enarr[ps], S.enarr[ps2], ncand, ncand2};
+            int il[4] = {0, 0, 0, 0};
+            for (;;) {
+                int slot = 1 << 30;
+                for (int q = 0; q < 4; ++q)
+                    if (il[q] < nl[q] && L[q][il[q]].slot < slot) slot = L[q][il[q]].slot;
+                if (slot == 1 << 30) break;
+                T32 T;
+                T32X X;
+                T.slot = slot;
+                T.row = S.bsta[slot];
+                T.skip = ps;
+                T.has_o = T.has_n = 0;
+                T.k0o = T.k0n = 0;
+                T.E0o = T.E0n = 0.f;
+                X.pair = 1;
+                X.exch = dr.exch;
+                X.skip2 = ps2;
+                X.has_o2 = X.has_n2 = X.k0o2 = X.k0n2 = 0;
+                X.E0o2 = X.E0n2 = 0.f;
+                int ws[4], nws = 0;   // window starts at this station, in start order
+                for (int q = 0; q < 4; ++q) {
+                    if (il[q] >= nl[q] || L[q][il[q]].slot != slot) continue;
+                    const A32 A = L[q][il[q]++];
+                    if (q == 0) { T.has_o = 1; T.k0o = A.k0; T.E0o = A.E0; }
+                    if (q == 1) { X.has_o2 = 1; X.k0o2 = A.k0; X.E0o2 = A.E0; }
+                    if (q == 2) { T.has_n = 1; T.k0n = A.k0; T.E0n = A.E0; }
+                    if (q == 3) { X.has_n2 = 1; X.k0n2 = A.k0; X.E0n2 = A.E0; }
+                    int w = nws++;
+                    for (; w > 0 && ws[w - 1] > A.k0; --w) ws[w] = ws[w - 1];
+                    ws[w] = A.k0;
+                }
+                // the two events may be far apart in time: one task per
+                // disjoint stretch of the windows' union, not their hull
+                for (int a = 0; a < nws && !err;) {
+                    int lo = ws[a];
+                    int hi = ws[a] + g.n_w;
+                    for (++a; a < nws && ws[a] <= hi; ++a) hi = max(hi, ws[a] + g.n_w);
+                    if (ntask >= g.task_cap) {
+                        err = CMH_ERR_CAPACITY;
+                        break;
+                    }
+                    lo = max(lo, 0);
+                    hi = (long long)hi > g.n_samp ? (int)g.n_samp : hi;
+                    if (lo < hi) {
+                        T.lo = lo;
+                        T.hi = hi;
+                        T.u0 = units;   // float4 groups [lo/4, ceil(hi/4)) continue the flat range
+                        units += ((hi + 3) >> 2) - (lo >> 2);
+                        width += hi - lo;
+                        tx[ntask] = X;
+                        tk[ntask++] = T;
+                    }
+                }
+                if (err) break;
+            }
+        }
+        if (err) S.err = err;
+        if (valid && !err) {
+            // symmetric proposal: the two events' prior ratio, the change of
+            // their magnitudes (0 for an exchange)
+            const double dm = __dadd_rn(__dsub_rn(c.m, S.mm[ps]), __dsub_rn(c2.m, S.mm[ps2]));
+            const double thr = (double)dr.logu + dm;
+            S.thr[sl] = thr;
+            S.thrf[sl] = (float)thr;
+            S.dlp[sl] = -dm;
+        }
+        S.valid[sl] = valid && !err;
+        S.ntask[sl] = ntask;
+        S.units[sl] = units;
+        S.width[sl] = width;
+        S.idx[sl] = idx;
+        S.type[sl] = dr.type;
+        S.ncand[sl] = ncand;
+        S.c[sl] = c;
+        S.idx2[sl] = idx2;
+        S.ncand2[sl] = ncand2;
+        S.c2[sl] = c2;
+    }
+    __syncwarp();
+}
+
+// the preparation of step `step` into buffer sl, by the kind of its move
+template <bool STAGE, bool PAIR, bool LAT>
+__device__ __forceinline__ void prepare(const Geo& g, const Dev& d, Sm& S, int step, int sl) {
+    if (PAIR && S.draws[step].type == 3) prepare_pair<LAT>(g, S, step, sl);
+    else prepare_step<STAGE, LAT>(g, d, S, step, sl);
 }
 
 // the change of the log-likelihood over one float4 group of samples
@@ -895,10 +932,11 @@ __device__ __forceinline__ float group_terms(const Geo& g, const Sm& S, const T3
 // pricing of step buffer sl by warps 1..: the change of the Gaussian
 // log-likelihood over the float4 groups of all tasks (one flat range; each
 // thread issues the loads of kUnroll groups before computing them), one
-// float-float partial per warp in S.redf
+// float-float partial per warp in S.redf.  PAIR: the tasks of a joint move
+// of a pair (the second event's arrivals in their extension records)
 // ---------------------------------------------------------------------------
 template <bool STAGE, bool MEAN, bool PAIR>
-__device__ __forceinline__ void price_step(const Geo& g, const Dev& d, Sm& S, int sl) {
+__device__ __forceinline__ void price_tasks(const Geo& g, const Dev& d, Sm& S, int sl) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const T32* tk = S.tasks + sl * g.task_cap;
     const int U = S.units[sl], ntask = S.ntask[sl];
@@ -948,6 +986,14 @@ __device__ __forceinline__ void price_step(const Geo& g, const Dev& d, Sm& S, in
         v = ff_add32(v, w2);
     }
     if (lane == 0) S.redf[wid] = v;
+}
+
+// every task of a step belongs to a joint move of a pair or none does: a
+// kernel with joint moves prices the other steps with the one-event loop
+template <bool STAGE, bool MEAN, bool PAIR>
+__device__ __forceinline__ void price_step(const Geo& g, const Dev& d, Sm& S, int sl) {
+    if (PAIR && S.type[sl] == 3) price_tasks<STAGE, MEAN, true>(g, d, S, sl);
+    else price_tasks<STAGE, MEAN, false>(g, d, S, sl);
 }
 
 // add the window [lo, hi) priced at blanket slot `slot` to the slot's disjoint
@@ -1030,9 +1076,9 @@ __device__ __forceinline__ int decide_lane0(const Geo& g, const Dev& d, Sm& S, l
         double dlo = 0.0;
         if (LAT && type != 4) {
             auto rowsum = [&](const double* row, int n) {
-                double t = 0.0;
-                for (int a = 0; a < n; ++a) t += log_off_prior1(g, row[a]);
-                return t;
+                double q = 0.0;
+                for (int a = 0; a < n; ++a) q += row[a] * row[a];
+                return (double)n * S.lop0 - q * S.lopi;
             };
             const int p1 = idx >= 0 ? S.order[idx] : -1;
             if (type != 1) dlo += rowsum(S.coff + sl * g.arr_cap, S.ncand[sl]);
@@ -1191,6 +1237,11 @@ __device__ __forceinline__ bool region_begin(const Geo& g, const Dev& d, int cel
         layout32(g, &S, smem, g.spill ? d.spill_buf + (size_t)blockIdx.x * (size_t)g.spill_bytes : nullptr);
         S.cell = cell;
         S.sweep = sweep;
+        if (LAT) {   // the offsets' prior, its constant part once per region
+            const double s2 = __dmul_rn(g.sig_a, g.sig_a);
+            S.lop0 = __dmul_rn(-0.5, log(__dmul_rn(2.0 * M_PI, s2)));
+            S.lopi = __ddiv_rn(1.0, __dmul_rn(2.0, s2));
+        }
         S.sx = d.shift[0];
         S.sy = d.shift[1];
         cell_rect(g, S.sx, S.sy, cell, S.rect);
@@ -1548,14 +1599,14 @@ __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell
         }
         __syncwarp();
     }
-    if (wid == 0) prepare_step<STAGE, PAIR, LAT>(g, d, S, 0, 0);
+    if (wid == 0) prepare<STAGE, PAIR, LAT>(g, d, S, 0, 0);
     __syncthreads();
     for (int step = 0; step < g.k; ++step) {
         const int sl = step & 1;
         const int valid = S.valid[sl];
         // ================ prepare step+1 (warp 0) || price step (warps 1..) =========
         if (wid == 0) {
-            if (step + 1 < g.k) prepare_step<STAGE, PAIR, LAT>(g, d, S, step + 1, sl ^ 1);   // assumes a rejection
+            if (step + 1 < g.k) prepare<STAGE, PAIR, LAT>(g, d, S, step + 1, sl ^ 1);   // assumes a rejection
         } else if (valid) {
             // (this buffer is refilled by bulk copies only after two more
             // barriers: these generic reads come first)
@@ -1609,14 +1660,14 @@ __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell
         if (S.acc) {
             const int rt = STAGE ? tid : tid - 32, rn = STAGE ? nthr : nthr - 32;
             if (!STAGE && wid == 0) {
-                if (step + 1 < g.k) prepare_step<STAGE, PAIR, LAT>(g, d, S, step + 1, sl ^ 1);
+                if (step + 1 < g.k) prepare<STAGE, PAIR, LAT>(g, d, S, step + 1, sl ^ 1);
             } else {
                 resynth(g, d, S, sl, rt, rn);
             }
             if (STAGE) {
                 fence_async_global();   // the new V is visible to the next bulk copies
                 __syncthreads();
-                if (wid == 0 && step + 1 < g.k) prepare_step<STAGE, PAIR, LAT>(g, d, S, step + 1, sl ^ 1);
+                if (wid == 0 && step + 1 < g.k) prepare<STAGE, PAIR, LAT>(g, d, S, step + 1, sl ^ 1);
             }
             if (__syncthreads_or(S.err != 0)) break;
         }

@@ -521,7 +521,7 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
     const int n_own = S.n_own;
     A32* cd = S.cand + sl * g.arr_cap;
     T32* tk = S.tasks + sl * g.task_cap;
-    int valid = 0, idx = -1, ps = -1, ai = -1;
+    int valid = 0, idx = -1, ps = -1;
     P32 c;
     clear_p32(c);
     if (dr.type == 0) {
@@ -529,21 +529,6 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
         c.x = dr.bx; c.y = dr.by; c.t = dr.bt; c.m = dr.bm;
         c.xr = dr.xr; c.yr = dr.yr; c.ph = dr.ph; c.mf = dr.mf; c.K = dr.bK;
         c.lq = dr.blq;
-    } else if (LAT && dr.type == 4) {
-        // arrival-time move: one entry of an event's arrival cache (in slot
-        // order: the stations it reaches in index order), its offset stepped
-        if (n_own > 0) {
-            idx = pick32(dr.pickw, n_own);
-            ps = S.order[idx];
-            if (S.enarr[ps] > 0) {
-                ai = pick32(dr.pick2, S.enarr[ps]);
-                c.x = S.mx[ps]; c.y = S.my[ps]; c.t = S.mt[ps]; c.m = S.mm[ps];
-                event_terms32(g, c.t, c.m, c.K, c.ph, c.mf);
-                c.xr = S.exr[ps];
-                c.yr = S.eyr[ps];
-                valid = 1;
-            }
-        }
     } else if (n_own > 0) {
         idx = pick32(dr.pickw, n_own);
         ps = S.order[idx];
@@ -559,22 +544,7 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
     }
     int ncand = 0;
     double* co = LAT ? S.coff + sl * g.arr_cap : nullptr;
-    if (LAT && valid && dr.type == 4) {
-        // the event's arrivals, the stepped one's window recomputed
-        const int na = S.enarr[ps];
-        for (int a = lane; a < na; a += 32) {
-            A32 A = S.earr[ps * g.arr_cap + a];
-            double dl = S.aoff[ps * g.arr_cap + a];
-            if (a == ai) {
-                dl = __dadd_rn(dl, dr.bx);
-                const double xs = S.bx[A.slot], ys = S.by[A.slot];
-                window32(g, c.x, c.y, c.t, c.K, c.ph, c.mf, xs, ys, dist32(c.x, c.y, xs, ys), dl, A.k0, A.E0);
-            }
-            cd[a] = A;
-            co[a] = dl;
-        }
-        ncand = na;
-    } else if (valid && dr.type != 1) {
+    if (valid && dr.type != 1) {
         ncand = cand_arrivals<LAT>(g, S, step, c, 0, dr.type == 0 ? -1 : ps, cd, co);
     }
     __syncwarp();
@@ -615,8 +585,6 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
                     lo = min(lo, A.k0);
                     hi = max(hi, A.k0 + g.n_w);
                 }
-                // an arrival-time move changes one station's variance only
-                if (LAT && dr.type == 4 && io - 1 != ai) continue;
                 lo = max(lo, 0);
                 hi = (long long)hi > g.n_samp ? (int)g.n_samp : hi;
                 T.lo = lo;
@@ -667,12 +635,6 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
             } else if (dr.type == 1) {
                 thr = (double)dr.logu - (S.tabD[n_own] - S.elq[ps]);
                 dlp = S.mm[ps] - g.lb0;
-            } else if (LAT && dr.type == 4) {
-                // symmetric step of one offset: its prior ratio
-                const double a = S.aoff[ps * g.arr_cap + ai], b = co[ai];
-                const double s2 = __dmul_rn(g.sig_a, g.sig_a);
-                dlp = __ddiv_rn(__dsub_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(2.0, s2));
-                thr = (double)dr.logu - dlp;
             } else {
                 const double dm = __dsub_rn(c.m, S.mm[ps]);
                 thr = (double)dr.logu + dm;
@@ -690,7 +652,6 @@ __device__ __noinline__ void prepare_step(const Geo& g, const Dev& d, Sm& S, int
         S.type[sl] = dr.type;
         S.ncand[sl] = ncand;
         S.c[sl] = c;
-        if (LAT) S.ai[sl] = ai;
     }
     __syncwarp();
 }
@@ -825,10 +786,98 @@ __device__ __noinline__ void prepare_pair(const Geo& g, Sm& S, int step, int sl)
     __syncwarp();
 }
 
+// preparation of an arrival-time move (all lanes of warp 0; latent offsets,
+// no staging): one entry of an event's arrival cache (in slot order: the
+// stations it reaches in index order), its offset stepped; the event's
+// arrivals become the candidate's with that one's window recomputed, and
+// the one station whose variance changes is the step's only task
+__device__ __noinline__ void prepare_arrival(const Geo& g, Sm& S, int step, int sl) {
+    const int lane = threadIdx.x & 31;
+    const D32& dr = S.draws[step];
+    const int n_own = S.n_own;
+    A32* cd = S.cand + sl * g.arr_cap;
+    double* co = S.coff + sl * g.arr_cap;
+    T32* tk = S.tasks + sl * g.task_cap;
+    int valid = 0, idx = -1, ps = -1, ai = -1, na = 0;
+    P32 c;
+    clear_p32(c);
+    if (n_own > 0) {
+        idx = pick32(dr.pickw, n_own);
+        ps = S.order[idx];
+        na = S.enarr[ps];
+        if (na > 0) {
+            ai = pick32(dr.pick2, na);
+            c.x = S.mx[ps]; c.y = S.my[ps]; c.t = S.mt[ps]; c.m = S.mm[ps];
+            event_terms32(g, c.t, c.m, c.K, c.ph, c.mf);
+            c.xr = S.exr[ps];
+            c.yr = S.eyr[ps];
+            valid = 1;
+        }
+    }
+    if (valid) {
+        for (int a = lane; a < na; a += 32) {
+            A32 A = S.earr[ps * g.arr_cap + a];
+            double dl = S.aoff[ps * g.arr_cap + a];
+            if (a == ai) {
+                dl = __dadd_rn(dl, dr.bx);
+                const double xs = S.bx[A.slot], ys = S.by[A.slot];
+                window32(g, c.x, c.y, c.t, c.K, c.ph, c.mf, xs, ys, dist32(c.x, c.y, xs, ys), dl, A.k0, A.E0);
+            }
+            cd[a] = A;
+            co[a] = dl;
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        int ntask = 0, units = 0, width = 0;
+        if (valid) {
+            const A32 O = S.earr[ps * g.arr_cap + ai], N = cd[ai];
+            T32 T;
+            T.slot = O.slot;
+            T.row = S.bsta[O.slot];
+            T.has_o = T.has_n = 1;
+            T.k0o = O.k0; T.E0o = O.E0;
+            T.k0n = N.k0; T.E0n = N.E0;
+            T.skip = ps;
+            const int lo = max(min(O.k0, N.k0), 0);
+            const long long h = (long long)max(O.k0, N.k0) + g.n_w;
+            const int hi = h > g.n_samp ? (int)g.n_samp : (int)h;
+            T.lo = lo;
+            T.hi = hi;
+            if (lo < hi) {
+                T.u0 = 0;   // float4 groups [lo/4, ceil(hi/4))
+                units = ((hi + 3) >> 2) - (lo >> 2);
+                width = hi - lo;
+                tk[ntask++] = T;
+            }
+            // symmetric step of one offset: its prior ratio
+            const double a = S.aoff[ps * g.arr_cap + ai], b = co[ai];
+            const double s2 = __dmul_rn(g.sig_a, g.sig_a);
+            const double dlp = __ddiv_rn(__dsub_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(2.0, s2));
+            const double thr = (double)dr.logu - dlp;
+            S.thr[sl] = thr;
+            S.thrf[sl] = (float)thr;
+            S.dlp[sl] = dlp;
+        }
+        S.valid[sl] = valid;
+        S.ntask[sl] = ntask;
+        S.units[sl] = units;
+        S.width[sl] = width;
+        S.idx[sl] = idx;
+        S.type[sl] = dr.type;
+        S.ncand[sl] = na;
+        S.c[sl] = c;
+        S.ai[sl] = ai;
+    }
+    __syncwarp();
+}
+
 // the preparation of step `step` into buffer sl, by the kind of its move
 template <bool STAGE, bool PAIR, bool LAT>
 __device__ __forceinline__ void prepare(const Geo& g, const Dev& d, Sm& S, int step, int sl) {
-    if (PAIR && S.draws[step].type == 3) prepare_pair<LAT>(g, S, step, sl);
+    const int type = S.draws[step].type;
+    if (PAIR && type == 3) prepare_pair<LAT>(g, S, step, sl);
+    else if (LAT && type == 4) prepare_arrival(g, S, step, sl);
     else prepare_step<STAGE, LAT>(g, d, S, step, sl);
 }
 

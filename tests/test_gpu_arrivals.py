@@ -237,3 +237,41 @@ def test_fp32_offsets_give_the_oracles_log_density(cm, orc):
     assert lp_zero == pytest.approx(o.log_density(w.events, None), rel=1e-6)
     assert lp > lp_zero
     m.destroy()
+
+
+def test_fp32_latent_persistent_sweep_matches_colour_by_colour(cm):
+    """The instantiation with latent offsets: one persistent launch per sweep
+    gives the chain (events, offsets, trace, log-density) of the
+    colour-by-colour schedule bit for bit."""
+    w = _f32_world(74)
+    runs = []
+    for schedule in (0, 1):
+        params = cm.make_params(w.params, k_per_phase=32, seed=17, dtype=cm.F32, schedule=schedule, **MIX)
+        m = cm.create_model(w.events, w.stations, w.signals, params)
+        m.set_arrival_offsets(w.offsets)
+        m.partition_and_color(w.params.L, shift_mode=1)
+        ncx = int(np.floor(w.params.W / w.params.L)) + 2
+        m.set_trace(8 * ncx * ncx * 32)
+        m.run_sweeps(8)
+        ev, ids, logp, stats = m.read_state()
+        runs.append((ev, ids, logp, np.sort(m.read_trace(), order=TRACE_KEYS), stats,
+                     m.read_arrival_offsets(len(w.stations))))
+        m.destroy()
+    assert runs[0][4]["arrival"][2] > 10
+    assert runs[0][4]["kernel_launches"] < runs[1][4]["kernel_launches"]
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    assert runs[0][2] == runs[1][2]
+    assert np.array_equal(runs[0][3], runs[1][3])
+    assert np.array_equal(runs[0][5], runs[1][5])
+
+
+def test_batch_refuses_latent_offsets(cm):
+    """A batch runs the kernel without latent offsets: a model with them is
+    refused."""
+    w = _f32_world(75)
+    m = cm.create_model(w.events, w.stations, w.signals,
+                        cm.make_params(w.params, k_per_phase=16, seed=3, dtype=cm.F32, **MIX))
+    m.partition_and_color(w.params.L, 1)
+    with pytest.raises(cm.ChromhError):
+        cm.create_batch([m])
+    m.destroy()

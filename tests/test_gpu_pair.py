@@ -181,3 +181,33 @@ def test_fp32_swapped_pair_reaches_its_true_mode(cm):
             m.destroy()
         hits[shift_mode] = n
     assert hits[1] >= 5 and hits[0] <= 1, hits
+
+
+def test_fp32_pairs_persistent_sweep_matches_colour_by_colour(cm):
+    """The instantiation with joint moves: one persistent launch per sweep
+    (regions waiting only for their lower-colour neighbours) gives the chain
+    of the colour-by-colour schedule bit for bit."""
+    w = _f32_world(63)
+    runs = []
+    for schedule in (0, 1):
+        m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=8, k=32, events=w.events, seed=15, schedule=schedule,
+                                              p_pair=PAIR)
+        runs.append((ev, ids, logp, tr, stats))
+        m.destroy()
+    assert runs[0][4]["pair"][2] > 10
+    assert runs[0][4]["kernel_launches"] < runs[1][4]["kernel_launches"]
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    assert runs[0][2] == runs[1][2]
+    assert np.array_equal(runs[0][3], runs[1][3])
+
+
+def test_batch_refuses_joint_moves(cm):
+    """A batch runs the kernel without joint moves: a model with them is
+    refused."""
+    w = _f32_world(64)
+    m = cm.create_model(w.events, w.stations, w.signals,
+                        cm.make_params(w.params, k_per_phase=16, seed=3, dtype=cm.F32, p_pair=PAIR))
+    m.partition_and_color(w.params.L, 1)
+    with pytest.raises(cm.ChromhError):
+        cm.create_batch([m])
+    m.destroy()

@@ -271,6 +271,37 @@ def test_fp32_precision_at_scale_density(cm, orc):
     m.destroy()
 
 
+def test_fp32_bench_workload_at_full_size(cm, orc):
+    """The bench workload at its full size (4000 x 4000 km, 24 h, 1600
+    stations x 864,000 float32 samples, ~1e4 events, 40 x 40 regions,
+    k = 32), in the launch configuration bench.py times (signals on the
+    device, one persistent launch per sweep), dry run (commit off) from the
+    ground truth for 3 sweeps: every step's type, validity and event count
+    equal the oracle's, and every evaluated change of the log-likelihood
+    (~150,000) is within 1e-4 (to max(|x|, 1)) of the oracle's float64 change
+    for the same (state, candidate)."""
+    w = worldgen.config_scale(seed=1000)
+    sweeps = 3
+    m, ev, ids, logp, stats, tr = run_gpu(cm, w, sweeps=sweeps, k=32, events=w.events, commit=False, seed=29,
+                                          on_device=True)
+    o, oev, oids, otr, odlp = run_oracle(orc, w, sweeps=sweeps, k=32, events=w.events, commit=False, seed=29,
+                                         threads=os.cpu_count() or 1)
+    assert len(tr) == len(otr) > 150000
+    for key in ("sweep", "cell", "step", "type", "n_before", "evaluated"):
+        assert np.array_equal(tr[key], otr[key]), key
+    ev_ = otr["evaluated"] == 1
+    d32, d64 = tr["dll"][ev_], otr["dll"][ev_]
+    err = np.abs(d32 - d64) / np.maximum(np.abs(d64), 1.0)
+    print("full size: %d evaluated, error median %.3g p99 %.3g max %.3g, %d decisions differ"
+          % (err.size, np.median(err), np.quantile(err, 0.99), err.max(),
+             np.count_nonzero(tr["accepted"][ev_] != otr["accepted"][ev_])))
+    assert err.size > 140000
+    assert err.max() <= 1e-4
+    assert np.count_nonzero(tr["accepted"][ev_] != otr["accepted"][ev_]) <= max(2, err.size // 10000)
+    assert np.array_equal(ids, oids) and np.array_equal(ev, oev)
+    m.destroy()
+
+
 @pytest.mark.parametrize("init", ["empty", "truth"])
 def test_fp32_chain_tracks_recomputed_log_density(cm, orc, init):
     """float32 chain with commits: the running log-density (float64 sum of

@@ -447,6 +447,16 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def instance_capacities(p, k: int = K_PER_PHASE):
+    """Capacities of a batched instance from its density: events per region
+    and arrivals per station, mean + 6 sd + slack."""
+    per_region = p.Lambda * p.L * p.L / (p.W * p.W)
+    per_station = p.Lambda * math.pi * p.R_max ** 2 / (p.W * p.W)
+    ev_cap = int(min(512, max(128, per_region + 6 * math.sqrt(per_region) + k + 16)))
+    frz_cap = int(max(64, per_station + 6 * math.sqrt(per_station) + 16))
+    return ev_cap, frz_cap
+
+
 def instance_cost(n_stations: int, p) -> float:
     """Estimated work of one sweep of a batched instance: its regions times k
     steps times the samples a step prices (the stations within R_max of an
@@ -530,12 +540,7 @@ def run_batched(args):
     models, kept, skipped = [], [], []
     for i, w in zip(share, worlds):
         p = w.params
-        # capacities from the instance's density: events per region and
-        # arrivals per station, mean + 6 sd + slack
-        per_region = p.Lambda * p.L * p.L / (p.W * p.W)
-        per_station = p.Lambda * math.pi * p.R_max ** 2 / (p.W * p.W)
-        ev_cap = int(min(512, max(128, per_region + 6 * math.sqrt(per_region) + K_PER_PHASE + 16)))
-        frz_cap = int(max(64, per_station + 6 * math.sqrt(per_station) + 16))
+        ev_cap, frz_cap = instance_capacities(p)
         m = cm.create_model(w.events, w.stations, w.signals,
                             cm.make_params(p, k_per_phase=K_PER_PHASE, seed=CHAIN_SEED + i, dtype=cm.F32,
                                            ev_capacity=ev_cap, frozen_capacity=frz_cap))

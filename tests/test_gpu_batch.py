@@ -167,3 +167,58 @@ def test_batched_instances_match_oracle():
     b.destroy()
     for m in models:
         m.destroy()
+
+
+def test_batched_workload_at_full_size():
+    """All 256 instances of the batched workload (the sizes and worlds
+    bench.py draws, its capacities and its batched persistent launch, k = 32),
+    dry run (commit off) from each instance's ground truth for one sweep:
+    every instance's steps equal the oracle's (move type, validity, event
+    count), and every float32 change of the log-likelihood (~390,000) is
+    within 1e-4 (to max(|x|, 1)) of the oracle's on the same world and
+    seed."""
+    import os
+    import sys
+    import oracle
+    from gpu_helpers import TRACE_KEYS
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    cm = lib()
+    oracle.build()
+    worlds = worldgen.config_batched(256, seed=2000)
+    k = bench.K_PER_PHASE
+    models = []
+    for i, w in enumerate(worlds):
+        ev_cap, frz_cap = bench.instance_capacities(w.params)
+        m = cm.create_model(w.events, w.stations, w.signals,
+                            cm.make_params(w.params, k_per_phase=k, seed=bench.CHAIN_SEED + i, dtype=cm.F32,
+                                           commit=False, ev_capacity=ev_cap, frozen_capacity=frz_cap))
+        m.partition_and_color(w.params.L, shift_mode=1)
+        ncx = int(np.floor(w.params.W / w.params.L)) + 2
+        m.set_trace(ncx * ncx * k)
+        models.append(m)
+    b = cm.create_batch(models)
+    b.run_sweeps(1)
+    b.sync()
+    threads = os.cpu_count() or 1
+    errs, n_dec = [], 0
+    for i, (w, m) in enumerate(zip(worlds, models)):
+        tr = np.sort(m.read_trace(), order=TRACE_KEYS)
+        o = oracle.World(w, k_per_phase=k, seed=bench.CHAIN_SEED + i, commit=False)
+        _, _, otr, _ = o.run_chromatic(w.events, 1, trace_cap=len(tr) + 16, threads=threads)
+        otr = np.sort(otr, order=TRACE_KEYS)
+        assert len(tr) == len(otr), i
+        for key in ("sweep", "cell", "step", "type", "n_before", "evaluated"):
+            assert np.array_equal(tr[key], otr[key]), (i, key)
+        ev_ = otr["evaluated"] == 1
+        errs.append(np.abs(tr["dll"][ev_] - otr["dll"][ev_]) / np.maximum(np.abs(otr["dll"][ev_]), 1.0))
+        n_dec += int(np.count_nonzero(tr["accepted"][ev_] != otr["accepted"][ev_]))
+    b.destroy()
+    for m in models:
+        m.destroy()
+    err = np.concatenate(errs)
+    print("batched, full size: %d evaluated, error median %.3g p99 %.3g max %.3g, %d decisions differ"
+          % (err.size, np.median(err), np.quantile(err, 0.99), err.max(), n_dec))
+    assert err.size > 300000
+    assert err.max() <= 1e-4
+    assert n_dec <= max(2, err.size // 10000)

@@ -104,7 +104,9 @@ typedef struct {
                               magnitude: the other mode for stations near the pair's
                               perpendicular bisector), else both shift by one common Gaussian
                               offset of the move's scales.  0 (the default) turns it off;
-                              p_birth + p_death + p_pair <= 1 */
+                              p_birth + p_death + p_pair <= 1.  In CMH_F32 it needs the
+                              variance reading without staging (likelihood 0, stage_samples
+                              0; else CMH_ERR_ARG), and a batch refuses it */
     /* Latent arrival times (§Generative Model, Event Detections: the
      * arrival is Gaussian around t + d/v).  sig_a > 0 gives every (event, station it
      * reaches) a latent offset delta ~ N(0, sig_a^2), the arrival being t + d/v +
@@ -306,7 +308,8 @@ const char* cmh_strerror(int code);
  *
  * cmh_batch_create: models[0..n_models) must be distinct, partitioned, of
  *   dtype CMH_F32 and one likelihood reading, without staging (stage_samples
- *   0) and with ev_capacity <= 512 (CMH_ERR_ARG otherwise; CMH_ERR_STATE for an unpartitioned or
+ *   0), joint moves (p_pair 0) or latent arrival offsets (sig_a 0), and with
+ *   ev_capacity <= 512 (CMH_ERR_ARG otherwise; CMH_ERR_STATE for an unpartitioned or
  *   failed model).  The batch refers to the models (it does not own them)
  *   and to their current partitions; cuda_stream may be NULL (the batch
  *   creates its own).  Destroy the batch before its models.

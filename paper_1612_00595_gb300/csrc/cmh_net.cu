@@ -45,6 +45,7 @@ constexpr int kKW = 5;         // kernel width
 constexpr int kKC = kC * kKW;  // 320: im2col width
 constexpr int kNPix = 4096;    // 64 x 64 pixels of a tile
 constexpr int kNOut = kNPix + 1 + 4;
+constexpr int kNOutP = (kNOut + 7) & ~7;   // 4104: the BF16 output gradient's rows, zero-padded to whole 16-byte vectors
 constexpr int kF1In = 16 * kC; // 1024
 constexpr int kF1Out = 512;
 constexpr double kTile = 800.0;   // km, side of a tile (8 stations at 100 km)
@@ -436,6 +437,16 @@ __global__ void relu_back(const float* dY, const float* Y, long long n, float* d
 __global__ void to_bf16(const float* x, long long n, __nv_bfloat16* y) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] = __float2bfloat16(x[i]);
+}
+
+// the same for the first `cols` columns of `rows` rows (strides ldx, ldy):
+// the columns of y beyond `cols` are left as they are
+__global__ void to_bf16_rows(const float* x, int rows, int cols, int ldx, __nv_bfloat16* y, int ldy) {
+    const long long n = (long long)rows * cols;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / cols, c = i - r * cols;
+        y[r * ldy + c] = __float2bfloat16(x[r * ldx + c]);
+    }
 }
 
 // partial column sums of a [M][N] matrix (bias gradients): block (32, 8)
@@ -851,14 +862,15 @@ cudaError_t launch_tc(dim3 grid, cudaStream_t s, int M, int N, int K, const __nv
 template <bool TA, bool TB>
 cudaError_t launch_product(dim3 grid, cudaStream_t s, bool vec, int M, int N, int K, const __nv_bfloat16* A,
                            int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc, const float* bias, int relu,
-                           int acc, __nv_bfloat16* Cb, int kc, int a_lin, int a_lout, int b_lin, int b_lout) {
+                           int acc, __nv_bfloat16* Cb, int kc, int a_pad, int a_lin, int a_lout, int b_lin, int b_lout) {
     CUtensorMap ma, mb;
     std::memset(&ma, 0, sizeof(ma));
     std::memset(&mb, 0, sizeof(mb));
     if (!vec)
         return launch_tc<TA, TB, false, false, false>(grid, s, M, N, K, A, lda, B, ldb, C, ldc, bias, relu, acc, Cb,
                                                       kc, 0, 0, 0, 0, ma, mb);
-    const bool ta = !TA && a_lin == 0 && k_tensor_map(&ma, A, M, K, lda, TM);
+    // a zero-padded A is mapped over its padded extent
+    const bool ta = !TA && a_lin == 0 && k_tensor_map(&ma, A, M, a_pad ? (K + 7) & ~7 : K, lda, TM);
     const bool tb = TB && b_lin == 0 && k_tensor_map(&mb, B, N, K, ldb, TN);
     if constexpr (!TA && TB) {
         if (ta && tb)
@@ -880,9 +892,12 @@ cudaError_t launch_product(dim3 grid, cudaStream_t s, bool vec, int M, int N, in
 }
 
 template <bool TA, bool TB>
+// a_pad: every row of A (along its contiguous dimension: M when TA, else K)
+// is zero-padded in memory to a multiple of 8 elements, so 16-byte loads may
+// read past the extent
 cudaError_t gemm(cudaStream_t s, float* ws, int M, int N, int K, const __nv_bfloat16* A, int lda,
                  const __nv_bfloat16* B, int ldb, float* C, int ldc, const float* bias, int relu, int acc,
-                 __nv_bfloat16* Cb, int a_lin = 0, int a_lout = 0, int b_lin = 0, int b_lout = 0) {
+                 __nv_bfloat16* Cb, int a_lin = 0, int a_lout = 0, int b_lin = 0, int b_lout = 0, int a_pad = 0) {
     const int gx = (N + TN - 1) / TN, gy = (M + TM - 1) / TM, tiles = gx * gy;
     int splits = 1, kc = K;
     if (ws && !bias && !relu && !acc && !Cb && ldc == N && tiles < 152) {
@@ -896,15 +911,15 @@ cudaError_t gemm(cudaStream_t s, float* ws, int M, int N, int K, const __nv_bflo
     // 16-byte operand loads when both operands' contiguous dimensions come in
     // whole aligned vectors
     auto al16 = [](const void* p) { return ((unsigned long long)p & 15ULL) == 0; };
-    const bool vec = al16(A) && al16(B) && lda % 8 == 0 && ldb % 8 == 0 && (TA ? M % 8 == 0 : K % 8 == 0) &&
-                     (TB ? K % 8 == 0 : N % 8 == 0);
+    const bool vec = al16(A) && al16(B) && lda % 8 == 0 && ldb % 8 == 0 &&
+                     ((TA ? M % 8 == 0 : K % 8 == 0) || a_pad) && (TB ? K % 8 == 0 : N % 8 == 0);
     const dim3 grid(gx, gy, splits);
     float* out = splits > 1 ? ws : C;
     const float* bs = splits > 1 ? nullptr : bias;
     const int rl = splits > 1 ? 0 : relu, ac = splits > 1 ? 0 : acc;
     __nv_bfloat16* cb = splits > 1 ? nullptr : Cb;
     if ((a_lin > 0 || b_lin > 0) && !vec) return cudaErrorInvalidValue;   // im2col operands need the vector loader
-    cudaError_t e = launch_product<TA, TB>(grid, s, vec, M, N, K, A, lda, B, ldb, out, ldc, bs, rl, ac, cb, kc,
+    cudaError_t e = launch_product<TA, TB>(grid, s, vec, M, N, K, A, lda, B, ldb, out, ldc, bs, rl, ac, cb, kc, a_pad,
                                            a_lin, a_lout, b_lin, b_lout);
     if (e != cudaSuccess) return e;
     if (splits > 1) sum_splits<<<blocks_for((long long)M * N), 256, 0, s>>>(ws, (long long)M * N, splits, C);
@@ -947,14 +962,15 @@ cudaError_t backward(cmh_net* n, int Bn) {
     cudaStream_t s = n->stream;
     cudaError_t e;
     loss_grad<<<Bn, 256, 0, s>>>(n->o, n->label, n->tl, n->ml, Bn, n->dO, n->loss);
-    to_bf16<<<blocks_for((long long)Bn * kNOut), 256, 0, s>>>(n->dO, (long long)Bn * kNOut, n->dOb);
+    // the BF16 output gradient in rows of kNOutP (the padding stays zero)
+    to_bf16_rows<<<blocks_for((long long)Bn * kNOut), 256, 0, s>>>(n->dO, Bn, kNOut, kNOut, n->dOb, kNOutP);
     // FC2: dF2 = dO^T h, dfb2 = colsum dO, dh = dO F2
-    if ((e = gemm<true, false>(s, n->ws, kNOut, kF1Out, Bn, n->dOb, kNOut, n->hb, kF1Out, n->gr + kOffF2, kF1Out, nullptr, 0,
-                               0, nullptr)))
+    if ((e = gemm<true, false>(s, n->ws, kNOut, kF1Out, Bn, n->dOb, kNOutP, n->hb, kF1Out, n->gr + kOffF2, kF1Out,
+                               nullptr, 0, 0, nullptr, 0, 0, 0, 0, 1)))
         return e;
     colsum(s, n->ws, n->dO, Bn, kNOut, n->gr + kOffFb2);
-    if ((e = gemm<false, false>(s, n->ws, Bn, kF1Out, kNOut, n->dOb, kNOut, n->pb + kOffF2, kF1Out, n->dh, kF1Out, nullptr,
-                                0, 0, nullptr)))
+    if ((e = gemm<false, false>(s, n->ws, Bn, kF1Out, kNOut, n->dOb, kNOutP, n->pb + kOffF2, kF1Out, n->dh, kF1Out,
+                                nullptr, 0, 0, nullptr, 0, 0, 0, 0, 1)))
         return e;
     relu_back<<<blocks_for((long long)Bn * kF1Out), 256, 0, s>>>(n->dh, n->h, (long long)Bn * kF1Out, n->dh, n->dhb);
     // FC1: dF1 = dh^T x4, dfb1, dx4 = dh F1 (into dy as [B*16][64])
@@ -1025,12 +1041,12 @@ extern "C" int cmh_net_create(int32_t max_batch, uint64_t seed, void* cuda_strea
     bool ok = n->alloc(&n->p, kNParam) && n->alloc(&n->gr, kNParam) && n->alloc(&n->m1, kNParam) &&
               n->alloc(&n->m2, kNParam) && n->alloc(&n->pb, kNParam) && n->alloc(&n->x0, B * kNL * kNS) &&
               n->alloc(&n->h, B * kF1Out) && n->alloc(&n->hb, B * kF1Out) &&
-              n->alloc(&n->o, B * kNOut) && n->alloc(&n->dO, B * kNOut) && n->alloc(&n->dOb, B * kNOut) &&
+              n->alloc(&n->o, B * kNOut) && n->alloc(&n->dO, B * kNOut) && n->alloc(&n->dOb, B * kNOutP) &&
               n->alloc(&n->dh, B * kF1Out) && n->alloc(&n->dhb, B * kF1Out) && n->alloc(&n->dcol, B * 128 * kKC) &&
               n->alloc(&n->dy, B * 128 * kC) && n->alloc(&n->dyb, B * 128 * kC) && n->alloc(&n->dx, B * 256 * kC) &&
               n->alloc(&n->loss, B) && n->alloc(&n->tl, B) && n->alloc(&n->ml, B) && n->alloc(&n->label, B) && n->alloc(&n->ws, kWsFloats);
     for (int l = 0; l < 4 && ok; ++l) ok = n->alloc(&n->y[l], B * kLin[l + 1] * kC) && n->alloc(&n->yb[l], B * kLin[l + 1] * kC);
-    if (!ok) {
+    if (!ok || cudaMemset(n->dOb, 0, sizeof(__nv_bfloat16) * B * kNOutP) != cudaSuccess) {
         delete n;
         return CMH_ERR_OOM;
     }

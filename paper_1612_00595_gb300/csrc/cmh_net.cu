@@ -407,8 +407,10 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
     if (!ok && tid == 0) atomicExch(err, 1);
 }
 
-// the adjoint of im2col: dX[b][s][c] = sum over (t, k) with 2t - 2 + k = s of dA[(b,t)][k*64+c]
-__global__ void col2im(const float* dA, int Bn, int Lin, int Lout, float* dX) {
+// the adjoint of im2col, dX[b][s][c] = sum over (t, k) with 2t - 2 + k = s
+// of dA[(b,t)][k*64+c], then through the ReLU of the previous layer (output
+// Y): dZ = dX where Y > 0, else 0, and its BF16 copy
+__global__ void col2im_relu(const float* dA, int Bn, int Lin, int Lout, const float* Y, float* dZ, __nv_bfloat16* dZb) {
     const long long n = (long long)Bn * Lin * kC;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(i % kC);
@@ -421,7 +423,9 @@ __global__ void col2im(const float* dA, int Bn, int Lin, int Lout, float* dX) {
             if (t >= Lout) continue;
             v += dA[((long long)b * Lout + t) * kKC + k * kC + c];
         }
-        dX[i] = v;
+        v = Y[i] > 0.f ? v : 0.f;
+        dZ[i] = v;
+        dZb[i] = __float2bfloat16(v);
     }
 }
 
@@ -984,8 +988,8 @@ cudaError_t backward(cmh_net* n, int Bn) {
     for (int l = 3; l >= 0; --l) {
         const int Lin = kLin[l], Lout = kLin[l + 1];
         const long long rows = (long long)Bn * Lout;
-        // through the ReLU of layer l
-        relu_back<<<blocks_for(rows * kC), 256, 0, s>>>(n->dy, n->y[l], rows * kC, n->dy, n->dyb);
+        // through the ReLU of layer l (below the top layer, col2im_relu did it)
+        if (l == 3) relu_back<<<blocks_for(rows * kC), 256, 0, s>>>(n->dy, n->y[l], rows * kC, n->dy, n->dyb);
         // dW = dy^T col (the layer input's im2col matrix read in place), db = colsum dy
         const __nv_bfloat16* in = l == 0 ? n->x0 : n->yb[l - 1];
         if ((e = gemm<true, false>(s, n->ws, kC, kKC, (int)rows, n->dyb, kC, in, 0, n->gr + l * kConvP, kKC, nullptr, 0,
@@ -993,11 +997,13 @@ cudaError_t backward(cmh_net* n, int Bn) {
             return e;
         colsum(s, n->ws, n->dy, (int)rows, kC, n->gr + l * kConvP + kConvW);
         if (l == 0) break;
-        // dcol = dy W, dx = col2im(dcol) (the previous layer's output gradient)
+        // dcol = dy W, dx = col2im(dcol) (the previous layer's output
+        // gradient), through that layer's ReLU
         if ((e = gemm<false, false>(s, n->ws, (int)rows, kKC, kC, n->dyb, kC, n->pb + l * kConvP, kKC, n->dcol, kKC, nullptr,
                                     0, 0, nullptr)))
             return e;
-        col2im<<<blocks_for((long long)Bn * Lin * kC), 256, 0, s>>>(n->dcol, Bn, Lin, Lout, n->dy);
+        col2im_relu<<<blocks_for((long long)Bn * Lin * kC), 256, 0, s>>>(n->dcol, Bn, Lin, Lout, n->y[l - 1], n->dy,
+                                                                          n->dyb);
     }
     return cudaGetLastError();
 }

@@ -227,14 +227,42 @@ __device__ __forceinline__ void rebin_gather_body(const Geo& g, const Dev& d, in
     if (init_n >= 0) {
         collect(0, init_n);
     } else {
+        // the (up to) nine old cells around c: lanes 0..8 read their slices
+        // at once, then the warp scans their events as one flat range (the
+        // collection order does not matter: the events are ranked by id)
         const int ix = c % g.ncx, iy = c / g.ncx;
-        for (int jy = iy - 1; jy <= iy + 1; ++jy) {
-            if (jy < 0 || jy >= g.ncy) continue;
-            for (int jx = ix - 1; jx <= ix + 1; ++jx) {
-                if (jx < 0 || jx >= g.ncx) continue;
+        int s0 = 0, cnt = 0;
+        if (lane < 9) {
+            const int jx = ix - 1 + lane % 3, jy = iy - 1 + lane / 3;
+            if (jx >= 0 && jx < g.ncx && jy >= 0 && jy < g.ncy) {
                 const int oc = jy * g.ncx + jx;
-                collect(old.start[oc], old.count[oc]);
+                s0 = old.start[oc];
+                cnt = old.count[oc];
             }
+        }
+        int incl = cnt;   // inclusive prefix of the nine counts
+        for (int o = 1; o < 16; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(FULL, incl, 8);
+        for (int i0 = 0; i0 < total; i0 += 32) {
+            const int i = i0 + lane, ic = min(i, total - 1);   // every lane shuffles
+            int q = 0;   // the cell holding flat index ic: the first whose prefix exceeds it
+#pragma unroll
+            for (int u = 0; u < 8; ++u) q += ic >= __shfl_sync(FULL, incl, u) ? 1 : 0;
+            const int bq = __shfl_sync(FULL, incl, q > 0 ? q - 1 : 0);
+            const int src = __shfl_sync(FULL, s0, q) + (ic - (q > 0 ? bq : 0));
+            const bool hit = i < total && d.ncell[src] == c;
+            const unsigned bal = __ballot_sync(FULL, hit);
+            if (hit) {
+                const int p = got + __popc(bal & lt);
+                if (p < g.ev_cap) {
+                    bpos[p] = src;
+                    bid[p] = old.id[src];
+                }
+            }
+            got += __popc(bal);
         }
     }
     __syncwarp();

@@ -44,12 +44,13 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr float kDr = 2e-3f;   // km: margin of the region tests
 constexpr float kDm = 1e-5f;   // magnitude units: margin of the m >= 2 test
-constexpr int kThreads32 = 256;
+constexpr int kThreads32 = 288;
 constexpr int kUnroll = 2;     // float4 groups whose loads a pricing thread issues together
 constexpr int kFrozen = -2;    // owner tag of an arrival from a neighbouring region
 constexpr int kMinBlocks32 = 3;   // resident CTAs per SM the kernel is built for
 constexpr int kMaxPix = 256;      // pixels of the learned birth table a region's range may span
-static_assert(kThreads32 <= 256, "the decision reduces the worker warps' partials in a three-level tree");
+static_assert(kThreads32 <= 512, "the decision reduces the worker warps' partials in a four-level tree");
+constexpr int kTree0 = kThreads32 > 256 ? 8 : 4;
 constexpr unsigned kWaitLimit = 1u << 24;   // bounded mbarrier waits
 constexpr int kIv = 8;            // disjoint priced intervals kept per blanket station (unique-sample count)
 
@@ -1668,7 +1669,7 @@ __device__ __forceinline__ void region_rest(const Geo& g, const Dev& d, int cell
         if (wid == 0) {
             // partials of warps 1..7 in lanes 1..7: a three-level tree
             float2 t = (valid && lane > 0 && lane < nw) ? S.redf[lane] : make_float2(0.f, 0.f);
-            for (int o = 4; o > 0; o >>= 1) {
+            for (int o = kTree0; o > 0; o >>= 1) {
                 float2 w2;
                 w2.x = __shfl_xor_sync(FULL, t.x, o);
                 w2.y = __shfl_xor_sync(FULL, t.y, o);

@@ -121,3 +121,20 @@ def test_instance_split_covers_and_balances(n):
     loads = [sum(costs[i] for i in s) for s in shares]
     # largest-first greedy: no share exceeds another by more than one instance
     assert max(loads) - min(loads) <= max(costs)
+
+
+def test_instance_capacities_cover_the_density():
+    """The capacities bench.py gives a batched instance: at least the
+    defaults, growing with the events per region and the arrivals per
+    station, capped at 512 events per region."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import worldgen
+    sizes = worldgen.batched_instances(256, seed=2000)
+    caps = [bench.instance_capacities(p) for _, p in sizes]
+    assert all(ev >= 128 and fz >= 64 for ev, fz in caps)
+    assert all(ev <= 512 for ev, _ in caps)
+    dense = worldgen.ModelParams(W=300.0, T=900.0, Lambda=400.0)
+    ev, fz = bench.instance_capacities(dense)
+    per_region = dense.Lambda * dense.L ** 2 / dense.W ** 2
+    assert ev >= per_region + bench.K_PER_PHASE and fz > 64

@@ -211,3 +211,18 @@ def test_world_rejects_reach_sets_beyond_the_oracle_bound(orc):
     orc.World(w)   # fine without latent arrivals
     with pytest.raises(ValueError):
         orc.World(w, sig_a=1.0)
+
+
+def test_scale_world_with_latent_offsets():
+    """The bench's scale world at a small size with latent offsets: one
+    offset per (event, station it reaches), zero elsewhere, of the stated
+    scale, and the signals they shift differ from the deterministic ones."""
+    w = worldgen.config_scale(seed=11, side_regions=6, T=36000.0, sig_a=2.0)
+    w0 = worldgen.config_scale(seed=11, side_regions=6, T=36000.0)
+    off = w.offsets
+    assert off.shape == (len(w.events), len(w.stations))
+    reach = _reach(w.params, w.events, w.stations)
+    assert np.all(off[~reach] == 0.0) and np.count_nonzero(off[reach]) == reach.sum()
+    assert reach.sum() > 50
+    assert 1.5 < np.std(off[reach]) < 2.5   # +-25%: over 3 sd of the estimate at these counts
+    assert np.array_equal(w.events, w0.events) and not np.array_equal(w.signals, w0.signals)
